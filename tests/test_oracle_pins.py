@@ -1,0 +1,272 @@
+"""Pins of the FP64 CPU oracle against what the paper and mathematics fix.
+
+Each test ties the oracle to something other than itself: numpy / scipy
+routines, closed forms, identities that hold exactly (depth 0/1 FMM == direct
+sum, Sec. 2.2 with Def. 2.1; polynomial reproduction of the interpolant,
+Def. 2.2 / Eq. low-rank-form), the counts of Def. 2.1, symmetry of the
+approximation for a symmetric kernel, invariances, and the exponential error
+decay in p claimed in Sec. 2.2 and Sec. 4.1.  test_oracle_mutations.py shows
+that plausible mistakes planted in the oracle fail these pins.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from paper_1903_02153_gb300 import workloads as W
+
+K_INV_R, K_INV_R2, K_EXP, K_GAUSS, K_POLY, K_CONST = 1, 2, 3, 4, 100, 101
+
+
+def numpy_kernel_matrix(x, y, kid, ell=1.0):
+    d = x[:, None, :] - y[None, :, :]
+    r2 = np.einsum("ijk,ijk->ij", d, d)
+    with np.errstate(divide="ignore"):
+        if kid == K_INV_R:
+            K = np.where(r2 == 0.0, 0.0, 1.0 / np.sqrt(r2))
+        elif kid == K_INV_R2:
+            K = np.where(r2 == 0.0, 0.0, 1.0 / r2)
+        elif kid == K_EXP:
+            K = np.exp(-np.sqrt(r2) / ell)
+        elif kid == K_GAUSS:
+            K = np.exp(-r2 / ell ** 2)
+        elif kid == K_POLY:
+            K = 1.0 + d[..., 0] - 2.0 * d[..., 1] * d[..., 2] + 3.0 * d[..., 0] ** 2 * d[..., 1]
+        else:
+            K = np.ones_like(r2)
+    return K
+
+
+# --- kernels ---------------------------------------------------------------
+
+def test_kernel_closed_forms(oracle):
+    x, y = np.array([1.0, 2.0, 3.0]), np.array([4.0, 6.0, 3.0])   # r = 5
+    assert oracle.kernel(K_INV_R, x, y) == pytest.approx(0.2, rel=1e-15)
+    assert oracle.kernel(K_INV_R2, x, y) == pytest.approx(0.04, rel=1e-15)
+    assert oracle.kernel(K_EXP, x, y, ell=2.0) == pytest.approx(np.exp(-2.5), rel=1e-15)
+    assert oracle.kernel(K_GAUSS, x, y, ell=5.0) == pytest.approx(np.exp(-1.0), rel=1e-15)
+    # d = x - y = (-3, -4, 0): 1 - 3 - 0 + 3*9*(-4)
+    assert oracle.kernel(K_POLY, x, y) == pytest.approx(1 - 3 + 3 * 9 * (-4), rel=1e-15)
+    assert oracle.kernel(K_CONST, x, y) == 1.0
+    # K at r == 0: singular kernels give 0, smooth kernels their value
+    assert oracle.kernel(K_INV_R, x, x) == 0.0
+    assert oracle.kernel(K_INV_R2, x, x) == 0.0
+    assert oracle.kernel(K_EXP, x, x) == 1.0
+    assert oracle.kernel(K_GAUSS, x, x) == 1.0
+
+
+# --- interpolation (Sec. 2.2 nodes, Def. 2.2) -------------------------------
+
+@pytest.mark.parametrize("p", [2, 3, 4, 5, 6, 8, 10])
+def test_cheb_nodes_match_numpy(oracle, p):
+    ref = np.polynomial.chebyshev.chebpts1(p)        # first-kind points, ascending
+    np.testing.assert_allclose(np.sort(oracle.cheb_nodes(p)), ref, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("p", [2, 3, 5, 7])
+def test_lagrange_cardinal_and_partition_of_unity(oracle, p):
+    s = oracle.cheb_nodes(p)
+    for i in range(p):
+        np.testing.assert_allclose(oracle.lagrange_1d(p, s[i]), np.eye(p)[i], atol=1e-14)
+    for x in np.linspace(-1, 1, 13):
+        assert oracle.lagrange_1d(p, x).sum() == pytest.approx(1.0, abs=1e-13)
+
+
+@pytest.mark.parametrize("p", [3, 5, 8])
+def test_lagrange_matches_scipy_barycentric(oracle, p):
+    from scipy.interpolate import BarycentricInterpolator
+    s = oracle.cheb_nodes(p)
+    xs = np.random.default_rng(0).uniform(-1, 1, 9)
+    for i in range(p):
+        yi = np.eye(p)[i]
+        ref = BarycentricInterpolator(s, yi)(xs)
+        got = np.array([oracle.lagrange_1d(p, x)[i] for x in xs])
+        np.testing.assert_allclose(got, ref, atol=1e-12)
+
+
+# --- direct sum (Eq. summation) ---------------------------------------------
+
+@pytest.mark.parametrize("kid,ell", [(K_INV_R, 1.0), (K_INV_R2, 1.0), (K_EXP, 0.3),
+                                     (K_GAUSS, 0.5), (K_POLY, 1.0), (K_CONST, 1.0)])
+def test_direct_matches_numpy_bruteforce(oracle, kid, ell):
+    rng = np.random.default_rng(11)
+    x = rng.random((700, 3))
+    y = np.concatenate([rng.random((500, 3)), x[:50]])   # includes exact coincidences
+    sig = rng.uniform(-1, 1, (y.shape[0], 3))
+    ref = numpy_kernel_matrix(x, y, kid, ell) @ sig
+    got = oracle.direct(x, y, sig, kid, ell)
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_direct_const_kernel_is_sum(oracle):
+    x = W.uniform_points(300)
+    s = W.uniform_sigma(300)
+    np.testing.assert_allclose(oracle.direct(x, x, s, K_CONST), s.sum(), rtol=1e-12)
+
+
+# --- tree: Def. 2.1 ----------------------------------------------------------
+
+def test_neighbor_and_interaction_counts(oracle):
+    assert len(oracle.neighbors(3, 3, 4, 5)) == 27          # 3^3 for an interior box
+    assert len(oracle.neighbors(3, 0, 0, 0)) == 8
+    assert len(oracle.interaction_list(3, 3, 4, 5)) == 189   # 6^3 - 3^3
+    assert len(oracle.interaction_list(1, 0, 1, 0)) == 0     # level 1: all boxes adjacent
+    assert len(oracle.interaction_list(2, 0, 0, 0)) == 4 ** 3 - 2 ** 3
+    offsets = set()
+    for a, b, c in itertools.product(range(2, 6), repeat=3):
+        for nb in oracle.interaction_list(4, a, b, c):
+            offsets.add(tuple(nb - np.array([a, b, c])))
+    assert len(offsets) == 7 ** 3 - 3 ** 3                    # 316 distinct M2L operators
+    assert all(max(abs(o) for o in t) in (2, 3) for t in offsets)
+
+
+def test_interaction_partition_bruteforce(oracle):
+    """Every (target leaf, source leaf) pair is handled exactly once: by P2P if
+    the leaves are adjacent, else by exactly one M2L between ancestors at one
+    level (Fig. 2 caption; Sec. 2.2 closing paragraph)."""
+    D = 3
+    n = 2 ** D
+    ilists = {}
+    for l in range(2, D + 1):
+        m = 2 ** l
+        for a, b, c in itertools.product(range(m), repeat=3):
+            ilists[(l, a, b, c)] = {tuple(v) for v in oracle.interaction_list(l, a, b, c)}
+    for t in itertools.product(range(n), repeat=3):
+        near = {tuple(v) for v in oracle.neighbors(D, *t)}
+        for s in itertools.product(range(n), repeat=3):
+            cover = 1 if s in near else 0
+            for l in range(2, D + 1):
+                ta = tuple(v >> (D - l) for v in t)
+                sa = tuple(v >> (D - l) for v in s)
+                cover += sa in ilists[(l,) + ta]
+            assert cover == 1, (t, s, cover)
+
+
+def test_leaf_binning_rule(oracle):
+    pts = np.array([[0.0, 0.0, 0.0], [1.0, 1.0, 1.0], [0.5, 0.25, 0.125],
+                    [0.124999, 0.999999, 0.5000001]])
+    cells = oracle.leaf_cells(pts, np.zeros(3), 1.0, 3)
+    np.testing.assert_array_equal(cells, [[0, 0, 0], [7, 7, 7], [4, 2, 1], [0, 7, 4]])
+
+
+# --- the FMM (Sec. 2.2) ------------------------------------------------------
+
+@pytest.mark.parametrize("depth", [0, 1])
+@pytest.mark.parametrize("kid", [K_INV_R, K_EXP])
+def test_fmm_depth0_1_equals_direct(oracle, depth, kid):
+    x = W.uniform_points(900, seed=5)
+    s = W.uniform_sigma(900, seed=6)
+    ref = oracle.direct(x, x, s, kid)
+    got = oracle.bbfmm(x, s, kid, p=4, depth=depth)
+    assert oracle.rel_err(got, ref) < 1e-14
+
+
+@pytest.mark.parametrize("p,depth,kind", [(3, 2, "uniform"), (3, 3, "uniform"), (4, 3, "clustered"),
+                                          (5, 2, "clustered"), (5, 3, "uniform")])
+def test_fmm_reproduces_low_degree_polynomial_kernel(oracle, p, depth, kind):
+    """Interpolation with p >= 3 nodes per axis is exact for a kernel of degree
+    <= 2 in each coordinate of x - y (Def. 2.2), and so are M2M / L2L, so the
+    FMM equals the direct sum up to rounding for any tree."""
+    x = W.make_points(kind, 1500, seed=21)
+    s = W.uniform_sigma(1500, nrhs=2, seed=22)
+    ref = oracle.direct(x, x, s, K_POLY)
+    got = oracle.bbfmm(x, s, K_POLY, p=p, depth=depth)
+    assert oracle.rel_err(got, ref) < 1e-12
+
+
+def test_fmm_poly_kernel_not_reproduced_with_too_few_nodes(oracle):
+    # p = 2 interpolates linearly: the quadratic terms are not reproduced
+    x = W.uniform_points(800, seed=3)
+    s = W.uniform_sigma(800, seed=4)
+    ref = oracle.direct(x, x, s, K_POLY)
+    assert oracle.rel_err(oracle.bbfmm(x, s, K_POLY, p=2, depth=3), ref) > 1e-6
+
+
+def test_fmm_nested_interpolation_m2m_equals_p2m(oracle):
+    """M2M(P2M(children)) = P2M(parent): the children's interpolant of the
+    parent's degree-(p-1) basis is exact (Def. 2.2)."""
+    x = W.uniform_points(3000, seed=8)
+    s = W.uniform_sigma(3000, seed=9)
+    lo, side = np.zeros(3), 1.0
+    _, M3, _ = oracle.bbfmm(x, s, K_INV_R, p=4, depth=3, lo=lo, side=side, dump=True)
+    _, M2, _ = oracle.bbfmm(x, s, K_INV_R, p=4, depth=2, lo=lo, side=side, dump=True)
+    np.testing.assert_allclose(M3[2], M2[2], rtol=0, atol=1e-11 * np.abs(M2[2]).max())
+
+
+@pytest.mark.parametrize("kid", [K_INV_R, K_EXP])
+def test_fmm_symmetric_for_symmetric_kernel(oracle, kid):
+    """With targets = sources and a symmetric kernel, P2M and L2P are
+    transposes, M2M and L2L are transposes and each M2L block pair is
+    symmetric, so u^T (K_hat v) = v^T (K_hat u) up to rounding."""
+    x = W.clustered_points(2000, seed=13)
+    rng = np.random.default_rng(14)
+    u, v = rng.standard_normal(2000), rng.standard_normal(2000)
+    Kv = oracle.bbfmm(x, v, kid, p=4, depth=3)
+    Ku = oracle.bbfmm(x, u, kid, p=4, depth=3)
+    assert abs(u @ Kv - v @ Ku) < 1e-12 * np.linalg.norm(u) * np.linalg.norm(Kv)
+    # and the far-field approximation is not trivially exact
+    assert oracle.rel_err(Kv, oracle.direct(x, x, v, kid)) > 1e-10
+
+
+def test_fmm_translation_and_scale_invariance(oracle):
+    x = W.uniform_points(2500, seed=15)
+    s = W.uniform_sigma(2500, seed=16)
+    lo, side = np.zeros(3), 1.0
+    base = oracle.bbfmm(x, s, K_INV_R, p=4, depth=3, lo=lo, side=side)
+    shift = np.array([0.25, -0.5, 1.0])
+    moved = oracle.bbfmm(x + shift, s, K_INV_R, p=4, depth=3, lo=lo + shift, side=side)
+    assert oracle.rel_err(moved, base) < 1e-12
+    # scaling by 2 is exact in binary floating point: 1/r halves, 1/r^2 quarters
+    twice = oracle.bbfmm(2 * x, s, K_INV_R, p=4, depth=3, lo=lo, side=2 * side)
+    np.testing.assert_array_equal(twice, base / 2)
+    base2 = oracle.bbfmm(x, s, K_INV_R2, p=4, depth=3, lo=lo, side=side)
+    twice2 = oracle.bbfmm(2 * x, s, K_INV_R2, p=4, depth=3, lo=lo, side=2 * side)
+    np.testing.assert_array_equal(twice2, base2 / 4)
+    thrice = oracle.bbfmm(3 * x, s, K_INV_R, p=4, depth=3, lo=lo, side=3 * side)
+    assert oracle.rel_err(thrice, base / 3) < 1e-12
+
+
+@pytest.mark.parametrize("kid", [K_INV_R, K_EXP])
+def test_fmm_error_decays_with_p(oracle, kid):
+    """Sec. 2.2 (Chebyshev nodes: O(rho^-p)) and Sec. 4.1 (Fig. err_order):
+    the error against the direct sum falls as p grows (N = 10^4 uniform)."""
+    n = 10_000
+    x = W.uniform_points(n, seed=17)
+    s = W.uniform_sigma(n, seed=18)
+    ref = oracle.direct(x, x, s, kid)
+    errs = [oracle.rel_err(oracle.bbfmm(x, s, kid, p=p, depth=3), ref) for p in range(2, 8)]
+    for a, b in zip(errs, errs[1:]):
+        assert b < a, errs
+    assert errs[-1] < 1e-3 * errs[0], errs
+
+
+def test_fmm_error_magnitude_anchor(oracle):
+    """Table 1 (Sec. 4.2): 1/r, Chebyshev p = 4, uniform points in the unit cube,
+    relative error 2.10e-5 / 2.08e-5 / 2.10e-5.  The paper does not print its
+    weights or points per leaf; with nonnegative weights sigma ~ U(0,1) and
+    ~40 points per leaf the oracle lands on the same figure.  (Zero-mean weights
+    make phi smaller and the relative error about 18x larger.)"""
+    n = 20_000
+    x = W.uniform_points(n, seed=19)
+    s = np.random.default_rng(1).random(n)
+    ref = oracle.direct(x, x, s, K_INV_R)
+    err = oracle.rel_err(oracle.bbfmm(x, s, K_INV_R, p=4, depth=3), ref)
+    assert 1.5e-5 < err < 3.0e-5, err
+
+
+def test_fmm_sampled_targets_match_full_run(oracle):
+    x = W.clustered_points(4000, seed=23)
+    s = W.uniform_sigma(4000, nrhs=2, seed=24)
+    full = oracle.bbfmm(x, s, K_EXP, p=4, depth=4, ell=0.3)
+    idx = np.random.default_rng(25).choice(4000, 150, replace=False)
+    part = oracle.bbfmm(x, s, K_EXP, p=4, depth=4, ell=0.3, sample=idx)
+    np.testing.assert_allclose(part, full[idx], rtol=0, atol=1e-14 * np.abs(full).max())
+
+
+def test_fmm_multiple_rhs_columns_independent(oracle):
+    x = W.uniform_points(1500, seed=26)
+    s = W.uniform_sigma(1500, nrhs=3, seed=27)
+    both = oracle.bbfmm(x, s, K_INV_R, p=4, depth=3)
+    for c in range(3):
+        np.testing.assert_allclose(both[:, c], oracle.bbfmm(x, s[:, c], K_INV_R, p=4, depth=3),
+                                   rtol=0, atol=1e-15 * np.abs(both).max())
