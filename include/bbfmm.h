@@ -1,0 +1,171 @@
+/*
+ * bbfmm.h -- C ABI of the GB300 black-box FMM library (libbbfmm.so).
+ *
+ * The library evaluates phi = K sigma, phi_i = sum_j K(x_i, x_j) sigma_j
+ * (Sec. 1, Eq. summation / Eq. matvec of arXiv 1903.02153), targets = sources,
+ * with the black-box FMM of Sec. 2: a uniform octree (Sec. 2.1, Def. 2.1),
+ * Chebyshev interpolation (Sec. 2.2, Def. 2.2, Eq. low-rank-form), the four
+ * stages P2M/M2M, M2L, L2L/L2P, P2P (Sec. 2.2), SVD-compressed M2L operators
+ * (Sec. 2.5 "Fast M2L translation"), leaf-level operators scaled per level for
+ * homogeneous kernels (Sec. 2.5 "Homogeneous kernel"), and several weight
+ * vectors at once (Sec. 2.5 "Multiple right-hand-sides").  Every stage of a
+ * matvec runs in the library's own CUDA kernels for sm_103a.
+ *
+ * Conventions shared by all entry points:
+ *   - Return value: BBFMM_OK (0) or a negative status below.  No entry point
+ *     throws or aborts; bbfmm_last_error() gives a message for the calling
+ *     thread's last failure.
+ *   - Pointers may be host or device memory where stated; the library asks the
+ *     CUDA runtime which one it got.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *     enqueued on it; an entry point returns before the GPU finishes unless it
+ *     says otherwise.
+ *   - Arrays of several right-hand sides are column-major with leading
+ *     dimension n (column c of sigma starts at sigma + c*n).
+ *   - sigma and phi are indexed in the caller's original point order.
+ */
+#ifndef BBFMM_H
+#define BBFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define BBFMM_OK 0
+#define BBFMM_EINVAL -1    /* invalid argument (sizes, NaN coordinates, null pointers) */
+#define BBFMM_ENOMEM -2    /* device or host allocation failed; nothing leaked */
+#define BBFMM_ECUDA -3     /* a CUDA runtime / driver call failed */
+#define BBFMM_ETIMEOUT -4  /* a device-side wait ran out of iterations (status word) */
+#define BBFMM_EBUSY -5     /* the plan is in use by another thread */
+#define BBFMM_EINTERNAL -6 /* a device-side consistency check failed */
+
+/* kernels K(x, y) = k(|x - y|) (Sec. 1 and Sec. 4 name 1/r and exp(-r)) */
+#define BBFMM_K_INV_R 1        /* 1/r, 0 at r = 0; homogeneous of degree -1 */
+#define BBFMM_K_INV_R2 2       /* 1/r^2, 0 at r = 0; homogeneous of degree -2 */
+#define BBFMM_K_EXP 3          /* exp(-r/ell) (exponential covariance) */
+#define BBFMM_K_GAUSS 4        /* exp(-(r/ell)^2) */
+#define BBFMM_K_TEST_POLY 100  /* 1 + d1 - 2 d2 d3 + 3 d1^2 d2, d = x - y: exact for p >= 3 */
+#define BBFMM_K_TEST_CONST 101 /* 1 */
+
+/* arithmetic of the M2L stage (every other stage computes in FP32) */
+#define BBFMM_PREC_FP32 0   /* FP32 FMA on the CUDA cores */
+#define BBFMM_PREC_TF32 1   /* tensor cores, one TF32 pass, FP32 accumulation */
+#define BBFMM_PREC_TF32X3 2 /* tensor cores, 3-pass split TF32 (hi*hi + hi*lo + lo*hi) */
+#define BBFMM_PREC_BF16X3 3 /* tensor cores, 3-pass split BF16 (hi*hi + hi*lo + lo*hi) */
+
+typedef struct bbfmm_plan_s *bbfmm_plan_t; /* opaque; owned by the library */
+
+typedef struct {
+    double ell;        /* kernel length scale for BBFMM_K_EXP / _GAUSS (default 1) */
+    double svd_eps;    /* keep singular values >= svd_eps * sigma_max of the M2L
+                          operators (Sec. 2.5 "SVD truncation error"); default 1e-7;
+                          0 disables compression (rank = p^3) */
+    int precision;     /* BBFMM_PREC_* (default BBFMM_PREC_FP32) */
+    int domain_given;  /* 1: use lo/side below; 0: bounding cube of the points */
+    double lo[3];      /* lower corner of the cubical domain */
+    double side;       /* side length of the domain (> 0) */
+    int max_nrhs;      /* largest nrhs a matvec on this plan may use (default 1) */
+    int reserved[7];   /* zero */
+} bbfmm_opts;
+
+typedef struct {
+    int64_t n;          /* points */
+    int depth;          /* tree depth D: 8^D leaves, M2L on levels 2..D */
+    int order;          /* Chebyshev nodes per axis p */
+    int rank;           /* rank r of the compressed M2L operators */
+    int kernel;         /* BBFMM_K_* */
+    int precision;      /* BBFMM_PREC_* */
+    int max_nrhs;
+    double lo[3], side; /* domain actually used */
+    int64_t device_bytes; /* device memory held by the plan */
+    int64_t nonempty_leaves;
+    int64_t max_leaf_points;
+    int64_t p2p_pairs;  /* near-field kernel evaluations per right-hand side */
+    int64_t m2l_pairs;  /* M2L translations per right-hand side (dense grid) */
+    int reserved[8];
+} bbfmm_info;
+
+/* Fill *opts with the defaults listed above. */
+void bbfmm_default_opts(bbfmm_opts *opts);
+
+/*
+ * bbfmm_plan: build the tree and the operators for a point set (the
+ * H2_3D_Tree constructor + buildFMMTree + FMMDistribute of Sec. 3).
+ *   points:     n x 3 row-major FP64 coordinates, host or device; copied.
+ *   n:          1 <= n < 2^31.
+ *   kernel_id:  BBFMM_K_*.
+ *   cheb_order: p, Chebyshev nodes per axis (Sec. 2.2), 2..10.
+ *   depth:      D, 0..8; leaves are the 8^D boxes of level D.
+ *   opts:       NULL = defaults.
+ *   stream:     the plan's device work (tree build, uploads) runs on it; the
+ *               call synchronizes the stream before returning.
+ *   out:        receives the plan.
+ * Errors: EINVAL (bad sizes, NaN/inf coordinates, points outside a given
+ * domain by more than rounding), ENOMEM (device memory; partial allocations
+ * are released), ECUDA.
+ */
+int bbfmm_plan(const double *points, int64_t n, int kernel_id, int cheb_order, int depth,
+               const bbfmm_opts *opts, void *stream, bbfmm_plan_t *out);
+
+/*
+ * bbfmm_matvec: phi = K_hat sigma (Sec. 2.2, all four stages).
+ *   sigma: n x nrhs column-major FP32, host or device; read only.
+ *   phi:   n x nrhs column-major FP32, host or device; overwritten.
+ *   nrhs:  1..opts.max_nrhs of the plan.
+ * Device buffers: the call only enqueues work on `stream`.  Host buffers: the
+ * call copies sigma in and phi out through the plan's device buffers on
+ * `stream` and synchronizes it before returning.
+ * A plan runs one matvec at a time: concurrent calls on one plan from several
+ * threads return EBUSY; calls on one plan on different streams must be ordered
+ * by the caller.  Errors: EINVAL, EBUSY, ECUDA.
+ */
+int bbfmm_matvec(bbfmm_plan_t plan, const float *sigma, float *phi, int nrhs, void *stream);
+
+/* Release a plan (NULL is a no-op).  Synchronizes the device first. */
+int bbfmm_destroy(bbfmm_plan_t plan);
+
+/* Message for the calling thread's last failing call ("" if none). */
+const char *bbfmm_last_error(void);
+
+/* Sizes and counts of a plan. */
+int bbfmm_plan_info(bbfmm_plan_t plan, bbfmm_info *info);
+
+/*
+ * bbfmm_get_coefficients: copy the coefficients of the last matvec at one
+ * level to host memory, for stage-by-stage checks.
+ *   which: 0 = multipole M (Sec. 2.2 upward pass), 1 = local F after the
+ *          downward pass at that level (Sec. 2.2 items 2-3).
+ *   level: 2..D.
+ *   out:   host, 8^level x nrhs x p^3 FP32, boxes in lexicographic order
+ *          (a + 2^l (b + 2^l c)), node index i1 + p i2 + p^2 i3.
+ * Synchronizes the device.  Errors: EINVAL.
+ */
+int bbfmm_get_coefficients(bbfmm_plan_t plan, int which, int level, int nrhs, float *out);
+
+/*
+ * bbfmm_get_leaf_cells: the leaf cell (a, b, c) the plan assigned to each
+ * point, in the caller's point order (FMMDistribute, Sec. 3).
+ *   out: host, n x 3 int32.  Synchronizes the device.
+ */
+int bbfmm_get_leaf_cells(bbfmm_plan_t plan, int32_t *out);
+
+/*
+ * bbfmm_stage_times: device milliseconds of each stage of the last matvec,
+ * measured with CUDA events on the matvec's streams when the plan was built
+ * with timing on (see bbfmm_set_timing).  out[0..7] = gather, upward (P2M +
+ * M2M + compress), M2L, downward (decompress + L2L), L2P, P2P, combine,
+ * whole matvec.  Synchronizes the device.
+ */
+int bbfmm_stage_times(bbfmm_plan_t plan, float *out);
+
+/* Turn per-stage event timing on (1) or off (0) for later matvecs. */
+int bbfmm_set_timing(bbfmm_plan_t plan, int on);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BBFMM_H */

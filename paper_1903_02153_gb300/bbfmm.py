@@ -1,0 +1,237 @@
+"""Thin ctypes binding of include/bbfmm.h (argument marshalling only).
+
+Every function keeps the C name and calls straight into libbbfmm.so; every
+stage of a matvec runs in the library's CUDA kernels.  There is no other code
+path: if the library is missing, ``lib()`` raises.
+
+Tensors are PyTorch CUDA tensors (device memory and streams only) or numpy /
+pinned host arrays; the library finds out which from the pointer.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libbbfmm.so")
+
+BBFMM_OK, BBFMM_EINVAL, BBFMM_ENOMEM, BBFMM_ECUDA = 0, -1, -2, -3
+BBFMM_ETIMEOUT, BBFMM_EBUSY, BBFMM_EINTERNAL = -4, -5, -6
+BBFMM_K_INV_R, BBFMM_K_INV_R2, BBFMM_K_EXP, BBFMM_K_GAUSS = 1, 2, 3, 4
+BBFMM_K_TEST_POLY, BBFMM_K_TEST_CONST = 100, 101
+BBFMM_PREC_FP32, BBFMM_PREC_TF32, BBFMM_PREC_TF32X3, BBFMM_PREC_BF16X3 = 0, 1, 2, 3
+
+PRECISIONS = {"fp32": BBFMM_PREC_FP32, "tf32": BBFMM_PREC_TF32, "tf32x3": BBFMM_PREC_TF32X3,
+              "bf16x3": BBFMM_PREC_BF16X3}
+
+EXPORTED = ["bbfmm_default_opts", "bbfmm_plan", "bbfmm_matvec", "bbfmm_destroy",
+            "bbfmm_last_error", "bbfmm_plan_info", "bbfmm_get_coefficients",
+            "bbfmm_get_leaf_cells", "bbfmm_stage_times", "bbfmm_set_timing"]
+
+
+class bbfmm_opts(ctypes.Structure):
+    _fields_ = [("ell", ctypes.c_double), ("svd_eps", ctypes.c_double),
+                ("precision", ctypes.c_int), ("domain_given", ctypes.c_int),
+                ("lo", ctypes.c_double * 3), ("side", ctypes.c_double),
+                ("max_nrhs", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+
+
+class bbfmm_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("depth", ctypes.c_int), ("order", ctypes.c_int),
+                ("rank", ctypes.c_int), ("kernel", ctypes.c_int), ("precision", ctypes.c_int),
+                ("max_nrhs", ctypes.c_int), ("lo", ctypes.c_double * 3), ("side", ctypes.c_double),
+                ("device_bytes", ctypes.c_int64), ("nonempty_leaves", ctypes.c_int64),
+                ("max_leaf_points", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64),
+                ("m2l_pairs", ctypes.c_int64), ("reserved", ctypes.c_int * 8)]
+
+
+class BBFMMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("bbfmm status %d: %s" % (status, msg))
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libbbfmm.so (built by paper_1903_02153_gb300.build.build())."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libbbfmm.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+            L = ctypes.CDLL(LIB_PATH)
+            vp, i64, i32, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+            L.bbfmm_default_opts.argtypes = [ctypes.POINTER(bbfmm_opts)]
+            L.bbfmm_default_opts.restype = None
+            L.bbfmm_plan.argtypes = [vp, i64, i32, i32, i32, ctypes.POINTER(bbfmm_opts), vp,
+                                     ctypes.POINTER(vp)]
+            L.bbfmm_plan.restype = i32
+            L.bbfmm_matvec.argtypes = [vp, vp, vp, i32, vp]
+            L.bbfmm_matvec.restype = i32
+            L.bbfmm_destroy.argtypes = [vp]
+            L.bbfmm_destroy.restype = i32
+            L.bbfmm_last_error.argtypes = []
+            L.bbfmm_last_error.restype = ctypes.c_char_p
+            L.bbfmm_plan_info.argtypes = [vp, ctypes.POINTER(bbfmm_info)]
+            L.bbfmm_plan_info.restype = i32
+            L.bbfmm_get_coefficients.argtypes = [vp, i32, i32, i32, vp]
+            L.bbfmm_get_coefficients.restype = i32
+            L.bbfmm_get_leaf_cells.argtypes = [vp, vp]
+            L.bbfmm_get_leaf_cells.restype = i32
+            L.bbfmm_stage_times.argtypes = [vp, vp]
+            L.bbfmm_stage_times.restype = i32
+            L.bbfmm_set_timing.argtypes = [vp, i32]
+            L.bbfmm_set_timing.restype = i32
+            _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != BBFMM_OK:
+        raise BBFMMError(st, bbfmm_last_error())
+    return st
+
+
+def _ptr(x):
+    """Raw pointer of a torch tensor or numpy array (must be contiguous)."""
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not (x.flags.c_contiguous or x.flags.f_contiguous):
+            raise ValueError("array must be contiguous")
+        return ctypes.c_void_p(x.ctypes.data)
+    raise TypeError(type(x))
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return ctypes.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def bbfmm_last_error() -> str:
+    return lib().bbfmm_last_error().decode()
+
+
+def bbfmm_default_opts() -> bbfmm_opts:
+    o = bbfmm_opts()
+    lib().bbfmm_default_opts(ctypes.byref(o))
+    return o
+
+
+def bbfmm_plan(points, kernel_id, cheb_order, depth, opts=None, stream=None):
+    """points: (n, 3) float64 (torch CUDA tensor or numpy).  Returns a handle."""
+    n = int(points.shape[0])
+    h = ctypes.c_void_p()
+    _check(lib().bbfmm_plan(_ptr(points), n, int(kernel_id), int(cheb_order), int(depth),
+                            ctypes.byref(opts) if opts is not None else None, _stream(stream),
+                            ctypes.byref(h)))
+    return h
+
+
+def bbfmm_matvec(plan, sigma, phi, nrhs=1, stream=None):
+    """sigma, phi: n x nrhs column-major float32 (a torch tensor of shape
+    (nrhs, n), or numpy arrays); phi is overwritten."""
+    return _check(lib().bbfmm_matvec(plan, _ptr(sigma), _ptr(phi), int(nrhs), _stream(stream)))
+
+
+def bbfmm_destroy(plan):
+    return _check(lib().bbfmm_destroy(plan))
+
+
+def bbfmm_plan_info(plan) -> bbfmm_info:
+    info = bbfmm_info()
+    _check(lib().bbfmm_plan_info(plan, ctypes.byref(info)))
+    return info
+
+
+def bbfmm_get_coefficients(plan, which, level, nrhs, order):
+    out = np.zeros((8 ** level, nrhs, order ** 3), dtype=np.float32)
+    _check(lib().bbfmm_get_coefficients(plan, int(which), int(level), int(nrhs), _ptr(out)))
+    return out
+
+
+def bbfmm_get_leaf_cells(plan, n):
+    out = np.zeros((n, 3), dtype=np.int32)
+    _check(lib().bbfmm_get_leaf_cells(plan, _ptr(out)))
+    return out
+
+
+def bbfmm_set_timing(plan, on=True):
+    return _check(lib().bbfmm_set_timing(plan, 1 if on else 0))
+
+
+def bbfmm_stage_times(plan):
+    out = np.zeros(8, dtype=np.float32)
+    _check(lib().bbfmm_stage_times(plan, _ptr(out)))
+    return out
+
+
+STAGES = ["gather", "upward", "m2l", "downward", "l2p", "p2p", "combine", "total"]
+
+
+class Plan:
+    """Owning wrapper: ``Plan(points, kernel, p, depth, ...)``, then
+    ``plan.matvec(sigma)`` with sigma a CUDA tensor (n,) or (nrhs, n)."""
+
+    def __init__(self, points, kernel, order, depth, ell=1.0, svd_eps=1e-7, precision="fp32",
+                 domain=None, max_nrhs=1, stream=None):
+        import torch
+        o = bbfmm_default_opts()
+        o.ell = float(ell)
+        o.svd_eps = float(svd_eps)
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        o.max_nrhs = int(max_nrhs)
+        if domain is not None:
+            lo, side = domain
+            o.domain_given = 1
+            for d in range(3):
+                o.lo[d] = float(lo[d])
+            o.side = float(side)
+        if isinstance(points, np.ndarray):
+            points = np.ascontiguousarray(points, dtype=np.float64)
+        elif points.dtype != torch.float64:
+            points = points.to(torch.float64)
+        self.n = int(points.shape[0])
+        self.order = order
+        self.depth = depth
+        self.handle = bbfmm_plan(points, kernel, order, depth, o, stream)
+
+    def info(self):
+        return bbfmm_plan_info(self.handle)
+
+    def matvec(self, sigma, out=None, stream=None):
+        import torch
+        nrhs = 1 if sigma.dim() == 1 else int(sigma.shape[0])
+        sigma = sigma.contiguous()
+        if out is None:
+            out = torch.empty_like(sigma)
+        bbfmm_matvec(self.handle, sigma, out, nrhs, stream)
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            bbfmm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,241 @@
+// bbfmm_internal.h -- data layout, plan structure and kernel entry points of
+// the GB300 black-box FMM library.  Host code and device code both include it.
+//
+// Layout of one plan in device memory (N points, depth D, p nodes per axis,
+// p3 = p^3 coefficients per box, r = rank of the compressed M2L operators,
+// R = number of right-hand sides):
+//
+//   pts      [N] float4   leaf-local coordinates (x-lo)/h_D - (cell + 1/2),
+//                          points sorted by the Morton index of their leaf
+//   perm     [N] int      original index of the sorted point
+//   leaf_off [8^D + 1]    first sorted point of each leaf (Morton order)
+//   chunks   [nchunks]    near-field work items (leaf, first point, count <= 32)
+//   M_l, F_l [8^l][R][p3] multipole / local coefficients, boxes in Morton order
+//   Mt_l     [8][H+2][H][H][R][rp]  compressed multipoles, H = 2^(l-1):
+//                          split by box parity (octant o = x&1 | (y&1)<<1 | (z&1)<<2)
+//                          and indexed by the parent cell (X, Y, Z) = (x, y, z) >> 1,
+//                          with one zero slab below and above in Z
+//   Ft_l     [8][H][H][H][R][rp]    compressed local coefficients (M2L output)
+//
+// The parity split makes the sources of one M2L offset, for a block of targets
+// of one octant, a block of consecutive parent cells of one source octant.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/bbfmm.h"
+
+namespace bbfmm {
+
+constexpr int kMaxP = 10;
+constexpr int kMaxDepth = 8;
+constexpr int kNumOffsets = 316;      // 7^3 - 3^3 distinct M2L offsets (Sec. 2.2, Thm. 2.1)
+constexpr int kOffsetsPerClass = 189; // 6^3 - 3^3 interaction-list boxes (Def. 2.1)
+constexpr int kChunk = 32;            // near-field targets per warp
+
+// status word bits written by device-side checks
+constexpr int kStatusBounds = 1;
+constexpr int kStatusTimeout = 2;
+
+// ---------------------------------------------------------------------------
+// Morton / cell helpers (x in bit 0 of every 3-bit group)
+__host__ __device__ inline uint32_t spread3(uint32_t v)
+{
+    v &= 0x3ff;
+    v = (v | (v << 16)) & 0x030000ff;
+    v = (v | (v << 8)) & 0x0300f00f;
+    v = (v | (v << 4)) & 0x030c30c3;
+    v = (v | (v << 2)) & 0x09249249;
+    return v;
+}
+__host__ __device__ inline uint32_t compact3(uint32_t v)
+{
+    v &= 0x09249249;
+    v = (v | (v >> 2)) & 0x030c30c3;
+    v = (v | (v >> 4)) & 0x0300f00f;
+    v = (v | (v >> 8)) & 0x030000ff;
+    v = (v | (v >> 16)) & 0x000003ff;
+    return v;
+}
+__host__ __device__ inline uint32_t morton3(uint32_t x, uint32_t y, uint32_t z)
+{
+    return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
+}
+__host__ __device__ inline void demorton3(uint32_t m, int &x, int &y, int &z)
+{
+    x = (int)compact3(m);
+    y = (int)compact3(m >> 1);
+    z = (int)compact3(m >> 2);
+}
+
+// row offset (in floats) of box (x, y, z), right-hand side c, in the
+// parity-split layouts at level l (H = 2^(l-1), padZ = 1 for Mt, 0 for Ft)
+__host__ __device__ inline int64_t parity_row(int x, int y, int z, int c, int H, int padZ, int R)
+{
+    int o = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
+    int64_t Zs = H + 2 * padZ;
+    int64_t cell = (((int64_t)o * Zs + (z >> 1) + padZ) * H + (y >> 1)) * H + (x >> 1);
+    return cell * R + c;
+}
+
+// ---------------------------------------------------------------------------
+// Host FP64 operators (operators.cpp)
+struct HostOps {
+    int kernel = 0, p = 0, p3 = 0, r = 0, rank_u = 0, rank_v = 0;
+    double ell = 1.0, eps = 0.0;
+    int hom_degree = 0;         // m of K(a x, a y) = a^m K(x, y); 0 = not homogeneous
+    std::vector<double> nodes;  // Chebyshev nodes s_k, k = 0..p-1
+    std::vector<double> wbary;  // 1 / prod_{m != k} (s_k - s_m)
+    std::vector<double> S;      // S[o][i][j] = l_i((s_j + 2o - 1) / 2), o = 0, 1
+    // per operator level: (one level if homogeneous, else one per tree level 2..D)
+    std::vector<double> h;               // box side of the level the operators were made for
+    std::vector<std::vector<double>> U;  // p3 x r row-major
+    std::vector<std::vector<double>> V;  // p3 x r row-major
+    std::vector<std::vector<double>> C;  // 316 x r x r: C[t] = U^T K^(t) V
+    std::vector<std::vector<double>> sv; // singular values of the fat operator matrix
+};
+
+// offset index 0..315 of t = (tx, ty, tz) in [-3,3]^3 \ [-1,1]^3, or -1
+__host__ __device__ inline int offset_index(int tx, int ty, int tz)
+{
+    if (tx >= -1 && tx <= 1 && ty >= -1 && ty <= 1 && tz >= -1 && tz <= 1)
+        return -1;
+    int idx = 0;
+    for (int c = -3; c <= 3; ++c)
+        for (int b = -3; b <= 3; ++b)
+            for (int a = -3; a <= 3; ++a) {
+                if (a >= -1 && a <= 1 && b >= -1 && b <= 1 && c >= -1 && c <= 1)
+                    continue;
+                if (a == tx && b == ty && c == tz)
+                    return idx;
+                ++idx;
+            }
+    return -1;
+}
+
+std::shared_ptr<HostOps> build_host_ops(int kernel, double ell, int p, double eps, int depth,
+                                        double side, std::string &err);
+double kernel_value_host(int kernel, double ell, double d0, double d1, double d2);
+
+// interpolation tables passed by value to the transfer kernels
+struct InterpTables {
+    float nodes[kMaxP];
+    float wbary[kMaxP];
+    float S[2][kMaxP][kMaxP]; // S[o][i][j] = l_i((s_j + 2o - 1)/2)
+};
+InterpTables make_interp_tables(const HostOps &h);
+
+// ---------------------------------------------------------------------------
+// Device operator set, uploaded once per host operator set
+struct DevOps {
+    std::shared_ptr<HostOps> host;
+    int nlev = 0;            // operator levels
+    int r = 0, rp = 0;       // rank, row pitch (floats) of r-vectors
+    int rows64 = 0;          // r rounded up to 64 (FP32 M2L tile rows)
+    int p3p = 0;             // p3 rounded up to 16
+    std::vector<float *> V;  // [p3][rp]    compress weights
+    std::vector<float *> Ut; // [r][p3p]    decompress weights (U transposed)
+    std::vector<float *> C;  // [316][rows64][rp]
+    std::vector<float *> Chi, Clo; // split copies for the tensor-core M2L (hi/lo)
+    int64_t bytes = 0;
+    ~DevOps();
+};
+
+// ---------------------------------------------------------------------------
+// Plan
+struct Level {
+    float *M = nullptr, *Mt = nullptr, *Ft = nullptr, *F = nullptr;
+    float *Mt_hi = nullptr, *Mt_lo = nullptr;
+};
+
+struct Stage { // indices into Plan::ev
+    enum { Start = 0, Gather, Up, M2L, Down, L2P, P2P, Combine, NumEv };
+};
+
+struct bbfmm_plan_impl {
+    int64_t n = 0;
+    int D = 0, p = 0, p3 = 0, kernel = 0, precision = 0, max_nrhs = 1;
+    double ell = 1.0, lo[3] = {0, 0, 0}, side = 1.0, eps = 1e-7;
+    int device = 0;
+
+    // tree
+    float4 *pts = nullptr;
+    int *perm = nullptr;
+    int *leaf_off = nullptr;
+    int4 *chunks = nullptr;
+    int nchunks = 0;
+    int64_t nonempty_leaves = 0, max_leaf = 0, p2p_pairs = 0, m2l_pairs = 0;
+
+    // operators
+    std::shared_ptr<DevOps> ops;
+    InterpTables interp;
+
+    // work buffers
+    Level lev[kMaxDepth + 1];
+    float *sigma_s = nullptr, *phi_far = nullptr, *phi_near = nullptr;
+    float *io_sigma = nullptr, *io_phi = nullptr; // staging for host sigma / phi
+    int *status = nullptr;                        // device status word
+
+    std::vector<void *> allocations;
+    int64_t bytes = 0;
+
+    cudaStream_t side_stream = nullptr; // near field runs here, concurrent with the far field
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool timing = false;
+    cudaEvent_t ev[Stage::NumEv] = {};
+    cudaEvent_t ev_p2p0 = nullptr, ev_p2p1 = nullptr;
+    int last_nrhs = 0;
+    std::atomic<int> busy{0};
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (each checks its arguments and returns a cudaError_t)
+// tree.cu
+cudaError_t launch_domain_minmax(const double *pts, int64_t n, double *d_minmax, cudaStream_t s);
+cudaError_t launch_bin_points(const double *pts, int64_t n, const double *lo, double side, int D,
+                              uint32_t *keys, int *vals, int *bad, cudaStream_t s);
+cudaError_t radix_sort_pairs(uint32_t *keys, int *vals, uint32_t *keys_tmp, int *vals_tmp, int64_t n,
+                             int key_bits, int *scratch, int64_t scratch_ints, cudaStream_t s);
+int64_t radix_sort_scratch_ints(int64_t n);
+cudaError_t launch_leaf_offsets(const uint32_t *keys, int64_t n, int64_t nleaf, int *leaf_off,
+                                cudaStream_t s);
+cudaError_t launch_local_coords(const double *pts, const int *sorted_vals, int64_t n, const double *lo,
+                                double side, int D, float4 *local, int *perm, cudaStream_t s);
+cudaError_t build_chunks(const int *leaf_off, int64_t nleaf, int *scratch_counts, int4 **chunks_out,
+                         int *nchunks_out, int64_t *bytes_out, cudaStream_t s);
+cudaError_t exclusive_scan_int(const int *in, int *out, int64_t n, int *block_sums, cudaStream_t s);
+int64_t scan_scratch_ints(int64_t n);
+
+// transfers.cu
+cudaError_t launch_gather_sigma(const float *sigma, const int *perm, int64_t n, int nrhs, float *out,
+                                cudaStream_t s);
+cudaError_t launch_p2m(const InterpTables &T, const float4 *pts, const float *sig, const int *leaf_off, int64_t n, int D, int p,
+                       int nrhs, float *M, cudaStream_t s);
+cudaError_t launch_m2m(const InterpTables &T, const float *Mchild, float *Mparent, int lparent, int p, int nrhs, cudaStream_t s);
+cudaError_t launch_l2l(const InterpTables &T, const float *Fparent, float *Fchild, int lparent, int p, int nrhs, cudaStream_t s);
+cudaError_t launch_compress(const float *M, const float *V, float *Mt, int l, int p3, int r, int rp,
+                            int nrhs, cudaStream_t s);
+cudaError_t launch_decompress(const float *Ft, const float *Ut, float *F, int l, int p3, int p3p, int r,
+                              int rp, int nrhs, bool accumulate, cudaStream_t s);
+cudaError_t launch_l2p(const InterpTables &T, const float4 *pts, const float *F, const int *leaf_off, int64_t n, int D, int p,
+                       int nrhs, float *phi_far, cudaStream_t s);
+cudaError_t launch_combine(const float *phi_far, const float *phi_near, const int *perm, int64_t n,
+                           int nrhs, float *phi, cudaStream_t s);
+// m2l_fp32.cu
+cudaError_t launch_m2l_fp32(const float *Mt, const float *C, float *Ft, int l, int r, int rp, int rows64,
+                            int nrhs, float scale, cudaStream_t s);
+// p2p.cu
+cudaError_t launch_p2p(const float4 *pts, const float *sig, const int *leaf_off, const int4 *chunks,
+                       int nchunks, int64_t n, int D, int kernel, double ell, double h, int nrhs,
+                       float *phi_near, cudaStream_t s);
+
+} // namespace bbfmm
+
+struct bbfmm_plan_s : bbfmm::bbfmm_plan_impl {};

@@ -1,0 +1,676 @@
+// capi.cu -- the C ABI of include/bbfmm.h: plan construction (tree build on
+// the device, FP64 operators on the host, buffer layout), the matvec driver
+// that enqueues the four stages of Sec. 2.2 (Alg. 1 as level-synchronous
+// kernels, near field on a forked stream), and introspection helpers.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <tuple>
+
+#include "bbfmm_internal.h"
+
+namespace bbfmm {
+
+cudaError_t launch_m2l(bbfmm_plan_impl *P, int l, int nrhs, cudaStream_t s); // m2l_tc.cu
+
+static thread_local std::string g_last_error;
+
+static int fail(int status, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return status;
+}
+
+#define CUDA_TRY(call)                                                                                         \
+    do {                                                                                                       \
+        cudaError_t e_ = (call);                                                                               \
+        if (e_ != cudaSuccess)                                                                                 \
+            return fail(e_ == cudaErrorMemoryAllocation ? BBFMM_ENOMEM : BBFMM_ECUDA, "%s: %s (%s:%d)", #call, \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                                           \
+    } while (0)
+
+static bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// ---------------------------------------------------------------------------
+// operator cache: one device copy per (kernel, ell, p, eps, depth, side)
+DevOps::~DevOps()
+{
+    for (auto *v : {&V, &Ut, &C, &Chi, &Clo})
+        for (float *ptr : *v)
+            if (ptr)
+                cudaFree(ptr);
+}
+
+typedef std::tuple<int, double, int, double, int, double, int> OpsKey;
+static std::mutex g_ops_mu;
+static std::map<OpsKey, std::weak_ptr<DevOps>> g_ops_cache;
+
+void split_tf32(const float *in, float *hi, float *lo, int64_t n); // m2l_tc.cu (host helper)
+
+static int get_ops(int kernel, double ell, int p, double eps, int depth, double side, int device,
+                   std::shared_ptr<DevOps> &out)
+{
+    // homogeneous kernels depend on the domain only through h_D
+    double key_side = side;
+    int key_depth = depth;
+    if (kernel == BBFMM_K_INV_R || kernel == BBFMM_K_INV_R2) {
+        key_side = side / (double)(1LL << depth);
+        key_depth = 0;
+    }
+    OpsKey key(kernel, ell, p, eps, key_depth, key_side, device);
+    std::lock_guard<std::mutex> g(g_ops_mu);
+    auto it = g_ops_cache.find(key);
+    if (it != g_ops_cache.end()) {
+        if (auto sp = it->second.lock()) {
+            out = sp;
+            return BBFMM_OK;
+        }
+    }
+    std::string err;
+    auto host = build_host_ops(kernel, ell, p, eps, depth, side, err);
+    if (!host)
+        return fail(BBFMM_EINTERNAL, "operator precompute failed: %s", err.c_str());
+    auto d = std::make_shared<DevOps>();
+    d->host = host;
+    d->nlev = (int)host->C.size();
+    d->r = host->r;
+    d->rp = (int)round_up(std::max(host->r, 1), 16);
+    d->rows64 = (int)round_up(std::max(host->r, 1), 64);
+    d->p3p = (int)round_up(host->p3, 16);
+    const int p3 = host->p3, r = host->r, rp = d->rp, rows64 = d->rows64, p3p = d->p3p;
+    for (int k = 0; k < d->nlev; ++k) {
+        std::vector<float> V((size_t)p3 * rp, 0.f), Ut((size_t)r * p3p, 0.f),
+            C((size_t)kNumOffsets * rows64 * rp, 0.f);
+        for (int i = 0; i < p3; ++i)
+            for (int a = 0; a < r; ++a) {
+                V[(size_t)i * rp + a] = (float)host->V[k][(size_t)i * r + a];
+                Ut[(size_t)a * p3p + i] = (float)host->U[k][(size_t)i * r + a];
+            }
+        for (int t = 0; t < kNumOffsets; ++t)
+            for (int a = 0; a < r; ++a)
+                for (int b = 0; b < r; ++b)
+                    C[((size_t)t * rows64 + a) * rp + b] = (float)host->C[k][((size_t)t * r + a) * r + b];
+        std::vector<float> Chi(C.size()), Clo(C.size());
+        split_tf32(C.data(), Chi.data(), Clo.data(), (int64_t)C.size());
+        float *dV = nullptr, *dUt = nullptr, *dC = nullptr, *dChi = nullptr, *dClo = nullptr;
+        CUDA_TRY(cudaMalloc(&dV, V.size() * 4));
+        d->V.push_back(dV);
+        CUDA_TRY(cudaMalloc(&dUt, Ut.size() * 4));
+        d->Ut.push_back(dUt);
+        CUDA_TRY(cudaMalloc(&dC, C.size() * 4));
+        d->C.push_back(dC);
+        CUDA_TRY(cudaMalloc(&dChi, C.size() * 4));
+        d->Chi.push_back(dChi);
+        CUDA_TRY(cudaMalloc(&dClo, C.size() * 4));
+        d->Clo.push_back(dClo);
+        CUDA_TRY(cudaMemcpy(dV, V.data(), V.size() * 4, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(dUt, Ut.data(), Ut.size() * 4, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(dC, C.data(), C.size() * 4, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(dChi, Chi.data(), C.size() * 4, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(dClo, Clo.data(), C.size() * 4, cudaMemcpyHostToDevice));
+        d->bytes += (int64_t)(V.size() + Ut.size() + 3 * C.size()) * 4;
+    }
+    g_ops_cache[key] = d;
+    out = d;
+    return BBFMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+static int plan_alloc(bbfmm_plan_impl *P, void **ptr, int64_t bytes, bool zero, cudaStream_t s)
+{
+    *ptr = nullptr;
+    if (bytes <= 0)
+        return BBFMM_OK;
+    cudaError_t e = cudaMalloc(ptr, (size_t)bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BBFMM_ENOMEM, "cudaMalloc(%lld bytes) failed: %s", (long long)bytes, cudaGetErrorString(e));
+    }
+    P->allocations.push_back(*ptr);
+    P->bytes += bytes;
+    if (zero) {
+        e = cudaMemsetAsync(*ptr, 0, (size_t)bytes, s);
+        if (e != cudaSuccess)
+            return fail(BBFMM_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    }
+    return BBFMM_OK;
+}
+
+#define PTRY(x)                                                                                                \
+    do {                                                                                                       \
+        int st_ = (x);                                                                                         \
+        if (st_ != BBFMM_OK)                                                                                   \
+            return st_;                                                                                        \
+    } while (0)
+
+static void plan_free(bbfmm_plan_impl *P)
+{
+    if (!P)
+        return;
+    cudaDeviceSynchronize();
+    for (void *ptr : P->allocations)
+        cudaFree(ptr);
+    P->allocations.clear();
+    if (P->chunks)
+        cudaFree(P->chunks);
+    if (P->side_stream)
+        cudaStreamDestroy(P->side_stream);
+    if (P->ev_fork)
+        cudaEventDestroy(P->ev_fork);
+    if (P->ev_join)
+        cudaEventDestroy(P->ev_join);
+    for (auto &e : P->ev)
+        if (e)
+            cudaEventDestroy(e);
+    if (P->ev_p2p0)
+        cudaEventDestroy(P->ev_p2p0);
+    if (P->ev_p2p1)
+        cudaEventDestroy(P->ev_p2p1);
+    cudaGetLastError();
+}
+
+// number of (target, source) box pairs over the interaction lists of one
+// level of the dense grid: |I(alpha)| = |A_x||A_y||A_z| - |B_x||B_y||B_z| with
+// A = children of the parent's neighbours, B = neighbours, per axis
+static int64_t m2l_pairs_level(int l)
+{
+    int64_t n = 1LL << l, np = n / 2, sa = 0, sb = 0;
+    for (int64_t a = 0; a < n; ++a) {
+        int64_t P = a / 2, lo = std::max<int64_t>(P - 1, 0), hi = std::min<int64_t>(P + 1, np - 1);
+        sa += 2 * (hi - lo + 1);
+        sb += std::min<int64_t>(a + 1, n - 1) - std::max<int64_t>(a - 1, 0) + 1;
+    }
+    return sa * sa * sa - sb * sb * sb;
+}
+
+static int plan_build(bbfmm_plan_impl *P, const double *points, cudaStream_t s)
+{
+    const int64_t n = P->n;
+    const int D = P->D;
+    const int64_t nleaf = 1LL << (3 * D);
+    CUDA_TRY(cudaGetDevice(&P->device));
+
+    // points on the device (FP64)
+    double *dpts = nullptr;
+    bool own_pts = !is_device_ptr(points);
+    if (own_pts) {
+        CUDA_TRY(cudaMalloc(&dpts, sizeof(double) * 3 * n));
+        CUDA_TRY(cudaMemcpyAsync(dpts, points, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+    } else {
+        dpts = const_cast<double *>(points);
+    }
+    struct Tmp {
+        std::vector<void *> v;
+        ~Tmp()
+        {
+            for (void *p : v)
+                cudaFree(p);
+        }
+    } tmp;
+    if (own_pts)
+        tmp.v.push_back(dpts);
+    auto talloc = [&](void **ptr, int64_t bytes) -> int {
+        cudaError_t e = cudaMalloc(ptr, (size_t)std::max<int64_t>(bytes, 16));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(BBFMM_ENOMEM, "cudaMalloc(%lld bytes) failed", (long long)bytes);
+        }
+        tmp.v.push_back(*ptr);
+        return BBFMM_OK;
+    };
+
+    // domain
+    unsigned long long *mm = nullptr;
+    int *bad = nullptr;
+    PTRY(talloc((void **)&mm, 6 * 8));
+    PTRY(talloc((void **)&bad, 16));
+    CUDA_TRY(cudaMemsetAsync(bad, 0, 16, s));
+    if (P->side <= 0.0) {
+        CUDA_TRY(launch_domain_minmax(dpts, n, reinterpret_cast<double *>(mm), s));
+        unsigned long long h[6];
+        CUDA_TRY(cudaMemcpyAsync(h, mm, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        double v[6];
+        for (int k = 0; k < 6; ++k) {
+            unsigned long long e = h[k];
+            unsigned long long b = (e >> 63) ? (e & ~0x8000000000000000ull) : ~e;
+            memcpy(&v[k], &b, 8);
+        }
+        double side = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            if (!isfinite(v[d]) || !isfinite(v[3 + d]))
+                return fail(BBFMM_EINVAL, "points contain NaN or infinite coordinates");
+            P->lo[d] = v[d];
+            side = std::max(side, v[3 + d] - v[d]);
+        }
+        P->side = side > 0.0 ? side : 1.0;
+    }
+
+    // leaf binning and Morton sort
+    uint32_t *keys = nullptr, *keys2 = nullptr;
+    int *vals = nullptr, *vals2 = nullptr, *scratch = nullptr;
+    PTRY(talloc((void **)&keys, 4 * n));
+    PTRY(talloc((void **)&keys2, 4 * n));
+    PTRY(talloc((void **)&vals, 4 * n));
+    PTRY(talloc((void **)&vals2, 4 * n));
+    int64_t sc = std::max(radix_sort_scratch_ints(n), 2 * (nleaf + 1) + scan_scratch_ints(nleaf + 1));
+    PTRY(talloc((void **)&scratch, 4 * sc));
+    CUDA_TRY(launch_bin_points(dpts, n, P->lo, P->side, D, keys, vals, bad, s));
+    int hbad = 0;
+    CUDA_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (hbad)
+        return fail(BBFMM_EINVAL, "points contain NaN/inf coordinates or lie outside the domain");
+    CUDA_TRY(radix_sort_pairs(keys, vals, keys2, vals2, n, 3 * D, scratch, sc, s));
+    PTRY(plan_alloc(P, (void **)&P->leaf_off, 4 * (nleaf + 1), false, s));
+    CUDA_TRY(launch_leaf_offsets(keys, n, nleaf, P->leaf_off, s));
+    PTRY(plan_alloc(P, (void **)&P->pts, 16 * n, false, s));
+    PTRY(plan_alloc(P, (void **)&P->perm, 4 * n, false, s));
+    CUDA_TRY(launch_local_coords(dpts, vals, n, P->lo, P->side, D, P->pts, P->perm, s));
+    int64_t chunk_bytes = 0;
+    CUDA_TRY(build_chunks(P->leaf_off, nleaf, scratch, &P->chunks, &P->nchunks, &chunk_bytes, s));
+    P->bytes += chunk_bytes;
+
+    // statistics of the tree (host copy of the leaf offsets)
+    {
+        std::vector<int> off(nleaf + 1);
+        CUDA_TRY(cudaMemcpyAsync(off.data(), P->leaf_off, 4 * (nleaf + 1), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        if (off[nleaf] != n)
+            return fail(BBFMM_EINTERNAL, "leaf offsets do not cover all points");
+        int ns = 1 << D;
+        int64_t pairs = 0;
+        for (int64_t m = 0; m < nleaf; ++m) {
+            int64_t c = off[m + 1] - off[m];
+            if (c == 0)
+                continue;
+            P->nonempty_leaves++;
+            P->max_leaf = std::max(P->max_leaf, c);
+            int x, y, z;
+            demorton3((uint32_t)m, x, y, z);
+            int64_t src = 0;
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        int a = x + dx, b = y + dy, cc = z + dz;
+                        if (a < 0 || b < 0 || cc < 0 || a >= ns || b >= ns || cc >= ns)
+                            continue;
+                        uint32_t nm = morton3(a, b, cc);
+                        src += off[nm + 1] - off[nm];
+                    }
+            pairs += c * src;
+        }
+        P->p2p_pairs = pairs;
+        for (int l = 2; l <= D; ++l)
+            P->m2l_pairs += m2l_pairs_level(l);
+    }
+
+    // operators
+    PTRY(get_ops(P->kernel, P->ell, P->p, P->eps, D, P->side, P->device, P->ops));
+    P->interp = make_interp_tables(*P->ops->host);
+
+    // per-level coefficient buffers
+    const int R = P->max_nrhs, p3 = P->p3;
+    const int rp = P->ops->rp;
+    for (int l = 2; l <= D; ++l) {
+        Level &L = P->lev[l];
+        int64_t nb = 1LL << (3 * l), H = 1LL << (l - 1);
+        PTRY(plan_alloc(P, (void **)&L.M, 4 * nb * R * p3, false, s));
+        PTRY(plan_alloc(P, (void **)&L.F, 4 * nb * R * p3, false, s));
+        PTRY(plan_alloc(P, (void **)&L.Mt, 4 * 8 * (H + 2) * H * H * R * rp, true, s));
+        PTRY(plan_alloc(P, (void **)&L.Ft, 4 * nb * R * rp, true, s));
+        if (P->precision == BBFMM_PREC_TF32X3 || P->precision == BBFMM_PREC_BF16X3) {
+            PTRY(plan_alloc(P, (void **)&L.Mt_hi, 4 * 8 * (H + 2) * H * H * R * rp, true, s));
+            PTRY(plan_alloc(P, (void **)&L.Mt_lo, 4 * 8 * (H + 2) * H * H * R * rp, true, s));
+        }
+    }
+    PTRY(plan_alloc(P, (void **)&P->sigma_s, 4 * n * R, false, s));
+    PTRY(plan_alloc(P, (void **)&P->phi_far, 4 * n * R, false, s));
+    PTRY(plan_alloc(P, (void **)&P->phi_near, 4 * n * R, false, s));
+    PTRY(plan_alloc(P, (void **)&P->status, 16, true, s));
+
+    CUDA_TRY(cudaStreamCreateWithFlags(&P->side_stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
+    for (auto &e : P->ev)
+        CUDA_TRY(cudaEventCreate(&e));
+    CUDA_TRY(cudaEventCreate(&P->ev_p2p0));
+    CUDA_TRY(cudaEventCreate(&P->ev_p2p1));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return BBFMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int nrhs, cudaStream_t s)
+{
+    const int64_t n = P->n;
+    const int D = P->D, p = P->p, p3 = P->p3;
+    const DevOps &O = *P->ops;
+    const bool tm = P->timing;
+    if (tm)
+        CUDA_TRY(cudaEventRecord(P->ev[Stage::Start], s));
+    CUDA_TRY(launch_gather_sigma(sigma, P->perm, n, nrhs, P->sigma_s, s));
+    if (tm)
+        CUDA_TRY(cudaEventRecord(P->ev[Stage::Gather], s));
+
+    // near field on the side stream, concurrent with the far field
+    CUDA_TRY(cudaEventRecord(P->ev_fork, s));
+    CUDA_TRY(cudaStreamWaitEvent(P->side_stream, P->ev_fork, 0));
+    if (tm)
+        CUDA_TRY(cudaEventRecord(P->ev_p2p0, P->side_stream));
+    CUDA_TRY(launch_p2p(P->pts, P->sigma_s, P->leaf_off, P->chunks, P->nchunks, n, D, P->kernel, P->ell,
+                        P->side / (double)(1LL << D), nrhs, P->phi_near, P->side_stream));
+    if (tm)
+        CUDA_TRY(cudaEventRecord(P->ev_p2p1, P->side_stream));
+    CUDA_TRY(cudaEventRecord(P->ev_join, P->side_stream));
+
+    if (D >= 2) {
+        const InterpTables &T = P->interp;
+        auto V = [&](int l) { return O.V[O.nlev == 1 ? 0 : l - 2]; };
+        auto Ut = [&](int l) { return O.Ut[O.nlev == 1 ? 0 : l - 2]; };
+        // upward pass: P2M at the leaves, M2M up to level 2, compress every level
+        CUDA_TRY(launch_p2m(T, P->pts, P->sigma_s, P->leaf_off, n, D, p, nrhs, P->lev[D].M, s));
+        for (int l = D - 1; l >= 2; --l)
+            CUDA_TRY(launch_m2m(T, P->lev[l + 1].M, P->lev[l].M, l, p, nrhs, s));
+        for (int l = D; l >= 2; --l)
+            CUDA_TRY(launch_compress(P->lev[l].M, V(l), P->lev[l].Mt, l, p3, O.r, O.rp, nrhs, s));
+        if (tm)
+            CUDA_TRY(cudaEventRecord(P->ev[Stage::Up], s));
+        // far field
+        for (int l = 2; l <= D; ++l)
+            CUDA_TRY(launch_m2l(P, l, nrhs, s));
+        if (tm)
+            CUDA_TRY(cudaEventRecord(P->ev[Stage::M2L], s));
+        // downward pass
+        for (int l = 2; l <= D; ++l) {
+            if (l >= 3)
+                CUDA_TRY(launch_l2l(T, P->lev[l - 1].F, P->lev[l].F, l - 1, p, nrhs, s));
+            CUDA_TRY(launch_decompress(P->lev[l].Ft, Ut(l), P->lev[l].F, l, p3, O.p3p, O.r, O.rp, nrhs, l >= 3, s));
+        }
+        if (tm)
+            CUDA_TRY(cudaEventRecord(P->ev[Stage::Down], s));
+        CUDA_TRY(launch_l2p(T, P->pts, P->lev[D].F, P->leaf_off, n, D, p, nrhs, P->phi_far, s));
+        if (tm)
+            CUDA_TRY(cudaEventRecord(P->ev[Stage::L2P], s));
+    } else if (tm) {
+        for (int k = Stage::Up; k <= Stage::L2P; ++k)
+            CUDA_TRY(cudaEventRecord(P->ev[k], s));
+    }
+    CUDA_TRY(cudaStreamWaitEvent(s, P->ev_join, 0));
+    if (tm)
+        CUDA_TRY(cudaEventRecord(P->ev[Stage::P2P], s));
+    CUDA_TRY(launch_combine(D >= 2 ? P->phi_far : nullptr, P->phi_near, P->perm, n, nrhs, phi, s));
+    if (tm)
+        CUDA_TRY(cudaEventRecord(P->ev[Stage::Combine], s));
+    P->last_nrhs = nrhs;
+    return BBFMM_OK;
+}
+
+} // namespace bbfmm
+
+using namespace bbfmm;
+
+extern "C" {
+
+void bbfmm_default_opts(bbfmm_opts *o)
+{
+    if (!o)
+        return;
+    memset(o, 0, sizeof(*o));
+    o->ell = 1.0;
+    o->svd_eps = 1e-7;
+    o->precision = BBFMM_PREC_FP32;
+    o->domain_given = 0;
+    o->side = 1.0;
+    o->max_nrhs = 1;
+}
+
+const char *bbfmm_last_error(void) { return g_last_error.c_str(); }
+
+int bbfmm_plan(const double *points, int64_t n, int kernel_id, int cheb_order, int depth, const bbfmm_opts *opts_in,
+               void *stream, bbfmm_plan_t *out)
+{
+    g_last_error.clear();
+    if (!out)
+        return fail(BBFMM_EINVAL, "out is NULL");
+    *out = nullptr;
+    bbfmm_opts opts;
+    bbfmm_default_opts(&opts);
+    if (opts_in)
+        opts = *opts_in;
+    if (!points)
+        return fail(BBFMM_EINVAL, "points is NULL");
+    if (n < 1 || n >= (1LL << 31))
+        return fail(BBFMM_EINVAL, "n = %lld out of range [1, 2^31)", (long long)n);
+    if (!(kernel_id == BBFMM_K_INV_R || kernel_id == BBFMM_K_INV_R2 || kernel_id == BBFMM_K_EXP ||
+          kernel_id == BBFMM_K_GAUSS || kernel_id == BBFMM_K_TEST_POLY || kernel_id == BBFMM_K_TEST_CONST))
+        return fail(BBFMM_EINVAL, "unknown kernel id %d", kernel_id);
+    if (cheb_order < 2 || cheb_order > kMaxP)
+        return fail(BBFMM_EINVAL, "cheb_order %d out of range [2, %d]", cheb_order, kMaxP);
+    if (depth < 0 || depth > kMaxDepth)
+        return fail(BBFMM_EINVAL, "depth %d out of range [0, %d]", depth, kMaxDepth);
+    if (!(opts.ell > 0.0) || !(opts.svd_eps >= 0.0) || opts.max_nrhs < 1 || opts.max_nrhs > 1024)
+        return fail(BBFMM_EINVAL, "invalid options (ell > 0, svd_eps >= 0, 1 <= max_nrhs <= 1024)");
+    if (opts.precision < BBFMM_PREC_FP32 || opts.precision > BBFMM_PREC_BF16X3)
+        return fail(BBFMM_EINVAL, "unknown precision %d", opts.precision);
+    if (opts.domain_given && !(opts.side > 0.0 && isfinite(opts.side) && isfinite(opts.lo[0]) &&
+                               isfinite(opts.lo[1]) && isfinite(opts.lo[2])))
+        return fail(BBFMM_EINVAL, "invalid domain");
+    // memory estimate: coefficient grids + points
+    {
+        int64_t p3 = (int64_t)cheb_order * cheb_order * cheb_order, grid = 0;
+        for (int l = 2; l <= depth; ++l)
+            grid += (1LL << (3 * l)) * opts.max_nrhs * (4 * p3 + 8 * p3);
+        int64_t need = grid * 4 + n * (16 + 4 + 12LL * opts.max_nrhs) + (1LL << (3 * depth)) * 8;
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(BBFMM_ECUDA, "no usable CUDA device");
+        }
+        if ((double)need > 0.9 * (double)fr)
+            return fail(BBFMM_ENOMEM, "plan needs ~%.1f GB, %.1f GB free", need / 1e9, fr / 1e9);
+    }
+    auto *P = new (std::nothrow) bbfmm_plan_s();
+    if (!P)
+        return fail(BBFMM_ENOMEM, "host allocation failed");
+    P->n = n;
+    P->D = depth;
+    P->p = cheb_order;
+    P->p3 = cheb_order * cheb_order * cheb_order;
+    P->kernel = kernel_id;
+    P->precision = opts.precision;
+    P->max_nrhs = opts.max_nrhs;
+    P->ell = opts.ell;
+    P->eps = opts.svd_eps;
+    if (opts.domain_given) {
+        for (int d = 0; d < 3; ++d)
+            P->lo[d] = opts.lo[d];
+        P->side = opts.side;
+    } else {
+        P->side = -1.0;
+    }
+    int st = plan_build(P, points, (cudaStream_t)stream);
+    if (st != BBFMM_OK) {
+        std::string msg = g_last_error;
+        plan_free(P);
+        delete P;
+        g_last_error = msg;
+        return st;
+    }
+    *out = P;
+    return BBFMM_OK;
+}
+
+int bbfmm_matvec(bbfmm_plan_t plan, const float *sigma, float *phi, int nrhs, void *stream)
+{
+    g_last_error.clear();
+    if (!plan)
+        return fail(BBFMM_EINVAL, "plan is NULL");
+    if (!sigma || !phi)
+        return fail(BBFMM_EINVAL, "sigma / phi is NULL");
+    if (nrhs < 1 || nrhs > plan->max_nrhs)
+        return fail(BBFMM_EINVAL, "nrhs = %d out of range [1, %d]", nrhs, plan->max_nrhs);
+    int expected = 0;
+    if (!plan->busy.compare_exchange_strong(expected, 1))
+        return fail(BBFMM_EBUSY, "plan is in use by another thread");
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool dsig = is_device_ptr(sigma), dphi = is_device_ptr(phi);
+    const int64_t bytes = 4 * plan->n * nrhs;
+    int st = BBFMM_OK;
+    const float *sg = sigma;
+    float *ph = phi;
+    if (!dsig || !dphi) {
+        if (!plan->io_sigma) {
+            st = plan_alloc(plan, (void **)&plan->io_sigma, 4 * plan->n * plan->max_nrhs, false, s);
+            if (st == BBFMM_OK)
+                st = plan_alloc(plan, (void **)&plan->io_phi, 4 * plan->n * plan->max_nrhs, false, s);
+        }
+        if (st == BBFMM_OK && !dsig) {
+            cudaError_t e = cudaMemcpyAsync(plan->io_sigma, sigma, bytes, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess)
+                st = fail(BBFMM_ECUDA, "copy of sigma: %s", cudaGetErrorString(e));
+            sg = plan->io_sigma;
+        }
+        if (!dphi)
+            ph = plan->io_phi;
+    }
+    if (st == BBFMM_OK)
+        st = matvec_device(plan, sg, ph, nrhs, s);
+    if (st == BBFMM_OK && !dphi) {
+        cudaError_t e = cudaMemcpyAsync(phi, plan->io_phi, bytes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess)
+            st = fail(BBFMM_ECUDA, "copy of phi: %s", cudaGetErrorString(e));
+    }
+    plan->busy.store(0);
+    return st;
+}
+
+int bbfmm_destroy(bbfmm_plan_t plan)
+{
+    if (!plan)
+        return BBFMM_OK;
+    plan_free(plan);
+    delete plan;
+    return BBFMM_OK;
+}
+
+int bbfmm_plan_info(bbfmm_plan_t plan, bbfmm_info *info)
+{
+    if (!plan || !info)
+        return fail(BBFMM_EINVAL, "NULL argument");
+    memset(info, 0, sizeof(*info));
+    info->n = plan->n;
+    info->depth = plan->D;
+    info->order = plan->p;
+    info->rank = plan->ops ? plan->ops->r : 0;
+    info->kernel = plan->kernel;
+    info->precision = plan->precision;
+    info->max_nrhs = plan->max_nrhs;
+    for (int d = 0; d < 3; ++d)
+        info->lo[d] = plan->lo[d];
+    info->side = plan->side;
+    info->device_bytes = plan->bytes + (plan->ops ? plan->ops->bytes : 0);
+    info->nonempty_leaves = plan->nonempty_leaves;
+    info->max_leaf_points = plan->max_leaf;
+    info->p2p_pairs = plan->p2p_pairs;
+    info->m2l_pairs = plan->m2l_pairs;
+    return BBFMM_OK;
+}
+
+int bbfmm_get_coefficients(bbfmm_plan_t plan, int which, int level, int nrhs, float *out)
+{
+    if (!plan || !out)
+        return fail(BBFMM_EINVAL, "NULL argument");
+    if (level < 2 || level > plan->D || (which != 0 && which != 1) || nrhs < 1 || nrhs > plan->max_nrhs)
+        return fail(BBFMM_EINVAL, "bad which / level / nrhs");
+    const float *src = which == 0 ? plan->lev[level].M : plan->lev[level].F;
+    int64_t nb = 1LL << (3 * level), p3 = plan->p3;
+    std::vector<float> tmp(nb * nrhs * p3);
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMemcpy(tmp.data(), src, tmp.size() * 4, cudaMemcpyDeviceToHost));
+    int64_t ns = 1LL << level;
+    for (int64_t m = 0; m < nb; ++m) {
+        int x, y, z;
+        demorton3((uint32_t)m, x, y, z);
+        int64_t lex = x + ns * (y + ns * z);
+        memcpy(out + lex * nrhs * p3, tmp.data() + m * nrhs * p3, 4 * nrhs * p3);
+    }
+    return BBFMM_OK;
+}
+
+int bbfmm_get_leaf_cells(bbfmm_plan_t plan, int32_t *out)
+{
+    if (!plan || !out)
+        return fail(BBFMM_EINVAL, "NULL argument");
+    int64_t nleaf = 1LL << (3 * plan->D), n = plan->n;
+    std::vector<int> off(nleaf + 1), perm(n);
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMemcpy(off.data(), plan->leaf_off, 4 * (nleaf + 1), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(perm.data(), plan->perm, 4 * n, cudaMemcpyDeviceToHost));
+    for (int64_t m = 0; m < nleaf; ++m) {
+        int x, y, z;
+        demorton3((uint32_t)m, x, y, z);
+        for (int i = off[m]; i < off[m + 1]; ++i) {
+            out[3 * (int64_t)perm[i]] = x;
+            out[3 * (int64_t)perm[i] + 1] = y;
+            out[3 * (int64_t)perm[i] + 2] = z;
+        }
+    }
+    return BBFMM_OK;
+}
+
+int bbfmm_set_timing(bbfmm_plan_t plan, int on)
+{
+    if (!plan)
+        return fail(BBFMM_EINVAL, "plan is NULL");
+    plan->timing = on != 0;
+    return BBFMM_OK;
+}
+
+int bbfmm_stage_times(bbfmm_plan_t plan, float *out)
+{
+    if (!plan || !out)
+        return fail(BBFMM_EINVAL, "NULL argument");
+    if (!plan->timing)
+        return fail(BBFMM_EINVAL, "timing is off for this plan");
+    CUDA_TRY(cudaDeviceSynchronize());
+    auto el = [&](cudaEvent_t a, cudaEvent_t b) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+            cudaGetLastError();
+            ms = -1.f;
+        }
+        return ms;
+    };
+    out[0] = el(plan->ev[Stage::Start], plan->ev[Stage::Gather]);
+    out[1] = el(plan->ev[Stage::Gather], plan->ev[Stage::Up]);
+    out[2] = el(plan->ev[Stage::Up], plan->ev[Stage::M2L]);
+    out[3] = el(plan->ev[Stage::M2L], plan->ev[Stage::Down]);
+    out[4] = el(plan->ev[Stage::Down], plan->ev[Stage::L2P]);
+    out[5] = el(plan->ev_p2p0, plan->ev_p2p1);
+    out[6] = el(plan->ev[Stage::P2P], plan->ev[Stage::Combine]);
+    out[7] = el(plan->ev[Stage::Start], plan->ev[Stage::Combine]);
+    return BBFMM_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,217 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Gates (FP32 path): relative 2-norm difference from the oracle bbFMM <= 1e-5,
+and error against the direct sum <= 1.1 x the oracle's error at the same p.
+Stage checks compare the multipole / local coefficients of every level with
+the oracle's (uncompressed operators, svd_eps = 0)."""
+import numpy as np
+import pytest
+
+from paper_1903_02153_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+K_INV_R, K_INV_R2, K_EXP, K_GAUSS, K_POLY, K_CONST = 1, 2, 3, 4, 100, 101
+UNIT = (W.UNIT_LO, W.UNIT_SIDE)
+
+
+@pytest.fixture(scope="module")
+def bb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1903_02153_gb300 import build
+    build.build()
+    from paper_1903_02153_gb300 import bbfmm
+    bbfmm.lib()
+    return bbfmm
+
+
+def gpu_matvec(bb, pts, sig, kid, p, depth, ell=1.0, eps=1e-7, precision="fp32", domain=UNIT,
+               keep=False):
+    dev = torch.device("cuda:0")
+    sig = np.asarray(sig, dtype=np.float32)
+    nrhs = 1 if sig.ndim == 1 else sig.shape[1]
+    plan = bb.Plan(torch.from_numpy(np.ascontiguousarray(pts)).to(dev), kid, p, depth, ell=ell,
+                   svd_eps=eps, precision=precision, domain=domain, max_nrhs=nrhs)
+    s = torch.from_numpy(np.ascontiguousarray(sig.T if nrhs > 1 else sig)).to(dev)
+    phi = plan.matvec(s)
+    torch.cuda.synchronize()
+    out = phi.cpu().numpy().astype(np.float64)
+    out = out.T if nrhs > 1 else out
+    if keep:
+        return out, plan
+    plan.close()
+    return out
+
+
+def oracle_fmm(oracle, pts, sig, kid, p, depth, ell=1.0, domain=UNIT, **kw):
+    return oracle.bbfmm(pts, np.asarray(sig, dtype=np.float32).astype(np.float64), kid, p, depth,
+                        ell=ell, lo=domain[0], side=domain[1], **kw)
+
+
+def test_leaf_binning_matches_oracle_bitwise(bb, oracle):
+    for kind, depth in [("uniform", 4), ("clustered", 6)]:
+        pts = W.make_points(kind, 50_000, seed=41)
+        # include points exactly on cell faces and on the upper domain face
+        pts[:8] = [[0, 0, 0], [1, 1, 1], [0.5, 0.5, 0.5], [0.25, 0.75, 1.0], [1.0, 0.0, 0.5],
+                   [0.125, 0.0625, 0.03125], [1 - 2 ** -40, 0.5, 0.5], [2 ** -40, 0.5, 0.5]]
+        plan = bb.Plan(torch.from_numpy(pts).cuda(), K_INV_R, 4, depth, domain=UNIT)
+        got = bb.bbfmm_get_leaf_cells(plan.handle, pts.shape[0])
+        plan.close()
+        ref = oracle.leaf_cells(pts, W.UNIT_LO, W.UNIT_SIDE, depth)
+        np.testing.assert_array_equal(got, ref)
+
+
+def test_default_domain_is_bounding_cube(bb, oracle):
+    pts = W.uniform_points(3000, seed=42) * np.array([2.0, 1.0, 0.5]) + np.array([-1.0, 3.0, 0.25])
+    plan = bb.Plan(torch.from_numpy(pts).cuda(), K_INV_R, 4, 3)
+    info = plan.info()
+    lo, side = oracle.bounding_cube(pts)
+    np.testing.assert_array_equal(np.array(info.lo[:]), lo)
+    assert info.side == side
+    got = bb.bbfmm_get_leaf_cells(plan.handle, pts.shape[0])
+    plan.close()
+    np.testing.assert_array_equal(got, oracle.leaf_cells(pts, lo, side, 3))
+
+
+@pytest.mark.parametrize("depth", [0, 1])
+@pytest.mark.parametrize("kid,ell", [(K_INV_R, 1.0), (K_EXP, 0.3), (K_INV_R2, 1.0)])
+def test_depth0_1_is_direct_sum(bb, oracle, depth, kid, ell):
+    pts = W.uniform_points(3000, seed=43)
+    sig = W.uniform_sigma(3000, seed=44).astype(np.float32)
+    got = gpu_matvec(bb, pts, sig, kid, 4, depth, ell=ell)
+    ref = oracle.direct(pts, pts, sig.astype(np.float64), kid, ell)
+    assert oracle.rel_err(got, ref) < 2e-6
+
+
+@pytest.mark.parametrize("p,depth", [(4, 3), (5, 4)])
+def test_stage_coefficients_match_oracle(bb, oracle, p, depth):
+    """Uncompressed operators (svd_eps = 0): M (upward pass) and F (after M2L
+    and L2L) on every level 2..D match the oracle's stage outputs."""
+    n = 12_000
+    pts = W.uniform_points(n, seed=45)
+    sig = W.uniform_sigma(n, seed=46).astype(np.float32)
+    got, plan = gpu_matvec(bb, pts, sig, K_INV_R, p, depth, eps=0.0, keep=True)
+    ref, Ms, Fs = oracle_fmm(oracle, pts, sig, K_INV_R, p, depth, dump=True)
+    for l in range(2, depth + 1):
+        gm = bb.bbfmm_get_coefficients(plan.handle, 0, l, 1, p)
+        gf = bb.bbfmm_get_coefficients(plan.handle, 1, l, 1, p)
+        assert oracle.rel_err(gm, Ms[l]) < 2e-6, ("M", l)
+        assert oracle.rel_err(gf, Fs[l]) < 5e-6, ("F", l)
+    plan.close()
+    assert oracle.rel_err(got, ref) < 5e-6
+
+
+def test_config_uniform_4k_p4_d3(bb, oracle):
+    """Plain bbFMM, N = 4096 uniform, 1/r, p = 4, depth 3, 1 RHS: both gates,
+    against the full direct sum."""
+    c = W.CONFIGS["uniform-4k-p4-d3"]
+    pts = W.uniform_points(c["n"])
+    sig = W.uniform_sigma(c["n"]).astype(np.float32)
+    got = gpu_matvec(bb, pts, sig, c["kernel"], c["p"], c["depth"])
+    ref_fmm = oracle_fmm(oracle, pts, sig, c["kernel"], c["p"], c["depth"])
+    direct = oracle.direct(pts, pts, sig.astype(np.float64), c["kernel"])
+    e_or = oracle.rel_err(ref_fmm, direct)
+    assert oracle.rel_err(got, ref_fmm) <= 1e-5
+    assert oracle.rel_err(got, direct) <= 1.1 * e_or
+
+
+def test_poly_kernel_reproduced(bb, oracle):
+    pts = W.clustered_points(6000, seed=47)
+    sig = W.uniform_sigma(6000, seed=48).astype(np.float32)
+    got = gpu_matvec(bb, pts, sig, K_POLY, 4, 3, eps=1e-12)
+    ref = oracle.direct(pts, pts, sig.astype(np.float64), K_POLY)
+    assert oracle.rel_err(got, ref) < 2e-6
+
+
+@pytest.mark.parametrize("kid,ell,kind,p,depth", [(K_INV_R2, 1.0, "clustered", 4, 4),
+                                                  (K_EXP, 0.3, "clustered", 5, 4),
+                                                  (K_GAUSS, 0.2, "uniform", 4, 3),
+                                                  (K_INV_R, 1.0, "jittered_grid", 5, 4)])
+def test_kernels_and_distributions(bb, oracle, kid, ell, kind, p, depth):
+    n = 20_000
+    pts = W.make_points(kind, n, seed=49)
+    sig = W.uniform_sigma(n, seed=50).astype(np.float32)
+    got = gpu_matvec(bb, pts, sig, kid, p, depth, ell=ell)
+    ref = oracle_fmm(oracle, pts, sig, kid, p, depth, ell=ell)
+    assert oracle.rel_err(got, ref) <= 1e-5
+
+
+def test_multiple_rhs_columns_match_single(bb, oracle):
+    n = 8000
+    pts = W.uniform_points(n, seed=51)
+    sig = W.uniform_sigma(n, nrhs=3, seed=52).astype(np.float32)
+    both = gpu_matvec(bb, pts, sig, K_INV_R, 4, 3)
+    for c in range(3):
+        one = gpu_matvec(bb, pts, np.ascontiguousarray(sig[:, c]), K_INV_R, 4, 3)
+        np.testing.assert_allclose(both[:, c], one, rtol=0, atol=1e-6 * np.abs(one).max())
+    ref = oracle_fmm(oracle, pts, sig, K_INV_R, 4, 3)
+    assert oracle.rel_err(both, ref) <= 1e-5
+
+
+def test_repeatable_bitwise(bb):
+    n = 30_000
+    pts = W.clustered_points(n, seed=53)
+    sig = torch.from_numpy(W.uniform_sigma(n, seed=54).astype(np.float32)).cuda()
+    plan = bb.Plan(torch.from_numpy(pts).cuda(), K_EXP, 5, 4, ell=0.3, domain=UNIT)
+    a = plan.matvec(sig).clone()
+    b = plan.matvec(sig).clone()
+    plan.close()
+    assert torch.equal(a, b)
+
+
+def test_host_buffers_match_device_buffers(bb):
+    n = 10_000
+    pts = W.uniform_points(n, seed=55)
+    sig = W.uniform_sigma(n, seed=56).astype(np.float32)
+    plan = bb.Plan(pts, K_INV_R, 4, 3, domain=UNIT)       # host points
+    dev = plan.matvec(torch.from_numpy(sig).cuda()).cpu().numpy()
+    out = np.zeros(n, dtype=np.float32)
+    bb.bbfmm_matvec(plan.handle, sig, out, 1)               # host sigma and phi
+    plan.close()
+    np.testing.assert_array_equal(out, dev)
+
+
+def test_matvec_rejects_bad_nrhs(bb):
+    pts = W.uniform_points(1000, seed=57)
+    plan = bb.Plan(torch.from_numpy(pts).cuda(), K_INV_R, 4, 2, domain=UNIT, max_nrhs=2)
+    s = torch.zeros(3, 1000, device="cuda")
+    with pytest.raises(bb.BBFMMError) as ei:
+        bb.bbfmm_matvec(plan.handle, s, s.clone(), 3)
+    assert ei.value.status == bb.BBFMM_EINVAL
+    plan.close()
+
+
+def test_plan_rejects_nan_and_outside_points(bb):
+    pts = W.uniform_points(500, seed=58)
+    bad = pts.copy()
+    bad[7, 1] = np.nan
+    with pytest.raises(bb.BBFMMError) as ei:
+        bb.Plan(torch.from_numpy(bad).cuda(), K_INV_R, 4, 2)
+    assert ei.value.status == bb.BBFMM_EINVAL
+    out = pts.copy()
+    out[3, 0] = 1.5
+    with pytest.raises(bb.BBFMMError):
+        bb.Plan(torch.from_numpy(out).cuda(), K_INV_R, 4, 2, domain=UNIT)
+
+
+@pytest.mark.parametrize("name", ["uniform-1M-p5-d5", "uniform-1M-p5-d6"])
+def test_full_size_uniform_1M_sampled(bb, oracle, name):
+    """N = 1,048,576 uniform, 1/r, p = 5 (the configuration the benchmark
+    times): sampled targets against the oracle bbFMM (computed for those
+    targets only) and against exact direct-sum rows."""
+    c = W.CONFIGS[name]
+    n = c["n"]
+    pts = W.uniform_points(n)
+    sig = W.uniform_sigma(n).astype(np.float32)
+    got = gpu_matvec(bb, pts, sig, c["kernel"], c["p"], c["depth"])
+    idx = np.sort(np.random.default_rng(61).choice(n, 400, replace=False))
+    ref = oracle_fmm(oracle, pts, sig, c["kernel"], c["p"], c["depth"], sample=idx)
+    direct = oracle.direct(pts[idx], pts, sig.astype(np.float64), c["kernel"])
+    e_gpu_or = oracle.rel_err(got[idx], ref)
+    e_or = oracle.rel_err(ref, direct)
+    e_gpu = oracle.rel_err(got[idx], direct)
+    print("%s: |gpu-oracle| %.2e  oracle err %.2e  gpu err %.2e" % (name, e_gpu_or, e_or, e_gpu))
+    assert e_gpu_or <= 1e-5
+    assert e_gpu <= 1.1 * e_or
