@@ -164,6 +164,15 @@ int bbfmm_stage_times(bbfmm_plan_t plan, float *out);
 /* Turn per-stage event timing on (1) or off (0) for later matvecs. */
 int bbfmm_set_timing(bbfmm_plan_t plan, int on);
 
+/*
+ * bbfmm_status: synchronize the device, read and clear the plan's device
+ * status word.  Kernels that wait on barriers give up after a bounded number
+ * of cycles and record it there instead of hanging.
+ *   word: optional; receives the raw bits (1 = bounds check, 2 = wait timeout).
+ * Returns BBFMM_OK, BBFMM_ETIMEOUT or BBFMM_EINTERNAL.
+ */
+int bbfmm_status(bbfmm_plan_t plan, int *word);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,7 +29,7 @@ PRECISIONS = {"fp32": BBFMM_PREC_FP32, "tf32": BBFMM_PREC_TF32, "tf32x3": BBFMM_
 
 EXPORTED = ["bbfmm_default_opts", "bbfmm_plan", "bbfmm_matvec", "bbfmm_destroy",
             "bbfmm_last_error", "bbfmm_plan_info", "bbfmm_get_coefficients",
-            "bbfmm_get_leaf_cells", "bbfmm_stage_times", "bbfmm_set_timing"]
+            "bbfmm_get_leaf_cells", "bbfmm_stage_times", "bbfmm_set_timing", "bbfmm_status"]
 
 
 class bbfmm_opts(ctypes.Structure):
@@ -88,6 +88,8 @@ def lib():
             L.bbfmm_stage_times.restype = i32
             L.bbfmm_set_timing.argtypes = [vp, i32]
             L.bbfmm_set_timing.restype = i32
+            L.bbfmm_status.argtypes = [vp, ctypes.POINTER(i32)]
+            L.bbfmm_status.restype = i32
             _lib = L
     return _lib
 
@@ -181,6 +183,14 @@ def bbfmm_stage_times(plan):
     out = np.zeros(8, dtype=np.float32)
     _check(lib().bbfmm_stage_times(plan, _ptr(out)))
     return out
+
+
+def bbfmm_status(plan):
+    """Synchronize and return the device status word (raises on a timeout or
+    a failed device-side check)."""
+    w = ctypes.c_int(0)
+    _check(lib().bbfmm_status(plan, ctypes.byref(w)))
+    return w.value
 
 
 STAGES = ["gather", "upward", "m2l", "downward", "l2p", "p2p", "combine", "total"]

@@ -220,8 +220,8 @@ cudaError_t launch_p2m(const InterpTables &T, const float4 *pts, const float *si
                        int nrhs, float *M, cudaStream_t s);
 cudaError_t launch_m2m(const InterpTables &T, const float *Mchild, float *Mparent, int lparent, int p, int nrhs, cudaStream_t s);
 cudaError_t launch_l2l(const InterpTables &T, const float *Fparent, float *Fchild, int lparent, int p, int nrhs, cudaStream_t s);
-cudaError_t launch_compress(const float *M, const float *V, float *Mt, int l, int p3, int r, int rp,
-                            int nrhs, cudaStream_t s);
+cudaError_t launch_compress(const float *M, const float *V, float *Mt, float *Mt_hi, float *Mt_lo, int l, int p3,
+                            int r, int rp, int nrhs, cudaStream_t s);
 cudaError_t launch_decompress(const float *Ft, const float *Ut, float *F, int l, int p3, int p3p, int r,
                               int rp, int nrhs, bool accumulate, cudaStream_t s);
 cudaError_t launch_l2p(const InterpTables &T, const float4 *pts, const float *F, const int *leaf_off, int64_t n, int D, int p,
@@ -229,6 +229,9 @@ cudaError_t launch_l2p(const InterpTables &T, const float4 *pts, const float *F,
 cudaError_t launch_combine(const float *phi_far, const float *phi_near, const int *perm, int64_t n,
                            int nrhs, float *phi, cudaStream_t s);
 // m2l_fp32.cu
+// per octant class o: the 189 interaction-list offsets as (operator index,
+// source octant, packed parent-cell shift (ux+1) | (uy+1)<<2 | (uz+1)<<4)
+bool fill_m2l_table(int4 (*tab)[kOffsetsPerClass]);
 cudaError_t launch_m2l_fp32(const float *Mt, const float *C, float *Ft, int l, int r, int rp, int rows64,
                             int nrhs, float scale, cudaStream_t s);
 // p2p.cu

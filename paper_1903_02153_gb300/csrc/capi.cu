@@ -391,7 +391,8 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
         for (int l = D - 1; l >= 2; --l)
             CUDA_TRY(launch_m2m(T, P->lev[l + 1].M, P->lev[l].M, l, p, nrhs, s));
         for (int l = D; l >= 2; --l)
-            CUDA_TRY(launch_compress(P->lev[l].M, V(l), P->lev[l].Mt, l, p3, O.r, O.rp, nrhs, s));
+            CUDA_TRY(launch_compress(P->lev[l].M, V(l), P->lev[l].Mt, P->lev[l].Mt_hi, P->lev[l].Mt_lo, l, p3, O.r,
+                                     O.rp, nrhs, s));
         if (tm)
             CUDA_TRY(cudaEventRecord(P->ev[Stage::Up], s));
         // far field
@@ -469,8 +470,8 @@ int bbfmm_plan(const double *points, int64_t n, int kernel_id, int cheb_order, i
         return fail(BBFMM_EINVAL, "depth %d out of range [0, %d]", depth, kMaxDepth);
     if (!(opts.ell > 0.0) || !(opts.svd_eps >= 0.0) || opts.max_nrhs < 1 || opts.max_nrhs > 1024)
         return fail(BBFMM_EINVAL, "invalid options (ell > 0, svd_eps >= 0, 1 <= max_nrhs <= 1024)");
-    if (opts.precision < BBFMM_PREC_FP32 || opts.precision > BBFMM_PREC_BF16X3)
-        return fail(BBFMM_EINVAL, "unknown precision %d", opts.precision);
+    if (opts.precision < BBFMM_PREC_FP32 || opts.precision > BBFMM_PREC_TF32X3)
+        return fail(BBFMM_EINVAL, "precision %d is not available (FP32, TF32, TF32X3)", opts.precision);
     if (opts.domain_given && !(opts.side > 0.0 && isfinite(opts.side) && isfinite(opts.lo[0]) &&
                                isfinite(opts.lo[1]) && isfinite(opts.lo[2])))
         return fail(BBFMM_EINVAL, "invalid domain");
@@ -636,6 +637,23 @@ int bbfmm_get_leaf_cells(bbfmm_plan_t plan, int32_t *out)
             out[3 * (int64_t)perm[i] + 2] = z;
         }
     }
+    return BBFMM_OK;
+}
+
+int bbfmm_status(bbfmm_plan_t plan, int *word)
+{
+    if (!plan)
+        return fail(BBFMM_EINVAL, "plan is NULL");
+    int w = 0;
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMemcpy(&w, plan->status, sizeof(int), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemset(plan->status, 0, sizeof(int)));
+    if (word)
+        *word = w;
+    if (w & kStatusTimeout)
+        return fail(BBFMM_ETIMEOUT, "a device-side wait timed out (status word %d)", w);
+    if (w & kStatusBounds)
+        return fail(BBFMM_EINTERNAL, "a device-side bounds check failed (status word %d)", w);
     return BBFMM_OK;
 }
 

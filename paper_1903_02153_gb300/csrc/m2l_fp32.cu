@@ -23,12 +23,8 @@ __constant__ int4 c_m2l_tab[8][kOffsetsPerClass];
 static bool g_tab_ready = false;
 static std::mutex g_tab_mu;
 
-cudaError_t upload_m2l_table()
+bool fill_m2l_table(int4 (*tab)[kOffsetsPerClass])
 {
-    std::lock_guard<std::mutex> g(g_tab_mu);
-    if (g_tab_ready)
-        return cudaSuccess;
-    int4 tab[8][kOffsetsPerClass];
     for (int o = 0; o < 8; ++o) {
         int c[3] = {o & 1, (o >> 1) & 1, (o >> 2) & 1};
         int k = 0;
@@ -47,8 +43,19 @@ cudaError_t upload_m2l_table()
                                             (u[0] + 1) | ((u[1] + 1) << 2) | ((u[2] + 1) << 4), 0);
                 }
         if (k != kOffsetsPerClass)
-            return cudaErrorInvalidValue;
+            return false;
     }
+    return true;
+}
+
+static cudaError_t upload_m2l_table()
+{
+    std::lock_guard<std::mutex> g(g_tab_mu);
+    if (g_tab_ready)
+        return cudaSuccess;
+    int4 tab[8][kOffsetsPerClass];
+    if (!fill_m2l_table(tab))
+        return cudaErrorInvalidValue;
     cudaError_t e = cudaMemcpyToSymbol(c_m2l_tab, tab, sizeof(tab));
     if (e == cudaSuccess)
         g_tab_ready = true;

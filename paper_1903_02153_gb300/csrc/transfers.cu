@@ -297,10 +297,18 @@ __global__ void __launch_bounds__(128) k_l2l(const __grid_constant__ InterpTable
 //   decompress (MODE 1): F[row][i] (+)= sum_k Ft[row][k] Ut[k][i]  (F = U F~)
 // M and F rows are contiguous p3-vectors in Morton order; Mt / Ft rows sit at
 // parity_row() of their box.
+__device__ __forceinline__ float tf32_rna(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(256) k_node_gemm(const float *__restrict__ A, const float *__restrict__ W,
                                                    float *__restrict__ Out, int64_t rows, int K, int N, int ldw,
-                                                   int lda, int ldo, int level, int nrhs, int accumulate)
+                                                   int lda, int ldo, int level, int nrhs, int accumulate,
+                                                   float *__restrict__ Out_hi, float *__restrict__ Out_lo)
 {
     __shared__ float As[16][64 + 4];
     __shared__ float Ws[16][64 + 4];
@@ -369,16 +377,21 @@ __global__ void __launch_bounds__(256) k_node_gemm(const float *__restrict__ A, 
                 Out[obase + col] += acc[i][j];
             else
                 Out[obase + col] = acc[i][j];
+            if (MODE == 0 && Out_hi) { // split for the 3-pass tensor-core M2L
+                float hi = tf32_rna(acc[i][j]);
+                Out_hi[obase + col] = hi;
+                Out_lo[obase + col] = tf32_rna(acc[i][j] - hi);
+            }
         }
     }
 }
 
-cudaError_t launch_compress(const float *M, const float *V, float *Mt, int l, int p3, int r, int rp, int nrhs,
-                            cudaStream_t s)
+cudaError_t launch_compress(const float *M, const float *V, float *Mt, float *Mt_hi, float *Mt_lo, int l, int p3,
+                            int r, int rp, int nrhs, cudaStream_t s)
 {
     int64_t rows = ((int64_t)1 << (3 * l)) * nrhs;
     dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((r + 63) / 64));
-    k_node_gemm<0><<<grid, 256, 0, s>>>(M, V, Mt, rows, p3, r, rp, p3, rp, l, nrhs, 0);
+    k_node_gemm<0><<<grid, 256, 0, s>>>(M, V, Mt, rows, p3, r, rp, p3, rp, l, nrhs, 0, Mt_hi, Mt_lo);
     return cudaGetLastError();
 }
 
@@ -387,7 +400,8 @@ cudaError_t launch_decompress(const float *Ft, const float *Ut, float *F, int l,
 {
     int64_t rows = ((int64_t)1 << (3 * l)) * nrhs;
     dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((p3 + 63) / 64));
-    k_node_gemm<1><<<grid, 256, 0, s>>>(Ft, Ut, F, rows, r, p3, p3p, rp, p3, l, nrhs, accumulate ? 1 : 0);
+    k_node_gemm<1><<<grid, 256, 0, s>>>(Ft, Ut, F, rows, r, p3, p3p, rp, p3, l, nrhs, accumulate ? 1 : 0, nullptr,
+                                        nullptr);
     return cudaGetLastError();
 }
 

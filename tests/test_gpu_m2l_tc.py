@@ -1,0 +1,103 @@
+"""The tensor-core M2L (tcgen05, TF32 and split 3xTF32) against the FP32
+CUDA-core M2L and the FP64 oracle, from the smallest tree up.
+
+3xTF32 keeps ~21 mantissa bits per product, so its result must sit within
+2e-6 (relative 2-norm) of the FP32 path, and within the FP32 gates of the
+oracle (1e-5, and 1.1 x the oracle's error against the direct sum).  One-pass
+TF32 (10 bits) is reported with a loose bound only."""
+import numpy as np
+import pytest
+
+from paper_1903_02153_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+UNIT = (W.UNIT_LO, W.UNIT_SIDE)
+
+
+@pytest.fixture(scope="module")
+def bb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1903_02153_gb300 import build
+    build.build()
+    from paper_1903_02153_gb300 import bbfmm
+    bbfmm.lib()
+    return bbfmm
+
+
+def run(bb, pts, sig, kid, p, depth, precision, ell=1.0, eps=1e-7, nrhs=1):
+    dev = torch.device("cuda:0")
+    plan = bb.Plan(torch.from_numpy(pts).to(dev), kid, p, depth, ell=ell, svd_eps=eps, precision=precision,
+                   domain=UNIT, max_nrhs=nrhs)
+    s = torch.from_numpy(np.ascontiguousarray(sig.T if nrhs > 1 else sig).astype(np.float32)).to(dev)
+    phi = plan.matvec(s)
+    status = bb.bbfmm_status(plan.handle)
+    out = phi.cpu().numpy().astype(np.float64)
+    plan.close()
+    assert status == 0
+    return out.T if nrhs > 1 else out
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("n,p,depth", [(2000, 4, 2), (6000, 4, 3), (20000, 5, 4), (60000, 5, 5)])
+def test_tf32x3_matches_fp32(bb, n, p, depth):
+    pts = W.uniform_points(n, seed=71)
+    sig = W.uniform_sigma(n, seed=72).astype(np.float32)
+    a = run(bb, pts, sig, 1, p, depth, "fp32")
+    b = run(bb, pts, sig, 1, p, depth, "tf32x3")
+    assert rel(b, a) < 2e-6
+
+
+def test_tf32_one_pass_is_close(bb):
+    pts = W.uniform_points(20000, seed=73)
+    sig = W.uniform_sigma(20000, seed=74).astype(np.float32)
+    a = run(bb, pts, sig, 1, 5, 4, "fp32")
+    b = run(bb, pts, sig, 1, 5, 4, "tf32")
+    e = rel(b, a)
+    print("one-pass tf32 vs fp32: %.2e" % e)
+    assert e < 1e-3
+
+
+@pytest.mark.parametrize("kid,ell,kind,p,depth,eps", [(3, 0.3, "clustered", 6, 4, 1e-7),
+                                                      (2, 1.0, "uniform", 5, 4, 1e-7),
+                                                      (1, 1.0, "uniform", 5, 4, 0.0)])
+def test_tf32x3_vs_oracle(bb, oracle, kid, ell, kind, p, depth, eps):
+    n = 20000
+    pts = W.make_points(kind, n, seed=75)
+    sig = W.uniform_sigma(n, seed=76).astype(np.float32)
+    got = run(bb, pts, sig, kid, p, depth, "tf32x3", ell=ell, eps=eps)
+    ref = oracle.bbfmm(pts, sig.astype(np.float64), kid, p, depth, ell=ell, lo=W.UNIT_LO, side=W.UNIT_SIDE)
+    assert oracle.rel_err(got, ref) <= 1e-5
+
+
+def test_tf32x3_multiple_rhs(bb):
+    n = 12000
+    pts = W.uniform_points(n, seed=77)
+    sig = W.uniform_sigma(n, nrhs=4, seed=78).astype(np.float32)
+    a = run(bb, pts, sig, 1, 4, 4, "fp32", nrhs=4)
+    b = run(bb, pts, sig, 1, 4, 4, "tf32x3", nrhs=4)
+    assert rel(b, a) < 2e-6
+
+
+@pytest.mark.parametrize("depth", [5, 6])
+def test_tf32x3_full_size_uniform_1M(bb, oracle, depth):
+    c = W.CONFIGS["uniform-1M-p5-d6"]
+    n = c["n"]
+    pts = W.uniform_points(n)
+    sig = W.uniform_sigma(n).astype(np.float32)
+    got = run(bb, pts, sig, 1, 5, depth, "tf32x3")
+    plain = run(bb, pts, sig, 1, 5, depth, "fp32")
+    idx = np.sort(np.random.default_rng(62).choice(n, 400, replace=False))
+    ref = oracle.bbfmm(pts, sig.astype(np.float64), 1, 5, depth, lo=W.UNIT_LO, side=W.UNIT_SIDE, sample=idx)
+    direct = oracle.direct(pts[idx], pts, sig.astype(np.float64), 1)
+    e_or = oracle.rel_err(ref, direct)
+    print("depth %d: tf32x3 vs fp32 %.2e, vs oracle %.2e, err %.2e (oracle %.2e)"
+          % (depth, rel(got, plain), oracle.rel_err(got[idx], ref), oracle.rel_err(got[idx], direct), e_or))
+    assert rel(got, plain) < 2e-6
+    assert oracle.rel_err(got[idx], ref) <= 1e-5
+    assert oracle.rel_err(got[idx], direct) <= 1.1 * e_or
