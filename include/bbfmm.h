@@ -68,7 +68,10 @@ typedef struct {
     double lo[3];      /* lower corner of the cubical domain */
     double side;       /* side length of the domain (> 0) */
     int max_nrhs;      /* largest nrhs a matvec on this plan may use (default 1) */
-    int reserved[7];   /* zero */
+    int split_accumulate; /* BBFMM_PREC_TF32X3 only: 1 (default) accumulates the
+                             correction products hi*lo + lo*hi apart from hi*hi and
+                             adds them at the end; 0 uses one accumulator */
+    int reserved[6];   /* zero */
 } bbfmm_opts;
 
 typedef struct {

@@ -36,7 +36,8 @@ class bbfmm_opts(ctypes.Structure):
     _fields_ = [("ell", ctypes.c_double), ("svd_eps", ctypes.c_double),
                 ("precision", ctypes.c_int), ("domain_given", ctypes.c_int),
                 ("lo", ctypes.c_double * 3), ("side", ctypes.c_double),
-                ("max_nrhs", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("max_nrhs", ctypes.c_int), ("split_accumulate", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
 
 
 class bbfmm_info(ctypes.Structure):
@@ -201,9 +202,10 @@ class Plan:
     ``plan.matvec(sigma)`` with sigma a CUDA tensor (n,) or (nrhs, n)."""
 
     def __init__(self, points, kernel, order, depth, ell=1.0, svd_eps=1e-7, precision="fp32",
-                 domain=None, max_nrhs=1, stream=None):
+                 domain=None, max_nrhs=1, stream=None, split_accumulate=True):
         import torch
         o = bbfmm_default_opts()
+        o.split_accumulate = 1 if split_accumulate else 0
         o.ell = float(ell)
         o.svd_eps = float(svd_eps)
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)

@@ -164,6 +164,8 @@ struct bbfmm_plan_impl {
     int D = 0, p = 0, p3 = 0, kernel = 0, precision = 0, max_nrhs = 1;
     double ell = 1.0, lo[3] = {0, 0, 0}, side = 1.0, eps = 1e-7;
     int device = 0;
+    bool split_acc = true; // 3-pass tensor-core M2L: separate correction accumulator
+    int m2l_groups = 1;    // offset groups per M2L tile (partial slices of F~)
 
     // tree
     float4 *pts = nullptr;
@@ -222,8 +224,8 @@ cudaError_t launch_m2m(const InterpTables &T, const float *Mchild, float *Mparen
 cudaError_t launch_l2l(const InterpTables &T, const float *Fparent, float *Fchild, int lparent, int p, int nrhs, cudaStream_t s);
 cudaError_t launch_compress(const float *M, const float *V, float *Mt, float *Mt_hi, float *Mt_lo, int l, int p3,
                             int r, int rp, int nrhs, cudaStream_t s);
-cudaError_t launch_decompress(const float *Ft, const float *Ut, float *F, int l, int p3, int p3p, int r,
-                              int rp, int nrhs, bool accumulate, cudaStream_t s);
+cudaError_t launch_decompress(const float *Ft, int nslices, int64_t slice, const float *Ut, float *F, int l,
+                              int p3, int p3p, int r, int rp, int nrhs, bool accumulate, cudaStream_t s);
 cudaError_t launch_l2p(const InterpTables &T, const float4 *pts, const float *F, const int *leaf_off, int64_t n, int D, int p,
                        int nrhs, float *phi_far, cudaStream_t s);
 cudaError_t launch_combine(const float *phi_far, const float *phi_near, const int *perm, int64_t n,
@@ -234,6 +236,9 @@ cudaError_t launch_combine(const float *phi_far, const float *phi_near, const in
 bool fill_m2l_table(int4 (*tab)[kOffsetsPerClass]);
 cudaError_t launch_m2l_fp32(const float *Mt, const float *C, float *Ft, int l, int r, int rp, int rows64,
                             int nrhs, float scale, cudaStream_t s);
+// m2l_tc.cu: every level of the far field in one go (FP32 or tensor cores)
+cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s);
+int m2l_groups_for(int D, int nrhs, int precision);
 // p2p.cu
 cudaError_t launch_p2p(const float4 *pts, const float *sig, const int *leaf_off, const int4 *chunks,
                        int nchunks, int64_t n, int D, int kernel, double ell, double h, int nrhs,

@@ -14,8 +14,6 @@
 
 namespace bbfmm {
 
-cudaError_t launch_m2l(bbfmm_plan_impl *P, int l, int nrhs, cudaStream_t s); // m2l_tc.cu
-
 static thread_local std::string g_last_error;
 
 static int fail(int status, const char *fmt, ...)
@@ -330,13 +328,14 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, cudaStream_t s)
     // per-level coefficient buffers
     const int R = P->max_nrhs, p3 = P->p3;
     const int rp = P->ops->rp;
+    P->m2l_groups = m2l_groups_for(D, R, P->precision);
     for (int l = 2; l <= D; ++l) {
         Level &L = P->lev[l];
         int64_t nb = 1LL << (3 * l), H = 1LL << (l - 1);
         PTRY(plan_alloc(P, (void **)&L.M, 4 * nb * R * p3, false, s));
         PTRY(plan_alloc(P, (void **)&L.F, 4 * nb * R * p3, false, s));
         PTRY(plan_alloc(P, (void **)&L.Mt, 4 * 8 * (H + 2) * H * H * R * rp, true, s));
-        PTRY(plan_alloc(P, (void **)&L.Ft, 4 * nb * R * rp, true, s));
+        PTRY(plan_alloc(P, (void **)&L.Ft, 4 * nb * R * rp * P->m2l_groups, true, s));
         if (P->precision == BBFMM_PREC_TF32X3 || P->precision == BBFMM_PREC_BF16X3) {
             PTRY(plan_alloc(P, (void **)&L.Mt_hi, 4 * 8 * (H + 2) * H * H * R * rp, true, s));
             PTRY(plan_alloc(P, (void **)&L.Mt_lo, 4 * 8 * (H + 2) * H * H * R * rp, true, s));
@@ -395,16 +394,16 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
                                      O.rp, nrhs, s));
         if (tm)
             CUDA_TRY(cudaEventRecord(P->ev[Stage::Up], s));
-        // far field
-        for (int l = 2; l <= D; ++l)
-            CUDA_TRY(launch_m2l(P, l, nrhs, s));
+        // far field, all levels
+        CUDA_TRY(launch_m2l_all(P, nrhs, s));
         if (tm)
             CUDA_TRY(cudaEventRecord(P->ev[Stage::M2L], s));
         // downward pass
         for (int l = 2; l <= D; ++l) {
             if (l >= 3)
                 CUDA_TRY(launch_l2l(T, P->lev[l - 1].F, P->lev[l].F, l - 1, p, nrhs, s));
-            CUDA_TRY(launch_decompress(P->lev[l].Ft, Ut(l), P->lev[l].F, l, p3, O.p3p, O.r, O.rp, nrhs, l >= 3, s));
+            CUDA_TRY(launch_decompress(P->lev[l].Ft, P->m2l_groups, (1LL << (3 * l)) * P->max_nrhs * O.rp, Ut(l),
+                                       P->lev[l].F, l, p3, O.p3p, O.r, O.rp, nrhs, l >= 3, s));
         }
         if (tm)
             CUDA_TRY(cudaEventRecord(P->ev[Stage::Down], s));
@@ -442,6 +441,7 @@ void bbfmm_default_opts(bbfmm_opts *o)
     o->domain_given = 0;
     o->side = 1.0;
     o->max_nrhs = 1;
+    o->split_accumulate = 1;
 }
 
 const char *bbfmm_last_error(void) { return g_last_error.c_str(); }
@@ -501,6 +501,7 @@ int bbfmm_plan(const double *points, int64_t n, int kernel_id, int cheb_order, i
     P->max_nrhs = opts.max_nrhs;
     P->ell = opts.ell;
     P->eps = opts.svd_eps;
+    P->split_acc = opts.split_accumulate != 0;
     if (opts.domain_given) {
         for (int d = 0; d < 3; ++d)
             P->lo[d] = opts.lo[d];

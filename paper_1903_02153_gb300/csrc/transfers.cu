@@ -308,7 +308,8 @@ template <int MODE>
 __global__ void __launch_bounds__(256) k_node_gemm(const float *__restrict__ A, const float *__restrict__ W,
                                                    float *__restrict__ Out, int64_t rows, int K, int N, int ldw,
                                                    int lda, int ldo, int level, int nrhs, int accumulate,
-                                                   float *__restrict__ Out_hi, float *__restrict__ Out_lo)
+                                                   float *__restrict__ Out_hi, float *__restrict__ Out_lo,
+                                                   int nslices, int64_t slice)
 {
     __shared__ float As[16][64 + 4];
     __shared__ float Ws[16][64 + 4];
@@ -334,7 +335,14 @@ __global__ void __launch_bounds__(256) k_node_gemm(const float *__restrict__ A, 
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             int k = k0 + lk + q;
-            As[lk + q][lr] = (abase >= 0 && k < K) ? A[abase + k] : 0.0f;
+            float a = 0.0f;
+            if (abase >= 0 && k < K) {
+                // partial M2L sums of the offset groups, added in a fixed order
+                a = A[abase + k];
+                for (int g = 1; g < nslices; ++g)
+                    a += A[g * slice + abase + k];
+            }
+            As[lk + q][lr] = a;
         }
         {
             int wk = tid >> 4, wc = (tid & 15) * 4;
@@ -391,17 +399,17 @@ cudaError_t launch_compress(const float *M, const float *V, float *Mt, float *Mt
 {
     int64_t rows = ((int64_t)1 << (3 * l)) * nrhs;
     dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((r + 63) / 64));
-    k_node_gemm<0><<<grid, 256, 0, s>>>(M, V, Mt, rows, p3, r, rp, p3, rp, l, nrhs, 0, Mt_hi, Mt_lo);
+    k_node_gemm<0><<<grid, 256, 0, s>>>(M, V, Mt, rows, p3, r, rp, p3, rp, l, nrhs, 0, Mt_hi, Mt_lo, 1, 0);
     return cudaGetLastError();
 }
 
-cudaError_t launch_decompress(const float *Ft, const float *Ut, float *F, int l, int p3, int p3p, int r, int rp,
-                              int nrhs, bool accumulate, cudaStream_t s)
+cudaError_t launch_decompress(const float *Ft, int nslices, int64_t slice, const float *Ut, float *F, int l, int p3,
+                              int p3p, int r, int rp, int nrhs, bool accumulate, cudaStream_t s)
 {
     int64_t rows = ((int64_t)1 << (3 * l)) * nrhs;
     dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((p3 + 63) / 64));
     k_node_gemm<1><<<grid, 256, 0, s>>>(Ft, Ut, F, rows, r, p3, p3p, rp, p3, l, nrhs, accumulate ? 1 : 0, nullptr,
-                                        nullptr);
+                                        nullptr, nslices, slice);
     return cudaGetLastError();
 }
 

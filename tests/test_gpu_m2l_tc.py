@@ -64,15 +64,21 @@ def test_tf32_one_pass_is_close(bb):
 
 
 @pytest.mark.parametrize("kid,ell,kind,p,depth,eps", [(3, 0.3, "clustered", 6, 4, 1e-7),
-                                                      (2, 1.0, "uniform", 5, 4, 1e-7),
+                                                      (2, 1.0, "uniform", 5, 4, 1e-8),
                                                       (1, 1.0, "uniform", 5, 4, 0.0)])
 def test_tf32x3_vs_oracle(bb, oracle, kid, ell, kind, p, depth, eps):
+    """Against the uncompressed oracle; for 1/r^2 the SVD truncation at 1e-7
+    alone sits at ~1e-5 (in the FP32 path too), so that case uses 1e-8."""
     n = 20000
     pts = W.make_points(kind, n, seed=75)
     sig = W.uniform_sigma(n, seed=76).astype(np.float32)
     got = run(bb, pts, sig, kid, p, depth, "tf32x3", ell=ell, eps=eps)
+    plain = run(bb, pts, sig, kid, p, depth, "fp32", ell=ell, eps=eps)
     ref = oracle.bbfmm(pts, sig.astype(np.float64), kid, p, depth, ell=ell, lo=W.UNIT_LO, side=W.UNIT_SIDE)
+    print("kernel %d: tf32x3 vs oracle %.2e, fp32 vs oracle %.2e" % (kid, oracle.rel_err(got, ref),
+                                                                      oracle.rel_err(plain, ref)))
     assert oracle.rel_err(got, ref) <= 1e-5
+    assert rel(got, plain) < 2e-6
 
 
 def test_tf32x3_multiple_rhs(bb):
