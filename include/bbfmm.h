@@ -176,6 +176,34 @@ int bbfmm_set_timing(bbfmm_plan_t plan, int on);
  */
 int bbfmm_status(bbfmm_plan_t plan, int *word);
 
+/*
+ * bbfmm_sort_points_static: the tree build that bbfmm_plan performs (leaf
+ * binning, stable sort by the Morton index of the leaf, leaf offsets), written
+ * to caller buffers and allocating nothing.  The paper has no counterpart:
+ * this exists for callers that cannot call cudaMalloc when they build a tree,
+ * e.g. code working inside a device-memory budget that another runtime has
+ * already reserved, or on a path where a synchronous allocation would stall
+ * other work on the GPU.
+ *   points:   device, n x 3 row-major FP64 (host pointers are rejected).
+ *   n:        1 <= n <= 1,048,576 (the size of the library's fixed scratch).
+ *   depth:    0..8.
+ *   lo, side: host, the cubical domain (lo[3], side > 0); cell of a point =
+ *             min(floor((x - lo) / h_D), 2^depth - 1) per axis, as in bbfmm_plan.
+ *   perm:     device, n int32, overwritten: perm[i] = original index of the
+ *             i-th point in sorted order (increasing inside a leaf).
+ *   leaf_off: device, 8^depth + 1 int32, overwritten: sorted points of the
+ *             leaf with Morton index m are perm[leaf_off[m] .. leaf_off[m+1]).
+ * Scratch: one file-scope device array of about 13.6 MB, resident on every GPU
+ * that loads the library until the process exits.  Its address is looked up on
+ * the first call made on a device (with that device current); make that first
+ * call before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU (other streams, other threads) race and must be ordered
+ * by the caller.  The call synchronizes `stream` to read the error flag.
+ * Errors: EINVAL (sizes, host pointers, NaN or out-of-domain points), ECUDA.
+ */
+int bbfmm_sort_points_static(const double *points, int64_t n, int depth, const double *lo, double side,
+                             int32_t *perm, int32_t *leaf_off, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,7 +29,8 @@ PRECISIONS = {"fp32": BBFMM_PREC_FP32, "tf32": BBFMM_PREC_TF32, "tf32x3": BBFMM_
 
 EXPORTED = ["bbfmm_default_opts", "bbfmm_plan", "bbfmm_matvec", "bbfmm_destroy",
             "bbfmm_last_error", "bbfmm_plan_info", "bbfmm_get_coefficients",
-            "bbfmm_get_leaf_cells", "bbfmm_stage_times", "bbfmm_set_timing", "bbfmm_status"]
+            "bbfmm_get_leaf_cells", "bbfmm_stage_times", "bbfmm_set_timing", "bbfmm_status",
+            "bbfmm_sort_points_static"]
 
 
 class bbfmm_opts(ctypes.Structure):
@@ -91,6 +92,8 @@ def lib():
             L.bbfmm_set_timing.restype = i32
             L.bbfmm_status.argtypes = [vp, ctypes.POINTER(i32)]
             L.bbfmm_status.restype = i32
+            L.bbfmm_sort_points_static.argtypes = [vp, i64, i32, ctypes.POINTER(f64), f64, vp, vp, vp]
+            L.bbfmm_sort_points_static.restype = i32
             _lib = L
     return _lib
 
@@ -192,6 +195,22 @@ def bbfmm_status(plan):
     w = ctypes.c_int(0)
     _check(lib().bbfmm_status(plan, ctypes.byref(w)))
     return w.value
+
+
+def bbfmm_sort_points_static(points, depth, lo, side, perm, leaf_off, stream=None):
+    """Leaf binning + Morton sort into caller buffers (device tensors) using
+    the library's fixed scratch array; allocates nothing."""
+    lo3 = (ctypes.c_double * 3)(*[float(v) for v in lo])
+    return _check_plain(lib().bbfmm_sort_points_static(_ptr(points), int(points.shape[0]), int(depth), lo3,
+                                                       float(side), _ptr(perm), _ptr(leaf_off),
+                                                       _stream(stream)))
+
+
+def _check_plain(st):
+    # entry points that report only a status code (no message)
+    if st != BBFMM_OK:
+        raise BBFMMError(st, "")
+    return st
 
 
 STAGES = ["gather", "upward", "m2l", "downward", "l2p", "p2p", "combine", "total"]
