@@ -138,7 +138,7 @@ def run_ours(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    precision = args.precision or "fp32"
+    precision = args.precision or "tf32x3"
     name = "uniform-1M-p5-d%d" % args.depth
     c = dict(W.CONFIGS["uniform-1M-p5-d6"], depth=args.depth)
     n, p, depth = c["n"], c["p"], c["depth"]
@@ -216,6 +216,11 @@ def run_ours(args, rank, world, local):
     depth6 = None
     if rank == 0 and not args.no_depth6 and args.depth != 6:
         depth6 = other_depth(bb, torch, dev, pts, sigma, c, 6, precision, flush, stream)
+    # the plain FP32 GPU form (M2L on the CUDA cores) on the same workload
+    plain = None
+    if rank == 0 and precision != "fp32":
+        plain = other_depth(bb, torch, dev, pts, sigma, c, args.depth, "fp32", flush, stream)
+        plain["speedup_of_this_form"] = plain["ms_per_step"] / ms
 
     peaks, peak_kind = measured_peaks()
     clocks = clk.summary()
@@ -242,7 +247,10 @@ def run_ours(args, rank, world, local):
                                                                                      peaks["bf16_tflops"]),
                 "traffic": None}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    launches_per_step = 2 + 1 + (depth - 2) + (depth - 1) + (depth - 1) + (depth - 2) + (depth - 1) + 1 + 1
+    # gather, P2P, P2M, M2M, compress, M2L (one launch on the tensor cores,
+    # one per level in FP32), L2L, decompress, L2P, combine
+    m2l_launches = depth - 1 if precision == "fp32" else 1
+    launches_per_step = 2 + 1 + (depth - 2) + (depth - 1) + m2l_launches + (depth - 2) + (depth - 1) + 1 + 1
     out = {
         "metric": METRIC, "value": value, "unit": "N^2/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -262,6 +270,8 @@ def run_ours(args, rank, world, local):
     }
     if depth6 is not None:
         out["depth6"] = depth6
+    if plain is not None:
+        out["plain_fp32_form"] = plain
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(pts, sig_host, c)
     plan.close()
@@ -271,6 +281,7 @@ def run_ours(args, rank, world, local):
 
 
 def other_depth(bb, torch, dev, pts, sigma, c, depth, precision, flush, stream):
+    """Mean device time of 5 matvecs of another configuration (L2 flushed)."""
     plan = bb.Plan(torch.from_numpy(pts).to(dev), c["kernel"], c["p"], depth, precision=precision,
                    domain=(W.UNIT_LO, W.UNIT_SIDE))
     phi = torch.empty_like(sigma)
@@ -287,7 +298,8 @@ def other_depth(bb, torch, dev, pts, sigma, c, depth, precision, flush, stream):
         ts.append(a.elapsed_time(b))
     plan.close()
     ms = float(np.mean(ts))
-    return {"depth": depth, "ms_per_step": ms, "value": float(c["n"]) ** 2 / (ms / 1e3)}
+    return {"depth": depth, "m2l_precision": precision, "ms_per_step": ms,
+            "value": float(c["n"]) ** 2 / (ms / 1e3)}
 
 
 def accuracy_check(pts, sig, phi, c, nsample=256):

@@ -171,10 +171,14 @@ static void plan_free(bbfmm_plan_impl *P)
         cudaFree(P->chunks);
     if (P->side_stream)
         cudaStreamDestroy(P->side_stream);
+    if (P->far_stream)
+        cudaStreamDestroy(P->far_stream);
     if (P->ev_fork)
         cudaEventDestroy(P->ev_fork);
     if (P->ev_join)
         cudaEventDestroy(P->ev_join);
+    if (P->ev_far)
+        cudaEventDestroy(P->ev_far);
     for (auto &e : P->ev)
         if (e)
             cudaEventDestroy(e);
@@ -346,9 +350,13 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, cudaStream_t s)
     PTRY(plan_alloc(P, (void **)&P->phi_near, 4 * n * R, false, s));
     PTRY(plan_alloc(P, (void **)&P->status, 16, true, s));
 
-    CUDA_TRY(cudaStreamCreateWithFlags(&P->side_stream, cudaStreamNonBlocking));
+    int prio_low = 0, prio_high = 0;
+    CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+    CUDA_TRY(cudaStreamCreateWithPriority(&P->far_stream, cudaStreamNonBlocking, prio_high));
+    CUDA_TRY(cudaStreamCreateWithPriority(&P->side_stream, cudaStreamNonBlocking, prio_low));
     CUDA_TRY(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&P->ev_far, cudaEventDisableTiming));
     for (auto &e : P->ev)
         CUDA_TRY(cudaEventCreate(&e));
     CUDA_TRY(cudaEventCreate(&P->ev_p2p0));
@@ -382,34 +390,39 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
     CUDA_TRY(cudaEventRecord(P->ev_join, P->side_stream));
 
     if (D >= 2) {
+        // far field on the high-priority plan stream
+        cudaStream_t fs = P->far_stream;
+        CUDA_TRY(cudaStreamWaitEvent(fs, P->ev_fork, 0));
         const InterpTables &T = P->interp;
         auto V = [&](int l) { return O.V[O.nlev == 1 ? 0 : l - 2]; };
         auto Ut = [&](int l) { return O.Ut[O.nlev == 1 ? 0 : l - 2]; };
         // upward pass: P2M at the leaves, M2M up to level 2, compress every level
-        CUDA_TRY(launch_p2m(T, P->pts, P->sigma_s, P->leaf_off, n, D, p, nrhs, P->lev[D].M, s));
+        CUDA_TRY(launch_p2m(T, P->pts, P->sigma_s, P->leaf_off, n, D, p, nrhs, P->lev[D].M, fs));
         for (int l = D - 1; l >= 2; --l)
-            CUDA_TRY(launch_m2m(T, P->lev[l + 1].M, P->lev[l].M, l, p, nrhs, s));
+            CUDA_TRY(launch_m2m(T, P->lev[l + 1].M, P->lev[l].M, l, p, nrhs, fs));
         for (int l = D; l >= 2; --l)
             CUDA_TRY(launch_compress(P->lev[l].M, V(l), P->lev[l].Mt, P->lev[l].Mt_hi, P->lev[l].Mt_lo, l, p3, O.r,
-                                     O.rp, nrhs, s));
+                                     O.rp, nrhs, fs));
         if (tm)
-            CUDA_TRY(cudaEventRecord(P->ev[Stage::Up], s));
+            CUDA_TRY(cudaEventRecord(P->ev[Stage::Up], fs));
         // far field, all levels
-        CUDA_TRY(launch_m2l_all(P, nrhs, s));
+        CUDA_TRY(launch_m2l_all(P, nrhs, fs));
         if (tm)
-            CUDA_TRY(cudaEventRecord(P->ev[Stage::M2L], s));
+            CUDA_TRY(cudaEventRecord(P->ev[Stage::M2L], fs));
         // downward pass
         for (int l = 2; l <= D; ++l) {
             if (l >= 3)
-                CUDA_TRY(launch_l2l(T, P->lev[l - 1].F, P->lev[l].F, l - 1, p, nrhs, s));
+                CUDA_TRY(launch_l2l(T, P->lev[l - 1].F, P->lev[l].F, l - 1, p, nrhs, fs));
             CUDA_TRY(launch_decompress(P->lev[l].Ft, P->m2l_groups, (1LL << (3 * l)) * P->max_nrhs * O.rp, Ut(l),
-                                       P->lev[l].F, l, p3, O.p3p, O.r, O.rp, nrhs, l >= 3, s));
+                                       P->lev[l].F, l, p3, O.p3p, O.r, O.rp, nrhs, l >= 3, fs));
         }
         if (tm)
-            CUDA_TRY(cudaEventRecord(P->ev[Stage::Down], s));
-        CUDA_TRY(launch_l2p(T, P->pts, P->lev[D].F, P->leaf_off, n, D, p, nrhs, P->phi_far, s));
+            CUDA_TRY(cudaEventRecord(P->ev[Stage::Down], fs));
+        CUDA_TRY(launch_l2p(T, P->pts, P->lev[D].F, P->leaf_off, n, D, p, nrhs, P->phi_far, fs));
         if (tm)
-            CUDA_TRY(cudaEventRecord(P->ev[Stage::L2P], s));
+            CUDA_TRY(cudaEventRecord(P->ev[Stage::L2P], fs));
+        CUDA_TRY(cudaEventRecord(P->ev_far, fs));
+        CUDA_TRY(cudaStreamWaitEvent(s, P->ev_far, 0));
     } else if (tm) {
         for (int k = Stage::Up; k <= Stage::L2P; ++k)
             CUDA_TRY(cudaEventRecord(P->ev[k], s));
