@@ -81,7 +81,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.reader = threading.Thread(target=self._read, daemon=True)
             self.reader.start()
@@ -155,28 +155,35 @@ def run_ours(args, rank, world, local):
     def step():
         bb.bbfmm_matvec(plan.handle, sigma, phi, 1, stream)
 
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-
-    # per-stage device times (CUDA events inside the library, on its streams)
-    bb.bbfmm_set_timing(plan.handle, True)
-    stage = np.zeros(8)
-    for _ in range(3):
-        flush.fill_(1.0)
-        step()
-        torch.cuda.synchronize()
-        stage += bb.bbfmm_stage_times(plan.handle)
-    stage /= 3
-    bb.bbfmm_set_timing(plan.handle, False)
-
-    # timed steps
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # clocks are sampled (every 100 ms) from the last second of warm-up through
+    # the timed steps: the timed region alone is shorter than one sample period
     with ClockSampler(local) as clk:
+        t_end = time.perf_counter() + 1.0
+        k = 0
+        while k < max(args.warmup, 3) or time.perf_counter() < t_end:
+            step()
+            k += 1
+            if k % 16 == 0:
+                torch.cuda.synchronize()
+        torch.cuda.synchronize()
+
+        # per-stage device times (CUDA events inside the library, on its streams)
+        bb.bbfmm_set_timing(plan.handle, True)
+        stage = np.zeros(8)
+        for _ in range(3):
+            flush.fill_(1.0)
+            step()
+            torch.cuda.synchronize()
+            stage += bb.bbfmm_stage_times(plan.handle)
+        stage /= 3
+        bb.bbfmm_set_timing(plan.handle, False)
+
+        # timed steps
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         t_wall0 = time.perf_counter()
         for k in range(args.steps):
             flush.fill_(float(k))
@@ -226,7 +233,7 @@ def run_ours(args, rank, world, local):
     clocks = clk.summary()
     N = float(n)
     value = world * N * N / (ms / 1e3)
-    passes = {"fp32": 1, "tf32": 1, "tf32x3": 3, "bf16x3": 3}[precision]
+    passes = {"fp32": 1, "tf32": 1, "tf32x3": 3, "bf16x3": 3, "fp16x3": 3}[precision]
     m2l_ms = float(stage[2])
     p2p_ms = float(stage[5])
     m2l_fl = m2l_flops_per_rhs(info, passes)
@@ -239,12 +246,18 @@ def run_ours(args, rank, world, local):
                 "peak_source": "FP32 FMA: %d SMs x 128 lanes x 2 flop x median SM clock %.0f MHz"
                                % (props.multi_processor_count, f_mhz),
                 "traffic": None}
-    else:
+    elif precision in ("tf32", "tf32x3"):
         tf32 = peaks["bf16_tflops"] * (1.1 / 2.25)
         roof = {"kernel": "k_m2l_tc (all levels)", "bound": "tensor",
                 "achieved": m2l_fl / (m2l_ms / 1e3) / 1e12, "peak": tf32, "unit": "TFLOP/s",
                 "peak_source": "%s bf16 %.0f TF/s x nominal tf32/bf16 ratio 1.1/2.25" % (peak_kind,
                                                                                      peaks["bf16_tflops"]),
+                "traffic": None}
+    else:   # FP16 / BF16 operands run at the 16-bit dense rate
+        roof = {"kernel": "k_m2l_tc (all levels)", "bound": "tensor",
+                "achieved": m2l_fl / (m2l_ms / 1e3) / 1e12, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                "peak_source": "%s bf16 dense %.0f TF/s (fp16 runs at the same rate)" % (peak_kind,
+                                                                                      peaks["bf16_tflops"]),
                 "traffic": None}
     roof["frac"] = roof["achieved"] / roof["peak"]
     # gather, P2P, P2M, M2M, compress, M2L (one launch on the tensor cores,

@@ -53,8 +53,10 @@ extern "C" {
 /* arithmetic of the M2L stage (every other stage computes in FP32) */
 #define BBFMM_PREC_FP32 0   /* FP32 FMA on the CUDA cores */
 #define BBFMM_PREC_TF32 1   /* tensor cores, one TF32 pass, FP32 accumulation */
-#define BBFMM_PREC_TF32X3 2 /* tensor cores, 3-pass split TF32 (hi*hi + hi*lo + lo*hi) */
-#define BBFMM_PREC_BF16X3 3 /* tensor cores, 3-pass split BF16 (hi*hi + hi*lo + lo*hi) */
+#define BBFMM_PREC_TF32X3 2 /* tensor cores, 3-pass split TF32 (hi*hi + hi*lo + lo*hi), ~21 bits */
+#define BBFMM_PREC_BF16X3 3 /* tensor cores, 3-pass split BF16 (hi*hi + hi*lo + lo*hi), ~16 bits */
+#define BBFMM_PREC_FP16X3 4 /* tensor cores, 3-pass split FP16 with power-of-two scaling per
+                               level (hi*hi + hi*lo + lo*hi), ~21 bits */
 
 typedef struct bbfmm_plan_s *bbfmm_plan_t; /* opaque; owned by the library */
 

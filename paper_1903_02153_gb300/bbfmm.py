@@ -22,10 +22,10 @@ BBFMM_OK, BBFMM_EINVAL, BBFMM_ENOMEM, BBFMM_ECUDA = 0, -1, -2, -3
 BBFMM_ETIMEOUT, BBFMM_EBUSY, BBFMM_EINTERNAL = -4, -5, -6
 BBFMM_K_INV_R, BBFMM_K_INV_R2, BBFMM_K_EXP, BBFMM_K_GAUSS = 1, 2, 3, 4
 BBFMM_K_TEST_POLY, BBFMM_K_TEST_CONST = 100, 101
-BBFMM_PREC_FP32, BBFMM_PREC_TF32, BBFMM_PREC_TF32X3, BBFMM_PREC_BF16X3 = 0, 1, 2, 3
+BBFMM_PREC_FP32, BBFMM_PREC_TF32, BBFMM_PREC_TF32X3, BBFMM_PREC_BF16X3, BBFMM_PREC_FP16X3 = 0, 1, 2, 3, 4
 
 PRECISIONS = {"fp32": BBFMM_PREC_FP32, "tf32": BBFMM_PREC_TF32, "tf32x3": BBFMM_PREC_TF32X3,
-              "bf16x3": BBFMM_PREC_BF16X3}
+              "bf16x3": BBFMM_PREC_BF16X3, "fp16x3": BBFMM_PREC_FP16X3}
 
 EXPORTED = ["bbfmm_default_opts", "bbfmm_plan", "bbfmm_matvec", "bbfmm_destroy",
             "bbfmm_last_error", "bbfmm_plan_info", "bbfmm_get_coefficients",

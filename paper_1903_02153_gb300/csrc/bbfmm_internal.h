@@ -144,15 +144,22 @@ struct DevOps {
     std::vector<float *> Ut; // [r][p3p]    decompress weights (U transposed)
     std::vector<float *> C;  // [316][rows64][rp]
     std::vector<float *> Chi, Clo; // split copies for the tensor-core M2L (hi/lo)
+    // 16-bit split copies, made on first use: [0] = FP16 (scaled by c16_scale),
+    // [1] = BF16; same [316][rows64][rp] layout
+    std::vector<uint16_t *> C16hi[2], C16lo[2];
+    std::vector<float> c16_scale[2];
+    std::mutex mu16;
     int64_t bytes = 0;
     ~DevOps();
 };
+int ensure_ops16(DevOps &O, int fmt); // capi.cu; fmt 0 = FP16, 1 = BF16
 
 // ---------------------------------------------------------------------------
 // Plan
 struct Level {
     float *M = nullptr, *Mt = nullptr, *Ft = nullptr, *F = nullptr;
-    float *Mt_hi = nullptr, *Mt_lo = nullptr;
+    float *Mt_hi = nullptr, *Mt_lo = nullptr;        // split TF32 copies of Mt
+    uint16_t *Mt16_hi = nullptr, *Mt16_lo = nullptr; // split 16-bit copies of Mt
 };
 
 struct Stage { // indices into Plan::ev
@@ -184,6 +191,10 @@ struct bbfmm_plan_impl {
     float *sigma_s = nullptr, *phi_far = nullptr, *phi_near = nullptr;
     float *io_sigma = nullptr, *io_phi = nullptr; // staging for host sigma / phi
     int *status = nullptr;                        // device status word
+    // 16-bit split M2L: per level max |M~| (float bits) and the power-of-two
+    // scale applied before splitting, both written on the device each matvec
+    unsigned *a16_max = nullptr;
+    float *a16_scale = nullptr;
 
     std::vector<void *> allocations;
     int64_t bytes = 0;
@@ -224,8 +235,12 @@ cudaError_t launch_p2m(const InterpTables &T, const float4 *pts, const float *si
                        int nrhs, float *M, cudaStream_t s);
 cudaError_t launch_m2m(const InterpTables &T, const float *Mchild, float *Mparent, int lparent, int p, int nrhs, cudaStream_t s);
 cudaError_t launch_l2l(const InterpTables &T, const float *Fparent, float *Fchild, int lparent, int p, int nrhs, cudaStream_t s);
-cudaError_t launch_compress(const float *M, const float *V, float *Mt, float *Mt_hi, float *Mt_lo, int l, int p3,
-                            int r, int rp, int nrhs, cudaStream_t s);
+cudaError_t launch_compress(const float *M, const float *V, float *Mt, float *Mt_hi, float *Mt_lo, unsigned *maxbits,
+                            int l, int p3, int r, int rp, int nrhs, cudaStream_t s);
+// split Mt (n floats) into 16-bit hi / lo after scaling by a power of two
+// chosen from *maxbits (FP16) or 1 (BF16); the scale is written to *scale
+cudaError_t launch_split16(const float *Mt, int64_t n, int fmt, const unsigned *maxbits, float *scale, uint16_t *hi,
+                           uint16_t *lo, cudaStream_t s);
 cudaError_t launch_decompress(const float *Ft, int nslices, int64_t slice, const float *Ut, float *F, int l,
                               int p3, int p3p, int r, int rp, int nrhs, bool accumulate, cudaStream_t s);
 cudaError_t launch_l2p(const InterpTables &T, const float4 *pts, const float *F, const int *leaf_off, int64_t n, int D, int p,

@@ -7,6 +7,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include <map>
 #include <tuple>
 
@@ -55,6 +58,58 @@ DevOps::~DevOps()
         for (float *ptr : *v)
             if (ptr)
                 cudaFree(ptr);
+    for (int f = 0; f < 2; ++f)
+        for (auto *v : {&C16hi[f], &C16lo[f]})
+            for (uint16_t *ptr : *v)
+                if (ptr)
+                    cudaFree(ptr);
+}
+
+// 16-bit split copies of the M2L operators (fmt 0 = FP16 scaled by a power of
+// two per operator level so that max |C| s lies in (2^12, 2^13]; 1 = BF16)
+int ensure_ops16(DevOps &O, int fmt)
+{
+    std::lock_guard<std::mutex> g(O.mu16);
+    if ((int)O.C16hi[fmt].size() == O.nlev)
+        return BBFMM_OK;
+    const HostOps &h = *O.host;
+    const int r = O.r, rp = O.rp, rows64 = O.rows64;
+    for (int k = 0; k < O.nlev; ++k) {
+        double mx = 0.0;
+        for (double v : h.C[k])
+            mx = std::max(mx, fabs(v));
+        int e = 0;
+        if (mx > 0.0)
+            frexp(mx, &e);
+        const float s = fmt == 0 ? (float)ldexp(1.0, 13 - e) : 1.0f;
+        const size_t cnt = (size_t)kNumOffsets * rows64 * rp;
+        std::vector<uint16_t> hi(cnt, 0), lo(cnt, 0);
+        for (int t = 0; t < kNumOffsets; ++t)
+            for (int a = 0; a < r; ++a)
+                for (int b = 0; b < r; ++b) {
+                    const float x = (float)h.C[k][((size_t)t * r + a) * r + b] * s;
+                    const size_t i = ((size_t)t * rows64 + a) * rp + b;
+                    if (fmt == 0) {
+                        __half hh = __float2half_rn(x);
+                        hi[i] = __half_as_ushort(hh);
+                        lo[i] = __half_as_ushort(__float2half_rn(x - __half2float(hh)));
+                    } else {
+                        __nv_bfloat16 hh = __float2bfloat16_rn(x);
+                        hi[i] = __bfloat16_as_ushort(hh);
+                        lo[i] = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(hh)));
+                    }
+                }
+        uint16_t *dhi = nullptr, *dlo = nullptr;
+        CUDA_TRY(cudaMalloc(&dhi, cnt * 2));
+        O.C16hi[fmt].push_back(dhi);
+        CUDA_TRY(cudaMalloc(&dlo, cnt * 2));
+        O.C16lo[fmt].push_back(dlo);
+        CUDA_TRY(cudaMemcpy(dhi, hi.data(), cnt * 2, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(dlo, lo.data(), cnt * 2, cudaMemcpyHostToDevice));
+        O.c16_scale[fmt].push_back(s);
+        O.bytes += (int64_t)cnt * 4;
+    }
+    return BBFMM_OK;
 }
 
 typedef std::tuple<int, double, int, double, int, double, int> OpsKey;
@@ -340,10 +395,19 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, cudaStream_t s)
         PTRY(plan_alloc(P, (void **)&L.F, 4 * nb * R * p3, false, s));
         PTRY(plan_alloc(P, (void **)&L.Mt, 4 * 8 * (H + 2) * H * H * R * rp, true, s));
         PTRY(plan_alloc(P, (void **)&L.Ft, 4 * nb * R * rp * P->m2l_groups, true, s));
-        if (P->precision == BBFMM_PREC_TF32X3 || P->precision == BBFMM_PREC_BF16X3) {
+        if (P->precision == BBFMM_PREC_TF32X3) {
             PTRY(plan_alloc(P, (void **)&L.Mt_hi, 4 * 8 * (H + 2) * H * H * R * rp, true, s));
             PTRY(plan_alloc(P, (void **)&L.Mt_lo, 4 * 8 * (H + 2) * H * H * R * rp, true, s));
         }
+        if (P->precision == BBFMM_PREC_FP16X3 || P->precision == BBFMM_PREC_BF16X3) {
+            PTRY(plan_alloc(P, (void **)&L.Mt16_hi, 2 * 8 * (H + 2) * H * H * R * rp, true, s));
+            PTRY(plan_alloc(P, (void **)&L.Mt16_lo, 2 * 8 * (H + 2) * H * H * R * rp, true, s));
+        }
+    }
+    if (P->precision == BBFMM_PREC_FP16X3 || P->precision == BBFMM_PREC_BF16X3) {
+        PTRY(ensure_ops16(*P->ops, P->precision == BBFMM_PREC_FP16X3 ? 0 : 1));
+        PTRY(plan_alloc(P, (void **)&P->a16_max, 4 * (kMaxDepth + 1), true, s));
+        PTRY(plan_alloc(P, (void **)&P->a16_scale, 4 * (kMaxDepth + 1), true, s));
     }
     PTRY(plan_alloc(P, (void **)&P->sigma_s, 4 * n * R, false, s));
     PTRY(plan_alloc(P, (void **)&P->phi_far, 4 * n * R, false, s));
@@ -400,9 +464,19 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
         CUDA_TRY(launch_p2m(T, P->pts, P->sigma_s, P->leaf_off, n, D, p, nrhs, P->lev[D].M, fs));
         for (int l = D - 1; l >= 2; --l)
             CUDA_TRY(launch_m2m(T, P->lev[l + 1].M, P->lev[l].M, l, p, nrhs, fs));
-        for (int l = D; l >= 2; --l)
-            CUDA_TRY(launch_compress(P->lev[l].M, V(l), P->lev[l].Mt, P->lev[l].Mt_hi, P->lev[l].Mt_lo, l, p3, O.r,
-                                     O.rp, nrhs, fs));
+        const bool split16 = P->precision == BBFMM_PREC_FP16X3 || P->precision == BBFMM_PREC_BF16X3;
+        if (split16)
+            CUDA_TRY(cudaMemsetAsync(P->a16_max, 0, 4 * (kMaxDepth + 1), fs));
+        for (int l = D; l >= 2; --l) {
+            CUDA_TRY(launch_compress(P->lev[l].M, V(l), P->lev[l].Mt, P->lev[l].Mt_hi, P->lev[l].Mt_lo,
+                                     split16 ? P->a16_max + l : nullptr, l, p3, O.r, O.rp, nrhs, fs));
+            if (split16) {
+                const int64_t H = 1LL << (l - 1);
+                CUDA_TRY(launch_split16(P->lev[l].Mt, 8 * (H + 2) * H * H * P->max_nrhs * O.rp,
+                                        P->precision == BBFMM_PREC_FP16X3 ? 0 : 1, P->a16_max + l,
+                                        P->a16_scale + l, P->lev[l].Mt16_hi, P->lev[l].Mt16_lo, fs));
+            }
+        }
         if (tm)
             CUDA_TRY(cudaEventRecord(P->ev[Stage::Up], fs));
         // far field, all levels
@@ -483,8 +557,8 @@ int bbfmm_plan(const double *points, int64_t n, int kernel_id, int cheb_order, i
         return fail(BBFMM_EINVAL, "depth %d out of range [0, %d]", depth, kMaxDepth);
     if (!(opts.ell > 0.0) || !(opts.svd_eps >= 0.0) || opts.max_nrhs < 1 || opts.max_nrhs > 1024)
         return fail(BBFMM_EINVAL, "invalid options (ell > 0, svd_eps >= 0, 1 <= max_nrhs <= 1024)");
-    if (opts.precision < BBFMM_PREC_FP32 || opts.precision > BBFMM_PREC_TF32X3)
-        return fail(BBFMM_EINVAL, "precision %d is not available (FP32, TF32, TF32X3)", opts.precision);
+    if (opts.precision < BBFMM_PREC_FP32 || opts.precision > BBFMM_PREC_FP16X3)
+        return fail(BBFMM_EINVAL, "unknown precision %d", opts.precision);
     if (opts.domain_given && !(opts.side > 0.0 && isfinite(opts.side) && isfinite(opts.lo[0]) &&
                                isfinite(opts.lo[1]) && isfinite(opts.lo[2])))
         return fail(BBFMM_EINVAL, "invalid domain");

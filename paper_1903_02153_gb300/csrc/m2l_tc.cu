@@ -79,7 +79,7 @@ constexpr int kMaxTcLevels = 8;
 struct TcLevel {
     float *Ft;     // partial slice g at Ft + g * slice
     int64_t slice; // floats per slice
-    int H, tiles_x, tiles_y, tiles_z, ntiles, item_base, opl;
+    int H, tiles_x, tiles_y, tiles_z, ntiles, item_base, opl, l;
     float scale;
 };
 
@@ -87,6 +87,8 @@ struct TcLaunch {
     CUtensorMap a[kMaxTcLevels], alo[kMaxTcLevels]; // M~ (hi, lo) of each level
     CUtensorMap b[kMaxTcLevels], blo[kMaxTcLevels]; // C (hi, lo) of each operator level
     TcLevel lev[kMaxTcLevels];
+    float bscale_inv[kMaxTcLevels]; // 1 / (scale of the 16-bit operators), per operator level
+    const float *ascale;            // 16-bit forms: scale of M~ per tree level (device)
     int nlev, nitems, groups, per_group;
     int *status;
     int r, rp, nb, ncols, nrhs, nk, nstage;
@@ -121,9 +123,13 @@ __device__ __forceinline__ Item decode_item(const TcLaunch &P, int item)
     return it;
 }
 
-template <int NPROD, bool SPLIT, int CH>
+// FMT: operand format, 0 = TF32 (kind::tf32, 32 elements per 128-byte row,
+// K = 8 per MMA), 1 = FP16, 2 = BF16 (kind::f16, 64 elements per row, K = 16)
+template <int NPROD, bool SPLIT, int CH, int FMT>
 __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_constant__ TcLaunch P)
 {
+    constexpr int CHUNK = FMT == 0 ? 32 : 64; // K elements per stage (one 128-byte row)
+    constexpr int KSTEP = FMT == 0 ? 8 : 16;  // K elements per MMA (32 bytes)
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -182,16 +188,16 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
                     const uint32_t fb = full0 + 8 * s;
                     mbar_arrive_expect_tx(fb, P.stage_bytes);
                     last_round[s] = round;
-                    tma_load_5d(sa, &P.a[w.L], fb, 32 * kc, w.c, X0 + ux, Y0 + uy, zq);
+                    tma_load_5d(sa, &P.a[w.L], fb, CHUNK * kc, w.c, X0 + ux, Y0 + uy, zq);
                     uint32_t off = P.a_bytes;
                     if (NPROD == 3) {
-                        tma_load_5d(sa + off, &P.alo[w.L], fb, 32 * kc, w.c, X0 + ux, Y0 + uy, zq);
+                        tma_load_5d(sa + off, &P.alo[w.L], fb, CHUNK * kc, w.c, X0 + ux, Y0 + uy, zq);
                         off += P.a_bytes;
                     }
-                    tma_load_3d(sa + off, &P.b[lv.opl], fb, 32 * kc, 0, en.x);
+                    tma_load_3d(sa + off, &P.b[lv.opl], fb, CHUNK * kc, 0, en.x);
                     off += P.b_bytes;
                     if (NPROD == 3)
-                        tma_load_3d(sa + off, &P.blo[lv.opl], fb, 32 * kc, 0, en.x);
+                        tma_load_3d(sa + off, &P.blo[lv.opl], fb, CHUNK * kc, 0, en.x);
                 }
             }
         }
@@ -204,7 +210,7 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
             }
     } else if (warp == 1 && lane == 0) {
         // ------------------------------------------------------------ MMA issuer
-        const uint32_t idesc = idesc_tf32(128, P.nb);
+        const uint32_t idesc = FMT == 0 ? idesc_tf32(128, P.nb) : idesc_f16(128, P.nb, FMT == 2 ? 1 : 0);
         int it = 0, go = 0; // stage counter, offset counter (partial buffers)
         bool ok = true;
         for (int item = blockIdx.x; item < P.nitems && ok && !*abort_flag; item += gridDim.x) {
@@ -232,17 +238,25 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
                     const uint32_t b_off = NPROD == 3 ? 2 * P.a_bytes : P.a_bytes;
                     const uint64_t b_hi = sw128_desc(sa + b_off);
                     const uint64_t b_lo = sw128_desc(sa + b_off + P.b_bytes);
-                    const int rem = P.r - 32 * kc;
-                    const int ksteps = rem >= 32 ? 4 : (rem + 7) / 8;
+                    const int rem = P.r - CHUNK * kc;
+                    const int ksteps = rem >= CHUNK ? 4 : (rem + KSTEP - 1) / KSTEP;
                     for (int k = 0; k < ksteps; ++k) {
                         const uint64_t dk = (uint64_t)(2 * k); // 32 bytes >> 4
-                        mma_tf32(d, a_hi + dk, b_hi + dk, idesc, acc);
-                        acc = 1;
-                        if (NPROD == 3) {
-                            mma_tf32(dc, a_hi + dk, b_lo + dk, idesc, accc);
-                            accc = 1;
-                            mma_tf32(dc, a_lo + dk, b_hi + dk, idesc, 1);
+                        if (FMT == 0) {
+                            mma_tf32(d, a_hi + dk, b_hi + dk, idesc, acc);
+                            if (NPROD == 3) {
+                                mma_tf32(dc, a_hi + dk, b_lo + dk, idesc, accc);
+                                mma_tf32(dc, a_lo + dk, b_hi + dk, idesc, 1);
+                            }
+                        } else {
+                            mma_f16(d, a_hi + dk, b_hi + dk, idesc, acc);
+                            if (NPROD == 3) {
+                                mma_f16(dc, a_hi + dk, b_lo + dk, idesc, accc);
+                                mma_f16(dc, a_lo + dk, b_hi + dk, idesc, 1);
+                            }
                         }
+                        acc = 1;
+                        accc = 1;
                     }
                     mma_commit(empty0 + 8 * s); // frees the stage once these MMAs have read it
                 }
@@ -315,13 +329,16 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
                 float *out = lv.Ft + (int64_t)w.g * lv.slice +
                              ((((int64_t)w.ot * lv.H + Z) * lv.H + Y) * lv.H + X) * (int64_t)P.nrhs * P.rp +
                              (int64_t)w.c * P.rp;
+                // level scale; 16-bit forms also undo the power-of-two operand scales
+                float f = lv.scale;
+                if (FMT != 0)
+                    f *= P.bscale_inv[lv.opl] / __ldg(P.ascale + lv.l);
 #pragma unroll
                 for (int j = 0; j < 128; j += 4) {
                     const int col = 128 * half + j;
                     if (col < P.r)
                         *reinterpret_cast<float4 *>(out + col) =
-                            make_float4(lv.scale * acc[j], lv.scale * acc[j + 1], lv.scale * acc[j + 2],
-                                        lv.scale * acc[j + 3]);
+                            make_float4(f * acc[j], f * acc[j + 1], f * acc[j + 2], f * acc[j + 3]);
                 }
             }
         }
@@ -372,30 +389,38 @@ static cudaError_t tc_init()
     return cudaSuccess;
 }
 
-// M~ (parity split, padded in Z): dims (rp, R, H, H, 8 (H + 2)); box (32, 1, 8, 4, 4)
-static cudaError_t encode_a(CUtensorMap *tm, const float *ptr, int H, int R, int rp)
+
+// M~ (parity split, padded in Z): dims (rp, R, H, H, 8 (H + 2)); box (one
+// 128-byte row of K, 1, 8, 4, 4); elem = 4 (FP32 / TF32) or 2 (FP16 / BF16)
+static cudaError_t encode_a(CUtensorMap *tm, const void *ptr, int H, int R, int rp, int fmt)
 {
+    const cuuint64_t es_b = fmt == 0 ? 4 : 2;
     cuuint64_t dims[5] = {(cuuint64_t)rp, (cuuint64_t)R, (cuuint64_t)H, (cuuint64_t)H, (cuuint64_t)8 * (H + 2)};
-    cuuint64_t strides[4] = {(cuuint64_t)rp * 4, (cuuint64_t)R * rp * 4, (cuuint64_t)H * R * rp * 4,
-                             (cuuint64_t)H * H * R * rp * 4};
-    cuuint32_t box[5] = {32, 1, 8, 4, 4};
+    cuuint64_t strides[4] = {(cuuint64_t)rp * es_b, (cuuint64_t)R * rp * es_b, (cuuint64_t)H * R * rp * es_b,
+                             (cuuint64_t)H * H * R * rp * es_b};
+    cuuint32_t box[5] = {(cuuint32_t)(128 / es_b), 1, 8, 4, 4};
     cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, (void *)ptr, dims, strides, box, es,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUtensorMapDataType dt = fmt == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                      : (fmt == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+    CUresult r = g_encode(tm, dt, 5, (void *)ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// C (operators): dims (rp, rows64, 316); box (32, nb, 1)
-static cudaError_t encode_b(CUtensorMap *tm, const float *ptr, int rp, int rows64, int nb)
+// C (operators): dims (rp, rows64, 316); box (one 128-byte row of K, nb, 1)
+static cudaError_t encode_b(CUtensorMap *tm, const void *ptr, int rp, int rows64, int nb, int fmt)
 {
+    const cuuint64_t es_b = fmt == 0 ? 4 : 2;
     cuuint64_t dims[3] = {(cuuint64_t)rp, (cuuint64_t)rows64, (cuuint64_t)kNumOffsets};
-    cuuint64_t strides[2] = {(cuuint64_t)rp * 4, (cuuint64_t)rows64 * rp * 4};
-    cuuint32_t box[3] = {32, (cuuint32_t)nb, 1};
+    cuuint64_t strides[2] = {(cuuint64_t)rp * es_b, (cuuint64_t)rows64 * rp * es_b};
+    cuuint32_t box[3] = {(cuuint32_t)(128 / es_b), (cuuint32_t)nb, 1};
     cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)ptr, dims, strides, box, es,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUtensorMapDataType dt = fmt == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                      : (fmt == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+    CUresult r = g_encode(tm, dt, 3, (void *)ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -429,15 +454,23 @@ int m2l_groups_for(int D, int nrhs, int precision)
     return best;
 }
 
-template <int NPROD, bool SPLIT, int CH>
+template <int NPROD, bool SPLIT, int CH, int FMT>
 static cudaError_t launch_tc(const TcLaunch &P, int grid, size_t smem, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_m2l_tc<NPROD, SPLIT, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_m2l_tc<NPROD, SPLIT, CH, FMT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    k_m2l_tc<NPROD, SPLIT, CH><<<grid, 64 + 128 * CH, smem, s>>>(P);
+    k_m2l_tc<NPROD, SPLIT, CH, FMT><<<grid, 64 + 128 * CH, smem, s>>>(P);
     return cudaGetLastError();
+}
+
+template <int FMT>
+static cudaError_t launch_three(const TcLaunch &L, bool split, int CH, int grid, size_t smem, cudaStream_t s)
+{
+    if (split)
+        return launch_tc<3, true, 1, FMT>(L, grid, smem, s);
+    return CH == 1 ? launch_tc<3, false, 1, FMT>(L, grid, smem, s) : launch_tc<3, false, 2, FMT>(L, grid, smem, s);
 }
 
 cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
@@ -460,9 +493,14 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
     cudaError_t e = tc_init();
     if (e != cudaSuccess)
         return e;
-    const bool three = P->precision == BBFMM_PREC_TF32X3;
+    // operand format: 0 = TF32 (1 or 3 passes), 1 = FP16 x3, 2 = BF16 x3
+    const int fmt = P->precision == BBFMM_PREC_FP16X3 ? 1 : P->precision == BBFMM_PREC_BF16X3 ? 2 : 0;
+    const bool three = P->precision != BBFMM_PREC_TF32;
+    const int elem = fmt == 0 ? 4 : 2, chunk = 128 / elem;
     const int nb = (O.r + 15) / 16 * 16;
     if (nb > 256 || O.rp % 16 != 0 || P->D - 1 > kMaxTcLevels)
+        return cudaErrorInvalidValue;
+    if (fmt != 0 && (int)O.C16hi[fmt - 1].size() != O.nlev)
         return cudaErrorInvalidValue;
     TcLaunch L;
     memset(&L, 0, sizeof(L));
@@ -472,12 +510,13 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
     L.nb = nb;
     L.ncols = nb <= 32 ? 32 : nb <= 64 ? 64 : nb <= 128 ? 128 : 256;
     L.nrhs = nrhs;
-    L.nk = (O.r + 31) / 32;
+    L.nk = (O.r + chunk - 1) / chunk;
     L.groups = P->m2l_groups;
     L.per_group = (kOffsetsPerClass + L.groups - 1) / L.groups;
     L.a_bytes = 128 * 128;
     L.b_bytes = (uint32_t)nb * 128;
     L.stage_bytes = (three ? 2 : 1) * (L.a_bytes + L.b_bytes);
+    L.ascale = P->a16_scale;
     const size_t budget = 220 * 1024;
     int nstage = (int)((budget - 1024 - 256) / L.stage_bytes);
     nstage = nstage > 8 ? 8 : nstage;
@@ -500,21 +539,39 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
         lv.ntiles = tiles_of_level(l, nrhs);
         lv.item_base = items;
         lv.opl = O.nlev == 1 ? 0 : l - 2;
+        lv.l = l;
         lv.scale = scale_of(l);
         items += lv.ntiles * L.groups;
-        const float *A = three ? P->lev[l].Mt_hi : P->lev[l].Mt;
-        e = encode_a(&L.a[L.nlev], A, H, P->max_nrhs, O.rp);
+        const void *A, *Alo;
+        if (fmt != 0) {
+            A = P->lev[l].Mt16_hi;
+            Alo = P->lev[l].Mt16_lo;
+        } else {
+            A = three ? (const void *)P->lev[l].Mt_hi : (const void *)P->lev[l].Mt;
+            Alo = three ? (const void *)P->lev[l].Mt_lo : A;
+        }
+        e = encode_a(&L.a[L.nlev], A, H, P->max_nrhs, O.rp, fmt);
         if (e == cudaSuccess)
-            e = encode_a(&L.alo[L.nlev], three ? P->lev[l].Mt_lo : A, H, P->max_nrhs, O.rp);
+            e = encode_a(&L.alo[L.nlev], Alo, H, P->max_nrhs, O.rp, fmt);
         if (e != cudaSuccess)
             return e;
         L.nlev++;
     }
     L.nitems = items;
     for (int k = 0; k < O.nlev; ++k) {
-        e = encode_b(&L.b[k], three ? O.Chi[k] : O.C[k], O.rp, O.rows64, nb);
+        const void *B, *Blo;
+        if (fmt != 0) {
+            B = O.C16hi[fmt - 1][k];
+            Blo = O.C16lo[fmt - 1][k];
+            L.bscale_inv[k] = 1.0f / O.c16_scale[fmt - 1][k];
+        } else {
+            B = three ? (const void *)O.Chi[k] : (const void *)O.C[k];
+            Blo = three ? (const void *)O.Clo[k] : B;
+            L.bscale_inv[k] = 1.0f;
+        }
+        e = encode_b(&L.b[k], B, O.rp, O.rows64, nb, fmt);
         if (e == cudaSuccess)
-            e = encode_b(&L.blo[k], three ? O.Clo[k] : O.C[k], O.rp, O.rows64, nb);
+            e = encode_b(&L.blo[k], Blo, O.rp, O.rows64, nb, fmt);
         if (e != cudaSuccess)
             return e;
     }
@@ -522,11 +579,13 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
     const int CH = nb > 128 ? 2 : 1;
     // two accumulators per partial buffer need 4 x ncols <= 512 TMEM columns
     const bool split = three && P->split_acc && L.ncols <= 128;
-    if (three && split)
-        return launch_tc<3, true, 1>(L, grid, smem, s);
-    if (three)
-        return CH == 1 ? launch_tc<3, false, 1>(L, grid, smem, s) : launch_tc<3, false, 2>(L, grid, smem, s);
-    return CH == 1 ? launch_tc<1, false, 1>(L, grid, smem, s) : launch_tc<1, false, 2>(L, grid, smem, s);
+    if (!three)
+        return CH == 1 ? launch_tc<1, false, 1, 0>(L, grid, smem, s) : launch_tc<1, false, 2, 0>(L, grid, smem, s);
+    if (fmt == 0)
+        return launch_three<0>(L, split, CH, grid, smem, s);
+    if (fmt == 1)
+        return launch_three<1>(L, split, CH, grid, smem, s);
+    return launch_three<2>(L, split, CH, grid, smem, s);
 }
 
 } // namespace bbfmm

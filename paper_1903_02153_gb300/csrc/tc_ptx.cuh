@@ -94,6 +94,15 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uin
                  "l"(a), "l"(b), "r"(idesc), "r"(acc)
                  : "memory");
 }
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (FP16 or BF16 operands, both the
+// same type), FP32 accumulate
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+                 "l"(a), "l"(b), "r"(idesc), "r"(acc)
+                 : "memory");
+}
 // arrive (once) on an mbarrier when all MMAs issued so far by this thread are done
 __device__ __forceinline__ void mma_commit(uint32_t bar)
 {
@@ -134,6 +143,14 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
 {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// instruction descriptor of kind::f16: D = F32, A = B = FP16 (bf16 = 0) or
+// BF16 (bf16 = 1), both K-major
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int bf16)
+{
+    return (1u << 4) | ((uint32_t)bf16 << 7) | ((uint32_t)bf16 << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
 }
 
 } // namespace bbfmm

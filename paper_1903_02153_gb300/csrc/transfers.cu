@@ -7,6 +7,9 @@
 // reference coordinate of a point in its leaf (the [-1,1] frame of Def. 2.2)
 // is s = 2u.  The 1D Lagrange basis is evaluated as
 // l_i(s) = w_i prod_{k != i} (s - s_k) with w_i = 1 / prod_{k != i} (s_i - s_k).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "bbfmm_internal.h"
 
 namespace bbfmm {
@@ -309,7 +312,7 @@ __global__ void __launch_bounds__(256) k_node_gemm(const float *__restrict__ A, 
                                                    float *__restrict__ Out, int64_t rows, int K, int N, int ldw,
                                                    int lda, int ldo, int level, int nrhs, int accumulate,
                                                    float *__restrict__ Out_hi, float *__restrict__ Out_lo,
-                                                   int nslices, int64_t slice)
+                                                   int nslices, int64_t slice, unsigned *__restrict__ maxbits)
 {
     __shared__ float As[16][64 + 4];
     __shared__ float Ws[16][64 + 4];
@@ -392,14 +395,72 @@ __global__ void __launch_bounds__(256) k_node_gemm(const float *__restrict__ A, 
             }
         }
     }
+    if (MODE == 0 && maxbits) { // max |M~| of the level (order-independent)
+        float m = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (row0 + ty * 4 + i < rows && col0 + tx * 4 + j < N)
+                    m = fmaxf(m, fabsf(acc[i][j]));
+        for (int o = 16; o > 0; o >>= 1)
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((tid & 31) == 0)
+            atomicMax(maxbits, __float_as_uint(m));
+    }
 }
 
-cudaError_t launch_compress(const float *M, const float *V, float *Mt, float *Mt_hi, float *Mt_lo, int l, int p3,
-                            int r, int rp, int nrhs, cudaStream_t s)
+// 16-bit split: x * s = hi + lo, hi = round16(x s), lo = round16(x s - hi);
+// s = 2^(13 - e) with 2^(e-1) < max|x| <= 2^e for FP16 (keeps hi below the
+// FP16 range limit and lo away from the subnormals), s = 1 for BF16
+template <int FMT>
+__global__ void k_split16(const float *__restrict__ x, int64_t n, const unsigned *__restrict__ maxbits,
+                          float *__restrict__ scale, uint16_t *__restrict__ hi, uint16_t *__restrict__ lo)
+{
+    float s = 1.0f;
+    if (FMT == 0) {
+        float mx = __uint_as_float(*maxbits);
+        int e = 0;
+        if (mx > 0.0f)
+            frexpf(mx, &e);
+        s = ldexpf(1.0f, 13 - e);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        *scale = s;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float v = x[i] * s;
+        if (FMT == 0) {
+            __half h = __float2half_rn(v);
+            __half l = __float2half_rn(v - __half2float(h));
+            hi[i] = __half_as_ushort(h);
+            lo[i] = __half_as_ushort(l);
+        } else {
+            __nv_bfloat16 h = __float2bfloat16_rn(v);
+            __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+            hi[i] = __bfloat16_as_ushort(h);
+            lo[i] = __bfloat16_as_ushort(l);
+        }
+    }
+}
+
+cudaError_t launch_split16(const float *Mt, int64_t n, int fmt, const unsigned *maxbits, float *scale, uint16_t *hi,
+                           uint16_t *lo, cudaStream_t s)
+{
+    int64_t blocks = (n + 255) / 256;
+    blocks = blocks > 4096 ? 4096 : blocks;
+    if (fmt == 0)
+        k_split16<0><<<(unsigned)blocks, 256, 0, s>>>(Mt, n, maxbits, scale, hi, lo);
+    else
+        k_split16<1><<<(unsigned)blocks, 256, 0, s>>>(Mt, n, maxbits, scale, hi, lo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compress(const float *M, const float *V, float *Mt, float *Mt_hi, float *Mt_lo, unsigned *maxbits,
+                            int l, int p3, int r, int rp, int nrhs, cudaStream_t s)
 {
     int64_t rows = ((int64_t)1 << (3 * l)) * nrhs;
     dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((r + 63) / 64));
-    k_node_gemm<0><<<grid, 256, 0, s>>>(M, V, Mt, rows, p3, r, rp, p3, rp, l, nrhs, 0, Mt_hi, Mt_lo, 1, 0);
+    k_node_gemm<0><<<grid, 256, 0, s>>>(M, V, Mt, rows, p3, r, rp, p3, rp, l, nrhs, 0, Mt_hi, Mt_lo, 1, 0, maxbits);
     return cudaGetLastError();
 }
 
@@ -409,7 +470,7 @@ cudaError_t launch_decompress(const float *Ft, int nslices, int64_t slice, const
     int64_t rows = ((int64_t)1 << (3 * l)) * nrhs;
     dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((p3 + 63) / 64));
     k_node_gemm<1><<<grid, 256, 0, s>>>(Ft, Ut, F, rows, r, p3, p3p, rp, p3, l, nrhs, accumulate ? 1 : 0, nullptr,
-                                        nullptr, nslices, slice);
+                                        nullptr, nslices, slice, nullptr);
     return cudaGetLastError();
 }
 
