@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default=None)
     ap.add_argument("--depth", type=int, default=5)
+    ap.add_argument("--svd-eps", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-depth6", action="store_true")
     return ap.parse_args()
@@ -138,14 +139,14 @@ def run_ours(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    precision = args.precision or "tf32x3"
+    precision = args.precision or "fp16x3"
     name = "uniform-1M-p5-d%d" % args.depth
     c = dict(W.CONFIGS["uniform-1M-p5-d6"], depth=args.depth)
     n, p, depth = c["n"], c["p"], c["depth"]
     pts = W.uniform_points(n)
     sig_host = W.uniform_sigma(n).astype(np.float32)
     plan = bb.Plan(torch.from_numpy(pts).to(dev), c["kernel"], p, depth, precision=precision,
-                   domain=(W.UNIT_LO, W.UNIT_SIDE))
+                   svd_eps=args.svd_eps, domain=(W.UNIT_LO, W.UNIT_SIDE))
     info = plan.info()
     sigma = torch.from_numpy(sig_host).to(dev)
     phi = torch.empty_like(sigma)
@@ -222,11 +223,11 @@ def run_ours(args, rank, world, local):
 
     depth6 = None
     if rank == 0 and not args.no_depth6 and args.depth != 6:
-        depth6 = other_depth(bb, torch, dev, pts, sigma, c, 6, precision, flush, stream)
+        depth6 = other_depth(bb, torch, dev, pts, sigma, c, 6, precision, flush, stream, args.svd_eps)
     # the plain FP32 GPU form (M2L on the CUDA cores) on the same workload
     plain = None
     if rank == 0 and precision != "fp32":
-        plain = other_depth(bb, torch, dev, pts, sigma, c, args.depth, "fp32", flush, stream)
+        plain = other_depth(bb, torch, dev, pts, sigma, c, args.depth, "fp32", flush, stream, args.svd_eps)
         plain["speedup_of_this_form"] = plain["ms_per_step"] / ms
 
     peaks, peak_kind = measured_peaks()
@@ -270,7 +271,7 @@ def run_ours(args, rank, world, local):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "%s: N=%d uniform unit cube, 1/r, p=%d, depth %d, 1 RHS, sigma~U(-1,1)"
                                % (name, n, p, depth), "n": n, "kernel": "1/r", "p": p, "depth": depth,
-                   "nrhs": 1, "m2l_precision": precision, "svd_rank": info.rank,
+                   "nrhs": 1, "m2l_precision": precision, "svd_rank": info.rank, "svd_eps": args.svd_eps,
                    "l2": "flushed between timed steps (512 MB write)", "parallelism": "replicas"},
         "stages_ms": {k: float(v) for k, v in zip(bb.STAGES, stage)},
         "roofline": roof,
@@ -293,10 +294,10 @@ def run_ours(args, rank, world, local):
     return out if rank == 0 else None
 
 
-def other_depth(bb, torch, dev, pts, sigma, c, depth, precision, flush, stream):
+def other_depth(bb, torch, dev, pts, sigma, c, depth, precision, flush, stream, eps):
     """Mean device time of 5 matvecs of another configuration (L2 flushed)."""
     plan = bb.Plan(torch.from_numpy(pts).to(dev), c["kernel"], c["p"], depth, precision=precision,
-                   domain=(W.UNIT_LO, W.UNIT_SIDE))
+                   svd_eps=eps, domain=(W.UNIT_LO, W.UNIT_SIDE))
     phi = torch.empty_like(sigma)
     for _ in range(3):
         bb.bbfmm_matvec(plan.handle, sigma, phi, 1, stream)

@@ -234,6 +234,8 @@ static void plan_free(bbfmm_plan_impl *P)
         cudaEventDestroy(P->ev_join);
     if (P->ev_far)
         cudaEventDestroy(P->ev_far);
+    if (P->ev_up)
+        cudaEventDestroy(P->ev_up);
     for (auto &e : P->ev)
         if (e)
             cudaEventDestroy(e);
@@ -421,6 +423,7 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, cudaStream_t s)
     CUDA_TRY(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
     CUDA_TRY(cudaEventCreateWithFlags(&P->ev_far, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&P->ev_up, cudaEventDisableTiming));
     for (auto &e : P->ev)
         CUDA_TRY(cudaEventCreate(&e));
     CUDA_TRY(cudaEventCreate(&P->ev_p2p0));
@@ -442,16 +445,23 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
     if (tm)
         CUDA_TRY(cudaEventRecord(P->ev[Stage::Gather], s));
 
-    // near field on the side stream, concurrent with the far field
     CUDA_TRY(cudaEventRecord(P->ev_fork, s));
-    CUDA_TRY(cudaStreamWaitEvent(P->side_stream, P->ev_fork, 0));
-    if (tm)
-        CUDA_TRY(cudaEventRecord(P->ev_p2p0, P->side_stream));
-    CUDA_TRY(launch_p2p(P->pts, P->sigma_s, P->leaf_off, P->chunks, P->nchunks, n, D, P->kernel, P->ell,
-                        P->side / (double)(1LL << D), nrhs, P->phi_near, P->side_stream));
-    if (tm)
-        CUDA_TRY(cudaEventRecord(P->ev_p2p1, P->side_stream));
-    CUDA_TRY(cudaEventRecord(P->ev_join, P->side_stream));
+    // near field on the low-priority side stream, started once `after` has
+    // fired: its blocks then fill the SMs next to the tensor-core M2L instead of
+    // delaying the many short launches of the upward pass
+    auto near_field = [&](cudaEvent_t after) -> int {
+        CUDA_TRY(cudaStreamWaitEvent(P->side_stream, after, 0));
+        if (tm)
+            CUDA_TRY(cudaEventRecord(P->ev_p2p0, P->side_stream));
+        CUDA_TRY(launch_p2p(P->pts, P->sigma_s, P->leaf_off, P->chunks, P->nchunks, n, D, P->kernel, P->ell,
+                            P->side / (double)(1LL << D), nrhs, P->phi_near, P->side_stream));
+        if (tm)
+            CUDA_TRY(cudaEventRecord(P->ev_p2p1, P->side_stream));
+        CUDA_TRY(cudaEventRecord(P->ev_join, P->side_stream));
+        return BBFMM_OK;
+    };
+    if (D < 2)
+        PTRY(near_field(P->ev_fork));
 
     if (D >= 2) {
         // far field on the high-priority plan stream
@@ -479,6 +489,8 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
         }
         if (tm)
             CUDA_TRY(cudaEventRecord(P->ev[Stage::Up], fs));
+        CUDA_TRY(cudaEventRecord(P->ev_up, fs));
+        PTRY(near_field(P->ev_up));
         // far field, all levels
         CUDA_TRY(launch_m2l_all(P, nrhs, fs));
         if (tm)
