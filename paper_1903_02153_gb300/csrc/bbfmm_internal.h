@@ -9,7 +9,7 @@
 //                          points sorted by the Morton index of their leaf
 //   perm     [N] int      original index of the sorted point
 //   leaf_off [8^D + 1]    first sorted point of each leaf (Morton order)
-//   chunks   [nchunks]    near-field work items (leaf, first point, count <= 32)
+//   chunks   [nchunks]    near-field work items (leaf, first point, count <= 128)
 //   M_l, F_l [8^l][R][p3] multipole / local coefficients, boxes in Morton order
 //   Mt_l     [8][H+2][H][H][R][rp]  compressed multipoles, H = 2^(l-1):
 //                          split by box parity (octant o = x&1 | (y&1)<<1 | (z&1)<<2)
@@ -38,7 +38,7 @@ constexpr int kMaxP = 10;
 constexpr int kMaxDepth = 8;
 constexpr int kNumOffsets = 316;      // 7^3 - 3^3 distinct M2L offsets (Sec. 2.2, Thm. 2.1)
 constexpr int kOffsetsPerClass = 189; // 6^3 - 3^3 interaction-list boxes (Def. 2.1)
-constexpr int kChunk = 32;            // near-field targets per warp
+constexpr int kChunk = 128;           // near-field targets per work item (one block)
 
 // status word bits written by device-side checks
 constexpr int kStatusBounds = 1;
