@@ -4,66 +4,93 @@
 //
 // Work item = up to kChunk consecutive targets of one leaf; one block of 128
 // threads per item.  The block first gathers the neighbour leaves' sources
-// into shared memory (all threads at once, coalesced, 2048 at a time) as
-// float4 (x, y, z, sigma) with coordinates in the target leaf's cell units:
-// y' = u_y + (cell_y - cell_x).  The offset is an exact small integer, so the
-// FP32 difference u_x - y' only carries the rounding of u (|u| <= 1/2), not
-// that of absolute coordinates.  Threads are (target, slice) pairs,
-// thread = target + nt * slice: every slice walks a strided share of the
-// staged sources for its target (all lanes of a warp read the same source, a
-// shared-memory broadcast), and the slices of a target are summed in a fixed
-// order at the end (deterministic).
+// into shared memory (all threads at once, coalesced, kStageSrc at a time),
+// with coordinates in the target leaf's cell units: y' = u_y + (cell_y -
+// cell_x).  The offset is an exact small integer, so the FP32 difference
+// u_x - y' only carries the rounding of u (|u| <= 1/2), not that of absolute
+// coordinates.
+//
+// Each thread owns two targets (a and b) and evaluates both against every
+// source it visits with the packed two-lane FP32 instructions of sm_100+
+// (FADD2 / FMUL2 / FFMA2); a source is staged as (x, x, y, y), (z, z, s, s) so
+// both halves of a packed operand come from one shared-memory broadcast.
+// Threads are (target pair, slice): slice s walks sources s, s + S, ...; the
+// slices of a target are added in a fixed order at the end (deterministic).
 // K at r = 0 follows the library's convention: 0 for 1/r and 1/r^2.
 #include "bbfmm_internal.h"
 
 namespace bbfmm {
 
 constexpr int kP2PThreads = 128;
-constexpr int kStageSrc = 2048; // staged sources per pass (32 KB)
+constexpr int kStageSrc = 1024; // staged sources per pass (32 KB)
 
+// single hardware approximations (MUFU); distinct points never give a
+// subnormal squared distance here (|u| <= 1.5, so r2 >= 2^-48 or r2 = 0)
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// each kernel maps the packed squared distances (in cell units) r2 and the
+// packed offsets to the packed kernel values
 struct KInvR {
     float a; // unused
-    __device__ float operator()(float dx, float dy, float dz) const
+    __device__ float2 operator()(float2 r2, float2, float2, float2) const
     {
-        float r2 = dx * dx + dy * dy + dz * dz;
-        return r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+        return make_float2(r2.x > 0.0f ? rsqrt_approx(r2.x) : 0.0f, r2.y > 0.0f ? rsqrt_approx(r2.y) : 0.0f);
     }
 };
 struct KInvR2 {
     float a;
-    __device__ float operator()(float dx, float dy, float dz) const
+    __device__ float2 operator()(float2 r2, float2, float2, float2) const
     {
-        float r2 = dx * dx + dy * dy + dz * dz;
-        return r2 > 0.0f ? 1.0f / r2 : 0.0f;
+        return make_float2(r2.x > 0.0f ? rcp_approx(r2.x) : 0.0f, r2.y > 0.0f ? rcp_approx(r2.y) : 0.0f);
     }
 };
 struct KExp { // exp(-h r / ell) = 2^(-a r), a = h / (ell ln 2)
     float a;
-    __device__ float operator()(float dx, float dy, float dz) const
+    __device__ float r(float r2) const { return r2 > 0.0f ? r2 * rsqrt_approx(r2) : 0.0f; }
+    __device__ float2 operator()(float2 r2, float2, float2, float2) const
     {
-        float r2 = dx * dx + dy * dy + dz * dz;
-        return exp2f(-a * sqrtf(r2));
+        return make_float2(ex2_approx(-a * r(r2.x)), ex2_approx(-a * r(r2.y)));
     }
 };
 struct KGauss { // exp(-(h r / ell)^2) = 2^(-a r^2), a = h^2 / (ell^2 ln 2)
     float a;
-    __device__ float operator()(float dx, float dy, float dz) const
+    __device__ float2 operator()(float2 r2, float2, float2, float2) const
     {
-        float r2 = dx * dx + dy * dy + dz * dz;
-        return exp2f(-a * r2);
+        return make_float2(ex2_approx(-a * r2.x), ex2_approx(-a * r2.y));
     }
 };
 struct KPoly { // q(d) with d = h * (x - y) in physical units
-    float a; // h
-    __device__ float operator()(float dx, float dy, float dz) const
+    float a;   // h
+    __device__ float q(float dx, float dy, float dz) const
     {
         float d0 = a * dx, d1 = a * dy, d2 = a * dz;
         return 1.0f + d0 - 2.0f * d1 * d2 + 3.0f * d0 * d0 * d1;
     }
+    __device__ float2 operator()(float2, float2 dx, float2 dy, float2 dz) const
+    {
+        return make_float2(q(dx.x, dy.x, dz.x), q(dx.y, dy.y, dz.y));
+    }
 };
 struct KConst {
     float a;
-    __device__ float operator()(float, float, float) const { return 1.0f; }
+    __device__ float2 operator()(float2, float2, float2, float2) const { return make_float2(1.0f, 1.0f); }
 };
 
 template <class Kern>
@@ -72,15 +99,17 @@ __global__ void __launch_bounds__(kP2PThreads)
           const int4 *__restrict__ chunks, int nchunks, int64_t n, int D, Kern kern, float scale, int nrhs,
           float *__restrict__ phi)
 {
-    __shared__ float4 stage[kStageSrc];
+    __shared__ float4 stage_xy[kStageSrc]; // (x, x, y, y)
+    __shared__ float4 stage_zs[kStageSrc]; // (z, z, sigma, sigma)
     __shared__ int nb_start[28], nb_pre[28];
     __shared__ float4 nb_delta[27];
-    __shared__ float red[kP2PThreads];
+    __shared__ float2 red[kP2PThreads];
     const int tid = threadIdx.x;
     const int4 ch = chunks[blockIdx.x];
     const int nt = ch.z;
-    const int S = kP2PThreads / nt; // slices per target (>= 1)
-    const int t = tid % nt, slice = tid / nt;
+    const int np = (nt + 1) >> 1;    // target pairs
+    const int S = kP2PThreads / np; // slices per pair (>= 1)
+    const int t = tid % np, slice = tid / np;
     const bool active = slice < S;
     int ax, ay, az;
     demorton3((uint32_t)ch.x, ax, ay, az);
@@ -111,11 +140,14 @@ __global__ void __launch_bounds__(kP2PThreads)
     }
     __syncthreads();
     const int ns = nb_pre[27];
-    const float4 xt = pts[ch.y + (active ? t : 0)];
+    // the pair's two targets; a missing second target duplicates the first
+    const int ia = active ? t : 0, ib = active && t + np < nt ? t + np : ia;
+    const float4 xa = pts[ch.y + ia], xb = pts[ch.y + ib];
+    const float2 X = make_float2(xa.x, xb.x), Y = make_float2(xa.y, xb.y), Z = make_float2(xa.z, xb.z);
 
     for (int c = 0; c < nrhs; ++c) {
         const float *sg = sig + (int64_t)c * n;
-        float acc = 0.0f;
+        float2 acc = make_float2(0.0f, 0.0f);
         for (int base = 0; base < ns; base += kStageSrc) {
             const int cnt = min(kStageSrc, ns - base);
             for (int g = tid; g < cnt; g += kP2PThreads) {
@@ -128,25 +160,41 @@ __global__ void __launch_bounds__(kP2PThreads)
                 const int src = nb_start[k] + (gg - nb_pre[k]);
                 const float4 u = pts[src];
                 const float4 d = nb_delta[k];
-                stage[g] = make_float4(u.x + d.x, u.y + d.y, u.z + d.z, sg[src]);
+                const float s = sg[src];
+                // staged negated so that x_target - y' is one packed add
+                const float x = -(u.x + d.x), y = -(u.y + d.y), z = -(u.z + d.z);
+                stage_xy[g] = make_float4(x, x, y, y);
+                stage_zs[g] = make_float4(z, z, s, s);
             }
             __syncthreads();
             if (active) {
 #pragma unroll 4
                 for (int j = slice; j < cnt; j += S) {
-                    const float4 q = stage[j];
-                    acc += kern(xt.x - q.x, xt.y - q.y, xt.z - q.z) * q.w;
+                    const float4 qa = stage_xy[j];
+                    const float4 qb = stage_zs[j];
+                    const float2 dx = __fadd2_rn(X, make_float2(qa.x, qa.y));
+                    const float2 dy = __fadd2_rn(Y, make_float2(qa.z, qa.w));
+                    const float2 dz = __fadd2_rn(Z, make_float2(qb.x, qb.y));
+                    float2 r2 = __fmul2_rn(dx, dx);
+                    r2 = __ffma2_rn(dy, dy, r2);
+                    r2 = __ffma2_rn(dz, dz, r2);
+                    acc = __ffma2_rn(kern(r2, dx, dy, dz), make_float2(qb.z, qb.w), acc);
                 }
             }
             __syncthreads();
         }
-        red[tid] = active ? acc : 0.0f;
+        red[tid] = active ? acc : make_float2(0.0f, 0.0f);
         __syncthreads();
-        if (tid < nt) {
-            float sum = 0.0f;
-            for (int q = 0; q < S; ++q)
-                sum += red[tid + q * nt];
-            phi[(int64_t)c * n + ch.y + tid] = scale * sum;
+        if (tid < np) {
+            float sa = 0.0f, sb = 0.0f;
+            for (int q = 0; q < S; ++q) {
+                const float2 v = red[tid + q * np];
+                sa += v.x;
+                sb += v.y;
+            }
+            phi[(int64_t)c * n + ch.y + tid] = scale * sa;
+            if (tid + np < nt)
+                phi[(int64_t)c * n + ch.y + tid + np] = scale * sb;
         }
         __syncthreads();
     }
@@ -166,7 +214,7 @@ cudaError_t launch_p2p(const float4 *pts, const float *sig, const int *leaf_off,
                        int64_t n, int D, int kernel, double ell, double h, int nrhs, float *phi_near,
                        cudaStream_t s)
 {
-    static_assert(kChunk <= kP2PThreads, "a work item holds at most one target per thread");
+    static_assert(kChunk <= 2 * kP2PThreads, "a work item holds at most two targets per thread");
     const double ln2 = 0.69314718055994530942;
     switch (kernel) {
     case BBFMM_K_INV_R:
