@@ -22,7 +22,7 @@
 namespace bbfmm {
 
 constexpr int kP2PThreads = 128;
-constexpr int kStageSrc = 1024; // staged sources per pass (32 KB)
+constexpr int kStageSrc = 512; // staged sources per pass (16 KB): 8+ blocks per SM
 
 // single hardware approximations (MUFU); distinct points never give a
 // subnormal squared distance here (|u| <= 1.5, so r2 >= 2^-48 or r2 = 0)
@@ -94,7 +94,7 @@ struct KConst {
 };
 
 template <class Kern>
-__global__ void __launch_bounds__(kP2PThreads)
+__global__ void __launch_bounds__(kP2PThreads, 8)
     k_p2p(const float4 *__restrict__ pts, const float *__restrict__ sig, const int *__restrict__ off,
           const int4 *__restrict__ chunks, int nchunks, int64_t n, int D, Kern kern, float scale, int nrhs,
           float *__restrict__ phi)
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kP2PThreads)
 
     for (int c = 0; c < nrhs; ++c) {
         const float *sg = sig + (int64_t)c * n;
-        float2 acc = make_float2(0.0f, 0.0f);
+        float2 acc = make_float2(0.0f, 0.0f), acc2 = make_float2(0.0f, 0.0f);
         for (int base = 0; base < ns; base += kStageSrc) {
             const int cnt = min(kStageSrc, ns - base);
             for (int g = tid; g < cnt; g += kP2PThreads) {
@@ -168,8 +168,9 @@ __global__ void __launch_bounds__(kP2PThreads)
             }
             __syncthreads();
             if (active) {
-#pragma unroll 4
-                for (int j = slice; j < cnt; j += S) {
+                // two sources per iteration into two accumulators (shorter
+                // dependency chains); the accumulators are added in a fixed order
+                auto pair = [&](int j, float2 &a) {
                     const float4 qa = stage_xy[j];
                     const float4 qb = stage_zs[j];
                     const float2 dx = __fadd2_rn(X, make_float2(qa.x, qa.y));
@@ -178,12 +179,20 @@ __global__ void __launch_bounds__(kP2PThreads)
                     float2 r2 = __fmul2_rn(dx, dx);
                     r2 = __ffma2_rn(dy, dy, r2);
                     r2 = __ffma2_rn(dz, dz, r2);
-                    acc = __ffma2_rn(kern(r2, dx, dy, dz), make_float2(qb.z, qb.w), acc);
+                    a = __ffma2_rn(kern(r2, dx, dy, dz), make_float2(qb.z, qb.w), a);
+                };
+                int j = slice;
+#pragma unroll 2
+                for (; j + S < cnt; j += 2 * S) {
+                    pair(j, acc);
+                    pair(j + S, acc2);
                 }
+                if (j < cnt)
+                    pair(j, acc);
             }
             __syncthreads();
         }
-        red[tid] = active ? acc : make_float2(0.0f, 0.0f);
+        red[tid] = active ? make_float2(acc.x + acc2.x, acc.y + acc2.y) : make_float2(0.0f, 0.0f);
         __syncthreads();
         if (tid < np) {
             float sa = 0.0f, sb = 0.0f;
