@@ -45,53 +45,45 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
-// each kernel maps the packed squared distances (in cell units) r2 and the
-// packed offsets to the packed kernel values
+// each kernel maps the squared distance r2 (cell units) and the offsets to
+// K; the packed form applies it to both lanes
 struct KInvR {
     float a; // unused
-    __device__ float2 operator()(float2 r2, float2, float2, float2) const
-    {
-        return make_float2(r2.x > 0.0f ? rsqrt_approx(r2.x) : 0.0f, r2.y > 0.0f ? rsqrt_approx(r2.y) : 0.0f);
-    }
+    __device__ float one(float r2, float, float, float) const { return r2 > 0.0f ? rsqrt_approx(r2) : 0.0f; }
 };
 struct KInvR2 {
     float a;
-    __device__ float2 operator()(float2 r2, float2, float2, float2) const
-    {
-        return make_float2(r2.x > 0.0f ? rcp_approx(r2.x) : 0.0f, r2.y > 0.0f ? rcp_approx(r2.y) : 0.0f);
-    }
+    __device__ float one(float r2, float, float, float) const { return r2 > 0.0f ? rcp_approx(r2) : 0.0f; }
 };
 struct KExp { // exp(-h r / ell) = 2^(-a r), a = h / (ell ln 2)
     float a;
-    __device__ float r(float r2) const { return r2 > 0.0f ? r2 * rsqrt_approx(r2) : 0.0f; }
-    __device__ float2 operator()(float2 r2, float2, float2, float2) const
+    __device__ float one(float r2, float, float, float) const
     {
-        return make_float2(ex2_approx(-a * r(r2.x)), ex2_approx(-a * r(r2.y)));
+        return ex2_approx(-a * (r2 > 0.0f ? r2 * rsqrt_approx(r2) : 0.0f));
     }
 };
 struct KGauss { // exp(-(h r / ell)^2) = 2^(-a r^2), a = h^2 / (ell^2 ln 2)
     float a;
-    __device__ float2 operator()(float2 r2, float2, float2, float2) const
-    {
-        return make_float2(ex2_approx(-a * r2.x), ex2_approx(-a * r2.y));
-    }
+    __device__ float one(float r2, float, float, float) const { return ex2_approx(-a * r2); }
 };
 struct KPoly { // q(d) with d = h * (x - y) in physical units
     float a;   // h
-    __device__ float q(float dx, float dy, float dz) const
+    __device__ float one(float, float dx, float dy, float dz) const
     {
         float d0 = a * dx, d1 = a * dy, d2 = a * dz;
         return 1.0f + d0 - 2.0f * d1 * d2 + 3.0f * d0 * d0 * d1;
     }
-    __device__ float2 operator()(float2, float2 dx, float2 dy, float2 dz) const
-    {
-        return make_float2(q(dx.x, dy.x, dz.x), q(dx.y, dy.y, dz.y));
-    }
 };
 struct KConst {
     float a;
-    __device__ float2 operator()(float2, float2, float2, float2) const { return make_float2(1.0f, 1.0f); }
+    __device__ float one(float, float, float, float) const { return 1.0f; }
 };
+
+template <class Kern>
+__device__ __forceinline__ float2 kern2(const Kern &k, float2 r2, float2 dx, float2 dy, float2 dz)
+{
+    return make_float2(k.one(r2.x, dx.x, dy.x, dz.x), k.one(r2.y, dx.y, dy.y, dz.y));
+}
 
 template <class Kern>
 __global__ void __launch_bounds__(kP2PThreads, 8)
@@ -179,7 +171,7 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
                     float2 r2 = __fmul2_rn(dx, dx);
                     r2 = __ffma2_rn(dy, dy, r2);
                     r2 = __ffma2_rn(dz, dz, r2);
-                    a = __ffma2_rn(kern(r2, dx, dy, dz), make_float2(qb.z, qb.w), a);
+                    a = __ffma2_rn(kern2(kern, r2, dx, dy, dz), make_float2(qb.z, qb.w), a);
                 };
                 int j = slice;
 #pragma unroll 2
@@ -209,13 +201,117 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
     }
 }
 
+// Several right-hand sides (Sec. 2.5 "Multiple right-hand-sides"): each pair's
+// K is evaluated once and applied to up to kRC weight columns staged next to
+// the source; threads are (target, slice) with one target each.
+constexpr int kRC = 8;
+constexpr int kStageMulti = 256;
+
+template <class Kern>
+__global__ void __launch_bounds__(kP2PThreads)
+    k_p2p_multi(const float4 *__restrict__ pts, const float *__restrict__ sig, const int *__restrict__ off,
+                const int4 *__restrict__ chunks, int64_t n, int D, Kern kern, float scale, int nrhs,
+                float *__restrict__ phi)
+{
+    __shared__ float4 spos[kStageMulti];
+    __shared__ float ssig[kStageMulti][kRC];
+    __shared__ int nb_start[28], nb_pre[28];
+    __shared__ float4 nb_delta[27];
+    __shared__ float red[kP2PThreads][kRC + 1];
+    const int tid = threadIdx.x;
+    const int4 ch = chunks[blockIdx.x];
+    const int nt = ch.z;
+    const int S = kP2PThreads / nt;
+    const int t = tid % nt, slice = tid / nt;
+    const bool active = slice < S;
+    int ax, ay, az;
+    demorton3((uint32_t)ch.x, ax, ay, az);
+    const int nside = 1 << D;
+    if (tid < 32) {
+        int cnt = 0, start = 0;
+        if (tid < 27) {
+            const int dx = tid % 3 - 1, dy = (tid / 3) % 3 - 1, dz = tid / 9 - 1;
+            const int bx = ax + dx, by = ay + dy, bz = az + dz;
+            if (bx >= 0 && by >= 0 && bz >= 0 && bx < nside && by < nside && bz < nside) {
+                const uint32_t nm = morton3((uint32_t)bx, (uint32_t)by, (uint32_t)bz);
+                start = off[nm];
+                cnt = off[nm + 1] - start;
+            }
+            nb_start[tid] = start;
+            nb_delta[tid] = make_float4((float)dx, (float)dy, (float)dz, 0.0f);
+        }
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (tid >= o)
+                incl += v;
+        }
+        if (tid < 28)
+            nb_pre[tid] = incl - cnt;
+    }
+    __syncthreads();
+    const int ns = nb_pre[27];
+    const float4 xt = pts[ch.y + (active ? t : 0)];
+    for (int c0 = 0; c0 < nrhs; c0 += kRC) {
+        const int rc = min(kRC, nrhs - c0);
+        float acc[kRC];
+#pragma unroll
+        for (int q = 0; q < kRC; ++q)
+            acc[q] = 0.0f;
+        for (int base = 0; base < ns; base += kStageMulti) {
+            const int cnt = min(kStageMulti, ns - base);
+            for (int g = tid; g < cnt; g += kP2PThreads) {
+                const int gg = base + g;
+                int k = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (k + step < 27 && nb_pre[k + step] <= gg)
+                        k += step;
+                const int src = nb_start[k] + (gg - nb_pre[k]);
+                const float4 u = pts[src];
+                const float4 d = nb_delta[k];
+                spos[g] = make_float4(u.x + d.x, u.y + d.y, u.z + d.z, 0.0f);
+#pragma unroll
+                for (int q = 0; q < kRC; ++q)
+                    ssig[g][q] = q < rc ? sig[(int64_t)(c0 + q) * n + src] : 0.0f;
+            }
+            __syncthreads();
+            if (active)
+                for (int j = slice; j < cnt; j += S) {
+                    const float4 p = spos[j];
+                    const float dx = xt.x - p.x, dy = xt.y - p.y, dz = xt.z - p.z;
+                    const float K = kern.one(dx * dx + dy * dy + dz * dz, dx, dy, dz);
+#pragma unroll
+                    for (int q = 0; q < kRC; ++q)
+                        acc[q] += K * ssig[j][q];
+                }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int q = 0; q < kRC; ++q)
+            red[tid][q] = active ? acc[q] : 0.0f;
+        __syncthreads();
+        if (tid < nt)
+            for (int q = 0; q < rc; ++q) {
+                float sum = 0.0f;
+                for (int sl = 0; sl < S; ++sl)
+                    sum += red[tid + sl * nt][q];
+                phi[(int64_t)(c0 + q) * n + ch.y + tid] = scale * sum;
+            }
+        __syncthreads();
+    }
+}
+
 template <class Kern>
 static cudaError_t p2p_launch(const float4 *pts, const float *sig, const int *off, const int4 *chunks, int nchunks,
                               int64_t n, int D, Kern k, float scale, int nrhs, float *phi, cudaStream_t s)
 {
     if (nchunks <= 0)
         return cudaSuccess;
-    k_p2p<Kern><<<nchunks, kP2PThreads, 0, s>>>(pts, sig, off, chunks, nchunks, n, D, k, scale, nrhs, phi);
+    if (nrhs > 1)
+        k_p2p_multi<Kern><<<nchunks, kP2PThreads, 0, s>>>(pts, sig, off, chunks, n, D, k, scale, nrhs, phi);
+    else
+        k_p2p<Kern><<<nchunks, kP2PThreads, 0, s>>>(pts, sig, off, chunks, nchunks, n, D, k, scale, nrhs, phi);
     return cudaGetLastError();
 }
 

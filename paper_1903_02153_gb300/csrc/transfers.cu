@@ -154,21 +154,21 @@ __global__ void __launch_bounds__(32 * kL2PWarps) k_l2p(const __grid_constant__ 
     const int s0 = off[m], s1 = off[m + 1];
     if (s1 == s0)
         return;
-    for (int c = 0; c < nrhs; ++c) {
-        __syncwarp();
-        const float *Fm = F + ((int64_t)m * nrhs + c) * P3;
-        for (int i = lane; i < P3; i += 32)
-            sF[w][i] = Fm[i];
-        __syncwarp();
-        for (int c0 = s0; c0 < s1; c0 += 32) {
-            int j = c0 + lane;
-            if (j >= s1)
-                continue;
-            float4 u = pts[j];
-            float Lx[P], Ly[P], Lz[P];
-            lagrange_1d<P>(T, 2.0f * u.x, Lx);
-            lagrange_1d<P>(T, 2.0f * u.y, Ly);
-            lagrange_1d<P>(T, 2.0f * u.z, Lz);
+    for (int c0 = s0; c0 < s1; c0 += 32) {
+        // the lane's point and its basis values, reused for every right-hand side
+        const int j = c0 + lane;
+        const bool has = j < s1;
+        float Lx[P], Ly[P], Lz[P];
+        const float4 u = pts[has ? j : s0];
+        lagrange_1d<P>(T, 2.0f * u.x, Lx);
+        lagrange_1d<P>(T, 2.0f * u.y, Ly);
+        lagrange_1d<P>(T, 2.0f * u.z, Lz);
+        for (int c = 0; c < nrhs; ++c) {
+            __syncwarp();
+            const float *Fm = F + ((int64_t)m * nrhs + c) * P3;
+            for (int i = lane; i < P3; i += 32)
+                sF[w][i] = Fm[i];
+            __syncwarp();
             float acc = 0.0f;
 #pragma unroll
             for (int i3 = 0; i3 < P; ++i3) {
@@ -182,7 +182,8 @@ __global__ void __launch_bounds__(32 * kL2PWarps) k_l2p(const __grid_constant__ 
                     acc += part * yz;
                 }
             }
-            phi[(int64_t)c * n + j] = acc;
+            if (has)
+                phi[(int64_t)c * n + j] = acc;
         }
     }
 }
