@@ -73,7 +73,10 @@ typedef struct {
     int split_accumulate; /* BBFMM_PREC_TF32X3 only: 1 (default) accumulates the
                              correction products hi*lo + lo*hi apart from hi*hi and
                              adds them at the end; 0 uses one accumulator */
-    int reserved[6];   /* zero */
+    int use_graph;     /* 1 (default): the first matvec with a given nrhs captures
+                          the whole launch sequence into a CUDA graph, later ones
+                          replay it; 0: launch the kernels one by one */
+    int reserved[5];   /* zero */
 } bbfmm_opts;
 
 typedef struct {

@@ -208,6 +208,17 @@ struct bbfmm_plan_impl {
     cudaEvent_t ev_p2p0 = nullptr, ev_p2p1 = nullptr;
     int last_nrhs = 0;
     std::atomic<int> busy{0};
+
+    // captured CUDA graphs of the whole matvec, one per nrhs
+    bool use_graph = true;
+    cudaStream_t cap_stream = nullptr;
+    struct Graph {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaGraphNode_t gather = nullptr, combine = nullptr;
+        cudaKernelNodeParams gp{}, cp{};
+    };
+    Graph graphs[1025];
 };
 
 // ---------------------------------------------------------------------------
@@ -247,6 +258,11 @@ cudaError_t launch_l2p(const InterpTables &T, const float4 *pts, const float *F,
                        int nrhs, float *phi_far, cudaStream_t s);
 cudaError_t launch_combine(const float *phi_far, const float *phi_near, const int *perm, int64_t n,
                            int nrhs, float *phi, cudaStream_t s);
+// entry points of the two kernels whose pointer arguments (the caller's sigma
+// and phi) change from call to call of a captured matvec graph
+const void *gather_kernel();
+const void *combine_kernel();
+cudaError_t m2l_fp32_init(); // uploads the offset table (outside any stream capture)
 // m2l_fp32.cu
 // per octant class o: the 189 interaction-list offsets as (operator index,
 // source octant, packed parent-cell shift (ux+1) | (uy+1)<<2 | (uz+1)<<4)

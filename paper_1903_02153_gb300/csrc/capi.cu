@@ -224,10 +224,18 @@ static void plan_free(bbfmm_plan_impl *P)
     P->allocations.clear();
     if (P->chunks)
         cudaFree(P->chunks);
+    for (auto &g : P->graphs) {
+        if (g.exec)
+            cudaGraphExecDestroy(g.exec);
+        if (g.graph)
+            cudaGraphDestroy(g.graph);
+    }
     if (P->side_stream)
         cudaStreamDestroy(P->side_stream);
     if (P->far_stream)
         cudaStreamDestroy(P->far_stream);
+    if (P->cap_stream)
+        cudaStreamDestroy(P->cap_stream);
     if (P->ev_fork)
         cudaEventDestroy(P->ev_fork);
     if (P->ev_join)
@@ -416,6 +424,9 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, cudaStream_t s)
     PTRY(plan_alloc(P, (void **)&P->phi_near, 4 * n * R, false, s));
     PTRY(plan_alloc(P, (void **)&P->status, 16, true, s));
 
+    // constant tables the matvec kernels read, uploaded before any capture
+    CUDA_TRY(m2l_fp32_init());
+    CUDA_TRY(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
     int prio_low = 0, prio_high = 0;
     CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
     CUDA_TRY(cudaStreamCreateWithPriority(&P->far_stream, cudaStreamNonBlocking, prio_high));
@@ -523,6 +534,74 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
     return BBFMM_OK;
 }
 
+// The matvec as one CUDA graph: captured on the plan's capture stream the
+// first time a given nrhs is used, then replayed on the caller's stream.  The
+// caller's sigma / phi enter only the gather and the combine kernels; their
+// graph nodes get the pointers of each call before the launch.
+static int matvec_graph(bbfmm_plan_impl *P, const float *sigma, float *phi, int nrhs, cudaStream_t s)
+{
+    auto &g = P->graphs[nrhs];
+    if (!g.exec) {
+        cudaStream_t cs = P->cap_stream;
+        CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        int st = matvec_device(P, sigma, phi, nrhs, cs);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        if (st != BBFMM_OK || e != cudaSuccess) {
+            if (graph)
+                cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return st != BBFMM_OK ? st : fail(BBFMM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        }
+        size_t nn = 0;
+        CUDA_TRY(cudaGraphGetNodes(graph, nullptr, &nn));
+        std::vector<cudaGraphNode_t> nodes(nn);
+        CUDA_TRY(cudaGraphGetNodes(graph, nodes.data(), &nn));
+        for (cudaGraphNode_t node : nodes) {
+            cudaGraphNodeType type;
+            CUDA_TRY(cudaGraphNodeGetType(node, &type));
+            if (type != cudaGraphNodeTypeKernel)
+                continue;
+            cudaKernelNodeParams kp;
+            CUDA_TRY(cudaGraphKernelNodeGetParams(node, &kp));
+            if (kp.func == gather_kernel()) {
+                g.gather = node;
+                g.gp = kp;
+            } else if (kp.func == combine_kernel()) {
+                g.combine = node;
+                g.cp = kp;
+            }
+        }
+        if (!g.gather || !g.combine) {
+            cudaGraphDestroy(graph);
+            return fail(BBFMM_EINTERNAL, "captured matvec graph lacks its gather / combine node");
+        }
+        cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+        if (ie != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            g.exec = nullptr;
+            return fail(BBFMM_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ie));
+        }
+        g.graph = graph;
+    }
+    // this call's pointers into the two boundary kernels
+    const int64_t n = P->n;
+    const float *far = P->D >= 2 ? P->phi_far : nullptr;
+    void *gargs[] = {(void *)&sigma, (void *)&P->perm, (void *)&n, (void *)&nrhs, (void *)&P->sigma_s};
+    void *cargs[] = {(void *)&far, (void *)&P->phi_near, (void *)&P->perm, (void *)&n, (void *)&nrhs,
+                     (void *)&phi};
+    cudaKernelNodeParams gp = g.gp, cp = g.cp;
+    gp.kernelParams = gargs;
+    gp.extra = nullptr;
+    cp.kernelParams = cargs;
+    cp.extra = nullptr;
+    CUDA_TRY(cudaGraphExecKernelNodeSetParams(g.exec, g.gather, &gp));
+    CUDA_TRY(cudaGraphExecKernelNodeSetParams(g.exec, g.combine, &cp));
+    CUDA_TRY(cudaGraphLaunch(g.exec, s));
+    P->last_nrhs = nrhs;
+    return BBFMM_OK;
+}
+
 } // namespace bbfmm
 
 using namespace bbfmm;
@@ -541,6 +620,7 @@ void bbfmm_default_opts(bbfmm_opts *o)
     o->side = 1.0;
     o->max_nrhs = 1;
     o->split_accumulate = 1;
+    o->use_graph = 1;
 }
 
 const char *bbfmm_last_error(void) { return g_last_error.c_str(); }
@@ -601,6 +681,7 @@ int bbfmm_plan(const double *points, int64_t n, int kernel_id, int cheb_order, i
     P->ell = opts.ell;
     P->eps = opts.svd_eps;
     P->split_acc = opts.split_accumulate != 0;
+    P->use_graph = opts.use_graph != 0;
     if (opts.domain_given) {
         for (int d = 0; d < 3; ++d)
             P->lo[d] = opts.lo[d];
@@ -654,7 +735,8 @@ int bbfmm_matvec(bbfmm_plan_t plan, const float *sigma, float *phi, int nrhs, vo
             ph = plan->io_phi;
     }
     if (st == BBFMM_OK)
-        st = matvec_device(plan, sg, ph, nrhs, s);
+        st = plan->use_graph && !plan->timing ? matvec_graph(plan, sg, ph, nrhs, s)
+                                              : matvec_device(plan, sg, ph, nrhs, s);
     if (st == BBFMM_OK && !dphi) {
         cudaError_t e = cudaMemcpyAsync(phi, plan->io_phi, bytes, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess)

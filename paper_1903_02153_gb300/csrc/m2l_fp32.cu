@@ -135,6 +135,8 @@ __global__ void __launch_bounds__(256) k_m2l_fp32(const float *__restrict__ Mt, 
     }
 }
 
+cudaError_t m2l_fp32_init() { return upload_m2l_table(); }
+
 cudaError_t launch_m2l_fp32(const float *Mt, const float *C, float *Ft, int l, int r, int rp, int rows64,
                             int nrhs, float scale, cudaStream_t s)
 {

@@ -54,6 +54,8 @@ __global__ void k_gather(const float *__restrict__ sigma, const int *__restrict_
         out[(int64_t)c * n + i] = sigma[(int64_t)c * n + j];
 }
 
+const void *gather_kernel() { return (const void *)k_gather; }
+
 cudaError_t launch_gather_sigma(const float *sigma, const int *perm, int64_t n, int nrhs, float *out,
                                 cudaStream_t s)
 {
@@ -490,6 +492,8 @@ __global__ void k_combine(const float *__restrict__ far, const float *__restrict
         phi[(int64_t)c * n + j] = v;
     }
 }
+
+const void *combine_kernel() { return (const void *)k_combine; }
 
 cudaError_t launch_combine(const float *phi_far, const float *phi_near, const int *perm, int64_t n, int nrhs,
                            float *phi, cudaStream_t s)
