@@ -52,7 +52,70 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-depth6", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--serving", type=int, default=0,
+                    help="also run N requests of the Poisson serving stream (p50/p99 latency, throughput)")
     return ap.parse_args()
+
+
+def serving(args, torch):
+    """Continuous-batching request loop on a Poisson stream (workloads.
+    serving_stream): mixed N (log-uniform 10k..500k), kernels, p, nrhs; plans
+    on the unit-cube domain stay resident.  Warm-up requests run one at a time
+    (they also build the plans and operator sets); the service rate of the
+    warm-up requests that hit a resident plan sets the arrival rate of the timed
+    requests to 0.8 x that capacity."""
+    from paper_1903_02153_gb300 import serve as S
+    warm = 40
+    reqs = W.serving_stream(warm + args.serving, n_hi=500_000)
+    pts_cache = {}
+
+    def point_source(key):
+        kind, n, seed, kid, ell, p, depth = key
+        if (kind, n, seed) not in pts_cache:
+            pts_cache[(kind, n, seed)] = W.make_points(kind, n, seed)
+        return pts_cache[(kind, n, seed)], kid, ell, p, depth
+
+    def make(d):
+        key = (d["kind"], d["n"], d["point_seed"], d["kernel"], d["ell"], d["p"], d["depth"])
+        sig = W.uniform_sigma(d["n"], d["nrhs"], seed=d["sigma_seed"]).astype(np.float32)
+        return S.Request(key, sig.reshape(d["n"], d["nrhs"]))
+
+    ex = S.GpuExecutor(point_source, precision=args.precision, svd_eps=args.svd_eps, slots=4,
+                       domain=(W.UNIT_LO, W.UNIT_SIDE))
+    srv = S.Server(ex, device_budget_bytes=96 << 30, slots=4, max_batch_nrhs=32).start()
+    t_build0 = time.perf_counter()
+    service = []
+    for d in reqs[:warm]:
+        fresh = srv.builds
+        t0 = time.perf_counter()
+        srv.submit(make(d)).wait(600)
+        if srv.builds == fresh:
+            service.append(time.perf_counter() - t0)
+    warm_s = time.perf_counter() - t_build0
+    capacity = 1.0 / float(np.mean(service)) if service else 50.0
+    rate = 0.8 * capacity
+    timed = []
+    t_start = time.perf_counter()
+    t_next = t_start
+    for d in reqs[warm:]:
+        t_next += d["gap"] / rate
+        while time.perf_counter() < t_next:
+            time.sleep(50e-6)
+        timed.append(srv.submit(make(d)))
+    for r in timed:
+        r.wait(600)
+    wall = max(r.t_done for r in timed) - t_start
+    srv.stop()
+    ok = [r for r in timed if r.error is None]
+    lat = np.array([r.latency for r in ok])
+    return {"requests": len(timed), "failed": len(timed) - len(ok), "warmup_requests": warm,
+            "warmup_s_incl_plan_builds": warm_s, "arrival_rate_per_s": rate,
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "throughput_N2nrhs_per_s": sum(float(r.n) ** 2 * r.nrhs for r in ok) / wall,
+            "requests_per_s": len(ok) / wall, "mean_batch": float(np.mean([r.batch_size for r in ok])),
+            "plan_builds": srv.builds, "plan_evictions": srv.evictions,
+            "mix": "N log-uniform 10k..500k, uniform/clustered, K in {1/r, 1/r^2, exp(-r), exp(-r^2)}, "
+                   "p in {4,5,6}, nrhs in {1,8,32}, Poisson arrivals at 0.8 x measured capacity, 4 slots"}
 
 
 def dist_env():
@@ -303,6 +366,8 @@ def run_ours(args, rank, world, local):
         "accuracy": acc,
     }
     out.update(extra)
+    if rank == 0 and args.serving > 0:
+        out["serving"] = serving(args, torch)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(pts, sig_host, c)
     plan.close()
