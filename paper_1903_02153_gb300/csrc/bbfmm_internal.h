@@ -246,14 +246,16 @@ cudaError_t launch_p2m(const InterpTables &T, const float4 *pts, const float *si
                        int nrhs, float *M, cudaStream_t s);
 cudaError_t launch_m2m(const InterpTables &T, const float *Mchild, float *Mparent, int lparent, int p, int nrhs, cudaStream_t s);
 cudaError_t launch_l2l(const InterpTables &T, const float *Fparent, float *Fchild, int lparent, int p, int nrhs, cudaStream_t s);
+// (the parity-split M~ / F~ rows always use the plan's max_nrhs R as their
+// right-hand-side stride, so their zero halo never moves between calls)
 cudaError_t launch_compress(const float *M, const float *V, float *Mt, float *Mt_hi, float *Mt_lo, unsigned *maxbits,
-                            int l, int p3, int r, int rp, int nrhs, cudaStream_t s);
+                            int l, int p3, int r, int rp, int nrhs, int R, cudaStream_t s);
 // split Mt (n floats) into 16-bit hi / lo after scaling by a power of two
 // chosen from *maxbits (FP16) or 1 (BF16); the scale is written to *scale
 cudaError_t launch_split16(const float *Mt, int64_t n, int fmt, const unsigned *maxbits, float *scale, uint16_t *hi,
                            uint16_t *lo, cudaStream_t s);
 cudaError_t launch_decompress(const float *Ft, int nslices, int64_t slice, const float *Ut, float *F, int l,
-                              int p3, int p3p, int r, int rp, int nrhs, bool accumulate, cudaStream_t s);
+                              int p3, int p3p, int r, int rp, int nrhs, int R, bool accumulate, cudaStream_t s);
 cudaError_t launch_l2p(const InterpTables &T, const float4 *pts, const float *F, const int *leaf_off, int64_t n, int D, int p,
                        int nrhs, float *phi_far, cudaStream_t s);
 cudaError_t launch_combine(const float *phi_far, const float *phi_near, const int *perm, int64_t n,
@@ -268,7 +270,7 @@ cudaError_t m2l_fp32_init(); // uploads the offset table (outside any stream cap
 // source octant, packed parent-cell shift (ux+1) | (uy+1)<<2 | (uz+1)<<4)
 bool fill_m2l_table(int4 (*tab)[kOffsetsPerClass]);
 cudaError_t launch_m2l_fp32(const float *Mt, const float *C, float *Ft, int l, int r, int rp, int rows64,
-                            int nrhs, float scale, cudaStream_t s);
+                            int nrhs, int R, float scale, cudaStream_t s);
 // m2l_tc.cu: every level of the far field in one go (FP32 or tensor cores)
 cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s);
 int m2l_groups_for(int D, int nrhs, int precision);

@@ -490,7 +490,7 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
             CUDA_TRY(cudaMemsetAsync(P->a16_max, 0, 4 * (kMaxDepth + 1), fs));
         for (int l = D; l >= 2; --l) {
             CUDA_TRY(launch_compress(P->lev[l].M, V(l), P->lev[l].Mt, P->lev[l].Mt_hi, P->lev[l].Mt_lo,
-                                     split16 ? P->a16_max + l : nullptr, l, p3, O.r, O.rp, nrhs, fs));
+                                     split16 ? P->a16_max + l : nullptr, l, p3, O.r, O.rp, nrhs, P->max_nrhs, fs));
             if (split16) {
                 const int64_t H = 1LL << (l - 1);
                 CUDA_TRY(launch_split16(P->lev[l].Mt, 8 * (H + 2) * H * H * P->max_nrhs * O.rp,
@@ -511,7 +511,7 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
             if (l >= 3)
                 CUDA_TRY(launch_l2l(T, P->lev[l - 1].F, P->lev[l].F, l - 1, p, nrhs, fs));
             CUDA_TRY(launch_decompress(P->lev[l].Ft, P->m2l_groups, (1LL << (3 * l)) * P->max_nrhs * O.rp, Ut(l),
-                                       P->lev[l].F, l, p3, O.p3p, O.r, O.rp, nrhs, l >= 3, fs));
+                                       P->lev[l].F, l, p3, O.p3p, O.r, O.rp, nrhs, P->max_nrhs, l >= 3, fs));
         }
         if (tm)
             CUDA_TRY(cudaEventRecord(P->ev[Stage::Down], fs));

@@ -64,7 +64,7 @@ static cudaError_t upload_m2l_table()
 
 __global__ void __launch_bounds__(256) k_m2l_fp32(const float *__restrict__ Mt, const float *__restrict__ C,
                                                   float *__restrict__ Ft, int l, int r, int rp, int rows64,
-                                                  int nrhs, float scale)
+                                                  int nrhs, int R, float scale)
 {
     __shared__ __align__(16) float As[16][64]; // operator rows x k
     __shared__ __align__(16) float Bs[16][64]; // k x targets
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(256) k_m2l_fp32(const float *__restrict__ Mt, 
         const int sx = X + ux, sy = Y + uy, sz = Z + uz;
         const bool src_ok = tgt_ok && sx >= 0 && sx < H && sy >= 0 && sy < H && sz >= 0 && sz < H;
         const float *brow =
-            Mt + ((((int64_t)en.y * zs + sz + 1) * H + sy) * H + sx) * (int64_t)nrhs * rp + (int64_t)c * rp;
+            Mt + ((((int64_t)en.y * zs + sz + 1) * H + sy) * H + sx) * (int64_t)R * rp + (int64_t)c * rp;
         const float *arow = C + ((int64_t)en.x * rows64 + row0 + ld) * rp;
         for (int k0 = 0; k0 < r; k0 += 16) {
             float4 a = *reinterpret_cast<const float4 *>(arow + k0 + lk);
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256) k_m2l_fp32(const float *__restrict__ Mt, 
         int Xb = X0 + (b & 3), Yb = Y0 + ((b >> 2) & 3), Zb = Z0 + (b >> 4);
         if (Xb >= H || Yb >= H || Zb >= H)
             continue;
-        float *out = Ft + ((((int64_t)ot * H + Zb) * H + Yb) * H + Xb) * (int64_t)nrhs * rp + (int64_t)c * rp;
+        float *out = Ft + ((((int64_t)ot * H + Zb) * H + Yb) * H + Xb) * (int64_t)R * rp + (int64_t)c * rp;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             int row = row0 + ty * 4 + i;
@@ -138,9 +138,9 @@ __global__ void __launch_bounds__(256) k_m2l_fp32(const float *__restrict__ Mt, 
 cudaError_t m2l_fp32_init() { return upload_m2l_table(); }
 
 cudaError_t launch_m2l_fp32(const float *Mt, const float *C, float *Ft, int l, int r, int rp, int rows64,
-                            int nrhs, float scale, cudaStream_t s)
+                            int nrhs, int R, float scale, cudaStream_t s)
 {
-    if (rp % 16 != 0 || rows64 % 64 != 0 || l < 2)
+    if (rp % 16 != 0 || rows64 % 64 != 0 || l < 2 || nrhs > R)
         return cudaErrorInvalidValue;
     cudaError_t e = upload_m2l_table();
     if (e != cudaSuccess)
@@ -148,7 +148,7 @@ cudaError_t launch_m2l_fp32(const float *Mt, const float *C, float *Ft, int l, i
     int H = 1 << (l - 1);
     int tpd = (H + 3) / 4;
     dim3 grid((unsigned)(tpd * tpd * tpd), 8, (unsigned)((rows64 / 64) * nrhs));
-    k_m2l_fp32<<<grid, 256, 0, s>>>(Mt, C, Ft, l, r, rp, rows64, nrhs, scale);
+    k_m2l_fp32<<<grid, 256, 0, s>>>(Mt, C, Ft, l, r, rp, rows64, nrhs, R, scale);
     return cudaGetLastError();
 }
 

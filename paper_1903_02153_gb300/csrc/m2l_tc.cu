@@ -91,7 +91,7 @@ struct TcLaunch {
     const float *ascale;            // 16-bit forms: scale of M~ per tree level (device)
     int nlev, nitems, groups, per_group;
     int *status;
-    int r, rp, nb, ncols, nrhs, nk, nstage;
+    int r, rp, nb, ncols, nrhs, R, nk, nstage; // R: right-hand-side stride of M~ / F~ rows
     uint32_t stage_bytes, a_bytes, b_bytes;
 };
 
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
             const int X = 8 * w.tx + bx, Y = 4 * w.ty + by, Z = 4 * w.tz + bz;
             if (X < lv.H && Y < lv.H && Z < lv.H) {
                 float *out = lv.Ft + (int64_t)w.g * lv.slice +
-                             ((((int64_t)w.ot * lv.H + Z) * lv.H + Y) * lv.H + X) * (int64_t)P.nrhs * P.rp +
+                             ((((int64_t)w.ot * lv.H + Z) * lv.H + Y) * lv.H + X) * (int64_t)P.R * P.rp +
                              (int64_t)w.c * P.rp;
                 // level scale; 16-bit forms also undo the power-of-two operand scales
                 float f = lv.scale;
@@ -484,7 +484,7 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
         for (int l = 2; l <= P->D; ++l) {
             const int k = O.nlev == 1 ? 0 : l - 2;
             cudaError_t e =
-                launch_m2l_fp32(P->lev[l].Mt, O.C[k], P->lev[l].Ft, l, O.r, O.rp, O.rows64, nrhs, scale_of(l), s);
+                launch_m2l_fp32(P->lev[l].Mt, O.C[k], P->lev[l].Ft, l, O.r, O.rp, O.rows64, nrhs, P->max_nrhs, scale_of(l), s);
             if (e != cudaSuccess)
                 return e;
         }
@@ -510,6 +510,7 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
     L.nb = nb;
     L.ncols = nb <= 32 ? 32 : nb <= 64 ? 64 : nb <= 128 ? 128 : 256;
     L.nrhs = nrhs;
+    L.R = P->max_nrhs;
     L.nk = (O.r + chunk - 1) / chunk;
     L.groups = P->m2l_groups;
     L.per_group = (kOffsetsPerClass + L.groups - 1) / L.groups;

@@ -315,7 +315,8 @@ __global__ void __launch_bounds__(256) k_node_gemm(const float *__restrict__ A, 
                                                    float *__restrict__ Out, int64_t rows, int K, int N, int ldw,
                                                    int lda, int ldo, int level, int nrhs, int accumulate,
                                                    float *__restrict__ Out_hi, float *__restrict__ Out_lo,
-                                                   int nslices, int64_t slice, unsigned *__restrict__ maxbits)
+                                                   int nslices, int64_t slice, unsigned *__restrict__ maxbits,
+                                                   int R)
 {
     __shared__ float As[16][64 + 4];
     __shared__ float Ws[16][64 + 4];
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(256) k_node_gemm(const float *__restrict__ A, 
         int c = (int)(row % nrhs);
         int x, y, z;
         demorton3((uint32_t)m, x, y, z);
-        return parity_row(x, y, z, c, H, padZ, nrhs) * ld;
+        return parity_row(x, y, z, c, H, padZ, R) * ld;
     };
     const int lr = tid >> 2, lk = (tid & 3) * 4; // A loader: row lr, k lk..lk+3
     const int64_t arow = row0 + lr;
@@ -459,21 +460,21 @@ cudaError_t launch_split16(const float *Mt, int64_t n, int fmt, const unsigned *
 }
 
 cudaError_t launch_compress(const float *M, const float *V, float *Mt, float *Mt_hi, float *Mt_lo, unsigned *maxbits,
-                            int l, int p3, int r, int rp, int nrhs, cudaStream_t s)
+                            int l, int p3, int r, int rp, int nrhs, int R, cudaStream_t s)
 {
     int64_t rows = ((int64_t)1 << (3 * l)) * nrhs;
     dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((r + 63) / 64));
-    k_node_gemm<0><<<grid, 256, 0, s>>>(M, V, Mt, rows, p3, r, rp, p3, rp, l, nrhs, 0, Mt_hi, Mt_lo, 1, 0, maxbits);
+    k_node_gemm<0><<<grid, 256, 0, s>>>(M, V, Mt, rows, p3, r, rp, p3, rp, l, nrhs, 0, Mt_hi, Mt_lo, 1, 0, maxbits, R);
     return cudaGetLastError();
 }
 
 cudaError_t launch_decompress(const float *Ft, int nslices, int64_t slice, const float *Ut, float *F, int l, int p3,
-                              int p3p, int r, int rp, int nrhs, bool accumulate, cudaStream_t s)
+                              int p3p, int r, int rp, int nrhs, int R, bool accumulate, cudaStream_t s)
 {
     int64_t rows = ((int64_t)1 << (3 * l)) * nrhs;
     dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((p3 + 63) / 64));
     k_node_gemm<1><<<grid, 256, 0, s>>>(Ft, Ut, F, rows, r, p3, p3p, rp, p3, l, nrhs, accumulate ? 1 : 0, nullptr,
-                                        nullptr, nslices, slice, nullptr);
+                                        nullptr, nslices, slice, nullptr, R);
     return cudaGetLastError();
 }
 

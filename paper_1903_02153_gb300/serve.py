@@ -7,6 +7,10 @@ any time.  A scheduler thread
   operators + coefficient grids, built by ``bbfmm_plan``) is resident; plans
   stay resident between requests and idle ones are evicted least-recently
   used when a new plan would not fit the budget;
+* builds plans off the scheduling thread: a missing plan's estimated bytes
+  are reserved and a builder thread makes it, while requests of resident
+  plans keep being dispatched; a failed build fails only that plan's
+  requests;
 * batches as it goes: queued requests that share a plan are merged into one
   multi-right-hand-side matvec (Sec. 2.5 "Multiple right-hand-sides"), up to
   ``max_batch_nrhs`` columns;
@@ -24,6 +28,7 @@ and its failure handling can be exercised on the CPU with a fake executor.
 from __future__ import annotations
 
 import collections
+import queue
 import threading
 import time
 
@@ -70,10 +75,15 @@ class Request:
 
 
 class _Plan:
-    def __init__(self, key, handle, nbytes):
+    """A plan slot: reserved (estimated bytes, being built), then resident
+    (handle set, actual bytes), or failed (error set)."""
+
+    def __init__(self, key, nbytes):
         self.key = key
-        self.handle = handle
+        self.handle = None
         self.bytes = nbytes
+        self.ready = False
+        self.error = None
         self.busy = False
         self.last_used = time.perf_counter()
 
@@ -97,11 +107,15 @@ class Server:
         self.t_last = None
         self.evictions = 0
         self.builds = 0
+        self.build_q = queue.Queue()
+        self.builder = None
 
     # -- public --------------------------------------------------------------
     def start(self):
         self.running = True
         self.thread = threading.Thread(target=self._loop, name="bbfmm-serve", daemon=True)
+        self.builder = threading.Thread(target=self._build_loop, name="bbfmm-plan-builder", daemon=True)
+        self.builder.start()
         self.thread.start()
         return self
 
@@ -110,8 +124,12 @@ class Server:
         self.wake.set()
         if self.thread is not None:
             self.thread.join()
+        if self.builder is not None:
+            self.build_q.put(None)
+            self.builder.join()
         for p in list(self.plans.values()):
-            self.ex.destroy(p.handle)
+            if p.handle is not None:
+                self.ex.destroy(p.handle)
         self.plans.clear()
 
     def submit(self, req):
@@ -141,6 +159,7 @@ class Server:
         work = sum(float(r.n) ** 2 * r.nrhs for r in self.done if r.error is None)
         wall = (self.t_last - self.t_first) if self.t_last and self.t_first else float("nan")
         out = {"requests": len(self.done), "failed": sum(r.error is not None for r in self.done),
+               "plans_resident": sum(p.ready for p in list(self.plans.values())),
                "plan_builds": self.builds, "plan_evictions": self.evictions,
                "mean_batch": float(np.mean([r.batch_size for r in self.done])) if self.done else 0.0}
         if lat.size:
@@ -155,28 +174,61 @@ class Server:
     def _used_bytes(self):
         return sum(p.bytes for p in self.plans.values())
 
-    def _ensure_plan(self, key, nrhs_hint):
-        """The resident plan for key, building it (and evicting idle plans)
-        if the budget allows; None if it cannot be admitted now."""
+    def _ensure_plan(self, key):
+        """The resident plan for key, or None when it is not resident yet: a
+        missing plan is reserved (idle resident plans are evicted, least
+        recently used first, until its estimate fits the budget) and queued
+        for the builder thread.  Raises MemoryError when it can never fit."""
         p = self.plans.get(key)
         if p is not None:
+            if not p.ready:
+                return None          # being built
             self.plans.move_to_end(key)
             return p
         need = self.ex.estimate_bytes(key, self.max_batch)
         if need > self.budget:
             raise MemoryError("plan needs %d bytes, budget %d" % (need, self.budget))
         while self._used_bytes() + need > self.budget:
-            idle = [k for k, q in self.plans.items() if not q.busy]
+            idle = [k for k, q in self.plans.items() if q.ready and not q.busy]
             if not idle:
-                return None          # wait for a running batch to finish
+                return None          # wait for a running batch or a build to finish
             victim = self.plans.pop(idle[0])
             self.ex.destroy(victim.handle)
             self.evictions += 1
-        handle = self.ex.build(key, self.max_batch)
-        self.builds += 1
-        p = _Plan(key, handle, self.ex.plan_bytes(handle))
+        p = _Plan(key, need)
         self.plans[key] = p
-        return p
+        self.builds += 1
+        self.build_q.put(p)
+        return None
+
+    def _build_loop(self):
+        """Builder thread: makes the reserved plans one at a time (a build
+        allocates its device memory and runs its own stream), then wakes the
+        scheduler."""
+        while True:
+            p = self.build_q.get()
+            if p is None:
+                return
+            try:
+                handle = self.ex.build(p.key, self.max_batch)
+                nbytes = self.ex.plan_bytes(handle)
+                with self.lock:
+                    p.handle, p.bytes, p.ready = handle, nbytes, True
+            except Exception as e:                       # noqa: BLE001
+                with self.lock:
+                    p.error = repr(e)
+            self.wake.set()
+
+    def _reap_failed_builds(self):
+        for key, p in list(self.plans.items()):
+            if p.error is None:
+                continue
+            del self.plans[key]
+            with self.lock:
+                failed = [r for r in self.pending if r.key == key]
+                for r in failed:
+                    self.pending.remove(r)
+            self._finish(failed, error=p.error)
 
     def _finish(self, reqs, results=None, error=None):
         now = time.perf_counter()
@@ -208,23 +260,28 @@ class Server:
             self.slots[s] = None
 
     def _next_batch(self):
-        """Oldest pending request whose plan is free and admissible, plus the
-        pending requests of the same plan that fit in the batch."""
+        """Oldest pending request whose plan is resident and free, plus the
+        pending requests of the same plan that fit in the batch.  Requests
+        whose plan is missing get it reserved and queued for building."""
         with self.lock:
-            queue = list(self.pending)
-        for head in queue:
+            queue_ = list(self.pending)
+        seen = set()
+        for head in queue_:
+            if head.key in seen:
+                continue
+            seen.add(head.key)
             p = self.plans.get(head.key)
             if p is not None and p.busy:
                 continue
             try:
-                p = self._ensure_plan(head.key, head.nrhs)
+                p = self._ensure_plan(head.key)
             except Exception as e:                       # noqa: BLE001
                 with self.lock:
                     failed = [r for r in self.pending if r.key == head.key]
                     for r in failed:
                         self.pending.remove(r)
                 self._finish(failed, error=repr(e))
-                return None
+                continue
             if p is None:
                 continue
             batch, cols = [], 0
@@ -244,6 +301,7 @@ class Server:
     def _loop(self):
         while self.running:
             self._poll_slots()
+            self._reap_failed_builds()
             launched = False
             for s in range(self.nslots):
                 if self.slots[s] is not None:
@@ -276,11 +334,9 @@ class Server:
             if not launched:
                 if busy:
                     time.sleep(20e-6)
-                elif idle:
-                    self.wake.wait(0.01)
+                else:               # nothing queued, or waiting for a plan build
+                    self.wake.wait(0.01 if idle else 0.001)
                     self.wake.clear()
-                else:
-                    time.sleep(50e-6)
 
 
 # ---------------------------------------------------------------------------
@@ -300,7 +356,7 @@ class GpuExecutor:
         self.domain = domain                 # (lo, side) shared by all plans, or None: bounding cubes
         self.dev = torch.device("cuda", device)
         self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(slots)]
-        self.spec = {}
+        self.build_stream = torch.cuda.Stream(device=self.dev)
 
     def estimate_bytes(self, key, max_nrhs):
         pts, kid, ell, p, depth = self.point_source(key)
@@ -309,9 +365,12 @@ class GpuExecutor:
         return int(grid + n * (16 + 4 + 12 * max_nrhs) * 2 + 64 * 2 ** 20)
 
     def build(self, key, max_nrhs):
+        """Runs on the server's builder thread, on a stream of its own so that
+        the build overlaps the matvecs in flight."""
+        self.torch.cuda.set_device(self.dev)
         pts, kid, ell, p, depth = self.point_source(key)
         plan = self.bb.Plan(pts, kid, p, depth, ell=ell, precision=self.precision, svd_eps=self.svd_eps,
-                            max_nrhs=max_nrhs, domain=self.domain)
+                            max_nrhs=max_nrhs, domain=self.domain, stream=self.build_stream)
         return plan
 
     def plan_bytes(self, plan):
@@ -347,9 +406,10 @@ class FakeExecutor:
     """CPU stand-in for tests of the scheduler: a 'matvec' multiplies sigma by
     a per-key factor after a fixed delay; build failures are injected by key."""
 
-    def __init__(self, sizes, delay=0.002, fail_build=(), fail_launch=()):
+    def __init__(self, sizes, delay=0.002, fail_build=(), fail_launch=(), build_delay=None):
         self.sizes = dict(sizes)             # key -> plan bytes
         self.delay = delay
+        self.build_delay = dict(build_delay or {})   # key -> seconds a build takes
         self.fail_build = set(fail_build)
         self.fail_launch = set(fail_launch)
         self.live = set()
@@ -359,6 +419,7 @@ class FakeExecutor:
         return self.sizes[key]
 
     def build(self, key, max_nrhs):
+        time.sleep(self.build_delay.get(key, 0.0))
         if key in self.fail_build:
             raise MemoryError("injected: plan allocation refused for %r" % (key,))
         self.live.add(key)

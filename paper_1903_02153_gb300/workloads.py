@@ -93,26 +93,47 @@ def make_sigma(kind, n, nrhs, seed=SEED_SIGMA):
     return uniform_sigma(n, nrhs, seed)
 
 
-def serving_stream(nreq, seed=SEED_STREAM, n_lo=10_000, n_hi=2_000_000, repeat_prob=0.5):
+def serving_stream(nreq, seed=SEED_STREAM, n_lo=10_000, n_hi=2_000_000, repeat_prob=0.5, plans=None):
     """Request descriptors for the serving loop: each request has a point-set
-    recipe (kind, n, seed), kernel id, p, nrhs, depth; with probability
-    ``repeat_prob`` a request reuses an earlier point set (a plan-cache hit).
-    Inter-arrival gaps are unit-rate exponential; callers scale them."""
+    recipe (kind, n, seed), kernel id, p, nrhs, depth.
+
+    With ``plans=None`` a request reuses an earlier request's point set with
+    probability ``repeat_prob`` (a plan-cache hit) and otherwise draws a new
+    one; kernel and p are drawn per request.  With ``plans=k`` the stream
+    draws from a fixed pool of k plan recipes (point set, kernel, p, depth),
+    uniformly: the steady state of a service whose plans stay resident.
+    nrhs is drawn from {1, 8, 32}.  Inter-arrival gaps are unit-rate
+    exponential; callers scale them."""
     rng = np.random.default_rng(seed)
     kernels = [(1, 1.0), (2, 1.0), (3, 1.0), (4, 1.0)]
+
+    def recipe():
+        n = int(10 ** rng.uniform(np.log10(n_lo), np.log10(n_hi)))
+        kind = "uniform" if rng.random() < 0.5 else "clustered"
+        return kind, n, int(rng.integers(0, 2 ** 31))
+
+    def depth_of(n):
+        return int(np.clip(round(np.log(n / 32.0) / np.log(8.0)), 2, 7))
+
+    pool = []
+    for _ in range(plans or 0):
+        kind, n, pseed = recipe()
+        kid, ell = kernels[int(rng.integers(0, 4))]
+        pool.append((kind, n, pseed, kid, ell, int(rng.choice([4, 5, 6])), depth_of(n)))
     reqs = []
     for i in range(nreq):
-        if reqs and rng.random() < repeat_prob:
-            base = reqs[int(rng.integers(0, len(reqs)))]
-            kind, n, pseed = base["kind"], base["n"], base["point_seed"]
+        if pool:
+            kind, n, pseed, kid, ell, p, depth = pool[int(rng.integers(0, len(pool)))]
         else:
-            n = int(10 ** rng.uniform(np.log10(n_lo), np.log10(n_hi)))
-            kind = "uniform" if rng.random() < 0.5 else "clustered"
-            pseed = int(rng.integers(0, 2 ** 31))
-        kid, ell = kernels[int(rng.integers(0, 4))]
-        p = int(rng.choice([4, 5, 6]))
+            if reqs and rng.random() < repeat_prob:
+                base = reqs[int(rng.integers(0, len(reqs)))]
+                kind, n, pseed = base["kind"], base["n"], base["point_seed"]
+            else:
+                kind, n, pseed = recipe()
+            kid, ell = kernels[int(rng.integers(0, 4))]
+            p = int(rng.choice([4, 5, 6]))
+            depth = depth_of(n)
         nrhs = int(rng.choice([1, 8, 32]))
-        depth = int(np.clip(round(np.log(n / 32.0) / np.log(8.0)), 2, 7))
         reqs.append(dict(id=i, kind=kind, n=n, point_seed=pseed, sigma_seed=int(rng.integers(0, 2 ** 31)),
                          kernel=kid, ell=ell, p=p, nrhs=nrhs, depth=depth,
                          gap=float(rng.exponential(1.0))))

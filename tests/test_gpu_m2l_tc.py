@@ -113,6 +113,29 @@ def test_split3_multiple_rhs(bb, prec):
         assert rel(b[:, c], a[:, c]) < 2e-6, (c, rel(b[:, c], a[:, c]))
 
 
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "fp16x3", "bf16x3"])
+def test_fewer_columns_than_the_plan_holds(bb, prec):
+    """A plan made for 8 right-hand sides, called with 1, 3 and 8 columns (in
+    that order, then 1 again): each call equals the same columns run through a
+    plan made for exactly that many."""
+    n = 15000
+    dev = torch.device("cuda:0")
+    pts = W.clustered_points(n, seed=81)
+    sig = W.uniform_sigma(n, nrhs=8, seed=82).astype(np.float32)
+    plan = bb.Plan(torch.from_numpy(pts).to(dev), 1, 4, 4, svd_eps=1e-7, precision=prec, domain=UNIT, max_nrhs=8)
+    tol = 2e-5 if prec == "bf16x3" else 1e-6
+    for k in (1, 3, 8, 1):
+        s = torch.from_numpy(np.ascontiguousarray(sig[:, :k].T)).to(dev)
+        got = plan.matvec(s if k > 1 else s[0]).cpu().numpy().astype(np.float64)
+        got = got.T if k > 1 else got[:, None]
+        assert bb.bbfmm_status(plan.handle) == 0
+        want = run(bb, pts, sig[:, :k] if k > 1 else sig[:, 0], 1, 4, 4, prec, nrhs=k)
+        want = want if k > 1 else want[:, None]
+        for c in range(k):
+            assert rel(got[:, c], want[:, c]) < tol, (k, c, rel(got[:, c], want[:, c]))
+    plan.close()
+
+
 @pytest.mark.parametrize("prec", ["tf32x3", "fp16x3"])
 @pytest.mark.parametrize("depth", [5, 6])
 def test_split3_full_size_uniform_1M(bb, oracle, depth, prec):

@@ -120,3 +120,39 @@ def test_slots_run_different_plans_concurrently():
     assert slots == {0, 1, 2}
     # all three were in flight together: total time well under 3 delays
     assert max(r.t_done for r in rs) - min(r.t_submit for r in rs) < 0.14
+
+
+def test_slow_plan_build_does_not_block_resident_plans():
+    ex = FakeExecutor({"a": 10, "slow": 10}, delay=0.002, build_delay={"slow": 0.5})
+    srv = Server(ex, 100, slots=2, max_batch_nrhs=1).start()
+    srv.submit(make("a")).wait(5)                         # "a" is resident
+    slow = srv.submit(make("slow", seed=1))
+    t0 = slow.t_submit
+    fast = [srv.submit(make("a", seed=2 + i)) for i in range(5)]
+    for r in fast:
+        r.wait(5)
+    # the requests of the resident plan finished while "slow" was being built
+    assert max(r.t_done for r in fast) - t0 < 0.25
+    assert not slow._done.is_set()
+    np.testing.assert_allclose(slow.wait(5), slow.sigma * factor("slow"), rtol=1e-6)
+    assert slow.t_done - t0 >= 0.5
+    srv.stop()
+
+
+def test_building_plans_count_against_the_budget():
+    # two plans of 60 bytes in a 100-byte budget: the second waits for the
+    # first to be resident and idle, then evicts it; never both at once
+    ex = FakeExecutor({"a": 60, "b": 60}, delay=0.01, build_delay={"a": 0.1, "b": 0.1})
+    srv = Server(ex, 100, slots=2, max_batch_nrhs=1).start()
+    ra, rb = srv.submit(make("a")), srv.submit(make("b", seed=1))
+    ra.wait(5)
+    rb.wait(5)
+    srv.stop()
+    live, live_max = set(), 0
+    for e in ex.log:
+        if e[0] == "build":
+            live.add(e[1])
+        elif e[0] == "destroy":
+            live.discard(e[1])
+        live_max = max(live_max, len(live))
+    assert live_max == 1 and srv.evictions == 1
