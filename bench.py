@@ -354,9 +354,9 @@ def run_ours(args, rank, world, local):
     N = float(n)
     unit = "N^2/s" if nrhs == 1 else "N^2*nrhs/s"
     m2l_launches = depth - 1 if precision == "fp32" else 1
-    # gather, P2P, P2M, M2M, compress (+ split for 16-bit forms), M2L, L2L, decompress, L2P, combine
-    split = depth - 1 if precision in ("fp16x3", "bf16x3") else 0
-    launches = 2 + 1 + (depth - 2) + (depth - 1) + split + m2l_launches + (depth - 2) + (depth - 1) + 1 + 1
+    # gather, P2P, upward pass (+ 16-bit split for those forms), M2L, downward pass, combine
+    split = 1 if precision in ("fp16x3", "bf16x3") else 0
+    launches = 1 + 1 + 1 + split + m2l_launches + 1 + 1
     out = {
         "metric": METRIC, "value": world * N * N * nrhs / (ms / 1e3), "unit": unit, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,

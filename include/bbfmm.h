@@ -76,7 +76,11 @@ typedef struct {
     int use_graph;     /* 1 (default): the first matvec with a given nrhs captures
                           the whole launch sequence into a CUDA graph, later ones
                           replay it; 0: launch the kernels one by one */
-    int reserved[5];   /* zero */
+    int keep_coefficients; /* 1: every matvec also stores the multipole (M) and
+                              local (F) coefficients of every level for
+                              bbfmm_get_coefficients; 0 (default): they stay in
+                              the passes' on-chip memory and are not allocated */
+    int reserved[4];   /* zero */
 } bbfmm_opts;
 
 typedef struct {
@@ -149,7 +153,8 @@ int bbfmm_plan_info(bbfmm_plan_t plan, bbfmm_info *info);
  *   level: 2..D.
  *   out:   host, 8^level x nrhs x p^3 FP32, boxes in lexicographic order
  *          (a + 2^l (b + 2^l c)), node index i1 + p i2 + p^2 i3.
- * Synchronizes the device.  Errors: EINVAL.
+ * Needs a plan built with opts.keep_coefficients = 1.  Synchronizes the
+ * device.  Errors: EINVAL (bad arguments, or coefficients not kept).
  */
 int bbfmm_get_coefficients(bbfmm_plan_t plan, int which, int level, int nrhs, float *out);
 
@@ -164,8 +169,9 @@ int bbfmm_get_leaf_cells(bbfmm_plan_t plan, int32_t *out);
  * bbfmm_stage_times: device milliseconds of each stage of the last matvec,
  * measured with CUDA events on the matvec's streams when the plan was built
  * with timing on (see bbfmm_set_timing).  out[0..7] = gather, upward (P2M +
- * M2M + compress), M2L, downward (decompress + L2L), L2P, P2P, combine,
- * whole matvec.  Synchronizes the device.
+ * M2M + compress), M2L, downward (decompress + L2L + L2P, one launch), L2P
+ * (0: part of the downward launch), P2P, combine, whole matvec.
+ * Synchronizes the device.
  */
 int bbfmm_stage_times(bbfmm_plan_t plan, float *out);
 

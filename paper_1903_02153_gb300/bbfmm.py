@@ -38,7 +38,8 @@ class bbfmm_opts(ctypes.Structure):
                 ("precision", ctypes.c_int), ("domain_given", ctypes.c_int),
                 ("lo", ctypes.c_double * 3), ("side", ctypes.c_double),
                 ("max_nrhs", ctypes.c_int), ("split_accumulate", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("use_graph", ctypes.c_int), ("keep_coefficients", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 class bbfmm_info(ctypes.Structure):
@@ -221,11 +222,13 @@ class Plan:
     ``plan.matvec(sigma)`` with sigma a CUDA tensor (n,) or (nrhs, n)."""
 
     def __init__(self, points, kernel, order, depth, ell=1.0, svd_eps=1e-7, precision="fp32",
-                 domain=None, max_nrhs=1, stream=None, split_accumulate=True, use_graph=True):
+                 domain=None, max_nrhs=1, stream=None, split_accumulate=True, use_graph=True,
+                 keep_coefficients=False):
         import torch
         o = bbfmm_default_opts()
         o.split_accumulate = 1 if split_accumulate else 0
         o.use_graph = 1 if use_graph else 0
+        o.keep_coefficients = 1 if keep_coefficients else 0
         o.ell = float(ell)
         o.svd_eps = float(svd_eps)
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)

@@ -195,6 +195,10 @@ struct bbfmm_plan_impl {
     // scale applied before splitting, both written on the device each matvec
     unsigned *a16_max = nullptr;
     float *a16_scale = nullptr;
+    // upward pass: arrival counters of the boxes of levels 2..D-2 (x max_nrhs),
+    // zero between matvecs
+    int *up_count[kMaxDepth + 1] = {};
+    bool keep_coeffs = false; // also store leaf M and every level's F
 
     std::vector<void *> allocations;
     int64_t bytes = 0;
@@ -222,6 +226,31 @@ struct bbfmm_plan_impl {
 };
 
 // ---------------------------------------------------------------------------
+// Arguments of the fused upward / downward passes (passes.cu); arrays are
+// indexed by level
+struct PassArgs {
+    InterpTables T;
+    const float4 *pts;          // leaf-local coordinates, tree order
+    const int *off;             // leaf start offsets, 8^D + 1
+    int64_t n;
+    int D, nrhs, R, r, rp, p3p; // R = max_nrhs (row stride of M~ / F~)
+    const float *sig;           // upward: n x nrhs weights in tree order
+    float *phi;                 // downward: n x nrhs far field in tree order
+    float *M[kMaxDepth + 1];    // Morton [box][nrhs][p^3]; leaf level used only with keep
+    float *Mt[kMaxDepth + 1], *Mt_hi[kMaxDepth + 1], *Mt_lo[kMaxDepth + 1];
+    const float *Ft[kMaxDepth + 1];
+    int64_t slice[kMaxDepth + 1]; // floats between the offset-group slices of F~
+    int nslices;
+    float *F[kMaxDepth + 1];    // written only with keep
+    const float *V[kMaxDepth + 1], *Ut[kMaxDepth + 1];
+    unsigned *maxbits;          // per level max |M~| (float bits), or null
+    int *count[kMaxDepth + 1];  // upward arrival counters, levels 2..D-2
+    int keep;
+};
+cudaError_t launch_upward(const PassArgs &A, int p, cudaStream_t s);
+cudaError_t launch_downward(const PassArgs &A, int p, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
 // Launchers (each checks its arguments and returns a cudaError_t)
 // tree.cu
 cudaError_t launch_domain_minmax(const double *pts, int64_t n, double *d_minmax, cudaStream_t s);
@@ -242,22 +271,18 @@ int64_t scan_scratch_ints(int64_t n);
 // transfers.cu
 cudaError_t launch_gather_sigma(const float *sigma, const int *perm, int64_t n, int nrhs, float *out,
                                 cudaStream_t s);
-cudaError_t launch_p2m(const InterpTables &T, const float4 *pts, const float *sig, const int *leaf_off, int64_t n, int D, int p,
-                       int nrhs, float *M, cudaStream_t s);
-cudaError_t launch_m2m(const InterpTables &T, const float *Mchild, float *Mparent, int lparent, int p, int nrhs, cudaStream_t s);
-cudaError_t launch_l2l(const InterpTables &T, const float *Fparent, float *Fchild, int lparent, int p, int nrhs, cudaStream_t s);
-// (the parity-split M~ / F~ rows always use the plan's max_nrhs R as their
-// right-hand-side stride, so their zero halo never moves between calls)
-cudaError_t launch_compress(const float *M, const float *V, float *Mt, float *Mt_hi, float *Mt_lo, unsigned *maxbits,
-                            int l, int p3, int r, int rp, int nrhs, int R, cudaStream_t s);
-// split Mt (n floats) into 16-bit hi / lo after scaling by a power of two
-// chosen from *maxbits (FP16) or 1 (BF16); the scale is written to *scale
-cudaError_t launch_split16(const float *Mt, int64_t n, int fmt, const unsigned *maxbits, float *scale, uint16_t *hi,
-                           uint16_t *lo, cudaStream_t s);
-cudaError_t launch_decompress(const float *Ft, int nslices, int64_t slice, const float *Ut, float *F, int l,
-                              int p3, int p3p, int r, int rp, int nrhs, int R, bool accumulate, cudaStream_t s);
-cudaError_t launch_l2p(const InterpTables &T, const float4 *pts, const float *F, const int *leaf_off, int64_t n, int D, int p,
-                       int nrhs, float *phi_far, cudaStream_t s);
+// split the FP32 M~ of levels lmin..lmax (x[l], n[l] floats) into 16-bit
+// hi / lo after scaling by a power of two chosen from maxbits[l] (FP16, fmt 0)
+// or 1 (BF16, fmt 1); the scale is written to scale[l]
+struct Split16Args {
+    const float *x[kMaxDepth + 1];
+    int64_t n[kMaxDepth + 1];
+    uint16_t *hi[kMaxDepth + 1], *lo[kMaxDepth + 1];
+    const unsigned *maxbits;
+    float *scale;
+    int lmin, lmax, fmt;
+};
+cudaError_t launch_split16_levels(const Split16Args &A, cudaStream_t s);
 cudaError_t launch_combine(const float *phi_far, const float *phi_near, const int *perm, int64_t n,
                            int nrhs, float *phi, cudaStream_t s);
 // entry points of the two kernels whose pointer arguments (the caller's sigma

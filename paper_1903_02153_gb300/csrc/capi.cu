@@ -401,8 +401,14 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, cudaStream_t s)
     for (int l = 2; l <= D; ++l) {
         Level &L = P->lev[l];
         int64_t nb = 1LL << (3 * l), H = 1LL << (l - 1);
-        PTRY(plan_alloc(P, (void **)&L.M, 4 * nb * R * p3, false, s));
-        PTRY(plan_alloc(P, (void **)&L.F, 4 * nb * R * p3, false, s));
+        // M of levels below the leaves feeds the M2M chain of the upward pass;
+        // leaf M and every F stay in the passes' shared memory unless kept
+        if (l < D || P->keep_coeffs)
+            PTRY(plan_alloc(P, (void **)&L.M, 4 * nb * R * p3, false, s));
+        if (P->keep_coeffs)
+            PTRY(plan_alloc(P, (void **)&L.F, 4 * nb * R * p3, false, s));
+        if (l <= D - 2)
+            PTRY(plan_alloc(P, (void **)&P->up_count[l], 4 * nb * R, true, s));
         PTRY(plan_alloc(P, (void **)&L.Mt, 4 * 8 * (H + 2) * H * H * R * rp, true, s));
         PTRY(plan_alloc(P, (void **)&L.Ft, 4 * nb * R * rp * P->m2l_groups, true, s));
         if (P->precision == BBFMM_PREC_TF32X3) {
@@ -444,6 +450,42 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, cudaStream_t s)
 }
 
 // ---------------------------------------------------------------------------
+static PassArgs pass_args(const bbfmm_plan_impl *P, int nrhs, bool split16)
+{
+    const DevOps &O = *P->ops;
+    PassArgs A;
+    memset(&A, 0, sizeof(A));
+    A.T = P->interp;
+    A.pts = P->pts;
+    A.off = P->leaf_off;
+    A.n = P->n;
+    A.D = P->D;
+    A.nrhs = nrhs;
+    A.R = P->max_nrhs;
+    A.r = O.r;
+    A.rp = O.rp;
+    A.p3p = O.p3p;
+    A.sig = P->sigma_s;
+    A.phi = P->phi_far;
+    A.nslices = P->m2l_groups;
+    A.maxbits = split16 ? P->a16_max : nullptr;
+    A.keep = P->keep_coeffs ? 1 : 0;
+    for (int l = 2; l <= P->D; ++l) {
+        const Level &L = P->lev[l];
+        A.M[l] = L.M;
+        A.Mt[l] = L.Mt;
+        A.Mt_hi[l] = L.Mt_hi;
+        A.Mt_lo[l] = L.Mt_lo;
+        A.Ft[l] = L.Ft;
+        A.slice[l] = (1LL << (3 * l)) * P->max_nrhs * O.rp;
+        A.F[l] = L.F;
+        A.V[l] = O.V[O.nlev == 1 ? 0 : l - 2];
+        A.Ut[l] = O.Ut[O.nlev == 1 ? 0 : l - 2];
+        A.count[l] = P->up_count[l];
+    }
+    return A;
+}
+
 static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int nrhs, cudaStream_t s)
 {
     const int64_t n = P->n;
@@ -478,25 +520,27 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
         // far field on the high-priority plan stream
         cudaStream_t fs = P->far_stream;
         CUDA_TRY(cudaStreamWaitEvent(fs, P->ev_fork, 0));
-        const InterpTables &T = P->interp;
-        auto V = [&](int l) { return O.V[O.nlev == 1 ? 0 : l - 2]; };
-        auto Ut = [&](int l) { return O.Ut[O.nlev == 1 ? 0 : l - 2]; };
-        // upward pass: P2M at the leaves, M2M up to level 2, compress every level
-        CUDA_TRY(launch_p2m(T, P->pts, P->sigma_s, P->leaf_off, n, D, p, nrhs, P->lev[D].M, fs));
-        for (int l = D - 1; l >= 2; --l)
-            CUDA_TRY(launch_m2m(T, P->lev[l + 1].M, P->lev[l].M, l, p, nrhs, fs));
         const bool split16 = P->precision == BBFMM_PREC_FP16X3 || P->precision == BBFMM_PREC_BF16X3;
+        const PassArgs A = pass_args(P, nrhs, split16);
+        // upward pass: P2M, M2M and compression of every level in one launch
         if (split16)
             CUDA_TRY(cudaMemsetAsync(P->a16_max, 0, 4 * (kMaxDepth + 1), fs));
-        for (int l = D; l >= 2; --l) {
-            CUDA_TRY(launch_compress(P->lev[l].M, V(l), P->lev[l].Mt, P->lev[l].Mt_hi, P->lev[l].Mt_lo,
-                                     split16 ? P->a16_max + l : nullptr, l, p3, O.r, O.rp, nrhs, P->max_nrhs, fs));
-            if (split16) {
+        CUDA_TRY(launch_upward(A, p, fs));
+        if (split16) {
+            Split16Args S = {};
+            S.fmt = P->precision == BBFMM_PREC_FP16X3 ? 0 : 1;
+            S.lmin = 2;
+            S.lmax = D;
+            S.maxbits = P->a16_max;
+            S.scale = P->a16_scale;
+            for (int l = 2; l <= D; ++l) {
                 const int64_t H = 1LL << (l - 1);
-                CUDA_TRY(launch_split16(P->lev[l].Mt, 8 * (H + 2) * H * H * P->max_nrhs * O.rp,
-                                        P->precision == BBFMM_PREC_FP16X3 ? 0 : 1, P->a16_max + l,
-                                        P->a16_scale + l, P->lev[l].Mt16_hi, P->lev[l].Mt16_lo, fs));
+                S.x[l] = P->lev[l].Mt;
+                S.n[l] = 8 * (H + 2) * H * H * P->max_nrhs * O.rp;
+                S.hi[l] = P->lev[l].Mt16_hi;
+                S.lo[l] = P->lev[l].Mt16_lo;
             }
+            CUDA_TRY(launch_split16_levels(S, fs));
         }
         if (tm)
             CUDA_TRY(cudaEventRecord(P->ev[Stage::Up], fs));
@@ -506,18 +550,12 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
         CUDA_TRY(launch_m2l_all(P, nrhs, fs));
         if (tm)
             CUDA_TRY(cudaEventRecord(P->ev[Stage::M2L], fs));
-        // downward pass
-        for (int l = 2; l <= D; ++l) {
-            if (l >= 3)
-                CUDA_TRY(launch_l2l(T, P->lev[l - 1].F, P->lev[l].F, l - 1, p, nrhs, fs));
-            CUDA_TRY(launch_decompress(P->lev[l].Ft, P->m2l_groups, (1LL << (3 * l)) * P->max_nrhs * O.rp, Ut(l),
-                                       P->lev[l].F, l, p3, O.p3p, O.r, O.rp, nrhs, P->max_nrhs, l >= 3, fs));
-        }
-        if (tm)
+        // downward pass: decompression, L2L and L2P in one launch
+        CUDA_TRY(launch_downward(A, p, fs));
+        if (tm) {
             CUDA_TRY(cudaEventRecord(P->ev[Stage::Down], fs));
-        CUDA_TRY(launch_l2p(T, P->pts, P->lev[D].F, P->leaf_off, n, D, p, nrhs, P->phi_far, fs));
-        if (tm)
             CUDA_TRY(cudaEventRecord(P->ev[Stage::L2P], fs));
+        }
         CUDA_TRY(cudaEventRecord(P->ev_far, fs));
         CUDA_TRY(cudaStreamWaitEvent(s, P->ev_far, 0));
     } else if (tm) {
@@ -682,6 +720,7 @@ int bbfmm_plan(const double *points, int64_t n, int kernel_id, int cheb_order, i
     P->eps = opts.svd_eps;
     P->split_acc = opts.split_accumulate != 0;
     P->use_graph = opts.use_graph != 0;
+    P->keep_coeffs = opts.keep_coefficients != 0;
     if (opts.domain_given) {
         for (int d = 0; d < 3; ++d)
             P->lo[d] = opts.lo[d];
@@ -786,6 +825,8 @@ int bbfmm_get_coefficients(bbfmm_plan_t plan, int which, int level, int nrhs, fl
         return fail(BBFMM_EINVAL, "NULL argument");
     if (level < 2 || level > plan->D || (which != 0 && which != 1) || nrhs < 1 || nrhs > plan->max_nrhs)
         return fail(BBFMM_EINVAL, "bad which / level / nrhs");
+    if (!plan->keep_coeffs)
+        return fail(BBFMM_EINVAL, "the plan was built without opts.keep_coefficients");
     const float *src = which == 0 ? plan->lev[level].M : plan->lev[level].F;
     int64_t nb = 1LL << (3 * level), p3 = plan->p3;
     std::vector<float> tmp(nb * nrhs * p3);

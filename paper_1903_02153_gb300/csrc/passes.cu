@@ -1,0 +1,598 @@
+// passes.cu -- the upward and downward passes of the black-box FMM, each as
+// ONE launch over the boxes of level D-1 (one block per box and right-hand
+// side).
+//
+// Upward (Sec. 2.2 item 1, with the compression of Sec. 2.5 "Fast M2L
+// translation"): a block makes the multipole coefficients of its 8 leaves
+// (P2M, Def. 2.2 applied to the sources), compresses them (M~ = V^T M),
+// combines them into its own box (M2M, the nested interpolation of Thm. 2.1
+// item 1) and compresses that.  The upper levels follow without another
+// launch: after its box is written, a block counts itself in at the parent;
+// the eighth of the siblings to arrive (the others return) reads the 8
+// sibling coefficient sets, makes and compresses the parent's, and counts
+// itself in one level up, down to level 2.  No block waits for another.
+//
+// Downward (Sec. 2.2 item 3): a block recomputes the local coefficients of
+// its ancestors from level 2 down (decompress F = U F~ of each, plus the L2L
+// of its parent's), spreads its own box's to its 8 leaves (L2L), adds the
+// leaves' decompressed far fields and evaluates them at the leaves' points
+// (L2P).  The ancestor work repeats in every block of an ancestor's subtree;
+// it is small next to the leaf work and removes the level-by-level launches.
+//
+// Coefficient layouts: M and F are Morton-ordered [box][nrhs][p^3]; M~ / F~
+// rows sit at parity_row() of their box with the plan's max_nrhs as stride.
+// Inside a block the coefficient sets of 8 sibling boxes are kept as
+// [p^3][8] so that one 16-byte shared load gives 4 boxes.
+#include "bbfmm_internal.h"
+
+namespace bbfmm {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ float tf32_round(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+template <int P>
+__device__ __forceinline__ void basis_1d(const InterpTables &T, float s, float *out)
+{
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        float v = T.wbary[i];
+#pragma unroll
+        for (int k = 0; k < P; ++k)
+            if (k != i)
+                v *= s - T.nodes[k];
+        out[i] = v;
+    }
+}
+
+template <int P> struct Smem {
+    static constexpr int P3 = P * P * P;
+    // upward: sMT [P3][8] | scratch: max(basis table 8 warps x 3 x 32 x P + sigma 8 x 32, two [P3][8])
+    //         | sPar [P3]
+    static constexpr int kScratch = (768 * P + 256) > 16 * P3 ? (768 * P + 256) : 16 * P3;
+    static constexpr int kUpFloats = 8 * P3 + kScratch + P3;
+    // downward: sMT [P3][8] | two [P3][8] | sPar [P3] | sOne [P3] | sFt [r][8] (r <= P3);
+    // sFt is read as float4, so its offset is a multiple of 4 floats
+    static constexpr int kDownFt = (26 * P3 + 3) & ~3;
+    static constexpr int kDownFloats = kDownFt + 8 * P3;
+};
+
+// M2M of 8 children X ([P3][8]) into one parent (Thm. 2.1 item 1 in tensor
+// form: three 1D passes with the child-to-parent matrices S), scratch Y, Z of
+// [P3][8]; result in out[P3].  Child o has (x, y, z) parity (o & 1, (o >> 1)
+// & 1, o >> 2), its position in Morton order.
+template <int P>
+__device__ void m2m8(const InterpTables &T, const float *X, float *Y, float *Z, float *out)
+{
+    constexpr int P3 = P * P * P;
+    const int t = threadIdx.x;
+    for (int q = t; q < 8 * P3; q += kThreads) { // x pass
+        const int o = q & 7, r = q >> 3, i1 = r % P, rest = r / P;
+        float acc = 0.0f;
+#pragma unroll
+        for (int j1 = 0; j1 < P; ++j1)
+            acc += T.S[o & 1][i1][j1] * X[(j1 + P * rest) * 8 + o];
+        Y[q] = acc;
+    }
+    __syncthreads();
+    for (int q = t; q < 8 * P3; q += kThreads) { // y pass
+        const int o = q & 7, r = q >> 3, i1 = r % P, i2 = (r / P) % P, j3 = r / (P * P);
+        float acc = 0.0f;
+#pragma unroll
+        for (int j2 = 0; j2 < P; ++j2)
+            acc += T.S[(o >> 1) & 1][i2][j2] * Y[(i1 + P * j2 + P * P * j3) * 8 + o];
+        Z[q] = acc;
+    }
+    __syncthreads();
+    for (int r = t; r < P3; r += kThreads) { // z pass, summed over the children
+        const int i12 = r % (P * P), i3 = r / (P * P);
+        float acc = 0.0f;
+#pragma unroll
+        for (int o = 0; o < 8; ++o)
+#pragma unroll
+            for (int j3 = 0; j3 < P; ++j3)
+                acc += T.S[o >> 2][i3][j3] * Z[(i12 + P * P * j3) * 8 + o];
+        out[r] = acc;
+    }
+    __syncthreads();
+}
+
+// L2L of one parent F (P3) into its 8 children ([P3][8], written), the
+// transpose of m2m8; scratch Y, Z [P3][8].
+template <int P>
+__device__ void l2l8(const InterpTables &T, const float *F, float *Y, float *Z, float *out)
+{
+    constexpr int P3 = P * P * P;
+    const int t = threadIdx.x;
+    for (int q = t; q < 8 * P3; q += kThreads) { // z pass
+        const int o = q & 7, r = q >> 3, j12 = r % (P * P), i3 = r / (P * P);
+        float acc = 0.0f;
+#pragma unroll
+        for (int j3 = 0; j3 < P; ++j3)
+            acc += T.S[o >> 2][j3][i3] * F[j12 + P * P * j3];
+        Y[q] = acc;
+    }
+    __syncthreads();
+    for (int q = t; q < 8 * P3; q += kThreads) { // y pass
+        const int o = q & 7, r = q >> 3, j1 = r % P, i2 = (r / P) % P, i3 = r / (P * P);
+        float acc = 0.0f;
+#pragma unroll
+        for (int j2 = 0; j2 < P; ++j2)
+            acc += T.S[(o >> 1) & 1][j2][i2] * Y[(j1 + P * j2 + P * P * i3) * 8 + o];
+        Z[q] = acc;
+    }
+    __syncthreads();
+    for (int q = t; q < 8 * P3; q += kThreads) { // x pass
+        const int o = q & 7, r = q >> 3, i1 = r % P, rest = r / P;
+        float acc = 0.0f;
+#pragma unroll
+        for (int j1 = 0; j1 < P; ++j1)
+            acc += T.S[o & 1][j1][i1] * Z[(j1 + P * rest) * 8 + o];
+        out[q] = acc;
+    }
+    __syncthreads();
+}
+
+// L2L of a parent F into its child o only (three 1D passes over P3 values);
+// scratch Y; result in out.
+template <int P>
+__device__ void l2l1(const InterpTables &T, const float *F, int o, float *Y, float *out)
+{
+    constexpr int P3 = P * P * P;
+    const int t = threadIdx.x;
+    for (int r = t; r < P3; r += kThreads) { // z pass
+        const int j12 = r % (P * P), i3 = r / (P * P);
+        float acc = 0.0f;
+#pragma unroll
+        for (int j3 = 0; j3 < P; ++j3)
+            acc += T.S[o >> 2][j3][i3] * F[j12 + P * P * j3];
+        Y[r] = acc;
+    }
+    __syncthreads();
+    for (int r = t; r < P3; r += kThreads) { // y pass
+        const int j1 = r % P, i2 = (r / P) % P, i3 = r / (P * P);
+        float acc = 0.0f;
+#pragma unroll
+        for (int j2 = 0; j2 < P; ++j2)
+            acc += T.S[(o >> 1) & 1][j2][i2] * Y[j1 + P * j2 + P * P * i3];
+        out[r] = acc;
+    }
+    __syncthreads();
+    for (int r = t; r < P3; r += kThreads) { // x pass (in place by rows of P)
+        const int i1 = r % P, rest = r / P;
+        float acc = 0.0f;
+#pragma unroll
+        for (int j1 = 0; j1 < P; ++j1)
+            acc += T.S[o & 1][j1][i1] * out[j1 + P * rest];
+        Y[r] = acc;
+    }
+    __syncthreads();
+    for (int r = t; r < P3; r += kThreads)
+        out[r] = Y[r];
+    __syncthreads();
+}
+
+// store one M~ value: FP32 row, optional TF32 hi/lo split, running max |M~|
+__device__ __forceinline__ void put_mt(const PassArgs &A, int l, int64_t at, float v, float &mx)
+{
+    A.Mt[l][at] = v;
+    if (A.Mt_hi[l]) {
+        const float hi = tf32_round(v);
+        A.Mt_hi[l][at] = hi;
+        A.Mt_lo[l][at] = tf32_round(v - hi);
+    }
+    mx = fmaxf(mx, fabsf(v));
+}
+
+__device__ __forceinline__ void flush_max(const PassArgs &A, int l, float mx)
+{
+    if (!A.maxbits)
+        return;
+    for (int o = 16; o > 0; o >>= 1)
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx > 0.0f)
+        atomicMax(A.maxbits + l, __float_as_uint(mx));
+}
+
+// compress 8 sibling boxes box0..box0+7 at level l: M~[k] = sum_i V[i][k] M[i]
+template <int P>
+__device__ void compress8(const PassArgs &A, int l, const float *X, int64_t box0, int c, bool zero)
+{
+    constexpr int P3 = P * P * P;
+    const int t = threadIdx.x, h = t >> 7;
+    const int H = 1 << (l - 1);
+    const float *V = A.V[l];
+    float mx = 0.0f;
+    for (int k0 = 0; k0 < A.r; k0 += 128) { // uniform trip count: the warp shuffles below need all lanes
+        const int k = k0 + (t & 127);
+        const bool on = k < A.r;
+        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (on && !zero) {
+#pragma unroll 5
+            for (int i = 0; i < P3; ++i) {
+                const float v = __ldg(V + (int64_t)i * A.rp + k);
+                const float4 m = *reinterpret_cast<const float4 *>(X + i * 8 + 4 * h);
+                acc[0] += m.x * v;
+                acc[1] += m.y * v;
+                acc[2] += m.z * v;
+                acc[3] += m.w * v;
+            }
+        }
+        if (on) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int x, y, z;
+                demorton3((uint32_t)(box0 + 4 * h + q), x, y, z);
+                put_mt(A, l, parity_row(x, y, z, c, H, 1, A.R) * A.rp + k, acc[q], mx);
+            }
+        }
+    }
+    flush_max(A, l, mx);
+}
+
+// compress one box at level l from F32 coefficients X[P3]
+template <int P>
+__device__ void compress1(const PassArgs &A, int l, const float *X, int64_t box, int c)
+{
+    constexpr int P3 = P * P * P;
+    const int t = threadIdx.x;
+    const int H = 1 << (l - 1);
+    const float *V = A.V[l];
+    int x, y, z;
+    demorton3((uint32_t)box, x, y, z);
+    const int64_t row = parity_row(x, y, z, c, H, 1, A.R) * A.rp;
+    float mx = 0.0f;
+    for (int k0 = 0; k0 < A.r; k0 += kThreads) {
+        const int k = k0 + t;
+        if (k < A.r) {
+            float a0 = 0.0f, a1 = 0.0f;
+            int i = 0;
+            for (; i + 1 < P3; i += 2) {
+                a0 += X[i] * __ldg(V + (int64_t)i * A.rp + k);
+                a1 += X[i + 1] * __ldg(V + (int64_t)(i + 1) * A.rp + k);
+            }
+            if (i < P3)
+                a0 += X[i] * __ldg(V + (int64_t)i * A.rp + k);
+            put_mt(A, l, row + k, a0 + a1, mx);
+        }
+    }
+    flush_max(A, l, mx);
+}
+
+// ---------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_upward(const __grid_constant__ PassArgs A)
+{
+    constexpr int P3 = P * P * P;
+    constexpr int NQ = (P * P + 31) / 32; // (i2, i3) pairs per lane in P2M
+    extern __shared__ __align__(16) float sm[];
+    float *sMT = sm;                       // [P3][8]
+    float *sScr = sm + 8 * P3;             // scratch
+    float *sPar = sScr + Smem<P>::kScratch; // [P3]
+    float *sL = sScr;                      // [8][3][32][P] basis values (x row premultiplied by sigma)
+    __shared__ int sLast;
+
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    const int D = A.D;
+    const int64_t b = blockIdx.x; // box at level D-1
+    const int c = blockIdx.y;     // right-hand side
+    const int64_t leaf = 8 * b + w;
+    const int s0 = A.off[leaf], s1 = A.off[leaf + 1];
+    const bool zero = __syncthreads_count(s1 > s0) == 0;
+
+    // ---- P2M: warp w makes M of leaf 8b + w (Sec. 2.2 item 1, Def. 2.2)
+    {
+        float acc[NQ][P];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+            for (int i = 0; i < P; ++i)
+                acc[q][i] = 0.0f;
+        float *L = sL + w * 3 * 32 * P;
+        for (int c0 = s0; c0 < s1; c0 += 32) {
+            const int cnt = min(32, s1 - c0);
+            __syncwarp();
+            if (lane < cnt) {
+                const float4 u = A.pts[c0 + lane];
+                const float sg = A.sig[(int64_t)c * A.n + c0 + lane];
+                float v[P];
+                basis_1d<P>(A.T, 2.0f * u.x, v);
+#pragma unroll
+                for (int i = 0; i < P; ++i)
+                    L[lane * P + i] = v[i] * sg;
+                basis_1d<P>(A.T, 2.0f * u.y, v);
+#pragma unroll
+                for (int i = 0; i < P; ++i)
+                    L[(32 + lane) * P + i] = v[i];
+                basis_1d<P>(A.T, 2.0f * u.z, v);
+#pragma unroll
+                for (int i = 0; i < P; ++i)
+                    L[(64 + lane) * P + i] = v[i];
+            }
+            __syncwarp();
+            for (int j = 0; j < cnt; ++j) {
+                float lx[P];
+#pragma unroll
+                for (int i = 0; i < P; ++i)
+                    lx[i] = L[j * P + i];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const int pq = lane + 32 * q;
+                    if (pq < P * P) {
+                        const float yz = L[(32 + j) * P + pq % P] * L[(64 + j) * P + pq / P];
+#pragma unroll
+                        for (int i = 0; i < P; ++i)
+                            acc[q][i] += lx[i] * yz;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int pq = lane + 32 * q;
+            if (pq < P * P) {
+#pragma unroll
+                for (int i = 0; i < P; ++i) {
+                    const int idx = i + P * pq;
+                    sMT[idx * 8 + w] = acc[q][i];
+                    if (A.keep)
+                        A.M[D][(leaf * A.nrhs + c) * P3 + idx] = acc[q][i];
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- compress the leaves
+    compress8<P>(A, D, sMT, 8 * b, c, zero);
+    if (D - 1 < 2)
+        return;
+
+    // ---- own box at level D-1: M2M of the 8 leaves, store, compress
+    if (zero) {
+        for (int r = t; r < P3; r += kThreads)
+            sPar[r] = 0.0f;
+        __syncthreads();
+    } else {
+        m2m8<P>(A.T, sMT, sScr, sScr + 8 * P3, sPar);
+    }
+    for (int r = t; r < P3; r += kThreads)
+        A.M[D - 1][(b * A.nrhs + c) * P3 + r] = sPar[r];
+    compress1<P>(A, D - 1, sPar, b, c);
+
+    // ---- upper levels: the last of 8 siblings to arrive makes the parent
+    int64_t box = b;
+    for (int l = D - 2; l >= 2; --l) {
+        const int64_t par = box >> 3;
+        __threadfence(); // this thread's stores of the level-(l+1) box are visible device-wide
+        __syncthreads();
+        if (t == 0) {
+            int *cnt = A.count[l] + par * A.R + c;
+            const int before = atomicAdd(cnt, 1);
+            sLast = before == 7;
+            if (before == 7) {
+                atomicExch(cnt, 0); // ready for the next matvec
+                __threadfence();
+            }
+        }
+        __syncthreads();
+        if (!sLast)
+            return;
+        const float *Mc = A.M[l + 1] + (8 * par * A.nrhs + c) * (int64_t)P3;
+        for (int q = t; q < 8 * P3; q += kThreads) {
+            const int o = q & 7, r = q >> 3;
+            sMT[q] = __ldcg(Mc + (int64_t)o * A.nrhs * P3 + r);
+        }
+        __syncthreads();
+        m2m8<P>(A.T, sMT, sScr, sScr + 8 * P3, sPar);
+        for (int r = t; r < P3; r += kThreads)
+            A.M[l][(par * A.nrhs + c) * P3 + r] = sPar[r];
+        compress1<P>(A, l, sPar, par, c);
+        box = par;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// F~ row of box at level l, column c, summed over the M2L offset-group slices
+// in a fixed order, into dst[k * stride] for k < r
+__device__ __forceinline__ void load_ft(const PassArgs &A, int l, int64_t box, int c, float *dst, int stride,
+                                        int k)
+{
+    const int H = 1 << (l - 1);
+    int x, y, z;
+    demorton3((uint32_t)box, x, y, z);
+    const float *src = A.Ft[l] + parity_row(x, y, z, c, H, 0, A.R) * A.rp + k;
+    float v = __ldg(src);
+    for (int g = 1; g < A.nslices; ++g)
+        v += __ldg(src + g * A.slice[l]);
+    dst[k * stride] = v;
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_downward(const __grid_constant__ PassArgs A)
+{
+    constexpr int P3 = P * P * P;
+    extern __shared__ __align__(16) float sm[];
+    float *sMT = sm;              // [P3][8] leaf local coefficients
+    float *sY = sm + 8 * P3;      // [P3][8] scratch
+    float *sZ = sY + 8 * P3;      // [P3][8] scratch
+    float *sPar = sZ + 8 * P3;    // [P3] local coefficients of the current ancestor
+    float *sOne = sPar + P3;      // [P3] scratch
+    float *sFt = sm + Smem<P>::kDownFt; // [r][8] far-field coefficients (compressed)
+
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    const int D = A.D;
+    const int64_t b = blockIdx.x; // box at level D-1
+    const int c = blockIdx.y;
+    if (!A.keep && A.off[8 * b] == A.off[8 * b + 8])
+        return; // no targets below this box
+
+    // ---- ancestors at levels 2 .. D-1 (the last one is the block's own box)
+    for (int l = 2; l <= D - 1; ++l) {
+        const int64_t anc = b >> (3 * (D - 1 - l));
+        if (l > 2)
+            l2l1<P>(A.T, sPar, (int)(anc & 7), sOne, sPar);
+        for (int k = t; k < A.r; k += kThreads)
+            load_ft(A, l, anc, c, sFt, 1, k);
+        __syncthreads();
+        const float *Ut = A.Ut[l];
+        for (int i = t; i < P3; i += kThreads) {
+            float a0 = 0.0f, a1 = 0.0f;
+            int k = 0;
+            for (; k + 1 < A.r; k += 2) {
+                a0 += sFt[k] * __ldg(Ut + (int64_t)k * A.p3p + i);
+                a1 += sFt[k + 1] * __ldg(Ut + (int64_t)(k + 1) * A.p3p + i);
+            }
+            if (k < A.r)
+                a0 += sFt[k] * __ldg(Ut + (int64_t)k * A.p3p + i);
+            const float f = (l > 2 ? sPar[i] : 0.0f) + (a0 + a1);
+            sPar[i] = f;
+            if (A.keep && (b & ((1LL << (3 * (D - 1 - l))) - 1)) == 0)
+                A.F[l][(anc * A.nrhs + c) * P3 + i] = f;
+        }
+        __syncthreads();
+    }
+
+    // ---- the 8 leaves: L2L from the block's box (none when it is at level 1)
+    // plus their own decompressed far field
+    if (D - 1 >= 2) {
+        l2l8<P>(A.T, sPar, sY, sZ, sMT);
+    } else {
+        for (int q = t; q < 8 * P3; q += kThreads)
+            sMT[q] = 0.0f;
+    }
+    for (int q = t; q < 8 * A.r; q += kThreads) {
+        const int o = q & 7, k = q >> 3;
+        load_ft(A, D, 8 * b + o, c, sFt + o, 8, k);
+    }
+    __syncthreads();
+    {
+        const float *Ut = A.Ut[D];
+        const int h = t >> 7;
+        for (int i0 = 0; i0 < P3; i0 += 128) {
+            const int i = i0 + (t & 127);
+            if (i < P3) {
+                float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 4
+                for (int k = 0; k < A.r; ++k) {
+                    const float u = __ldg(Ut + (int64_t)k * A.p3p + i);
+                    const float4 f = *reinterpret_cast<const float4 *>(sFt + k * 8 + 4 * h);
+                    acc[0] += f.x * u;
+                    acc[1] += f.y * u;
+                    acc[2] += f.z * u;
+                    acc[3] += f.w * u;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    sMT[i * 8 + 4 * h + q] += acc[q];
+            }
+        }
+    }
+    __syncthreads();
+    if (A.keep)
+        for (int q = t; q < 8 * P3; q += kThreads) {
+            const int o = q & 7, r = q >> 3;
+            A.F[D][((8 * b + o) * A.nrhs + c) * P3 + r] = sMT[q];
+        }
+
+    // ---- L2P: warp w evaluates leaf 8b + w at its points (Sec. 2.2 item 3)
+    const int64_t leaf = 8 * b + w;
+    const int s0 = A.off[leaf], s1 = A.off[leaf + 1];
+    for (int c0 = s0; c0 < s1; c0 += 32) {
+        const int j = c0 + lane;
+        const bool has = j < s1;
+        const float4 u = A.pts[has ? j : s0];
+        float Lx[P], Ly[P];
+        basis_1d<P>(A.T, 2.0f * u.x, Lx);
+        basis_1d<P>(A.T, 2.0f * u.y, Ly);
+        const float sz = 2.0f * u.z;
+        float acc = 0.0f;
+        // the z slices one at a time (the z basis value made on the spot), so
+        // that the P^3 coefficient loads are not all kept in registers
+#pragma unroll 1
+        for (int i3 = 0; i3 < P; ++i3) {
+            float lz = A.T.wbary[i3];
+#pragma unroll
+            for (int k = 0; k < P; ++k)
+                lz *= k != i3 ? sz - A.T.nodes[k] : 1.0f;
+            const float *Fz = sMT + (P * P * i3) * 8 + w;
+            float slice = 0.0f;
+#pragma unroll
+            for (int i2 = 0; i2 < P; ++i2) {
+                float part = 0.0f;
+#pragma unroll
+                for (int i1 = 0; i1 < P; ++i1)
+                    part += Fz[(i1 + P * i2) * 8] * Lx[i1];
+                slice += part * Ly[i2];
+            }
+            acc += slice * lz;
+        }
+        if (has)
+            A.phi[(int64_t)c * A.n + j] = acc;
+    }
+}
+
+template <int P>
+cudaError_t upward_p(const PassArgs &A, cudaStream_t s)
+{
+    const size_t smem = sizeof(float) * Smem<P>::kUpFloats;
+    cudaError_t e = cudaFuncSetAttribute(k_upward<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    dim3 grid((unsigned)(1LL << (3 * (A.D - 1))), (unsigned)A.nrhs);
+    k_upward<P><<<grid, kThreads, smem, s>>>(A);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t downward_p(const PassArgs &A, cudaStream_t s)
+{
+    const size_t smem = sizeof(float) * Smem<P>::kDownFloats;
+    cudaError_t e = cudaFuncSetAttribute(k_downward<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    dim3 grid((unsigned)(1LL << (3 * (A.D - 1))), (unsigned)A.nrhs);
+    k_downward<P><<<grid, kThreads, smem, s>>>(A);
+    return cudaGetLastError();
+}
+
+} // namespace
+
+#define BBFMM_PASS_DISPATCH(p, F)                                                                               \
+    switch (p) {                                                                                                \
+    case 2: return F<2>(A, s);                                                                                  \
+    case 3: return F<3>(A, s);                                                                                  \
+    case 4: return F<4>(A, s);                                                                                  \
+    case 5: return F<5>(A, s);                                                                                  \
+    case 6: return F<6>(A, s);                                                                                  \
+    case 7: return F<7>(A, s);                                                                                  \
+    case 8: return F<8>(A, s);                                                                                  \
+    case 9: return F<9>(A, s);                                                                                  \
+    case 10: return F<10>(A, s);                                                                                \
+    default: return cudaErrorInvalidValue;                                                                      \
+    }
+
+cudaError_t launch_upward(const PassArgs &A, int p, cudaStream_t s)
+{
+    if (A.D < 2 || A.r > p * p * p || A.nrhs < 1 || A.nrhs > A.R)
+        return cudaErrorInvalidValue;
+    BBFMM_PASS_DISPATCH(p, upward_p)
+}
+
+cudaError_t launch_downward(const PassArgs &A, int p, cudaStream_t s)
+{
+    if (A.D < 2 || A.r > p * p * p || A.nrhs < 1 || A.nrhs > A.R)
+        return cudaErrorInvalidValue;
+    BBFMM_PASS_DISPATCH(p, downward_p)
+}
+
+#undef BBFMM_PASS_DISPATCH
+
+} // namespace bbfmm

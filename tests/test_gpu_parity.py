@@ -33,7 +33,7 @@ def gpu_matvec(bb, pts, sig, kid, p, depth, ell=1.0, eps=1e-7, precision="fp32",
     sig = np.asarray(sig, dtype=np.float32)
     nrhs = 1 if sig.ndim == 1 else sig.shape[1]
     plan = bb.Plan(torch.from_numpy(np.ascontiguousarray(pts)).to(dev), kid, p, depth, ell=ell,
-                   svd_eps=eps, precision=precision, domain=domain, max_nrhs=nrhs)
+                   svd_eps=eps, precision=precision, domain=domain, max_nrhs=nrhs, keep_coefficients=keep)
     s = torch.from_numpy(np.ascontiguousarray(sig.T if nrhs > 1 else sig)).to(dev)
     phi = plan.matvec(s)
     torch.cuda.synchronize()
@@ -86,12 +86,15 @@ def test_depth0_1_is_direct_sum(bb, oracle, depth, kid, ell):
     assert oracle.rel_err(got, ref) < 1e-5
 
 
-@pytest.mark.parametrize("p,depth", [(4, 3), (5, 4)])
-def test_stage_coefficients_match_oracle(bb, oracle, p, depth):
+@pytest.mark.parametrize("p,depth,kind", [(4, 3, "uniform"), (5, 4, "uniform"), (2, 2, "uniform"),
+                                          (3, 5, "clustered"), (7, 3, "uniform")])
+def test_stage_coefficients_match_oracle(bb, oracle, p, depth, kind):
     """Uncompressed operators (svd_eps = 0): M (upward pass) and F (after M2L
-    and L2L) on every level 2..D match the oracle's stage outputs."""
+    and L2L) on every level 2..D match the oracle's stage outputs.  Depth 2
+    has no M2M / L2L; depth 5 runs the upward pass's arrival chain over three
+    levels; the clustered set leaves whole level-(D-1) boxes empty."""
     n = 12_000
-    pts = W.uniform_points(n, seed=45)
+    pts = W.make_points(kind, n, seed=45)
     sig = W.uniform_sigma(n, seed=46).astype(np.float32)
     got, plan = gpu_matvec(bb, pts, sig, K_INV_R, p, depth, eps=0.0, keep=True)
     ref, Ms, Fs = oracle_fmm(oracle, pts, sig, K_INV_R, p, depth, dump=True)
@@ -106,7 +109,41 @@ def test_stage_coefficients_match_oracle(bb, oracle, p, depth):
         occ = np.unique(c[:, 0] + 2 ** l * (c[:, 1] + 2 ** l * c[:, 2]))
         assert oracle.rel_err(gf[occ], Fs[l][occ]) < 5e-6, ("F", l)
     plan.close()
-    assert oracle.rel_err(got, ref) < 5e-6
+    # whole result: the near field's FP32 leaf-local coordinates alone cost
+    # 2.0e-5 on the clustered set (close pairs under 1/r; the same rounding
+    # emulated on the CPU gives 2.00e-5), under 1e-6 on the uniform ones
+    assert oracle.rel_err(got, ref) < (3e-5 if kind == "clustered" else 5e-6)
+
+
+def test_coefficients_need_keep(bb):
+    pts = W.uniform_points(2000, seed=57)
+    plan = bb.Plan(torch.from_numpy(pts).cuda(), K_INV_R, 4, 3, domain=UNIT)
+    plan.matvec(torch.from_numpy(W.uniform_sigma(2000, seed=58).astype(np.float32)).cuda())
+    with pytest.raises(bb.BBFMMError, match="keep_coefficients"):
+        bb.bbfmm_get_coefficients(plan.handle, 0, 2, 1, 4)
+    plan.close()
+
+
+@pytest.mark.parametrize("depth", [5, 6])
+def test_repeated_calls_deep_tree(bb, oracle, depth):
+    """The upward pass's arrival counters reset themselves: the second and
+    third matvec of a plan equal the first bitwise (eager and graph replay),
+    and match the oracle at sampled targets."""
+    n = 200_000
+    pts = W.uniform_points(n, seed=59)
+    sig = W.uniform_sigma(n, nrhs=2, seed=60).astype(np.float32)
+    dev = torch.device("cuda:0")
+    plan = bb.Plan(torch.from_numpy(pts).to(dev), K_INV_R, 4, depth, svd_eps=1e-7, domain=UNIT, max_nrhs=2)
+    s = torch.from_numpy(np.ascontiguousarray(sig.T)).to(dev)
+    outs = [plan.matvec(s).clone() for _ in range(3)]
+    assert bb.bbfmm_status(plan.handle) == 0
+    plan.close()
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+    got = outs[0].cpu().numpy().T.astype(np.float64)
+    sample = np.random.default_rng(61).choice(n, 256, replace=False)
+    ref = oracle.bbfmm(pts, sig.astype(np.float64), K_INV_R, 4, depth, lo=W.UNIT_LO, side=W.UNIT_SIDE,
+                       sample=sample)
+    assert oracle.rel_err(got[sample], ref) <= 1e-5
 
 
 def test_config_uniform_4k_p4_d3(bb, oracle):
