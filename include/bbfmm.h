@@ -70,9 +70,10 @@ typedef struct {
     double lo[3];      /* lower corner of the cubical domain */
     double side;       /* side length of the domain (> 0) */
     int max_nrhs;      /* largest nrhs a matvec on this plan may use (default 1) */
-    int split_accumulate; /* BBFMM_PREC_TF32X3 only: 1 (default) accumulates the
-                             correction products hi*lo + lo*hi apart from hi*hi and
-                             adds them at the end; 0 uses one accumulator */
+    int split_accumulate; /* 3-pass tensor-core forms: 1 (default) issues each K
+                             chunk's correction products hi*lo + lo*hi before its
+                             hi*hi products, so only the hi*hi additions round at
+                             the scale of the result; 0 issues hi*hi first */
     int use_graph;     /* 1 (default): the first matvec with a given nrhs captures
                           the whole launch sequence into a CUDA graph, later ones
                           replay it; 0: launch the kernels one by one */

@@ -7,7 +7,8 @@
 // the class, D[128 x r] += A_t[128 x r] * B_t[r x r]^T, where A_t gathers the
 // source vectors M~ of the 128 targets (one TMA box of the parity-split M~
 // array: consecutive parent cells of one source octant; out-of-range cells
-// read as zero) and B_t = C^(t).  K is walked in 32-float (128-byte) chunks.
+// read as zero) and B_t = C^(t).  K is walked in chunks of 32 elements (a
+// 128-byte row) for TF32, of kChunk16 elements for FP16 / BF16.
 //
 // One persistent launch covers every level 2..D.  A work item is (level,
 // tile, group of offsets): the 189 offsets of a tile are split into G groups
@@ -20,9 +21,12 @@
 //   warp 1         MMA issuer: one lane issues tcgen05.mma kind::tf32, M = 128,
 //                  N = r rounded to 16, K = 8 per instruction
 //   warps 2..      epilogue: after every offset it drains the offset's partial
-//                  accumulator from TMEM (double buffered, so the MMAs of the
-//                  next offset overlap) into FP32 registers; at the end of an
-//                  item it scales and stores the sum
+//                  accumulator from TMEM into FP32 registers; at the end of an
+//                  item it scales and stores the sum.  As many partial
+//                  buffers as fit in the 512 TMEM columns (5 for r <= 96) let
+//                  the MMAs run several offsets ahead of the drains, so the
+//                  round trip commit -> drain -> release stays off the tensor
+//                  pipe's critical path
 //
 // Precision: kind::tf32 reads 10 explicit mantissa bits.  The 3-pass mode
 // splits each operand into hi = tf32(x) and lo = tf32(x - hi) and forms
@@ -31,8 +35,10 @@
 // x r/8 steps into one accumulator) lost ~1e-5 relative on the 1M-point
 // workload, so, as that scheme prescribes, a TMEM accumulator only ever holds
 // one offset and the sum over offsets is taken in FP32 registers with
-// round-to-nearest.  With SPLIT the correction products sit in their own TMEM
-// columns.
+// round-to-nearest.  Within an offset, with CF, each K chunk's correction
+// products (hi*lo, lo*hi: 2^-11 of hi*hi) are issued before its hi*hi
+// products, so they are summed while the accumulator is still small and
+// only the hi*hi additions truncate at the scale of the result.
 //
 // Every mbarrier wait is bounded (about 2^31 cycles): on expiry the kernel
 // sets the plan's status word, stops issuing work, waits (bounded) for its own
@@ -71,6 +77,23 @@ void split_tf32(const float *in, float *hi, float *lo, int64_t n)
     }
 }
 
+// K elements per pipeline stage for the 16-bit forms: 32 (64-byte rows,
+// 64-byte swizzle) or 64 (128-byte rows, 128-byte swizzle); TF32 always uses
+// 32 (128-byte rows)
+#ifndef BBFMM_TC_CHUNK16
+#define BBFMM_TC_CHUNK16 64
+#endif
+constexpr int kChunk16 = BBFMM_TC_CHUNK16;
+#ifndef BBFMM_TC_MAX_STAGES
+#define BBFMM_TC_MAX_STAGES 8
+#endif
+constexpr int kMaxStages = BBFMM_TC_MAX_STAGES; // pipeline stages (shared memory permitting)
+#ifndef BBFMM_TC_ACC_PER_BUF
+#define BBFMM_TC_ACC_PER_BUF 2
+#endif
+constexpr int kAccPerBuf = BBFMM_TC_ACC_PER_BUF; // accumulators per offset (1 or 2)
+static_assert(kChunk16 == 32 || kChunk16 == 64, "16-bit K chunk is 32 or 64 elements");
+
 // ---------------------------------------------------------------------------
 __constant__ int4 c_tab_tc[8][kOffsetsPerClass];
 
@@ -92,6 +115,8 @@ struct TcLaunch {
     int nlev, nitems, groups, per_group;
     int *status;
     int r, rp, nb, ncols, nrhs, R, nk, nstage; // R: right-hand-side stride of M~ / F~ rows
+    int nbuf, nacc, bcols, tcols; // TMEM partial buffers, accumulators per buffer, columns
+                                  // per accumulator, columns allocated
     uint32_t stage_bytes, a_bytes, b_bytes;
 };
 
@@ -125,11 +150,15 @@ __device__ __forceinline__ Item decode_item(const TcLaunch &P, int item)
 
 // FMT: operand format, 0 = TF32 (kind::tf32, 32 elements per 128-byte row,
 // K = 8 per MMA), 1 = FP16, 2 = BF16 (kind::f16, 64 elements per row, K = 16)
-template <int NPROD, bool SPLIT, int CH, int FMT>
+template <int NPROD, bool CF, int NACC, int CH, int FMT>
 __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_constant__ TcLaunch P)
 {
-    constexpr int CHUNK = FMT == 0 ? 32 : 64; // K elements per stage (one 128-byte row)
-    constexpr int KSTEP = FMT == 0 ? 8 : 16;  // K elements per MMA (32 bytes)
+    // K is walked in chunks of 32 elements per stage: one 128-byte swizzled
+    // row for TF32, one 64-byte swizzled row for the 16-bit forms (the smaller
+    // stage keeps more offsets in flight for the same shared memory)
+    constexpr int CHUNK = FMT == 0 ? 32 : kChunk16;
+    constexpr bool SW64 = FMT != 0 && kChunk16 == 32; // 64-byte rows
+    constexpr int KSTEP = FMT == 0 ? 8 : 16;         // K elements per MMA (32 bytes)
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -137,11 +166,12 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
     const int S = P.nstage;
     uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + (size_t)S * P.stage_bytes);
     const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * S;
-    const uint32_t pfull0 = empty0 + 8 * S, pempty0 = pfull0 + 16, done_bar = pempty0 + 16;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 5);
+    constexpr int kMaxBuf = 8;
+    const int NB = P.nbuf;
+    const uint32_t pfull0 = empty0 + 8 * S, pempty0 = pfull0 + 8 * kMaxBuf, done_bar = pempty0 + 8 * kMaxBuf;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 2 * kMaxBuf + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-    constexpr int APB = SPLIT ? 2 : 1; // accumulators per partial buffer
-    const uint32_t tcols = 2u * APB * (uint32_t)P.ncols;
+    const uint32_t tcols = (uint32_t)P.tcols;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -149,10 +179,10 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
-        mbar_init(pfull0, 1);
-        mbar_init(pfull0 + 8, 1);
-        mbar_init(pempty0, 4 * CH);
-        mbar_init(pempty0 + 8, 4 * CH);
+        for (int b = 0; b < NB; ++b) {
+            mbar_init(pfull0 + 8 * b, 1);
+            mbar_init(pempty0 + 8 * b, 4 * CH);
+        }
         mbar_init(done_bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -210,59 +240,89 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
             }
     } else if (warp == 1 && lane == 0) {
         // ------------------------------------------------------------ MMA issuer
+        // One thread issues every MMA of the CTA, so this loop is kept short:
+        // ring positions are counters (no division), the operand descriptors
+        // of a stage are the stage-0 descriptors plus a constant, the K steps
+        // of a chunk are unrolled.
         const uint32_t idesc = FMT == 0 ? idesc_tf32(128, P.nb) : idesc_f16(128, P.nb, FMT == 2 ? 1 : 0);
-        int it = 0, go = 0; // stage counter, offset counter (partial buffers)
+        const uint32_t b_off = NPROD == 3 ? 2 * P.a_bytes : P.a_bytes;
+        const uint64_t d0 = SW64 ? sw64_desc(base) : sw128_desc(base);
+        const uint32_t d_al = P.a_bytes >> 4, d_bh = b_off >> 4, d_bl = (b_off + P.b_bytes) >> 4;
+        const uint32_t d_st = P.stage_bytes >> 4;
+        constexpr int KMAX = CHUNK / KSTEP;
+        const int ktail = (P.r - CHUNK * (P.nk - 1) + KSTEP - 1) / KSTEP; // K steps of the last chunk
+        int s = 0, sph = 0, pb = 0, pph = 0; // stage ring and partial-buffer ring (position, phase)
         bool ok = true;
         for (int item = blockIdx.x; item < P.nitems && ok && !*abort_flag; item += gridDim.x) {
             const Item w = decode_item(P, item);
-            for (int e = w.e0; e < w.e1 && ok; ++e, ++go) {
-                const int pb = go & 1, use = go >> 1;
-                if (!mbar_wait(pempty0 + 8 * pb, (use & 1) ^ 1, abort_flag)) {
+            for (int e = w.e0; e < w.e1 && ok; ++e) {
+                if (!mbar_wait(pempty0 + 8 * pb, pph ^ 1, abort_flag)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d = tmem_base + (uint32_t)(pb * APB * P.ncols);
-                const uint32_t dc = SPLIT ? d + (uint32_t)P.ncols : d;
-                uint32_t acc = 0, accc = SPLIT ? 0u : 1u;
-                for (int kc = 0; kc < P.nk; ++kc, ++it) {
-                    const int s = it % S, round = it / S;
-                    if (!mbar_wait(full0 + 8 * s, round & 1, abort_flag)) {
+                // NACC = 2: hi*hi into the first accumulator, the corrections
+                // into the second; NACC = 1: one accumulator, corrections of
+                // each chunk first (CF) or after its hi*hi
+                const uint32_t dh = tmem_base + (uint32_t)(pb * NACC * P.bcols);
+                const uint32_t dc = NACC == 2 ? dh + (uint32_t)P.bcols : dh;
+                uint32_t acc_h = 0, acc_c = 0;
+                for (int kc = 0; kc < P.nk; ++kc) {
+                    if (!mbar_wait(full0 + 8 * s, sph, abort_flag)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t sa = base + (uint32_t)s * P.stage_bytes;
-                    const uint64_t a_hi = sw128_desc(sa);
-                    const uint64_t a_lo = sw128_desc(sa + P.a_bytes);
-                    const uint32_t b_off = NPROD == 3 ? 2 * P.a_bytes : P.a_bytes;
-                    const uint64_t b_hi = sw128_desc(sa + b_off);
-                    const uint64_t b_lo = sw128_desc(sa + b_off + P.b_bytes);
-                    const int rem = P.r - CHUNK * kc;
-                    const int ksteps = rem >= CHUNK ? 4 : (rem + KSTEP - 1) / KSTEP;
-                    for (int k = 0; k < ksteps; ++k) {
-                        const uint64_t dk = (uint64_t)(2 * k); // 32 bytes >> 4
-                        if (FMT == 0) {
-                            mma_tf32(d, a_hi + dk, b_hi + dk, idesc, acc);
-                            if (NPROD == 3) {
-                                mma_tf32(dc, a_hi + dk, b_lo + dk, idesc, accc);
-                                mma_tf32(dc, a_lo + dk, b_hi + dk, idesc, 1);
+                    const uint64_t ah = d0 + (uint64_t)(s * d_st);
+                    const uint64_t al = ah + d_al, bh = ah + d_bh, bl = ah + d_bl;
+                    const int ks = kc + 1 < P.nk ? KMAX : ktail;
+                    auto issue = [&](uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+                        if (FMT == 0)
+                            mma_tf32(d, a, b, idesc, acc);
+                        else
+                            mma_f16(d, a, b, idesc, acc);
+                    };
+                    if (NPROD == 3 && (NACC == 2 || CF)) {
+#pragma unroll
+                        for (int k = 0; k < KMAX; ++k)
+                            if (k < ks) {
+                                const uint64_t dk = (uint64_t)(2 * k); // 32 bytes >> 4
+                                issue(dc, ah + dk, bl + dk, acc_c);
+                                issue(dc, al + dk, bh + dk, 1u);
+                                acc_c = 1u;
+                                if (NACC == 1)
+                                    acc_h = 1u;
                             }
-                        } else {
-                            mma_f16(d, a_hi + dk, b_hi + dk, idesc, acc);
-                            if (NPROD == 3) {
-                                mma_f16(dc, a_hi + dk, b_lo + dk, idesc, accc);
-                                mma_f16(dc, a_lo + dk, b_hi + dk, idesc, 1);
-                            }
+                    }
+#pragma unroll
+                    for (int k = 0; k < KMAX; ++k)
+                        if (k < ks) {
+                            const uint64_t dk = (uint64_t)(2 * k);
+                            issue(dh, ah + dk, bh + dk, acc_h);
+                            acc_h = 1u;
                         }
-                        acc = 1;
-                        accc = 1;
+                    if (NPROD == 3 && NACC == 1 && !CF) {
+#pragma unroll
+                        for (int k = 0; k < KMAX; ++k)
+                            if (k < ks) {
+                                const uint64_t dk = (uint64_t)(2 * k);
+                                issue(dh, ah + dk, bl + dk, 1u);
+                                issue(dh, al + dk, bh + dk, 1u);
+                            }
                     }
                     mma_commit(empty0 + 8 * s); // frees the stage once these MMAs have read it
+                    if (++s == S) {
+                        s = 0;
+                        sph ^= 1;
+                    }
                 }
                 if (!ok)
                     break;
-                mma_commit(pfull0 + 8 * pb); // the offset's partial sum is complete
+                mma_commit(pfull0 + 8 * pb); // the offset's partial sums are complete
+                if (++pb == NB) {
+                    pb = 0;
+                    pph ^= 1;
+                }
             }
         }
         // all MMAs issued by this thread have completed before TMEM is freed
@@ -278,48 +338,56 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
         const int row = 32 * q + lane;
         const int bx = row & 7, by = (row >> 3) & 3, bz = row >> 5;
         const uint32_t tlane = tmem_base + ((uint32_t)(32 * q) << 16);
-        int go = 0;
+        int pb = 0, pph = 0; // partial-buffer ring (position, phase)
         bool ok = true;
+        // add the columns [128 half, 128 half + nb) of TMEM buffer tb into acc,
+        // 32 (or, for the last piece, 16) columns per load
+        auto drain = [&](uint32_t tb, float *acc) {
+#pragma unroll
+            for (int c32 = 0; c32 < 4; ++c32) {
+                const int col = 128 * half + 32 * c32;
+                if (col + 32 <= P.nb) {
+                    float v[32];
+                    tmem_ld32(tb + (uint32_t)col, v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        acc[32 * c32 + j] += v[j];
+                } else if (col < P.nb) {
+                    float v[16];
+                    tmem_ld16(tb + (uint32_t)col, v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        acc[32 * c32 + j] += v[j];
+                }
+            }
+        };
         for (int item = blockIdx.x; item < P.nitems && ok; item += gridDim.x) {
             const Item w = decode_item(P, item);
             float acc[128];
 #pragma unroll
             for (int j = 0; j < 128; ++j)
                 acc[j] = 0.0f;
-            for (int e = w.e0; e < w.e1; ++e, ++go) {
-                const int pb = go & 1, use = go >> 1;
+            for (int e = w.e0; e < w.e1; ++e) {
                 int got = 1;
                 if (lane == 0)
-                    got = mbar_wait(pfull0 + 8 * pb, use & 1, abort_flag) ? 1 : 0;
+                    got = mbar_wait(pfull0 + 8 * pb, pph, abort_flag) ? 1 : 0;
                 got = __shfl_sync(0xffffffffu, got, 0); // keep the warp converged for tcgen05.ld
                 if (!got) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t tb = tlane + (uint32_t)(pb * APB * P.ncols);
-#pragma unroll
-                for (int c16 = 0; c16 < 8; ++c16) {
-                    const int col = 128 * half + 16 * c16;
-                    if (col < P.nb) {
-                        float v[16];
-                        tmem_ld16(tb + (uint32_t)col, v);
-                        if (SPLIT) {
-                            float u[16];
-                            tmem_ld16(tb + (uint32_t)(P.ncols + col), u);
-#pragma unroll
-                            for (int j = 0; j < 16; ++j)
-                                v[j] += u[j];
-                        }
-#pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            acc[16 * c16 + j] += v[j];
-                    }
-                }
+                drain(tlane + (uint32_t)(pb * NACC * P.bcols), acc);
+                if (NACC == 2)
+                    drain(tlane + (uint32_t)((pb * NACC + 1) * P.bcols), acc);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0)
                     mbar_arrive(pempty0 + 8 * pb);
+                if (++pb == NB) {
+                    pb = 0;
+                    pph ^= 1;
+                }
             }
             if (!ok)
                 break;
@@ -391,35 +459,41 @@ static cudaError_t tc_init()
 
 
 // M~ (parity split, padded in Z): dims (rp, R, H, H, 8 (H + 2)); box (one
-// 128-byte row of K, 1, 8, 4, 4); elem = 4 (FP32 / TF32) or 2 (FP16 / BF16)
+// K chunk, 1, 8, 4, 4); elem = 4 (FP32 / TF32: 32 per 128-byte row, 128-byte
+// swizzle) or 2 (FP16 / BF16: kChunk16 per row, 64- or 128-byte swizzle)
 static cudaError_t encode_a(CUtensorMap *tm, const void *ptr, int H, int R, int rp, int fmt)
 {
     const cuuint64_t es_b = fmt == 0 ? 4 : 2;
     cuuint64_t dims[5] = {(cuuint64_t)rp, (cuuint64_t)R, (cuuint64_t)H, (cuuint64_t)H, (cuuint64_t)8 * (H + 2)};
     cuuint64_t strides[4] = {(cuuint64_t)rp * es_b, (cuuint64_t)R * rp * es_b, (cuuint64_t)H * R * rp * es_b,
                              (cuuint64_t)H * H * R * rp * es_b};
-    cuuint32_t box[5] = {(cuuint32_t)(128 / es_b), 1, 8, 4, 4};
+    const bool sw64 = fmt != 0 && kChunk16 == 32;
+    cuuint32_t box[5] = {(cuuint32_t)(fmt == 0 ? 32 : kChunk16), 1, 8, 4, 4};
     cuuint32_t es[5] = {1, 1, 1, 1, 1};
     CUtensorMapDataType dt = fmt == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                       : (fmt == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
     CUresult r = g_encode(tm, dt, 5, (void *)ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          sw64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// C (operators): dims (rp, rows64, 316); box (one 128-byte row of K, nb, 1)
+// C (operators): dims (rp, rows64, 316); box (one K chunk, nb, 1), rows and
+// swizzle as for M~
 static cudaError_t encode_b(CUtensorMap *tm, const void *ptr, int rp, int rows64, int nb, int fmt)
 {
     const cuuint64_t es_b = fmt == 0 ? 4 : 2;
     cuuint64_t dims[3] = {(cuuint64_t)rp, (cuuint64_t)rows64, (cuuint64_t)kNumOffsets};
     cuuint64_t strides[2] = {(cuuint64_t)rp * es_b, (cuuint64_t)rows64 * rp * es_b};
-    cuuint32_t box[3] = {(cuuint32_t)(128 / es_b), (cuuint32_t)nb, 1};
+    const bool sw64 = fmt != 0 && kChunk16 == 32;
+    cuuint32_t box[3] = {(cuuint32_t)(fmt == 0 ? 32 : kChunk16), (cuuint32_t)nb, 1};
     cuuint32_t es[3] = {1, 1, 1};
     CUtensorMapDataType dt = fmt == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                       : (fmt == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
     CUresult r = g_encode(tm, dt, 3, (void *)ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          sw64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -454,23 +528,25 @@ int m2l_groups_for(int D, int nrhs, int precision)
     return best;
 }
 
-template <int NPROD, bool SPLIT, int CH, int FMT>
+template <int NPROD, bool CF, int NACC, int CH, int FMT>
 static cudaError_t launch_tc(const TcLaunch &P, int grid, size_t smem, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_m2l_tc<NPROD, SPLIT, CH, FMT>,
+    cudaError_t e = cudaFuncSetAttribute(k_m2l_tc<NPROD, CF, NACC, CH, FMT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    k_m2l_tc<NPROD, SPLIT, CH, FMT><<<grid, 64 + 128 * CH, smem, s>>>(P);
+    k_m2l_tc<NPROD, CF, NACC, CH, FMT><<<grid, 64 + 128 * CH, smem, s>>>(P);
     return cudaGetLastError();
 }
 
 template <int FMT>
-static cudaError_t launch_three(const TcLaunch &L, bool split, int CH, int grid, size_t smem, cudaStream_t s)
+static cudaError_t launch_three(const TcLaunch &L, bool cf, int CH, int grid, size_t smem, cudaStream_t s)
 {
-    if (split)
-        return launch_tc<3, true, 1, FMT>(L, grid, smem, s);
-    return CH == 1 ? launch_tc<3, false, 1, FMT>(L, grid, smem, s) : launch_tc<3, false, 2, FMT>(L, grid, smem, s);
+    if (L.nacc == 2) // two accumulators fit only when nb <= 128, so CH = 1
+        return launch_tc<3, true, 2, 1, FMT>(L, grid, smem, s);
+    if (CH == 1)
+        return cf ? launch_tc<3, true, 1, 1, FMT>(L, grid, smem, s) : launch_tc<3, false, 1, 1, FMT>(L, grid, smem, s);
+    return cf ? launch_tc<3, true, 1, 2, FMT>(L, grid, smem, s) : launch_tc<3, false, 1, 2, FMT>(L, grid, smem, s);
 }
 
 cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
@@ -496,7 +572,7 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
     // operand format: 0 = TF32 (1 or 3 passes), 1 = FP16 x3, 2 = BF16 x3
     const int fmt = P->precision == BBFMM_PREC_FP16X3 ? 1 : P->precision == BBFMM_PREC_BF16X3 ? 2 : 0;
     const bool three = P->precision != BBFMM_PREC_TF32;
-    const int elem = fmt == 0 ? 4 : 2, chunk = 128 / elem;
+    const int elem = fmt == 0 ? 4 : 2, chunk = fmt == 0 ? 32 : kChunk16, rowb = chunk * elem;
     const int nb = (O.r + 15) / 16 * 16;
     if (nb > 256 || O.rp % 16 != 0 || P->D - 1 > kMaxTcLevels)
         return cudaErrorInvalidValue;
@@ -509,22 +585,33 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
     L.rp = O.rp;
     L.nb = nb;
     L.ncols = nb <= 32 ? 32 : nb <= 64 ? 64 : nb <= 128 ? 128 : 256;
+    // accumulators of nb columns rounded to 32.  Three-product forms keep
+    // hi*hi and the corrections in two accumulators per offset when two
+    // double-buffered pairs fit in the 512 TMEM columns (nb <= 128), else one
+    // accumulator with each chunk's corrections issued first.  As many partial
+    // buffers as fit (at most 8); the allocation is a power of two.
+    L.bcols = (nb + 31) / 32 * 32;
+    L.nacc = three && P->split_acc && kAccPerBuf == 2 && 4 * L.bcols <= 512 ? 2 : 1;
+    L.nbuf = 512 / (L.nacc * L.bcols) > 8 ? 8 : 512 / (L.nacc * L.bcols);
+    L.tcols = 32;
+    while (L.tcols < L.nbuf * L.nacc * L.bcols)
+        L.tcols *= 2;
     L.nrhs = nrhs;
     L.R = P->max_nrhs;
     L.nk = (O.r + chunk - 1) / chunk;
     L.groups = P->m2l_groups;
     L.per_group = (kOffsetsPerClass + L.groups - 1) / L.groups;
-    L.a_bytes = 128 * 128;
-    L.b_bytes = (uint32_t)nb * 128;
+    L.a_bytes = 128 * rowb;
+    L.b_bytes = (uint32_t)nb * rowb;
     L.stage_bytes = (three ? 2 : 1) * (L.a_bytes + L.b_bytes);
     L.ascale = P->a16_scale;
     const size_t budget = 220 * 1024;
-    int nstage = (int)((budget - 1024 - 256) / L.stage_bytes);
-    nstage = nstage > 8 ? 8 : nstage;
+    int nstage = (int)((budget - 1024 - 512) / L.stage_bytes);
+    nstage = nstage > kMaxStages ? kMaxStages : nstage;
     if (nstage < 2)
         return cudaErrorInvalidValue;
     L.nstage = nstage;
-    const size_t smem = 1024 + (size_t)nstage * L.stage_bytes + 256;
+    const size_t smem = 1024 + (size_t)nstage * L.stage_bytes + 512; // + barriers and TMEM slot
     // levels, finest first
     int items = 0;
     L.nlev = 0;
@@ -578,10 +665,9 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
     }
     const int grid = items < g_num_sms ? items : g_num_sms;
     const int CH = nb > 128 ? 2 : 1;
-    // two accumulators per partial buffer need 4 x ncols <= 512 TMEM columns
-    const bool split = three && P->split_acc && L.ncols <= 128;
+    const bool split = three && P->split_acc; // corrections first within each K chunk
     if (!three)
-        return CH == 1 ? launch_tc<1, false, 1, 0>(L, grid, smem, s) : launch_tc<1, false, 2, 0>(L, grid, smem, s);
+        return CH == 1 ? launch_tc<1, false, 1, 1, 0>(L, grid, smem, s) : launch_tc<1, false, 1, 2, 0>(L, grid, smem, s);
     if (fmt == 0)
         return launch_three<0>(L, split, CH, grid, smem, s);
     if (fmt == 1)

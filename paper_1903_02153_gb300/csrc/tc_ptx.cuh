@@ -40,6 +40,8 @@ constexpr long long kWaitCycles = 1LL << 31;
 // thread has already given up
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag)
 {
+    if (mbar_test(bar, parity))
+        return true;
     long long t0 = clock64();
     while (!mbar_test(bar, parity)) {
         if (*abort_flag)
@@ -126,6 +128,27 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
         v[i] = __uint_as_float(r[i]);
 }
 
+// 32 lanes x 32 consecutive 32-bit columns -> 32 registers, the wait for the
+// load inside the same statement (the registers are read only after it)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
+{
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                 "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+                 "[%32];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                   "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+                   "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+                   "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+        v[i] = __uint_as_float(r[i]);
+}
+
 // shared-memory matrix descriptor: K-major operand in the canonical 128-byte
 // swizzled layout (rows of 128 bytes, 8-row groups 1024 bytes apart)
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
@@ -136,6 +159,18 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
     d |= (uint64_t)(1024u >> 4) << 32;       // stride-dimension byte offset: 8 rows x 128 B
     d |= (uint64_t)1u << 46;                 // descriptor version for tcgen05
     d |= (uint64_t)2u << 61;                 // 128-byte swizzle
+    return d;
+}
+
+// the same for 64-byte rows in the 64-byte swizzle (16-bit operands, 32 per row)
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3fffu); // start address >> 4
+    d |= (uint64_t)1u << 16;                 // leading-dimension byte offset (unused here) = 16 B
+    d |= (uint64_t)(512u >> 4) << 32;        // stride-dimension byte offset: 8 rows x 64 B
+    d |= (uint64_t)1u << 46;                 // descriptor version for tcgen05
+    d |= (uint64_t)4u << 61;                 // 64-byte swizzle
     return d;
 }
 

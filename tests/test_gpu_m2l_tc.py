@@ -1,10 +1,12 @@
-"""The tensor-core M2L (tcgen05, TF32 and split 3xTF32) against the FP32
-CUDA-core M2L and the FP64 oracle, from the smallest tree up.
+"""The tensor-core M2L (tcgen05: TF32, split 3xTF32, FP16x3, BF16x3) against
+the FP64 oracle and the FP32 CUDA-core M2L, from the smallest tree up.
 
-3xTF32 keeps ~21 mantissa bits per product, so its result must sit within
-2e-6 (relative 2-norm) of the FP32 path, and within the FP32 gates of the
-oracle (1e-5, and 1.1 x the oracle's error against the direct sum).  One-pass
-TF32 (10 bits) is reported with a loose bound only."""
+The split forms keep ~21 mantissa bits per product and sum the offsets in FP32
+registers, so against the oracle they must be at least as close as the FP32
+CUDA-core form (whose own FP32 accumulation over 189 offsets x r terms costs
+~2e-6 at depth 5), and within the FP32 gates of the oracle (1e-5, and 1.1 x
+the oracle's error against the direct sum).  One-pass TF32 (10 bits) is
+reported with a loose bound only."""
 import numpy as np
 import pytest
 
@@ -46,12 +48,17 @@ def rel(a, b):
 
 @pytest.mark.parametrize("prec", ["tf32x3", "fp16x3"])
 @pytest.mark.parametrize("n,p,depth", [(2000, 4, 2), (6000, 4, 3), (20000, 5, 4), (60000, 5, 5)])
-def test_split3_matches_fp32(bb, n, p, depth, prec):
+def test_split3_at_least_as_close_as_fp32(bb, oracle, n, p, depth, prec):
     pts = W.uniform_points(n, seed=71)
     sig = W.uniform_sigma(n, seed=72).astype(np.float32)
     a = run(bb, pts, sig, 1, p, depth, "fp32")
     b = run(bb, pts, sig, 1, p, depth, prec)
-    assert rel(b, a) < 2e-6
+    samp = np.random.default_rng(73).choice(n, min(n, 3000), replace=False)
+    ref = oracle.bbfmm(pts, sig.astype(np.float64), 1, p, depth, lo=W.UNIT_LO, side=W.UNIT_SIDE, sample=samp)
+    e_fp32, e_split = oracle.rel_err(a[samp], ref), oracle.rel_err(b[samp], ref)
+    assert e_split <= 1.1 * e_fp32 + 2e-7, (e_split, e_fp32)
+    assert e_split <= 1e-5
+    assert rel(b, a) < 4e-6   # the two forms differ by about the FP32 form's own error
 
 
 def test_bf16x3_error_is_reported(bb, oracle):
@@ -85,7 +92,8 @@ def test_tf32x3_vs_oracle(bb, oracle, kid, ell, kind, p, depth, eps, tol):
     ~1.0e-5: the FP32 rounding of the leaf-local coordinates in the near field
     alone accounts for 1.02e-5 on this point set (1/r^2 amplifies the
     coordinate error of very close pairs; emulated on the CPU), hence 2e-5
-    there.  The tensor-core form must track the FP32 form to 2e-6."""
+    there.  The tensor-core forms track the FP32 form to within that form's
+    own FP32 error."""
     n = 20000
     pts = W.make_points(kind, n, seed=75)
     sig = W.uniform_sigma(n, seed=76).astype(np.float32)
@@ -96,9 +104,9 @@ def test_tf32x3_vs_oracle(bb, oracle, kid, ell, kind, p, depth, eps, tol):
     print("kernel %d: tf32x3 vs oracle %.2e, fp32 vs oracle %.2e" % (kid, oracle.rel_err(got, ref),
                                                                       oracle.rel_err(plain, ref)))
     assert oracle.rel_err(got, ref) <= tol
-    assert rel(got, plain) < 2e-6
+    assert rel(got, plain) < 4e-6
     assert oracle.rel_err(half, ref) <= tol
-    assert rel(half, plain) < 2e-6
+    assert rel(half, plain) < 4e-6
 
 
 @pytest.mark.parametrize("prec", ["tf32x3", "fp16x3"])
@@ -151,6 +159,6 @@ def test_split3_full_size_uniform_1M(bb, oracle, depth, prec):
     e_or = oracle.rel_err(ref, direct)
     print("depth %d %s: vs fp32 %.2e, vs oracle %.2e, err %.2e (oracle %.2e)"
           % (depth, prec, rel(got, plain), oracle.rel_err(got[idx], ref), oracle.rel_err(got[idx], direct), e_or))
-    assert rel(got, plain) < 2e-6
+    assert rel(got, plain) < 4e-6
     assert oracle.rel_err(got[idx], ref) <= 1e-5
     assert oracle.rel_err(got[idx], direct) <= 1.1 * e_or
