@@ -298,7 +298,7 @@ cudaError_t launch_m2l_fp32(const float *Mt, const float *C, float *Ft, int l, i
                             int nrhs, int R, float scale, cudaStream_t s);
 // m2l_tc.cu: every level of the far field in one go (FP32 or tensor cores)
 cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s);
-int m2l_groups_for(int D, int nrhs, int precision);
+int m2l_groups_for(int D, int nrhs, int precision, int r);
 // p2p.cu
 cudaError_t launch_p2p(const float4 *pts, const float *sig, const int *leaf_off, const int4 *chunks,
                        int nchunks, int64_t n, int D, int kernel, double ell, double h, int nrhs,

@@ -397,7 +397,7 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, cudaStream_t s)
     // per-level coefficient buffers
     const int R = P->max_nrhs, p3 = P->p3;
     const int rp = P->ops->rp;
-    P->m2l_groups = m2l_groups_for(D, R, P->precision);
+    P->m2l_groups = m2l_groups_for(D, R, P->precision, P->ops->r);
     for (int l = 2; l <= D; ++l) {
         Level &L = P->lev[l];
         int64_t nb = 1LL << (3 * l), H = 1LL << (l - 1);
