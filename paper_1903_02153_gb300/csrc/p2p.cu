@@ -17,6 +17,8 @@
 // Threads are (target pair, slice): slice s walks sources s, s + S, ...; the
 // slices of a target are added in a fixed order at the end (deterministic).
 // K at r = 0 follows the library's convention: 0 for 1/r and 1/r^2.
+#include <type_traits>
+
 #include "bbfmm_internal.h"
 
 namespace bbfmm {
@@ -46,14 +48,22 @@ __device__ __forceinline__ float ex2_approx(float x)
 }
 
 // each kernel maps the squared distance r2 (cell units) and the offsets to
-// K; the packed form applies it to both lanes
+// K; the packed form applies it to both lanes.  one() follows the r = 0
+// convention (0 for the singular kernels) and serves the target's own leaf,
+// the only place where a point meets itself or an exact duplicate; far()
+// serves the other 26 leaves, where r2 = 0 can only come from FP32 rounding
+// of two distinct points closer than ~1e-7 cells: there the singular kernels
+// are clamped at 2^24 / h (finite) instead of tested.
+constexpr float kClampInvR = 16777216.0f, kClampInvR2 = 281474976710656.0f;
 struct KInvR {
     float a; // unused
     __device__ float one(float r2, float, float, float) const { return r2 > 0.0f ? rsqrt_approx(r2) : 0.0f; }
+    __device__ float far(float r2, float, float, float) const { return fminf(rsqrt_approx(r2), kClampInvR); }
 };
 struct KInvR2 {
     float a;
     __device__ float one(float r2, float, float, float) const { return r2 > 0.0f ? rcp_approx(r2) : 0.0f; }
+    __device__ float far(float r2, float, float, float) const { return fminf(rcp_approx(r2), kClampInvR2); }
 };
 struct KExp { // exp(-h r / ell) = 2^(-a r), a = h / (ell ln 2)
     float a;
@@ -61,10 +71,12 @@ struct KExp { // exp(-h r / ell) = 2^(-a r), a = h / (ell ln 2)
     {
         return ex2_approx(-a * (r2 > 0.0f ? r2 * rsqrt_approx(r2) : 0.0f));
     }
+    __device__ float far(float r2, float dx, float dy, float dz) const { return one(r2, dx, dy, dz); }
 };
 struct KGauss { // exp(-(h r / ell)^2) = 2^(-a r^2), a = h^2 / (ell^2 ln 2)
     float a;
     __device__ float one(float r2, float, float, float) const { return ex2_approx(-a * r2); }
+    __device__ float far(float r2, float dx, float dy, float dz) const { return one(r2, dx, dy, dz); }
 };
 struct KPoly { // q(d) with d = h * (x - y) in physical units
     float a;   // h
@@ -73,16 +85,20 @@ struct KPoly { // q(d) with d = h * (x - y) in physical units
         float d0 = a * dx, d1 = a * dy, d2 = a * dz;
         return 1.0f + d0 - 2.0f * d1 * d2 + 3.0f * d0 * d0 * d1;
     }
+    __device__ float far(float r2, float dx, float dy, float dz) const { return one(r2, dx, dy, dz); }
 };
 struct KConst {
     float a;
     __device__ float one(float, float, float, float) const { return 1.0f; }
+    __device__ float far(float, float, float, float) const { return 1.0f; }
 };
 
-template <class Kern>
+template <bool OWN, class Kern>
 __device__ __forceinline__ float2 kern2(const Kern &k, float2 r2, float2 dx, float2 dy, float2 dz)
 {
-    return make_float2(k.one(r2.x, dx.x, dy.x, dz.x), k.one(r2.y, dx.y, dy.y, dz.y));
+    if (OWN)
+        return make_float2(k.one(r2.x, dx.x, dy.x, dz.x), k.one(r2.y, dx.y, dy.y, dz.y));
+    return make_float2(k.far(r2.x, dx.x, dy.x, dz.x), k.far(r2.y, dx.y, dy.y, dz.y));
 }
 
 template <class Kern>
@@ -107,11 +123,13 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
     demorton3((uint32_t)ch.x, ax, ay, az);
     const int nside = 1 << D;
 
-    // neighbour leaves: start, count (prefix) and cell offset
+    // neighbour leaves: start, count (prefix) and cell offset; the target's
+    // own leaf comes first, so its sources are staged ahead of the others
     if (tid < 32) {
         int cnt = 0, start = 0;
         if (tid < 27) {
-            const int dx = tid % 3 - 1, dy = (tid / 3) % 3 - 1, dz = tid / 9 - 1;
+            const int nid = tid == 0 ? 13 : (tid <= 13 ? tid - 1 : tid);
+            const int dx = nid % 3 - 1, dy = (nid / 3) % 3 - 1, dz = nid / 9 - 1;
             const int bx = ax + dx, by = ay + dy, bz = az + dz;
             if (bx >= 0 && by >= 0 && bz >= 0 && bx < nside && by < nside && bz < nside) {
                 const uint32_t nm = morton3((uint32_t)bx, (uint32_t)by, (uint32_t)bz);
@@ -131,7 +149,7 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
             nb_pre[tid] = incl - cnt; // exclusive prefix; nb_pre[27] = total
     }
     __syncthreads();
-    const int ns = nb_pre[27];
+    const int ns = nb_pre[27], nown = nb_pre[1]; // all sources; those of the own leaf
     // the pair's two targets; a missing second target duplicates the first
     const int ia = active ? t : 0, ib = active && t + np < nt ? t + np : ia;
     const float4 xa = pts[ch.y + ia], xb = pts[ch.y + ib];
@@ -142,13 +160,11 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
         float2 acc = make_float2(0.0f, 0.0f), acc2 = make_float2(0.0f, 0.0f);
         for (int base = 0; base < ns; base += kStageSrc) {
             const int cnt = min(kStageSrc, ns - base);
+            int k = 0; // neighbour holding source gg: it only moves forward as gg grows
             for (int g = tid; g < cnt; g += kP2PThreads) {
                 const int gg = base + g;
-                int k = 0; // neighbour holding source gg: largest k with nb_pre[k] <= gg
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1)
-                    if (k + step < 27 && nb_pre[k + step] <= gg)
-                        k += step;
+                while (nb_pre[k + 1] <= gg)
+                    ++k;
                 const int src = nb_start[k] + (gg - nb_pre[k]);
                 const float4 u = pts[src];
                 const float4 d = nb_delta[k];
@@ -162,7 +178,7 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
             if (active) {
                 // two sources per iteration into two accumulators (shorter
                 // dependency chains); the accumulators are added in a fixed order
-                auto pair = [&](int j, float2 &a) {
+                auto pair = [&](auto own, int j, float2 &a) {
                     const float4 qa = stage_xy[j];
                     const float4 qb = stage_zs[j];
                     const float2 dx = __fadd2_rn(X, make_float2(qa.x, qa.y));
@@ -171,16 +187,20 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
                     float2 r2 = __fmul2_rn(dx, dx);
                     r2 = __ffma2_rn(dy, dy, r2);
                     r2 = __ffma2_rn(dz, dz, r2);
-                    a = __ffma2_rn(kern2(kern, r2, dx, dy, dz), make_float2(qb.z, qb.w), a);
+                    a = __ffma2_rn(kern2<decltype(own)::value>(kern, r2, dx, dy, dz), make_float2(qb.z, qb.w), a);
                 };
+                // the own leaf's sources (staged first) with the r = 0 test
+                const int cown = min(cnt, max(0, nown - base));
                 int j = slice;
+                for (; j < cown; j += S)
+                    pair(std::true_type{}, j, acc);
 #pragma unroll 2
                 for (; j + S < cnt; j += 2 * S) {
-                    pair(j, acc);
-                    pair(j + S, acc2);
+                    pair(std::false_type{}, j, acc);
+                    pair(std::false_type{}, j + S, acc2);
                 }
                 if (j < cnt)
-                    pair(j, acc);
+                    pair(std::false_type{}, j, acc);
             }
             __syncthreads();
         }

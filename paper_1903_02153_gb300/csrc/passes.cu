@@ -30,6 +30,11 @@ namespace bbfmm {
 namespace {
 
 constexpr int kThreads = 256;
+// the wide upward pass (a block per box of level D-2) pays off once its
+// 8^(D-2) blocks fill the GPU several times over; below that the narrow one
+// (a block per box of level D-1) keeps more blocks in flight
+constexpr int kWideMaxP = 7;     // largest p whose 64 leaf sets fit in shared memory
+constexpr int kWideMinDepth = 6; // 4096 blocks
 
 __device__ __forceinline__ float tf32_round(float x)
 {
@@ -68,7 +73,9 @@ template <int P> struct Smem {
 // form: three 1D passes with the child-to-parent matrices S), scratch Y, Z of
 // [P3][8]; result in out[P3].  Child o has (x, y, z) parity (o & 1, (o >> 1)
 // & 1, o >> 2), its position in Morton order.
-template <int P>
+// (XS: row stride of X, e.g. 64 when the 8 children are 8 columns of a
+// [P3][64] array; OS: stride of out)
+template <int P, int XS = 8, int OS = 1>
 __device__ void m2m8(const InterpTables &T, const float *X, float *Y, float *Z, float *out)
 {
     constexpr int P3 = P * P * P;
@@ -78,7 +85,7 @@ __device__ void m2m8(const InterpTables &T, const float *X, float *Y, float *Z, 
         float acc = 0.0f;
 #pragma unroll
         for (int j1 = 0; j1 < P; ++j1)
-            acc += T.S[o & 1][i1][j1] * X[(j1 + P * rest) * 8 + o];
+            acc += T.S[o & 1][i1][j1] * X[(j1 + P * rest) * XS + o];
         Y[q] = acc;
     }
     __syncthreads();
@@ -99,14 +106,15 @@ __device__ void m2m8(const InterpTables &T, const float *X, float *Y, float *Z, 
 #pragma unroll
             for (int j3 = 0; j3 < P; ++j3)
                 acc += T.S[o >> 2][i3][j3] * Z[(i12 + P * P * j3) * 8 + o];
-        out[r] = acc;
+        out[r * OS] = acc;
     }
     __syncthreads();
 }
 
 // L2L of one parent F (P3) into its 8 children ([P3][8], written), the
 // transpose of m2m8; scratch Y, Z [P3][8].
-template <int P>
+// (FS: stride of F; OS: row stride of out, 64 for 8 columns of [P3][64])
+template <int P, int FS = 1, int OS = 8>
 __device__ void l2l8(const InterpTables &T, const float *F, float *Y, float *Z, float *out)
 {
     constexpr int P3 = P * P * P;
@@ -116,7 +124,7 @@ __device__ void l2l8(const InterpTables &T, const float *F, float *Y, float *Z, 
         float acc = 0.0f;
 #pragma unroll
         for (int j3 = 0; j3 < P; ++j3)
-            acc += T.S[o >> 2][j3][i3] * F[j12 + P * P * j3];
+            acc += T.S[o >> 2][j3][i3] * F[(j12 + P * P * j3) * FS];
         Y[q] = acc;
     }
     __syncthreads();
@@ -135,7 +143,7 @@ __device__ void l2l8(const InterpTables &T, const float *F, float *Y, float *Z, 
 #pragma unroll
         for (int j1 = 0; j1 < P; ++j1)
             acc += T.S[o & 1][j1][i1] * Z[(j1 + P * rest) * 8 + o];
-        out[q] = acc;
+        out[r * OS + o] = acc;
     }
     __syncthreads();
 }
@@ -539,9 +547,222 @@ __global__ void __launch_bounds__(kThreads) k_downward(const __grid_constant__ P
     }
 }
 
+// ---------------------------------------------------------------------------
+// Wide upward pass: one block per (box of level D-2, right-hand side), i.e.
+// 64 leaves and their 8 parents; used for depth >= kWideMinDepth and p <=
+// kWideMaxP.  The 64 leaf coefficient sets sit as [p^3][64] in shared
+// memory, so the compression GEMM reuses every operator element it loads for
+// 8 boxes per thread and every coefficient load (two float4) for 3 columns.
+template <int P> struct SmemW {
+    static constexpr int P3 = P * P * P;
+    // leaves [P3][64] | mids [P3][8] | top [P3] | scratch: max(basis 8 x 96 P, two [P3][8])
+    static constexpr int kMid = 64 * P3;
+    static constexpr int kTop = kMid + 8 * P3;
+    static constexpr int kScr = (kTop + P3 + 3) & ~3;
+    static constexpr int kScrN = 768 * P > 16 * P3 ? 768 * P : 16 * P3;
+    static constexpr int kUpFloats = kScr + kScrN;
+};
+
+// P2M of leaf `leaf` (column `col` of X, row stride XS) by one warp
+template <int P, int XS>
+__device__ __forceinline__ void p2m_leaf(const PassArgs &A, int64_t leaf, int c, float *L, float *X, int col)
+{
+    constexpr int P3 = P * P * P;
+    constexpr int NQ = (P * P + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    const int s0 = A.off[leaf], s1 = A.off[leaf + 1];
+    float acc[NQ][P];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int i = 0; i < P; ++i)
+            acc[q][i] = 0.0f;
+    for (int c0 = s0; c0 < s1; c0 += 32) {
+        const int cnt = min(32, s1 - c0);
+        __syncwarp();
+        if (lane < cnt) {
+            const float4 u = A.pts[c0 + lane];
+            const float sg = A.sig[(int64_t)c * A.n + c0 + lane];
+            float v[P];
+            basis_1d<P>(A.T, 2.0f * u.x, v);
+#pragma unroll
+            for (int i = 0; i < P; ++i)
+                L[lane * P + i] = v[i] * sg;
+            basis_1d<P>(A.T, 2.0f * u.y, v);
+#pragma unroll
+            for (int i = 0; i < P; ++i)
+                L[(32 + lane) * P + i] = v[i];
+            basis_1d<P>(A.T, 2.0f * u.z, v);
+#pragma unroll
+            for (int i = 0; i < P; ++i)
+                L[(64 + lane) * P + i] = v[i];
+        }
+        __syncwarp();
+        for (int j = 0; j < cnt; ++j) {
+            float lx[P];
+#pragma unroll
+            for (int i = 0; i < P; ++i)
+                lx[i] = L[j * P + i];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int pq = lane + 32 * q;
+                if (pq < P * P) {
+                    const float yz = L[(32 + j) * P + pq % P] * L[(64 + j) * P + pq / P];
+#pragma unroll
+                    for (int i = 0; i < P; ++i)
+                        acc[q][i] += lx[i] * yz;
+                }
+            }
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int pq = lane + 32 * q;
+        if (pq < P * P) {
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+                const int idx = i + P * pq;
+                X[idx * XS + col] = acc[q][i];
+                if (A.keep)
+                    A.M[A.D][(leaf * A.nrhs + c) * P3 + idx] = acc[q][i];
+            }
+        }
+    }
+}
+
+// compress the 64 leaves (columns of X [P3][64]) of box B at level D: thread
+// (kg = t % 32, bg = t / 32) makes coefficients k = k0 + 3 kg + {0, 1, 2} of
+// boxes 8 bg .. 8 bg + 7
+template <int P>
+__device__ void compress64(const PassArgs &A, const float *X, int64_t B, int c, bool zero)
+{
+    constexpr int P3 = P * P * P;
+    const int t = threadIdx.x, kg = t & 31, bg = t >> 5;
+    const int l = A.D, H = 1 << (l - 1);
+    const float *V = A.V[l];
+    float mx = 0.0f;
+    for (int k0 = 0; k0 < A.r; k0 += 96) {
+        const int kb = k0 + 3 * kg;
+        float acc[3][8];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int b = 0; b < 8; ++b)
+                acc[j][b] = 0.0f;
+        if (!zero) {
+#pragma unroll 2
+            for (int i = 0; i < P3; ++i) {
+                const float *vr = V + (int64_t)i * A.rp;
+                const float v0 = kb < A.r ? __ldg(vr + kb) : 0.0f;
+                const float v1 = kb + 1 < A.r ? __ldg(vr + kb + 1) : 0.0f;
+                const float v2 = kb + 2 < A.r ? __ldg(vr + kb + 2) : 0.0f;
+                const float4 m0 = *reinterpret_cast<const float4 *>(X + i * 64 + 8 * bg);
+                const float4 m1 = *reinterpret_cast<const float4 *>(X + i * 64 + 8 * bg + 4);
+                const float m[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    acc[0][b] += m[b] * v0;
+                    acc[1][b] += m[b] * v1;
+                    acc[2][b] += m[b] * v2;
+                }
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            int x, y, z;
+            demorton3((uint32_t)(64 * B + 8 * bg + b), x, y, z);
+            const int64_t row = parity_row(x, y, z, c, H, 1, A.R) * A.rp;
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if (kb + j < A.r)
+                    put_mt(A, l, row + kb + j, acc[j][b], mx);
+        }
+    }
+    flush_max(A, l, mx);
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_upward_wide(const __grid_constant__ PassArgs A)
+{
+    constexpr int P3 = P * P * P;
+    extern __shared__ __align__(16) float sm[];
+    float *sLeaf = sm;
+    float *sMid = sm + SmemW<P>::kMid;
+    float *sTop = sm + SmemW<P>::kTop;
+    float *sScr = sm + SmemW<P>::kScr;
+    __shared__ int sLast;
+    const int t = threadIdx.x, w = t >> 5;
+    const int D = A.D;
+    const int64_t B = blockIdx.x; // box at level D-2
+    const int c = blockIdx.y;
+    const bool zero = A.off[64 * B] == A.off[64 * B + 64];
+
+    // P2M: warp w makes leaves 64 B + 8 j + w, j = 0..7 (column 8 j + w)
+    for (int j = 0; j < 8; ++j)
+        p2m_leaf<P, 64>(A, 64 * B + 8 * j + w, c, sScr + w * 96 * P, sLeaf, 8 * j + w);
+    __syncthreads();
+    compress64<P>(A, sLeaf, B, c, zero);
+    // the 8 boxes of level D-1: M2M of their leaves, compression
+    for (int m = 0; m < 8; ++m)
+        m2m8<P, 64, 8>(A.T, sLeaf + 8 * m, sScr, sScr + 8 * P3, sMid + m);
+    if (A.keep)
+        for (int q = t; q < 8 * P3; q += kThreads)
+            A.M[D - 1][((8 * B + (q & 7)) * A.nrhs + c) * P3 + (q >> 3)] = sMid[q];
+    compress8<P>(A, D - 1, sMid, 8 * B, c, zero);
+    if (D - 2 < 2)
+        return;
+    // the block's own box (level D-2)
+    m2m8<P>(A.T, sMid, sScr, sScr + 8 * P3, sTop);
+    for (int r = t; r < P3; r += kThreads)
+        A.M[D - 2][(B * A.nrhs + c) * P3 + r] = sTop[r];
+    compress1<P>(A, D - 2, sTop, B, c);
+
+    // upper levels: the last of 8 siblings to arrive makes the parent
+    int64_t box = B;
+    for (int l = D - 3; l >= 2; --l) {
+        const int64_t par = box >> 3;
+        __threadfence(); // this thread's stores of the level-(l+1) box are visible device-wide
+        __syncthreads();
+        if (t == 0) {
+            int *cnt = A.count[l] + par * A.R + c;
+            const int before = atomicAdd(cnt, 1);
+            sLast = before == 7;
+            if (before == 7) {
+                atomicExch(cnt, 0); // ready for the next matvec
+                __threadfence();
+            }
+        }
+        __syncthreads();
+        if (!sLast)
+            return;
+        const float *Mc = A.M[l + 1] + (8 * par * A.nrhs + c) * (int64_t)P3;
+        for (int q = t; q < 8 * P3; q += kThreads) {
+            const int o = q & 7, r = q >> 3;
+            sMid[q] = __ldcg(Mc + (int64_t)o * A.nrhs * P3 + r);
+        }
+        __syncthreads();
+        m2m8<P>(A.T, sMid, sScr, sScr + 8 * P3, sTop);
+        for (int r = t; r < P3; r += kThreads)
+            A.M[l][(par * A.nrhs + c) * P3 + r] = sTop[r];
+        compress1<P>(A, l, sTop, par, c);
+        box = par;
+    }
+}
+
 template <int P>
 cudaError_t upward_p(const PassArgs &A, cudaStream_t s)
 {
+    if (P <= kWideMaxP && A.D >= kWideMinDepth) {
+        const size_t smem = sizeof(float) * SmemW<P>::kUpFloats;
+        cudaError_t e =
+            cudaFuncSetAttribute(k_upward_wide<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        dim3 grid((unsigned)(1LL << (3 * (A.D - 2))), (unsigned)A.nrhs);
+        k_upward_wide<P><<<grid, kThreads, smem, s>>>(A);
+        return cudaGetLastError();
+    }
     const size_t smem = sizeof(float) * Smem<P>::kUpFloats;
     cudaError_t e = cudaFuncSetAttribute(k_upward<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)

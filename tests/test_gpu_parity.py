@@ -87,12 +87,13 @@ def test_depth0_1_is_direct_sum(bb, oracle, depth, kid, ell):
 
 
 @pytest.mark.parametrize("p,depth,kind", [(4, 3, "uniform"), (5, 4, "uniform"), (2, 2, "uniform"),
-                                          (3, 5, "clustered"), (7, 3, "uniform")])
+                                          (3, 5, "clustered"), (7, 3, "uniform"), (3, 6, "clustered")])
 def test_stage_coefficients_match_oracle(bb, oracle, p, depth, kind):
     """Uncompressed operators (svd_eps = 0): M (upward pass) and F (after M2L
     and L2L) on every level 2..D match the oracle's stage outputs.  Depth 2
     has no M2M / L2L; depth 5 runs the upward pass's arrival chain over three
-    levels; the clustered set leaves whole level-(D-1) boxes empty."""
+    levels; depth 6 takes the wide upward pass (a block per box of level
+    D-2); the clustered sets leave whole boxes empty."""
     n = 12_000
     pts = W.make_points(kind, n, seed=45)
     sig = W.uniform_sigma(n, seed=46).astype(np.float32)
@@ -110,9 +111,11 @@ def test_stage_coefficients_match_oracle(bb, oracle, p, depth, kind):
         assert oracle.rel_err(gf[occ], Fs[l][occ]) < 5e-6, ("F", l)
     plan.close()
     # whole result: the near field's FP32 leaf-local coordinates alone cost
-    # 2.0e-5 on the clustered set (close pairs under 1/r; the same rounding
-    # emulated on the CPU gives 2.00e-5), under 1e-6 on the uniform ones
-    assert oracle.rel_err(got, ref) < (3e-5 if kind == "clustered" else 5e-6)
+    # 2.0e-5 (depth 5) and 8.9e-5 (depth 6) on the clustered set (close pairs
+    # under 1/r; the same rounding emulated on the CPU gives 2.00e-5 and
+    # 8.87e-5), under 1e-6 on the uniform ones
+    tol = {5: 3e-5, 6: 1.2e-4}.get(depth, 5e-6) if kind == "clustered" else 5e-6
+    assert oracle.rel_err(got, ref) < tol
 
 
 def test_coefficients_need_keep(bb):
