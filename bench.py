@@ -234,7 +234,12 @@ def time_plan(bb, torch, dev, pts, sig_dev, c, depth, precision, eps, flush, str
             "value": float(c["n"]) ** 2 * c["nrhs"] / (ms / 1e3)}
 
 
-def roofline(precision, info, nrhs, m2l_ms, clocks, torch, dev):
+# DRAM bytes (read + write) of one k_m2l_tc launch, from the ncu capture in
+# profiles/m2l_tc_fp16x3_uniform1M_d5.md; valid for the kernel as captured
+M2L_TRAFFIC = {("uniform-1M-p5-d5", "fp16x3"): 28382464 + 752128}
+
+
+def roofline(precision, info, nrhs, m2l_ms, clocks, torch, dev, workload=None):
     peaks, kind = measured_peaks()
     passes = {"fp32": 1, "tf32": 1, "tf32x3": 3, "bf16x3": 3, "fp16x3": 3}[precision]
     flops = 2.0 * info.m2l_pairs * info.rank * info.rank * passes * nrhs
@@ -251,7 +256,8 @@ def roofline(precision, info, nrhs, m2l_ms, clocks, torch, dev):
     else:
         r = {"kernel": "k_m2l_tc (all levels)", "bound": "tensor", "peak": peaks["bf16_tflops"],
              "peak_source": "%s bf16 dense %.0f TF/s (fp16 runs at the same rate)" % (kind, peaks["bf16_tflops"])}
-    r.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / r["peak"], "traffic": None,
+    r.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / r["peak"],
+              "traffic": M2L_TRAFFIC.get((workload, precision)),
               "work": "2 r^2 flops x %d interaction pairs x %d pass(es) x %d RHS, r = %d"
                       % (info.m2l_pairs, passes, nrhs, info.rank)})
     return r
@@ -366,7 +372,7 @@ def run_ours(args, rank, world, local):
                    "svd_eps": args.svd_eps, "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": "replicas"},
         "stages_ms": {k: float(v) for k, v in zip(bb.STAGES, stage)},
-        "roofline": roofline(precision, info, nrhs, float(stage[2]), clocks, torch, dev),
+        "roofline": roofline(precision, info, nrhs, float(stage[2]), clocks, torch, dev, args.workload),
         "e2e": {"value": world * N * N * nrhs / e2e_s, "unit": unit, "ms": e2e_s * 1e3,
                 "h2d_bytes_per_step": 4 * n * nrhs, "d2h_bytes_per_step": 4 * n * nrhs},
         "gpu_launches": launches * args.steps,
