@@ -10,11 +10,12 @@
 // u_x - y' only carries the rounding of u (|u| <= 1/2), not that of absolute
 // coordinates.
 //
-// Each thread owns two targets (a and b) and evaluates both against every
-// source it visits with the packed two-lane FP32 instructions of sm_100+
-// (FADD2 / FMUL2 / FFMA2); a source is staged as (x, x, y, y), (z, z, s, s) so
-// both halves of a packed operand come from one shared-memory broadcast.
-// Threads are (target pair, slice): slice s walks sources s, s + S, ...; the
+// Each thread owns kTPT targets (two packed pairs by default) and evaluates
+// them against every source it visits with the packed two-lane FP32
+// instructions of sm_100+ (FADD2 / FMUL2 / FFMA2); a source is staged as
+// (x, x, y, y), (z, z, s, s) so both halves of a packed operand come from one
+// shared-memory broadcast.
+// Threads are (target group, slice): slice s walks sources s, s + S, ...; the
 // slices of a target are added in a fixed order at the end (deterministic).
 // K at r = 0 follows the library's convention: 0 for 1/r and 1/r^2.
 #include <type_traits>
@@ -51,19 +52,20 @@ __device__ __forceinline__ float ex2_approx(float x)
 // K; the packed form applies it to both lanes.  one() follows the r = 0
 // convention (0 for the singular kernels) and serves the target's own leaf,
 // the only place where a point meets itself or an exact duplicate; far()
-// serves the other 26 leaves, where r2 = 0 can only come from FP32 rounding
-// of two distinct points closer than ~1e-7 cells: there the singular kernels
-// are clamped at 2^24 / h (finite) instead of tested.
-constexpr float kClampInvR = 16777216.0f, kClampInvR2 = 281474976710656.0f;
+// serves the other 26 leaves.  There r2 = 0 could only come from FP32
+// rounding of two distinct points closer than ~1e-7 cells, so the kernel
+// adds kR2Floor = 2^-48 (cell units squared) to r2 instead of testing it:
+// 1/r stays below 2^24 / h, and the shift is 1e-14 of any r2 that can occur.
+constexpr float kR2Floor = 3.5527136788005009e-15f; // 2^-48
 struct KInvR {
     float a; // unused
     __device__ float one(float r2, float, float, float) const { return r2 > 0.0f ? rsqrt_approx(r2) : 0.0f; }
-    __device__ float far(float r2, float, float, float) const { return fminf(rsqrt_approx(r2), kClampInvR); }
+    __device__ float far(float r2, float, float, float) const { return rsqrt_approx(r2); }
 };
 struct KInvR2 {
     float a;
     __device__ float one(float r2, float, float, float) const { return r2 > 0.0f ? rcp_approx(r2) : 0.0f; }
-    __device__ float far(float r2, float, float, float) const { return fminf(rcp_approx(r2), kClampInvR2); }
+    __device__ float far(float r2, float, float, float) const { return rcp_approx(r2); }
 };
 struct KExp { // exp(-h r / ell) = 2^(-a r), a = h / (ell ln 2)
     float a;
@@ -71,7 +73,7 @@ struct KExp { // exp(-h r / ell) = 2^(-a r), a = h / (ell ln 2)
     {
         return ex2_approx(-a * (r2 > 0.0f ? r2 * rsqrt_approx(r2) : 0.0f));
     }
-    __device__ float far(float r2, float dx, float dy, float dz) const { return one(r2, dx, dy, dz); }
+    __device__ float far(float r2, float, float, float) const { return ex2_approx(-a * (r2 * rsqrt_approx(r2))); }
 };
 struct KGauss { // exp(-(h r / ell)^2) = 2^(-a r^2), a = h^2 / (ell^2 ln 2)
     float a;
@@ -101,23 +103,33 @@ __device__ __forceinline__ float2 kern2(const Kern &k, float2 r2, float2 dx, flo
     return make_float2(k.far(r2.x, dx.x, dy.x, dz.x), k.far(r2.y, dx.y, dy.y, dz.y));
 }
 
+// targets per thread (2 or 4): each thread runs 1 or 2 packed target pairs
+// against every source it visits, so a source's two shared-memory loads serve
+// that many targets
+#ifndef BBFMM_P2P_TPT
+#define BBFMM_P2P_TPT 4
+#endif
+constexpr int kTPT = BBFMM_P2P_TPT;
+static_assert(kTPT == 2 || kTPT == 4, "2 or 4 targets per thread");
+
 template <class Kern>
 __global__ void __launch_bounds__(kP2PThreads, 8)
     k_p2p(const float4 *__restrict__ pts, const float *__restrict__ sig, const int *__restrict__ off,
           const int4 *__restrict__ chunks, int nchunks, int64_t n, int D, Kern kern, float scale, int nrhs,
           float *__restrict__ phi)
 {
+    constexpr int NPK = kTPT / 2; // packed target pairs per thread
     __shared__ float4 stage_xy[kStageSrc]; // (x, x, y, y)
     __shared__ float4 stage_zs[kStageSrc]; // (z, z, sigma, sigma)
     __shared__ int nb_start[28], nb_pre[28];
     __shared__ float4 nb_delta[27];
-    __shared__ float2 red[kP2PThreads];
+    __shared__ float2 red[NPK][kP2PThreads];
     const int tid = threadIdx.x;
     const int4 ch = chunks[blockIdx.x];
     const int nt = ch.z;
-    const int np = (nt + 1) >> 1;    // target pairs
-    const int S = kP2PThreads / np; // slices per pair (>= 1)
-    const int t = tid % np, slice = tid / np;
+    const int nq = (nt + kTPT - 1) / kTPT; // target groups (one per thread and slice)
+    const int S = kP2PThreads / nq;        // slices per group (>= 1)
+    const int t = tid % nq, slice = tid / nq;
     const bool active = slice < S;
     int ax, ay, az;
     demorton3((uint32_t)ch.x, ax, ay, az);
@@ -150,14 +162,25 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
     }
     __syncthreads();
     const int ns = nb_pre[27], nown = nb_pre[1]; // all sources; those of the own leaf
-    // the pair's two targets; a missing second target duplicates the first
-    const int ia = active ? t : 0, ib = active && t + np < nt ? t + np : ia;
-    const float4 xa = pts[ch.y + ia], xb = pts[ch.y + ib];
-    const float2 X = make_float2(xa.x, xb.x), Y = make_float2(xa.y, xb.y), Z = make_float2(xa.z, xb.z);
+    // the group's targets t + q nq; a missing one duplicates target t
+    float2 X[NPK], Y[NPK], Z[NPK];
+#pragma unroll
+    for (int pk = 0; pk < NPK; ++pk) {
+        const int i0 = t + 2 * pk * nq, i1 = i0 + nq;
+        const float4 xa = pts[ch.y + (active && i0 < nt ? i0 : 0)];
+        const float4 xb = pts[ch.y + (active && i1 < nt ? i1 : 0)];
+        X[pk] = make_float2(xa.x, xb.x);
+        Y[pk] = make_float2(xa.y, xb.y);
+        Z[pk] = make_float2(xa.z, xb.z);
+    }
+    const float2 floor2 = make_float2(kR2Floor, kR2Floor);
 
     for (int c = 0; c < nrhs; ++c) {
         const float *sg = sig + (int64_t)c * n;
-        float2 acc = make_float2(0.0f, 0.0f), acc2 = make_float2(0.0f, 0.0f);
+        float2 acc[NPK], acc2[NPK];
+#pragma unroll
+        for (int pk = 0; pk < NPK; ++pk)
+            acc[pk] = acc2[pk] = make_float2(0.0f, 0.0f);
         for (int base = 0; base < ns; base += kStageSrc) {
             const int cnt = min(kStageSrc, ns - base);
             int k = 0; // neighbour holding source gg: it only moves forward as gg grows
@@ -176,46 +199,59 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
             }
             __syncthreads();
             if (active) {
-                // two sources per iteration into two accumulators (shorter
-                // dependency chains); the accumulators are added in a fixed order
-                auto pair = [&](auto own, int j, float2 &a) {
+                // one source against the thread's NPK target pairs
+                auto visit = [&](auto own, int j, float2 *a) {
                     const float4 qa = stage_xy[j];
                     const float4 qb = stage_zs[j];
-                    const float2 dx = __fadd2_rn(X, make_float2(qa.x, qa.y));
-                    const float2 dy = __fadd2_rn(Y, make_float2(qa.z, qa.w));
-                    const float2 dz = __fadd2_rn(Z, make_float2(qb.x, qb.y));
-                    float2 r2 = __fmul2_rn(dx, dx);
-                    r2 = __ffma2_rn(dy, dy, r2);
-                    r2 = __ffma2_rn(dz, dz, r2);
-                    a = __ffma2_rn(kern2<decltype(own)::value>(kern, r2, dx, dy, dz), make_float2(qb.z, qb.w), a);
+#pragma unroll
+                    for (int pk = 0; pk < NPK; ++pk) {
+                        const float2 dx = __fadd2_rn(X[pk], make_float2(qa.x, qa.y));
+                        const float2 dy = __fadd2_rn(Y[pk], make_float2(qa.z, qa.w));
+                        const float2 dz = __fadd2_rn(Z[pk], make_float2(qb.x, qb.y));
+                        float2 r2 = decltype(own)::value ? __fmul2_rn(dx, dx) : __ffma2_rn(dx, dx, floor2);
+                        r2 = __ffma2_rn(dy, dy, r2);
+                        r2 = __ffma2_rn(dz, dz, r2);
+                        a[pk] = __ffma2_rn(kern2<decltype(own)::value>(kern, r2, dx, dy, dz),
+                                           make_float2(qb.z, qb.w), a[pk]);
+                    }
                 };
                 // the own leaf's sources (staged first) with the r = 0 test
                 const int cown = min(cnt, max(0, nown - base));
                 int j = slice;
                 for (; j < cown; j += S)
-                    pair(std::true_type{}, j, acc);
+                    visit(std::true_type{}, j, acc);
+                // two sources per iteration into two accumulator sets (shorter
+                // dependency chains), added in a fixed order at the end
 #pragma unroll 2
                 for (; j + S < cnt; j += 2 * S) {
-                    pair(std::false_type{}, j, acc);
-                    pair(std::false_type{}, j + S, acc2);
+                    visit(std::false_type{}, j, acc);
+                    visit(std::false_type{}, j + S, acc2);
                 }
                 if (j < cnt)
-                    pair(std::false_type{}, j, acc);
+                    visit(std::false_type{}, j, acc);
             }
             __syncthreads();
         }
-        red[tid] = active ? make_float2(acc.x + acc2.x, acc.y + acc2.y) : make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int pk = 0; pk < NPK; ++pk)
+            red[pk][tid] = active ? make_float2(acc[pk].x + acc2[pk].x, acc[pk].y + acc2[pk].y)
+                                  : make_float2(0.0f, 0.0f);
         __syncthreads();
-        if (tid < np) {
-            float sa = 0.0f, sb = 0.0f;
-            for (int q = 0; q < S; ++q) {
-                const float2 v = red[tid + q * np];
-                sa += v.x;
-                sb += v.y;
+        if (tid < nq) {
+#pragma unroll
+            for (int pk = 0; pk < NPK; ++pk) {
+                float sa = 0.0f, sb = 0.0f;
+                for (int q = 0; q < S; ++q) {
+                    const float2 v = red[pk][tid + q * nq];
+                    sa += v.x;
+                    sb += v.y;
+                }
+                const int i0 = tid + 2 * pk * nq, i1 = i0 + nq;
+                if (i0 < nt)
+                    phi[(int64_t)c * n + ch.y + i0] = scale * sa;
+                if (i1 < nt)
+                    phi[(int64_t)c * n + ch.y + i1] = scale * sb;
             }
-            phi[(int64_t)c * n + ch.y + tid] = scale * sa;
-            if (tid + np < nt)
-                phi[(int64_t)c * n + ch.y + tid + np] = scale * sb;
         }
         __syncthreads();
     }
@@ -340,6 +376,7 @@ cudaError_t launch_p2p(const float4 *pts, const float *sig, const int *leaf_off,
                        cudaStream_t s)
 {
     static_assert(kChunk <= 2 * kP2PThreads, "a work item holds at most two targets per thread");
+    static_assert(kChunk <= kTPT * kP2PThreads, "a work item holds at most kTPT targets per thread");
     const double ln2 = 0.69314718055994530942;
     switch (kernel) {
     case BBFMM_K_INV_R:
