@@ -147,6 +147,29 @@ const char *bbfmm_last_error(void);
 int bbfmm_plan_info(bbfmm_plan_t plan, bbfmm_info *info);
 
 /*
+ * bbfmm_rand_eig: the k largest eigenvalues (and eigenvectors) of the kernel
+ * matrix K of a plan (K_ij = K(x_i, x_j), symmetric kernels), by the
+ * randomized range finder and Rayleigh-Ritz step of the randomized PCA used
+ * in Sec. 4.3 (two batched matvecs with m right-hand sides, plus `power`
+ * subspace iterations): Y = K Omega; Q = orth(Y); B = Q^T K Q = V L V^T;
+ * evals = the k largest of L, evecs = Q V.  The matvecs are bbfmm_matvec;
+ * the tall-skinny products run in the library's kernels (FP32 products,
+ * FP64 sums), the m x m eigenproblems on the host in FP64.
+ *   omega:  device, n x m column-major FP32, the caller's random test block
+ *           (e.g. standard normal), caller's point order; read only.
+ *   m:      columns of omega, k <= m <= opts.max_nrhs of the plan.
+ *   k:      eigenpairs wanted.
+ *   power:  subspace iterations, 0..8 (0 = the plain range finder).
+ *   evals:  host, k doubles, decreasing; 0 past the rank of K Omega.
+ *   evecs:  device n x k column-major FP32 (caller's point order), or NULL.
+ * Allocates 2 n m floats of scratch for the call; synchronizes the stream.
+ * Errors: EINVAL (ranges, NULL, host pointers, K Omega = 0), ENOMEM, ECUDA,
+ * EBUSY.
+ */
+int bbfmm_rand_eig(bbfmm_plan_t plan, const float *omega, int m, int k, int power, double *evals,
+                   float *evecs, void *stream);
+
+/*
  * bbfmm_get_coefficients: copy the coefficients of the last matvec at one
  * level to host memory, for stage-by-stage checks.
  *   which: 0 = multipole M (Sec. 2.2 upward pass), 1 = local F after the

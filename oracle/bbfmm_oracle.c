@@ -107,6 +107,20 @@ int oracle_num_threads(void)
 }
 
 /* ------------------------------------------------------------------------- */
+/* The dense kernel matrix K[i][j] = K(x_i, x_j) (n x n, row-major), whose
+ * leading eigenvalues the randomized PCA of Sec. 4.3 approximates; the same
+ * K(0) convention as everywhere else. */
+void oracle_kernel_matrix(int64_t n, const double *x, int kid, double ell, double *K)
+{
+    int64_t i;
+#pragma omp parallel for schedule(static)
+    for (i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j)
+            K[i * n + j] = or_kernel(kid, ell, x[3 * i] - x[3 * j], x[3 * i + 1] - x[3 * j + 1],
+                                     x[3 * i + 2] - x[3 * j + 2]);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Direct sum, Sec. 1 Eq. summation: phi_i = sum_j K(x_i, y_j) sigma_j.
  * x: nt x 3 row-major targets, y: ns x 3 row-major sources,
  * sigma: ns x nrhs column-major, phi: nt x nrhs column-major (overwritten). */

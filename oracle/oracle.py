@@ -63,6 +63,8 @@ def lib():
             L.oracle_interaction_list.argtypes = [i32, i64, i64, i64, lp]
             L.oracle_interaction_list.restype = i32
             L.oracle_leaf_cells.argtypes = [i64, dp, dp, f64, i32, lp]
+            L.oracle_kernel_matrix.argtypes = [i64, dp, i32, f64, dp]
+            L.oracle_kernel_matrix.restype = None
             L.oracle_kernel.argtypes = [i32, f64, dp, dp]
             L.oracle_kernel.restype = f64
             L.oracle_num_threads.restype = i32
@@ -123,6 +125,39 @@ def direct(targets, sources, sigma, kid, ell=1.0):
     out = np.zeros((x.shape[0], nrhs), dtype=np.float64, order="F")
     lib().oracle_direct(x.shape[0], _dp(x), y.shape[0], _dp(y), _dp(s), nrhs, kid, ell, _dp(out))
     return out[:, 0] if np.ndim(sigma) == 1 else out
+
+
+def kernel_matrix(points, kid, ell=1.0):
+    """Dense FP64 kernel matrix K[i][j] = K(x_i, x_j) (the covariance matrix
+    of the randomized PCA of Sec. 4.3); n x n, so small n only."""
+    x = _f64c(points)
+    n = x.shape[0]
+    out = np.zeros((n, n), dtype=np.float64)
+    lib().oracle_kernel_matrix(n, _dp(x), kid, ell, _dp(out))
+    return out
+
+
+def top_eigenvalues(points, kid, k, ell=1.0):
+    """The k largest eigenvalues of the dense kernel matrix (numpy's symmetric
+    eigensolver on kernel_matrix), in decreasing order."""
+    w = np.linalg.eigvalsh(kernel_matrix(points, kid, ell))
+    return w[::-1][:k].copy()
+
+
+def rand_eig(K, omega, k, power=0):
+    """The randomized PCA of Sec. 4.3 on a dense FP64 matrix, step by step
+    (the randomized range finder with `power` subspace iterations, then the
+    Rayleigh-Ritz eigen-decomposition of Halko, Martinsson & Tropp): Y = K W
+    with W = omega^T (n x m); Q = qr(Y); repeat Y = K Q, Q = qr(Y) `power`
+    times; B = Q^T K Q = V L V^T.  Returns the k largest eigenvalues
+    (decreasing) and the matching columns of Q V."""
+    Q, _ = np.linalg.qr(K @ np.asarray(omega, dtype=np.float64).T)
+    for _ in range(power):
+        Q, _ = np.linalg.qr(K @ Q)
+    B = Q.T @ (K @ Q)
+    w, V = np.linalg.eigh(0.5 * (B + B.T))
+    order = np.argsort(w)[::-1][:k]
+    return w[order], Q @ V[:, order]
 
 
 def cheb_nodes(p):

@@ -30,7 +30,7 @@ PRECISIONS = {"fp32": BBFMM_PREC_FP32, "tf32": BBFMM_PREC_TF32, "tf32x3": BBFMM_
 EXPORTED = ["bbfmm_default_opts", "bbfmm_plan", "bbfmm_matvec", "bbfmm_destroy",
             "bbfmm_last_error", "bbfmm_plan_info", "bbfmm_get_coefficients",
             "bbfmm_get_leaf_cells", "bbfmm_stage_times", "bbfmm_set_timing", "bbfmm_status",
-            "bbfmm_sort_points_static"]
+            "bbfmm_sort_points_static", "bbfmm_rand_eig"]
 
 
 class bbfmm_opts(ctypes.Structure):
@@ -95,6 +95,8 @@ def lib():
             L.bbfmm_status.restype = i32
             L.bbfmm_sort_points_static.argtypes = [vp, i64, i32, ctypes.POINTER(f64), f64, vp, vp, vp]
             L.bbfmm_sort_points_static.restype = i32
+            L.bbfmm_rand_eig.argtypes = [vp, vp, i32, i32, i32, ctypes.POINTER(f64), vp, vp]
+            L.bbfmm_rand_eig.restype = i32
             _lib = L
     return _lib
 
@@ -205,6 +207,21 @@ def bbfmm_sort_points_static(points, depth, lo, side, perm, leaf_off, stream=Non
     return _check_plain(lib().bbfmm_sort_points_static(_ptr(points), int(points.shape[0]), int(depth), lo3,
                                                        float(side), _ptr(perm), _ptr(leaf_off),
                                                        _stream(stream)))
+
+
+def bbfmm_rand_eig(plan, omega, k, power=0, vectors=True, stream=None):
+    """Randomized eigen-decomposition of the plan's kernel matrix.  omega: a
+    CUDA float32 tensor of shape (m, n) (n x m column-major).  Returns the k
+    largest eigenvalues (numpy, decreasing) and, with ``vectors``, a CUDA
+    tensor (k, n) of eigenvectors."""
+    import torch
+    m = int(omega.shape[0])
+    evals = np.zeros(k, dtype=np.float64)
+    evecs = torch.empty((k, omega.shape[1]), dtype=torch.float32, device=omega.device) if vectors else None
+    _check(lib().bbfmm_rand_eig(plan, _ptr(omega.contiguous()), m, int(k), int(power),
+                                evals.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                _ptr(evecs) if vectors else None, _stream(stream)))
+    return evals, evecs
 
 
 def _check_plain(st):

@@ -131,6 +131,10 @@ struct InterpTables {
     float S[2][kMaxP][kMaxP]; // S[o][i][j] = l_i((s_j + 2o - 1)/2)
 };
 InterpTables make_interp_tables(const HostOps &h);
+// cyclic Jacobi eigen-decomposition of a symmetric n x n matrix A (row-major,
+// destroyed): eigenvalues w in decreasing order, eigenvectors in the columns
+// of Q (row-major n x n); operators.cpp
+void jacobi_eigen(int n, std::vector<double> &A, std::vector<double> &w, std::vector<double> &Q);
 
 // ---------------------------------------------------------------------------
 // Device operator set, uploaded once per host operator set
@@ -198,6 +202,9 @@ struct bbfmm_plan_impl {
     // upward pass: arrival counters of the boxes of levels 2..D-2 (x max_nrhs),
     // zero between matvecs
     int *up_count[kMaxDepth + 1] = {};
+    // tensor-core M2L: the tiles with occupied targets (device), per level
+    int4 *m2l_tiles = nullptr;
+    int m2l_ntiles[kMaxDepth + 1] = {}, m2l_tile_off[kMaxDepth + 1] = {};
     bool keep_coeffs = false; // also store leaf M and every level's F
 
     std::vector<void *> allocations;
@@ -283,6 +290,14 @@ struct Split16Args {
     int lmin, lmax, fmt;
 };
 cudaError_t launch_split16_levels(const Split16Args &A, cudaStream_t s);
+
+// eig.cu: tall-skinny products for the randomized eigen-decomposition
+int gram_splits(int64_t n);
+// partial[split][a][b] (FP64) = rows of the split of A^T B, A and B column-major n x m
+cudaError_t launch_gram(const float *A, const float *B, int64_t n, int m, double *partial, int splits,
+                        cudaStream_t s);
+// out (n x mo) = Y (n x m) T (m x mo), all column-major; out must not alias Y
+cudaError_t launch_rmul(const float *Y, int64_t n, int m, const float *T, int mo, float *out, cudaStream_t s);
 cudaError_t launch_combine(const float *phi_far, const float *phi_near, const int *perm, int64_t n,
                            int nrhs, float *phi, cudaStream_t s);
 // entry points of the two kernels whose pointer arguments (the caller's sigma
@@ -298,7 +313,11 @@ cudaError_t launch_m2l_fp32(const float *Mt, const float *C, float *Ft, int l, i
                             int nrhs, int R, float scale, cudaStream_t s);
 // m2l_tc.cu: every level of the far field in one go (FP32 or tensor cores)
 cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s);
-int m2l_groups_for(int D, int nrhs, int precision, int r);
+int m2l_groups_for(int D, int nrhs, int precision, int r, int64_t active_tiles);
+// the tensor-core M2L tiles that hold at least one occupied target box, level
+// by level from D down to 2, as {tx, ty, tz, octant}; count[l] per level
+void m2l_active_tiles(int D, int precision, const std::vector<uint8_t> &leaf_occ, std::vector<int4> &tiles,
+                      int *count);
 // p2p.cu
 cudaError_t launch_p2p(const float4 *pts, const float *sig, const int *leaf_off, const int4 *chunks,
                        int nchunks, int64_t n, int D, int kernel, double ell, double h, int nrhs,

@@ -357,10 +357,14 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, cudaStream_t s)
     P->bytes += chunk_bytes;
 
     // statistics of the tree (host copy of the leaf offsets)
+    std::vector<uint8_t> leaf_occ;
     {
         std::vector<int> off(nleaf + 1);
         CUDA_TRY(cudaMemcpyAsync(off.data(), P->leaf_off, 4 * (nleaf + 1), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaStreamSynchronize(s));
+        leaf_occ.resize(nleaf);
+        for (int64_t m = 0; m < nleaf; ++m)
+            leaf_occ[m] = off[m + 1] > off[m] ? 1 : 0;
         if (off[nleaf] != n)
             return fail(BBFMM_EINTERNAL, "leaf offsets do not cover all points");
         int ns = 1 << D;
@@ -397,7 +401,18 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, cudaStream_t s)
     // per-level coefficient buffers
     const int R = P->max_nrhs, p3 = P->p3;
     const int rp = P->ops->rp;
-    P->m2l_groups = m2l_groups_for(D, R, P->precision, P->ops->r);
+    // the tensor-core M2L visits only tiles with occupied targets
+    std::vector<int4> tiles;
+    m2l_active_tiles(D, P->precision, leaf_occ, tiles, P->m2l_ntiles);
+    for (int l = D, o = 0; l >= 2; --l) {
+        P->m2l_tile_off[l] = o;
+        o += P->m2l_ntiles[l];
+    }
+    if (!tiles.empty()) {
+        PTRY(plan_alloc(P, (void **)&P->m2l_tiles, sizeof(int4) * tiles.size(), false, s));
+        CUDA_TRY(cudaMemcpyAsync(P->m2l_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s));
+    }
+    P->m2l_groups = m2l_groups_for(D, R, P->precision, P->ops->r, (int64_t)tiles.size());
     for (int l = 2; l <= D; ++l) {
         Level &L = P->lev[l];
         int64_t nb = 1LL << (3 * l), H = 1LL << (l - 1);
@@ -785,6 +800,117 @@ int bbfmm_matvec(bbfmm_plan_t plan, const float *sigma, float *phi, int nrhs, vo
     }
     plan->busy.store(0);
     return st;
+}
+
+// ---------------------------------------------------------------------------
+// randomized eigen-decomposition of the kernel matrix (Sec. 4.3)
+namespace {
+struct DevBuffer {
+    void *p = nullptr;
+    ~DevBuffer()
+    {
+        if (p)
+            cudaFree(p);
+    }
+};
+} // namespace
+
+// G (m x m, FP64, row-major) = A^T B, partial sums added in split order
+static int gram_host(const float *A, const float *B, int64_t n, int m, double *dpartial, int splits,
+                     cudaStream_t s, std::vector<double> &G)
+{
+    CUDA_TRY(launch_gram(A, B, n, m, dpartial, splits, s));
+    std::vector<double> h((size_t)splits * m * m);
+    CUDA_TRY(cudaMemcpyAsync(h.data(), dpartial, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    G.assign((size_t)m * m, 0.0);
+    for (int sp = 0; sp < splits; ++sp)
+        for (size_t q = 0; q < (size_t)m * m; ++q)
+            G[q] += h[(size_t)sp * m * m + q];
+    return BBFMM_OK;
+}
+
+// Q (n x mq) = an orthonormal basis of the columns of Y (n x m): with
+// Y^T Y = W L W^T, Q = Y W_k L_k^(-1/2) over the eigenvalues above 1e-10 of
+// the largest (directions below that are lost to FP32 rounding of Y)
+static int orthonormalize(const float *Y, int64_t n, int m, float *Q, int &mq, double *dpartial, int splits,
+                          float *dT, cudaStream_t s)
+{
+    std::vector<double> G, w, W;
+    PTRY(gram_host(Y, Y, n, m, dpartial, splits, s, G));
+    jacobi_eigen(m, G, w, W);
+    int k = 0;
+    while (k < m && w[k] > 0.0 && w[k] > 1e-10 * w[0])
+        ++k;
+    if (k == 0)
+        return fail(BBFMM_EINVAL, "the block K Omega is zero");
+    std::vector<float> T((size_t)m * k); // column-major m x k
+    for (int c = 0; c < k; ++c)
+        for (int a = 0; a < m; ++a)
+            T[a + (size_t)c * m] = (float)(W[(size_t)a * m + c] / sqrt(w[c]));
+    CUDA_TRY(cudaMemcpyAsync(dT, T.data(), sizeof(float) * T.size(), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(launch_rmul(Y, n, m, dT, k, Q, s));
+    mq = k;
+    return BBFMM_OK;
+}
+
+int bbfmm_rand_eig(bbfmm_plan_t plan, const float *omega, int m, int k, int power, double *evals, float *evecs,
+                   void *stream)
+{
+    g_last_error.clear();
+    if (!plan || !omega || !evals)
+        return fail(BBFMM_EINVAL, "NULL argument");
+    if (m < 1 || m > plan->max_nrhs || k < 1 || k > m || power < 0 || power > 8)
+        return fail(BBFMM_EINVAL, "need 1 <= k <= m <= max_nrhs (%d) and 0 <= power <= 8", plan->max_nrhs);
+    if (!is_device_ptr(omega) || (evecs && !is_device_ptr(evecs)))
+        return fail(BBFMM_EINVAL, "omega and evecs must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = plan->n;
+    const int splits = gram_splits(n);
+    DevBuffer b1, b2, bp, bt;
+    CUDA_TRY(cudaMalloc(&b1.p, sizeof(float) * n * m));
+    CUDA_TRY(cudaMalloc(&b2.p, sizeof(float) * n * m));
+    CUDA_TRY(cudaMalloc(&bp.p, sizeof(double) * (size_t)splits * m * m));
+    CUDA_TRY(cudaMalloc(&bt.p, sizeof(float) * (size_t)m * m));
+    float *Y = (float *)b1.p, *Q = (float *)b2.p, *dT = (float *)bt.p;
+    double *dpartial = (double *)bp.p;
+    // range finder: Y = K Omega, then `power` rounds of Y = K orth(Y)
+    PTRY(bbfmm_matvec(plan, omega, Y, m, stream));
+    int mq = m;
+    for (int it = 0; it < power; ++it) {
+        PTRY(orthonormalize(Y, n, mq, Q, mq, dpartial, splits, dT, s));
+        PTRY(bbfmm_matvec(plan, Q, Y, mq, stream));
+    }
+    // Q = orth(Y), twice: the second pass restores the orthogonality that
+    // the first loses to rounding
+    PTRY(orthonormalize(Y, n, mq, Q, mq, dpartial, splits, dT, s));
+    PTRY(orthonormalize(Q, n, mq, Y, mq, dpartial, splits, dT, s));
+    float *basis = Y, *Z = Q;
+    // Rayleigh-Ritz: B = Q^T K Q, B = V L V^T; eigenvectors U = Q V
+    PTRY(bbfmm_matvec(plan, basis, Z, mq, stream));
+    std::vector<double> Bm, w, V;
+    PTRY(gram_host(basis, Z, n, mq, dpartial, splits, s, Bm));
+    for (int a = 0; a < mq; ++a)
+        for (int b = a + 1; b < mq; ++b) {
+            const double v = 0.5 * (Bm[(size_t)a * mq + b] + Bm[(size_t)b * mq + a]);
+            Bm[(size_t)a * mq + b] = Bm[(size_t)b * mq + a] = v;
+        }
+    jacobi_eigen(mq, Bm, w, V);
+    const int kk = k < mq ? k : mq;
+    for (int j = 0; j < k; ++j)
+        evals[j] = j < kk ? w[j] : 0.0;
+    if (evecs) {
+        std::vector<float> T((size_t)mq * kk);
+        for (int c = 0; c < kk; ++c)
+            for (int a = 0; a < mq; ++a)
+                T[a + (size_t)c * mq] = (float)V[(size_t)a * mq + c];
+        CUDA_TRY(cudaMemcpyAsync(dT, T.data(), sizeof(float) * T.size(), cudaMemcpyHostToDevice, s));
+        CUDA_TRY(launch_rmul(basis, n, mq, dT, kk, evecs, s));
+        if (kk < k)
+            CUDA_TRY(cudaMemsetAsync(evecs + (size_t)kk * n, 0, sizeof(float) * n * (k - kk), s));
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return BBFMM_OK;
 }
 
 int bbfmm_destroy(bbfmm_plan_t plan)

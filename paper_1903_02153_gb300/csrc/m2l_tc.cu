@@ -51,6 +51,8 @@
 // sets the plan's status word, stops issuing work, waits (bounded) for its own
 // copies and MMAs in flight, frees its TMEM and returns.
 #include <cudaTypedefs.h>
+
+#include <algorithm>
 #include <math.h>
 #include <string.h>
 
@@ -108,7 +110,8 @@ struct TcLevel {
     float *Ft;                // partial slice g at Ft + g * slice
     int64_t slice;            // floats per slice
     int H, bx, by, bz, lbx, lby, n; // tile extent (log2 of bx, by) and N = bx by bz
-    int tiles_x, tiles_y, tiles_z, ntiles, tile_base, opl, l;
+    const int4 *tl;           // the level's active tiles {tx, ty, tz, octant} (device)
+    int nact, ntiles, tile_base, opl, l; // active tiles; x right-hand sides; first tile number
     uint32_t idesc;           // instruction descriptor (N of this level)
     uint32_t b_load;          // bytes of one source box (one piece, one chunk)
     float scale;
@@ -145,15 +148,13 @@ __device__ __forceinline__ Item decode_segment(const TcLaunch &P, int64_t pos, i
         ++L;
     it.L = L;
     const TcLevel &lv = P.lev[L];
-    int u = t - lv.tile_base;
-    it.tx = u % lv.tiles_x;
-    u /= lv.tiles_x;
-    it.ty = u % lv.tiles_y;
-    u /= lv.tiles_y;
-    it.tz = u % lv.tiles_z;
-    u /= lv.tiles_z;
-    it.ot = u & 7;
-    it.c = u >> 3;
+    const int u = t - lv.tile_base;
+    it.c = u / lv.nact;
+    const int4 e = lv.tl[u - it.c * lv.nact];
+    it.tx = e.x;
+    it.ty = e.y;
+    it.tz = e.z;
+    it.ot = e.w;
     return it;
 }
 
@@ -520,36 +521,66 @@ static void tile_of(int H, int nt, int &bx, int &by, int &bz)
     }
 }
 
-static int tile_count(int H, int nt, int nrhs)
-{
-    int bx, by, bz;
-    tile_of(H, nt, bx, by, bz);
-    return ((H + bx - 1) / bx) * ((H + by - 1) / by) * ((H + bz - 1) / bz) * 8 * nrhs;
-}
-
 static int tile_targets(int precision)
 {
     return precision == BBFMM_PREC_FP16X3 || precision == BBFMM_PREC_BF16X3 ? kTile16 : 128;
 }
 
-static int64_t tiles_all(int D, int nt, int nrhs)
+void m2l_active_tiles(int D, int precision, const std::vector<uint8_t> &leaf_occ, std::vector<int4> &tiles,
+                      int *count)
 {
-    int64_t T = 0;
-    for (int l = 2; l <= D; ++l)
-        T += tile_count(1 << (l - 1), nt, nrhs);
-    return T;
+    tiles.clear();
+    for (int l = 0; l <= kMaxDepth; ++l)
+        count[l] = 0;
+    if (D < 2)
+        return;
+    const int nt = tile_targets(precision);
+    // occupancy of the boxes of every level, from the leaves (Morton order)
+    std::vector<std::vector<uint8_t>> occ(D + 1);
+    occ[D] = leaf_occ;
+    for (int l = D - 1; l >= 2; --l) {
+        occ[l].assign((size_t)1 << (3 * l), 0);
+        for (size_t b = 0; b < occ[l + 1].size(); ++b)
+            if (occ[l + 1][b])
+                occ[l][b >> 3] = 1;
+    }
+    for (int l = D; l >= 2; --l) { // finest first, the order of the launch
+        const int H = 1 << (l - 1);
+        int bx, by, bz;
+        tile_of(H, nt, bx, by, bz);
+        const int size = 1 << l;
+        for (int ot = 0; ot < 8; ++ot)
+            for (int tz = 0; tz * bz < H; ++tz)
+                for (int ty = 0; ty * by < H; ++ty)
+                    for (int tx = 0; tx * bx < H; ++tx) {
+                        bool any = false;
+                        for (int Z = tz * bz; Z < std::min(H, (tz + 1) * bz) && !any; ++Z)
+                            for (int Y = ty * by; Y < std::min(H, (ty + 1) * by) && !any; ++Y)
+                                for (int X = tx * bx; X < std::min(H, (tx + 1) * bx) && !any; ++X) {
+                                    const int x = 2 * X + (ot & 1), y = 2 * Y + ((ot >> 1) & 1),
+                                              z = 2 * Z + (ot >> 2);
+                                    if (x < size && y < size && z < size &&
+                                        occ[l][morton3((uint32_t)x, (uint32_t)y, (uint32_t)z)])
+                                        any = true;
+                                }
+                        if (any) {
+                            tiles.push_back(make_int4(tx, ty, tz, ot));
+                            count[l]++;
+                        }
+                    }
+    }
 }
 
-// slices of F~ per level: 2 when the tiles outnumber the SMs (every CTA's
-// range is then at least one tile long, so a tile meets at most one range
-// boundary), else 4 (ranges of at least 63 offsets)
-int m2l_groups_for(int D, int nrhs, int precision, int r)
+// slices of F~ per level: 2 when the (active) tiles outnumber the SMs (every
+// CTA's range is then at least one tile long, so a tile meets at most one
+// range boundary), else 4 (ranges of at least 63 offsets)
+int m2l_groups_for(int D, int nrhs, int precision, int r, int64_t active_tiles)
 {
     if (precision == BBFMM_PREC_FP32 || D < 2 || r > 128)
         return 1;
     if (tc_init() != cudaSuccess)
         return 1;
-    return tiles_all(D, tile_targets(precision), nrhs) >= g_num_sms ? 2 : 4;
+    return active_tiles * nrhs >= g_num_sms ? 2 : 4;
 }
 
 template <int NPROD, int NACC, bool CF, int CH, int FMT>
@@ -647,10 +678,9 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
         lv.lbx = __builtin_ctz((unsigned)lv.bx);
         lv.lby = __builtin_ctz((unsigned)lv.by);
         lv.n = lv.bx * lv.by * lv.bz;
-        lv.tiles_x = (H + lv.bx - 1) / lv.bx;
-        lv.tiles_y = (H + lv.by - 1) / lv.by;
-        lv.tiles_z = (H + lv.bz - 1) / lv.bz;
-        lv.ntiles = tile_count(H, nt, nrhs);
+        lv.tl = P->m2l_tiles + P->m2l_tile_off[l];
+        lv.nact = P->m2l_ntiles[l];
+        lv.ntiles = lv.nact * nrhs;
         lv.tile_base = tiles;
         lv.opl = O.nlev == 1 ? 0 : l - 2;
         lv.l = l;

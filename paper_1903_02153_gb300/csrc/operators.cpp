@@ -68,7 +68,7 @@ static bool symmetric_kernel(int kernel)
 // Cyclic Jacobi eigen-decomposition of a symmetric n x n matrix A (row-major,
 // destroyed).  On return w holds the eigenvalues in decreasing order and the
 // columns of Q (row-major n x n) the matching orthonormal eigenvectors.
-static void jacobi_eigen(int n, std::vector<double> &A, std::vector<double> &w, std::vector<double> &Q)
+void jacobi_eigen(int n, std::vector<double> &A, std::vector<double> &w, std::vector<double> &Q)
 {
     Q.assign((size_t)n * n, 0.0);
     for (int i = 0; i < n; ++i)

@@ -162,3 +162,20 @@ def test_split3_full_size_uniform_1M(bb, oracle, depth, prec):
     assert rel(got, plain) < 4e-6
     assert oracle.rel_err(got[idx], ref) <= 1e-5
     assert oracle.rel_err(got[idx], direct) <= 1.1 * e_or
+
+
+@pytest.mark.parametrize("depth", [5, 6])
+@pytest.mark.parametrize("prec", ["fp16x3", "tf32x3"])
+def test_clustered_points_visit_only_occupied_tiles(bb, oracle, depth, prec):
+    """Clustered points leave most boxes empty; the tensor-core M2L then visits
+    only the tiles holding occupied targets.  Against the oracle at sampled
+    targets, and against the FP32 form (which computes every tile)."""
+    n = 200_000
+    pts = W.clustered_points(n, seed=83)
+    sig = W.uniform_sigma(n, seed=84).astype(np.float32)
+    got = run(bb, pts, sig, 3, 5, depth, prec, ell=0.3)
+    plain = run(bb, pts, sig, 3, 5, depth, "fp32", ell=0.3)
+    idx = np.sort(np.random.default_rng(85).choice(n, 300, replace=False))
+    ref = oracle.bbfmm(pts, sig.astype(np.float64), 3, 5, depth, ell=0.3, lo=W.UNIT_LO, side=W.UNIT_SIDE, sample=idx)
+    assert oracle.rel_err(got[idx], ref) <= 1e-5
+    assert rel(got, plain) < 4e-6

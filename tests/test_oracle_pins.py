@@ -270,3 +270,46 @@ def test_fmm_multiple_rhs_columns_independent(oracle):
     for c in range(3):
         np.testing.assert_allclose(both[:, c], oracle.bbfmm(x, s[:, c], K_INV_R, p=4, depth=3),
                                    rtol=0, atol=1e-15 * np.abs(both).max())
+
+
+@pytest.mark.parametrize("kid,ell", [(3, 0.2), (1, 1.0), (100, 1.0)])
+def test_kernel_matrix_times_vector_is_direct_sum(oracle, kid, ell):
+    """The dense kernel matrix of the PCA check (Sec. 4.3) applied to a weight
+    vector equals the direct sum, a separate code path."""
+    pts = W.uniform_points(300, seed=91)
+    sig = W.uniform_sigma(300, seed=92)
+    K = oracle.kernel_matrix(pts, kid, ell)
+    assert np.array_equal(K, K.T) or kid == 100       # the test polynomial is not symmetric
+    np.testing.assert_allclose(K @ sig, oracle.direct(pts, pts, sig, kid, ell), rtol=1e-12, atol=1e-10)
+
+
+def test_top_eigenvalues_closed_forms(oracle):
+    """Constant kernel: K = 1 1^T has the single nonzero eigenvalue N.  And
+    exp(-(r/ell)^2) on points spaced 20 ell apart is the identity to 1e-170:
+    every eigenvalue is 1."""
+    pts = W.uniform_points(200, seed=93)
+    w = oracle.top_eigenvalues(pts, 101, 3)
+    np.testing.assert_allclose(w[0], 200.0, rtol=1e-12)
+    assert abs(w[1]) < 1e-10 and abs(w[2]) < 1e-10
+    line = np.zeros((50, 3))
+    line[:, 0] = np.arange(50) * 10.0
+    np.testing.assert_allclose(oracle.top_eigenvalues(line, 4, 5, ell=0.5), np.ones(5), rtol=0, atol=1e-12)
+
+
+def test_rand_eig_exact_on_low_rank_matrices(oracle):
+    """The randomized PCA oracle is exact when the test block spans the range:
+    on a rank-6 PSD matrix with 10 test vectors it returns the 6 nonzero
+    eigenvalues of numpy's dense solver, and eigenvectors with K u = lambda u;
+    on the constant kernel, the single eigenvalue N."""
+    rng = np.random.default_rng(97)
+    A = rng.standard_normal((300, 6))
+    K = A @ A.T
+    omega = rng.standard_normal((10, 300))
+    w, U = oracle.rand_eig(K, omega, 6, power=0)
+    ref = np.linalg.eigvalsh(K)[::-1][:6]
+    np.testing.assert_allclose(w, ref, rtol=1e-10)
+    np.testing.assert_allclose(K @ U, U * w, atol=1e-8 * ref[0])
+    pts = W.uniform_points(150, seed=98)
+    w1, _ = oracle.rand_eig(oracle.kernel_matrix(pts, 101), rng.standard_normal((4, 150)), 2)
+    np.testing.assert_allclose(w1[0], 150.0, rtol=1e-12)
+    assert abs(w1[1]) < 1e-9
