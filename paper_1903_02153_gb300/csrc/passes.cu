@@ -69,121 +69,189 @@ template <int P> struct Smem {
     static constexpr int kDownFloats = kDownFt + 8 * P3;
 };
 
-// M2M of 8 children X ([P3][8]) into one parent (Thm. 2.1 item 1 in tensor
-// form: three 1D passes with the child-to-parent matrices S), scratch Y, Z of
-// [P3][8]; result in out[P3].  Child o has (x, y, z) parity (o & 1, (o >> 1)
-// & 1, o >> 2), its position in Morton order.
-// (XS: row stride of X, e.g. 64 when the 8 children are 8 columns of a
-// [P3][64] array; OS: stride of out)
+// The child-to-parent transfers are tensor products of 1D matrices
+// (Thm. 2.1 item 1): M^parent = sum_o (S_oz (x) S_oy (x) S_ox) M^child_o,
+// with child o = (x, y, z parity) = (o & 1, (o >> 1) & 1, o >> 2), its
+// position in Morton order.  They are applied one axis at a time, and the
+// children that share the remaining axes' matrices are summed as soon as the
+// axis that tells them apart is done (x pass on 8, y pass on 4 pairs, z pass
+// on 2 quadruples: 14 p^4 products instead of 24 p^4).  A thread owns one
+// line of p values along the current axis: it loads the p inputs once and
+// writes the p outputs, so index arithmetic is paid once per line.
+
+// M2M of 8 children X ([P3][8], row stride XS) into one parent out[r * OS];
+// scratch Y [P3][8], Z [P3][4]
 template <int P, int XS = 8, int OS = 1>
 __device__ void m2m8(const InterpTables &T, const float *X, float *Y, float *Z, float *out)
 {
-    constexpr int P3 = P * P * P;
+    constexpr int P2 = P * P;
     const int t = threadIdx.x;
-    for (int q = t; q < 8 * P3; q += kThreads) { // x pass
-        const int o = q & 7, r = q >> 3, i1 = r % P, rest = r / P;
-        float acc = 0.0f;
+    for (int q = t; q < 8 * P2; q += kThreads) { // x pass: line (child o, j2 + P j3)
+        const int o = q & 7, rest = q >> 3;
+        float x[P];
 #pragma unroll
-        for (int j1 = 0; j1 < P; ++j1)
-            acc += T.S[o & 1][i1][j1] * X[(j1 + P * rest) * XS + o];
-        Y[q] = acc;
+        for (int j = 0; j < P; ++j)
+            x[j] = X[(j + P * rest) * XS + o];
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            float a = 0.0f;
+#pragma unroll
+            for (int j = 0; j < P; ++j)
+                a += T.S[o & 1][i][j] * x[j];
+            Y[(i + P * rest) * 8 + o] = a;
+        }
     }
     __syncthreads();
-    for (int q = t; q < 8 * P3; q += kThreads) { // y pass
-        const int o = q & 7, r = q >> 3, i1 = r % P, i2 = (r / P) % P, j3 = r / (P * P);
-        float acc = 0.0f;
+    for (int q = t; q < 4 * P2; q += kThreads) { // y pass: line (oy + 2 oz, i1, j3), x pairs summed
+        const int yz = q & 3, u = q >> 2, i1 = u % P, j3 = u / P;
+        float y[P];
 #pragma unroll
-        for (int j2 = 0; j2 < P; ++j2)
-            acc += T.S[(o >> 1) & 1][i2][j2] * Y[(i1 + P * j2 + P * P * j3) * 8 + o];
-        Z[q] = acc;
+        for (int j = 0; j < P; ++j) {
+            const float *src = Y + (i1 + P * j + P2 * j3) * 8 + 2 * yz;
+            y[j] = src[0] + src[1];
+        }
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            float a = 0.0f;
+#pragma unroll
+            for (int j = 0; j < P; ++j)
+                a += T.S[yz & 1][i][j] * y[j];
+            Z[(i1 + P * i + P2 * j3) * 4 + yz] = a;
+        }
     }
     __syncthreads();
-    for (int r = t; r < P3; r += kThreads) { // z pass, summed over the children
-        const int i12 = r % (P * P), i3 = r / (P * P);
-        float acc = 0.0f;
+    for (int q = t; q < P2; q += kThreads) { // z pass: line i1 + P i2, y pairs summed
+        float z0[P], z1[P];
 #pragma unroll
-        for (int o = 0; o < 8; ++o)
+        for (int j = 0; j < P; ++j) {
+            const float *src = Z + (q + P2 * j) * 4;
+            z0[j] = src[0] + src[1];
+            z1[j] = src[2] + src[3];
+        }
 #pragma unroll
-            for (int j3 = 0; j3 < P; ++j3)
-                acc += T.S[o >> 2][i3][j3] * Z[(i12 + P * P * j3) * 8 + o];
-        out[r * OS] = acc;
+        for (int i = 0; i < P; ++i) {
+            float a = 0.0f;
+#pragma unroll
+            for (int j = 0; j < P; ++j)
+                a += T.S[0][i][j] * z0[j] + T.S[1][i][j] * z1[j];
+            out[(q + P2 * i) * OS] = a;
+        }
     }
     __syncthreads();
 }
 
-// L2L of one parent F (P3) into its 8 children ([P3][8], written), the
-// transpose of m2m8; scratch Y, Z [P3][8].
-// (FS: stride of F; OS: row stride of out, 64 for 8 columns of [P3][64])
-template <int P, int FS = 1, int OS = 8>
+// L2L of one parent F (P3) into its 8 children (out[r * OS + o]), the
+// transpose of m2m8, the children sharing a z (then y) matrix sharing the
+// pass: z pass for 2, y pass for 4, x pass for 8; scratch Y, Z (>= 4 P3 each)
+template <int P, int OS = 8>
 __device__ void l2l8(const InterpTables &T, const float *F, float *Y, float *Z, float *out)
 {
-    constexpr int P3 = P * P * P;
+    constexpr int P2 = P * P, P3 = P2 * P;
     const int t = threadIdx.x;
-    for (int q = t; q < 8 * P3; q += kThreads) { // z pass
-        const int o = q & 7, r = q >> 3, j12 = r % (P * P), i3 = r / (P * P);
-        float acc = 0.0f;
+    for (int q = t; q < 2 * P2; q += kThreads) { // z pass: line (oz, j1 + P j2)
+        const int oz = q & 1, j12 = q >> 1;
+        float f[P];
 #pragma unroll
-        for (int j3 = 0; j3 < P; ++j3)
-            acc += T.S[o >> 2][j3][i3] * F[(j12 + P * P * j3) * FS];
-        Y[q] = acc;
+        for (int j = 0; j < P; ++j)
+            f[j] = F[j12 + P2 * j];
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            float a = 0.0f;
+#pragma unroll
+            for (int j = 0; j < P; ++j)
+                a += T.S[oz][j][i] * f[j];
+            Y[oz * P3 + j12 + P2 * i] = a;
+        }
     }
     __syncthreads();
-    for (int q = t; q < 8 * P3; q += kThreads) { // y pass
-        const int o = q & 7, r = q >> 3, j1 = r % P, i2 = (r / P) % P, i3 = r / (P * P);
-        float acc = 0.0f;
+    for (int q = t; q < 4 * P2; q += kThreads) { // y pass: line (oy + 2 oz, j1, i3)
+        const int yz = q & 3, u = q >> 2, j1 = u % P, i3 = u / P;
+        const float *src = Y + (yz >> 1) * P3 + j1 + P2 * i3;
+        float f[P];
 #pragma unroll
-        for (int j2 = 0; j2 < P; ++j2)
-            acc += T.S[(o >> 1) & 1][j2][i2] * Y[(j1 + P * j2 + P * P * i3) * 8 + o];
-        Z[q] = acc;
+        for (int j = 0; j < P; ++j)
+            f[j] = src[P * j];
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            float a = 0.0f;
+#pragma unroll
+            for (int j = 0; j < P; ++j)
+                a += T.S[yz & 1][j][i] * f[j];
+            Z[yz * P3 + j1 + P * i + P2 * i3] = a;
+        }
     }
     __syncthreads();
-    for (int q = t; q < 8 * P3; q += kThreads) { // x pass
-        const int o = q & 7, r = q >> 3, i1 = r % P, rest = r / P;
-        float acc = 0.0f;
+    for (int q = t; q < 8 * P2; q += kThreads) { // x pass: line (child o, i2 + P i3)
+        const int o = q & 7, rest = q >> 3;
+        const float *src = Z + (o >> 1) * P3 + P * rest;
+        float f[P];
 #pragma unroll
-        for (int j1 = 0; j1 < P; ++j1)
-            acc += T.S[o & 1][j1][i1] * Z[(j1 + P * rest) * 8 + o];
-        out[r * OS + o] = acc;
+        for (int j = 0; j < P; ++j)
+            f[j] = src[j];
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            float a = 0.0f;
+#pragma unroll
+            for (int j = 0; j < P; ++j)
+                a += T.S[o & 1][j][i] * f[j];
+            out[(i + P * rest) * OS + o] = a;
+        }
     }
     __syncthreads();
 }
 
-// L2L of a parent F into its child o only (three 1D passes over P3 values);
-// scratch Y; result in out.
+// L2L of a parent F into its child o only; scratch Y (P3); result in out
+// (which may be F)
 template <int P>
 __device__ void l2l1(const InterpTables &T, const float *F, int o, float *Y, float *out)
 {
-    constexpr int P3 = P * P * P;
+    constexpr int P2 = P * P;
     const int t = threadIdx.x;
-    for (int r = t; r < P3; r += kThreads) { // z pass
-        const int j12 = r % (P * P), i3 = r / (P * P);
-        float acc = 0.0f;
+    for (int q = t; q < P2; q += kThreads) { // z pass: line j1 + P j2
+        float f[P];
 #pragma unroll
-        for (int j3 = 0; j3 < P; ++j3)
-            acc += T.S[o >> 2][j3][i3] * F[j12 + P * P * j3];
-        Y[r] = acc;
+        for (int j = 0; j < P; ++j)
+            f[j] = F[q + P2 * j];
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            float a = 0.0f;
+#pragma unroll
+            for (int j = 0; j < P; ++j)
+                a += T.S[o >> 2][j][i] * f[j];
+            Y[q + P2 * i] = a;
+        }
     }
     __syncthreads();
-    for (int r = t; r < P3; r += kThreads) { // y pass
-        const int j1 = r % P, i2 = (r / P) % P, i3 = r / (P * P);
-        float acc = 0.0f;
+    for (int q = t; q < P2; q += kThreads) { // y pass: line (j1, i3), into out
+        const int j1 = q % P, i3 = q / P;
+        float f[P];
 #pragma unroll
-        for (int j2 = 0; j2 < P; ++j2)
-            acc += T.S[(o >> 1) & 1][j2][i2] * Y[j1 + P * j2 + P * P * i3];
-        out[r] = acc;
+        for (int j = 0; j < P; ++j)
+            f[j] = Y[j1 + P * j + P2 * i3];
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            float a = 0.0f;
+#pragma unroll
+            for (int j = 0; j < P; ++j)
+                a += T.S[(o >> 1) & 1][j][i] * f[j];
+            out[j1 + P * i + P2 * i3] = a;
+        }
     }
     __syncthreads();
-    for (int r = t; r < P3; r += kThreads) { // x pass (in place by rows of P)
-        const int i1 = r % P, rest = r / P;
-        float acc = 0.0f;
+    for (int q = t; q < P2; q += kThreads) { // x pass: line i2 + P i3, in place
+        float f[P];
 #pragma unroll
-        for (int j1 = 0; j1 < P; ++j1)
-            acc += T.S[o & 1][j1][i1] * out[j1 + P * rest];
-        Y[r] = acc;
+        for (int j = 0; j < P; ++j)
+            f[j] = out[P * q + j];
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            float a = 0.0f;
+#pragma unroll
+            for (int j = 0; j < P; ++j)
+                a += T.S[o & 1][j][i] * f[j];
+            out[P * q + i] = a;
+        }
     }
-    __syncthreads();
-    for (int r = t; r < P3; r += kThreads)
-        out[r] = Y[r];
     __syncthreads();
 }
 
@@ -476,9 +544,22 @@ __global__ void __launch_bounds__(kThreads) k_downward(const __grid_constant__ P
         for (int q = t; q < 8 * P3; q += kThreads)
             sMT[q] = 0.0f;
     }
-    for (int q = t; q < 8 * A.r; q += kThreads) {
-        const int o = q & 7, k = q >> 3;
-        load_ft(A, D, 8 * b + o, c, sFt + o, 8, k);
+    {
+        __shared__ int64_t sRow[8]; // F~ row offsets of the 8 leaves
+        if (t < 8) {
+            int x, y, z;
+            demorton3((uint32_t)(8 * b + t), x, y, z);
+            sRow[t] = parity_row(x, y, z, c, 1 << (D - 1), 0, A.R) * A.rp;
+        }
+        __syncthreads();
+        for (int q = t; q < 8 * A.r; q += kThreads) {
+            const int o = q & 7, k = q >> 3;
+            const float *src = A.Ft[D] + sRow[o] + k;
+            float v = __ldg(src);
+            for (int g = 1; g < A.nslices; ++g)
+                v += __ldg(src + g * A.slice[D]);
+            sFt[k * 8 + o] = v;
+        }
     }
     __syncthreads();
     {
