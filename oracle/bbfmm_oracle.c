@@ -484,16 +484,16 @@ static void or_l2l(or_tree *t, int l /* child level */)
 }
 
 /* L2P: phi_i = sum_j F^alpha_j L_p(x*_j, x_i) for a target x_i in leaf alpha. */
-static void or_l2p(const or_tree *t, int64_t i, double *out /* nrhs */)
+static void or_l2p(const or_tree *t, const double *x, int64_t bi, double *out /* nrhs */)
 {
     int D = t->D, p = t->p, p3 = p * p * p;
     double h = t->side / (double)((int64_t)1 << D);
-    int64_t bi = t->leaf_of[i], a, b, c;
+    int64_t a, b, c;
     or_unlex(D, bi, &a, &b, &c);
     double ctr[3], xs[3], L[1000];
     or_center(t, D, a, b, c, ctr);
     for (int d = 0; d < 3; ++d)
-        xs[d] = 2.0 * (t->pts[3 * i + d] - ctr[d]) / h;
+        xs[d] = 2.0 * (x[d] - ctr[d]) / h;
     or_lagrange_3d(p, t->s, xs, L);
     const double *F = t->F[D] + bi * (int64_t)t->nrhs * p3;
     for (int r = 0; r < t->nrhs; ++r) {
@@ -507,19 +507,18 @@ static void or_l2p(const or_tree *t, int64_t i, double *out /* nrhs */)
 /* ------------------------------------------------------------------------- */
 /* Stage 4, near field (Sec. 2.2 item 4):
  *   phi_i += sum_{beta in N(alpha)} sum_{y_j in beta} K(x_i, y_j) sigma_j. */
-static void or_p2p(const or_tree *t, int64_t i, double *out /* nrhs */)
+static void or_p2p(const or_tree *t, const double *x, int64_t bi, double *out /* nrhs */)
 {
     int D = t->D;
-    int64_t bi = t->leaf_of[i], a, b, c, nb[27 * 3];
+    int64_t a, b, c, nb[27 * 3];
     or_unlex(D, bi, &a, &b, &c);
     int nn = oracle_neighbors(D, a, b, c, nb);
     for (int k = 0; k < nn; ++k) {
         int64_t bj = or_lex(D, nb[3 * k], nb[3 * k + 1], nb[3 * k + 2]);
         for (int64_t q = t->lstart[bj]; q < t->lstart[bj + 1]; ++q) {
             int64_t j = t->order[q];
-            double K = or_kernel(t->kid, t->ell, t->pts[3 * i] - t->pts[3 * j],
-                                 t->pts[3 * i + 1] - t->pts[3 * j + 1],
-                                 t->pts[3 * i + 2] - t->pts[3 * j + 2]);
+            double K = or_kernel(t->kid, t->ell, x[0] - t->pts[3 * j], x[1] - t->pts[3 * j + 1],
+                                 x[2] - t->pts[3 * j + 2]);
             for (int r = 0; r < t->nrhs; ++r)
                 out[r] += K * t->sigma[(int64_t)r * t->n + j];
         }
@@ -527,9 +526,62 @@ static void or_p2p(const or_tree *t, int64_t i, double *out /* nrhs */)
 }
 
 /* ------------------------------------------------------------------------- */
-/* The whole FMM (Alg. 1 without the OpenMP task structure).
- *
- * pts: n x 3 row-major (targets = sources), sigma: n x nrhs column-major.
+/* The whole FMM (Alg. 1 without the OpenMP task structure), for targets
+ * tx[q] (ntgt x 3 row-major) lying in leaves tleaf[q] of the source tree. */
+static int or_run(or_tree *t, int64_t ntgt, const double *tx, const int64_t *tleaf, double *phi,
+                  double *M_dump, double *F_dump, double *times);
+
+/* Bin the sources of t into leaves (FMMDistribute, Sec. 3): a counting sort
+ * keeps increasing point ids inside each leaf. */
+static void or_bin_sources(or_tree *t)
+{
+    int D = t->D;
+    int64_t n = t->n, nleaf = or_nbox(D);
+    double hD = t->side / (double)((int64_t)1 << D);
+    t->leaf_of = (int64_t *)malloc(sizeof(int64_t) * n);
+    t->lstart = (int64_t *)calloc(nleaf + 1, sizeof(int64_t));
+    t->order = (int64_t *)malloc(sizeof(int64_t) * n);
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t a = or_cell(t->pts[3 * i], t->lo[0], hD, D);
+        int64_t b = or_cell(t->pts[3 * i + 1], t->lo[1], hD, D);
+        int64_t c = or_cell(t->pts[3 * i + 2], t->lo[2], hD, D);
+        t->leaf_of[i] = or_lex(D, a, b, c);
+        t->lstart[t->leaf_of[i] + 1]++;
+    }
+    for (int64_t k = 0; k < nleaf; ++k)
+        t->lstart[k + 1] += t->lstart[k];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * nleaf);
+    memcpy(fill, t->lstart, sizeof(int64_t) * nleaf);
+    for (int64_t i = 0; i < n; ++i)
+        t->order[fill[t->leaf_of[i]]++] = i;
+    free(fill);
+}
+
+static int or_setup(or_tree *t, int64_t n, const double *pts, const double *sigma, int nrhs, int kid, double ell,
+                    int p, int D, const double *lo, double side)
+{
+    if (n < 1 || nrhs < 1 || nrhs > 256 || p < 2 || p > 10 || D < 0 || D > 8 || !(side > 0.0))
+        return -1;
+    memset(t, 0, sizeof(*t));
+    t->D = D;
+    t->p = p;
+    t->nrhs = nrhs;
+    t->kid = kid;
+    t->ell = ell;
+    t->lo[0] = lo[0];
+    t->lo[1] = lo[1];
+    t->lo[2] = lo[2];
+    t->side = side;
+    t->n = n;
+    t->pts = pts;
+    t->sigma = sigma;
+    t->s = (double *)malloc(sizeof(double) * p);
+    oracle_cheb_nodes(p, t->s);
+    or_bin_sources(t);
+    return 0;
+}
+
+/* pts: n x 3 row-major (targets = sources), sigma: n x nrhs column-major.
  * lo[3], side: the cubical domain.  p: Chebyshev nodes per axis (2..10).
  * D: depth, 8^D leaves.  nsample >= 0 with sample != NULL: phi is produced only
  * for those targets (phi: nsample x nrhs column-major); the far field is then
@@ -543,51 +595,53 @@ int oracle_bbfmm(int64_t n, const double *pts, const double *sigma, int nrhs, in
                  int p, int D, const double *lo, double side, int64_t nsample, const int64_t *sample,
                  double *phi, double *M_dump, double *F_dump, double *times)
 {
-    if (n < 1 || nrhs < 1 || nrhs > 256 || p < 2 || p > 10 || D < 0 || D > 8 || !(side > 0.0))
-        return -1;
     or_tree t;
-    memset(&t, 0, sizeof(t));
-    t.D = D;
-    t.p = p;
-    t.nrhs = nrhs;
-    t.kid = kid;
-    t.ell = ell;
-    t.lo[0] = lo[0];
-    t.lo[1] = lo[1];
-    t.lo[2] = lo[2];
-    t.side = side;
-    t.n = n;
-    t.pts = pts;
-    t.sigma = sigma;
-    int p3 = p * p * p;
-    double tm[4] = {0, 0, 0, 0}, t0;
+    if (or_setup(&t, n, pts, sigma, nrhs, kid, ell, p, D, lo, side) != 0)
+        return -1;
+    int64_t ntgt = nsample >= 0 && sample ? nsample : n;
+    double *tx = (double *)malloc(sizeof(double) * 3 * ntgt);
+    int64_t *tleaf = (int64_t *)malloc(sizeof(int64_t) * ntgt);
+    for (int64_t q = 0; q < ntgt; ++q) {
+        int64_t i = nsample >= 0 && sample ? sample[q] : q;
+        memcpy(tx + 3 * q, pts + 3 * i, sizeof(double) * 3);
+        tleaf[q] = t.leaf_of[i];
+    }
+    int rc = or_run(&t, ntgt, tx, tleaf, phi, M_dump, F_dump, times);
+    free(tx);
+    free(tleaf);
+    return rc;
+}
 
-    t.s = (double *)malloc(sizeof(double) * p);
-    oracle_cheb_nodes(p, t.s);
-
-    /* FMMDistribute (Sec. 3): bin every point into its leaf; a counting sort
-     * keeps increasing point ids inside each leaf. */
-    int64_t nleaf = or_nbox(D);
+/* Separate targets (Sec. 1: the target and source sets may differ; here
+ * they share the domain, which must contain both): sources src (ns x 3) with
+ * weights sigma (ns x nrhs column-major), targets tgt (nt x 3); phi: nt x nrhs
+ * column-major.  Every other argument as in oracle_bbfmm.  Returns 0, or -1
+ * on invalid arguments. */
+int oracle_bbfmm_targets(int64_t ns, const double *src, const double *sigma, int nrhs, int kid, double ell,
+                         int p, int D, const double *lo, double side, int64_t nt, const double *tgt,
+                         double *phi, double *times)
+{
+    or_tree t;
+    if (nt < 1 || or_setup(&t, ns, src, sigma, nrhs, kid, ell, p, D, lo, side) != 0)
+        return -1;
     double hD = side / (double)((int64_t)1 << D);
-    t.leaf_of = (int64_t *)malloc(sizeof(int64_t) * n);
-    t.lstart = (int64_t *)calloc(nleaf + 1, sizeof(int64_t));
-    t.order = (int64_t *)malloc(sizeof(int64_t) * n);
-    for (int64_t i = 0; i < n; ++i) {
-        int64_t a = or_cell(pts[3 * i], lo[0], hD, D);
-        int64_t b = or_cell(pts[3 * i + 1], lo[1], hD, D);
-        int64_t c = or_cell(pts[3 * i + 2], lo[2], hD, D);
-        t.leaf_of[i] = or_lex(D, a, b, c);
-        t.lstart[t.leaf_of[i] + 1]++;
-    }
-    for (int64_t k = 0; k < nleaf; ++k)
-        t.lstart[k + 1] += t.lstart[k];
-    {
-        int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * nleaf);
-        memcpy(fill, t.lstart, sizeof(int64_t) * nleaf);
-        for (int64_t i = 0; i < n; ++i)
-            t.order[fill[t.leaf_of[i]]++] = i;
-        free(fill);
-    }
+    int64_t *tleaf = (int64_t *)malloc(sizeof(int64_t) * nt);
+    for (int64_t q = 0; q < nt; ++q)
+        tleaf[q] = or_lex(D, or_cell(tgt[3 * q], lo[0], hD, D), or_cell(tgt[3 * q + 1], lo[1], hD, D),
+                          or_cell(tgt[3 * q + 2], lo[2], hD, D));
+    int rc = or_run(&t, nt, tgt, tleaf, phi, NULL, NULL, times);
+    free(tleaf);
+    return rc;
+}
+
+static int or_run(or_tree *tp, int64_t ntgt, const double *tx, const int64_t *tleaf, double *phi,
+                  double *M_dump, double *F_dump, double *times)
+{
+    or_tree t = *tp;
+    int D = t.D, p = t.p, nrhs = t.nrhs;
+    int p3 = p * p * p;
+    int64_t nleaf = or_nbox(D);
+    double tm[4] = {0, 0, 0, 0}, t0;
 
     t.M = (double **)calloc(D + 1, sizeof(double *));
     t.F = (double **)calloc(D + 1, sizeof(double *));
@@ -608,11 +662,9 @@ int oracle_bbfmm(int64_t n, const double *pts, const double *sigma, int nrhs, in
                 or_unlex(l + 1, k, &a, &b, &c);
                 t.nonempty[l][or_lex(l, a >> 1, b >> 1, c >> 1)] = 1;
             }
-    int64_t ntgt = nsample >= 0 && sample ? nsample : n;
     for (int64_t q = 0; q < ntgt; ++q) {
-        int64_t i = nsample >= 0 && sample ? sample[q] : q;
         int64_t a, b, c;
-        or_unlex(D, t.leaf_of[i], &a, &b, &c);
+        or_unlex(D, tleaf[q], &a, &b, &c);
         for (int l = D; l >= 0; --l)
             t.needed[l][or_lex(l, a >> (D - l), b >> (D - l), c >> (D - l))] = 1;
     }
@@ -637,10 +689,9 @@ int oracle_bbfmm(int64_t n, const double *pts, const double *sigma, int nrhs, in
     int64_t q;
 #pragma omp parallel for schedule(dynamic, 256)
     for (q = 0; q < ntgt; ++q) {
-        int64_t i = nsample >= 0 && sample ? sample[q] : q;
         double out[256];
         if (D >= 2) {
-            or_l2p(&t, i, out);
+            or_l2p(&t, tx + 3 * q, tleaf[q], out);
         } else {
             for (int r = 0; r < nrhs; ++r)
                 out[r] = 0.0;
@@ -654,11 +705,10 @@ int oracle_bbfmm(int64_t n, const double *pts, const double *sigma, int nrhs, in
     t0 = or_now();
 #pragma omp parallel for schedule(dynamic, 256)
     for (q = 0; q < ntgt; ++q) {
-        int64_t i = nsample >= 0 && sample ? sample[q] : q;
         double out[256];
         for (int r = 0; r < nrhs; ++r)
             out[r] = 0.0;
-        or_p2p(&t, i, out);
+        or_p2p(&t, tx + 3 * q, tleaf[q], out);
         for (int r = 0; r < nrhs; ++r)
             phi[(int64_t)r * ntgt + q] += out[r];
     }

@@ -56,6 +56,8 @@ def lib():
             L.oracle_bbfmm.argtypes = [i64, dp, dp, i32, i32, f64, i32, i32, dp, f64,
                                        i64, lp, dp, dp, dp, dp]
             L.oracle_bbfmm.restype = i32
+            L.oracle_bbfmm_targets.argtypes = [i64, dp, dp, i32, i32, f64, i32, i32, dp, f64, i64, dp, dp, dp]
+            L.oracle_bbfmm_targets.restype = i32
             L.oracle_cheb_nodes.argtypes = [i32, dp]
             L.oracle_lagrange_1d.argtypes = [i32, dp, f64, dp]
             L.oracle_neighbors.argtypes = [i32, i64, i64, i64, lp]
@@ -235,6 +237,25 @@ def bbfmm(points, sigma, kid, p, depth, ell=1.0, lo=None, side=None, sample=None
     if times:
         extra.append(tm)
     return (res, *extra) if extra else res
+
+
+def bbfmm_targets(sources, sigma, targets, kid, p, depth, ell=1.0, lo=None, side=None):
+    """FP64 black-box FMM with a target set apart from the sources (Sec. 1:
+    the two sets may differ).  Both must lie in the cubical domain (default:
+    the bounding cube of their union).  Returns phi at the targets, (nt,) or
+    (nt, nrhs)."""
+    src = _f64c(sources)
+    tgt = _f64c(targets)
+    s, nrhs = _sigma_colmajor(sigma, src.shape[0])
+    if lo is None or side is None:
+        lo, side = bounding_cube(np.concatenate([src, tgt]))
+    lo = _f64c(lo, (3,))
+    phi = np.zeros((tgt.shape[0], nrhs), dtype=np.float64, order="F")
+    rc = lib().oracle_bbfmm_targets(src.shape[0], _dp(src), _dp(s), nrhs, kid, float(ell), p, depth, _dp(lo),
+                                    float(side), tgt.shape[0], _dp(tgt), _dp(phi), None)
+    if rc != 0:
+        raise ValueError("oracle_bbfmm_targets rejected its arguments")
+    return phi[:, 0] if np.ndim(sigma) == 1 else phi
 
 
 def rel_err(approx, exact):

@@ -313,3 +313,22 @@ def test_rand_eig_exact_on_low_rank_matrices(oracle):
     w1, _ = oracle.rand_eig(oracle.kernel_matrix(pts, 101), rng.standard_normal((4, 150)), 2)
     np.testing.assert_allclose(w1[0], 150.0, rtol=1e-12)
     assert abs(w1[1]) < 1e-9
+
+
+def test_fmm_separate_targets(oracle):
+    """Targets apart from the sources (Sec. 1).  Passing the sources as
+    targets reproduces the one-set run bitwise; the polynomial kernel is
+    reproduced exactly at separate targets; depth 1 is the direct sum."""
+    src = W.uniform_points(3000, seed=102)
+    sig = W.uniform_sigma(3000, seed=103)
+    tgt = W.clustered_points(1500, seed=104)
+    lo, side = np.zeros(3), 1.0
+    same = oracle.bbfmm_targets(src, sig, src, oracle.K_INV_R, 4, 3, lo=lo, side=side)
+    ref = oracle.bbfmm(src, sig, oracle.K_INV_R, 4, 3, lo=lo, side=side)
+    assert np.array_equal(same, ref)
+    poly = oracle.bbfmm_targets(src, sig, tgt, oracle.K_POLY, 4, 3, lo=lo, side=side)
+    np.testing.assert_allclose(poly, oracle.direct(tgt, src, sig, oracle.K_POLY), rtol=1e-10, atol=1e-9)
+    d1 = oracle.bbfmm_targets(src, sig, tgt, oracle.K_INV_R, 4, 1, lo=lo, side=side)
+    np.testing.assert_allclose(d1, oracle.direct(tgt, src, sig, oracle.K_INV_R), rtol=1e-10, atol=1e-10)
+    far = oracle.bbfmm_targets(src, sig, tgt, oracle.K_INV_R, 6, 3, lo=lo, side=side)
+    assert oracle.rel_err(far, oracle.direct(tgt, src, sig, oracle.K_INV_R)) < 1e-5
