@@ -85,7 +85,7 @@ typedef struct {
 } bbfmm_opts;
 
 typedef struct {
-    int64_t n;          /* points */
+    int64_t n;          /* points (the sources of a bbfmm_plan_targets plan) */
     int depth;          /* tree depth D: 8^D leaves, M2L on levels 2..D */
     int order;          /* Chebyshev nodes per axis p */
     int rank;           /* rank r of the compressed M2L operators */
@@ -94,11 +94,12 @@ typedef struct {
     int max_nrhs;
     double lo[3], side; /* domain actually used */
     int64_t device_bytes; /* device memory held by the plan */
-    int64_t nonempty_leaves;
-    int64_t max_leaf_points;
+    int64_t nonempty_leaves;  /* leaves holding sources */
+    int64_t max_leaf_points;  /* most sources in one leaf */
     int64_t p2p_pairs;  /* near-field kernel evaluations per right-hand side */
     int64_t m2l_pairs;  /* M2L translations per right-hand side (dense grid) */
-    int reserved[8];
+    int64_t n_targets;  /* targets (= n unless built by bbfmm_plan_targets) */
+    int reserved[6];
 } bbfmm_info;
 
 /* Fill *opts with the defaults listed above. */
@@ -124,9 +125,28 @@ int bbfmm_plan(const double *points, int64_t n, int kernel_id, int cheb_order, i
                const bbfmm_opts *opts, void *stream, bbfmm_plan_t *out);
 
 /*
+ * bbfmm_plan_targets: a plan whose targets x_i are a point set of their own,
+ * apart from the sources y_j (Sec. 1: f(x_i) = sum_j K(x_i, y_j) sigma_j
+ * with x and y different sets).  Both sets are binned into the one tree of
+ * the domain (given in opts, else the bounding cube of both sets); the upward
+ * pass runs over the sources, the downward pass and the near field over the
+ * targets, and the M2L visits the target boxes that hold targets.  A target
+ * at distance 0 from a source follows the r = 0 convention of the kernel.
+ *   sources: ns x 3 row-major FP64, host or device; copied.  1 <= ns < 2^31.
+ *   targets: nt x 3 row-major FP64, host or device; copied.  1 <= nt < 2^31.
+ *   other arguments and errors as for bbfmm_plan.
+ * bbfmm_matvec on such a plan reads sigma as ns x nrhs and writes phi as
+ * nt x nrhs; bbfmm_get_leaf_cells reports the sources; bbfmm_rand_eig
+ * rejects it (EINVAL).
+ */
+int bbfmm_plan_targets(const double *sources, int64_t ns, const double *targets, int64_t nt, int kernel_id,
+                       int cheb_order, int depth, const bbfmm_opts *opts, void *stream, bbfmm_plan_t *out);
+
+/*
  * bbfmm_matvec: phi = K_hat sigma (Sec. 2.2, all four stages).
- *   sigma: n x nrhs column-major FP32, host or device; read only.
- *   phi:   n x nrhs column-major FP32, host or device; overwritten.
+ *   sigma: n x nrhs column-major FP32 (n sources), host or device; read only.
+ *   phi:   nt x nrhs column-major FP32 (nt targets; nt = n unless the plan
+ *          came from bbfmm_plan_targets), host or device; overwritten.
  *   nrhs:  1..opts.max_nrhs of the plan.
  * Device buffers: the call only enqueues work on `stream`.  Host buffers: the
  * call copies sigma in and phi out through the plan's device buffers on

@@ -30,7 +30,7 @@ PRECISIONS = {"fp32": BBFMM_PREC_FP32, "tf32": BBFMM_PREC_TF32, "tf32x3": BBFMM_
 EXPORTED = ["bbfmm_default_opts", "bbfmm_plan", "bbfmm_matvec", "bbfmm_destroy",
             "bbfmm_last_error", "bbfmm_plan_info", "bbfmm_get_coefficients",
             "bbfmm_get_leaf_cells", "bbfmm_stage_times", "bbfmm_set_timing", "bbfmm_status",
-            "bbfmm_sort_points_static", "bbfmm_rand_eig"]
+            "bbfmm_sort_points_static", "bbfmm_rand_eig", "bbfmm_plan_targets"]
 
 
 class bbfmm_opts(ctypes.Structure):
@@ -48,7 +48,7 @@ class bbfmm_info(ctypes.Structure):
                 ("max_nrhs", ctypes.c_int), ("lo", ctypes.c_double * 3), ("side", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("nonempty_leaves", ctypes.c_int64),
                 ("max_leaf_points", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64),
-                ("m2l_pairs", ctypes.c_int64), ("reserved", ctypes.c_int * 8)]
+                ("m2l_pairs", ctypes.c_int64), ("n_targets", ctypes.c_int64), ("reserved", ctypes.c_int * 6)]
 
 
 class BBFMMError(RuntimeError):
@@ -97,6 +97,9 @@ def lib():
             L.bbfmm_sort_points_static.restype = i32
             L.bbfmm_rand_eig.argtypes = [vp, vp, i32, i32, i32, ctypes.POINTER(f64), vp, vp]
             L.bbfmm_rand_eig.restype = i32
+            L.bbfmm_plan_targets.argtypes = [vp, i64, vp, i64, i32, i32, i32, ctypes.POINTER(bbfmm_opts), vp,
+                                             ctypes.POINTER(vp)]
+            L.bbfmm_plan_targets.restype = i32
             _lib = L
     return _lib
 
@@ -154,9 +157,20 @@ def bbfmm_plan(points, kernel_id, cheb_order, depth, opts=None, stream=None):
     return h
 
 
+def bbfmm_plan_targets(sources, targets, kernel_id, cheb_order, depth, opts=None, stream=None):
+    """sources (ns, 3), targets (nt, 3): float64 (torch CUDA tensors or
+    numpy).  Returns a handle whose matvec maps ns weights to nt values."""
+    h = ctypes.c_void_p()
+    _check(lib().bbfmm_plan_targets(_ptr(sources), int(sources.shape[0]), _ptr(targets), int(targets.shape[0]),
+                                    int(kernel_id), int(cheb_order), int(depth),
+                                    ctypes.byref(opts) if opts is not None else None, _stream(stream),
+                                    ctypes.byref(h)))
+    return h
+
+
 def bbfmm_matvec(plan, sigma, phi, nrhs=1, stream=None):
-    """sigma, phi: n x nrhs column-major float32 (a torch tensor of shape
-    (nrhs, n), or numpy arrays); phi is overwritten."""
+    """sigma: ns x nrhs, phi: nt x nrhs column-major float32 (torch tensors
+    of shape (nrhs, n), or numpy arrays); phi is overwritten."""
     return _check(lib().bbfmm_matvec(plan, _ptr(sigma), _ptr(phi), int(nrhs), _stream(stream)))
 
 
@@ -236,11 +250,13 @@ STAGES = ["gather", "upward", "m2l", "downward", "l2p", "p2p", "combine", "total
 
 class Plan:
     """Owning wrapper: ``Plan(points, kernel, p, depth, ...)``, then
-    ``plan.matvec(sigma)`` with sigma a CUDA tensor (n,) or (nrhs, n)."""
+    ``plan.matvec(sigma)`` with sigma a CUDA tensor (n,) or (nrhs, n).  With
+    ``targets`` (nt, 3) the points are the sources and matvec returns the
+    values at the targets, (nt,) or (nrhs, nt)."""
 
     def __init__(self, points, kernel, order, depth, ell=1.0, svd_eps=1e-7, precision="fp32",
                  domain=None, max_nrhs=1, stream=None, split_accumulate=True, use_graph=True,
-                 keep_coefficients=False):
+                 keep_coefficients=False, targets=None):
         import torch
         o = bbfmm_default_opts()
         o.split_accumulate = 1 if split_accumulate else 0
@@ -256,14 +272,19 @@ class Plan:
             for d in range(3):
                 o.lo[d] = float(lo[d])
             o.side = float(side)
-        if isinstance(points, np.ndarray):
-            points = np.ascontiguousarray(points, dtype=np.float64)
-        elif points.dtype != torch.float64:
-            points = points.to(torch.float64)
+        def f64(x):
+            if isinstance(x, np.ndarray):
+                return np.ascontiguousarray(x, dtype=np.float64)
+            return x.to(torch.float64).contiguous()
+        points = f64(points)
         self.n = int(points.shape[0])
+        self.nt = self.n if targets is None else int(targets.shape[0])
         self.order = order
         self.depth = depth
-        self.handle = bbfmm_plan(points, kernel, order, depth, o, stream)
+        if targets is None:
+            self.handle = bbfmm_plan(points, kernel, order, depth, o, stream)
+        else:
+            self.handle = bbfmm_plan_targets(points, f64(targets), kernel, order, depth, o, stream)
 
     def info(self):
         return bbfmm_plan_info(self.handle)
@@ -273,7 +294,8 @@ class Plan:
         nrhs = 1 if sigma.dim() == 1 else int(sigma.shape[0])
         sigma = sigma.contiguous()
         if out is None:
-            out = torch.empty_like(sigma)
+            shape = (self.nt,) if sigma.dim() == 1 else (nrhs, self.nt)
+            out = torch.empty(shape, dtype=torch.float32, device=sigma.device)
         bbfmm_matvec(self.handle, sigma, out, nrhs, stream)
         return out
 

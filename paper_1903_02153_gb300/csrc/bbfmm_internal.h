@@ -171,18 +171,23 @@ struct Stage { // indices into Plan::ev
 };
 
 struct bbfmm_plan_impl {
-    int64_t n = 0;
+    int64_t n = 0;         // sources
+    int64_t nt = 0;        // targets (= n when the targets are the sources)
+    bool separate = false; // targets are a point set of their own
     int D = 0, p = 0, p3 = 0, kernel = 0, precision = 0, max_nrhs = 1;
     double ell = 1.0, lo[3] = {0, 0, 0}, side = 1.0, eps = 1e-7;
     int device = 0;
     bool split_acc = true; // 3-pass tensor-core M2L: separate correction accumulator
     int m2l_groups = 1;    // offset groups per M2L tile (partial slices of F~)
 
-    // tree
+    // tree: sources, and the targets (the same arrays unless separate)
     float4 *pts = nullptr;
     int *perm = nullptr;
     int *leaf_off = nullptr;
-    int4 *chunks = nullptr;
+    float4 *tpts = nullptr;
+    int *tperm = nullptr;
+    int *tleaf_off = nullptr;
+    int4 *chunks = nullptr; // near-field work items over the target leaves
     int nchunks = 0;
     int64_t nonempty_leaves = 0, max_leaf = 0, p2p_pairs = 0, m2l_pairs = 0;
 
@@ -237,12 +242,15 @@ struct bbfmm_plan_impl {
 // indexed by level
 struct PassArgs {
     InterpTables T;
-    const float4 *pts;          // leaf-local coordinates, tree order
-    const int *off;             // leaf start offsets, 8^D + 1
+    const float4 *pts;          // sources: leaf-local coordinates, tree order
+    const int *off;             // sources: leaf start offsets, 8^D + 1
     int64_t n;
+    const float4 *tpts;         // targets: leaf-local coordinates, tree order
+    const int *toff;            // targets: leaf start offsets
+    int64_t nt;
     int D, nrhs, R, r, rp, p3p; // R = max_nrhs (row stride of M~ / F~)
     const float *sig;           // upward: n x nrhs weights in tree order
-    float *phi;                 // downward: n x nrhs far field in tree order
+    float *phi;                 // downward: nt x nrhs far field in target tree order
     float *M[kMaxDepth + 1];    // Morton [box][nrhs][p^3]; leaf level used only with keep
     float *Mt[kMaxDepth + 1], *Mt_hi[kMaxDepth + 1], *Mt_lo[kMaxDepth + 1];
     const float *Ft[kMaxDepth + 1];
@@ -319,9 +327,21 @@ int m2l_groups_for(int D, int nrhs, int precision, int r, int64_t active_tiles);
 void m2l_active_tiles(int D, int precision, const std::vector<uint8_t> &leaf_occ, std::vector<int4> &tiles,
                       int *count);
 // p2p.cu
-cudaError_t launch_p2p(const float4 *pts, const float *sig, const int *leaf_off, const int4 *chunks,
-                       int nchunks, int64_t n, int D, int kernel, double ell, double h, int nrhs,
-                       float *phi_near, cudaStream_t s);
+// targets: tree-order coordinates and the work items over their leaves;
+// sources: tree-order coordinates, weights (ns x nrhs) and leaf offsets
+struct P2PArgs {
+    const float4 *tpts;
+    const int4 *chunks;
+    int nchunks;
+    int64_t nt;
+    const float4 *spts;
+    const float *sig;
+    const int *soff;
+    int64_t ns;
+    int D;
+};
+cudaError_t launch_p2p(const P2PArgs &A, int kernel, double ell, double h, int nrhs, float *phi_near,
+                       cudaStream_t s);
 
 } // namespace bbfmm
 

@@ -268,22 +268,12 @@ static int64_t m2l_pairs_level(int l)
     return sa * sa * sa - sb * sb * sb;
 }
 
-static int plan_build(bbfmm_plan_impl *P, const double *points, cudaStream_t s)
+static int plan_build(bbfmm_plan_impl *P, const double *points, const double *targets, cudaStream_t s)
 {
-    const int64_t n = P->n;
+    const int64_t n = P->n, nt = P->nt;
     const int D = P->D;
     const int64_t nleaf = 1LL << (3 * D);
     CUDA_TRY(cudaGetDevice(&P->device));
-
-    // points on the device (FP64)
-    double *dpts = nullptr;
-    bool own_pts = !is_device_ptr(points);
-    if (own_pts) {
-        CUDA_TRY(cudaMalloc(&dpts, sizeof(double) * 3 * n));
-        CUDA_TRY(cudaMemcpyAsync(dpts, points, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
-    } else {
-        dpts = const_cast<double *>(points);
-    }
     struct Tmp {
         std::vector<void *> v;
         ~Tmp()
@@ -292,8 +282,6 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, cudaStream_t s)
                 cudaFree(p);
         }
     } tmp;
-    if (own_pts)
-        tmp.v.push_back(dpts);
     auto talloc = [&](void **ptr, int64_t bytes) -> int {
         cudaError_t e = cudaMalloc(ptr, (size_t)std::max<int64_t>(bytes, 16));
         if (e != cudaSuccess) {
@@ -303,23 +291,40 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, cudaStream_t s)
         tmp.v.push_back(*ptr);
         return BBFMM_OK;
     };
+    // point sets on the device (FP64)
+    auto upload = [&](const double *h, int64_t cnt, double **d) -> int {
+        if (is_device_ptr(h)) {
+            *d = const_cast<double *>(h);
+            return BBFMM_OK;
+        }
+        PTRY(talloc((void **)d, sizeof(double) * 3 * cnt));
+        CUDA_TRY(cudaMemcpyAsync(*d, h, sizeof(double) * 3 * cnt, cudaMemcpyHostToDevice, s));
+        return BBFMM_OK;
+    };
+    double *dpts = nullptr, *dtgt = nullptr;
+    PTRY(upload(points, n, &dpts));
+    if (P->separate)
+        PTRY(upload(targets, nt, &dtgt));
 
-    // domain
+    // domain: the given cube, or the bounding cube of all points
     unsigned long long *mm = nullptr;
     int *bad = nullptr;
     PTRY(talloc((void **)&mm, 6 * 8));
     PTRY(talloc((void **)&bad, 16));
-    CUDA_TRY(cudaMemsetAsync(bad, 0, 16, s));
     if (P->side <= 0.0) {
-        CUDA_TRY(launch_domain_minmax(dpts, n, reinterpret_cast<double *>(mm), s));
-        unsigned long long h[6];
-        CUDA_TRY(cudaMemcpyAsync(h, mm, sizeof(h), cudaMemcpyDeviceToHost, s));
-        CUDA_TRY(cudaStreamSynchronize(s));
-        double v[6];
-        for (int k = 0; k < 6; ++k) {
-            unsigned long long e = h[k];
-            unsigned long long b = (e >> 63) ? (e & ~0x8000000000000000ull) : ~e;
-            memcpy(&v[k], &b, 8);
+        double v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        for (int set = 0; set < (P->separate ? 2 : 1); ++set) {
+            CUDA_TRY(launch_domain_minmax(set ? dtgt : dpts, set ? nt : n, reinterpret_cast<double *>(mm), s));
+            unsigned long long h[6];
+            CUDA_TRY(cudaMemcpyAsync(h, mm, sizeof(h), cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaStreamSynchronize(s));
+            for (int k = 0; k < 6; ++k) {
+                unsigned long long e = h[k];
+                unsigned long long b = (e >> 63) ? (e & ~0x8000000000000000ull) : ~e;
+                double x;
+                memcpy(&x, &b, 8);
+                v[k] = k < 3 ? std::min(v[k], x) : std::max(v[k], x);
+            }
         }
         double side = 0.0;
         for (int d = 0; d < 3; ++d) {
@@ -331,50 +336,71 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, cudaStream_t s)
         P->side = side > 0.0 ? side : 1.0;
     }
 
-    // leaf binning and Morton sort
+    // leaf binning and Morton sort of one point set
+    const int64_t nmax = std::max(n, nt);
     uint32_t *keys = nullptr, *keys2 = nullptr;
     int *vals = nullptr, *vals2 = nullptr, *scratch = nullptr;
-    PTRY(talloc((void **)&keys, 4 * n));
-    PTRY(talloc((void **)&keys2, 4 * n));
-    PTRY(talloc((void **)&vals, 4 * n));
-    PTRY(talloc((void **)&vals2, 4 * n));
-    int64_t sc = std::max(radix_sort_scratch_ints(n), 2 * (nleaf + 1) + scan_scratch_ints(nleaf + 1));
+    PTRY(talloc((void **)&keys, 4 * nmax));
+    PTRY(talloc((void **)&keys2, 4 * nmax));
+    PTRY(talloc((void **)&vals, 4 * nmax));
+    PTRY(talloc((void **)&vals2, 4 * nmax));
+    int64_t sc = std::max(radix_sort_scratch_ints(nmax), 2 * (nleaf + 1) + scan_scratch_ints(nleaf + 1));
     PTRY(talloc((void **)&scratch, 4 * sc));
-    CUDA_TRY(launch_bin_points(dpts, n, P->lo, P->side, D, keys, vals, bad, s));
-    int hbad = 0;
-    CUDA_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
-    if (hbad)
-        return fail(BBFMM_EINVAL, "points contain NaN/inf coordinates or lie outside the domain");
-    CUDA_TRY(radix_sort_pairs(keys, vals, keys2, vals2, n, 3 * D, scratch, sc, s));
-    PTRY(plan_alloc(P, (void **)&P->leaf_off, 4 * (nleaf + 1), false, s));
-    CUDA_TRY(launch_leaf_offsets(keys, n, nleaf, P->leaf_off, s));
-    PTRY(plan_alloc(P, (void **)&P->pts, 16 * n, false, s));
-    PTRY(plan_alloc(P, (void **)&P->perm, 4 * n, false, s));
-    CUDA_TRY(launch_local_coords(dpts, vals, n, P->lo, P->side, D, P->pts, P->perm, s));
+    auto build_set = [&](const double *dp, int64_t cnt, float4 **pts, int **perm, int **off) -> int {
+        CUDA_TRY(cudaMemsetAsync(bad, 0, 16, s));
+        CUDA_TRY(launch_bin_points(dp, cnt, P->lo, P->side, D, keys, vals, bad, s));
+        int hbad = 0;
+        CUDA_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        if (hbad)
+            return fail(BBFMM_EINVAL, "points contain NaN/inf coordinates or lie outside the domain");
+        CUDA_TRY(radix_sort_pairs(keys, vals, keys2, vals2, cnt, 3 * D, scratch, sc, s));
+        PTRY(plan_alloc(P, (void **)off, 4 * (nleaf + 1), false, s));
+        CUDA_TRY(launch_leaf_offsets(keys, cnt, nleaf, *off, s));
+        PTRY(plan_alloc(P, (void **)pts, 16 * cnt, false, s));
+        PTRY(plan_alloc(P, (void **)perm, 4 * cnt, false, s));
+        CUDA_TRY(launch_local_coords(dp, vals, cnt, P->lo, P->side, D, *pts, *perm, s));
+        return BBFMM_OK;
+    };
+    PTRY(build_set(dpts, n, &P->pts, &P->perm, &P->leaf_off));
+    if (P->separate) {
+        PTRY(build_set(dtgt, nt, &P->tpts, &P->tperm, &P->tleaf_off));
+    } else {
+        P->tpts = P->pts;
+        P->tperm = P->perm;
+        P->tleaf_off = P->leaf_off;
+    }
+    // near-field work items: chunks of the target leaves
     int64_t chunk_bytes = 0;
-    CUDA_TRY(build_chunks(P->leaf_off, nleaf, scratch, &P->chunks, &P->nchunks, &chunk_bytes, s));
+    CUDA_TRY(build_chunks(P->tleaf_off, nleaf, scratch, &P->chunks, &P->nchunks, &chunk_bytes, s));
     P->bytes += chunk_bytes;
 
-    // statistics of the tree (host copy of the leaf offsets)
-    std::vector<uint8_t> leaf_occ;
+    // statistics of the tree (host copies of the leaf offsets)
+    std::vector<uint8_t> leaf_occ; // leaves holding targets
     {
-        std::vector<int> off(nleaf + 1);
+        std::vector<int> off(nleaf + 1), toff;
         CUDA_TRY(cudaMemcpyAsync(off.data(), P->leaf_off, 4 * (nleaf + 1), cudaMemcpyDeviceToHost, s));
+        if (P->separate) {
+            toff.resize(nleaf + 1);
+            CUDA_TRY(cudaMemcpyAsync(toff.data(), P->tleaf_off, 4 * (nleaf + 1), cudaMemcpyDeviceToHost, s));
+        }
         CUDA_TRY(cudaStreamSynchronize(s));
+        const std::vector<int> &to = P->separate ? toff : off;
+        if (off[nleaf] != n || to[nleaf] != nt)
+            return fail(BBFMM_EINTERNAL, "leaf offsets do not cover all points");
         leaf_occ.resize(nleaf);
         for (int64_t m = 0; m < nleaf; ++m)
-            leaf_occ[m] = off[m + 1] > off[m] ? 1 : 0;
-        if (off[nleaf] != n)
-            return fail(BBFMM_EINTERNAL, "leaf offsets do not cover all points");
-        int ns = 1 << D;
+            leaf_occ[m] = to[m + 1] > to[m] ? 1 : 0;
+        int side_cells = 1 << D;
         int64_t pairs = 0;
         for (int64_t m = 0; m < nleaf; ++m) {
-            int64_t c = off[m + 1] - off[m];
-            if (c == 0)
+            const int64_t cs = off[m + 1] - off[m], ct = to[m + 1] - to[m];
+            if (cs > 0) {
+                P->nonempty_leaves++;
+                P->max_leaf = std::max(P->max_leaf, cs);
+            }
+            if (ct == 0)
                 continue;
-            P->nonempty_leaves++;
-            P->max_leaf = std::max(P->max_leaf, c);
             int x, y, z;
             demorton3((uint32_t)m, x, y, z);
             int64_t src = 0;
@@ -382,12 +408,12 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, cudaStream_t s)
                 for (int dy = -1; dy <= 1; ++dy)
                     for (int dx = -1; dx <= 1; ++dx) {
                         int a = x + dx, b = y + dy, cc = z + dz;
-                        if (a < 0 || b < 0 || cc < 0 || a >= ns || b >= ns || cc >= ns)
+                        if (a < 0 || b < 0 || cc < 0 || a >= side_cells || b >= side_cells || cc >= side_cells)
                             continue;
                         uint32_t nm = morton3(a, b, cc);
                         src += off[nm + 1] - off[nm];
                     }
-            pairs += c * src;
+            pairs += ct * src;
         }
         P->p2p_pairs = pairs;
         for (int l = 2; l <= D; ++l)
@@ -441,8 +467,8 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, cudaStream_t s)
         PTRY(plan_alloc(P, (void **)&P->a16_scale, 4 * (kMaxDepth + 1), true, s));
     }
     PTRY(plan_alloc(P, (void **)&P->sigma_s, 4 * n * R, false, s));
-    PTRY(plan_alloc(P, (void **)&P->phi_far, 4 * n * R, false, s));
-    PTRY(plan_alloc(P, (void **)&P->phi_near, 4 * n * R, false, s));
+    PTRY(plan_alloc(P, (void **)&P->phi_far, 4 * nt * R, false, s));
+    PTRY(plan_alloc(P, (void **)&P->phi_near, 4 * nt * R, false, s));
     PTRY(plan_alloc(P, (void **)&P->status, 16, true, s));
 
     // constant tables the matvec kernels read, uploaded before any capture
@@ -474,6 +500,9 @@ static PassArgs pass_args(const bbfmm_plan_impl *P, int nrhs, bool split16)
     A.pts = P->pts;
     A.off = P->leaf_off;
     A.n = P->n;
+    A.tpts = P->tpts;
+    A.toff = P->tleaf_off;
+    A.nt = P->nt;
     A.D = P->D;
     A.nrhs = nrhs;
     A.R = P->max_nrhs;
@@ -503,7 +532,7 @@ static PassArgs pass_args(const bbfmm_plan_impl *P, int nrhs, bool split16)
 
 static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int nrhs, cudaStream_t s)
 {
-    const int64_t n = P->n;
+    const int64_t n = P->n, nt = P->nt;
     const int D = P->D, p = P->p, p3 = P->p3;
     const DevOps &O = *P->ops;
     const bool tm = P->timing;
@@ -521,8 +550,9 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
         CUDA_TRY(cudaStreamWaitEvent(P->side_stream, after, 0));
         if (tm)
             CUDA_TRY(cudaEventRecord(P->ev_p2p0, P->side_stream));
-        CUDA_TRY(launch_p2p(P->pts, P->sigma_s, P->leaf_off, P->chunks, P->nchunks, n, D, P->kernel, P->ell,
-                            P->side / (double)(1LL << D), nrhs, P->phi_near, P->side_stream));
+        const P2PArgs pa = {P->tpts, P->chunks, P->nchunks, nt, P->pts, P->sigma_s, P->leaf_off, n, D};
+        CUDA_TRY(launch_p2p(pa, P->kernel, P->ell, P->side / (double)(1LL << D), nrhs, P->phi_near,
+                            P->side_stream));
         if (tm)
             CUDA_TRY(cudaEventRecord(P->ev_p2p1, P->side_stream));
         CUDA_TRY(cudaEventRecord(P->ev_join, P->side_stream));
@@ -580,7 +610,7 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
     CUDA_TRY(cudaStreamWaitEvent(s, P->ev_join, 0));
     if (tm)
         CUDA_TRY(cudaEventRecord(P->ev[Stage::P2P], s));
-    CUDA_TRY(launch_combine(D >= 2 ? P->phi_far : nullptr, P->phi_near, P->perm, n, nrhs, phi, s));
+    CUDA_TRY(launch_combine(D >= 2 ? P->phi_far : nullptr, P->phi_near, P->tperm, nt, nrhs, phi, s));
     if (tm)
         CUDA_TRY(cudaEventRecord(P->ev[Stage::Combine], s));
     P->last_nrhs = nrhs;
@@ -638,10 +668,10 @@ static int matvec_graph(bbfmm_plan_impl *P, const float *sigma, float *phi, int 
         g.graph = graph;
     }
     // this call's pointers into the two boundary kernels
-    const int64_t n = P->n;
+    const int64_t n = P->n, nt = P->nt;
     const float *far = P->D >= 2 ? P->phi_far : nullptr;
     void *gargs[] = {(void *)&sigma, (void *)&P->perm, (void *)&n, (void *)&nrhs, (void *)&P->sigma_s};
-    void *cargs[] = {(void *)&far, (void *)&P->phi_near, (void *)&P->perm, (void *)&n, (void *)&nrhs,
+    void *cargs[] = {(void *)&far, (void *)&P->phi_near, (void *)&P->tperm, (void *)&nt, (void *)&nrhs,
                      (void *)&phi};
     cudaKernelNodeParams gp = g.gp, cp = g.cp;
     gp.kernelParams = gargs;
@@ -678,8 +708,8 @@ void bbfmm_default_opts(bbfmm_opts *o)
 
 const char *bbfmm_last_error(void) { return g_last_error.c_str(); }
 
-int bbfmm_plan(const double *points, int64_t n, int kernel_id, int cheb_order, int depth, const bbfmm_opts *opts_in,
-               void *stream, bbfmm_plan_t *out)
+static int plan_create(const double *points, int64_t n, const double *targets, int64_t nt, int kernel_id,
+                       int cheb_order, int depth, const bbfmm_opts *opts_in, void *stream, bbfmm_plan_t *out)
 {
     g_last_error.clear();
     if (!out)
@@ -693,6 +723,8 @@ int bbfmm_plan(const double *points, int64_t n, int kernel_id, int cheb_order, i
         return fail(BBFMM_EINVAL, "points is NULL");
     if (n < 1 || n >= (1LL << 31))
         return fail(BBFMM_EINVAL, "n = %lld out of range [1, 2^31)", (long long)n);
+    if (targets && (nt < 1 || nt >= (1LL << 31)))
+        return fail(BBFMM_EINVAL, "number of targets %lld out of range [1, 2^31)", (long long)nt);
     if (!(kernel_id == BBFMM_K_INV_R || kernel_id == BBFMM_K_INV_R2 || kernel_id == BBFMM_K_EXP ||
           kernel_id == BBFMM_K_GAUSS || kernel_id == BBFMM_K_TEST_POLY || kernel_id == BBFMM_K_TEST_CONST))
         return fail(BBFMM_EINVAL, "unknown kernel id %d", kernel_id);
@@ -712,7 +744,9 @@ int bbfmm_plan(const double *points, int64_t n, int kernel_id, int cheb_order, i
         int64_t p3 = (int64_t)cheb_order * cheb_order * cheb_order, grid = 0;
         for (int l = 2; l <= depth; ++l)
             grid += (1LL << (3 * l)) * opts.max_nrhs * (4 * p3 + 8 * p3);
-        int64_t need = grid * 4 + n * (16 + 4 + 12LL * opts.max_nrhs) + (1LL << (3 * depth)) * 8;
+        const int64_t ntg = targets ? nt : 0;
+        int64_t need = grid * 4 + n * (16 + 4 + 12LL * opts.max_nrhs) + ntg * (16 + 4 + 8LL * opts.max_nrhs) +
+                       (1LL << (3 * depth)) * 8;
         size_t fr = 0, tot = 0;
         if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
             cudaGetLastError();
@@ -725,6 +759,8 @@ int bbfmm_plan(const double *points, int64_t n, int kernel_id, int cheb_order, i
     if (!P)
         return fail(BBFMM_ENOMEM, "host allocation failed");
     P->n = n;
+    P->separate = targets != nullptr;
+    P->nt = targets ? nt : n;
     P->D = depth;
     P->p = cheb_order;
     P->p3 = cheb_order * cheb_order * cheb_order;
@@ -743,7 +779,7 @@ int bbfmm_plan(const double *points, int64_t n, int kernel_id, int cheb_order, i
     } else {
         P->side = -1.0;
     }
-    int st = plan_build(P, points, (cudaStream_t)stream);
+    int st = plan_build(P, points, targets, (cudaStream_t)stream);
     if (st != BBFMM_OK) {
         std::string msg = g_last_error;
         plan_free(P);
@@ -753,6 +789,24 @@ int bbfmm_plan(const double *points, int64_t n, int kernel_id, int cheb_order, i
     }
     *out = P;
     return BBFMM_OK;
+}
+
+int bbfmm_plan(const double *points, int64_t n, int kernel_id, int cheb_order, int depth, const bbfmm_opts *opts,
+               void *stream, bbfmm_plan_t *out)
+{
+    return plan_create(points, n, nullptr, 0, kernel_id, cheb_order, depth, opts, stream, out);
+}
+
+int bbfmm_plan_targets(const double *sources, int64_t ns, const double *targets, int64_t nt, int kernel_id,
+                       int cheb_order, int depth, const bbfmm_opts *opts, void *stream, bbfmm_plan_t *out)
+{
+    if (!targets) {
+        g_last_error.clear();
+        if (out)
+            *out = nullptr;
+        return fail(BBFMM_EINVAL, "targets is NULL");
+    }
+    return plan_create(sources, ns, targets, nt, kernel_id, cheb_order, depth, opts, stream, out);
 }
 
 int bbfmm_matvec(bbfmm_plan_t plan, const float *sigma, float *phi, int nrhs, void *stream)
@@ -769,7 +823,7 @@ int bbfmm_matvec(bbfmm_plan_t plan, const float *sigma, float *phi, int nrhs, vo
         return fail(BBFMM_EBUSY, "plan is in use by another thread");
     cudaStream_t s = (cudaStream_t)stream;
     const bool dsig = is_device_ptr(sigma), dphi = is_device_ptr(phi);
-    const int64_t bytes = 4 * plan->n * nrhs;
+    const int64_t bytes_in = 4 * plan->n * nrhs, bytes_out = 4 * plan->nt * nrhs;
     int st = BBFMM_OK;
     const float *sg = sigma;
     float *ph = phi;
@@ -777,10 +831,10 @@ int bbfmm_matvec(bbfmm_plan_t plan, const float *sigma, float *phi, int nrhs, vo
         if (!plan->io_sigma) {
             st = plan_alloc(plan, (void **)&plan->io_sigma, 4 * plan->n * plan->max_nrhs, false, s);
             if (st == BBFMM_OK)
-                st = plan_alloc(plan, (void **)&plan->io_phi, 4 * plan->n * plan->max_nrhs, false, s);
+                st = plan_alloc(plan, (void **)&plan->io_phi, 4 * plan->nt * plan->max_nrhs, false, s);
         }
         if (st == BBFMM_OK && !dsig) {
-            cudaError_t e = cudaMemcpyAsync(plan->io_sigma, sigma, bytes, cudaMemcpyHostToDevice, s);
+            cudaError_t e = cudaMemcpyAsync(plan->io_sigma, sigma, bytes_in, cudaMemcpyHostToDevice, s);
             if (e != cudaSuccess)
                 st = fail(BBFMM_ECUDA, "copy of sigma: %s", cudaGetErrorString(e));
             sg = plan->io_sigma;
@@ -792,7 +846,7 @@ int bbfmm_matvec(bbfmm_plan_t plan, const float *sigma, float *phi, int nrhs, vo
         st = plan->use_graph && !plan->timing ? matvec_graph(plan, sg, ph, nrhs, s)
                                               : matvec_device(plan, sg, ph, nrhs, s);
     if (st == BBFMM_OK && !dphi) {
-        cudaError_t e = cudaMemcpyAsync(phi, plan->io_phi, bytes, cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaMemcpyAsync(phi, plan->io_phi, bytes_out, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess)
             e = cudaStreamSynchronize(s);
         if (e != cudaSuccess)
@@ -864,6 +918,8 @@ int bbfmm_rand_eig(bbfmm_plan_t plan, const float *omega, int m, int k, int powe
         return fail(BBFMM_EINVAL, "need 1 <= k <= m <= max_nrhs (%d) and 0 <= power <= 8", plan->max_nrhs);
     if (!is_device_ptr(omega) || (evecs && !is_device_ptr(evecs)))
         return fail(BBFMM_EINVAL, "omega and evecs must be device memory");
+    if (plan->separate)
+        return fail(BBFMM_EINVAL, "the plan's targets are not its sources (the kernel matrix is not square)");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = plan->n;
     const int splits = gram_splits(n);
@@ -928,6 +984,7 @@ int bbfmm_plan_info(bbfmm_plan_t plan, bbfmm_info *info)
         return fail(BBFMM_EINVAL, "NULL argument");
     memset(info, 0, sizeof(*info));
     info->n = plan->n;
+    info->n_targets = plan->nt;
     info->depth = plan->D;
     info->order = plan->p;
     info->rank = plan->ops ? plan->ops->r : 0;

@@ -2,8 +2,9 @@
 //   phi_i += sum_{beta in N(alpha)} sum_{y_j in beta} K(x_i, y_j) sigma_j,
 // N(alpha) = the up to 27 leaves adjacent to alpha, alpha included (Def. 2.1).
 //
-// Work item = up to kChunk consecutive targets of one leaf; one block of 128
-// threads per item.  The block first gathers the neighbour leaves' sources
+// Targets and sources are two point sets binned into the same leaves (the
+// same arrays when the targets are the sources).  Work item = up to kChunk
+// consecutive targets of one leaf; one block of 128 threads per item.  The block first gathers the neighbour leaves' sources
 // into shared memory (all threads at once, coalesced, kStageSrc at a time),
 // with coordinates in the target leaf's cell units: y' = u_y + (cell_y -
 // cell_x).  The offset is an exact small integer, so the FP32 difference
@@ -114,9 +115,9 @@ static_assert(kTPT == 2 || kTPT == 4, "2 or 4 targets per thread");
 
 template <class Kern>
 __global__ void __launch_bounds__(kP2PThreads, 8)
-    k_p2p(const float4 *__restrict__ pts, const float *__restrict__ sig, const int *__restrict__ off,
-          const int4 *__restrict__ chunks, int nchunks, int64_t n, int D, Kern kern, float scale, int nrhs,
-          float *__restrict__ phi)
+    k_p2p(const float4 *__restrict__ tpts, const int4 *__restrict__ chunks, int64_t n_tgt,
+          const float4 *__restrict__ spts, const float *__restrict__ sig, const int *__restrict__ off, int64_t n_src,
+          int D, Kern kern, float scale, int nrhs, float *__restrict__ phi)
 {
     constexpr int NPK = kTPT / 2; // packed target pairs per thread
     __shared__ float4 stage_xy[kStageSrc]; // (x, x, y, y)
@@ -167,8 +168,8 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
 #pragma unroll
     for (int pk = 0; pk < NPK; ++pk) {
         const int i0 = t + 2 * pk * nq, i1 = i0 + nq;
-        const float4 xa = pts[ch.y + (active && i0 < nt ? i0 : 0)];
-        const float4 xb = pts[ch.y + (active && i1 < nt ? i1 : 0)];
+        const float4 xa = tpts[ch.y + (active && i0 < nt ? i0 : 0)];
+        const float4 xb = tpts[ch.y + (active && i1 < nt ? i1 : 0)];
         X[pk] = make_float2(xa.x, xb.x);
         Y[pk] = make_float2(xa.y, xb.y);
         Z[pk] = make_float2(xa.z, xb.z);
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
     const float2 floor2 = make_float2(kR2Floor, kR2Floor);
 
     for (int c = 0; c < nrhs; ++c) {
-        const float *sg = sig + (int64_t)c * n;
+        const float *sg = sig + (int64_t)c * n_src;
         float2 acc[NPK], acc2[NPK];
 #pragma unroll
         for (int pk = 0; pk < NPK; ++pk)
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
                 while (nb_pre[k + 1] <= gg)
                     ++k;
                 const int src = nb_start[k] + (gg - nb_pre[k]);
-                const float4 u = pts[src];
+                const float4 u = spts[src];
                 const float4 d = nb_delta[k];
                 const float s = sg[src];
                 // staged negated so that x_target - y' is one packed add
@@ -248,9 +249,9 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
                 }
                 const int i0 = tid + 2 * pk * nq, i1 = i0 + nq;
                 if (i0 < nt)
-                    phi[(int64_t)c * n + ch.y + i0] = scale * sa;
+                    phi[(int64_t)c * n_tgt + ch.y + i0] = scale * sa;
                 if (i1 < nt)
-                    phi[(int64_t)c * n + ch.y + i1] = scale * sb;
+                    phi[(int64_t)c * n_tgt + ch.y + i1] = scale * sb;
             }
         }
         __syncthreads();
@@ -265,9 +266,9 @@ constexpr int kStageMulti = 256;
 
 template <class Kern>
 __global__ void __launch_bounds__(kP2PThreads)
-    k_p2p_multi(const float4 *__restrict__ pts, const float *__restrict__ sig, const int *__restrict__ off,
-                const int4 *__restrict__ chunks, int64_t n, int D, Kern kern, float scale, int nrhs,
-                float *__restrict__ phi)
+    k_p2p_multi(const float4 *__restrict__ tpts, const int4 *__restrict__ chunks, int64_t n_tgt,
+                const float4 *__restrict__ spts, const float *__restrict__ sig, const int *__restrict__ off,
+                int64_t n_src, int D, Kern kern, float scale, int nrhs, float *__restrict__ phi)
 {
     __shared__ float4 spos[kStageMulti];
     __shared__ float ssig[kStageMulti][kRC];
@@ -307,7 +308,7 @@ __global__ void __launch_bounds__(kP2PThreads)
     }
     __syncthreads();
     const int ns = nb_pre[27];
-    const float4 xt = pts[ch.y + (active ? t : 0)];
+    const float4 xt = tpts[ch.y + (active ? t : 0)];
     for (int c0 = 0; c0 < nrhs; c0 += kRC) {
         const int rc = min(kRC, nrhs - c0);
         float acc[kRC];
@@ -324,12 +325,12 @@ __global__ void __launch_bounds__(kP2PThreads)
                     if (k + step < 27 && nb_pre[k + step] <= gg)
                         k += step;
                 const int src = nb_start[k] + (gg - nb_pre[k]);
-                const float4 u = pts[src];
+                const float4 u = spts[src];
                 const float4 d = nb_delta[k];
                 spos[g] = make_float4(u.x + d.x, u.y + d.y, u.z + d.z, 0.0f);
 #pragma unroll
                 for (int q = 0; q < kRC; ++q)
-                    ssig[g][q] = q < rc ? sig[(int64_t)(c0 + q) * n + src] : 0.0f;
+                    ssig[g][q] = q < rc ? sig[(int64_t)(c0 + q) * n_src + src] : 0.0f;
             }
             __syncthreads();
             if (active)
@@ -352,27 +353,27 @@ __global__ void __launch_bounds__(kP2PThreads)
                 float sum = 0.0f;
                 for (int sl = 0; sl < S; ++sl)
                     sum += red[tid + sl * nt][q];
-                phi[(int64_t)(c0 + q) * n + ch.y + tid] = scale * sum;
+                phi[(int64_t)(c0 + q) * n_tgt + ch.y + tid] = scale * sum;
             }
         __syncthreads();
     }
 }
 
 template <class Kern>
-static cudaError_t p2p_launch(const float4 *pts, const float *sig, const int *off, const int4 *chunks, int nchunks,
-                              int64_t n, int D, Kern k, float scale, int nrhs, float *phi, cudaStream_t s)
+static cudaError_t p2p_launch(const P2PArgs &A, Kern k, float scale, int nrhs, float *phi, cudaStream_t s)
 {
-    if (nchunks <= 0)
+    if (A.nchunks <= 0)
         return cudaSuccess;
     if (nrhs > 1)
-        k_p2p_multi<Kern><<<nchunks, kP2PThreads, 0, s>>>(pts, sig, off, chunks, n, D, k, scale, nrhs, phi);
+        k_p2p_multi<Kern><<<A.nchunks, kP2PThreads, 0, s>>>(A.tpts, A.chunks, A.nt, A.spts, A.sig, A.soff, A.ns,
+                                                             A.D, k, scale, nrhs, phi);
     else
-        k_p2p<Kern><<<nchunks, kP2PThreads, 0, s>>>(pts, sig, off, chunks, nchunks, n, D, k, scale, nrhs, phi);
+        k_p2p<Kern><<<A.nchunks, kP2PThreads, 0, s>>>(A.tpts, A.chunks, A.nt, A.spts, A.sig, A.soff, A.ns, A.D, k,
+                                                       scale, nrhs, phi);
     return cudaGetLastError();
 }
 
-cudaError_t launch_p2p(const float4 *pts, const float *sig, const int *leaf_off, const int4 *chunks, int nchunks,
-                       int64_t n, int D, int kernel, double ell, double h, int nrhs, float *phi_near,
+cudaError_t launch_p2p(const P2PArgs &A, int kernel, double ell, double h, int nrhs, float *phi_near,
                        cudaStream_t s)
 {
     static_assert(kChunk <= 2 * kP2PThreads, "a work item holds at most two targets per thread");
@@ -380,21 +381,17 @@ cudaError_t launch_p2p(const float4 *pts, const float *sig, const int *leaf_off,
     const double ln2 = 0.69314718055994530942;
     switch (kernel) {
     case BBFMM_K_INV_R:
-        return p2p_launch(pts, sig, leaf_off, chunks, nchunks, n, D, KInvR{0.f}, (float)(1.0 / h), nrhs,
-                          phi_near, s);
+        return p2p_launch(A, KInvR{0.f}, (float)(1.0 / h), nrhs, phi_near, s);
     case BBFMM_K_INV_R2:
-        return p2p_launch(pts, sig, leaf_off, chunks, nchunks, n, D, KInvR2{0.f}, (float)(1.0 / (h * h)), nrhs,
-                          phi_near, s);
+        return p2p_launch(A, KInvR2{0.f}, (float)(1.0 / (h * h)), nrhs, phi_near, s);
     case BBFMM_K_EXP:
-        return p2p_launch(pts, sig, leaf_off, chunks, nchunks, n, D, KExp{(float)(h / (ell * ln2))}, 1.0f, nrhs,
-                          phi_near, s);
+        return p2p_launch(A, KExp{(float)(h / (ell * ln2))}, 1.0f, nrhs, phi_near, s);
     case BBFMM_K_GAUSS:
-        return p2p_launch(pts, sig, leaf_off, chunks, nchunks, n, D, KGauss{(float)(h * h / (ell * ell * ln2))},
-                          1.0f, nrhs, phi_near, s);
+        return p2p_launch(A, KGauss{(float)(h * h / (ell * ell * ln2))}, 1.0f, nrhs, phi_near, s);
     case BBFMM_K_TEST_POLY:
-        return p2p_launch(pts, sig, leaf_off, chunks, nchunks, n, D, KPoly{(float)h}, 1.0f, nrhs, phi_near, s);
+        return p2p_launch(A, KPoly{(float)h}, 1.0f, nrhs, phi_near, s);
     case BBFMM_K_TEST_CONST:
-        return p2p_launch(pts, sig, leaf_off, chunks, nchunks, n, D, KConst{0.f}, 1.0f, nrhs, phi_near, s);
+        return p2p_launch(A, KConst{0.f}, 1.0f, nrhs, phi_near, s);
     }
     return cudaErrorInvalidValue;
 }

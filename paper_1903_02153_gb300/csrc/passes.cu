@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(kThreads) k_downward(const __grid_constant__ P
     const int D = A.D;
     const int64_t b = blockIdx.x; // box at level D-1
     const int c = blockIdx.y;
-    if (!A.keep && A.off[8 * b] == A.off[8 * b + 8])
+    if (!A.keep && A.toff[8 * b] == A.toff[8 * b + 8])
         return; // no targets below this box
 
     // ---- ancestors at levels 2 .. D-1 (the last one is the block's own box)
@@ -591,13 +591,13 @@ __global__ void __launch_bounds__(kThreads) k_downward(const __grid_constant__ P
             A.F[D][((8 * b + o) * A.nrhs + c) * P3 + r] = sMT[q];
         }
 
-    // ---- L2P: warp w evaluates leaf 8b + w at its points (Sec. 2.2 item 3)
+    // ---- L2P: warp w evaluates leaf 8b + w at its targets (Sec. 2.2 item 3)
     const int64_t leaf = 8 * b + w;
-    const int s0 = A.off[leaf], s1 = A.off[leaf + 1];
+    const int s0 = A.toff[leaf], s1 = A.toff[leaf + 1];
     for (int c0 = s0; c0 < s1; c0 += 32) {
         const int j = c0 + lane;
         const bool has = j < s1;
-        const float4 u = A.pts[has ? j : s0];
+        const float4 u = A.tpts[has ? j : s0];
         float Lx[P], Ly[P];
         basis_1d<P>(A.T, 2.0f * u.x, Lx);
         basis_1d<P>(A.T, 2.0f * u.y, Ly);
@@ -624,7 +624,7 @@ __global__ void __launch_bounds__(kThreads) k_downward(const __grid_constant__ P
             acc += slice * lz;
         }
         if (has)
-            A.phi[(int64_t)c * A.n + j] = acc;
+            A.phi[(int64_t)c * A.nt + j] = acc;
     }
 }
 

@@ -88,3 +88,19 @@ def test_null_handles(lib):
     assert L.bbfmm_destroy(None) == 0
     assert L.bbfmm_matvec(None, None, None, 1, None) == lib.BBFMM_EINVAL
     assert L.bbfmm_plan_info(None, None) == lib.BBFMM_EINVAL
+
+
+def test_plan_targets_rejects_bad_arguments(lib):
+    """Separate-target plans: NULL targets, or a target count out of range,
+    answer EINVAL before any device call."""
+    pts = np.random.default_rng(1).random((10, 3))
+    L = lib.lib()
+    h = ctypes.c_void_p()
+    assert L.bbfmm_plan_targets(pts.ctypes.data, 10, None, 10, 1, 4, 3, None, None,
+                                ctypes.byref(h)) == lib.BBFMM_EINVAL
+    assert h.value is None
+    for nt in (0, -1, 1 << 31):
+        assert L.bbfmm_plan_targets(pts.ctypes.data, 10, pts.ctypes.data, nt, 1, 4, 3, None, None,
+                                    ctypes.byref(h)) == lib.BBFMM_EINVAL, nt
+    assert L.bbfmm_plan_targets(pts.ctypes.data, 0, pts.ctypes.data, 10, 1, 4, 3, None, None,
+                                ctypes.byref(h)) == lib.BBFMM_EINVAL
