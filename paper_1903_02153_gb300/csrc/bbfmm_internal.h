@@ -96,6 +96,7 @@ struct HostOps {
     std::vector<double> S;      // S[o][i][j] = l_i((s_j + 2o - 1) / 2), o = 0, 1
     // per operator level: (one level if homogeneous, else one per tree level 2..D)
     std::vector<double> h;               // box side of the level the operators were made for
+    std::vector<int> rl;                 // rank of each operator level before padding to r
     std::vector<std::vector<double>> U;  // p3 x r row-major
     std::vector<std::vector<double>> V;  // p3 x r row-major
     std::vector<std::vector<double>> C;  // 316 x r x r: C[t] = U^T K^(t) V
@@ -141,7 +142,8 @@ void jacobi_eigen(int n, std::vector<double> &A, std::vector<double> &w, std::ve
 struct DevOps {
     std::shared_ptr<HostOps> host;
     int nlev = 0;            // operator levels
-    int r = 0, rp = 0;       // rank, row pitch (floats) of r-vectors
+    int r = 0, rp = 0;       // rank (largest over the levels), row pitch (floats) of r-vectors
+    std::vector<int> rl;     // rank of each operator level (columns past it are zero)
     int rows64 = 0;          // r rounded up to 64 (FP32 M2L tile rows)
     int p3p = 0;             // p3 rounded up to 16
     std::vector<float *> V;  // [p3][rp]    compress weights
@@ -249,6 +251,7 @@ struct PassArgs {
     const int *toff;            // targets: leaf start offsets
     int64_t nt;
     int D, nrhs, R, r, rp, p3p; // R = max_nrhs (row stride of M~ / F~)
+    int rl[kMaxDepth + 1];      // rank of each level's operators (<= r; coefficients past it stay 0)
     const float *sig;           // upward: n x nrhs weights in tree order
     float *phi;                 // downward: nt x nrhs far field in target tree order
     float *M[kMaxDepth + 1];    // Morton [box][nrhs][p^3]; leaf level used only with keep

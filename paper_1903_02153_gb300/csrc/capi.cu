@@ -145,6 +145,7 @@ static int get_ops(int kernel, double ell, int p, double eps, int depth, double 
     d->host = host;
     d->nlev = (int)host->C.size();
     d->r = host->r;
+    d->rl = host->rl;
     d->rp = (int)round_up(std::max(host->r, 1), 16);
     d->rows64 = (int)round_up(std::max(host->r, 1), 64);
     d->p3p = (int)round_up(host->p3, 16);
@@ -525,6 +526,7 @@ static PassArgs pass_args(const bbfmm_plan_impl *P, int nrhs, bool split16)
         A.F[l] = L.F;
         A.V[l] = O.V[O.nlev == 1 ? 0 : l - 2];
         A.Ut[l] = O.Ut[O.nlev == 1 ? 0 : l - 2];
+        A.rl[l] = O.rl[O.nlev == 1 ? 0 : l - 2];
         A.count[l] = P->up_count[l];
     }
     return A;

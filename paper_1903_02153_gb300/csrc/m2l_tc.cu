@@ -9,7 +9,9 @@
 // The MMA's M side is the operator's r output coefficients (padded to 128
 // lanes), its N side the targets: one instruction then carries 128 x N x K
 // products, and the instruction count per target is a half (N = 256) of what
-// a targets-by-coefficients orientation (N = r) needs.  Source vectors come
+// a targets-by-coefficients orientation (N = r) needs.  Each level uses the
+// rank of its own operators (r_l, the columns past it are zero); a level with
+// r_l in (128, 256] runs every tile twice, once per half of the rows.  Source vectors come
 // straight out of the parity-split M~ array: for one offset and one tile the
 // sources are a box of consecutive parent cells of one source octant, one TMA
 // box load; out-of-range cells read as zero.  K is walked in chunks of 32
@@ -111,9 +113,10 @@ struct TcLevel {
     int64_t slice;            // floats per slice
     int H, bx, by, bz, lbx, lby, n; // tile extent (log2 of bx, by) and N = bx by bz
     const int4 *tl;           // the level's active tiles {tx, ty, tz, octant} (device)
-    int nact, ntiles, tile_base, opl, l; // active tiles; x right-hand sides; first tile number
+    int nact, ntiles, tile_base, opl, l; // active tiles; x right-hand sides x row halves; first tile number
+    int r, nk, ktail, nh;     // rank of the level's operators, K chunks, K steps of the last chunk, row halves
     uint32_t idesc;           // instruction descriptor (N of this level)
-    uint32_t b_load;          // bytes of one source box (one piece, one chunk)
+    uint32_t a_load, b_load;  // bytes of the operator rows loaded / of the sources (one piece, one chunk)
     float scale;
 };
 
@@ -126,13 +129,13 @@ struct TcLaunch {
     int nlev, ntiles;               // levels; tiles of all levels
     int64_t total, per_cta;         // (tile, offset) pairs; pairs per CTA
     int *status;
-    int r, rp, nb, nrhs, R, nk, nstage; // R: right-hand-side stride of M~ / F~ rows
+    int rp, nrhs, R, nstage;            // R: right-hand-side stride of M~ / F~ rows
     int nbuf, bcols, tcols;             // TMEM partial buffers, columns per accumulator, allocated
-    uint32_t stage_bytes, a_bytes, a_load, b_bytes; // a: C tile (128 rows, nb loaded); b: sources
+    uint32_t stage_bytes, a_bytes, b_bytes; // a: C tile (128 rows); b: sources
 };
 
 struct Item {
-    int L, tx, ty, tz, ot, c, g, e0, e1;
+    int L, tx, ty, tz, ot, c, h, g, e0, e1; // h: the 128 operator rows [128 h, 128 h + 128)
 };
 
 // the segment of this CTA's range that starts at pair `pos`
@@ -148,7 +151,12 @@ __device__ __forceinline__ Item decode_segment(const TcLaunch &P, int64_t pos, i
         ++L;
     it.L = L;
     const TcLevel &lv = P.lev[L];
-    const int u = t - lv.tile_base;
+    int u = t - lv.tile_base; // ((c nact) + tile) nh + h: the row halves of a tile run back to back
+    it.h = 0;
+    if (lv.nh > 1) {
+        it.h = u & 1;
+        u >>= 1;
+    }
     it.c = u / lv.nact;
     const int4 e = lv.tl[u - it.c * lv.nact];
     it.tx = e.x;
@@ -216,12 +224,13 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
             pos += w.e1 - w.e0;
             const TcLevel &lv = P.lev[w.L];
             const int X0 = lv.bx * w.tx, Y0 = lv.by * w.ty, Z0 = lv.bz * w.tz;
-            const uint32_t tx_bytes = (NPROD == 3 ? 2u : 1u) * (P.a_load + lv.b_load);
+            const uint32_t tx_bytes = (NPROD == 3 ? 2u : 1u) * (lv.a_load + lv.b_load);
+            const int row0 = 128 * w.h;
             for (int e = w.e0; e < w.e1 && !*abort_flag; ++e) {
                 const int4 en = c_tab_tc[w.ot][e];
                 const int ux = (en.z & 3) - 1, uy = ((en.z >> 2) & 3) - 1, uz = ((en.z >> 4) & 3) - 1;
                 const int zq = en.y * (lv.H + 2) + 1 + Z0 + uz;
-                for (int kc = 0; kc < P.nk; ++kc) {
+                for (int kc = 0; kc < lv.nk; ++kc) {
                     if (!mbar_wait(empty0 + 8 * s, round ^ 1, abort_flag))
                         break;
                     const uint32_t sa = base + (uint32_t)s * P.stage_bytes;
@@ -229,10 +238,10 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
                     mbar_arrive_expect_tx(fb, tx_bytes);
                     last_round[s] = round;
                     const uint32_t sb = sa + (NPROD == 3 ? 2u : 1u) * P.a_bytes;
-                    tma_load_3d(sa, &P.op[lv.opl], fb, kKChunk * kc, 0, en.x);
+                    tma_load_3d(sa, &P.op[lv.opl], fb, kKChunk * kc, row0, en.x);
                     tma_load_5d(sb, &P.src[w.L], fb, kKChunk * kc, w.c, X0 + ux, Y0 + uy, zq);
                     if (NPROD == 3) {
-                        tma_load_3d(sa + P.a_bytes, &P.oplo[lv.opl], fb, kKChunk * kc, 0, en.x);
+                        tma_load_3d(sa + P.a_bytes, &P.oplo[lv.opl], fb, kKChunk * kc, row0, en.x);
                         tma_load_5d(sb + P.b_bytes, &P.srclo[w.L], fb, kKChunk * kc, w.c, X0 + ux, Y0 + uy, zq);
                     }
                     if (++s == S) {
@@ -259,14 +268,15 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
         const uint64_t d0 = SW64 ? sw64_desc(base) : sw128_desc(base);
         const uint32_t d_al = P.a_bytes >> 4, d_bh = b_off >> 4, d_bl = (b_off + P.b_bytes) >> 4;
         const uint32_t d_st = P.stage_bytes >> 4;
-        const int ktail = (P.r - kKChunk * (P.nk - 1) + KSTEP - 1) / KSTEP; // K steps of the last chunk
         int s = 0, sph = 0, pb = 0, pph = 0; // stage ring and partial-buffer ring (position, phase)
         bool ok = true;
         const int64_t end = min(P.total, (int64_t)(blockIdx.x + 1) * P.per_cta);
         for (int64_t pos = (int64_t)blockIdx.x * P.per_cta; pos < end && ok && !*abort_flag;) {
             const Item w = decode_segment(P, pos, end);
             pos += w.e1 - w.e0;
-            const uint32_t idesc = P.lev[w.L].idesc;
+            const TcLevel &lv = P.lev[w.L];
+            const uint32_t idesc = lv.idesc;
+            const int nk = lv.nk, ktail = lv.ktail;
             for (int e = w.e0; e < w.e1 && ok; ++e) {
                 if (!mbar_wait(pempty0 + 8 * pb, pph ^ 1, abort_flag)) {
                     ok = false;
@@ -276,7 +286,7 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
                 const uint32_t dh = tmem_base + (uint32_t)(pb * NACC * P.bcols);
                 const uint32_t dc = NACC == 2 ? dh + (uint32_t)P.bcols : dh;
                 uint32_t acc_h = 0, acc_c = 0;
-                for (int kc = 0; kc < P.nk; ++kc) {
+                for (int kc = 0; kc < nk; ++kc) {
                     if (!mbar_wait(full0 + 8 * s, sph, abort_flag)) {
                         ok = false;
                         break;
@@ -284,7 +294,7 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
                     tc_fence_after();
                     const uint64_t ah = d0 + (uint64_t)(s * d_st); // C (operator) pieces
                     const uint64_t al = ah + d_al, bh = ah + d_bh, bl = ah + d_bl; // sources
-                    const int ks = kc + 1 < P.nk ? KMAX : ktail;
+                    const int ks = kc + 1 < nk ? KMAX : ktail;
                     auto issue = [&](uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
                         if (FMT == 0)
                             mma_tf32(d, a, b, idesc, acc);
@@ -344,8 +354,6 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
         const int ew = warp - 2;
         const int q = warp & 3;   // TMEM lane quadrant this warp may access
         const int half = ew >> 2; // target columns [128 half, 128 half + 128)
-        const int k = 32 * q + lane; // output coefficient of this thread
-        const bool rows = 32 * q < P.r; // warp-uniform: the quadrant holds coefficients
         const uint32_t tlane = tmem_base + ((uint32_t)(32 * q) << 16);
         int pb = 0, pph = 0; // partial-buffer ring (position, phase)
         bool ok = true;
@@ -355,6 +363,8 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
             pos += w.e1 - w.e0;
             const TcLevel &lv = P.lev[w.L];
             const int ncol = min(128, lv.n - 128 * half); // target columns of this warp
+            const int k = 128 * w.h + 32 * q + lane;     // output coefficient of this thread
+            const bool rows = 128 * w.h + 32 * q < lv.r; // warp-uniform: the quadrant holds coefficients
             float acc[128];
 #pragma unroll
             for (int j = 0; j < 128; ++j)
@@ -402,7 +412,7 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
             }
             if (!ok)
                 break;
-            if (!rows || k >= P.r)
+            if (!rows || k >= lv.r)
                 continue;
             // level scale; 16-bit forms also undo the power-of-two operand scales
             float f = lv.scale;
@@ -576,7 +586,7 @@ void m2l_active_tiles(int D, int precision, const std::vector<uint8_t> &leaf_occ
 // range boundary), else 4 (ranges of at least 63 offsets)
 int m2l_groups_for(int D, int nrhs, int precision, int r, int64_t active_tiles)
 {
-    if (precision == BBFMM_PREC_FP32 || D < 2 || r > 128)
+    if (precision == BBFMM_PREC_FP32 || D < 2 || r > 256)
         return 1;
     if (tc_init() != cudaSuccess)
         return 1;
@@ -609,10 +619,11 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
         // homogeneous kernels: operators made for the leaf box, scaled by (h_l / h_D)^m
         return O.host->hom_degree != 0 ? (float)pow(2.0, (double)O.host->hom_degree * (P->D - l)) : 1.0f;
     };
-    // operators of rank above 128 (high p with a small svd_eps) exceed the
-    // 128-lane M side of one MMA: they run on the FP32 CUDA-core form (with
-    // one offset group, see m2l_groups_for)
-    if (P->precision == BBFMM_PREC_FP32 || O.r > 128) {
+    // the M side of one MMA is 128 operator rows; a level whose rank is above
+    // 128 runs each tile as two row halves.  Ranks above 256 (high p with a
+    // small svd_eps) run on the FP32 CUDA-core form (with one offset group,
+    // see m2l_groups_for)
+    if (P->precision == BBFMM_PREC_FP32 || O.r > 256) {
         for (int l = 2; l <= P->D; ++l) {
             const int k = O.nlev == 1 ? 0 : l - 2;
             cudaError_t e = launch_m2l_fp32(P->lev[l].Mt, O.C[k], P->lev[l].Ft, l, O.r, O.rp, O.rows64, nrhs,
@@ -628,25 +639,28 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
     // operand format: 0 = TF32 (1 or 3 passes), 1 = FP16 x3, 2 = BF16 x3
     const int fmt = P->precision == BBFMM_PREC_FP16X3 ? 1 : P->precision == BBFMM_PREC_BF16X3 ? 2 : 0;
     const bool three = P->precision != BBFMM_PREC_TF32;
-    const int elem = fmt == 0 ? 4 : 2, rowb = kKChunk * elem;
-    const int nb = (O.r + 15) / 16 * 16; // operator rows loaded (the M side is always 128)
+    const int elem = fmt == 0 ? 4 : 2, rowb = kKChunk * elem, kstep = fmt == 0 ? 8 : 16;
     const int nt = tile_targets(P->precision);
-    if (O.rows64 < nb || O.rp % 16 != 0 || P->D - 1 > kMaxTcLevels)
+    if (O.rp % 16 != 0 || P->D - 1 > kMaxTcLevels || (int)O.rl.size() != O.nlev)
         return cudaErrorInvalidValue;
+    // operator rows loaded per tile of each operator level (the M side is
+    // always 128): the rank rounded to 16, or 128 per half above 128
+    int nbk[kMaxTcLevels];
+    for (int k = 0; k < O.nlev; ++k) {
+        if (O.rl[k] < 1 || O.rl[k] > O.r)
+            return cudaErrorInvalidValue;
+        nbk[k] = O.rl[k] > 128 ? 128 : (O.rl[k] + 15) / 16 * 16;
+    }
     if (fmt != 0 && (int)O.C16hi[fmt - 1].size() != O.nlev)
         return cudaErrorInvalidValue;
     TcLaunch L;
     memset(&L, 0, sizeof(L));
     L.status = P->status;
-    L.r = O.r;
     L.rp = O.rp;
-    L.nb = nb;
     L.nrhs = nrhs;
     L.R = P->max_nrhs;
-    L.nk = (O.r + kKChunk - 1) / kKChunk;
 
-    L.a_bytes = 128 * rowb; // C tile: 128 rows in shared memory, nb of them loaded
-    L.a_load = (uint32_t)nb * rowb;
+    L.a_bytes = 128 * rowb; // C tile: 128 rows in shared memory, nbk of them loaded
     L.b_bytes = (uint32_t)nt * rowb; // sources: up to nt rows
     L.stage_bytes = (three ? 2 : 1) * (L.a_bytes + L.b_bytes);
     L.ascale = P->a16_scale;
@@ -680,9 +694,14 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
         lv.n = lv.bx * lv.by * lv.bz;
         lv.tl = P->m2l_tiles + P->m2l_tile_off[l];
         lv.nact = P->m2l_ntiles[l];
-        lv.ntiles = lv.nact * nrhs;
-        lv.tile_base = tiles;
         lv.opl = O.nlev == 1 ? 0 : l - 2;
+        lv.r = O.rl[lv.opl];
+        lv.nh = lv.r > 128 ? 2 : 1;
+        lv.nk = (lv.r + kKChunk - 1) / kKChunk;
+        lv.ktail = (lv.r - kKChunk * (lv.nk - 1) + kstep - 1) / kstep;
+        lv.a_load = (uint32_t)nbk[lv.opl] * rowb;
+        lv.ntiles = lv.nact * nrhs * lv.nh;
+        lv.tile_base = tiles;
         lv.l = l;
         lv.scale = scale_of(l);
         lv.idesc = fmt == 0 ? idesc_tf32(128, lv.n) : idesc_f16(128, lv.n, fmt == 2 ? 1 : 0);
@@ -723,9 +742,9 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
             Blo = three ? (const void *)O.Clo[k] : B;
             L.bscale_inv[k] = 1.0f;
         }
-        e = encode_op(&L.op[k], B, O.rp, O.rows64, nb, fmt);
+        e = encode_op(&L.op[k], B, O.rp, O.rows64, nbk[k], fmt);
         if (e == cudaSuccess)
-            e = encode_op(&L.oplo[k], Blo, O.rp, O.rows64, nb, fmt);
+            e = encode_op(&L.oplo[k], Blo, O.rp, O.rows64, nbk[k], fmt);
         if (e != cudaSuccess)
             return e;
     }

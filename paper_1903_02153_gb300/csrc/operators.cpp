@@ -299,6 +299,7 @@ std::shared_ptr<HostOps> build_host_ops(int kernel, double ell, int p, double ep
         o->h[k] = h;
         int ru = 0, rv = 0;
         build_level(*o, h, o->U[k], o->V[k], o->C[k], o->sv[k], ru, rv);
+        o->rl.push_back(o->r);
         o->rank_u = std::max(o->rank_u, ru);
         o->rank_v = std::max(o->rank_v, rv);
         rmax = std::max(rmax, o->r);

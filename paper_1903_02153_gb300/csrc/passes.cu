@@ -286,9 +286,9 @@ __device__ void compress8(const PassArgs &A, int l, const float *X, int64_t box0
     const int H = 1 << (l - 1);
     const float *V = A.V[l];
     float mx = 0.0f;
-    for (int k0 = 0; k0 < A.r; k0 += 128) { // uniform trip count: the warp shuffles below need all lanes
+    for (int k0 = 0; k0 < A.rl[l]; k0 += 128) { // uniform trip count: the warp shuffles below need all lanes
         const int k = k0 + (t & 127);
-        const bool on = k < A.r;
+        const bool on = k < A.rl[l];
         float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         if (on && !zero) {
 #pragma unroll 5
@@ -325,9 +325,9 @@ __device__ void compress1(const PassArgs &A, int l, const float *X, int64_t box,
     demorton3((uint32_t)box, x, y, z);
     const int64_t row = parity_row(x, y, z, c, H, 1, A.R) * A.rp;
     float mx = 0.0f;
-    for (int k0 = 0; k0 < A.r; k0 += kThreads) {
+    for (int k0 = 0; k0 < A.rl[l]; k0 += kThreads) {
         const int k = k0 + t;
-        if (k < A.r) {
+        if (k < A.rl[l]) {
             float a0 = 0.0f, a1 = 0.0f;
             int i = 0;
             for (; i + 1 < P3; i += 2) {
@@ -515,18 +515,19 @@ __global__ void __launch_bounds__(kThreads) k_downward(const __grid_constant__ P
         const int64_t anc = b >> (3 * (D - 1 - l));
         if (l > 2)
             l2l1<P>(A.T, sPar, (int)(anc & 7), sOne, sPar);
-        for (int k = t; k < A.r; k += kThreads)
+        const int rl = A.rl[l];
+        for (int k = t; k < rl; k += kThreads)
             load_ft(A, l, anc, c, sFt, 1, k);
         __syncthreads();
         const float *Ut = A.Ut[l];
         for (int i = t; i < P3; i += kThreads) {
             float a0 = 0.0f, a1 = 0.0f;
             int k = 0;
-            for (; k + 1 < A.r; k += 2) {
+            for (; k + 1 < rl; k += 2) {
                 a0 += sFt[k] * __ldg(Ut + (int64_t)k * A.p3p + i);
                 a1 += sFt[k + 1] * __ldg(Ut + (int64_t)(k + 1) * A.p3p + i);
             }
-            if (k < A.r)
+            if (k < rl)
                 a0 += sFt[k] * __ldg(Ut + (int64_t)k * A.p3p + i);
             const float f = (l > 2 ? sPar[i] : 0.0f) + (a0 + a1);
             sPar[i] = f;
@@ -552,7 +553,7 @@ __global__ void __launch_bounds__(kThreads) k_downward(const __grid_constant__ P
             sRow[t] = parity_row(x, y, z, c, 1 << (D - 1), 0, A.R) * A.rp;
         }
         __syncthreads();
-        for (int q = t; q < 8 * A.r; q += kThreads) {
+        for (int q = t; q < 8 * A.rl[D]; q += kThreads) {
             const int o = q & 7, k = q >> 3;
             const float *src = A.Ft[D] + sRow[o] + k;
             float v = __ldg(src);
@@ -570,7 +571,7 @@ __global__ void __launch_bounds__(kThreads) k_downward(const __grid_constant__ P
             if (i < P3) {
                 float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll 4
-                for (int k = 0; k < A.r; ++k) {
+                for (int k = 0; k < A.rl[D]; ++k) {
                     const float u = __ldg(Ut + (int64_t)k * A.p3p + i);
                     const float4 f = *reinterpret_cast<const float4 *>(sFt + k * 8 + 4 * h);
                     acc[0] += f.x * u;
@@ -723,7 +724,7 @@ __device__ void compress64(const PassArgs &A, const float *X, int64_t B, int c, 
     const int l = A.D, H = 1 << (l - 1);
     const float *V = A.V[l];
     float mx = 0.0f;
-    for (int k0 = 0; k0 < A.r; k0 += 96) {
+    for (int k0 = 0; k0 < A.rl[l]; k0 += 96) {
         const int kb = k0 + 3 * kg;
         float acc[3][8];
 #pragma unroll
@@ -735,9 +736,9 @@ __device__ void compress64(const PassArgs &A, const float *X, int64_t B, int c, 
 #pragma unroll 2
             for (int i = 0; i < P3; ++i) {
                 const float *vr = V + (int64_t)i * A.rp;
-                const float v0 = kb < A.r ? __ldg(vr + kb) : 0.0f;
-                const float v1 = kb + 1 < A.r ? __ldg(vr + kb + 1) : 0.0f;
-                const float v2 = kb + 2 < A.r ? __ldg(vr + kb + 2) : 0.0f;
+                const float v0 = kb < A.rl[l] ? __ldg(vr + kb) : 0.0f;
+                const float v1 = kb + 1 < A.rl[l] ? __ldg(vr + kb + 1) : 0.0f;
+                const float v2 = kb + 2 < A.rl[l] ? __ldg(vr + kb + 2) : 0.0f;
                 const float4 m0 = *reinterpret_cast<const float4 *>(X + i * 64 + 8 * bg);
                 const float4 m1 = *reinterpret_cast<const float4 *>(X + i * 64 + 8 * bg + 4);
                 const float m[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
@@ -756,7 +757,7 @@ __device__ void compress64(const PassArgs &A, const float *X, int64_t B, int c, 
             const int64_t row = parity_row(x, y, z, c, H, 1, A.R) * A.rp;
 #pragma unroll
             for (int j = 0; j < 3; ++j)
-                if (kb + j < A.r)
+                if (kb + j < A.rl[l])
                     put_mt(A, l, row + kb + j, acc[j][b], mx);
         }
     }

@@ -179,3 +179,26 @@ def test_clustered_points_visit_only_occupied_tiles(bb, oracle, depth, prec):
     ref = oracle.bbfmm(pts, sig.astype(np.float64), 3, 5, depth, ell=0.3, lo=W.UNIT_LO, side=W.UNIT_SIDE, sample=idx)
     assert oracle.rel_err(got[idx], ref) <= 1e-5
     assert rel(got, plain) < 4e-6
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "fp16x3"])
+@pytest.mark.parametrize("eps", [1e-7, 1e-8])
+def test_rank_above_128_runs_in_row_halves(bb, oracle, prec, eps):
+    """exp(-r/0.3) at p = 6 has level ranks up to 152 (eps 1e-7) and 184
+    (eps 1e-8): the coarse levels run each tile as two halves of 128 operator
+    rows, the fine levels at their own lower rank.  Against the uncompressed
+    oracle and the FP32 form."""
+    n = 30_000
+    pts = W.clustered_points(n, seed=86)
+    sig = W.uniform_sigma(n, seed=87).astype(np.float32)
+    dev = torch.device("cuda:0")
+    plan = bb.Plan(torch.from_numpy(pts).to(dev), 3, 6, 4, ell=0.3, svd_eps=eps, precision=prec, domain=UNIT)
+    assert plan.info().rank > 128
+    plan.close()
+    got = run(bb, pts, sig, 3, 6, 4, prec, ell=0.3, eps=eps)
+    plain = run(bb, pts, sig, 3, 6, 4, "fp32", ell=0.3, eps=eps)
+    ref = oracle.bbfmm(pts, sig.astype(np.float64), 3, 6, 4, ell=0.3, lo=W.UNIT_LO, side=W.UNIT_SIDE)
+    print("rank>128 %s eps %.0e: vs oracle %.2e, fp32 vs oracle %.2e, vs fp32 %.2e"
+          % (prec, eps, oracle.rel_err(got, ref), oracle.rel_err(plain, ref), rel(got, plain)))
+    assert oracle.rel_err(got, ref) <= 1e-5
+    assert rel(got, plain) < 4e-6
