@@ -15,9 +15,12 @@
  *       far field:    M2L over the interaction list I(alpha)      (Sec. 2.2 item 2, Def. 2.1)
  *       downward:     L2L, then L2P on leaves                     (Sec. 2.2 item 3)
  *       near field:   P2P over the neighbours N(alpha)            (Sec. 2.2 item 4, Def. 2.1)
- *     with Chebyshev nodes (Sec. 2.2 node sets), the 1D/3D Lagrange basis
- *     (Def. 2.2) and the M2L operator K(x*_i, y*_j) evaluated at the nodes of
- *     the two boxes, uncompressed (Eq. low-rank-form).  The 316 distinct
+ *     with Chebyshev nodes or equally spaced nodes (the two node sets of
+ *     Sec. 2.2), the 1D/3D Lagrange basis (Def. 2.2) and the M2L operator
+ *     K(x*_i, y*_j) evaluated at the nodes of the two boxes, uncompressed
+ *     (Eq. low-rank-form).  With equally spaced nodes that dense operator is
+ *     the block-Toeplitz matrix the paper applies by FFT (Sec. 2.5 "Fast M2L
+ *     translation"); the oracle applies it as the plain matrix product.  The 316 distinct
  *     translation operators of a level are tabulated once per level, as the
  *     memory discussion after Thm. 2.1 states.
  *
@@ -32,11 +35,16 @@
  *     for the smooth ones.
  *   - the traversal is the level-by-level form Sec. 2.3 names as the
  *     alternative to the task-based one; results do not depend on it.
+ *   - equally spaced nodes: the paper prints them on [0, 1] as (k-1)/(p-1);
+ *     on the reference interval [-1, 1] of a box (where the Chebyshev nodes
+ *     live) they are -1 + 2 (k-1)/(p-1), k = 1..p, end points included.
  *
  * Parity pins: tests/test_oracle_pins.py checks this file against numpy brute
  * force, closed forms, depth-0/1 identity with the direct sum, exact
  * reproduction of a low-degree polynomial kernel, the interaction-list
- * partition, symmetry, invariances and error decay in p.
+ * partition, symmetry, invariances and error decay in p, for both node sets;
+ * the equally spaced nodes also against their closed form, and their M2L
+ * operator against its block-Toeplitz structure applied by numpy's FFT.
  */
 #include <math.h>
 #include <stdint.h>
@@ -151,6 +159,14 @@ void oracle_cheb_nodes(int p, double *s)
         s[k - 1] = cos((2.0 * k - 1.0) * OR_PI / (2.0 * p));
 }
 
+/* Equally spaced nodes (Sec. 2.2): (k-1)/(p-1) on [0, 1], i.e.
+ * -1 + 2 (k-1)/(p-1) on [-1, 1], k = 1..p, stored 0-based. */
+void oracle_uniform_nodes(int p, double *s)
+{
+    for (int k = 1; k <= p; ++k)
+        s[k - 1] = -1.0 + 2.0 * (k - 1.0) / (p - 1.0);
+}
+
 /* ell_p(x*_i, x) = prod_{k != i} (x - x*_k) / (x*_i - x*_k), for i = 0..p-1. */
 void oracle_lagrange_1d(int p, const double *s, double x, double *out)
 {
@@ -187,7 +203,7 @@ typedef struct {
     int64_t n;
     const double *pts;
     const double *sigma;
-    double *s;          /* p Chebyshev nodes */
+    double *s;          /* p interpolation nodes on [-1, 1] */
     int64_t *leaf_of;   /* leaf index of each point */
     int64_t *lstart;    /* CSR over leaves: points of leaf b are order[lstart[b] .. lstart[b+1]) */
     int64_t *order;     /* point ids, increasing inside a leaf */
@@ -558,9 +574,10 @@ static void or_bin_sources(or_tree *t)
 }
 
 static int or_setup(or_tree *t, int64_t n, const double *pts, const double *sigma, int nrhs, int kid, double ell,
-                    int p, int D, const double *lo, double side)
+                    int p, int D, const double *lo, double side, int nodes)
 {
-    if (n < 1 || nrhs < 1 || nrhs > 256 || p < 2 || p > 10 || D < 0 || D > 8 || !(side > 0.0))
+    if (n < 1 || nrhs < 1 || nrhs > 256 || p < 2 || p > 10 || D < 0 || D > 8 || !(side > 0.0) ||
+        (nodes != 0 && nodes != 1))
         return -1;
     memset(t, 0, sizeof(*t));
     t->D = D;
@@ -576,13 +593,17 @@ static int or_setup(or_tree *t, int64_t n, const double *pts, const double *sigm
     t->pts = pts;
     t->sigma = sigma;
     t->s = (double *)malloc(sizeof(double) * p);
-    oracle_cheb_nodes(p, t->s);
+    if (nodes == 0)
+        oracle_cheb_nodes(p, t->s);
+    else
+        oracle_uniform_nodes(p, t->s);
     or_bin_sources(t);
     return 0;
 }
 
 /* pts: n x 3 row-major (targets = sources), sigma: n x nrhs column-major.
- * lo[3], side: the cubical domain.  p: Chebyshev nodes per axis (2..10).
+ * lo[3], side: the cubical domain.  nodes: 0 = Chebyshev, 1 = equally spaced.
+ * p: nodes per axis (2..10).
  * D: depth, 8^D leaves.  nsample >= 0 with sample != NULL: phi is produced only
  * for those targets (phi: nsample x nrhs column-major); the far field is then
  * computed only for the boxes on their ancestor chains, which gives the same
@@ -592,11 +613,11 @@ static int or_setup(or_tree *t, int64_t n, const double *pts, const double *sigm
  * upward pass, far field, downward pass, near field.
  * Returns 0, or -1 on invalid arguments. */
 int oracle_bbfmm(int64_t n, const double *pts, const double *sigma, int nrhs, int kid, double ell,
-                 int p, int D, const double *lo, double side, int64_t nsample, const int64_t *sample,
+                 int p, int D, const double *lo, double side, int nodes, int64_t nsample, const int64_t *sample,
                  double *phi, double *M_dump, double *F_dump, double *times)
 {
     or_tree t;
-    if (or_setup(&t, n, pts, sigma, nrhs, kid, ell, p, D, lo, side) != 0)
+    if (or_setup(&t, n, pts, sigma, nrhs, kid, ell, p, D, lo, side, nodes) != 0)
         return -1;
     int64_t ntgt = nsample >= 0 && sample ? nsample : n;
     double *tx = (double *)malloc(sizeof(double) * 3 * ntgt);
@@ -618,11 +639,11 @@ int oracle_bbfmm(int64_t n, const double *pts, const double *sigma, int nrhs, in
  * column-major.  Every other argument as in oracle_bbfmm.  Returns 0, or -1
  * on invalid arguments. */
 int oracle_bbfmm_targets(int64_t ns, const double *src, const double *sigma, int nrhs, int kid, double ell,
-                         int p, int D, const double *lo, double side, int64_t nt, const double *tgt,
+                         int p, int D, const double *lo, double side, int nodes, int64_t nt, const double *tgt,
                          double *phi, double *times)
 {
     or_tree t;
-    if (nt < 1 || or_setup(&t, ns, src, sigma, nrhs, kid, ell, p, D, lo, side) != 0)
+    if (nt < 1 || or_setup(&t, ns, src, sigma, nrhs, kid, ell, p, D, lo, side, nodes) != 0)
         return -1;
     double hD = side / (double)((int64_t)1 << D);
     int64_t *tleaf = (int64_t *)malloc(sizeof(int64_t) * nt);

@@ -53,12 +53,13 @@ def lib():
             i64, i32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_double
             L.oracle_direct.argtypes = [i64, dp, i64, dp, dp, i32, i32, f64, dp]
             L.oracle_direct.restype = None
-            L.oracle_bbfmm.argtypes = [i64, dp, dp, i32, i32, f64, i32, i32, dp, f64,
+            L.oracle_bbfmm.argtypes = [i64, dp, dp, i32, i32, f64, i32, i32, dp, f64, i32,
                                        i64, lp, dp, dp, dp, dp]
             L.oracle_bbfmm.restype = i32
-            L.oracle_bbfmm_targets.argtypes = [i64, dp, dp, i32, i32, f64, i32, i32, dp, f64, i64, dp, dp, dp]
+            L.oracle_bbfmm_targets.argtypes = [i64, dp, dp, i32, i32, f64, i32, i32, dp, f64, i32, i64, dp, dp, dp]
             L.oracle_bbfmm_targets.restype = i32
             L.oracle_cheb_nodes.argtypes = [i32, dp]
+            L.oracle_uniform_nodes.argtypes = [i32, dp]
             L.oracle_lagrange_1d.argtypes = [i32, dp, f64, dp]
             L.oracle_neighbors.argtypes = [i32, i64, i64, i64, lp]
             L.oracle_neighbors.restype = i32
@@ -168,8 +169,14 @@ def cheb_nodes(p):
     return out
 
 
-def lagrange_1d(p, x):
-    s = cheb_nodes(p)
+def uniform_nodes(p):
+    out = np.zeros(p)
+    lib().oracle_uniform_nodes(p, _dp(out))
+    return out
+
+
+def lagrange_1d(p, x, nodes="chebyshev"):
+    s = cheb_nodes(p) if nodes == "chebyshev" else uniform_nodes(p)
     out = np.zeros(p)
     lib().oracle_lagrange_1d(p, _dp(s), float(x), _dp(out))
     return out
@@ -195,12 +202,17 @@ def leaf_cells(points, lo, side, depth):
     return out
 
 
+NODE_SETS = {"chebyshev": 0, "uniform": 1}
+
+
 def bbfmm(points, sigma, kid, p, depth, ell=1.0, lo=None, side=None, sample=None,
-          dump=False, times=False):
+          dump=False, times=False, nodes="chebyshev"):
     """FP64 black-box FMM (Sec. 2.2).  Returns phi (n,) / (n, nrhs), or for a
     ``sample`` of target indices phi at those targets only.  With ``dump`` also
     returns lists M[l], F[l] of arrays (8^l, nrhs, p^3) in lexicographic box
-    order; with ``times`` the four stage times in seconds."""
+    order; with ``times`` the four stage times in seconds.  ``nodes``: the
+    interpolation node set, "chebyshev" or "uniform" (equally spaced, Sec. 2.2),
+    the M2L always the dense operator K(x*_i, y*_j)."""
     pts = _f64c(points)
     n = pts.shape[0]
     s, nrhs = _sigma_colmajor(sigma, n)
@@ -219,7 +231,7 @@ def bbfmm(points, sigma, kid, p, depth, ell=1.0, lo=None, side=None, sample=None
     Fd = np.zeros(tot) if dump else None
     tm = np.zeros(4)
     rc = lib().oracle_bbfmm(n, _dp(pts), _dp(s), nrhs, kid, float(ell), p, depth, _dp(lo),
-                            float(side), ns, _lp(samp) if samp is not None else None,
+                            float(side), NODE_SETS[nodes], ns, _lp(samp) if samp is not None else None,
                             _dp(phi), _dp(Md) if dump else None, _dp(Fd) if dump else None,
                             _dp(tm))
     if rc != 0:
@@ -239,7 +251,7 @@ def bbfmm(points, sigma, kid, p, depth, ell=1.0, lo=None, side=None, sample=None
     return (res, *extra) if extra else res
 
 
-def bbfmm_targets(sources, sigma, targets, kid, p, depth, ell=1.0, lo=None, side=None):
+def bbfmm_targets(sources, sigma, targets, kid, p, depth, ell=1.0, lo=None, side=None, nodes="chebyshev"):
     """FP64 black-box FMM with a target set apart from the sources (Sec. 1:
     the two sets may differ).  Both must lie in the cubical domain (default:
     the bounding cube of their union).  Returns phi at the targets, (nt,) or
@@ -252,7 +264,7 @@ def bbfmm_targets(sources, sigma, targets, kid, p, depth, ell=1.0, lo=None, side
     lo = _f64c(lo, (3,))
     phi = np.zeros((tgt.shape[0], nrhs), dtype=np.float64, order="F")
     rc = lib().oracle_bbfmm_targets(src.shape[0], _dp(src), _dp(s), nrhs, kid, float(ell), p, depth, _dp(lo),
-                                    float(side), tgt.shape[0], _dp(tgt), _dp(phi), None)
+                                    float(side), NODE_SETS[nodes], tgt.shape[0], _dp(tgt), _dp(phi), None)
     if rc != 0:
         raise ValueError("oracle_bbfmm_targets rejected its arguments")
     return phi[:, 0] if np.ndim(sigma) == 1 else phi

@@ -54,32 +54,45 @@ def _build_mutant(tmp_path, name, old, new):
     dp = ctypes.POINTER(ctypes.c_double)
     lp = ctypes.POINTER(ctypes.c_int64)
     i64, i32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_double
-    L.oracle_bbfmm.argtypes = [i64, dp, dp, i32, i32, f64, i32, i32, dp, f64, i64, lp, dp, dp, dp, dp]
+    L.oracle_bbfmm.argtypes = [i64, dp, dp, i32, i32, f64, i32, i32, dp, f64, i32, i64, lp, dp, dp, dp, dp]
     L.oracle_bbfmm.restype = i32
+    L.oracle_uniform_nodes.argtypes = [i32, dp]
     return L
 
 
-def _run(L, x, s, kid, p, D):
+def _run(L, x, s, kid, p, D, nodes=0):
     dp = ctypes.POINTER(ctypes.c_double)
     x = np.ascontiguousarray(x)
     s = np.ascontiguousarray(s)
     lo = np.zeros(3)
     phi = np.zeros(x.shape[0])
     rc = L.oracle_bbfmm(x.shape[0], x.ctypes.data_as(dp), s.ctypes.data_as(dp), 1, kid, 1.0, p, D,
-                        lo.ctypes.data_as(dp), 1.0, -1, None, phi.ctypes.data_as(dp), None, None, None)
+                        lo.ctypes.data_as(dp), 1.0, nodes, -1, None, phi.ctypes.data_as(dp), None, None, None)
     assert rc == 0
     return phi
 
 
+@pytest.mark.parametrize("nodes", ["chebyshev", "uniform"])
 @pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_polynomial_pin_catches_mutant(oracle, tmp_path, name):
+def test_polynomial_pin_catches_mutant(oracle, tmp_path, name, nodes):
     old, new = MUTANTS[name]
     L = _build_mutant(tmp_path, name, old, new)
     x = W.uniform_points(1200, seed=31)
     s = W.uniform_sigma(1200, seed=32)
     ref = oracle.direct(x, x, s, 100)
     # the unmutated oracle reproduces the polynomial kernel to rounding ...
-    assert oracle.rel_err(oracle.bbfmm(x, s, 100, p=4, depth=3, lo=np.zeros(3), side=1.0), ref) < 1e-12
-    # ... each mutant does not
-    err = oracle.rel_err(_run(L, x, s, 100, 4, 3), ref)
+    assert oracle.rel_err(oracle.bbfmm(x, s, 100, p=4, depth=3, lo=np.zeros(3), side=1.0, nodes=nodes), ref) < 1e-12
+    # ... each mutant does not, with either node set
+    err = oracle.rel_err(_run(L, x, s, 100, 4, 3, oracle.NODE_SETS[nodes]), ref)
     assert err > 1e-8, (name, err)
+
+
+def test_node_formula_pin_catches_mutant(oracle, tmp_path):
+    """Any distinct nodes reproduce a polynomial kernel, so a wrong spacing of
+    the equally spaced nodes is caught by the closed-form pin instead."""
+    L = _build_mutant(tmp_path, "uniform_spacing", "s[k - 1] = -1.0 + 2.0 * (k - 1.0) / (p - 1.0);",
+                      "s[k - 1] = -1.0 + 2.0 * (k - 1.0) / p;")
+    out = np.zeros(5)
+    L.oracle_uniform_nodes(5, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    np.testing.assert_array_equal(oracle.uniform_nodes(5), np.linspace(-1.0, 1.0, 5))
+    assert not np.allclose(out, np.linspace(-1.0, 1.0, 5))

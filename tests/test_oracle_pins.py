@@ -332,3 +332,108 @@ def test_fmm_separate_targets(oracle):
     np.testing.assert_allclose(d1, oracle.direct(tgt, src, sig, oracle.K_INV_R), rtol=1e-10, atol=1e-10)
     far = oracle.bbfmm_targets(src, sig, tgt, oracle.K_INV_R, 6, 3, lo=lo, side=side)
     assert oracle.rel_err(far, oracle.direct(tgt, src, sig, oracle.K_INV_R)) < 1e-5
+
+
+# --- equally spaced nodes (Sec. 2.2) and the Toeplitz M2L they give (Sec. 2.5)
+
+@pytest.mark.parametrize("p", [2, 3, 5, 8])
+def test_uniform_nodes_closed_form(oracle, p):
+    # (k - 1) / (p - 1) on [0, 1] is -1 + 2 (k - 1) / (p - 1) on [-1, 1]
+    np.testing.assert_allclose(oracle.uniform_nodes(p), np.linspace(-1.0, 1.0, p), rtol=0, atol=1e-15)
+    if p == 5:
+        np.testing.assert_array_equal(oracle.uniform_nodes(5), [-1.0, -0.5, 0.0, 0.5, 1.0])
+
+
+@pytest.mark.parametrize("p", [3, 5, 7])
+def test_uniform_lagrange_cardinal_unity_and_scipy(oracle, p):
+    from scipy.interpolate import BarycentricInterpolator
+    s = oracle.uniform_nodes(p)
+    for i in range(p):
+        np.testing.assert_allclose(oracle.lagrange_1d(p, s[i], nodes="uniform"), np.eye(p)[i], atol=1e-14)
+    xs = np.random.default_rng(2).uniform(-1, 1, 9)
+    for x in xs:
+        assert oracle.lagrange_1d(p, x, nodes="uniform").sum() == pytest.approx(1.0, abs=1e-13)
+    for i in range(p):
+        ref = BarycentricInterpolator(s, np.eye(p)[i])(xs)
+        got = np.array([oracle.lagrange_1d(p, x, nodes="uniform")[i] for x in xs])
+        np.testing.assert_allclose(got, ref, atol=1e-12)
+
+
+@pytest.mark.parametrize("p,depth,kind", [(3, 2, "uniform"), (3, 3, "clustered"), (4, 3, "uniform")])
+def test_uniform_nodes_fmm_reproduces_low_degree_polynomial_kernel(oracle, p, depth, kind):
+    """Lagrange interpolation on any p >= 3 distinct nodes is exact for the
+    degree-2 test kernel, so the FMM with equally spaced nodes equals the
+    direct sum up to rounding."""
+    x = W.make_points(kind, 1500, seed=25)
+    s = W.uniform_sigma(1500, seed=26)
+    ref = oracle.direct(x, x, s, K_POLY)
+    assert oracle.rel_err(oracle.bbfmm(x, s, K_POLY, p=p, depth=depth, nodes="uniform"), ref) < 1e-12
+    # and two nodes (linear interpolation) do not reproduce it
+    assert oracle.rel_err(oracle.bbfmm(x, s, K_POLY, p=2, depth=depth, nodes="uniform"), ref) > 1e-6
+
+
+@pytest.mark.parametrize("depth", [0, 1])
+def test_uniform_nodes_depth0_1_equals_direct(oracle, depth):
+    x = W.uniform_points(700, seed=27)
+    s = W.uniform_sigma(700, seed=28)
+    ref = oracle.direct(x, x, s, K_INV_R)
+    assert oracle.rel_err(oracle.bbfmm(x, s, K_INV_R, p=4, depth=depth, nodes="uniform"), ref) < 1e-14
+
+
+@pytest.mark.parametrize("kid", [K_INV_R, K_EXP])
+def test_uniform_nodes_error_decays_with_p(oracle, kid):
+    """Equally spaced nodes: for the low orders the paper recommends the error
+    against the direct sum still falls with p (N = 10^4 uniform), at a level
+    within a small factor of the Chebyshev nodes'."""
+    n = 10_000
+    x = W.uniform_points(n, seed=17)
+    s = W.uniform_sigma(n, seed=18)
+    ref = oracle.direct(x, x, s, kid)
+    errs = [oracle.rel_err(oracle.bbfmm(x, s, kid, p=p, depth=3, nodes="uniform"), ref) for p in range(2, 7)]
+    for a, b in zip(errs, errs[1:]):
+        assert b < a, errs
+    cheb = oracle.rel_err(oracle.bbfmm(x, s, kid, p=5, depth=3), ref)
+    assert cheb < errs[3] < 4 * cheb, (errs[3], cheb)
+
+
+def _uniform_m2l_dense(oracle, p, h, t, kid, ell):
+    # K(x*_i, y*_j) between a target box at the origin and a source box at
+    # offset t (in boxes), equally spaced nodes, i = i1 + p i2 + p^2 i3
+    s = oracle.uniform_nodes(p)
+    g = np.array([[s[i1], s[i2], s[i3]] for i3 in range(p) for i2 in range(p) for i1 in range(p)]) * h / 2
+    K = np.zeros((p ** 3, p ** 3))
+    for i in range(p ** 3):
+        for j in range(p ** 3):
+            K[i, j] = oracle.kernel(kid, g[i], g[j] + h * np.asarray(t, dtype=float), ell)
+    return K
+
+
+@pytest.mark.parametrize("kid,ell,p,t", [(K_INV_R, 1.0, 4, (2, -1, 3)), (K_EXP, 0.3, 5, (-3, 0, 2)),
+                                         (K_GAUSS, 0.5, 3, (3, 3, -3))])
+def test_uniform_m2l_is_block_toeplitz_and_applies_by_fft(oracle, kid, ell, p, t):
+    """Sec. 2.5: with equally spaced nodes an M2L operator has (2p-1)^3
+    distinct entries, K[i][j] = c(i - j) per axis, and its product with a
+    vector equals a circular convolution of size (2p)^3 (zero-padded input,
+    the first p outputs per axis), i.e. three FFTs.  Checked on the oracle's
+    dense operator with numpy's FFT."""
+    h = 0.125
+    K = _uniform_m2l_dense(oracle, p, h, t, kid, ell)
+    n = 2 * p
+    # the (2p-1)^3 table from one row and one column per axis
+    c = np.zeros((n, n, n))      # c[dz, dy, dx] at index d mod n
+    for i3 in range(p):
+        for i2 in range(p):
+            for i1 in range(p):
+                for j3 in range(p):
+                    for j2 in range(p):
+                        for j1 in range(p):
+                            v = K[i1 + p * i2 + p * p * i3, j1 + p * j2 + p * p * j3]
+                            idx = ((i3 - j3) % n, (i2 - j2) % n, (i1 - j1) % n)
+                            if c[idx] != 0.0:     # Toeplitz: one value per difference
+                                assert v == pytest.approx(c[idx], rel=1e-13, abs=0)
+                            c[idx] = v
+    m = np.random.default_rng(29).standard_normal(p ** 3)
+    mp = np.zeros((n, n, n))
+    mp[:p, :p, :p] = m.reshape(p, p, p)
+    conv = np.fft.irfftn(np.fft.rfftn(c) * np.fft.rfftn(mp), s=(n, n, n), axes=(0, 1, 2))[:p, :p, :p].reshape(-1)
+    np.testing.assert_allclose(conv, K @ m, rtol=0, atol=1e-12 * np.abs(K @ m).max())
