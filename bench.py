@@ -13,6 +13,7 @@ steps by writing a 512 MB buffer (the working set is smaller than L2).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                     [--workload NAME] [--precision fp16x3|tf32x3|bf16x3|tf32|fp32]
+                    [--interp chebyshev|uniform]
 
 Prints one JSON line (rank 0).  Under torchrun every rank runs an
 independent replica of the workload (the matvec is single-GPU: replicas
@@ -48,6 +49,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="uniform-1M-p5-d5", choices=sorted(W.CONFIGS))
     ap.add_argument("--precision", default="fp16x3")
+    ap.add_argument("--interp", default="chebyshev", choices=["chebyshev", "uniform"],
+                    help="uniform: equally spaced nodes with the Fourier-domain M2L (FP32)")
     ap.add_argument("--svd-eps", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-depth6", action="store_true")
@@ -212,10 +215,10 @@ def describe(c):
             % (c["name"], c["n"], c["kind"], KERNEL_NAMES[c["kernel"]], c["ell"], c["p"], c["depth"], c["nrhs"]))
 
 
-def time_plan(bb, torch, dev, pts, sig_dev, c, depth, precision, eps, flush, stream, nsteps=5):
+def time_plan(bb, torch, dev, pts, sig_dev, c, depth, precision, eps, flush, stream, nsteps=5, interp="chebyshev"):
     """Mean device time of nsteps matvecs (L2 flushed before each)."""
     plan = bb.Plan(torch.from_numpy(pts).to(dev), c["kernel"], c["p"], depth, ell=c["ell"], precision=precision,
-                   svd_eps=eps, domain=(W.UNIT_LO, W.UNIT_SIDE), max_nrhs=c["nrhs"])
+                   svd_eps=eps, domain=(W.UNIT_LO, W.UNIT_SIDE), max_nrhs=c["nrhs"], interp=interp)
     phi = torch.empty_like(sig_dev)
     for _ in range(3):
         bb.bbfmm_matvec(plan.handle, sig_dev, phi, c["nrhs"], stream)
@@ -239,8 +242,23 @@ def time_plan(bb, torch, dev, pts, sig_dev, c, depth, precision, eps, flush, str
 M2L_TRAFFIC = {("uniform-1M-p5-d5", "fp16x3"): 28382464 + 752128}
 
 
-def roofline(precision, info, nrhs, m2l_ms, clocks, torch, dev, workload=None):
+def roofline(precision, info, nrhs, m2l_ms, clocks, torch, dev, workload=None, interp="chebyshev", p=5):
     peaks, kind = measured_peaks()
+    if interp == "uniform":
+        # Fourier-domain M2L: per interaction pair and kept frequency one
+        # complex multiply-add (8 flops) on the FP32 pipe; the per-box DFTs are
+        # not counted (they are ~5 % of the pairs' work at p = 5)
+        nf = 2 * p - 1
+        nw = nf * nf * p
+        flops = 8.0 * info.m2l_pairs * nw * nrhs
+        f_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = sms * 128 * 2 * f_mhz * 1e6 / 1e12
+        achieved = flops / (m2l_ms / 1e3) / 1e12
+        return {"kernel": "k_fft_fwd + k_fft_m2l + k_fft_inv (all levels)", "bound": "alu", "peak": peak,
+                "peak_source": "FP32 FMA: %d SMs x 128 lanes x 2 flop x median SM clock %.0f MHz" % (sms, f_mhz),
+                "achieved": achieved, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "work": "8 flops x %d interaction pairs x %d frequencies x %d RHS" % (info.m2l_pairs, nw, nrhs)}
     passes = {"fp32": 1, "tf32": 1, "tf32x3": 3, "bf16x3": 3, "fp16x3": 3}[precision]
     flops = 2.0 * info.m2l_pairs * info.rank * info.rank * passes * nrhs
     achieved = flops / (m2l_ms / 1e3) / 1e12
@@ -275,11 +293,12 @@ def run_ours(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    precision = args.precision
+    interp = args.interp
+    precision = args.precision if interp == "chebyshev" else "fp32"
     c, pts, sig_host = workload(args.workload)
     n, nrhs, depth = c["n"], c["nrhs"], c["depth"]
     plan = bb.Plan(torch.from_numpy(pts).to(dev), c["kernel"], c["p"], depth, ell=c["ell"], precision=precision,
-                   svd_eps=args.svd_eps, domain=(W.UNIT_LO, W.UNIT_SIDE), max_nrhs=nrhs)
+                   svd_eps=args.svd_eps, domain=(W.UNIT_LO, W.UNIT_SIDE), max_nrhs=nrhs, interp=interp)
     info = plan.info()
     sigma = torch.from_numpy(np.ascontiguousarray(sig_host.T)).to(dev)   # (nrhs, n): column-major n x nrhs
     phi = torch.empty_like(sigma)
@@ -347,10 +366,11 @@ def run_ours(args, rank, world, local):
         e2e.append(time.perf_counter() - t0)
     e2e_s = float(np.mean(e2e))
 
-    acc = accuracy_check(pts, sig_host, phi_pin.numpy().T.astype(np.float64), c) if rank == 0 else None
+    acc = accuracy_check(pts, sig_host, phi_pin.numpy().T.astype(np.float64), c, nodes=interp) if rank == 0 else None
     extra = {}
     if rank == 0 and not args.no_depth6 and args.workload == "uniform-1M-p5-d5":
-        extra["depth6"] = time_plan(bb, torch, dev, pts, sigma, c, 6, precision, args.svd_eps, flush, stream)
+        extra["depth6"] = time_plan(bb, torch, dev, pts, sigma, c, 6, precision, args.svd_eps, flush, stream,
+                                    interp=interp)
     if rank == 0 and precision != "fp32" and not args.no_plain:
         plain = time_plan(bb, torch, dev, pts, sigma, c, depth, "fp32", args.svd_eps, flush, stream)
         plain["speedup_of_this_form"] = plain["ms_per_step"] / ms
@@ -359,7 +379,7 @@ def run_ours(args, rank, world, local):
     clocks = clk.summary()
     N = float(n)
     unit = "N^2/s" if nrhs == 1 else "N^2*nrhs/s"
-    m2l_launches = depth - 1 if precision == "fp32" else 1
+    m2l_launches = (3 if interp == "uniform" else 1) * (depth - 1) if precision == "fp32" else 1
     # gather, P2P, upward pass (+ 16-bit split for those forms), M2L, downward pass, combine
     split = 1 if precision in ("fp16x3", "bf16x3") else 0
     launches = 1 + 1 + 1 + split + m2l_launches + 1 + 1
@@ -368,11 +388,13 @@ def run_ours(args, rank, world, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": describe(c), "n": n, "kernel": KERNEL_NAMES[c["kernel"]], "ell": c["ell"],
-                   "p": c["p"], "depth": depth, "nrhs": nrhs, "m2l_precision": precision, "svd_rank": info.rank,
+                   "p": c["p"], "depth": depth, "nrhs": nrhs, "interp": interp, "m2l_precision": precision,
+                   "svd_rank": info.rank,
                    "svd_eps": args.svd_eps, "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": "replicas"},
         "stages_ms": {k: float(v) for k, v in zip(bb.STAGES, stage)},
-        "roofline": roofline(precision, info, nrhs, float(stage[2]), clocks, torch, dev, args.workload),
+        "roofline": roofline(precision, info, nrhs, float(stage[2]), clocks, torch, dev, args.workload, interp,
+                             c["p"]),
         "e2e": {"value": world * N * N * nrhs / e2e_s, "unit": unit, "ms": e2e_s * 1e3,
                 "h2d_bytes_per_step": 4 * n * nrhs, "d2h_bytes_per_step": 4 * n * nrhs},
         "gpu_launches": launches * args.steps,
@@ -392,14 +414,14 @@ def run_ours(args, rank, world, local):
     return out if rank == 0 else None
 
 
-def accuracy_check(pts, sig, phi, c, nsample=256, ncols=4):
-    """Sampled targets against the oracle bbFMM (uncompressed M2L, FP64) and
-    exact direct-sum rows, on the first ncols right-hand sides."""
+def accuracy_check(pts, sig, phi, c, nsample=256, ncols=4, nodes="chebyshev"):
+    """Sampled targets against the oracle bbFMM (uncompressed M2L, FP64, same
+    node set) and exact direct-sum rows, on the first ncols right-hand sides."""
     from oracle import oracle
     idx = np.sort(np.random.default_rng(99).choice(pts.shape[0], nsample, replace=False))
     s64 = sig[:, :ncols].astype(np.float64)
     ref = oracle.bbfmm(pts, s64, c["kernel"], c["p"], c["depth"], ell=c["ell"], lo=W.UNIT_LO, side=W.UNIT_SIDE,
-                       sample=idx)
+                       sample=idx, nodes=nodes)
     direct = oracle.direct(pts[idx], pts, s64, c["kernel"], c["ell"])
     got = phi[idx, :ncols]
     return {"sample": nsample, "columns": int(min(ncols, sig.shape[1])),

@@ -50,6 +50,15 @@ extern "C" {
 #define BBFMM_K_TEST_POLY 100  /* 1 + d1 - 2 d2 d3 + 3 d1^2 d2, d = x - y: exact for p >= 3 */
 #define BBFMM_K_TEST_CONST 101 /* 1 */
 
+/* interpolation nodes and the M2L that goes with them (Sec. 2.2 node sets,
+ * Sec. 2.5 "Fast M2L translation") */
+#define BBFMM_INTERP_CHEBYSHEV 0 /* Chebyshev nodes, SVD-compressed M2L (default) */
+#define BBFMM_INTERP_UNIFORM 1   /* equally spaced nodes (end points included); the
+                                    block-Toeplitz M2L applied in the Fourier domain:
+                                    per box a (2p-1)^3 DFT of its coefficients, per
+                                    frequency a 189-term sum over the interaction list,
+                                    an inverse DFT per box; FP32; no compression */
+
 /* arithmetic of the M2L stage (every other stage computes in FP32) */
 #define BBFMM_PREC_FP32 0   /* FP32 FMA on the CUDA cores */
 #define BBFMM_PREC_TF32 1   /* tensor cores, one TF32 pass, FP32 accumulation */
@@ -81,7 +90,9 @@ typedef struct {
                               local (F) coefficients of every level for
                               bbfmm_get_coefficients; 0 (default): they stay in
                               the passes' on-chip memory and are not allocated */
-    int reserved[4];   /* zero */
+    int interp;        /* BBFMM_INTERP_* (default CHEBYSHEV); UNIFORM takes
+                          precision = BBFMM_PREC_FP32 and ignores svd_eps */
+    int reserved[3];   /* zero */
 } bbfmm_opts;
 
 typedef struct {

@@ -24,6 +24,8 @@ BBFMM_K_INV_R, BBFMM_K_INV_R2, BBFMM_K_EXP, BBFMM_K_GAUSS = 1, 2, 3, 4
 BBFMM_K_TEST_POLY, BBFMM_K_TEST_CONST = 100, 101
 BBFMM_PREC_FP32, BBFMM_PREC_TF32, BBFMM_PREC_TF32X3, BBFMM_PREC_BF16X3, BBFMM_PREC_FP16X3 = 0, 1, 2, 3, 4
 
+INTERPS = {"chebyshev": 0, "uniform": 1}   # BBFMM_INTERP_*
+
 PRECISIONS = {"fp32": BBFMM_PREC_FP32, "tf32": BBFMM_PREC_TF32, "tf32x3": BBFMM_PREC_TF32X3,
               "bf16x3": BBFMM_PREC_BF16X3, "fp16x3": BBFMM_PREC_FP16X3}
 
@@ -39,7 +41,7 @@ class bbfmm_opts(ctypes.Structure):
                 ("lo", ctypes.c_double * 3), ("side", ctypes.c_double),
                 ("max_nrhs", ctypes.c_int), ("split_accumulate", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("keep_coefficients", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("interp", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class bbfmm_info(ctypes.Structure):
@@ -256,12 +258,13 @@ class Plan:
 
     def __init__(self, points, kernel, order, depth, ell=1.0, svd_eps=1e-7, precision="fp32",
                  domain=None, max_nrhs=1, stream=None, split_accumulate=True, use_graph=True,
-                 keep_coefficients=False, targets=None):
+                 keep_coefficients=False, targets=None, interp="chebyshev"):
         import torch
         o = bbfmm_default_opts()
         o.split_accumulate = 1 if split_accumulate else 0
         o.use_graph = 1 if use_graph else 0
         o.keep_coefficients = 1 if keep_coefficients else 0
+        o.interp = INTERPS[interp] if isinstance(interp, str) else int(interp)
         o.ell = float(ell)
         o.svd_eps = float(svd_eps)
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)

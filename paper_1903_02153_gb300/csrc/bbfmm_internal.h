@@ -91,7 +91,8 @@ struct HostOps {
     int kernel = 0, p = 0, p3 = 0, r = 0, rank_u = 0, rank_v = 0;
     double ell = 1.0, eps = 0.0;
     int hom_degree = 0;         // m of K(a x, a y) = a^m K(x, y); 0 = not homogeneous
-    std::vector<double> nodes;  // Chebyshev nodes s_k, k = 0..p-1
+    int interp = 0;             // BBFMM_INTERP_*: node set, and SVD (0) or Fourier (1) M2L
+    std::vector<double> nodes;  // interpolation nodes s_k on [-1, 1], k = 0..p-1
     std::vector<double> wbary;  // 1 / prod_{m != k} (s_k - s_m)
     std::vector<double> S;      // S[o][i][j] = l_i((s_j + 2o - 1) / 2), o = 0, 1
     // per operator level: (one level if homogeneous, else one per tree level 2..D)
@@ -101,6 +102,12 @@ struct HostOps {
     std::vector<std::vector<double>> V;  // p3 x r row-major
     std::vector<std::vector<double>> C;  // 316 x r x r: C[t] = U^T K^(t) V
     std::vector<std::vector<double>> sv; // singular values of the fat operator matrix
+    // equally spaced nodes: n = 2p - 1 point DFTs; per operator level the
+    // spectra of the 316 offsets' kernel tables, [w][316] complex (re, im
+    // interleaved), w = (wz n + wy) p + wx with wx < p (real input), divided
+    // by n^3 (the inverse transform's normalisation)
+    int nfft = 0, nw = 0;
+    std::vector<std::vector<double>> khat;
 };
 
 // offset index 0..315 of t = (tx, ty, tz) in [-3,3]^3 \ [-1,1]^3, or -1
@@ -122,7 +129,7 @@ __host__ __device__ inline int offset_index(int tx, int ty, int tz)
 }
 
 std::shared_ptr<HostOps> build_host_ops(int kernel, double ell, int p, double eps, int depth,
-                                        double side, std::string &err);
+                                        double side, int interp, std::string &err);
 double kernel_value_host(int kernel, double ell, double d0, double d1, double d2);
 
 // interpolation tables passed by value to the transfer kernels
@@ -154,6 +161,8 @@ struct DevOps {
     // [1] = BF16; same [316][rows64][rp] layout
     std::vector<uint16_t *> C16hi[2], C16lo[2];
     std::vector<float> c16_scale[2];
+    int nfft = 0, nw = 0;           // equally spaced nodes: DFT size, frequencies kept
+    std::vector<float2 *> khat;     // [w][316] kernel spectra per operator level
     std::mutex mu16;
     int64_t bytes = 0;
     ~DevOps();
@@ -164,6 +173,7 @@ int ensure_ops16(DevOps &O, int fmt); // capi.cu; fmt 0 = FP16, 1 = BF16
 // Plan
 struct Level {
     float *M = nullptr, *Mt = nullptr, *Ft = nullptr, *F = nullptr;
+    float2 *Mhat = nullptr, *Fhat = nullptr; // equally spaced nodes: spectra [w][R][boxes]
     float *Mt_hi = nullptr, *Mt_lo = nullptr;        // split TF32 copies of Mt
     uint16_t *Mt16_hi = nullptr, *Mt16_lo = nullptr; // split 16-bit copies of Mt
 };
@@ -180,6 +190,7 @@ struct bbfmm_plan_impl {
     double ell = 1.0, lo[3] = {0, 0, 0}, side = 1.0, eps = 1e-7;
     int device = 0;
     bool split_acc = true; // 3-pass tensor-core M2L: separate correction accumulator
+    int nodeset = 0;       // BBFMM_INTERP_*: interpolation nodes and M2L form
     int m2l_groups = 1;    // offset groups per M2L tile (partial slices of F~)
 
     // tree: sources, and the targets (the same arrays unless separate)
@@ -213,6 +224,9 @@ struct bbfmm_plan_impl {
     int4 *m2l_tiles = nullptr;
     int m2l_ntiles[kMaxDepth + 1] = {}, m2l_tile_off[kMaxDepth + 1] = {};
     bool keep_coeffs = false; // also store leaf M and every level's F
+    // Fourier-domain M2L: the 8^3-box tiles holding targets, per level
+    int4 *fft_tiles = nullptr;
+    int fft_ntiles[kMaxDepth + 1] = {}, fft_tile_off[kMaxDepth + 1] = {};
 
     std::vector<void *> allocations;
     int64_t bytes = 0;
@@ -322,6 +336,13 @@ cudaError_t m2l_fp32_init(); // uploads the offset table (outside any stream cap
 bool fill_m2l_table(int4 (*tab)[kOffsetsPerClass]);
 cudaError_t launch_m2l_fp32(const float *Mt, const float *C, float *Ft, int l, int r, int rp, int rows64,
                             int nrhs, int R, float scale, cudaStream_t s);
+// m2l_fft.cu: the far field with equally spaced nodes (Fourier-domain M2L)
+cudaError_t launch_m2l_fft(bbfmm_plan_impl *P, int nrhs, cudaStream_t s);
+cudaError_t m2l_fft_init(); // tap tables and kernel attributes (outside any capture)
+// target tiles (T^3 boxes, T = min(8, 2^l)) holding targets, levels D..2, as
+// {tx, ty, tz, 0}; count[l] per level
+void fft_active_tiles(int D, const std::vector<uint8_t> &leaf_occ, std::vector<int4> &tiles, int *count);
+int64_t fft_grid_boxes(int l); // boxes of the zero-padded M^ grid of level l
 // m2l_tc.cu: every level of the far field in one go (FP32 or tensor cores)
 cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s);
 int m2l_groups_for(int D, int nrhs, int precision, int r, int64_t active_tiles);

@@ -63,6 +63,9 @@ DevOps::~DevOps()
             for (uint16_t *ptr : *v)
                 if (ptr)
                     cudaFree(ptr);
+    for (float2 *ptr : khat)
+        if (ptr)
+            cudaFree(ptr);
 }
 
 // 16-bit split copies of the M2L operators (fmt 0 = FP16 scaled by a power of
@@ -112,13 +115,13 @@ int ensure_ops16(DevOps &O, int fmt)
     return BBFMM_OK;
 }
 
-typedef std::tuple<int, double, int, double, int, double, int> OpsKey;
+typedef std::tuple<int, double, int, double, int, double, int, int> OpsKey;
 static std::mutex g_ops_mu;
 static std::map<OpsKey, std::weak_ptr<DevOps>> g_ops_cache;
 
 void split_tf32(const float *in, float *hi, float *lo, int64_t n); // m2l_tc.cu (host helper)
 
-static int get_ops(int kernel, double ell, int p, double eps, int depth, double side, int device,
+static int get_ops(int kernel, double ell, int p, double eps, int depth, double side, int device, int interp,
                    std::shared_ptr<DevOps> &out)
 {
     // homogeneous kernels depend on the domain only through h_D
@@ -128,7 +131,9 @@ static int get_ops(int kernel, double ell, int p, double eps, int depth, double 
         key_side = side / (double)(1LL << depth);
         key_depth = 0;
     }
-    OpsKey key(kernel, ell, p, eps, key_depth, key_side, device);
+    if (interp == BBFMM_INTERP_UNIFORM)
+        eps = 0.0; // no compression
+    OpsKey key(kernel, ell, p, eps, key_depth, key_side, device, interp);
     std::lock_guard<std::mutex> g(g_ops_mu);
     auto it = g_ops_cache.find(key);
     if (it != g_ops_cache.end()) {
@@ -138,49 +143,66 @@ static int get_ops(int kernel, double ell, int p, double eps, int depth, double 
         }
     }
     std::string err;
-    auto host = build_host_ops(kernel, ell, p, eps, depth, side, err);
+    auto host = build_host_ops(kernel, ell, p, eps, depth, side, interp, err);
     if (!host)
         return fail(BBFMM_EINTERNAL, "operator precompute failed: %s", err.c_str());
     auto d = std::make_shared<DevOps>();
     d->host = host;
-    d->nlev = (int)host->C.size();
+    d->nlev = (int)host->U.size(); // operator levels (both node sets)
     d->r = host->r;
     d->rl = host->rl;
     d->rp = (int)round_up(std::max(host->r, 1), 16);
     d->rows64 = (int)round_up(std::max(host->r, 1), 64);
     d->p3p = (int)round_up(host->p3, 16);
     const int p3 = host->p3, r = host->r, rp = d->rp, rows64 = d->rows64, p3p = d->p3p;
+    d->nfft = host->nfft;
+    d->nw = host->nw;
     for (int k = 0; k < d->nlev; ++k) {
-        std::vector<float> V((size_t)p3 * rp, 0.f), Ut((size_t)r * p3p, 0.f),
-            C((size_t)kNumOffsets * rows64 * rp, 0.f);
+        std::vector<float> V((size_t)p3 * rp, 0.f), Ut((size_t)r * p3p, 0.f);
         for (int i = 0; i < p3; ++i)
             for (int a = 0; a < r; ++a) {
                 V[(size_t)i * rp + a] = (float)host->V[k][(size_t)i * r + a];
                 Ut[(size_t)a * p3p + i] = (float)host->U[k][(size_t)i * r + a];
             }
+        float *dV = nullptr, *dUt = nullptr;
+        CUDA_TRY(cudaMalloc(&dV, V.size() * 4));
+        d->V.push_back(dV);
+        CUDA_TRY(cudaMalloc(&dUt, Ut.size() * 4));
+        d->Ut.push_back(dUt);
+        CUDA_TRY(cudaMemcpy(dV, V.data(), V.size() * 4, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(dUt, Ut.data(), Ut.size() * 4, cudaMemcpyHostToDevice));
+        d->bytes += (int64_t)(V.size() + Ut.size()) * 4;
+        if (host->interp == BBFMM_INTERP_UNIFORM) {
+            // kernel spectra for the Fourier-domain M2L
+            const std::vector<double> &kh = host->khat[k];
+            std::vector<float2> hk(kh.size() / 2);
+            for (size_t q = 0; q < hk.size(); ++q)
+                hk[q] = make_float2((float)kh[2 * q], (float)kh[2 * q + 1]);
+            float2 *dk = nullptr;
+            CUDA_TRY(cudaMalloc(&dk, hk.size() * sizeof(float2)));
+            d->khat.push_back(dk);
+            CUDA_TRY(cudaMemcpy(dk, hk.data(), hk.size() * sizeof(float2), cudaMemcpyHostToDevice));
+            d->bytes += (int64_t)hk.size() * 8;
+            continue;
+        }
+        std::vector<float> C((size_t)kNumOffsets * rows64 * rp, 0.f);
         for (int t = 0; t < kNumOffsets; ++t)
             for (int a = 0; a < r; ++a)
                 for (int b = 0; b < r; ++b)
                     C[((size_t)t * rows64 + a) * rp + b] = (float)host->C[k][((size_t)t * r + a) * r + b];
         std::vector<float> Chi(C.size()), Clo(C.size());
         split_tf32(C.data(), Chi.data(), Clo.data(), (int64_t)C.size());
-        float *dV = nullptr, *dUt = nullptr, *dC = nullptr, *dChi = nullptr, *dClo = nullptr;
-        CUDA_TRY(cudaMalloc(&dV, V.size() * 4));
-        d->V.push_back(dV);
-        CUDA_TRY(cudaMalloc(&dUt, Ut.size() * 4));
-        d->Ut.push_back(dUt);
+        float *dC = nullptr, *dChi = nullptr, *dClo = nullptr;
         CUDA_TRY(cudaMalloc(&dC, C.size() * 4));
         d->C.push_back(dC);
         CUDA_TRY(cudaMalloc(&dChi, C.size() * 4));
         d->Chi.push_back(dChi);
         CUDA_TRY(cudaMalloc(&dClo, C.size() * 4));
         d->Clo.push_back(dClo);
-        CUDA_TRY(cudaMemcpy(dV, V.data(), V.size() * 4, cudaMemcpyHostToDevice));
-        CUDA_TRY(cudaMemcpy(dUt, Ut.data(), Ut.size() * 4, cudaMemcpyHostToDevice));
         CUDA_TRY(cudaMemcpy(dC, C.data(), C.size() * 4, cudaMemcpyHostToDevice));
         CUDA_TRY(cudaMemcpy(dChi, Chi.data(), C.size() * 4, cudaMemcpyHostToDevice));
         CUDA_TRY(cudaMemcpy(dClo, Clo.data(), C.size() * 4, cudaMemcpyHostToDevice));
-        d->bytes += (int64_t)(V.size() + Ut.size() + 3 * C.size()) * 4;
+        d->bytes += (int64_t)(3 * C.size()) * 4;
     }
     g_ops_cache[key] = d;
     out = d;
@@ -422,7 +444,7 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
     }
 
     // operators
-    PTRY(get_ops(P->kernel, P->ell, P->p, P->eps, D, P->side, P->device, P->ops));
+    PTRY(get_ops(P->kernel, P->ell, P->p, P->eps, D, P->side, P->device, P->nodeset, P->ops));
     P->interp = make_interp_tables(*P->ops->host);
 
     // per-level coefficient buffers
@@ -461,6 +483,24 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
             PTRY(plan_alloc(P, (void **)&L.Mt16_hi, 2 * 8 * (H + 2) * H * H * R * rp, true, s));
             PTRY(plan_alloc(P, (void **)&L.Mt16_lo, 2 * 8 * (H + 2) * H * H * R * rp, true, s));
         }
+        if (P->nodeset == BBFMM_INTERP_UNIFORM) {
+            // spectra: M^ on the grid with a zero halo of 3 boxes, F^ per box
+            const int64_t nw = P->ops->nw;
+            PTRY(plan_alloc(P, (void **)&L.Mhat, 8 * nw * R * fft_grid_boxes(l), true, s));
+            PTRY(plan_alloc(P, (void **)&L.Fhat, 8 * nw * R * nb, false, s));
+        }
+    }
+    std::vector<int4> ft; // read by the asynchronous copy below until the final synchronize
+    if (P->nodeset == BBFMM_INTERP_UNIFORM) {
+        fft_active_tiles(D, leaf_occ, ft, P->fft_ntiles);
+        for (int l = D, o = 0; l >= 2; --l) {
+            P->fft_tile_off[l] = o;
+            o += P->fft_ntiles[l];
+        }
+        if (!ft.empty()) {
+            PTRY(plan_alloc(P, (void **)&P->fft_tiles, sizeof(int4) * ft.size(), false, s));
+            CUDA_TRY(cudaMemcpyAsync(P->fft_tiles, ft.data(), sizeof(int4) * ft.size(), cudaMemcpyHostToDevice, s));
+        }
     }
     if (P->precision == BBFMM_PREC_FP16X3 || P->precision == BBFMM_PREC_BF16X3) {
         PTRY(ensure_ops16(*P->ops, P->precision == BBFMM_PREC_FP16X3 ? 0 : 1));
@@ -474,6 +514,8 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
 
     // constant tables the matvec kernels read, uploaded before any capture
     CUDA_TRY(m2l_fp32_init());
+    if (P->nodeset == BBFMM_INTERP_UNIFORM)
+        CUDA_TRY(m2l_fft_init());
     CUDA_TRY(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
     int prio_low = 0, prio_high = 0;
     CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
@@ -738,6 +780,11 @@ static int plan_create(const double *points, int64_t n, const double *targets, i
         return fail(BBFMM_EINVAL, "invalid options (ell > 0, svd_eps >= 0, 1 <= max_nrhs <= 1024)");
     if (opts.precision < BBFMM_PREC_FP32 || opts.precision > BBFMM_PREC_FP16X3)
         return fail(BBFMM_EINVAL, "unknown precision %d", opts.precision);
+    if (opts.interp != BBFMM_INTERP_CHEBYSHEV && opts.interp != BBFMM_INTERP_UNIFORM)
+        return fail(BBFMM_EINVAL, "unknown interp %d", opts.interp);
+    if (opts.interp == BBFMM_INTERP_UNIFORM && opts.precision != BBFMM_PREC_FP32)
+        return fail(BBFMM_EINVAL, "equally spaced nodes run the Fourier-domain M2L in FP32 (precision must be "
+                                  "BBFMM_PREC_FP32)");
     if (opts.domain_given && !(opts.side > 0.0 && isfinite(opts.side) && isfinite(opts.lo[0]) &&
                                isfinite(opts.lo[1]) && isfinite(opts.lo[2])))
         return fail(BBFMM_EINVAL, "invalid domain");
@@ -749,6 +796,13 @@ static int plan_create(const double *points, int64_t n, const double *targets, i
         const int64_t ntg = targets ? nt : 0;
         int64_t need = grid * 4 + n * (16 + 4 + 12LL * opts.max_nrhs) + ntg * (16 + 4 + 8LL * opts.max_nrhs) +
                        (1LL << (3 * depth)) * 8;
+        if (opts.interp == BBFMM_INTERP_UNIFORM) {
+            const int64_t nf = 2LL * cheb_order - 1, nw = nf * nf * cheb_order;
+            for (int l = 2; l <= depth; ++l) {
+                const int64_t g = (1LL << l) + 6;
+                need += 8 * nw * opts.max_nrhs * (g * g * g + (1LL << (3 * l)));
+            }
+        }
         size_t fr = 0, tot = 0;
         if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
             cudaGetLastError();
@@ -774,6 +828,7 @@ static int plan_create(const double *points, int64_t n, const double *targets, i
     P->split_acc = opts.split_accumulate != 0;
     P->use_graph = opts.use_graph != 0;
     P->keep_coeffs = opts.keep_coefficients != 0;
+    P->nodeset = opts.interp;
     if (opts.domain_given) {
         for (int d = 0; d < 3; ++d)
             P->lo[d] = opts.lo[d];
@@ -905,6 +960,7 @@ static int orthonormalize(const float *Y, int64_t n, int m, float *Q, int &mq, d
         for (int a = 0; a < m; ++a)
             T[a + (size_t)c * m] = (float)(W[(size_t)a * m + c] / sqrt(w[c]));
     CUDA_TRY(cudaMemcpyAsync(dT, T.data(), sizeof(float) * T.size(), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s)); // T is a local vector
     CUDA_TRY(launch_rmul(Y, n, m, dT, k, Q, s));
     mq = k;
     return BBFMM_OK;
@@ -963,6 +1019,7 @@ int bbfmm_rand_eig(bbfmm_plan_t plan, const float *omega, int m, int k, int powe
             for (int a = 0; a < mq; ++a)
                 T[a + (size_t)c * mq] = (float)V[(size_t)a * mq + c];
         CUDA_TRY(cudaMemcpyAsync(dT, T.data(), sizeof(float) * T.size(), cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaStreamSynchronize(s)); // T is a local vector
         CUDA_TRY(launch_rmul(basis, n, mq, dT, kk, evecs, s));
         if (kk < k)
             CUDA_TRY(cudaMemsetAsync(evecs + (size_t)kk * n, 0, sizeof(float) * n * (k - kk), s));

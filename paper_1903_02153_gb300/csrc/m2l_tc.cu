@@ -614,6 +614,8 @@ static cudaError_t launch_three(const TcLaunch &L, int nacc, bool cf, int grid, 
 
 cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
 {
+    if (P->nodeset == BBFMM_INTERP_UNIFORM)
+        return launch_m2l_fft(P, nrhs, s); // equally spaced nodes: Fourier-domain M2L
     const DevOps &O = *P->ops;
     auto scale_of = [&](int l) {
         // homogeneous kernels: operators made for the leaf box, scaled by (h_l / h_D)^m

@@ -21,6 +21,14 @@
 //  * Homogeneous kernels (Sec. 2.5 "Homogeneous kernel"): K(a x, a y) =
 //    a^m K(x, y), so one operator set made for the leaf box size serves every
 //    level, scaled by (h_l / h_D)^m.
+//  * Equally spaced nodes s_k = -1 + 2k/(p-1) (Sec. 2.2; the paper prints them
+//    on [0, 1]): no compression (U = V = I); instead, per offset t, the
+//    (2p-1)^3 distinct values of the block-Toeplitz operator (Sec. 2.5 "Fast
+//    M2L translation"): x*_i - y*_j = h (-t + (i - j) / (p - 1)) per axis, so
+//    K^(t)_ij = c_t(i - j), and K^(t) M is the circular convolution of c_t
+//    (stored at index d mod n, n = 2p - 1, which keeps the 2p - 1 differences
+//    apart) with M zero-padded to n^3, i.e. a pointwise product of DFTs.  The
+//    DFTs of the c_t are tabulated here in FP64.
 #include <math.h>
 
 #include <algorithm>
@@ -251,8 +259,85 @@ static void build_level(HostOps &o, double h, std::vector<double> &U, std::vecto
     }
 }
 
+// spectra of the 316 kernel tables c_t of one level (box side h), equally
+// spaced nodes: out[(w * 316 + u) * 2 + {0, 1}] = DFT(c_t)(w) / n^3 with
+// DFT(c)(w) = sum_j c[j] exp(-2 pi i (w . j) / n), j, w in [0, n)^3, w =
+// (wz n + wy) p + wx, wx < p
+static void build_khat(const HostOps &o, double h, std::vector<double> &out)
+{
+    const int p = o.p, n = 2 * p - 1, nw = n * n * p;
+    out.assign((size_t)nw * kNumOffsets * 2, 0.0);
+    std::vector<double> cs(n), sn(n);
+    for (int k = 0; k < n; ++k) {
+        cs[k] = cos(2.0 * M_PI * k / n);
+        sn[k] = sin(2.0 * M_PI * k / n);
+    }
+    const double norm = 1.0 / ((double)n * n * n);
+#pragma omp parallel for schedule(dynamic)
+    for (int t = 0; t < 343; ++t) {
+        const int tx = t % 7 - 3, ty = (t / 7) % 7 - 3, tz = t / 49 - 3;
+        const int u = offset_index(tx, ty, tz);
+        if (u < 0)
+            continue;
+        // c[jz][jy][jx], j = d mod n for d in [-(p-1), p-1]
+        std::vector<double> c((size_t)n * n * n, 0.0);
+        for (int dz = 1 - p; dz < p; ++dz)
+            for (int dy = 1 - p; dy < p; ++dy)
+                for (int dx = 1 - p; dx < p; ++dx) {
+                    const double a = h * (-tx + dx / (p - 1.0)), b = h * (-ty + dy / (p - 1.0)),
+                                 e = h * (-tz + dz / (p - 1.0));
+                    const int jx = (dx + n) % n, jy = (dy + n) % n, jz = (dz + n) % n;
+                    c[((size_t)jz * n + jy) * n + jx] = kernel_value_host(o.kernel, o.ell, a, b, e);
+                }
+        // x: real -> complex, wx < p; then y and z complex, all n frequencies
+        std::vector<double> A((size_t)n * n * p * 2), B((size_t)n * n * p * 2);
+        for (int jz = 0; jz < n; ++jz)
+            for (int jy = 0; jy < n; ++jy)
+                for (int wx = 0; wx < p; ++wx) {
+                    double re = 0.0, im = 0.0;
+                    for (int jx = 0; jx < n; ++jx) {
+                        const double v = c[((size_t)jz * n + jy) * n + jx];
+                        const int k = (wx * jx) % n;
+                        re += v * cs[k];
+                        im -= v * sn[k];
+                    }
+                    const size_t q = (((size_t)jz * n + jy) * p + wx) * 2;
+                    A[q] = re;
+                    A[q + 1] = im;
+                }
+        for (int jz = 0; jz < n; ++jz)
+            for (int wy = 0; wy < n; ++wy)
+                for (int wx = 0; wx < p; ++wx) {
+                    double re = 0.0, im = 0.0;
+                    for (int jy = 0; jy < n; ++jy) {
+                        const size_t q = (((size_t)jz * n + jy) * p + wx) * 2;
+                        const int k = (wy * jy) % n;
+                        re += A[q] * cs[k] + A[q + 1] * sn[k];
+                        im += A[q + 1] * cs[k] - A[q] * sn[k];
+                    }
+                    const size_t q = (((size_t)jz * n + wy) * p + wx) * 2;
+                    B[q] = re;
+                    B[q + 1] = im;
+                }
+        for (int wz = 0; wz < n; ++wz)
+            for (int wy = 0; wy < n; ++wy)
+                for (int wx = 0; wx < p; ++wx) {
+                    double re = 0.0, im = 0.0;
+                    for (int jz = 0; jz < n; ++jz) {
+                        const size_t q = (((size_t)jz * n + wy) * p + wx) * 2;
+                        const int k = (wz * jz) % n;
+                        re += B[q] * cs[k] + B[q + 1] * sn[k];
+                        im += B[q + 1] * cs[k] - B[q] * sn[k];
+                    }
+                    const size_t w = ((size_t)wz * n + wy) * p + wx;
+                    out[(w * kNumOffsets + u) * 2] = re * norm;
+                    out[(w * kNumOffsets + u) * 2 + 1] = im * norm;
+                }
+    }
+}
+
 std::shared_ptr<HostOps> build_host_ops(int kernel, double ell, int p, double eps, int depth, double side,
-                                        std::string &err)
+                                        int interp, std::string &err)
 {
     auto o = std::make_shared<HostOps>();
     o->kernel = kernel;
@@ -261,9 +346,11 @@ std::shared_ptr<HostOps> build_host_ops(int kernel, double ell, int p, double ep
     o->p3 = p * p * p;
     o->eps = eps;
     o->hom_degree = homogeneity(kernel);
+    o->interp = interp;
     o->nodes.resize(p);
     for (int k = 1; k <= p; ++k)
-        o->nodes[k - 1] = cos((2.0 * k - 1.0) * M_PI / (2.0 * p));
+        o->nodes[k - 1] = interp == BBFMM_INTERP_UNIFORM ? -1.0 + 2.0 * (k - 1) / (p - 1.0)
+                                                         : cos((2.0 * k - 1.0) * M_PI / (2.0 * p));
     o->wbary.resize(p);
     for (int i = 0; i < p; ++i) {
         double d = 1.0;
@@ -287,6 +374,28 @@ std::shared_ptr<HostOps> build_host_ops(int kernel, double ell, int p, double ep
     if (depth < 2)
         return o; // no far field
     int nlev = o->hom_degree != 0 ? 1 : depth - 1;
+    if (interp == BBFMM_INTERP_UNIFORM) {
+        // no compression; the M2L works on the spectra of the kernel tables
+        const int p3 = o->p3;
+        o->nfft = 2 * p - 1;
+        o->nw = o->nfft * o->nfft * p;
+        o->r = o->rank_u = o->rank_v = p3;
+        std::vector<double> I((size_t)p3 * p3, 0.0);
+        for (int i = 0; i < p3; ++i)
+            I[(size_t)i * p3 + i] = 1.0;
+        for (int k = 0; k < nlev; ++k) {
+            int level = o->hom_degree != 0 ? depth : k + 2;
+            double h = side / (double)(1LL << level);
+            o->h.push_back(h);
+            o->rl.push_back(p3);
+            o->U.push_back(I);
+            o->V.push_back(I);
+            o->khat.emplace_back();
+            build_khat(*o, h, o->khat.back());
+        }
+        (void)err;
+        return o;
+    }
     o->U.resize(nlev);
     o->V.resize(nlev);
     o->C.resize(nlev);

@@ -104,3 +104,15 @@ def test_plan_targets_rejects_bad_arguments(lib):
                                     ctypes.byref(h)) == lib.BBFMM_EINVAL, nt
     assert L.bbfmm_plan_targets(pts.ctypes.data, 0, pts.ctypes.data, 10, 1, 4, 3, None, None,
                                 ctypes.byref(h)) == lib.BBFMM_EINVAL
+
+
+def test_plan_rejects_bad_interp(lib):
+    """interp must be CHEBYSHEV or UNIFORM, and UNIFORM (the Fourier-domain
+    M2L, FP32) takes no tensor-core precision: EINVAL before any device call."""
+    pts = np.random.default_rng(2).random((10, 3))
+    h = ctypes.c_void_p()
+    for interp, prec in [(2, 0), (-1, 0), (1, 4), (1, 2)]:
+        o = lib.bbfmm_default_opts()
+        o.interp, o.precision = interp, prec
+        assert lib.lib().bbfmm_plan(pts.ctypes.data, 10, 1, 4, 3, ctypes.byref(o), None,
+                                    ctypes.byref(h)) == lib.BBFMM_EINVAL, (interp, prec)
