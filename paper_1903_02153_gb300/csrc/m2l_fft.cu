@@ -11,10 +11,18 @@
 //               padded to n^3 (x, then y, then z; only w_x < p is kept, the
 //               other half is the complex conjugate), written frequency-major
 //               onto a box grid with a zero halo of 3 boxes.
-//   k_fft_m2l   per frequency w and tile of 8^3 target boxes: the 189-term
-//               sum over the interaction list, a stencil on the box grid.
-//               Warp = one octant class (its 189 offsets are warp-uniform),
-//               thread = two targets adjacent in x, packed two-lane FP32 FMA.
+//   k_fft_m2l_tiled  (levels with 16+ boxes per axis) per frequency w and
+//               tile of 16 x 16 x 8 target boxes: the 189-term sum over the
+//               interaction list, a stencil on the box grid.  Warp = one
+//               octant class (its offsets are warp-uniform), thread = 4 x 2
+//               targets of the class; per z offset and pair of x / y source
+//               parities the thread loads a 6 x 4 window of sources once and
+//               applies the 9 offsets that read it (register reuse: 24
+//               complex loads per 72 complex multiply-adds).  The 27 offsets
+//               of the own neighbourhood enter with a zero spectrum instead
+//               of a branch.
+//   k_fft_m2l   the same for the two coarsest levels (one tile each):
+//               thread = two targets adjacent in x.
 //   k_fft_inv   per box: the inverse DFT (z, y, then x with the conjugate
 //               half restored), only the p^3 outputs that are kept.
 // The kernel spectra K^_t (host, FP64 -> FP32) already carry the 1 / n^3 of
@@ -25,7 +33,16 @@
 namespace bbfmm {
 
 constexpr int kFftMaxN = 2 * kMaxP - 1;
-constexpr int kFftTile = 8;        // target tile edge (boxes); 4 on level 2
+// tiles of target boxes: 16 x 16 x 8 on levels with 16+ boxes per axis (the
+// tiled stencil), the whole level on the two coarsest
+constexpr int kTX = 16, kTY = 16, kTZ = 8;
+// halo tile of the tiled stencil, per source parity: 11 x 11 x 7 boxes,
+// stored with a row stride of 14 and a z stride of 155 (float2 units), so
+// that the 16 lanes of a half-warp read 16 different bank pairs
+constexpr int kHX = kTX / 2 + 3, kHY = kTY / 2 + 3, kHZ = kTZ / 2 + 3;
+constexpr int kPY = 14, kPZ = 155, kPP = kHZ * kPZ;
+static_assert(kPY >= kHX && kPZ >= kHY * kPY, "halo strides");
+constexpr int kTaps = 216; // 6^3 offsets per class, the 27 neighbours among them
 constexpr int kFftThreads = 256;   // 8 warps = 8 octant classes
 constexpr int kFftBoxes = 16;      // most boxes per block of the forward / inverse DFT
 constexpr int kFftSmem = 96 * 1024; // shared memory budget of the DFT blocks
@@ -35,8 +52,9 @@ struct FftArgs {
     float2 tw[kFftMaxN]; // (cos, sin)(2 pi k / n)
     int p, n, nw, p3, rp, R, nrhs;
     int l, S, G, H;      // level, boxes per axis, M^ grid edge (S + 6), parent cells per axis (S / 2)
-    int T, Ts, tsel;     // tile edge, halo edge per parity (T / 2 + 3), tap table (0: T = 8, 1: T = 4)
-    int nbf, nbi;        // boxes per block of the forward / inverse DFT
+    int TX, TY, TZ;      // tile (boxes)
+    int T, Ts, tsel;     // coarse levels: tile edge, halo edge per parity (T / 2 + 3), tap table (0: T = 8, 1: T = 4)
+    int wpb;             // frequencies per block of the stencil
     const float *Mt;     // M~ = M (no compression), parity-split rows of rp floats
     float *Ft;           // F~ = F, slice 0
     float2 *Mhat, *Fhat;
@@ -50,69 +68,88 @@ struct FftArgs {
 // of the source from the target in the parity-split halo tile (in float4
 // pairs), y = offset index 0..315 (the kernel spectrum's column)
 __constant__ int2 c_fft_tap[2][8][kOffsetsPerClass];
+// tiled stencil: spectrum column (0..315, or 316 = zero) of the tap
+// (tz, y parity, x parity, ey, ex) of each class, [8][216]
+static int16_t *g_kmap = nullptr;
 
 // ---------------------------------------------------------------------------
-// forward DFT: block = A.nbf consecutive boxes (lexicographic) x 1 RHS
-__global__ void __launch_bounds__(128) k_fft_fwd(const __grid_constant__ FftArgs A)
+// DFT sizes of order P: n = 2P - 1 points per axis, P^3 coefficients, the
+// kept half of the spectrum N W = n n P, and the boxes one block transforms
+// (as many as kFftSmem holds, at most kFftBoxes)
+template <int P> struct Dft {
+    static constexpr int N = 2 * P - 1, P3 = P * P * P, PNP = P * N * P, NW = N * N * P;
+    static constexpr int FWD_BOX = 4 * P3 + 8 * (P3 + PNP), INV_BOX = 8 * (NW + PNP);
+    static constexpr int NBF = FWD_BOX * kFftBoxes <= kFftSmem ? kFftBoxes : (kFftSmem / FWD_BOX > 0 ? kFftSmem / FWD_BOX : 1);
+    static constexpr int NBI = INV_BOX * kFftBoxes <= kFftSmem ? kFftBoxes : (kFftSmem / INV_BOX > 0 ? kFftSmem / INV_BOX : 1);
+    static constexpr size_t FWD_SMEM = (size_t)FWD_BOX * NBF + 16, INV_SMEM = (size_t)INV_BOX * NBI;
+};
+
+// twiddle table in shared memory: tw[w * P + x] = (cos, sin)(2 pi (w x mod n) / n), w < n, x < P
+template <int P> __device__ __forceinline__ void load_twiddles(const FftArgs &A, float2 *tw)
 {
+    constexpr int N = 2 * P - 1;
+    for (int q = threadIdx.x; q < N * P; q += blockDim.x) {
+        const int w = q / P, x = q - w * P;
+        tw[q] = A.tw[(w * x) % N];
+    }
+}
+
+// forward DFT: block = NBF consecutive boxes (lexicographic) x 1 RHS
+constexpr int kDftThreads = 256;
+
+template <int P> __global__ void __launch_bounds__(kDftThreads) k_fft_fwd(const __grid_constant__ FftArgs A)
+{
+    using D = Dft<P>;
+    constexpr int N = D::N, P3 = D::P3, PNP = D::PNP, NB = D::NBF;
     extern __shared__ float2 fsm[];
-    const int p = A.p, n = A.n, p3 = A.p3;
-    const int c = blockIdx.y;
-    const int64_t nbox = (int64_t)A.S * A.S * A.S;
-    const int NB = A.nbf;
-    const int64_t b0 = (int64_t)blockIdx.x * NB;
-    float *sM = reinterpret_cast<float *>(fsm); // [box][p3]
-    float2 *sA = fsm + (NB * p3 + 1) / 2;       // [box][z][y][wx]
-    float2 *sB = sA + NB * p3;                  // [box][z][wy][wx]
+    __shared__ float2 tw[N * P];
     __shared__ int sRow[kFftBoxes];
-    const int t = threadIdx.x;
+    float2 *sA = fsm;                                  // [box][z][y][wx]
+    float2 *sB = sA + NB * P3;                         // [box][z][wy][wx]
+    float *sM = reinterpret_cast<float *>(sB + NB * PNP); // [box][P3]
+    const int c = blockIdx.y, l = A.l;
+    const int64_t nbox = (int64_t)1 << (3 * l);
+    const int64_t b0 = (int64_t)blockIdx.x * NB;
+    const int t = threadIdx.x, S1 = A.S - 1;
+    load_twiddles<P>(A, tw);
     if (t < NB) {
         const int64_t b = b0 + t;
-        int row = -1;
-        if (b < nbox) {
-            const int x = (int)(b % A.S), y = (int)((b / A.S) % A.S), z = (int)(b / ((int64_t)A.S * A.S));
-            row = (int)parity_row(x, y, z, c, A.H, 1, A.R);
-        }
-        sRow[t] = row;
+        sRow[t] = b < nbox ? (int)parity_row((int)(b & S1), (int)((b >> l) & S1), (int)(b >> (2 * l)), c, A.H, 1, A.R)
+                           : -1;
     }
     __syncthreads();
-    for (int q = t; q < NB * p3; q += blockDim.x) {
-        const int bx = q / p3, k = q - bx * p3;
+#pragma unroll 8
+    for (int q = t; q < NB * P3; q += blockDim.x) {
+        const int bx = q / P3, k = q - bx * P3;
         const int row = sRow[bx];
         sM[q] = row >= 0 ? __ldg(A.Mt + (int64_t)row * A.rp + k) : 0.0f;
     }
     __syncthreads();
-    // x: A(wx; y, z) = sum_x M(x, y, z) e^{-2 pi i wx x / n}, wx < p
-    for (int q = t; q < NB * p3; q += blockDim.x) {
-        const int bx = q / p3, r = q - bx * p3;
-        const int wx = r % p, yz = r / p;
-        const float *m = sM + bx * p3 + yz * p;
+    // x: A(wx; y, z) = sum_x M(x, y, z) e^{-2 pi i wx x / n}, wx < P
+    for (int q = t; q < NB * P3; q += blockDim.x) {
+        const int wx = q % P, byz = q / P; // byz = box * P^2 + z P + y
+        const float *m = sM + byz * P;
+        const float2 *e = tw + wx * P;
         float re = 0.0f, im = 0.0f;
-        int k = 0;
-        for (int x = 0; x < p; ++x) {
-            const float2 w = A.tw[k];
-            re += m[x] * w.x;
-            im -= m[x] * w.y;
-            k += wx;
-            k -= k >= n ? n : 0;
+#pragma unroll
+        for (int x = 0; x < P; ++x) {
+            re = fmaf(m[x], e[x].x, re);
+            im = fmaf(-m[x], e[x].y, im);
         }
         sA[q] = make_float2(re, im);
     }
     __syncthreads();
     // y: B(wx, wy; z) = sum_y A(wx; y, z) e^{-2 pi i wy y / n}
-    const int pnp = p * n * p;
-    for (int q = t; q < NB * pnp; q += blockDim.x) {
-        const int bx = q / pnp, r = q - bx * pnp;
-        const int wx = r % p, wy = (r / p) % n, z = r / (p * n);
-        const float2 *a = sA + bx * p3 + z * p * p + wx;
+    for (int q = t; q < NB * PNP; q += blockDim.x) {
+        const int wx = q % P, r = q / P, wy = r % N, bz = r / N; // bz = box * P + z
+        const float2 *a = sA + bz * P * P + wx;
+        const float2 *e = tw + wy * P;
         float re = 0.0f, im = 0.0f;
-        int k = 0;
-        for (int y = 0; y < p; ++y) {
-            const float2 v = a[y * p], w = A.tw[k];
-            re += v.x * w.x + v.y * w.y;
-            im += v.y * w.x - v.x * w.y;
-            k += wy;
-            k -= k >= n ? n : 0;
+#pragma unroll
+        for (int y = 0; y < P; ++y) {
+            const float2 v = a[y * P];
+            re = fmaf(v.x, e[y].x, fmaf(v.y, e[y].y, re));
+            im = fmaf(v.y, e[y].x, fmaf(-v.x, e[y].y, im));
         }
         sB[q] = make_float2(re, im);
     }
@@ -120,24 +157,24 @@ __global__ void __launch_bounds__(128) k_fft_fwd(const __grid_constant__ FftArgs
     // z, and the store: consecutive threads take consecutive boxes of one
     // frequency (coalesced rows of the M^ grid)
     const int64_t G = A.G, plane = G * G * G;
-    for (int q = t; q < NB * A.nw; q += blockDim.x) {
-        const int bx = q % NB, w = q / NB;
+#pragma unroll 4
+    for (int q = t; q < NB * D::NW; q += blockDim.x) {
+        const int bx = q % NB, f = q / NB; // box, frequency
         const int64_t b = b0 + bx;
         if (b >= nbox)
             continue;
-        const int wx = w % p, wy = (w / p) % n, wz = w / (p * n);
-        const float2 *bb = sB + bx * pnp + wy * p + wx;
+        const int wx = f % P, wy = (f / P) % N, wz = f / (P * N);
+        const float2 *bb = sB + bx * PNP + wy * P + wx;
+        const float2 *e = tw + wz * P;
         float re = 0.0f, im = 0.0f;
-        int k = 0;
-        for (int z = 0; z < p; ++z) {
-            const float2 v = bb[z * n * p], tw = A.tw[k];
-            re += v.x * tw.x + v.y * tw.y;
-            im += v.y * tw.x - v.x * tw.y;
-            k += wz;
-            k -= k >= n ? n : 0;
+#pragma unroll
+        for (int z = 0; z < P; ++z) {
+            const float2 v = bb[z * N * P];
+            re = fmaf(v.x, e[z].x, fmaf(v.y, e[z].y, re));
+            im = fmaf(v.y, e[z].x, fmaf(-v.x, e[z].y, im));
         }
-        const int x = (int)(b % A.S), y = (int)((b / A.S) % A.S), z = (int)(b / ((int64_t)A.S * A.S));
-        A.Mhat[((int64_t)w * A.R + c) * plane + ((z + 3) * G + (y + 3)) * G + (x + 3)] = make_float2(re, im);
+        const int x = (int)(b & S1), y = (int)((b >> l) & S1), z = (int)(b >> (2 * l));
+        A.Mhat[((int64_t)f * A.R + c) * plane + ((z + 3) * G + (y + 3)) * G + (x + 3)] = make_float2(re, im);
     }
 }
 
@@ -165,7 +202,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_m2l(const __grid_constant__
     const int sbase = X + Ts * (Y + Ts * Z);
     const int2 *tap = c_fft_tap[A.tsel][warp];
     const int64_t G = A.G, plane = G * G * G;
-    const int w0 = blockIdx.y * kFftWPerBlock, w1 = min(A.nw, w0 + kFftWPerBlock);
+    const int w0 = blockIdx.y * A.wpb, w1 = min(A.nw, w0 + A.wpb);
     // output: parity-split F^ [w][c][oct][H][H][H], the pair adjacent in x
     const int px = warp & 1, py = (warp >> 1) & 1, pz = warp >> 2;
     const int64_t H = A.H, nb = 8 * H * H * H;
@@ -218,95 +255,190 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_m2l(const __grid_constant__
 }
 
 // ---------------------------------------------------------------------------
-// inverse DFT: block = A.nbi boxes of an active tile x 1 RHS
-__global__ void __launch_bounds__(128) k_fft_inv(const __grid_constant__ FftArgs A)
+// Fourier-domain M2L, tiled: block = one active 16 x 16 x 8 tile x A.wpb
+// frequencies x 1 RHS; warp = octant class, lane = 4 x 2 targets of it
+__global__ void __launch_bounds__(kFftThreads, 2) k_fft_m2l_tiled(const __grid_constant__ FftArgs A,
+                                                                   const int16_t *__restrict__ kmap)
 {
-    extern __shared__ float2 fsm[];
-    const int p = A.p, n = A.n, p3 = A.p3, nw = A.nw, pnp = p * n * p;
+    extern __shared__ float2 sH[];        // [8 parities][kHZ][kHY][kHX], strides kPP, kPZ, kPY
+    float2 *sKc = sH + 8 * kPP;           // [8 classes][216 taps]: the spectrum of each tap
+    constexpr int EX = kTX + 6, EY = kTY + 6, EZ = kTZ + 6;
     const int c = blockIdx.z;
-    const int T = A.T, Tc = T / 2;
-    const int per_tile = T * T * T;
     const int4 tile = A.tiles[blockIdx.x];
-    const int t = threadIdx.x, NB = A.nbi;
-    if (tile.x < 0 || tile.y < 0 || tile.z < 0 || (tile.x + 1) * T > A.S || (tile.y + 1) * T > A.S ||
-        (tile.z + 1) * T > A.S) {
+    const int x0 = tile.x * kTX, y0 = tile.y * kTY, z0 = tile.z * kTZ;
+    const int t = threadIdx.x, cls = t >> 5, lane = t & 31;
+    if (tile.x < 0 || tile.y < 0 || tile.z < 0 || x0 + kTX > A.S || y0 + kTY > A.S || z0 + kTZ > A.S) {
+        if (t == 0)
+            atomicOr(A.status, kStatusBounds);
+        return; // block-uniform
+    }
+    // the lane's targets: class cells (X0 + ix, Y0 + iy, Z), ix < 4, iy < 2;
+    // the 16 lanes of a half-warp differ in y and z (conflict-free rows)
+    const int X0 = 4 * (lane >> 4), Y0 = 2 * (lane & 3), Z = (lane >> 2) & 3;
+    const int64_t G = A.G, plane = G * G * G;
+    const int64_t H = A.H, nb = 8 * H * H * H;
+    const int w0 = blockIdx.y * A.wpb, w1 = min(A.nw, w0 + A.wpb);
+    for (int w = w0; w < w1; ++w) {
+        __syncthreads(); // the previous frequency's reads are done
+        const float2 *kh = A.khat + (int64_t)w * kNumOffsets;
+        for (int q = t; q < 8 * kTaps; q += kFftThreads) {
+            const int m = __ldg(kmap + q);
+            sKc[q] = m < kNumOffsets ? __ldg(kh + m) : make_float2(0.0f, 0.0f);
+        }
+        const float2 *src = A.Mhat + ((int64_t)w * A.R + c) * plane;
+#pragma unroll 4
+        for (int q = t; q < EX * EY * EZ; q += kFftThreads) {
+            const int hx = q % EX, hy = (q / EX) % EY, hz = q / (EX * EY);
+            const float2 v = __ldg(src + ((int64_t)(z0 + hz) * G + (y0 + hy)) * G + (x0 + hx));
+            const int par = (hx & 1) | ((hy & 1) << 1) | ((hz & 1) << 2);
+            sH[par * kPP + (hz >> 1) * kPZ + (hy >> 1) * kPY + (hx >> 1)] = v;
+        }
+        __syncthreads();
+        float ar[2][4], ai[2][4];
+#pragma unroll
+        for (int iy = 0; iy < 2; ++iy)
+#pragma unroll
+            for (int ix = 0; ix < 4; ++ix)
+                ar[iy][ix] = ai[iy][ix] = 0.0f;
+        const float2 *kc = sKc + cls * kTaps;
+#pragma unroll 1
+        for (int tzi = 0; tzi < 6; ++tzi) {
+            // z offset tz = tzi - 2 - pz: source z parity and cell shift do
+            // not depend on the class
+            const int qz = (tzi + 1) & 1, dz = (tzi + 1) >> 1;
+#pragma unroll
+            for (int qy = 0; qy < 2; ++qy)
+#pragma unroll
+                for (int qx = 0; qx < 2; ++qx) {
+                    // sources of the 9 offsets with these x / y parities:
+                    // cells (X0 + d0x + rx, Y0 + d0y + ry), d0 = 1 - parity
+                    const float2 *sp = sH + (qx | (qy << 1) | (qz << 2)) * kPP + (Z + dz) * kPZ +
+                                       (Y0 + 1 - qy) * kPY + (X0 + 1 - qx);
+                    float2 sv[4][6];
+#pragma unroll
+                    for (int ry = 0; ry < 4; ++ry)
+#pragma unroll
+                        for (int rx = 0; rx < 6; ++rx)
+                            sv[ry][rx] = sp[ry * kPY + rx];
+                    const float2 *kk = kc + ((tzi * 2 + qy) * 2 + qx) * 9;
+#pragma unroll
+                    for (int ey = 0; ey < 3; ++ey)
+#pragma unroll
+                        for (int ex = 0; ex < 3; ++ex) {
+                            const float2 k = kk[ey * 3 + ex];
+#pragma unroll
+                            for (int iy = 0; iy < 2; ++iy)
+#pragma unroll
+                                for (int ix = 0; ix < 4; ++ix) {
+                                    const float2 m = sv[iy + ey][ix + ex];
+                                    ar[iy][ix] = fmaf(m.x, k.x, ar[iy][ix]);
+                                    ar[iy][ix] = fmaf(-m.y, k.y, ar[iy][ix]);
+                                    ai[iy][ix] = fmaf(m.x, k.y, ai[iy][ix]);
+                                    ai[iy][ix] = fmaf(m.y, k.x, ai[iy][ix]);
+                                }
+                        }
+                }
+        }
+        // F^ [w][c][class][H][H][H]: four consecutive x cells per row
+        float2 *out = A.Fhat + ((int64_t)w * A.R + c) * nb;
+#pragma unroll
+        for (int iy = 0; iy < 2; ++iy) {
+            const int64_t row = (((int64_t)cls * H + (z0 / 2 + Z)) * H + (y0 / 2 + Y0 + iy)) * H + (x0 / 2 + X0);
+            float4 *o = reinterpret_cast<float4 *>(out + row);
+            o[0] = make_float4(ar[iy][0], ai[iy][0], ar[iy][1], ai[iy][1]);
+            o[1] = make_float4(ar[iy][2], ai[iy][2], ar[iy][3], ai[iy][3]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// inverse DFT: block = NBI boxes of an active tile x 1 RHS
+template <int P> __global__ void __launch_bounds__(kDftThreads) k_fft_inv(const __grid_constant__ FftArgs A)
+{
+    using D = Dft<P>;
+    constexpr int N = D::N, P3 = D::P3, PNP = D::PNP, NW = D::NW, NB = D::NBI;
+    extern __shared__ float2 fsm[];
+    __shared__ float2 tw[N * P];
+    __shared__ int64_t sIdx[kFftBoxes];
+    __shared__ int sRow[kFftBoxes];
+    const int c = blockIdx.z;
+    const int Cx = A.TX / 2, Cy = A.TY / 2, Cz = A.TZ / 2; // class cells of the tile per axis
+    const int per_tile = A.TX * A.TY * A.TZ;
+    const int4 tile = A.tiles[blockIdx.x];
+    const int t = threadIdx.x;
+    if (tile.x < 0 || tile.y < 0 || tile.z < 0 || (tile.x + 1) * A.TX > A.S || (tile.y + 1) * A.TY > A.S ||
+        (tile.z + 1) * A.TZ > A.S) {
         if (t == 0)
             atomicOr(A.status, kStatusBounds);
         return;
     }
     float2 *sG = fsm;           // [box][w]
-    float2 *sBz = sG + NB * nw; // [box][z][wy][wx]
+    float2 *sBz = sG + NB * NW; // [box][z][wy][wx]
     float2 *sAy = sG;           // [box][z][y][wx] (over sG once it is used)
-    __shared__ int64_t sIdx[kFftBoxes];
-    __shared__ int sRow[kFftBoxes];
     const int64_t H = A.H, nb = 8 * H * H * H;
+    load_twiddles<P>(A, tw);
     if (t < NB) {
         // box q of the tile in parity-split order: class, then Z, Y, X
         const int q = blockIdx.y * NB + t;
-        const int Tc3 = Tc * Tc * Tc;
-        const int oct = q / Tc3, r = q - oct * Tc3;
-        const int X = r % Tc, Y = (r / Tc) % Tc, Z = r / (Tc * Tc);
-        const int Xg = tile.x * Tc + X, Yg = tile.y * Tc + Y, Zg = tile.z * Tc + Z;
+        const int C3 = Cx * Cy * Cz;
+        const int oct = q / C3, r = q - oct * C3;
+        const int X = r % Cx, Y = (r / Cx) % Cy, Z = r / (Cx * Cy);
+        const int Xg = tile.x * Cx + X, Yg = tile.y * Cy + Y, Zg = tile.z * Cz + Z;
         const bool in = q < per_tile;
         sIdx[t] = in ? (((int64_t)oct * H + Zg) * H + Yg) * H + Xg : 0;
         const int x = 2 * Xg + (oct & 1), y = 2 * Yg + ((oct >> 1) & 1), z = 2 * Zg + (oct >> 2);
         sRow[t] = in ? (int)parity_row(x, y, z, c, A.H, 0, A.R) : -1;
     }
     __syncthreads();
-    for (int q = t; q < NB * nw; q += blockDim.x) {
+    const float2 *fh = A.Fhat + (int64_t)c * nb;
+    const int64_t fstride = (int64_t)A.R * nb;
+#pragma unroll 8
+    for (int q = t; q < NB * NW; q += blockDim.x) {
         const int bx = q % NB, w = q / NB;
-        sG[bx * nw + w] = sRow[bx] >= 0 ? A.Fhat[((int64_t)w * A.R + c) * nb + sIdx[bx]] : make_float2(0.0f, 0.0f);
+        sG[bx * NW + w] = sRow[bx] >= 0 ? __ldg(fh + w * fstride + sIdx[bx]) : make_float2(0.0f, 0.0f);
     }
     __syncthreads();
-    // z: Bz(wx, wy; z) = sum_wz G(wx, wy, wz) e^{+2 pi i wz z / n}, z < p
-    for (int q = t; q < NB * pnp; q += blockDim.x) {
-        const int bx = q / pnp, r = q - bx * pnp;
-        const int wx = r % p, wy = (r / p) % n, z = r / (p * n);
-        const float2 *g = sG + bx * nw + wy * p + wx;
+    // z: Bz(wx, wy; z) = sum_wz G(wx, wy, wz) e^{+2 pi i wz z / n}, z < P
+    for (int q = t; q < NB * PNP; q += blockDim.x) {
+        const int wx = q % P, r = q / P, wy = r % N, r2 = r / N, z = r2 % P, bx = r2 / P;
+        const float2 *g = sG + bx * NW + wy * P + wx;
         float re = 0.0f, im = 0.0f;
-        int k = 0;
-        for (int wz = 0; wz < n; ++wz) {
-            const float2 v = g[wz * n * p], tw = A.tw[k];
-            re += v.x * tw.x - v.y * tw.y;
-            im += v.y * tw.x + v.x * tw.y;
-            k += z;
-            k -= k >= n ? n : 0;
+#pragma unroll
+        for (int wz = 0; wz < N; ++wz) {
+            const float2 v = g[wz * N * P], e = tw[wz * P + z];
+            re = fmaf(v.x, e.x, fmaf(-v.y, e.y, re));
+            im = fmaf(v.y, e.x, fmaf(v.x, e.y, im));
         }
-        sBz[q] = make_float2(re, im);
+        sBz[q] = make_float2(re, im); // [box][z][wy][wx]
     }
     __syncthreads();
-    // y: Ay(wx; y, z) = sum_wy Bz(wx, wy; z) e^{+2 pi i wy y / n}, y < p
-    for (int q = t; q < NB * p3; q += blockDim.x) {
-        const int bx = q / p3, r = q - bx * p3;
-        const int wx = r % p, y = (r / p) % p, z = r / (p * p);
-        const float2 *b = sBz + bx * pnp + z * n * p + wx;
+    // y: Ay(wx; y, z) = sum_wy Bz(wx, wy; z) e^{+2 pi i wy y / n}, y < P
+    for (int q = t; q < NB * P3; q += blockDim.x) {
+        const int wx = q % P, r = q / P, y = r % P, bz = r / P; // bz = box * P + z
+        const float2 *b = sBz + bz * N * P + wx;
         float re = 0.0f, im = 0.0f;
-        int k = 0;
-        for (int wy = 0; wy < n; ++wy) {
-            const float2 v = b[wy * p], tw = A.tw[k];
-            re += v.x * tw.x - v.y * tw.y;
-            im += v.y * tw.x + v.x * tw.y;
-            k += y;
-            k -= k >= n ? n : 0;
+#pragma unroll
+        for (int wy = 0; wy < N; ++wy) {
+            const float2 v = b[wy * P], e = tw[wy * P + y];
+            re = fmaf(v.x, e.x, fmaf(-v.y, e.y, re));
+            im = fmaf(v.y, e.x, fmaf(v.x, e.y, im));
         }
-        sAy[q] = make_float2(re, im);
+        sAy[q] = make_float2(re, im); // [box][z][y][wx]
     }
     __syncthreads();
     // x (real output): f = Re Ay(0) + 2 sum_{wx >= 1} Re(Ay(wx) e^{+2 pi i wx x / n})
-    for (int q = t; q < NB * p3; q += blockDim.x) {
-        const int bx = q / p3, r = q - bx * p3;
+    for (int q = t; q < NB * P3; q += blockDim.x) {
+        const int bx = q / P3, r = q - bx * P3;
         const int row = sRow[bx];
         if (row < 0)
             continue;
-        const int x = r % p, yz = r / p;
-        const float2 *a = sAy + bx * p3 + yz * p;
+        const int x = r % P, yz = r / P;
+        const float2 *a = sAy + bx * P3 + yz * P;
         float f = 0.0f;
-        int k = x;
-        for (int wx = 1; wx < p; ++wx) {
-            const float2 v = a[wx], tw = A.tw[k];
-            f += v.x * tw.x - v.y * tw.y;
-            k += x;
-            k -= k >= n ? n : 0;
+#pragma unroll
+        for (int wx = 1; wx < P; ++wx) {
+            const float2 v = a[wx], e = tw[wx * P + x];
+            f = fmaf(v.x, e.x, fmaf(-v.y, e.y, f));
         }
         f = a[0].x + 2.0f * f;
         A.Ft[(int64_t)row * A.rp + r] = A.scale * f;
@@ -315,6 +447,45 @@ __global__ void __launch_bounds__(128) k_fft_inv(const __grid_constant__ FftArgs
 
 // ---------------------------------------------------------------------------
 // host side
+template <int P> static cudaError_t dft_attrs()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_fft_fwd<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Dft<P>::FWD_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fft_inv<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Dft<P>::INV_SMEM);
+    if (e != cudaSuccess || P == kMaxP)
+        return e;
+    return dft_attrs<(P < kMaxP ? P + 1 : P)>();
+}
+
+template <int P> static cudaError_t launch_fwd(const FftArgs &A, int nrhs, cudaStream_t s)
+{
+    const int64_t nbox = (int64_t)A.S * A.S * A.S;
+    k_fft_fwd<P><<<dim3((unsigned)((nbox + Dft<P>::NBF - 1) / Dft<P>::NBF), (unsigned)nrhs), kDftThreads,
+                   Dft<P>::FWD_SMEM, s>>>(A);
+    return cudaGetLastError();
+}
+
+template <int P> static cudaError_t launch_inv(const FftArgs &A, int ntile, int nrhs, cudaStream_t s)
+{
+    const int groups = (A.TX * A.TY * A.TZ + Dft<P>::NBI - 1) / Dft<P>::NBI;
+    k_fft_inv<P><<<dim3((unsigned)ntile, (unsigned)groups, (unsigned)nrhs), kDftThreads, Dft<P>::INV_SMEM, s>>>(A);
+    return cudaGetLastError();
+}
+
+#define BBFMM_DFT_DISPATCH(p, fn, args)                                                                         \
+    switch (p) {                                                                                                \
+    case 2: e = fn<2> args; break;                                                                              \
+    case 3: e = fn<3> args; break;                                                                              \
+    case 4: e = fn<4> args; break;                                                                              \
+    case 5: e = fn<5> args; break;                                                                              \
+    case 6: e = fn<6> args; break;                                                                              \
+    case 7: e = fn<7> args; break;                                                                              \
+    case 8: e = fn<8> args; break;                                                                              \
+    case 9: e = fn<9> args; break;                                                                              \
+    case 10: e = fn<10> args; break;                                                                            \
+    default: e = cudaErrorInvalidValue;                                                                         \
+    }
 static std::mutex g_fft_mu;
 static bool g_fft_ready = false;
 
@@ -354,11 +525,39 @@ cudaError_t m2l_fft_init()
                 return cudaErrorInvalidValue;
         }
     }
-    cudaError_t e = cudaMemcpyToSymbol(c_fft_tap, tab, sizeof(tab));
+    // tiled stencil: the spectrum column of every (class, tap)
+    std::vector<int16_t> km(8 * kTaps);
+    for (int cls = 0; cls < 8; ++cls) {
+        const int px = cls & 1, py = (cls >> 1) & 1, pz = cls >> 2;
+        for (int tzi = 0; tzi < 6; ++tzi)
+            for (int qy = 0; qy < 2; ++qy)
+                for (int qx = 0; qx < 2; ++qx)
+                    for (int ey = 0; ey < 3; ++ey)
+                        for (int ex = 0; ex < 3; ++ex) {
+                            // parity q, shift d = (1 - q) + e: t = 2 d + q - 3 - p
+                            const int tz = tzi - 2 - pz;
+                            const int ty = 2 * (1 - qy + ey) + qy - 3 - py;
+                            const int tx = 2 * (1 - qx + ex) + qx - 3 - px;
+                            const int u = offset_index(tx, ty, tz); // -1 for the 27 neighbours
+                            km[cls * kTaps + (((tzi * 2 + qy) * 2 + qx) * 3 + ey) * 3 + ex] =
+                                (int16_t)(u < 0 ? kNumOffsets : u);
+                        }
+    }
+    int used = 0;
+    for (int16_t v : km)
+        used += v < kNumOffsets;
+    if (used != 8 * kOffsetsPerClass)
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaMalloc(&g_kmap, km.size() * sizeof(int16_t));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_fft_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftSmem + 8);
+        e = cudaMemcpy(g_kmap, km.data(), km.size() * sizeof(int16_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_fft_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftSmem);
+        e = cudaMemcpyToSymbol(c_fft_tap, tab, sizeof(tab));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fft_m2l_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(float2) * (8 * kPP + 8 * kTaps)));
+    if (e == cudaSuccess)
+        e = dft_attrs<2>();
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_fft_m2l, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(float4) * 8 * 7 * 7 * 7));
@@ -390,18 +589,20 @@ void fft_active_tiles(int D, const std::vector<uint8_t> &leaf_occ, std::vector<i
                 occ[l][b >> 3] = 1;
     }
     for (int l = D; l >= 2; --l) {
-        const int S = 1 << l, T = std::min(kFftTile, S), nt = S / T;
-        std::vector<uint8_t> any((size_t)nt * nt * nt, 0);
+        const int S = 1 << l;
+        const int TX = S >= 16 ? kTX : S, TY = S >= 16 ? kTY : S, TZ = S >= 16 ? kTZ : S;
+        const int nx = S / TX, ny = S / TY, nz = S / TZ;
+        std::vector<uint8_t> any((size_t)nx * ny * nz, 0);
         for (size_t b = 0; b < occ[l].size(); ++b)
             if (occ[l][b]) {
                 int x, y, z;
                 demorton3((uint32_t)b, x, y, z);
-                any[((size_t)(z / T) * nt + y / T) * nt + x / T] = 1;
+                any[((size_t)(z / TZ) * ny + y / TY) * nx + x / TX] = 1;
             }
-        for (int tz = 0; tz < nt; ++tz)
-            for (int ty = 0; ty < nt; ++ty)
-                for (int tx = 0; tx < nt; ++tx)
-                    if (any[((size_t)tz * nt + ty) * nt + tx]) {
+        for (int tz = 0; tz < nz; ++tz)
+            for (int ty = 0; ty < ny; ++ty)
+                for (int tx = 0; tx < nx; ++tx)
+                    if (any[((size_t)tz * ny + ty) * nx + tx]) {
                         tiles.push_back(make_int4(tx, ty, tz, 0));
                         count[l]++;
                     }
@@ -429,23 +630,17 @@ cudaError_t launch_m2l_fft(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
     A.R = P->max_nrhs;
     A.nrhs = nrhs;
     A.status = P->status;
-    // boxes per DFT block: as many as the shared-memory budget holds (<= 16)
-    const int pnp = p * n * p;
-    const size_t fwd_box = sizeof(float) * A.p3 + sizeof(float2) * (A.p3 + pnp);
-    const size_t inv_box = sizeof(float2) * (A.nw + pnp);
-    A.nbf = (int)std::max<size_t>(1, std::min<size_t>(kFftBoxes, (kFftSmem - 8) / fwd_box));
-    A.nbi = (int)std::max<size_t>(1, std::min<size_t>(kFftBoxes, kFftSmem / inv_box));
-    const size_t fwd_smem = sizeof(float) * (A.nbf * A.p3 + 1) + sizeof(float2) * A.nbf * (A.p3 + pnp);
-    const size_t inv_smem = inv_box * A.nbi;
-    if (fwd_smem > kFftSmem + 8 || inv_smem > kFftSmem)
-        return cudaErrorInvalidValue; // p beyond what one box's transform fits in
     for (int l = 2; l <= P->D; ++l) {
         const int k = O.nlev == 1 ? 0 : l - 2;
         A.l = l;
         A.S = 1 << l;
         A.G = A.S + 6;
         A.H = A.S / 2;
-        A.T = std::min(kFftTile, A.S);
+        const bool tiled = A.S >= 16;
+        A.TX = tiled ? kTX : A.S;
+        A.TY = tiled ? kTY : A.S;
+        A.TZ = tiled ? kTZ : A.S;
+        A.T = A.S; // coarse levels: one tile of the whole level
         A.Ts = A.T / 2 + 3;
         A.tsel = A.T == 8 ? 0 : 1;
         A.Mt = P->lev[l].Mt;
@@ -456,22 +651,25 @@ cudaError_t launch_m2l_fft(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
         A.tiles = P->fft_tiles + P->fft_tile_off[l];
         A.scale = O.host->hom_degree != 0 ? (float)pow(2.0, (double)O.host->hom_degree * (P->D - l)) : 1.0f;
         const int ntile = P->fft_ntiles[l];
-        const int64_t nbox = (int64_t)A.S * A.S * A.S;
-        k_fft_fwd<<<dim3((unsigned)((nbox + A.nbf - 1) / A.nbf), (unsigned)nrhs), 128, fwd_smem, s>>>(A);
-        e = cudaGetLastError();
+        BBFMM_DFT_DISPATCH(p, launch_fwd, (A, nrhs, s))
         if (e != cudaSuccess)
             return e;
         if (ntile == 0)
             continue;
-        const size_t smem = sizeof(float4) * 8 * A.Ts * A.Ts * A.Ts;
-        k_fft_m2l<<<dim3((unsigned)ntile, (unsigned)((A.nw + kFftWPerBlock - 1) / kFftWPerBlock), (unsigned)nrhs),
-                    kFftThreads, smem, s>>>(A);
+        // frequencies per block: enough blocks to fill the GPU several times
+        A.wpb = (int)std::max<int64_t>(1, std::min<int64_t>(kFftWPerBlock, (int64_t)ntile * nrhs * A.nw / 1200));
+        const unsigned nwb = (unsigned)((A.nw + A.wpb - 1) / A.wpb);
+        if (tiled) {
+            const size_t smem = sizeof(float2) * (8 * kPP + 8 * kTaps);
+            k_fft_m2l_tiled<<<dim3((unsigned)ntile, nwb, (unsigned)nrhs), kFftThreads, smem, s>>>(A, g_kmap);
+        } else {
+            const size_t smem = sizeof(float4) * 8 * A.Ts * A.Ts * A.Ts;
+            k_fft_m2l<<<dim3((unsigned)ntile, nwb, (unsigned)nrhs), kFftThreads, smem, s>>>(A);
+        }
         e = cudaGetLastError();
         if (e != cudaSuccess)
             return e;
-        const int groups = (A.T * A.T * A.T + A.nbi - 1) / A.nbi;
-        k_fft_inv<<<dim3((unsigned)ntile, (unsigned)groups, (unsigned)nrhs), 128, inv_smem, s>>>(A);
-        e = cudaGetLastError();
+        BBFMM_DFT_DISPATCH(p, launch_inv, (A, ntile, nrhs, s))
         if (e != cudaSuccess)
             return e;
     }
