@@ -49,6 +49,7 @@ extern "C" {
 #define BBFMM_K_GAUSS 4        /* exp(-(r/ell)^2) */
 #define BBFMM_K_TEST_POLY 100  /* 1 + d1 - 2 d2 d3 + 3 d1^2 d2, d = x - y: exact for p >= 3 */
 #define BBFMM_K_TEST_CONST 101 /* 1 */
+#define BBFMM_K_USER_FIRST 1000 /* ids of kernels registered by bbfmm_kernel_register */
 
 /* interpolation nodes and the M2L that goes with them (Sec. 2.2 node sets,
  * Sec. 2.5 "Fast M2L translation") */
@@ -112,6 +113,27 @@ typedef struct {
     int64_t n_targets;  /* targets (= n unless built by bbfmm_plan_targets) */
     int reserved[6];
 } bbfmm_info;
+
+/*
+ * bbfmm_kernel_register: a kernel function supplied by the caller (the
+ * black-box interface: the method needs only evaluations of K, Sec. 1 and
+ * Sec. 3).  source is CUDA C that defines
+ *     __device__ double bbfmm_kernel_f64(double d0, double d1, double d2);
+ *     __device__ float  bbfmm_kernel_f32(float d0, float d1, float d2);
+ * K(x, y) = k(d), d = x - y in the caller's units; both must give the value
+ * wanted at d = 0 (the self and duplicate-point terms of the near field).
+ * The FP64 function fills the operator tables, the FP32 one runs in the near
+ * field.  The source is compiled at once with NVRTC for sm_103a.
+ *   homogeneity: m with k(a d) = a^m k(d) for all a > 0 (one operator set for
+ *                every level, scaled), or 0 (operators per level); -8..8.
+ *   symmetric:   1 if k(-d) = k(d) (one Gram matrix in the SVD), else 0.
+ *   kernel_id:   receives an id >= BBFMM_K_USER_FIRST, usable as kernel_id
+ *                in bbfmm_plan and bbfmm_plan_targets (opts.ell is unused
+ *                for it).  Registrations last until the process exits.
+ * Errors: EINVAL (NULL, homogeneity; a compile error, with the NVRTC log in
+ * bbfmm_last_error), ECUDA (no device, NVRTC not found, load failure).
+ */
+int bbfmm_kernel_register(const char *source, int homogeneity, int symmetric, int *kernel_id);
 
 /* Fill *opts with the defaults listed above. */
 void bbfmm_default_opts(bbfmm_opts *opts);

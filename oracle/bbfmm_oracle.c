@@ -62,6 +62,7 @@
 #define ORK_GAUSS 4
 #define ORK_POLY 100
 #define ORK_CONST 101
+#define ORK_USER 1000 /* the function set by oracle_set_user_kernel */
 
 static const double OR_PI = 3.14159265358979323846264338327950288;
 
@@ -71,10 +72,18 @@ static const double OR_PI = 3.14159265358979323846264338327950288;
  * the paper's exp(-r)).
  * poly: q(d) = 1 + d1 - 2 d2 d3 + 3 d1^2 d2, degree <= 2 in every coordinate,
  * reproduced exactly by interpolation with p >= 3 nodes (Def. 2.2).
- * const: 1. */
+ * const: 1.
+ * user: a caller-supplied function of d (the black-box interface: the method
+ * needs only evaluations of K, Sec. 1). */
+static double (*or_user_kernel)(double, double, double) = NULL;
+
+void oracle_set_user_kernel(double (*k)(double, double, double)) { or_user_kernel = k; }
+
 static double or_kernel(int kid, double ell, double d1, double d2, double d3)
 {
     double r2 = d1 * d1 + d2 * d2 + d3 * d3;
+    if (kid == ORK_USER)
+        return or_user_kernel ? or_user_kernel(d1, d2, d3) : NAN;
     switch (kid) {
     case ORK_INV_R:
         return r2 == 0.0 ? 0.0 : 1.0 / sqrt(r2);

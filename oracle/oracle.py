@@ -59,6 +59,8 @@ def lib():
             L.oracle_bbfmm_targets.argtypes = [i64, dp, dp, i32, i32, f64, i32, i32, dp, f64, i32, i64, dp, dp, dp]
             L.oracle_bbfmm_targets.restype = i32
             L.oracle_cheb_nodes.argtypes = [i32, dp]
+            L.oracle_set_user_kernel.argtypes = [ctypes.c_void_p]
+            L.oracle_set_user_kernel.restype = None
             L.oracle_uniform_nodes.argtypes = [i32, dp]
             L.oracle_lagrange_1d.argtypes = [i32, dp, f64, dp]
             L.oracle_neighbors.argtypes = [i32, i64, i64, i64, lp]
@@ -112,6 +114,31 @@ def bounding_cube(points):
 
 def num_threads() -> int:
     return int(lib().oracle_num_threads())
+
+
+K_USER = 1000   # the caller-supplied kernel set by use_user_kernel
+_user_libs = {}
+
+
+def use_user_kernel(c_body):
+    """Make K_USER the kernel k(d) = the C function body ``c_body`` of
+    ``double k(double d0, double d1, double d2)`` (d = x - y), compiled with
+    gcc into its own small library (the caller states the kernel; the oracle
+    only evaluates it).  Returns K_USER."""
+    import hashlib
+    key = hashlib.sha256(c_body.encode()).hexdigest()[:16]
+    if key not in _user_libs:
+        os.makedirs(_BUILD, exist_ok=True)
+        src = os.path.join(_BUILD, "user_%s.c" % key)
+        so = os.path.join(_BUILD, "libuser_%s.so" % key)
+        with open(src, "w") as fh:
+            fh.write("#include <math.h>\ndouble bbfmm_oracle_user_k(double d0, double d1, double d2)\n{\n%s\n}\n"
+                     % c_body)
+        subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", src, "-o", so, "-lm"], check=True)
+        _user_libs[key] = ctypes.CDLL(so)
+    fn = ctypes.cast(_user_libs[key].bbfmm_oracle_user_k, ctypes.c_void_p)
+    lib().oracle_set_user_kernel(fn)
+    return K_USER
 
 
 def kernel(kid, x, y, ell=1.0):

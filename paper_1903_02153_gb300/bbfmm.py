@@ -25,6 +25,7 @@ BBFMM_K_TEST_POLY, BBFMM_K_TEST_CONST = 100, 101
 BBFMM_PREC_FP32, BBFMM_PREC_TF32, BBFMM_PREC_TF32X3, BBFMM_PREC_BF16X3, BBFMM_PREC_FP16X3 = 0, 1, 2, 3, 4
 
 INTERPS = {"chebyshev": 0, "uniform": 1}   # BBFMM_INTERP_*
+BBFMM_K_USER_FIRST = 1000                   # ids of kernels from bbfmm_kernel_register
 
 PRECISIONS = {"fp32": BBFMM_PREC_FP32, "tf32": BBFMM_PREC_TF32, "tf32x3": BBFMM_PREC_TF32X3,
               "bf16x3": BBFMM_PREC_BF16X3, "fp16x3": BBFMM_PREC_FP16X3}
@@ -32,7 +33,7 @@ PRECISIONS = {"fp32": BBFMM_PREC_FP32, "tf32": BBFMM_PREC_TF32, "tf32x3": BBFMM_
 EXPORTED = ["bbfmm_default_opts", "bbfmm_plan", "bbfmm_matvec", "bbfmm_destroy",
             "bbfmm_last_error", "bbfmm_plan_info", "bbfmm_get_coefficients",
             "bbfmm_get_leaf_cells", "bbfmm_stage_times", "bbfmm_set_timing", "bbfmm_status",
-            "bbfmm_sort_points_static", "bbfmm_rand_eig", "bbfmm_plan_targets"]
+            "bbfmm_sort_points_static", "bbfmm_rand_eig", "bbfmm_plan_targets", "bbfmm_kernel_register"]
 
 
 class bbfmm_opts(ctypes.Structure):
@@ -102,6 +103,8 @@ def lib():
             L.bbfmm_plan_targets.argtypes = [vp, i64, vp, i64, i32, i32, i32, ctypes.POINTER(bbfmm_opts), vp,
                                              ctypes.POINTER(vp)]
             L.bbfmm_plan_targets.restype = i32
+            L.bbfmm_kernel_register.argtypes = [ctypes.c_char_p, i32, i32, ctypes.POINTER(i32)]
+            L.bbfmm_kernel_register.restype = i32
             _lib = L
     return _lib
 
@@ -168,6 +171,15 @@ def bbfmm_plan_targets(sources, targets, kernel_id, cheb_order, depth, opts=None
                                     ctypes.byref(opts) if opts is not None else None, _stream(stream),
                                     ctypes.byref(h)))
     return h
+
+
+def bbfmm_kernel_register(source, homogeneity=0, symmetric=False):
+    """Compile a user kernel (CUDA C defining bbfmm_kernel_f64 / _f32 of
+    d = x - y); returns its kernel id for Plan / bbfmm_plan."""
+    kid = ctypes.c_int(0)
+    _check(lib().bbfmm_kernel_register(source.encode(), int(homogeneity), 1 if symmetric else 0,
+                                       ctypes.byref(kid)))
+    return kid.value
 
 
 def bbfmm_matvec(plan, sigma, phi, nrhs=1, stream=None):

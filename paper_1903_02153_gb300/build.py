@@ -22,7 +22,10 @@ LIB = os.path.join(LIBDIR, "libbbfmm.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
-                     "-Xcompiler", "-fPIC,-fopenmp,-O3", "-I", os.path.join(ROOT, "include")]
+                     "-Xcompiler", "-fPIC,-fopenmp,-O3", "-I", os.path.join(ROOT, "include"), "-I", BUILD]
+# headers whose text the library embeds for run-time compilation (NVRTC) of
+# user-supplied kernels, in include order
+NVRTC_HEADERS = ["morton.cuh", "p2p_kernels.cuh"]
 
 
 def _nvcc():
@@ -48,6 +51,30 @@ def _digest():
     return h.hexdigest()
 
 
+def _c_string(text):
+    out = []
+    for line in text.splitlines(True):
+        esc = line.replace("\\", "\\\\").replace('"', '\\"').replace("\n", "\\n")
+        out.append('"%s"' % esc)
+    return "\n".join(out) if out else '""'
+
+
+def write_nvrtc_headers():
+    """Write _build/nvrtc_headers.inc: the {name, text} of every header in
+    NVRTC_HEADERS, as C string literals."""
+    parts = ["// generated by build.py from csrc/ (do not edit)",
+             "struct NvrtcHeader { const char *name, *text; };",
+             "static const NvrtcHeader kNvrtcHeaders[] = {"]
+    for name in NVRTC_HEADERS:
+        with open(os.path.join(CSRC, name)) as fh:
+            parts.append('    {"%s",\n%s},' % (name, _c_string(fh.read())))
+    parts.append("};")
+    path = os.path.join(BUILD, "nvrtc_headers.inc")
+    with open(path, "w") as fh:
+        fh.write("\n".join(parts) + "\n")
+    return path
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
@@ -56,6 +83,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dig:
         return LIB
     nvcc = _nvcc()
+    write_nvrtc_headers()
     objs = []
 
     def compile_one(src):

@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "../../include/bbfmm.h"
+#include "morton.cuh"
 
 namespace bbfmm {
 
@@ -43,37 +44,6 @@ constexpr int kChunk = 128;           // near-field targets per work item (one b
 // status word bits written by device-side checks
 constexpr int kStatusBounds = 1;
 constexpr int kStatusTimeout = 2;
-
-// ---------------------------------------------------------------------------
-// Morton / cell helpers (x in bit 0 of every 3-bit group)
-__host__ __device__ inline uint32_t spread3(uint32_t v)
-{
-    v &= 0x3ff;
-    v = (v | (v << 16)) & 0x030000ff;
-    v = (v | (v << 8)) & 0x0300f00f;
-    v = (v | (v << 4)) & 0x030c30c3;
-    v = (v | (v << 2)) & 0x09249249;
-    return v;
-}
-__host__ __device__ inline uint32_t compact3(uint32_t v)
-{
-    v &= 0x09249249;
-    v = (v | (v >> 2)) & 0x030c30c3;
-    v = (v | (v >> 4)) & 0x0300f00f;
-    v = (v | (v >> 8)) & 0x030000ff;
-    v = (v | (v >> 16)) & 0x000003ff;
-    return v;
-}
-__host__ __device__ inline uint32_t morton3(uint32_t x, uint32_t y, uint32_t z)
-{
-    return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
-}
-__host__ __device__ inline void demorton3(uint32_t m, int &x, int &y, int &z)
-{
-    x = (int)compact3(m);
-    y = (int)compact3(m >> 1);
-    z = (int)compact3(m >> 2);
-}
 
 // row offset (in floats) of box (x, y, z), right-hand side c, in the
 // parity-split layouts at level l (H = 2^(l-1), padZ = 1 for Mt, 0 for Ft)
@@ -131,6 +101,14 @@ __host__ __device__ inline int offset_index(int tx, int ty, int tz)
 std::shared_ptr<HostOps> build_host_ops(int kernel, double ell, int p, double eps, int depth,
                                         double side, int interp, std::string &err);
 double kernel_value_host(int kernel, double ell, double d0, double d1, double d2);
+int kernel_homogeneity(int kernel); // m of K(a x, a y) = a^m K(x, y), 0 if none
+
+// user_kernel.cu: kernels registered through bbfmm_kernel_register
+int user_kernel_register(const char *source, int homogeneity, int symmetric, int *id, std::string &err);
+bool user_kernel_known(int id);
+bool user_kernel_traits(int id, int *homogeneity, int *symmetric);
+// K(d) in FP64 on the device for n difference vectors (host arrays n x 3 -> n)
+cudaError_t user_kernel_eval(int id, const double *d, int64_t n, double *out);
 
 // interpolation tables passed by value to the transfer kernels
 struct InterpTables {
@@ -366,6 +344,7 @@ struct P2PArgs {
 };
 cudaError_t launch_p2p(const P2PArgs &A, int kernel, double ell, double h, int nrhs, float *phi_near,
                        cudaStream_t s);
+cudaError_t launch_p2p_user(const P2PArgs &A, int id, double h, int nrhs, float *phi_near, cudaStream_t s);
 
 } // namespace bbfmm
 

@@ -127,7 +127,7 @@ static int get_ops(int kernel, double ell, int p, double eps, int depth, double 
     // homogeneous kernels depend on the domain only through h_D
     double key_side = side;
     int key_depth = depth;
-    if (kernel == BBFMM_K_INV_R || kernel == BBFMM_K_INV_R2) {
+    if (kernel_homogeneity(kernel) != 0) {
         key_side = side / (double)(1LL << depth);
         key_depth = 0;
     }
@@ -690,7 +690,12 @@ static int matvec_graph(bbfmm_plan_impl *P, const float *sigma, float *phi, int 
             if (type != cudaGraphNodeTypeKernel)
                 continue;
             cudaKernelNodeParams kp;
-            CUDA_TRY(cudaGraphKernelNodeGetParams(node, &kp));
+            if (cudaGraphKernelNodeGetParams(node, &kp) != cudaSuccess) {
+                // kernels of a run-time compiled library (user kernels) do not
+                // report their parameters here; they are not gather / combine
+                cudaGetLastError();
+                continue;
+            }
             if (kp.func == gather_kernel()) {
                 g.gather = node;
                 g.gp = kp;
@@ -752,6 +757,21 @@ void bbfmm_default_opts(bbfmm_opts *o)
 
 const char *bbfmm_last_error(void) { return g_last_error.c_str(); }
 
+int bbfmm_kernel_register(const char *source, int homogeneity, int symmetric, int *kernel_id)
+{
+    g_last_error.clear();
+    if (!source || !kernel_id)
+        return fail(BBFMM_EINVAL, "NULL argument");
+    *kernel_id = 0;
+    if (homogeneity < -8 || homogeneity > 8)
+        return fail(BBFMM_EINVAL, "homogeneity %d out of range [-8, 8]", homogeneity);
+    std::string err;
+    int st = user_kernel_register(source, homogeneity, symmetric, kernel_id, err);
+    if (st != BBFMM_OK)
+        return fail(st, "%s", err.c_str());
+    return BBFMM_OK;
+}
+
 static int plan_create(const double *points, int64_t n, const double *targets, int64_t nt, int kernel_id,
                        int cheb_order, int depth, const bbfmm_opts *opts_in, void *stream, bbfmm_plan_t *out)
 {
@@ -770,7 +790,8 @@ static int plan_create(const double *points, int64_t n, const double *targets, i
     if (targets && (nt < 1 || nt >= (1LL << 31)))
         return fail(BBFMM_EINVAL, "number of targets %lld out of range [1, 2^31)", (long long)nt);
     if (!(kernel_id == BBFMM_K_INV_R || kernel_id == BBFMM_K_INV_R2 || kernel_id == BBFMM_K_EXP ||
-          kernel_id == BBFMM_K_GAUSS || kernel_id == BBFMM_K_TEST_POLY || kernel_id == BBFMM_K_TEST_CONST))
+          kernel_id == BBFMM_K_GAUSS || kernel_id == BBFMM_K_TEST_POLY || kernel_id == BBFMM_K_TEST_CONST ||
+          (kernel_id >= BBFMM_K_USER_FIRST && user_kernel_known(kernel_id))))
         return fail(BBFMM_EINVAL, "unknown kernel id %d", kernel_id);
     if (cheb_order < 2 || cheb_order > kMaxP)
         return fail(BBFMM_EINVAL, "cheb_order %d out of range [2, %d]", cheb_order, kMaxP);

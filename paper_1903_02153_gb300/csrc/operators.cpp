@@ -58,19 +58,42 @@ double kernel_value_host(int kernel, double ell, double d0, double d1, double d2
     return 0.0;
 }
 
-static int homogeneity(int kernel)
+int kernel_homogeneity(int kernel)
 {
     if (kernel == BBFMM_K_INV_R)
         return -1;
     if (kernel == BBFMM_K_INV_R2)
         return -2;
+    int h = 0, sym = 0;
+    if (kernel >= BBFMM_K_USER_FIRST && user_kernel_traits(kernel, &h, &sym))
+        return h;
     return 0;
 }
 
 static bool symmetric_kernel(int kernel)
 {
+    int h = 0, sym = 0;
+    if (kernel >= BBFMM_K_USER_FIRST && user_kernel_traits(kernel, &h, &sym))
+        return sym != 0;
     return kernel == BBFMM_K_INV_R || kernel == BBFMM_K_INV_R2 || kernel == BBFMM_K_EXP ||
            kernel == BBFMM_K_GAUSS || kernel == BBFMM_K_TEST_CONST;
+}
+
+// K at n difference vectors d (n x 3, physical units): built-in kernels on
+// the host, user kernels on the device in batches
+static bool eval_kernel(const HostOps &o, const double *d, int64_t n, double *out)
+{
+    if (o.kernel < BBFMM_K_USER_FIRST) {
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i)
+            out[i] = kernel_value_host(o.kernel, o.ell, d[3 * i], d[3 * i + 1], d[3 * i + 2]);
+        return true;
+    }
+    const int64_t batch = 1 << 22;
+    for (int64_t i0 = 0; i0 < n; i0 += batch)
+        if (user_kernel_eval(o.kernel, d + 3 * i0, std::min(batch, n - i0), out + i0) != cudaSuccess)
+            return false;
+    return true;
 }
 
 // Cyclic Jacobi eigen-decomposition of a symmetric n x n matrix A (row-major,
@@ -145,29 +168,41 @@ static int rank_at(const std::vector<double> &w, double eps)
 }
 
 // operators of one level with box side h
-static void build_level(HostOps &o, double h, std::vector<double> &U, std::vector<double> &V,
+static bool build_level(HostOps &o, double h, std::vector<double> &U, std::vector<double> &V,
                         std::vector<double> &C, std::vector<double> &sv, int &ru, int &rv)
 {
     const int p = o.p, p3 = o.p3;
-    // K^(t) for all 316 offsets, row = target node i, column = source node j
+    // K^(t) for all 316 offsets, row = target node i, column = source node j;
+    // evaluated in groups of offsets (the difference vectors of one group at
+    // a time)
     std::vector<double> K((size_t)kNumOffsets * p3 * p3);
+    const int group = (int)std::max<int64_t>(1, std::min<int64_t>(kNumOffsets, (1 << 22) / ((int64_t)p3 * p3)));
+    std::vector<double> dv((size_t)group * p3 * p3 * 3);
+    for (int u0 = 0; u0 < kNumOffsets; u0 += group) {
+        const int u1 = std::min(kNumOffsets, u0 + group);
 #pragma omp parallel for schedule(dynamic)
-    for (int t = 0; t < 343; ++t) {
-        int tx = t % 7 - 3, ty = (t / 7) % 7 - 3, tz = t / 49 - 3;
-        int idx = offset_index(tx, ty, tz);
-        if (idx < 0)
-            continue;
-        double *Kt = &K[(size_t)idx * p3 * p3];
-        for (int i = 0; i < p3; ++i) {
-            double x0 = 0.5 * h * o.nodes[i % p], x1 = 0.5 * h * o.nodes[(i / p) % p],
-                   x2 = 0.5 * h * o.nodes[i / (p * p)];
-            for (int j = 0; j < p3; ++j) {
-                double y0 = tx * h + 0.5 * h * o.nodes[j % p];
-                double y1 = ty * h + 0.5 * h * o.nodes[(j / p) % p];
-                double y2 = tz * h + 0.5 * h * o.nodes[j / (p * p)];
-                Kt[(size_t)i * p3 + j] = kernel_value_host(o.kernel, o.ell, x0 - y0, x1 - y1, x2 - y2);
+        for (int t = 0; t < 343; ++t) {
+            int tx = t % 7 - 3, ty = (t / 7) % 7 - 3, tz = t / 49 - 3;
+            int idx = offset_index(tx, ty, tz);
+            if (idx < u0 || idx >= u1)
+                continue;
+            double *dt = &dv[(size_t)(idx - u0) * p3 * p3 * 3];
+            for (int i = 0; i < p3; ++i) {
+                double x0 = 0.5 * h * o.nodes[i % p], x1 = 0.5 * h * o.nodes[(i / p) % p],
+                       x2 = 0.5 * h * o.nodes[i / (p * p)];
+                for (int j = 0; j < p3; ++j) {
+                    double y0 = tx * h + 0.5 * h * o.nodes[j % p];
+                    double y1 = ty * h + 0.5 * h * o.nodes[(j / p) % p];
+                    double y2 = tz * h + 0.5 * h * o.nodes[j / (p * p)];
+                    double *e = dt + ((size_t)i * p3 + j) * 3;
+                    e[0] = x0 - y0;
+                    e[1] = x1 - y1;
+                    e[2] = x2 - y2;
+                }
             }
         }
+        if (!eval_kernel(o, dv.data(), (int64_t)(u1 - u0) * p3 * p3, &K[(size_t)u0 * p3 * p3]))
+            return false;
     }
     if (o.eps <= 0.0) { // no compression: U = V = I, C = K
         o.r = p3;
@@ -178,7 +213,7 @@ static void build_level(HostOps &o, double h, std::vector<double> &U, std::vecto
         V = U;
         C = K;
         sv.assign(p3, 0.0);
-        return;
+        return true;
     }
     // Gram matrices of the fat and the tall operator matrices
     std::vector<double> GU((size_t)p3 * p3, 0.0), GV;
@@ -257,15 +292,16 @@ static void build_level(HostOps &o, double h, std::vector<double> &U, std::vecto
                     Ct[(size_t)a * r + k] += u * KV[(size_t)i * r + k];
             }
     }
+    return true;
 }
 
 // spectra of the 316 kernel tables c_t of one level (box side h), equally
 // spaced nodes: out[(w * 316 + u) * 2 + {0, 1}] = DFT(c_t)(w) / n^3 with
 // DFT(c)(w) = sum_j c[j] exp(-2 pi i (w . j) / n), j, w in [0, n)^3, w =
 // (wz n + wy) p + wx, wx < p
-static void build_khat(const HostOps &o, double h, std::vector<double> &out)
+static bool build_khat(const HostOps &o, double h, std::vector<double> &out)
 {
-    const int p = o.p, n = 2 * p - 1, nw = n * n * p;
+    const int p = o.p, n = 2 * p - 1, nw = n * n * p, n3 = n * n * n;
     out.assign((size_t)nw * kNumOffsets * 2, 0.0);
     std::vector<double> cs(n), sn(n);
     for (int k = 0; k < n; ++k) {
@@ -273,22 +309,32 @@ static void build_khat(const HostOps &o, double h, std::vector<double> &out)
         sn[k] = sin(2.0 * M_PI * k / n);
     }
     const double norm = 1.0 / ((double)n * n * n);
+    // the kernel tables c_t[jz][jy][jx], j = d mod n for d in [-(p-1), p-1]
+    std::vector<double> dv((size_t)kNumOffsets * n3 * 3), cv((size_t)kNumOffsets * n3);
+    for (int t = 0; t < 343; ++t) {
+        const int tx = t % 7 - 3, ty = (t / 7) % 7 - 3, tz = t / 49 - 3;
+        const int u = offset_index(tx, ty, tz);
+        if (u < 0)
+            continue;
+        for (int dz = 1 - p; dz < p; ++dz)
+            for (int dy = 1 - p; dy < p; ++dy)
+                for (int dx = 1 - p; dx < p; ++dx) {
+                    const int jx = (dx + n) % n, jy = (dy + n) % n, jz = (dz + n) % n;
+                    double *e = &dv[((size_t)u * n3 + ((size_t)jz * n + jy) * n + jx) * 3];
+                    e[0] = h * (-tx + dx / (p - 1.0));
+                    e[1] = h * (-ty + dy / (p - 1.0));
+                    e[2] = h * (-tz + dz / (p - 1.0));
+                }
+    }
+    if (!eval_kernel(o, dv.data(), (int64_t)kNumOffsets * n3, cv.data()))
+        return false;
 #pragma omp parallel for schedule(dynamic)
     for (int t = 0; t < 343; ++t) {
         const int tx = t % 7 - 3, ty = (t / 7) % 7 - 3, tz = t / 49 - 3;
         const int u = offset_index(tx, ty, tz);
         if (u < 0)
             continue;
-        // c[jz][jy][jx], j = d mod n for d in [-(p-1), p-1]
-        std::vector<double> c((size_t)n * n * n, 0.0);
-        for (int dz = 1 - p; dz < p; ++dz)
-            for (int dy = 1 - p; dy < p; ++dy)
-                for (int dx = 1 - p; dx < p; ++dx) {
-                    const double a = h * (-tx + dx / (p - 1.0)), b = h * (-ty + dy / (p - 1.0)),
-                                 e = h * (-tz + dz / (p - 1.0));
-                    const int jx = (dx + n) % n, jy = (dy + n) % n, jz = (dz + n) % n;
-                    c[((size_t)jz * n + jy) * n + jx] = kernel_value_host(o.kernel, o.ell, a, b, e);
-                }
+        const double *c = &cv[(size_t)u * n3];
         // x: real -> complex, wx < p; then y and z complex, all n frequencies
         std::vector<double> A((size_t)n * n * p * 2), B((size_t)n * n * p * 2);
         for (int jz = 0; jz < n; ++jz)
@@ -334,6 +380,7 @@ static void build_khat(const HostOps &o, double h, std::vector<double> &out)
                     out[(w * kNumOffsets + u) * 2 + 1] = im * norm;
                 }
     }
+    return true;
 }
 
 std::shared_ptr<HostOps> build_host_ops(int kernel, double ell, int p, double eps, int depth, double side,
@@ -345,7 +392,7 @@ std::shared_ptr<HostOps> build_host_ops(int kernel, double ell, int p, double ep
     o->p = p;
     o->p3 = p * p * p;
     o->eps = eps;
-    o->hom_degree = homogeneity(kernel);
+    o->hom_degree = kernel_homogeneity(kernel);
     o->interp = interp;
     o->nodes.resize(p);
     for (int k = 1; k <= p; ++k)
@@ -391,9 +438,11 @@ std::shared_ptr<HostOps> build_host_ops(int kernel, double ell, int p, double ep
             o->U.push_back(I);
             o->V.push_back(I);
             o->khat.emplace_back();
-            build_khat(*o, h, o->khat.back());
+            if (!build_khat(*o, h, o->khat.back())) {
+                err = "evaluating the kernel tables failed";
+                return nullptr;
+            }
         }
-        (void)err;
         return o;
     }
     o->U.resize(nlev);
@@ -407,7 +456,10 @@ std::shared_ptr<HostOps> build_host_ops(int kernel, double ell, int p, double ep
         double h = side / (double)(1LL << level);
         o->h[k] = h;
         int ru = 0, rv = 0;
-        build_level(*o, h, o->U[k], o->V[k], o->C[k], o->sv[k], ru, rv);
+        if (!build_level(*o, h, o->U[k], o->V[k], o->C[k], o->sv[k], ru, rv)) {
+            err = "evaluating the M2L operators failed";
+            return nullptr;
+        }
         o->rl.push_back(o->r);
         o->rank_u = std::max(o->rank_u, ru);
         o->rank_v = std::max(o->rank_v, rv);

@@ -1,363 +1,12 @@
-// p2p.cu -- near-field stage (Sec. 2.2 item 4):
-//   phi_i += sum_{beta in N(alpha)} sum_{y_j in beta} K(x_i, y_j) sigma_j,
-// N(alpha) = the up to 27 leaves adjacent to alpha, alpha included (Def. 2.1).
-//
-// Targets and sources are two point sets binned into the same leaves (the
-// same arrays when the targets are the sources).  Work item = up to kChunk
-// consecutive targets of one leaf; one block of 128 threads per item.  The block first gathers the neighbour leaves' sources
-// into shared memory (all threads at once, coalesced, kStageSrc at a time),
-// with coordinates in the target leaf's cell units: y' = u_y + (cell_y -
-// cell_x).  The offset is an exact small integer, so the FP32 difference
-// u_x - y' only carries the rounding of u (|u| <= 1/2), not that of absolute
-// coordinates.
-//
-// Each thread owns kTPT targets (two packed pairs by default) and evaluates
-// them against every source it visits with the packed two-lane FP32
-// instructions of sm_100+ (FADD2 / FMUL2 / FFMA2); a source is staged as
-// (x, x, y, y), (z, z, s, s) so both halves of a packed operand come from one
-// shared-memory broadcast.
-// Threads are (target group, slice): slice s walks sources s, s + S, ...; the
-// slices of a target are added in a fixed order at the end (deterministic).
-// K at r = 0 follows the library's convention: 0 for 1/r and 1/r^2.
-#include <type_traits>
-
+// p2p.cu -- near-field stage (Sec. 2.2 item 4): launches of the kernels in
+// p2p_kernels.cuh for the built-in kernel functions; user-supplied kernels
+// run the same templates compiled at run time (user_kernel.cu).
 #include "bbfmm_internal.h"
+#include "p2p_kernels.cuh"
 
 namespace bbfmm {
 
-constexpr int kP2PThreads = 128;
-constexpr int kStageSrc = 512; // staged sources per pass (16 KB): 8+ blocks per SM
-
-// single hardware approximations (MUFU); distinct points never give a
-// subnormal squared distance here (|u| <= 1.5, so r2 >= 2^-48 or r2 = 0)
-__device__ __forceinline__ float rsqrt_approx(float x)
-{
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float rcp_approx(float x)
-{
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float ex2_approx(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// each kernel maps the squared distance r2 (cell units) and the offsets to
-// K; the packed form applies it to both lanes.  one() follows the r = 0
-// convention (0 for the singular kernels) and serves the target's own leaf,
-// the only place where a point meets itself or an exact duplicate; far()
-// serves the other 26 leaves.  There r2 = 0 could only come from FP32
-// rounding of two distinct points closer than ~1e-7 cells, so the kernel
-// adds kR2Floor = 2^-48 (cell units squared) to r2 instead of testing it:
-// 1/r stays below 2^24 / h, and the shift is 1e-14 of any r2 that can occur.
-constexpr float kR2Floor = 3.5527136788005009e-15f; // 2^-48
-struct KInvR {
-    float a; // unused
-    __device__ float one(float r2, float, float, float) const { return r2 > 0.0f ? rsqrt_approx(r2) : 0.0f; }
-    __device__ float far(float r2, float, float, float) const { return rsqrt_approx(r2); }
-};
-struct KInvR2 {
-    float a;
-    __device__ float one(float r2, float, float, float) const { return r2 > 0.0f ? rcp_approx(r2) : 0.0f; }
-    __device__ float far(float r2, float, float, float) const { return rcp_approx(r2); }
-};
-struct KExp { // exp(-h r / ell) = 2^(-a r), a = h / (ell ln 2)
-    float a;
-    __device__ float one(float r2, float, float, float) const
-    {
-        return ex2_approx(-a * (r2 > 0.0f ? r2 * rsqrt_approx(r2) : 0.0f));
-    }
-    __device__ float far(float r2, float, float, float) const { return ex2_approx(-a * (r2 * rsqrt_approx(r2))); }
-};
-struct KGauss { // exp(-(h r / ell)^2) = 2^(-a r^2), a = h^2 / (ell^2 ln 2)
-    float a;
-    __device__ float one(float r2, float, float, float) const { return ex2_approx(-a * r2); }
-    __device__ float far(float r2, float dx, float dy, float dz) const { return one(r2, dx, dy, dz); }
-};
-struct KPoly { // q(d) with d = h * (x - y) in physical units
-    float a;   // h
-    __device__ float one(float, float dx, float dy, float dz) const
-    {
-        float d0 = a * dx, d1 = a * dy, d2 = a * dz;
-        return 1.0f + d0 - 2.0f * d1 * d2 + 3.0f * d0 * d0 * d1;
-    }
-    __device__ float far(float r2, float dx, float dy, float dz) const { return one(r2, dx, dy, dz); }
-};
-struct KConst {
-    float a;
-    __device__ float one(float, float, float, float) const { return 1.0f; }
-    __device__ float far(float, float, float, float) const { return 1.0f; }
-};
-
-template <bool OWN, class Kern>
-__device__ __forceinline__ float2 kern2(const Kern &k, float2 r2, float2 dx, float2 dy, float2 dz)
-{
-    if (OWN)
-        return make_float2(k.one(r2.x, dx.x, dy.x, dz.x), k.one(r2.y, dx.y, dy.y, dz.y));
-    return make_float2(k.far(r2.x, dx.x, dy.x, dz.x), k.far(r2.y, dx.y, dy.y, dz.y));
-}
-
-// targets per thread (2 or 4): each thread runs 1 or 2 packed target pairs
-// against every source it visits, so a source's two shared-memory loads serve
-// that many targets
-#ifndef BBFMM_P2P_TPT
-#define BBFMM_P2P_TPT 4
-#endif
-constexpr int kTPT = BBFMM_P2P_TPT;
-static_assert(kTPT == 2 || kTPT == 4, "2 or 4 targets per thread");
-
-template <class Kern>
-__global__ void __launch_bounds__(kP2PThreads, 8)
-    k_p2p(const float4 *__restrict__ tpts, const int4 *__restrict__ chunks, int64_t n_tgt,
-          const float4 *__restrict__ spts, const float *__restrict__ sig, const int *__restrict__ off, int64_t n_src,
-          int D, Kern kern, float scale, int nrhs, float *__restrict__ phi)
-{
-    constexpr int NPK = kTPT / 2; // packed target pairs per thread
-    __shared__ float4 stage_xy[kStageSrc]; // (x, x, y, y)
-    __shared__ float4 stage_zs[kStageSrc]; // (z, z, sigma, sigma)
-    __shared__ int nb_start[28], nb_pre[28];
-    __shared__ float4 nb_delta[27];
-    __shared__ float2 red[NPK][kP2PThreads];
-    const int tid = threadIdx.x;
-    const int4 ch = chunks[blockIdx.x];
-    const int nt = ch.z;
-    const int nq = (nt + kTPT - 1) / kTPT; // target groups (one per thread and slice)
-    const int S = kP2PThreads / nq;        // slices per group (>= 1)
-    const int t = tid % nq, slice = tid / nq;
-    const bool active = slice < S;
-    int ax, ay, az;
-    demorton3((uint32_t)ch.x, ax, ay, az);
-    const int nside = 1 << D;
-
-    // neighbour leaves: start, count (prefix) and cell offset; the target's
-    // own leaf comes first, so its sources are staged ahead of the others
-    if (tid < 32) {
-        int cnt = 0, start = 0;
-        if (tid < 27) {
-            const int nid = tid == 0 ? 13 : (tid <= 13 ? tid - 1 : tid);
-            const int dx = nid % 3 - 1, dy = (nid / 3) % 3 - 1, dz = nid / 9 - 1;
-            const int bx = ax + dx, by = ay + dy, bz = az + dz;
-            if (bx >= 0 && by >= 0 && bz >= 0 && bx < nside && by < nside && bz < nside) {
-                const uint32_t nm = morton3((uint32_t)bx, (uint32_t)by, (uint32_t)bz);
-                start = off[nm];
-                cnt = off[nm + 1] - start;
-            }
-            nb_start[tid] = start;
-            nb_delta[tid] = make_float4((float)dx, (float)dy, (float)dz, 0.0f);
-        }
-        int incl = cnt; // inclusive warp scan of the counts
-        for (int o = 1; o < 32; o <<= 1) {
-            int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (tid >= o)
-                incl += v;
-        }
-        if (tid < 28)
-            nb_pre[tid] = incl - cnt; // exclusive prefix; nb_pre[27] = total
-    }
-    __syncthreads();
-    const int ns = nb_pre[27], nown = nb_pre[1]; // all sources; those of the own leaf
-    // the group's targets t + q nq; a missing one duplicates target t
-    float2 X[NPK], Y[NPK], Z[NPK];
-#pragma unroll
-    for (int pk = 0; pk < NPK; ++pk) {
-        const int i0 = t + 2 * pk * nq, i1 = i0 + nq;
-        const float4 xa = tpts[ch.y + (active && i0 < nt ? i0 : 0)];
-        const float4 xb = tpts[ch.y + (active && i1 < nt ? i1 : 0)];
-        X[pk] = make_float2(xa.x, xb.x);
-        Y[pk] = make_float2(xa.y, xb.y);
-        Z[pk] = make_float2(xa.z, xb.z);
-    }
-    const float2 floor2 = make_float2(kR2Floor, kR2Floor);
-
-    for (int c = 0; c < nrhs; ++c) {
-        const float *sg = sig + (int64_t)c * n_src;
-        float2 acc[NPK], acc2[NPK];
-#pragma unroll
-        for (int pk = 0; pk < NPK; ++pk)
-            acc[pk] = acc2[pk] = make_float2(0.0f, 0.0f);
-        for (int base = 0; base < ns; base += kStageSrc) {
-            const int cnt = min(kStageSrc, ns - base);
-            int k = 0; // neighbour holding source gg: it only moves forward as gg grows
-            for (int g = tid; g < cnt; g += kP2PThreads) {
-                const int gg = base + g;
-                while (nb_pre[k + 1] <= gg)
-                    ++k;
-                const int src = nb_start[k] + (gg - nb_pre[k]);
-                const float4 u = spts[src];
-                const float4 d = nb_delta[k];
-                const float s = sg[src];
-                // staged negated so that x_target - y' is one packed add
-                const float x = -(u.x + d.x), y = -(u.y + d.y), z = -(u.z + d.z);
-                stage_xy[g] = make_float4(x, x, y, y);
-                stage_zs[g] = make_float4(z, z, s, s);
-            }
-            __syncthreads();
-            if (active) {
-                // one source against the thread's NPK target pairs
-                auto visit = [&](auto own, int j, float2 *a) {
-                    const float4 qa = stage_xy[j];
-                    const float4 qb = stage_zs[j];
-#pragma unroll
-                    for (int pk = 0; pk < NPK; ++pk) {
-                        const float2 dx = __fadd2_rn(X[pk], make_float2(qa.x, qa.y));
-                        const float2 dy = __fadd2_rn(Y[pk], make_float2(qa.z, qa.w));
-                        const float2 dz = __fadd2_rn(Z[pk], make_float2(qb.x, qb.y));
-                        float2 r2 = decltype(own)::value ? __fmul2_rn(dx, dx) : __ffma2_rn(dx, dx, floor2);
-                        r2 = __ffma2_rn(dy, dy, r2);
-                        r2 = __ffma2_rn(dz, dz, r2);
-                        a[pk] = __ffma2_rn(kern2<decltype(own)::value>(kern, r2, dx, dy, dz),
-                                           make_float2(qb.z, qb.w), a[pk]);
-                    }
-                };
-                // the own leaf's sources (staged first) with the r = 0 test
-                const int cown = min(cnt, max(0, nown - base));
-                int j = slice;
-                for (; j < cown; j += S)
-                    visit(std::true_type{}, j, acc);
-                // two sources per iteration into two accumulator sets (shorter
-                // dependency chains), added in a fixed order at the end
-#pragma unroll 2
-                for (; j + S < cnt; j += 2 * S) {
-                    visit(std::false_type{}, j, acc);
-                    visit(std::false_type{}, j + S, acc2);
-                }
-                if (j < cnt)
-                    visit(std::false_type{}, j, acc);
-            }
-            __syncthreads();
-        }
-#pragma unroll
-        for (int pk = 0; pk < NPK; ++pk)
-            red[pk][tid] = active ? make_float2(acc[pk].x + acc2[pk].x, acc[pk].y + acc2[pk].y)
-                                  : make_float2(0.0f, 0.0f);
-        __syncthreads();
-        if (tid < nq) {
-#pragma unroll
-            for (int pk = 0; pk < NPK; ++pk) {
-                float sa = 0.0f, sb = 0.0f;
-                for (int q = 0; q < S; ++q) {
-                    const float2 v = red[pk][tid + q * nq];
-                    sa += v.x;
-                    sb += v.y;
-                }
-                const int i0 = tid + 2 * pk * nq, i1 = i0 + nq;
-                if (i0 < nt)
-                    phi[(int64_t)c * n_tgt + ch.y + i0] = scale * sa;
-                if (i1 < nt)
-                    phi[(int64_t)c * n_tgt + ch.y + i1] = scale * sb;
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// Several right-hand sides (Sec. 2.5 "Multiple right-hand-sides"): each pair's
-// K is evaluated once and applied to up to kRC weight columns staged next to
-// the source; threads are (target, slice) with one target each.
-constexpr int kRC = 8;
-constexpr int kStageMulti = 256;
-
-template <class Kern>
-__global__ void __launch_bounds__(kP2PThreads)
-    k_p2p_multi(const float4 *__restrict__ tpts, const int4 *__restrict__ chunks, int64_t n_tgt,
-                const float4 *__restrict__ spts, const float *__restrict__ sig, const int *__restrict__ off,
-                int64_t n_src, int D, Kern kern, float scale, int nrhs, float *__restrict__ phi)
-{
-    __shared__ float4 spos[kStageMulti];
-    __shared__ float ssig[kStageMulti][kRC];
-    __shared__ int nb_start[28], nb_pre[28];
-    __shared__ float4 nb_delta[27];
-    __shared__ float red[kP2PThreads][kRC + 1];
-    const int tid = threadIdx.x;
-    const int4 ch = chunks[blockIdx.x];
-    const int nt = ch.z;
-    const int S = kP2PThreads / nt;
-    const int t = tid % nt, slice = tid / nt;
-    const bool active = slice < S;
-    int ax, ay, az;
-    demorton3((uint32_t)ch.x, ax, ay, az);
-    const int nside = 1 << D;
-    if (tid < 32) {
-        int cnt = 0, start = 0;
-        if (tid < 27) {
-            const int dx = tid % 3 - 1, dy = (tid / 3) % 3 - 1, dz = tid / 9 - 1;
-            const int bx = ax + dx, by = ay + dy, bz = az + dz;
-            if (bx >= 0 && by >= 0 && bz >= 0 && bx < nside && by < nside && bz < nside) {
-                const uint32_t nm = morton3((uint32_t)bx, (uint32_t)by, (uint32_t)bz);
-                start = off[nm];
-                cnt = off[nm + 1] - start;
-            }
-            nb_start[tid] = start;
-            nb_delta[tid] = make_float4((float)dx, (float)dy, (float)dz, 0.0f);
-        }
-        int incl = cnt;
-        for (int o = 1; o < 32; o <<= 1) {
-            int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (tid >= o)
-                incl += v;
-        }
-        if (tid < 28)
-            nb_pre[tid] = incl - cnt;
-    }
-    __syncthreads();
-    const int ns = nb_pre[27];
-    const float4 xt = tpts[ch.y + (active ? t : 0)];
-    for (int c0 = 0; c0 < nrhs; c0 += kRC) {
-        const int rc = min(kRC, nrhs - c0);
-        float acc[kRC];
-#pragma unroll
-        for (int q = 0; q < kRC; ++q)
-            acc[q] = 0.0f;
-        for (int base = 0; base < ns; base += kStageMulti) {
-            const int cnt = min(kStageMulti, ns - base);
-            for (int g = tid; g < cnt; g += kP2PThreads) {
-                const int gg = base + g;
-                int k = 0;
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1)
-                    if (k + step < 27 && nb_pre[k + step] <= gg)
-                        k += step;
-                const int src = nb_start[k] + (gg - nb_pre[k]);
-                const float4 u = spts[src];
-                const float4 d = nb_delta[k];
-                spos[g] = make_float4(u.x + d.x, u.y + d.y, u.z + d.z, 0.0f);
-#pragma unroll
-                for (int q = 0; q < kRC; ++q)
-                    ssig[g][q] = q < rc ? sig[(int64_t)(c0 + q) * n_src + src] : 0.0f;
-            }
-            __syncthreads();
-            if (active)
-                for (int j = slice; j < cnt; j += S) {
-                    const float4 p = spos[j];
-                    const float dx = xt.x - p.x, dy = xt.y - p.y, dz = xt.z - p.z;
-                    const float K = kern.one(dx * dx + dy * dy + dz * dz, dx, dy, dz);
-#pragma unroll
-                    for (int q = 0; q < kRC; ++q)
-                        acc[q] += K * ssig[j][q];
-                }
-            __syncthreads();
-        }
-#pragma unroll
-        for (int q = 0; q < kRC; ++q)
-            red[tid][q] = active ? acc[q] : 0.0f;
-        __syncthreads();
-        if (tid < nt)
-            for (int q = 0; q < rc; ++q) {
-                float sum = 0.0f;
-                for (int sl = 0; sl < S; ++sl)
-                    sum += red[tid + sl * nt][q];
-                phi[(int64_t)(c0 + q) * n_tgt + ch.y + tid] = scale * sum;
-            }
-        __syncthreads();
-    }
-}
+static_assert(kP2PChunk == kChunk, "near-field work items");
 
 template <class Kern>
 static cudaError_t p2p_launch(const P2PArgs &A, Kern k, float scale, int nrhs, float *phi, cudaStream_t s)
@@ -393,6 +42,8 @@ cudaError_t launch_p2p(const P2PArgs &A, int kernel, double ell, double h, int n
     case BBFMM_K_TEST_CONST:
         return p2p_launch(A, KConst{0.f}, 1.0f, nrhs, phi_near, s);
     }
+    if (kernel >= BBFMM_K_USER_FIRST)
+        return launch_p2p_user(A, kernel, h, nrhs, phi_near, s);
     return cudaErrorInvalidValue;
 }
 

@@ -116,3 +116,12 @@ def test_plan_rejects_bad_interp(lib):
         o.interp, o.precision = interp, prec
         assert lib.lib().bbfmm_plan(pts.ctypes.data, 10, 1, 4, 3, ctypes.byref(o), None,
                                     ctypes.byref(h)) == lib.BBFMM_EINVAL, (interp, prec)
+
+
+def test_unknown_user_kernel_id_is_rejected(lib):
+    pts = np.random.default_rng(3).random((10, 3))
+    h = ctypes.c_void_p()
+    assert lib.lib().bbfmm_plan(pts.ctypes.data, 10, 1999, 4, 3, None, None, ctypes.byref(h)) == lib.BBFMM_EINVAL
+    kid = ctypes.c_int(0)
+    assert lib.lib().bbfmm_kernel_register(None, 0, 0, ctypes.byref(kid)) == lib.BBFMM_EINVAL
+    assert lib.lib().bbfmm_kernel_register(b"x", 9, 0, ctypes.byref(kid)) == lib.BBFMM_EINVAL

@@ -437,3 +437,24 @@ def test_uniform_m2l_is_block_toeplitz_and_applies_by_fft(oracle, kid, ell, p, t
     mp[:p, :p, :p] = m.reshape(p, p, p)
     conv = np.fft.irfftn(np.fft.rfftn(c) * np.fft.rfftn(mp), s=(n, n, n), axes=(0, 1, 2))[:p, :p, :p].reshape(-1)
     np.testing.assert_allclose(conv, K @ m, rtol=0, atol=1e-12 * np.abs(K @ m).max())
+
+
+# --- caller-supplied kernels (the black-box interface, Sec. 1) --------------
+
+def test_user_kernel_restating_a_builtin_is_identical(oracle):
+    """A user kernel that restates exp(-r/0.3) gives the built-in kernel's
+    direct sum and FMM bit for bit (the dispatch adds nothing)."""
+    x = W.clustered_points(1500, seed=33)
+    s = W.uniform_sigma(1500, seed=34)
+    k = oracle.use_user_kernel("return exp(-sqrt(d0 * d0 + d1 * d1 + d2 * d2) / 0.3);")
+    np.testing.assert_array_equal(oracle.direct(x, x, s, k), oracle.direct(x, x, s, K_EXP, 0.3))
+    np.testing.assert_array_equal(oracle.bbfmm(x, s, k, 4, 3), oracle.bbfmm(x, s, K_EXP, 4, 3, ell=0.3))
+
+
+def test_user_kernel_direct_matches_numpy(oracle):
+    x = W.uniform_points(600, seed=35)
+    s = W.uniform_sigma(600, seed=36)
+    k = oracle.use_user_kernel("return (1.0 + 0.3 * d0) / sqrt(d0 * d0 + d1 * d1 + d2 * d2 + 0.0025);")
+    d = x[:, None, :] - x[None, :, :]
+    K = (1.0 + 0.3 * d[..., 0]) / np.sqrt((d ** 2).sum(-1) + 0.0025)
+    np.testing.assert_allclose(oracle.direct(x, x, s, k), K @ s, rtol=1e-12, atol=1e-12)
