@@ -189,6 +189,7 @@ struct bbfmm_plan_impl {
     // work buffers
     Level lev[kMaxDepth + 1];
     float *sigma_s = nullptr, *phi_far = nullptr, *phi_near = nullptr;
+    float *sigma_rows = nullptr;                  // max_nrhs > 1: sigma_s row-major, for the near field
     float *io_sigma = nullptr, *io_phi = nullptr; // staging for host sigma / phi
     int *status = nullptr;                        // device status word
     // 16-bit split M2L: per level max |M~| (float bits) and the power-of-two
@@ -279,7 +280,7 @@ cudaError_t exclusive_scan_int(const int *in, int *out, int64_t n, int *block_su
 int64_t scan_scratch_ints(int64_t n);
 
 // transfers.cu
-cudaError_t launch_gather_sigma(const float *sigma, const int *perm, int64_t n, int nrhs, float *out,
+cudaError_t launch_gather_sigma(const float *sigma, const int *perm, int64_t n, int nrhs, float *out, float *rows,
                                 cudaStream_t s);
 // split the FP32 M~ of levels lmin..lmax (x[l], n[l] floats) into 16-bit
 // hi / lo after scaling by a power of two chosen from maxbits[l] (FP16, fmt 0)
@@ -337,7 +338,8 @@ struct P2PArgs {
     int nchunks;
     int64_t nt;
     const float4 *spts;
-    const float *sig;
+    const float *sig;      // ns x nrhs column-major
+    const float *sig_rows; // the same row-major (nrhs per source); used with several RHS
     const int *soff;
     int64_t ns;
     int D;

@@ -508,6 +508,8 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
         PTRY(plan_alloc(P, (void **)&P->a16_scale, 4 * (kMaxDepth + 1), true, s));
     }
     PTRY(plan_alloc(P, (void **)&P->sigma_s, 4 * n * R, false, s));
+    if (R > 1)
+        PTRY(plan_alloc(P, (void **)&P->sigma_rows, 4 * n * R, false, s));
     PTRY(plan_alloc(P, (void **)&P->phi_far, 4 * nt * R, false, s));
     PTRY(plan_alloc(P, (void **)&P->phi_near, 4 * nt * R, false, s));
     PTRY(plan_alloc(P, (void **)&P->status, 16, true, s));
@@ -582,7 +584,8 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
     const bool tm = P->timing;
     if (tm)
         CUDA_TRY(cudaEventRecord(P->ev[Stage::Start], s));
-    CUDA_TRY(launch_gather_sigma(sigma, P->perm, n, nrhs, P->sigma_s, s));
+    float *rows = nrhs > 1 ? P->sigma_rows : nullptr;
+    CUDA_TRY(launch_gather_sigma(sigma, P->perm, n, nrhs, P->sigma_s, rows, s));
     if (tm)
         CUDA_TRY(cudaEventRecord(P->ev[Stage::Gather], s));
 
@@ -594,7 +597,7 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
         CUDA_TRY(cudaStreamWaitEvent(P->side_stream, after, 0));
         if (tm)
             CUDA_TRY(cudaEventRecord(P->ev_p2p0, P->side_stream));
-        const P2PArgs pa = {P->tpts, P->chunks, P->nchunks, nt, P->pts, P->sigma_s, P->leaf_off, n, D};
+        const P2PArgs pa = {P->tpts, P->chunks, P->nchunks, nt, P->pts, P->sigma_s, rows, P->leaf_off, n, D};
         CUDA_TRY(launch_p2p(pa, P->kernel, P->ell, P->side / (double)(1LL << D), nrhs, P->phi_near,
                             P->side_stream));
         if (tm)
@@ -719,7 +722,9 @@ static int matvec_graph(bbfmm_plan_impl *P, const float *sigma, float *phi, int 
     // this call's pointers into the two boundary kernels
     const int64_t n = P->n, nt = P->nt;
     const float *far = P->D >= 2 ? P->phi_far : nullptr;
-    void *gargs[] = {(void *)&sigma, (void *)&P->perm, (void *)&n, (void *)&nrhs, (void *)&P->sigma_s};
+    float *rows = nrhs > 1 ? P->sigma_rows : nullptr;
+    void *gargs[] = {(void *)&sigma, (void *)&P->perm, (void *)&n, (void *)&nrhs, (void *)&P->sigma_s,
+                     (void *)&rows};
     void *cargs[] = {(void *)&far, (void *)&P->phi_near, (void *)&P->tperm, (void *)&nt, (void *)&nrhs,
                      (void *)&phi};
     cudaKernelNodeParams gp = g.gp, cp = g.cp;

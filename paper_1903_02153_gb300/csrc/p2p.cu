@@ -13,12 +13,13 @@ static cudaError_t p2p_launch(const P2PArgs &A, Kern k, float scale, int nrhs, f
 {
     if (A.nchunks <= 0)
         return cudaSuccess;
-    if (nrhs > 1)
-        k_p2p_multi<Kern><<<A.nchunks, kP2PThreads, 0, s>>>(A.tpts, A.chunks, A.nt, A.spts, A.sig, A.soff, A.ns,
-                                                             A.D, k, scale, nrhs, phi);
-    else
+    if (nrhs > 1) {
+        k_p2p_gemm<Kern, kGemmT><<<A.nchunks, gemm_threads(kGemmT), 0, s>>>(
+            A.tpts, A.chunks, A.nt, A.spts, A.sig_rows, A.soff, A.ns, A.D, k, scale, nrhs, phi);
+    } else {
         k_p2p<Kern><<<A.nchunks, kP2PThreads, 0, s>>>(A.tpts, A.chunks, A.nt, A.spts, A.sig, A.soff, A.ns, A.D, k,
                                                        scale, nrhs, phi);
+    }
     return cudaGetLastError();
 }
 

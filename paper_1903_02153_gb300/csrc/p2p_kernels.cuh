@@ -272,36 +272,45 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
     }
 }
 
-// Several right-hand sides (Sec. 2.5 "Multiple right-hand-sides"): each pair's
-// K is evaluated once and applied to up to kRC weight columns staged next to
-// the source; threads are (target, slice) with one target each.
-constexpr int kRC = 8;
-constexpr int kStageMulti = 256;
+// Several right-hand sides (Sec. 2.5 "Multiple right-hand-sides"): the near
+// field of a work item is a product of its kernel matrix (targets x
+// neighbourhood sources) with the weights (sources x nrhs, read row-major).  The block walks
+// the item's targets in sub-tiles of TT; per chunk of kGemmS sources it
+// evaluates the K tile once (TT x kGemmS, shared memory), stages the
+// weights (kGemmS x kGemmC) and adds K . sigma into registers: thread = 4
+// targets x 8 columns, 32 FMAs per source for three shared-memory loads.
+// Columns run in passes of kGemmC.  Leaves hold tens of points, so the tile
+// is narrow and the block small (two warps, many blocks per SM).
+constexpr int kGemmT = 32;  // targets per sub-tile (measured: 16 was slower on ~15-point leaves)
+constexpr int kGemmS = 32;  // sources per chunk
+constexpr int kGemmC = 64;  // right-hand sides per pass
+__host__ __device__ constexpr int gemm_threads(int TT) { return (TT / 4) * (kGemmC / 8); }
 
-template <class Kern>
-__global__ void __launch_bounds__(kP2PThreads)
-    k_p2p_multi(const float4 *__restrict__ tpts, const int4 *__restrict__ chunks, long long n_tgt,
-                const float4 *__restrict__ spts, const float *__restrict__ sig, const int *__restrict__ off,
-                long long n_src, int D, Kern kern, float scale, int nrhs, float *__restrict__ phi)
+// TT: targets per sub-tile (kGemmT), gemm_threads(TT) threads
+template <class Kern, int TT>
+__global__ void __launch_bounds__(gemm_threads(TT))
+    k_p2p_gemm(const float4 *__restrict__ tpts, const int4 *__restrict__ chunks, long long n_tgt,
+               const float4 *__restrict__ spts, const float *__restrict__ sig_rows, const int *__restrict__ off,
+               long long n_src, int D, Kern kern, float scale, int nrhs, float *__restrict__ phi)
 {
-    __shared__ float4 spos[kStageMulti];
-    __shared__ float ssig[kStageMulti][kRC];
+    __shared__ float4 sTgt[TT];
+    __shared__ float4 sPos[kGemmS];                     // (x, y, z) in the target leaf's frame, w = own leaf
+    __shared__ int sSrc[kGemmS];
+    __shared__ __align__(16) float sK[kGemmS][TT];
+    __shared__ __align__(16) float sSig[kGemmS][kGemmC];
     __shared__ int nb_start[28], nb_pre[28];
     __shared__ float4 nb_delta[27];
-    __shared__ float red[kP2PThreads][kRC + 1];
     const int tid = threadIdx.x;
     const int4 ch = chunks[blockIdx.x];
-    const int nt = ch.z;
-    const int S = kP2PThreads / nt;
-    const int t = tid % nt, slice = tid / nt;
-    const bool active = slice < S;
     int ax, ay, az;
     demorton3((unsigned)ch.x, ax, ay, az);
     const int nside = 1 << D;
+    // neighbour leaves, the target's own first (as in k_p2p)
     if (tid < 32) {
         int cnt = 0, start = 0;
         if (tid < 27) {
-            const int dx = tid % 3 - 1, dy = (tid / 3) % 3 - 1, dz = tid / 9 - 1;
+            const int nid = tid == 0 ? 13 : (tid <= 13 ? tid - 1 : tid);
+            const int dx = nid % 3 - 1, dy = (nid / 3) % 3 - 1, dz = nid / 9 - 1;
             const int bx = ax + dx, by = ay + dy, bz = az + dz;
             if (bx >= 0 && by >= 0 && bz >= 0 && bx < nside && by < nside && bz < nside) {
                 const unsigned nm = morton3((unsigned)bx, (unsigned)by, (unsigned)bz);
@@ -321,55 +330,107 @@ __global__ void __launch_bounds__(kP2PThreads)
             nb_pre[tid] = incl - cnt;
     }
     __syncthreads();
-    const int ns = nb_pre[27];
-    const float4 xt = tpts[ch.y + (active ? t : 0)];
-    for (int c0 = 0; c0 < nrhs; c0 += kRC) {
-        const int rc = min(kRC, nrhs - c0);
-        float acc[kRC];
+    const int ns = nb_pre[27], nown = nb_pre[1];
+    const int tg = tid % (TT / 4), cg = tid / (TT / 4);
+    const bool vec4 = (nrhs & 3) == 0; // rows of sig_rows start on 16-byte boundaries
+    const int t0 = 4 * tg, c8 = 8 * cg; // this thread's targets (in the sub-tile) and columns (in the pass)
+    for (int tt = 0; tt < ch.z; tt += TT) {
+        const int nt = min(TT, ch.z - tt); // targets of this sub-tile
+        for (int c0 = 0; c0 < nrhs; c0 += kGemmC) {
+            float acc[4][8];
 #pragma unroll
-        for (int q = 0; q < kRC; ++q)
-            acc[q] = 0.0f;
-        for (int base = 0; base < ns; base += kStageMulti) {
-            const int cnt = min(kStageMulti, ns - base);
-            for (int g = tid; g < cnt; g += kP2PThreads) {
-                const int gg = base + g;
-                int k = 0;
+            for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int step = 16; step > 0; step >>= 1)
-                    if (k + step < 27 && nb_pre[k + step] <= gg)
-                        k += step;
-                const int src = nb_start[k] + (gg - nb_pre[k]);
-                const float4 u = spts[src];
-                const float4 d = nb_delta[k];
-                spos[g] = make_float4(u.x + d.x, u.y + d.y, u.z + d.z, 0.0f);
-#pragma unroll
-                for (int q = 0; q < kRC; ++q)
-                    ssig[g][q] = q < rc ? sig[(long long)(c0 + q) * n_src + src] : 0.0f;
-            }
-            __syncthreads();
-            if (active)
-                for (int j = slice; j < cnt; j += S) {
-                    const float4 p = spos[j];
-                    const float dx = xt.x - p.x, dy = xt.y - p.y, dz = xt.z - p.z;
-                    const float K = kern.one(dx * dx + dy * dy + dz * dz, dx, dy, dz);
-#pragma unroll
-                    for (int q = 0; q < kRC; ++q)
-                        acc[q] += K * ssig[j][q];
+                for (int j = 0; j < 8; ++j)
+                    acc[i][j] = 0.0f;
+            for (int base = 0; base < ns; base += kGemmS) {
+                const int cnt = min(kGemmS, ns - base);
+                __syncthreads(); // the previous chunk's tiles are consumed
+                if (tid < TT)
+                    sTgt[tid] = tpts[ch.y + tt + (tid < nt ? tid : 0)];
+                if (tid < kGemmS) {
+                    const int gg = base + tid;
+                    float4 p = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    int src = -1;
+                    if (tid < cnt) {
+                        int k = 0;
+                        while (nb_pre[k + 1] <= gg)
+                            ++k;
+                        src = nb_start[k] + (gg - nb_pre[k]);
+                        const float4 u = spts[src];
+                        const float4 d = nb_delta[k];
+                        p = make_float4(u.x + d.x, u.y + d.y, u.z + d.z, gg < nown ? 1.0f : 0.0f);
+                    }
+                    sPos[tid] = p;
+                    sSrc[tid] = src;
                 }
-            __syncthreads();
-        }
+                __syncthreads();
+                // weights, row-major (nrhs per source): consecutive threads take
+                // consecutive columns of one source, four at a time when the
+                // rows are 16-byte aligned
+                if (vec4) {
+#pragma unroll 8
+                    for (int q = tid; q < kGemmS * kGemmC / 4; q += gemm_threads(TT)) {
+                        const int c = 4 * (q % (kGemmC / 4)), sidx = q / (kGemmC / 4);
+                        const int src = sSrc[sidx];
+                        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                        if (src >= 0 && c0 + c < nrhs) // nrhs % 4 == 0: the whole quad is in range
+                            v = __ldg(reinterpret_cast<const float4 *>(sig_rows + (long long)src * nrhs + c0 + c));
+                        *reinterpret_cast<float4 *>(&sSig[sidx][c]) = v;
+                    }
+                } else {
+#pragma unroll 8
+                    for (int q = tid; q < kGemmS * kGemmC; q += gemm_threads(TT)) {
+                        const int c = q % kGemmC, sidx = q / kGemmC;
+                        const int src = sSrc[sidx];
+                        sSig[sidx][c] =
+                            (src >= 0 && c0 + c < nrhs) ? __ldg(sig_rows + (long long)src * nrhs + c0 + c) : 0.0f;
+                    }
+                }
+                // K tile: thread = one target (coordinates in registers) and
+                // a stride of sources; a source's position is one broadcast
+                {
+                    constexpr int SPLIT = gemm_threads(TT) / TT; // threads per target
+                    const int t = tid % TT;
+                    const float4 x = sTgt[t];
+                    const bool tv = t < nt;
+#pragma unroll 4
+                    for (int sidx = tid / TT; sidx < kGemmS; sidx += SPLIT) {
+                        const float4 y = sPos[sidx];
+                        const float dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        float K = 0.0f;
+                        if (sidx < cnt && tv)
+                            K = y.w != 0.0f ? kern.one(r2, dx, dy, dz) : kern.far(r2 + kR2Floor, dx, dy, dz);
+                        sK[sidx][t] = K;
+                    }
+                }
+                __syncthreads();
+#pragma unroll 4
+                for (int sidx = 0; sidx < cnt; ++sidx) {
+                    const float4 k4 = *reinterpret_cast<const float4 *>(&sK[sidx][t0]);
+                    const float4 sa = *reinterpret_cast<const float4 *>(&sSig[sidx][c8]);
+                    const float4 sb = *reinterpret_cast<const float4 *>(&sSig[sidx][c8 + 4]);
+                    const float kv[4] = {k4.x, k4.y, k4.z, k4.w};
+                    const float sv[8] = {sa.x, sa.y, sa.z, sa.w, sb.x, sb.y, sb.z, sb.w};
 #pragma unroll
-        for (int q = 0; q < kRC; ++q)
-            red[tid][q] = active ? acc[q] : 0.0f;
-        __syncthreads();
-        if (tid < nt)
-            for (int q = 0; q < rc; ++q) {
-                float sum = 0.0f;
-                for (int sl = 0; sl < S; ++sl)
-                    sum += red[tid + sl * nt][q];
-                phi[(long long)(c0 + q) * n_tgt + ch.y + tid] = scale * sum;
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            acc[i][j] = fmaf(kv[i], sv[j], acc[i][j]);
+                }
             }
-        __syncthreads();
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = c0 + c8 + j;
+                if (c >= nrhs)
+                    continue;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (t0 + i < nt)
+                        phi[(long long)c * n_tgt + ch.y + tt + t0 + i] = scale * acc[i][j];
+            }
+        }
     }
 }
 

@@ -26,23 +26,29 @@ InterpTables make_interp_tables(const HostOps &h)
 }
 
 // ---------------------------------------------------------------------------
+// out: tree order, column-major (n x nrhs); rows (if not null): the same
+// values row-major (nrhs per point), the layout of the several-RHS near field
 __global__ void k_gather(const float *__restrict__ sigma, const int *__restrict__ perm, int64_t n, int nrhs,
-                         float *__restrict__ out)
+                         float *__restrict__ out, float *__restrict__ rows)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n)
         return;
     int j = perm[i];
-    for (int c = 0; c < nrhs; ++c)
-        out[(int64_t)c * n + i] = sigma[(int64_t)c * n + j];
+    for (int c = 0; c < nrhs; ++c) {
+        const float v = sigma[(int64_t)c * n + j];
+        out[(int64_t)c * n + i] = v;
+        if (rows)
+            rows[i * nrhs + c] = v;
+    }
 }
 
 const void *gather_kernel() { return (const void *)k_gather; }
 
-cudaError_t launch_gather_sigma(const float *sigma, const int *perm, int64_t n, int nrhs, float *out,
+cudaError_t launch_gather_sigma(const float *sigma, const int *perm, int64_t n, int nrhs, float *out, float *rows,
                                 cudaStream_t s)
 {
-    k_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sigma, perm, n, nrhs, out);
+    k_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sigma, perm, n, nrhs, out, rows);
     return cudaGetLastError();
 }
 

@@ -20,6 +20,8 @@
 
 namespace bbfmm {
 
+static_assert(kGemmT == 32, "the run-time instantiation below names k_p2p_gemm<KUser, 32>");
+
 namespace {
 
 // NVRTC, opened on first use (the library does not link it)
@@ -123,7 +125,7 @@ int user_kernel_register(const char *source, int homogeneity, int symmetric, int
         err = "nvrtcCreateProgram failed";
         return BBFMM_ECUDA;
     }
-    const char *p2p_name = "bbfmm::k_p2p<bbfmm::KUser>", *multi_name = "bbfmm::k_p2p_multi<bbfmm::KUser>";
+    const char *p2p_name = "bbfmm::k_p2p<bbfmm::KUser>", *multi_name = "bbfmm::k_p2p_gemm<bbfmm::KUser, 32>";
     nv.add_name(prog, p2p_name);
     nv.add_name(prog, multi_name);
     const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-default-device"};
@@ -157,6 +159,7 @@ int user_kernel_register(const char *source, int homogeneity, int symmetric, int
         e = cudaLibraryGetKernel(&k.p2p, k.lib, p2p_sym.c_str());
     if (e == cudaSuccess)
         e = cudaLibraryGetKernel(&k.p2p_multi, k.lib, multi_sym.c_str());
+
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (k.lib)
@@ -237,11 +240,14 @@ cudaError_t launch_p2p_user(const P2PArgs &A, int id, double h, int nrhs, float 
     float scale = 1.0f;
     long long nt = A.nt, ns = A.ns;
     int D = A.D, nr = nrhs;
-    void *args[] = {(void *)&A.tpts, (void *)&A.chunks, (void *)&nt,    (void *)&A.spts,
-                    (void *)&A.sig,  (void *)&A.soff,   (void *)&ns,    (void *)&D,
-                    (void *)&kern,   (void *)&scale,    (void *)&nr,    (void *)&phi};
-    return cudaLaunchKernel((const void *)(nrhs > 1 ? k.p2p_multi : k.p2p), dim3((unsigned)A.nchunks),
-                            dim3(kP2PThreads), args, 0, s);
+    void *args[] = {(void *)&A.tpts, (void *)&A.chunks,  (void *)&nt,    (void *)&A.spts,
+                    (void *)(nrhs > 1 ? &A.sig_rows : &A.sig), (void *)&A.soff,
+                    (void *)&ns,     (void *)&D,        (void *)&kern,  (void *)&scale,
+                    (void *)&nr,     (void *)&phi};
+    if (nrhs == 1)
+        return cudaLaunchKernel((const void *)k.p2p, dim3((unsigned)A.nchunks), dim3(kP2PThreads), args, 0, s);
+    return cudaLaunchKernel((const void *)k.p2p_multi, dim3((unsigned)A.nchunks), dim3(gemm_threads(kGemmT)), args, 0,
+                            s);
 }
 
 } // namespace bbfmm
