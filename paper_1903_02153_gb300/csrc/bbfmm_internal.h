@@ -324,7 +324,7 @@ void fft_active_tiles(int D, const std::vector<uint8_t> &leaf_occ, std::vector<i
 int64_t fft_grid_boxes(int l); // boxes of the zero-padded M^ grid of level l
 // m2l_tc.cu: every level of the far field in one go (FP32 or tensor cores)
 cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s);
-int m2l_groups_for(int D, int nrhs, int precision, int r, int64_t active_tiles);
+int m2l_groups_for(int D, int nrhs, int precision, int r, const int *ntiles, const std::vector<int> &rl);
 // the tensor-core M2L tiles that hold at least one occupied target box, level
 // by level from D down to 2, as {tx, ty, tz, octant}; count[l] per level
 void m2l_active_tiles(int D, int precision, const std::vector<uint8_t> &leaf_occ, std::vector<int4> &tiles,

@@ -461,7 +461,7 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
         PTRY(plan_alloc(P, (void **)&P->m2l_tiles, sizeof(int4) * tiles.size(), false, s));
         CUDA_TRY(cudaMemcpyAsync(P->m2l_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s));
     }
-    P->m2l_groups = m2l_groups_for(D, R, P->precision, P->ops->r, (int64_t)tiles.size());
+    P->m2l_groups = m2l_groups_for(D, R, P->precision, P->ops->r, P->m2l_ntiles, P->ops->rl);
     for (int l = 2; l <= D; ++l) {
         Level &L = P->lev[l];
         int64_t nb = 1LL << (3 * l), H = 1LL << (l - 1);

@@ -91,6 +91,14 @@ void split_tf32(const float *in, float *hi, float *lo, int64_t n)
 // K elements per pipeline stage: 32 (one 128-byte TF32 row, or one 64-byte
 // FP16 / BF16 row in the 64-byte swizzle)
 constexpr int kKChunk = 32;
+// K elements per stage of the 16-bit forms: 32 (64-byte rows, 64-byte
+// swizzle) or 64 (128-byte rows, 128-byte swizzle: half the TMA rows per byte)
+#ifndef BBFMM_TC_K16
+#define BBFMM_TC_K16 32
+#endif
+constexpr int kKChunk16 = BBFMM_TC_K16;
+static_assert(kKChunk16 == 32 || kKChunk16 == 64, "16-bit K chunk is 32 or 64 elements");
+__host__ __device__ constexpr int kchunk_of(int fmt) { return fmt == 0 ? kKChunk : kKChunk16; }
 #ifndef BBFMM_TC_MAX_STAGES
 #define BBFMM_TC_MAX_STAGES 8
 #endif
@@ -103,7 +111,20 @@ constexpr int kTile16 = BBFMM_TC_TILE16;
 static_assert(kTile16 == 128 || kTile16 == 256, "16-bit tile is 128 or 256 targets");
 
 // ---------------------------------------------------------------------------
-__constant__ int4 c_tab_tc[8][kOffsetsPerClass];
+// Work entries of an octant class: a group of offsets that share a source
+// octant and (ux, uy) and differ in uz.  The entry's sources are one box load
+// of bz + zspan slabs; offset j of the entry reads it from slab d_j, so one
+// load serves up to kMaxOps operators.  Table 0: one offset per entry (189);
+// table 1: grouped (72 entries).  Encoding: x = op0 | op1 << 10 | op2 << 20,
+// y = source octant | nops << 3 | zspan << 5, z = (ux + 1) | (uy + 1) << 2 |
+// (uz_min + 1) << 4, w = d0 | d1 << 2 | d2 << 4.
+constexpr int kMaxOps = 3;
+constexpr int kEntries16 = 72; // grouped entries per class
+#ifndef BBFMM_TC_GROUP
+#define BBFMM_TC_GROUP 1
+#endif
+constexpr bool kGroupEntries = BBFMM_TC_GROUP != 0; // 16-bit forms: group the offsets that share sources
+__constant__ int4 c_ent_tc[2][8][kOffsetsPerClass];
 
 constexpr int kMaxTcLevels = 8;
 constexpr int kMaxBuf = 8;
@@ -117,17 +138,23 @@ struct TcLevel {
     int r, nk, ktail, nh;     // rank of the level's operators, K chunks, K steps of the last chunk, row halves
     uint32_t idesc;           // instruction descriptor (N of this level)
     uint32_t a_load, b_load;  // bytes of the operator rows loaded / of the sources (one piece, one chunk)
+    uint32_t b_load2;         // sources of a grouped entry: bz + 2 slabs
+    uint32_t slab16;          // one slab of sources (bx by rows) in descriptor units (16 bytes)
+    int E, grp;               // entries per class and entry table of this level
+    int64_t pair_base;        // first (tile, entry) pair of the level
     float scale;
 };
 
 struct TcLaunch {
     CUtensorMap src[kMaxTcLevels], srclo[kMaxTcLevels]; // M~ (hi, lo) of each level
+    CUtensorMap src2[kMaxTcLevels], srclo2[kMaxTcLevels]; // the same with bz + 2 slabs (grouped entries)
     CUtensorMap op[kMaxTcLevels], oplo[kMaxTcLevels];   // C (hi, lo) of each operator level
     TcLevel lev[kMaxTcLevels];
     float bscale_inv[kMaxTcLevels]; // 1 / (scale of the 16-bit operators), per operator level
     const float *ascale;            // 16-bit forms: scale of M~ per tree level (device)
     int nlev, ntiles;               // levels; tiles of all levels
-    int64_t total, per_cta;         // (tile, offset) pairs; pairs per CTA
+    int64_t total, per_cta;         // (tile, entry) pairs; pairs per CTA
+    int maxops;                     // operator tiles per stage
     int *status;
     int rp, nrhs, R, nstage;            // R: right-hand-side stride of M~ / F~ rows
     int nbuf, bcols, tcols;             // TMEM partial buffers, columns per accumulator, allocated
@@ -142,16 +169,16 @@ struct Item {
 __device__ __forceinline__ Item decode_segment(const TcLaunch &P, int64_t pos, int64_t end)
 {
     Item it;
-    const int t = (int)(pos / kOffsetsPerClass);
-    it.e0 = (int)(pos - (int64_t)t * kOffsetsPerClass);
-    it.e1 = (int)min((int64_t)kOffsetsPerClass, it.e0 + (end - pos));
-    it.g = (int)(pos / P.per_cta - ((int64_t)t * kOffsetsPerClass) / P.per_cta);
     int L = 0;
-    while (L + 1 < P.nlev && t >= P.lev[L + 1].tile_base)
+    while (L + 1 < P.nlev && pos >= P.lev[L + 1].pair_base)
         ++L;
     it.L = L;
     const TcLevel &lv = P.lev[L];
-    int u = t - lv.tile_base; // ((c nact) + tile) nh + h: the row halves of a tile run back to back
+    const int64_t rel = pos - lv.pair_base;
+    int u = (int)(rel / lv.E); // the level's tile: ((c nact) + tile) nh + h, the row halves back to back
+    it.e0 = (int)(rel - (int64_t)u * lv.E);
+    it.e1 = (int)min((int64_t)lv.E, it.e0 + (end - pos));
+    it.g = (int)(pos / P.per_cta - (lv.pair_base + (int64_t)u * lv.E) / P.per_cta);
     it.h = 0;
     if (lv.nh > 1) {
         it.h = u & 1;
@@ -174,8 +201,10 @@ template <int NPROD, int NACC, bool CF, int CH, int FMT>
 __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_constant__ TcLaunch P)
 {
     constexpr int KSTEP = FMT == 0 ? 8 : 16; // K elements per MMA (32 bytes)
-    constexpr int KMAX = kKChunk / KSTEP;     // MMAs per piece product and chunk
-    constexpr bool SW64 = FMT != 0;          // 64-byte rows
+    constexpr int KCH = kchunk_of(FMT);      // K elements per stage
+    constexpr int KMAX = KCH / KSTEP;        // MMAs per piece product and chunk
+    constexpr bool SW64 = FMT != 0 && KCH == 32; // 64-byte rows
+    constexpr int MAXOPS = FMT != 0 && kGroupEntries ? kMaxOps : 1; // operators per entry
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -224,12 +253,16 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
             pos += w.e1 - w.e0;
             const TcLevel &lv = P.lev[w.L];
             const int X0 = lv.bx * w.tx, Y0 = lv.by * w.ty, Z0 = lv.bz * w.tz;
-            const uint32_t tx_bytes = (NPROD == 3 ? 2u : 1u) * (lv.a_load + lv.b_load);
+            constexpr uint32_t npc = NPROD == 3 ? 2u : 1u; // pieces (hi, lo)
             const int row0 = 128 * w.h;
             for (int e = w.e0; e < w.e1 && !*abort_flag; ++e) {
-                const int4 en = c_tab_tc[w.ot][e];
+                const int4 en = c_ent_tc[lv.grp][w.ot][e];
+                const int nops = MAXOPS == 1 ? 1 : (en.y >> 3) & 3, zspan = en.y >> 5, soct = en.y & 7;
                 const int ux = (en.z & 3) - 1, uy = ((en.z >> 2) & 3) - 1, uz = ((en.z >> 4) & 3) - 1;
-                const int zq = en.y * (lv.H + 2) + 1 + Z0 + uz;
+                const int zq = soct * (lv.H + 2) + 1 + Z0 + uz;
+                const uint32_t tx_bytes = npc * ((uint32_t)nops * lv.a_load + (zspan ? lv.b_load2 : lv.b_load));
+                const CUtensorMap *bm = zspan ? &P.src2[w.L] : &P.src[w.L];
+                const CUtensorMap *bml = zspan ? &P.srclo2[w.L] : &P.srclo[w.L];
                 for (int kc = 0; kc < lv.nk; ++kc) {
                     if (!mbar_wait(empty0 + 8 * s, round ^ 1, abort_flag))
                         break;
@@ -237,13 +270,20 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
                     const uint32_t fb = full0 + 8 * s;
                     mbar_arrive_expect_tx(fb, tx_bytes);
                     last_round[s] = round;
-                    const uint32_t sb = sa + (NPROD == 3 ? 2u : 1u) * P.a_bytes;
-                    tma_load_3d(sa, &P.op[lv.opl], fb, kKChunk * kc, row0, en.x);
-                    tma_load_5d(sb, &P.src[w.L], fb, kKChunk * kc, w.c, X0 + ux, Y0 + uy, zq);
-                    if (NPROD == 3) {
-                        tma_load_3d(sa + P.a_bytes, &P.oplo[lv.opl], fb, kKChunk * kc, row0, en.x);
-                        tma_load_5d(sb + P.b_bytes, &P.srclo[w.L], fb, kKChunk * kc, w.c, X0 + ux, Y0 + uy, zq);
-                    }
+                    // stage: [op 0 hi, lo][op 1 hi, lo]... (maxops slots) [sources hi][lo]
+                    const uint32_t sb = sa + npc * (uint32_t)P.maxops * P.a_bytes;
+#pragma unroll
+                    for (int j = 0; j < MAXOPS; ++j)
+                        if (MAXOPS == 1 || j < nops) {
+                            const int opi = (en.x >> (10 * j)) & 1023;
+                            const uint32_t aj = sa + npc * (uint32_t)j * P.a_bytes;
+                            tma_load_3d(aj, &P.op[lv.opl], fb, KCH * kc, row0, opi);
+                            if (NPROD == 3)
+                                tma_load_3d(aj + P.a_bytes, &P.oplo[lv.opl], fb, KCH * kc, row0, opi);
+                        }
+                    tma_load_5d(sb, bm, fb, KCH * kc, w.c, X0 + ux, Y0 + uy, zq);
+                    if (NPROD == 3)
+                        tma_load_5d(sb + P.b_bytes, bml, fb, KCH * kc, w.c, X0 + ux, Y0 + uy, zq);
                     if (++s == S) {
                         s = 0;
                         round ^= 1;
@@ -264,9 +304,11 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
         // ring positions are counters (no division), the descriptors of a
         // stage are the stage-0 descriptors plus a constant, the K steps of a
         // chunk are unrolled.
-        const uint32_t b_off = (NPROD == 3 ? 2 : 1) * P.a_bytes;
+        constexpr uint32_t npc = NPROD == 3 ? 2u : 1u;
+        const uint32_t b_off = npc * (uint32_t)P.maxops * P.a_bytes;
         const uint64_t d0 = SW64 ? sw64_desc(base) : sw128_desc(base);
-        const uint32_t d_al = P.a_bytes >> 4, d_bh = b_off >> 4, d_bl = (b_off + P.b_bytes) >> 4;
+        const uint32_t d_al = P.a_bytes >> 4, d_aop = (npc * P.a_bytes) >> 4; // lo piece; next operator
+        const uint32_t d_bh = b_off >> 4, d_bl = (b_off + P.b_bytes) >> 4;
         const uint32_t d_st = P.stage_bytes >> 4;
         int s = 0, sph = 0, pb = 0, pph = 0; // stage ring and partial-buffer ring (position, phase)
         bool ok = true;
@@ -278,6 +320,13 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
             const uint32_t idesc = lv.idesc;
             const int nk = lv.nk, ktail = lv.ktail;
             for (int e = w.e0; e < w.e1 && ok; ++e) {
+                const int4 en = c_ent_tc[lv.grp][w.ot][e];
+                const int nops = MAXOPS == 1 ? 1 : (en.y >> 3) & 3;
+                // source slab of operator j within the entry's box load
+                uint32_t sh[MAXOPS];
+#pragma unroll
+                for (int j = 0; j < MAXOPS; ++j)
+                    sh[j] = MAXOPS == 1 ? 0u : (uint32_t)((en.w >> (2 * j)) & 3) * lv.slab16;
                 if (!mbar_wait(pempty0 + 8 * pb, pph ^ 1, abort_flag)) {
                     ok = false;
                     break;
@@ -292,8 +341,8 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
                         break;
                     }
                     tc_fence_after();
-                    const uint64_t ah = d0 + (uint64_t)(s * d_st); // C (operator) pieces
-                    const uint64_t al = ah + d_al, bh = ah + d_bh, bl = ah + d_bl; // sources
+                    const uint64_t sbase = d0 + (uint64_t)(s * d_st);
+                    const uint64_t bh0 = sbase + d_bh, bl0 = sbase + d_bl; // sources (hi, lo)
                     const int ks = kc + 1 < nk ? KMAX : ktail;
                     auto issue = [&](uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
                         if (FMT == 0)
@@ -301,32 +350,53 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
                         else
                             mma_f16(d, a, b, idesc, acc);
                     };
+                    // the entry's operators one after the other, all into the
+                    // entry's partial accumulator; operator j reads the
+                    // sources from its slab
                     if (NPROD == 3 && (NACC == 2 || CF)) {
 #pragma unroll
-                        for (int k = 0; k < KMAX; ++k)
-                            if (k < ks) {
-                                const uint64_t dk = (uint64_t)(2 * k); // 32 bytes >> 4
-                                issue(dc, ah + dk, bl + dk, acc_c);
-                                issue(dc, al + dk, bh + dk, 1u);
-                                acc_c = 1u;
-                                if (NACC == 1)
-                                    acc_h = 1u;
+                        for (int j = 0; j < MAXOPS; ++j)
+                            if (MAXOPS == 1 || j < nops) {
+                                const uint64_t ah = sbase + (uint64_t)(j * d_aop), al = ah + d_al;
+                                const uint64_t bh = bh0 + sh[j], bl = bl0 + sh[j];
+#pragma unroll
+                                for (int k = 0; k < KMAX; ++k)
+                                    if (k < ks) {
+                                        const uint64_t dk = (uint64_t)(2 * k); // 32 bytes >> 4
+                                        issue(dc, ah + dk, bl + dk, acc_c);
+                                        issue(dc, al + dk, bh + dk, 1u);
+                                        acc_c = 1u;
+                                        if (NACC == 1)
+                                            acc_h = 1u;
+                                    }
                             }
                     }
 #pragma unroll
-                    for (int k = 0; k < KMAX; ++k)
-                        if (k < ks) {
-                            const uint64_t dk = (uint64_t)(2 * k);
-                            issue(dh, ah + dk, bh + dk, acc_h);
-                            acc_h = 1u;
+                    for (int j = 0; j < MAXOPS; ++j)
+                        if (MAXOPS == 1 || j < nops) {
+                            const uint64_t ah = sbase + (uint64_t)(j * d_aop);
+                            const uint64_t bh = bh0 + sh[j];
+#pragma unroll
+                            for (int k = 0; k < KMAX; ++k)
+                                if (k < ks) {
+                                    const uint64_t dk = (uint64_t)(2 * k);
+                                    issue(dh, ah + dk, bh + dk, acc_h);
+                                    acc_h = 1u;
+                                }
                         }
                     if (NPROD == 3 && NACC == 1 && !CF) {
 #pragma unroll
-                        for (int k = 0; k < KMAX; ++k)
-                            if (k < ks) {
-                                const uint64_t dk = (uint64_t)(2 * k);
-                                issue(dh, ah + dk, bl + dk, 1u);
-                                issue(dh, al + dk, bh + dk, 1u);
+                        for (int j = 0; j < MAXOPS; ++j)
+                            if (MAXOPS == 1 || j < nops) {
+                                const uint64_t ah = sbase + (uint64_t)(j * d_aop), al = ah + d_al;
+                                const uint64_t bh = bh0 + sh[j], bl = bl0 + sh[j];
+#pragma unroll
+                                for (int k = 0; k < KMAX; ++k)
+                                    if (k < ks) {
+                                        const uint64_t dk = (uint64_t)(2 * k);
+                                        issue(dh, ah + dk, bl + dk, 1u);
+                                        issue(dh, al + dk, bh + dk, 1u);
+                                    }
                             }
                     }
                     mma_commit(empty0 + 8 * s); // frees the stage once these MMAs have read it
@@ -461,10 +531,54 @@ static cudaError_t tc_init()
         g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
     if (!g_tab_tc_ready) {
-        int4 tab[8][kOffsetsPerClass];
+        static int4 tab[8][kOffsetsPerClass];
         if (!fill_m2l_table(tab))
             return cudaErrorInvalidValue;
-        cudaError_t e = cudaMemcpyToSymbol(c_tab_tc, tab, sizeof(tab));
+        static int4 ent[2][8][kOffsetsPerClass];
+        memset(ent, 0, sizeof(ent));
+        for (int o = 0; o < 8; ++o) {
+            // table 0: one offset per entry
+            for (int k = 0; k < kOffsetsPerClass; ++k) {
+                const int4 t = tab[o][k];
+                ent[0][o][k] = make_int4(t.x, t.y | (1 << 3), t.z, 0);
+            }
+            // table 1: offsets grouped by (source octant, ux, uy), uz ascending
+            int n = 0, covered = 0;
+            for (int q = 0; q < 8; ++q)
+                for (int uy = -1; uy <= 1; ++uy)
+                    for (int ux = -1; ux <= 1; ++ux) {
+                        int ops[3], uzs[3], m = 0;
+                        for (int uz = -1; uz <= 1; ++uz)
+                            for (int k = 0; k < kOffsetsPerClass; ++k) {
+                                const int4 t = tab[o][k];
+                                if (t.y == q && (t.z & 3) - 1 == ux && ((t.z >> 2) & 3) - 1 == uy &&
+                                    ((t.z >> 4) & 3) - 1 == uz) {
+                                    if (m >= kMaxOps)
+                                        return cudaErrorInvalidValue;
+                                    ops[m] = t.x;
+                                    uzs[m++] = uz;
+                                }
+                            }
+                        if (m == 0)
+                            continue;
+                        const int uzmin = uzs[0], zspan = uzs[m - 1] - uzs[0];
+                        if (zspan != 0 && zspan != 2 && !(zspan == 1 && m == 2))
+                            return cudaErrorInvalidValue;
+                        int x = 0, wv = 0;
+                        for (int j = 0; j < m; ++j) {
+                            x |= ops[j] << (10 * j);
+                            wv |= (uzs[j] - uzmin) << (2 * j);
+                        }
+                        // the box load always covers bz + 2 slabs when the group spans z
+                        const int span = zspan > 0 ? 2 : 0;
+                        ent[1][o][n++] = make_int4(x, q | (m << 3) | (span << 5),
+                                                   (ux + 1) | ((uy + 1) << 2) | ((uzmin + 1) << 4), wv);
+                        covered += m;
+                    }
+            if (covered != kOffsetsPerClass || n != kEntries16)
+                return cudaErrorInvalidValue;
+        }
+        cudaError_t e = cudaMemcpyToSymbol(c_ent_tc, ent, sizeof(ent));
         if (e != cudaSuccess)
             return e;
         g_tab_tc_ready = true;
@@ -492,10 +606,11 @@ static cudaError_t encode_src(CUtensorMap *tm, const void *ptr, int H, int R, in
     cuuint64_t dims[5] = {(cuuint64_t)rp, (cuuint64_t)R, (cuuint64_t)H, (cuuint64_t)H, (cuuint64_t)8 * (H + 2)};
     cuuint64_t strides[4] = {(cuuint64_t)rp * es_b, (cuuint64_t)R * rp * es_b, (cuuint64_t)H * R * rp * es_b,
                              (cuuint64_t)H * H * R * rp * es_b};
-    cuuint32_t box[5] = {(cuuint32_t)kKChunk, 1, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+    const int kch = kchunk_of(fmt);
+    cuuint32_t box[5] = {(cuuint32_t)kch, 1, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
     cuuint32_t es[5] = {1, 1, 1, 1, 1};
     CUresult r = g_encode(tm, tm_type(fmt), 5, (void *)ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          fmt == 0 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                          kch * es_b == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -506,17 +621,18 @@ static cudaError_t encode_op(CUtensorMap *tm, const void *ptr, int rp, int rows6
     const cuuint64_t es_b = fmt == 0 ? 4 : 2;
     cuuint64_t dims[3] = {(cuuint64_t)rp, (cuuint64_t)rows64, (cuuint64_t)kNumOffsets};
     cuuint64_t strides[2] = {(cuuint64_t)rp * es_b, (cuuint64_t)rows64 * rp * es_b};
-    cuuint32_t box[3] = {(cuuint32_t)kKChunk, (cuuint32_t)nb, 1};
+    const int kch = kchunk_of(fmt);
+    cuuint32_t box[3] = {(cuuint32_t)kch, (cuuint32_t)nb, 1};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = g_encode(tm, tm_type(fmt), 3, (void *)ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          fmt == 0 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                          kch * es_b == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 // tile of a level with H parent cells per axis, for a largest tile of nt
-// targets: (8, 4, nt / 32) on the fine levels, the whole class (padded in z
-// to 16 targets) on the coarse ones
+// targets: (8, 4, nt / 32) on the fine levels, the whole class on the coarse
+// ones (padded in y to 16 targets on level 2)
 static void tile_of(int H, int nt, int &bx, int &by, int &bz)
 {
     if (H >= 8) {
@@ -526,8 +642,11 @@ static void tile_of(int H, int nt, int &bx, int &by, int &bz)
     } else if (H == 4) {
         bx = by = bz = 4;
     } else {
-        bx = by = H;
-        bz = 16 / (H * H);
+        // H = 2: 2 x 4 x 2 parent cells (y padded), 16 targets; a z slab is
+        // 8 rows, one swizzle atom, so the level's offsets can be grouped
+        bx = 2;
+        by = 4;
+        bz = 2;
     }
 }
 
@@ -584,13 +703,36 @@ void m2l_active_tiles(int D, int precision, const std::vector<uint8_t> &leaf_occ
 // slices of F~ per level: 2 when the (active) tiles outnumber the SMs (every
 // CTA's range is then at least one tile long, so a tile meets at most one
 // range boundary), else 4 (ranges of at least 63 offsets)
-int m2l_groups_for(int D, int nrhs, int precision, int r, int64_t active_tiles)
+// grouped entries on a level: 16-bit forms, a slab of whole 8-row swizzle
+// atoms, and sources of bz + 2 slabs within the stage's source buffer
+static bool level_grouped(int H, int nt, int fmt)
+{
+    int bx, by, bz;
+    tile_of(H, nt, bx, by, bz);
+    return fmt != 0 && kGroupEntries && (bx * by) % 8 == 0 && bx * by * bz + 2 * bx * by <= nt + 64;
+}
+
+// slices of F~ per level: enough that, with equal ranges of (tile, entry)
+// pairs over the SMs, a tile meets at most G - 1 range boundaries
+int m2l_groups_for(int D, int nrhs, int precision, int r, const int *ntiles, const std::vector<int> &rl)
 {
     if (precision == BBFMM_PREC_FP32 || D < 2 || r > 256)
         return 1;
     if (tc_init() != cudaSuccess)
         return 1;
-    return active_tiles * nrhs >= g_num_sms ? 2 : 4;
+    const int fmt = precision == BBFMM_PREC_FP16X3 ? 1 : precision == BBFMM_PREC_BF16X3 ? 2 : 0;
+    const int nt = tile_targets(precision);
+    int64_t pairs = 0;
+    int emax = 1;
+    for (int l = 2; l <= D; ++l) {
+        const int E = level_grouped(1 << (l - 1), nt, fmt) ? kEntries16 : kOffsetsPerClass;
+        const int rk = rl.empty() ? r : rl[rl.size() == 1 ? 0 : l - 2];
+        pairs += (int64_t)ntiles[l] * nrhs * (rk > 128 ? 2 : 1) * E;
+        emax = std::max(emax, E);
+    }
+    const int64_t per_cta = std::max<int64_t>(1, (pairs + g_num_sms - 1) / g_num_sms);
+    const int64_t need = 1 + (emax + per_cta - 1) / per_cta;
+    return (int)std::max<int64_t>(2, std::min<int64_t>(8, need));
 }
 
 template <int NPROD, int NACC, bool CF, int CH, int FMT>
@@ -641,7 +783,8 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
     // operand format: 0 = TF32 (1 or 3 passes), 1 = FP16 x3, 2 = BF16 x3
     const int fmt = P->precision == BBFMM_PREC_FP16X3 ? 1 : P->precision == BBFMM_PREC_BF16X3 ? 2 : 0;
     const bool three = P->precision != BBFMM_PREC_TF32;
-    const int elem = fmt == 0 ? 4 : 2, rowb = kKChunk * elem, kstep = fmt == 0 ? 8 : 16;
+    const int kch = kchunk_of(fmt);
+    const int elem = fmt == 0 ? 4 : 2, rowb = kch * elem, kstep = fmt == 0 ? 8 : 16;
     const int nt = tile_targets(P->precision);
     if (O.rp % 16 != 0 || P->D - 1 > kMaxTcLevels || (int)O.rl.size() != O.nlev)
         return cudaErrorInvalidValue;
@@ -662,9 +805,13 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
     L.nrhs = nrhs;
     L.R = P->max_nrhs;
 
+    // grouped entries (16-bit forms): a stage holds up to kMaxOps operator
+    // tiles and sources of bz + 2 slabs (2 slabs = 64 rows on the fine levels)
+    const bool group = fmt != 0 && kGroupEntries;
+    L.maxops = group ? kMaxOps : 1;
     L.a_bytes = 128 * rowb; // C tile: 128 rows in shared memory, nbk of them loaded
-    L.b_bytes = (uint32_t)nt * rowb; // sources: up to nt rows
-    L.stage_bytes = (three ? 2 : 1) * (L.a_bytes + L.b_bytes);
+    L.b_bytes = (uint32_t)(nt + (group ? 64 : 0)) * rowb; // sources
+    L.stage_bytes = (three ? 2 : 1) * ((uint32_t)L.maxops * L.a_bytes + L.b_bytes);
     L.ascale = P->a16_scale;
     // TMEM: one accumulator of nt columns per partial buffer; two per buffer
     // (hi*hi and corrections apart) when two double-buffered pairs still fit
@@ -682,7 +829,8 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
     L.nstage = nstage;
     const size_t smem = 1024 + (size_t)nstage * L.stage_bytes + 512; // + barriers and TMEM slot
     // levels, finest first
-    int tiles = 0;
+    int tiles = 0, emax = 0;
+    int64_t pairs = 0;
     L.nlev = 0;
     for (int l = P->D; l >= 2; --l) {
         TcLevel &lv = L.lev[L.nlev];
@@ -699,8 +847,8 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
         lv.opl = O.nlev == 1 ? 0 : l - 2;
         lv.r = O.rl[lv.opl];
         lv.nh = lv.r > 128 ? 2 : 1;
-        lv.nk = (lv.r + kKChunk - 1) / kKChunk;
-        lv.ktail = (lv.r - kKChunk * (lv.nk - 1) + kstep - 1) / kstep;
+        lv.nk = (lv.r + kch - 1) / kch;
+        lv.ktail = (lv.r - kch * (lv.nk - 1) + kstep - 1) / kstep;
         lv.a_load = (uint32_t)nbk[lv.opl] * rowb;
         lv.ntiles = lv.nact * nrhs * lv.nh;
         lv.tile_base = tiles;
@@ -708,6 +856,15 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
         lv.scale = scale_of(l);
         lv.idesc = fmt == 0 ? idesc_tf32(128, lv.n) : idesc_f16(128, lv.n, fmt == 2 ? 1 : 0);
         lv.b_load = (uint32_t)lv.n * rowb;
+        // a slab shift must keep the swizzle phase: whole 8-row atoms
+        const uint32_t slab_bytes = (uint32_t)(lv.bx * lv.by) * rowb;
+        lv.grp = group && level_grouped(H, nt, fmt) ? 1 : 0;
+        lv.E = lv.grp ? kEntries16 : kOffsetsPerClass;
+        lv.slab16 = slab_bytes >> 4;
+        lv.b_load2 = (uint32_t)(lv.n + 2 * lv.bx * lv.by) * rowb;
+        lv.pair_base = pairs;
+        pairs += (int64_t)lv.ntiles * lv.E;
+        emax = std::max(emax, lv.E);
         tiles += lv.ntiles;
         const void *A, *Alo;
         if (fmt != 0) {
@@ -720,16 +877,20 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
         e = encode_src(&L.src[L.nlev], A, H, P->max_nrhs, O.rp, fmt, lv.bx, lv.by, lv.bz);
         if (e == cudaSuccess)
             e = encode_src(&L.srclo[L.nlev], Alo, H, P->max_nrhs, O.rp, fmt, lv.bx, lv.by, lv.bz);
+        if (e == cudaSuccess && lv.grp)
+            e = encode_src(&L.src2[L.nlev], A, H, P->max_nrhs, O.rp, fmt, lv.bx, lv.by, lv.bz + 2);
+        if (e == cudaSuccess && lv.grp)
+            e = encode_src(&L.srclo2[L.nlev], Alo, H, P->max_nrhs, O.rp, fmt, lv.bx, lv.by, lv.bz + 2);
         if (e != cudaSuccess)
             return e;
         L.nlev++;
     }
-    // equal ranges of (tile, offset) pairs; a range is long enough that no
+    // equal ranges of (tile, entry) pairs; a range is long enough that no
     // tile meets more than G - 1 range boundaries (G = slices allocated)
     const int G = P->m2l_groups;
     L.ntiles = tiles;
-    L.total = (int64_t)tiles * kOffsetsPerClass;
-    const int64_t min_len = G >= 2 ? (kOffsetsPerClass + G - 2) / (G - 1) : L.total;
+    L.total = pairs;
+    const int64_t min_len = G >= 2 ? (emax + G - 2) / (G - 1) : L.total;
     L.per_cta = (L.total + g_num_sms - 1) / g_num_sms;
     if (L.per_cta < min_len)
         L.per_cta = min_len;
