@@ -239,7 +239,7 @@ def time_plan(bb, torch, dev, pts, sig_dev, c, depth, precision, eps, flush, str
 
 # DRAM bytes (read + write) of one k_m2l_tc launch, from the ncu capture in
 # profiles/m2l_tc_fp16x3_uniform1M_d5.md; valid for the kernel as captured
-M2L_TRAFFIC = {("uniform-1M-p5-d5", "fp16x3"): 28400640 + 815616}
+M2L_TRAFFIC = {("uniform-1M-p5-d5", "fp16x3"): 28387072 + 660224}
 
 
 def roofline(precision, info, nrhs, m2l_ms, clocks, torch, dev, workload=None, interp="chebyshev", p=5):

@@ -134,8 +134,8 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
           int D, Kern kern, float scale, int nrhs, float *__restrict__ phi)
 {
     constexpr int NPK = kTPT / 2; // packed target pairs per thread
-    __shared__ float4 stage_xy[kStageSrc]; // (x, x, y, y)
-    __shared__ float4 stage_zs[kStageSrc]; // (z, z, sigma, sigma)
+    // staged sources: [j] = (x, x, y, y), [kStageSrc + j] = (z, z, sigma, sigma)
+    __shared__ float4 stage[2 * kStageSrc];
     __shared__ int nb_start[28], nb_pre[28];
     __shared__ float4 nb_delta[27];
     __shared__ float2 red[NPK][kP2PThreads];
@@ -209,15 +209,15 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
                 const float s = sg[src];
                 // staged negated so that x_target - y' is one packed add
                 const float x = -(u.x + d.x), y = -(u.y + d.y), z = -(u.z + d.z);
-                stage_xy[g] = make_float4(x, x, y, y);
-                stage_zs[g] = make_float4(z, z, s, s);
+                stage[g] = make_float4(x, x, y, y);
+                stage[kStageSrc + g] = make_float4(z, z, s, s);
             }
             __syncthreads();
             if (active) {
-                // one source against the thread's NPK target pairs
-                auto visit = [&](auto own, int j, float2 *a) {
-                    const float4 qa = stage_xy[j];
-                    const float4 qb = stage_zs[j];
+                // one source (at p) against the thread's NPK target pairs
+                auto visit = [&](auto own, const float4 *p, float2 *a) {
+                    const float4 qa = p[0];
+                    const float4 qb = p[kStageSrc];
 #pragma unroll
                     for (int pk = 0; pk < NPK; ++pk) {
                         const float2 dx = __fadd2_rn(X[pk], make_float2(qa.x, qa.y));
@@ -226,24 +226,25 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
                         float2 r2 = decltype(own)::value ? __fmul2_rn(dx, dx) : __ffma2_rn(dx, dx, floor2);
                         r2 = __ffma2_rn(dy, dy, r2);
                         r2 = __ffma2_rn(dz, dz, r2);
-                        a[pk] = __ffma2_rn(kern2<decltype(own)::value>(kern, r2, dx, dy, dz),
-                                           make_float2(qb.z, qb.w), a[pk]);
+                        const float2 K = kern2<decltype(own)::value>(kern, r2, dx, dy, dz);
+                        a[pk] = __ffma2_rn(K, make_float2(qb.z, qb.w), a[pk]);
                     }
                 };
-                // the own leaf's sources (staged first) with the r = 0 test
-                const int cown = min(cnt, max(0, nown - base));
-                int j = slice;
-                for (; j < cown; j += S)
-                    visit(OwnLeaf{}, j, acc);
+                // the own leaf's sources (staged first) with the r = 0 test;
+                // the thread walks its sources with one pointer
+                const float4 *p = stage + slice;
+                const float4 *const pown = stage + min(cnt, max(0, nown - base)), *const pend = stage + cnt;
+                for (; p < pown; p += S)
+                    visit(OwnLeaf{}, p, acc);
                 // two sources per iteration into two accumulator sets (shorter
                 // dependency chains), added in a fixed order at the end
 #pragma unroll 2
-                for (; j + S < cnt; j += 2 * S) {
-                    visit(FarLeaf{}, j, acc);
-                    visit(FarLeaf{}, j + S, acc2);
+                for (; p + S < pend; p += 2 * S) {
+                    visit(FarLeaf{}, p, acc);
+                    visit(FarLeaf{}, p + S, acc2);
                 }
-                if (j < cnt)
-                    visit(FarLeaf{}, j, acc);
+                if (p < pend)
+                    visit(FarLeaf{}, p, acc);
             }
             __syncthreads();
         }
