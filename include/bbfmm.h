@@ -60,6 +60,12 @@ extern "C" {
                                     frequency a 189-term sum over the interaction list,
                                     an inverse DFT per box; FP32; no compression */
 
+/* near-field evaluation order (Sec. 2.5, symmetry of the kernel) */
+#define BBFMM_NEAR_AUTO 0    /* symmetric kernel, targets = sources, one right-hand
+                                side: each pair of neighbour leaves is evaluated once
+                                and used both ways (default); otherwise as ORDERED */
+#define BBFMM_NEAR_ORDERED 1 /* every target leaf evaluates all its neighbour pairs */
+
 /* arithmetic of the M2L stage (every other stage computes in FP32) */
 #define BBFMM_PREC_FP32 0   /* FP32 FMA on the CUDA cores */
 #define BBFMM_PREC_TF32 1   /* tensor cores, one TF32 pass, FP32 accumulation */
@@ -93,7 +99,10 @@ typedef struct {
                               the passes' on-chip memory and are not allocated */
     int interp;        /* BBFMM_INTERP_* (default CHEBYSHEV); UNIFORM takes
                           precision = BBFMM_PREC_FP32 and ignores svd_eps */
-    int reserved[3];   /* zero */
+    int near_mode;     /* BBFMM_NEAR_* (default AUTO).  AUTO holds 13 floats per
+                          point more (the two-way column sums); both orders are
+                          deterministic, and they differ by FP32 rounding */
+    int reserved[2];   /* zero */
 } bbfmm_opts;
 
 typedef struct {
@@ -111,7 +120,8 @@ typedef struct {
     int64_t p2p_pairs;  /* near-field kernel evaluations per right-hand side */
     int64_t m2l_pairs;  /* M2L translations per right-hand side (dense grid) */
     int64_t n_targets;  /* targets (= n unless built by bbfmm_plan_targets) */
-    int reserved[6];
+    int near_symmetric; /* 1: one-RHS matvecs evaluate each neighbour leaf pair once */
+    int reserved[5];
 } bbfmm_info;
 
 /*

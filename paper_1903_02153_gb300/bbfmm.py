@@ -25,6 +25,7 @@ BBFMM_K_TEST_POLY, BBFMM_K_TEST_CONST = 100, 101
 BBFMM_PREC_FP32, BBFMM_PREC_TF32, BBFMM_PREC_TF32X3, BBFMM_PREC_BF16X3, BBFMM_PREC_FP16X3 = 0, 1, 2, 3, 4
 
 INTERPS = {"chebyshev": 0, "uniform": 1}   # BBFMM_INTERP_*
+NEAR_MODES = {"auto": 0, "ordered": 1}      # BBFMM_NEAR_*
 BBFMM_K_USER_FIRST = 1000                   # ids of kernels from bbfmm_kernel_register
 
 PRECISIONS = {"fp32": BBFMM_PREC_FP32, "tf32": BBFMM_PREC_TF32, "tf32x3": BBFMM_PREC_TF32X3,
@@ -42,7 +43,7 @@ class bbfmm_opts(ctypes.Structure):
                 ("lo", ctypes.c_double * 3), ("side", ctypes.c_double),
                 ("max_nrhs", ctypes.c_int), ("split_accumulate", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("keep_coefficients", ctypes.c_int),
-                ("interp", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("interp", ctypes.c_int), ("near_mode", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class bbfmm_info(ctypes.Structure):
@@ -51,7 +52,8 @@ class bbfmm_info(ctypes.Structure):
                 ("max_nrhs", ctypes.c_int), ("lo", ctypes.c_double * 3), ("side", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("nonempty_leaves", ctypes.c_int64),
                 ("max_leaf_points", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64),
-                ("m2l_pairs", ctypes.c_int64), ("n_targets", ctypes.c_int64), ("reserved", ctypes.c_int * 6)]
+                ("m2l_pairs", ctypes.c_int64), ("n_targets", ctypes.c_int64), ("near_symmetric", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class BBFMMError(RuntimeError):
@@ -270,13 +272,14 @@ class Plan:
 
     def __init__(self, points, kernel, order, depth, ell=1.0, svd_eps=1e-7, precision="fp32",
                  domain=None, max_nrhs=1, stream=None, split_accumulate=True, use_graph=True,
-                 keep_coefficients=False, targets=None, interp="chebyshev"):
+                 keep_coefficients=False, targets=None, interp="chebyshev", near_mode="auto"):
         import torch
         o = bbfmm_default_opts()
         o.split_accumulate = 1 if split_accumulate else 0
         o.use_graph = 1 if use_graph else 0
         o.keep_coefficients = 1 if keep_coefficients else 0
         o.interp = INTERPS[interp] if isinstance(interp, str) else int(interp)
+        o.near_mode = NEAR_MODES[near_mode] if isinstance(near_mode, str) else int(near_mode)
         o.ell = float(ell)
         o.svd_eps = float(svd_eps)
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)

@@ -40,6 +40,7 @@ constexpr int kMaxDepth = 8;
 constexpr int kNumOffsets = 316;      // 7^3 - 3^3 distinct M2L offsets (Sec. 2.2, Thm. 2.1)
 constexpr int kOffsetsPerClass = 189; // 6^3 - 3^3 interaction-list boxes (Def. 2.1)
 constexpr int kChunk = 128;           // near-field targets per work item (one block)
+constexpr int kSymSlotsHost = 13;     // two-way column sums per point (symmetric near field)
 
 // status word bits written by device-side checks
 constexpr int kStatusBounds = 1;
@@ -102,6 +103,7 @@ std::shared_ptr<HostOps> build_host_ops(int kernel, double ell, int p, double ep
                                         double side, int interp, std::string &err);
 double kernel_value_host(int kernel, double ell, double d0, double d1, double d2);
 int kernel_homogeneity(int kernel); // m of K(a x, a y) = a^m K(x, y), 0 if none
+bool kernel_symmetric(int kernel);  // K(x, y) = K(y, x)
 
 // user_kernel.cu: kernels registered through bbfmm_kernel_register
 int user_kernel_register(const char *source, int homogeneity, int symmetric, int *id, std::string &err);
@@ -190,6 +192,8 @@ struct bbfmm_plan_impl {
     Level lev[kMaxDepth + 1];
     float *sigma_s = nullptr, *phi_far = nullptr, *phi_near = nullptr;
     float *sigma_rows = nullptr;                  // max_nrhs > 1: sigma_s row-major, for the near field
+    bool near_sym = false;                        // near field evaluated pairwise both ways (one RHS)
+    float *near_slots = nullptr;                  // symmetric near field: 13 x n column sums (zeroed at plan time)
     float *io_sigma = nullptr, *io_phi = nullptr; // staging for host sigma / phi
     int *status = nullptr;                        // device status word
     // 16-bit split M2L: per level max |M~| (float bits) and the power-of-two
@@ -302,7 +306,7 @@ cudaError_t launch_gram(const float *A, const float *B, int64_t n, int m, double
                         cudaStream_t s);
 // out (n x mo) = Y (n x m) T (m x mo), all column-major; out must not alias Y
 cudaError_t launch_rmul(const float *Y, int64_t n, int m, const float *T, int mo, float *out, cudaStream_t s);
-cudaError_t launch_combine(const float *phi_far, const float *phi_near, const int *perm, int64_t n,
+cudaError_t launch_combine(const float *phi_far, const float *phi_near, const float *slots, const int *perm, int64_t n,
                            int nrhs, float *phi, cudaStream_t s);
 // entry points of the two kernels whose pointer arguments (the caller's sigma
 // and phi) change from call to call of a captured matvec graph
@@ -343,6 +347,7 @@ struct P2PArgs {
     const int *soff;
     int64_t ns;
     int D;
+    float *slots; // non-null: symmetric near field (one RHS), 13 x ns two-way column sums
 };
 cudaError_t launch_p2p(const P2PArgs &A, int kernel, double ell, double h, int nrhs, float *phi_near,
                        cudaStream_t s);

@@ -512,6 +512,8 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
         PTRY(plan_alloc(P, (void **)&P->sigma_rows, 4 * n * R, false, s));
     PTRY(plan_alloc(P, (void **)&P->phi_far, 4 * nt * R, false, s));
     PTRY(plan_alloc(P, (void **)&P->phi_near, 4 * nt * R, false, s));
+    if (P->near_sym) // slots nobody writes stay zero for the plan's lifetime
+        PTRY(plan_alloc(P, (void **)&P->near_slots, 4 * (int64_t)kSymSlotsHost * n, true, s));
     PTRY(plan_alloc(P, (void **)&P->status, 16, true, s));
 
     // constant tables the matvec kernels read, uploaded before any capture
@@ -585,6 +587,7 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
     if (tm)
         CUDA_TRY(cudaEventRecord(P->ev[Stage::Start], s));
     float *rows = nrhs > 1 ? P->sigma_rows : nullptr;
+    float *slots = nrhs == 1 ? P->near_slots : nullptr;
     CUDA_TRY(launch_gather_sigma(sigma, P->perm, n, nrhs, P->sigma_s, rows, s));
     if (tm)
         CUDA_TRY(cudaEventRecord(P->ev[Stage::Gather], s));
@@ -597,7 +600,8 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
         CUDA_TRY(cudaStreamWaitEvent(P->side_stream, after, 0));
         if (tm)
             CUDA_TRY(cudaEventRecord(P->ev_p2p0, P->side_stream));
-        const P2PArgs pa = {P->tpts, P->chunks, P->nchunks, nt, P->pts, P->sigma_s, rows, P->leaf_off, n, D};
+        const P2PArgs pa = {P->tpts, P->chunks,   P->nchunks, nt, P->pts, P->sigma_s,
+                            rows,    P->leaf_off, n,          D,  slots};
         CUDA_TRY(launch_p2p(pa, P->kernel, P->ell, P->side / (double)(1LL << D), nrhs, P->phi_near,
                             P->side_stream));
         if (tm)
@@ -657,7 +661,7 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
     CUDA_TRY(cudaStreamWaitEvent(s, P->ev_join, 0));
     if (tm)
         CUDA_TRY(cudaEventRecord(P->ev[Stage::P2P], s));
-    CUDA_TRY(launch_combine(D >= 2 ? P->phi_far : nullptr, P->phi_near, P->tperm, nt, nrhs, phi, s));
+    CUDA_TRY(launch_combine(D >= 2 ? P->phi_far : nullptr, P->phi_near, slots, P->tperm, nt, nrhs, phi, s));
     if (tm)
         CUDA_TRY(cudaEventRecord(P->ev[Stage::Combine], s));
     P->last_nrhs = nrhs;
@@ -725,8 +729,9 @@ static int matvec_graph(bbfmm_plan_impl *P, const float *sigma, float *phi, int 
     float *rows = nrhs > 1 ? P->sigma_rows : nullptr;
     void *gargs[] = {(void *)&sigma, (void *)&P->perm, (void *)&n, (void *)&nrhs, (void *)&P->sigma_s,
                      (void *)&rows};
-    void *cargs[] = {(void *)&far, (void *)&P->phi_near, (void *)&P->tperm, (void *)&nt, (void *)&nrhs,
-                     (void *)&phi};
+    const float *slots = nrhs == 1 ? P->near_slots : nullptr;
+    void *cargs[] = {(void *)&far,  (void *)&P->phi_near, (void *)&slots, (void *)&P->tperm,
+                     (void *)&nt,   (void *)&nrhs,        (void *)&phi};
     cudaKernelNodeParams gp = g.gp, cp = g.cp;
     gp.kernelParams = gargs;
     gp.extra = nullptr;
@@ -808,6 +813,8 @@ static int plan_create(const double *points, int64_t n, const double *targets, i
         return fail(BBFMM_EINVAL, "unknown precision %d", opts.precision);
     if (opts.interp != BBFMM_INTERP_CHEBYSHEV && opts.interp != BBFMM_INTERP_UNIFORM)
         return fail(BBFMM_EINVAL, "unknown interp %d", opts.interp);
+    if (opts.near_mode != BBFMM_NEAR_AUTO && opts.near_mode != BBFMM_NEAR_ORDERED)
+        return fail(BBFMM_EINVAL, "unknown near_mode %d", opts.near_mode);
     if (opts.interp == BBFMM_INTERP_UNIFORM && opts.precision != BBFMM_PREC_FP32)
         return fail(BBFMM_EINVAL, "equally spaced nodes run the Fourier-domain M2L in FP32 (precision must be "
                                   "BBFMM_PREC_FP32)");
@@ -855,6 +862,10 @@ static int plan_create(const double *points, int64_t n, const double *targets, i
     P->use_graph = opts.use_graph != 0;
     P->keep_coeffs = opts.keep_coefficients != 0;
     P->nodeset = opts.interp;
+    // the symmetric near field needs K(x, y) = K(y, x) and one point set; the
+    // run-time compiled kernels keep the ordered form
+    P->near_sym = opts.near_mode == BBFMM_NEAR_AUTO && !targets && kernel_id < BBFMM_K_USER_FIRST &&
+                  kernel_symmetric(kernel_id);
     if (opts.domain_given) {
         for (int d = 0; d < 3; ++d)
             P->lo[d] = opts.lo[d];
@@ -1070,6 +1081,7 @@ int bbfmm_plan_info(bbfmm_plan_t plan, bbfmm_info *info)
     memset(info, 0, sizeof(*info));
     info->n = plan->n;
     info->n_targets = plan->nt;
+    info->near_symmetric = plan->near_sym ? 1 : 0;
     info->depth = plan->D;
     info->order = plan->p;
     info->rank = plan->ops ? plan->ops->r : 0;

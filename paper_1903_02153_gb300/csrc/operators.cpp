@@ -70,7 +70,7 @@ int kernel_homogeneity(int kernel)
     return 0;
 }
 
-static bool symmetric_kernel(int kernel)
+bool kernel_symmetric(int kernel)
 {
     int h = 0, sym = 0;
     if (kernel >= BBFMM_K_USER_FIRST && user_kernel_traits(kernel, &h, &sym))
@@ -231,7 +231,7 @@ static bool build_level(HostOps &o, double h, std::vector<double> &U, std::vecto
     for (int i = 0; i < p3; ++i)
         for (int j = 0; j < i; ++j)
             GU[(size_t)j * p3 + i] = GU[(size_t)i * p3 + j];
-    bool sym = symmetric_kernel(o.kernel);
+    bool sym = kernel_symmetric(o.kernel);
     if (!sym) {
         GV.assign((size_t)p3 * p3, 0.0);
 #pragma omp parallel for schedule(dynamic)

@@ -7,13 +7,17 @@
 namespace bbfmm {
 
 static_assert(kP2PChunk == kChunk, "near-field work items");
+static_assert(kSymSlots == kSymSlotsHost, "slots of the symmetric near field");
 
 template <class Kern>
 static cudaError_t p2p_launch(const P2PArgs &A, Kern k, float scale, int nrhs, float *phi, cudaStream_t s)
 {
     if (A.nchunks <= 0)
         return cudaSuccess;
-    if (nrhs > 1) {
+    if (nrhs == 1 && A.slots) {
+        k_p2p_sym<Kern><<<A.nchunks, kP2PThreads, 0, s>>>(A.spts, A.chunks, A.ns, A.sig, A.soff, A.D, k, scale, phi,
+                                                           A.slots);
+    } else if (nrhs > 1) {
         k_p2p_gemm<Kern, kGemmT><<<A.nchunks, gemm_threads(kGemmT), 0, s>>>(
             A.tpts, A.chunks, A.nt, A.spts, A.sig_rows, A.soff, A.ns, A.D, k, scale, nrhs, phi);
     } else {

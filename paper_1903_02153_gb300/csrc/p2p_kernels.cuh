@@ -273,6 +273,226 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
     }
 }
 
+// Symmetric near field (K(d) = K(-d), the targets are the sources, one
+// right-hand side).  K(x_i, y_j) = K(x_j, y_i), so a pair of neighbour leaves
+// needs its kernel values once (the paper's remark on symmetry, Sec. 2.5):
+// the work item of leaf alpha takes
+//   - its own leaf, one way (rows of alpha only, r = 0 test);
+//   - the 13 "forward" neighbours beta = alpha + d (nid > 13 in the 3x3x3
+//     numbering): both ways when alpha is one work item -- rows of alpha in
+//     registers, and for every source of beta the column sum
+//     sum_t K(x_t, y_j) sigma_t over alpha's targets, which goes to slot
+//     26 - nid of that point (the nid under which beta sees alpha);
+//   - a backward neighbour (nid < 13) only when that leaf is split into
+//     several work items: such a leaf writes no slots (its items would
+//     collide), so both sides then take their own rows of the pair.
+// Each (slot, point) is written by one work item and never by two, and the
+// combine adds the 13 slots in a fixed order after the point's own rows:
+// the result does not depend on scheduling.  Slots no work item writes (the
+// backward neighbour is absent, empty or split) stay at the zero they were
+// given when the plan was made.
+//
+// Column sums: the thread of target group q visiting source j stores its
+// partial sum over its kTPT targets in colpart[q][j]; after the pass one
+// thread per source adds the nq partials in order.
+constexpr int kSymSlots = 13;
+struct OneWay {
+    static constexpr bool value = false;
+};
+struct TwoWay {
+    static constexpr bool value = true;
+};
+constexpr int kSymStage = 256; // staged sources per pass
+constexpr int kColBuf = 2048;  // column partials per pass (nq x pass length)
+
+template <class Kern>
+__global__ void __launch_bounds__(kP2PThreads, 8)
+    k_p2p_sym(const float4 *__restrict__ pts, const int4 *__restrict__ chunks, long long n,
+              const float *__restrict__ sig, const int *__restrict__ off, int D, Kern kern, float scale,
+              float *__restrict__ phi, float *__restrict__ slots)
+{
+    constexpr int NPK = kTPT / 2;
+    // staged sources: [j] = (x, x, y, y), [kSymStage + j] = (z, z, sigma, sigma)
+    __shared__ float4 stage[2 * kSymStage];
+    __shared__ float colpart[kColBuf];
+    __shared__ int sSrc[kSymStage];            // point index of a staged source
+    __shared__ unsigned char sSlot[kSymStage]; // its slot (symmetric segment only)
+    __shared__ int nb_start[28], nb_pre[28], nb_cnt[28], nb_slot[28];
+    __shared__ float4 nb_delta[27];
+    __shared__ float2 red[NPK][kP2PThreads];
+    __shared__ int s_nsym0;
+    const int tid = threadIdx.x;
+    const int4 ch = chunks[blockIdx.x];
+    const int nt = ch.z;
+    const int nq = (nt + kTPT - 1) / kTPT;
+    const int S = kP2PThreads / nq;
+    const int t = tid % nq, slice = tid / nq;
+    const bool active = slice < S;
+    const bool whole = off[ch.x + 1] - off[ch.x] <= kP2PChunk; // alpha is one work item
+    int ax, ay, az;
+    demorton3((unsigned)ch.x, ax, ay, az);
+    const int nside = 1 << D;
+
+    // neighbour leaves in staging order: own (key 0), one way (key 1), both
+    // ways (key 2); key 3 is not visited
+    if (tid < 32) {
+        int cnt = 0, start = 0, key = 3;
+        float4 dl = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (tid < 27) {
+            const int dx = tid % 3 - 1, dy = (tid / 3) % 3 - 1, dz = tid / 9 - 1;
+            const int bx = ax + dx, by = ay + dy, bz = az + dz;
+            if (bx >= 0 && by >= 0 && bz >= 0 && bx < nside && by < nside && bz < nside) {
+                const unsigned nm = morton3((unsigned)bx, (unsigned)by, (unsigned)bz);
+                start = off[nm];
+                cnt = off[nm + 1] - start;
+            }
+            if (cnt > 0)
+                key = tid == 13 ? 0 : tid > 13 ? (whole ? 2 : 1) : (cnt > kP2PChunk ? 1 : 3);
+            dl = make_float4((float)dx, (float)dy, (float)dz, 0.0f);
+        }
+        const unsigned lt = (1u << tid) - 1u;
+        const unsigned m0 = __ballot_sync(0xffffffffu, key == 0), m1 = __ballot_sync(0xffffffffu, key == 1),
+                       m2 = __ballot_sync(0xffffffffu, key == 2);
+        const int n0 = __popc(m0), n1 = __popc(m1), nst = n0 + n1 + __popc(m2);
+        const int rank = key == 0   ? __popc(m0 & lt)
+                         : key == 1 ? n0 + __popc(m1 & lt)
+                         : key == 2 ? n0 + n1 + __popc(m2 & lt)
+                                    : -1;
+        if (rank >= 0) {
+            nb_start[rank] = start;
+            nb_cnt[rank] = cnt;
+            nb_delta[rank] = dl;
+            nb_slot[rank] = 26 - tid;
+        }
+        __syncwarp();
+        const int c = tid < nst ? nb_cnt[tid] : 0;
+        int incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (tid >= o)
+                incl += v;
+        }
+        if (tid < 28)
+            nb_pre[tid] = incl - c;
+        const int sym0 = __shfl_sync(0xffffffffu, incl - c, n0 + n1); // first position of key 2
+        if (tid == 0)
+            s_nsym0 = sym0;
+    }
+    __syncthreads();
+    const int ns = nb_pre[27], nown = nb_pre[1], nsym0 = s_nsym0;
+    float2 X[NPK], Y[NPK], Z[NPK], SG[NPK];
+#pragma unroll
+    for (int pk = 0; pk < NPK; ++pk) {
+        const int i0 = t + 2 * pk * nq, i1 = i0 + nq;
+        const bool h0 = active && i0 < nt, h1 = active && i1 < nt;
+        const float4 xa = pts[ch.y + (h0 ? i0 : 0)];
+        const float4 xb = pts[ch.y + (h1 ? i1 : 0)];
+        X[pk] = make_float2(xa.x, xb.x);
+        Y[pk] = make_float2(xa.y, xb.y);
+        Z[pk] = make_float2(xa.z, xb.z);
+        // a missing target (a duplicate of target t) adds nothing to the columns
+        SG[pk] = make_float2(h0 ? sig[ch.y + i0] : 0.0f, h1 ? sig[ch.y + i1] : 0.0f);
+    }
+    const float2 floor2 = make_float2(kR2Floor, kR2Floor);
+    const int PL = min(kSymStage, kColBuf / nq); // pass length
+
+    float2 acc[NPK], acc2[NPK];
+#pragma unroll
+    for (int pk = 0; pk < NPK; ++pk)
+        acc[pk] = acc2[pk] = make_float2(0.0f, 0.0f);
+    for (int base = 0; base < ns; base += PL) {
+        const int cnt = min(PL, ns - base);
+        int k = 0;
+        for (int g = tid; g < cnt; g += kP2PThreads) {
+            const int gg = base + g;
+            while (nb_pre[k + 1] <= gg)
+                ++k;
+            const int src = nb_start[k] + (gg - nb_pre[k]);
+            const float4 u = pts[src];
+            const float4 d = nb_delta[k];
+            const float s = sig[src];
+            const float x = -(u.x + d.x), y = -(u.y + d.y), z = -(u.z + d.z);
+            stage[g] = make_float4(x, x, y, y);
+            stage[kSymStage + g] = make_float4(z, z, s, s);
+            if (gg >= nsym0) {
+                sSrc[g] = src;
+                sSlot[g] = (unsigned char)nb_slot[k];
+            }
+        }
+        __syncthreads();
+        if (active) {
+            // one source (at p) against the thread's targets: rows into a;
+            // two ways, also the source's column partial over those targets
+            auto visit = [&](auto own, auto two, const float4 *p, float2 *a, float *col) {
+                const float4 qa = p[0];
+                const float4 qb = p[kSymStage];
+                float2 cs = make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int pk = 0; pk < NPK; ++pk) {
+                    const float2 dx = __fadd2_rn(X[pk], make_float2(qa.x, qa.y));
+                    const float2 dy = __fadd2_rn(Y[pk], make_float2(qa.z, qa.w));
+                    const float2 dz = __fadd2_rn(Z[pk], make_float2(qb.x, qb.y));
+                    float2 r2 = decltype(own)::value ? __fmul2_rn(dx, dx) : __ffma2_rn(dx, dx, floor2);
+                    r2 = __ffma2_rn(dy, dy, r2);
+                    r2 = __ffma2_rn(dz, dz, r2);
+                    const float2 K = kern2<decltype(own)::value>(kern, r2, dx, dy, dz);
+                    a[pk] = __ffma2_rn(K, make_float2(qb.z, qb.w), a[pk]);
+                    if (decltype(two)::value)
+                        cs = __ffma2_rn(K, SG[pk], cs);
+                }
+                if (decltype(two)::value)
+                    *col = cs.x + cs.y;
+            };
+            const float4 *p = stage + slice;
+            const float4 *const pown = stage + min(cnt, max(0, nown - base));
+            const float4 *const psym = stage + min(cnt, max(0, nsym0 - base)), *const pend = stage + cnt;
+            for (; p < pown; p += S)
+                visit(OwnLeaf{}, OneWay{}, p, acc, nullptr);
+#pragma unroll 2
+            for (; p + S < psym; p += 2 * S) {
+                visit(FarLeaf{}, OneWay{}, p, acc, nullptr);
+                visit(FarLeaf{}, OneWay{}, p + S, acc2, nullptr);
+            }
+            if (p < psym) {
+                visit(FarLeaf{}, OneWay{}, p, acc, nullptr);
+                p += S;
+            }
+            float *const colq = colpart + t * PL;
+            for (; p < pend; p += S)
+                visit(FarLeaf{}, TwoWay{}, p, acc2, colq + (p - stage));
+        }
+        __syncthreads();
+        // column sums of this pass's two-way sources, in target-group order
+        for (int g = max(0, nsym0 - base) + tid; g < cnt; g += kP2PThreads) {
+            float v = 0.0f;
+            for (int q = 0; q < nq; ++q)
+                v += colpart[q * PL + g];
+            slots[(long long)sSlot[g] * n + sSrc[g]] = scale * v;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int pk = 0; pk < NPK; ++pk)
+        red[pk][tid] = active ? make_float2(acc[pk].x + acc2[pk].x, acc[pk].y + acc2[pk].y) : make_float2(0.0f, 0.0f);
+    __syncthreads();
+    if (tid < nq) {
+#pragma unroll
+        for (int pk = 0; pk < NPK; ++pk) {
+            float sa = 0.0f, sb = 0.0f;
+            for (int q = 0; q < S; ++q) {
+                const float2 v = red[pk][tid + q * nq];
+                sa += v.x;
+                sb += v.y;
+            }
+            const int i0 = tid + 2 * pk * nq, i1 = i0 + nq;
+            if (i0 < nt)
+                phi[ch.y + i0] = scale * sa;
+            if (i1 < nt)
+                phi[ch.y + i1] = scale * sb;
+        }
+    }
+}
+
 // Several right-hand sides (Sec. 2.5 "Multiple right-hand-sides"): the near
 // field of a work item is a product of its kernel matrix (targets x
 // neighbourhood sources) with the weights (sources x nrhs, read row-major).  The block walks

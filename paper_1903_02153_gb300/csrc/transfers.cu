@@ -100,8 +100,11 @@ cudaError_t launch_split16_levels(const Split16Args &A, cudaStream_t s)
 }
 
 // ---------------------------------------------------------------------------
+// slots (symmetric near field, one RHS): the 13 column sums a point receives
+// from its backward neighbour leaves, added in slot order
 __global__ void k_combine(const float *__restrict__ far, const float *__restrict__ near,
-                          const int *__restrict__ perm, int64_t n, int nrhs, float *__restrict__ phi)
+                          const float *__restrict__ slots, const int *__restrict__ perm, int64_t n, int nrhs,
+                          float *__restrict__ phi)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n)
@@ -109,6 +112,9 @@ __global__ void k_combine(const float *__restrict__ far, const float *__restrict
     int j = perm[i];
     for (int c = 0; c < nrhs; ++c) {
         float v = near[(int64_t)c * n + i];
+        if (slots)
+            for (int q = 0; q < 13; ++q)
+                v += slots[q * n + i];
         if (far)
             v += far[(int64_t)c * n + i];
         phi[(int64_t)c * n + j] = v;
@@ -117,10 +123,10 @@ __global__ void k_combine(const float *__restrict__ far, const float *__restrict
 
 const void *combine_kernel() { return (const void *)k_combine; }
 
-cudaError_t launch_combine(const float *phi_far, const float *phi_near, const int *perm, int64_t n, int nrhs,
-                           float *phi, cudaStream_t s)
+cudaError_t launch_combine(const float *phi_far, const float *phi_near, const float *slots, const int *perm,
+                           int64_t n, int nrhs, float *phi, cudaStream_t s)
 {
-    k_combine<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(phi_far, phi_near, perm, n, nrhs, phi);
+    k_combine<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(phi_far, phi_near, slots, perm, n, nrhs, phi);
     return cudaGetLastError();
 }
 

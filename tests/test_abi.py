@@ -125,3 +125,15 @@ def test_unknown_user_kernel_id_is_rejected(lib):
     kid = ctypes.c_int(0)
     assert lib.lib().bbfmm_kernel_register(None, 0, 0, ctypes.byref(kid)) == lib.BBFMM_EINVAL
     assert lib.lib().bbfmm_kernel_register(b"x", 9, 0, ctypes.byref(kid)) == lib.BBFMM_EINVAL
+
+
+def test_plan_rejects_bad_near_mode(lib):
+    """near_mode must be AUTO or ORDERED: EINVAL before any device call."""
+    pts = np.random.default_rng(4).random((10, 3))
+    h = ctypes.c_void_p()
+    for mode in (2, -1, 7):
+        o = lib.bbfmm_default_opts()
+        o.near_mode = mode
+        assert lib.lib().bbfmm_plan(pts.ctypes.data, 10, 1, 4, 3, ctypes.byref(o), None,
+                                    ctypes.byref(h)) == lib.BBFMM_EINVAL, mode
+        assert "near_mode" in lib.bbfmm_last_error()
