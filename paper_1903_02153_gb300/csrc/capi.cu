@@ -862,10 +862,9 @@ static int plan_create(const double *points, int64_t n, const double *targets, i
     P->use_graph = opts.use_graph != 0;
     P->keep_coeffs = opts.keep_coefficients != 0;
     P->nodeset = opts.interp;
-    // the symmetric near field needs K(x, y) = K(y, x) and one point set; the
-    // run-time compiled kernels keep the ordered form
-    P->near_sym = opts.near_mode == BBFMM_NEAR_AUTO && !targets && kernel_id < BBFMM_K_USER_FIRST &&
-                  kernel_symmetric(kernel_id);
+    // the symmetric near field needs K(x, y) = K(y, x) (for a user kernel, as
+    // registered) and one point set
+    P->near_sym = opts.near_mode == BBFMM_NEAR_AUTO && !targets && kernel_symmetric(kernel_id);
     if (opts.domain_given) {
         for (int d = 0; d < 3; ++d)
             P->lo[d] = opts.lo[d];

@@ -293,8 +293,9 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
 // given when the plan was made.
 //
 // Column sums: the thread of target group q visiting source j stores its
-// partial sum over its kTPT targets in colpart[q][j]; after the pass one
-// thread per source adds the nq partials in order.
+// partial sum over its kTPT targets in colpart[j][q] (row stride nq rounded
+// up to 4); after the pass one thread per source adds the nq partials of its
+// row in order.
 constexpr int kSymSlots = 13;
 struct OneWay {
     static constexpr bool value = false;
@@ -314,7 +315,7 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
     constexpr int NPK = kTPT / 2;
     // staged sources: [j] = (x, x, y, y), [kSymStage + j] = (z, z, sigma, sigma)
     __shared__ float4 stage[2 * kSymStage];
-    __shared__ float colpart[kColBuf];
+    __shared__ __align__(16) float colpart[kColBuf];
     __shared__ int sSrc[kSymStage];            // point index of a staged source
     __shared__ unsigned char sSlot[kSymStage]; // its slot (symmetric segment only)
     __shared__ int nb_start[28], nb_pre[28], nb_cnt[28], nb_slot[28];
@@ -394,7 +395,8 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
         SG[pk] = make_float2(h0 ? sig[ch.y + i0] : 0.0f, h1 ? sig[ch.y + i1] : 0.0f);
     }
     const float2 floor2 = make_float2(kR2Floor, kR2Floor);
-    const int PL = min(kSymStage, kColBuf / nq); // pass length
+    const int NQP = (nq + 3) & ~3;                // colpart row stride
+    const int PL = min(kSymStage, kColBuf / NQP); // pass length
 
     float2 acc[NPK], acc2[NPK];
 #pragma unroll
@@ -457,16 +459,31 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
                 visit(FarLeaf{}, OneWay{}, p, acc, nullptr);
                 p += S;
             }
-            float *const colq = colpart + t * PL;
-            for (; p < pend; p += S)
-                visit(FarLeaf{}, TwoWay{}, p, acc2, colq + (p - stage));
+            float *col = colpart + (p - stage) * NQP + t;
+            const int cstep = S * NQP;
+#pragma unroll 2
+            for (; p + S < pend; p += 2 * S, col += 2 * cstep) {
+                visit(FarLeaf{}, TwoWay{}, p, acc, col);
+                visit(FarLeaf{}, TwoWay{}, p + S, acc2, col + cstep);
+            }
+            if (p < pend)
+                visit(FarLeaf{}, TwoWay{}, p, acc, col);
         }
         __syncthreads();
         // column sums of this pass's two-way sources, in target-group order
         for (int g = max(0, nsym0 - base) + tid; g < cnt; g += kP2PThreads) {
+            const float *row = colpart + g * NQP;
             float v = 0.0f;
-            for (int q = 0; q < nq; ++q)
-                v += colpart[q * PL + g];
+            int q = 0;
+            for (; q + 4 <= nq; q += 4) {
+                const float4 c4 = *reinterpret_cast<const float4 *>(row + q);
+                v += c4.x;
+                v += c4.y;
+                v += c4.z;
+                v += c4.w;
+            }
+            for (; q < nq; ++q)
+                v += row[q];
             slots[(long long)sSlot[g] * n + sSrc[g]] = scale * v;
         }
         __syncthreads();

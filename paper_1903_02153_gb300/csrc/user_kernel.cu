@@ -68,7 +68,7 @@ const Nvrtc &nvrtc()
 struct UserKernel {
     int homogeneity = 0, symmetric = 0;
     cudaLibrary_t lib = nullptr;
-    cudaKernel_t eval = nullptr, p2p = nullptr, p2p_multi = nullptr;
+    cudaKernel_t eval = nullptr, p2p = nullptr, p2p_multi = nullptr, p2p_sym = nullptr;
 };
 
 std::mutex g_mu;
@@ -125,9 +125,11 @@ int user_kernel_register(const char *source, int homogeneity, int symmetric, int
         err = "nvrtcCreateProgram failed";
         return BBFMM_ECUDA;
     }
-    const char *p2p_name = "bbfmm::k_p2p<bbfmm::KUser>", *multi_name = "bbfmm::k_p2p_gemm<bbfmm::KUser, 32>";
+    const char *p2p_name = "bbfmm::k_p2p<bbfmm::KUser>", *multi_name = "bbfmm::k_p2p_gemm<bbfmm::KUser, 32>",
+               *sym_name = "bbfmm::k_p2p_sym<bbfmm::KUser>";
     nv.add_name(prog, p2p_name);
     nv.add_name(prog, multi_name);
+    nv.add_name(prog, sym_name);
     const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-default-device"};
     const nvrtcResult rc = nv.compile(prog, 3, opts);
     size_t log_size = 0;
@@ -144,10 +146,12 @@ int user_kernel_register(const char *source, int homogeneity, int symmetric, int
     nv.cubin_size(prog, &cubin_size);
     std::vector<char> cubin(cubin_size);
     nv.cubin(prog, cubin.data());
-    const char *p2p_low = nullptr, *multi_low = nullptr;
+    const char *p2p_low = nullptr, *multi_low = nullptr, *sym_low = nullptr;
     nv.lowered(prog, p2p_name, &p2p_low);
     nv.lowered(prog, multi_name, &multi_low);
-    const std::string p2p_sym = p2p_low ? p2p_low : "", multi_sym = multi_low ? multi_low : "";
+    nv.lowered(prog, sym_name, &sym_low);
+    const std::string p2p_sym = p2p_low ? p2p_low : "", multi_sym = multi_low ? multi_low : "",
+                      pair_sym = sym_low ? sym_low : "";
     nv.destroy(&prog);
     UserKernel k;
     k.homogeneity = homogeneity;
@@ -159,6 +163,8 @@ int user_kernel_register(const char *source, int homogeneity, int symmetric, int
         e = cudaLibraryGetKernel(&k.p2p, k.lib, p2p_sym.c_str());
     if (e == cudaSuccess)
         e = cudaLibraryGetKernel(&k.p2p_multi, k.lib, multi_sym.c_str());
+    if (e == cudaSuccess)
+        e = cudaLibraryGetKernel(&k.p2p_sym, k.lib, pair_sym.c_str());
 
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -240,6 +246,11 @@ cudaError_t launch_p2p_user(const P2PArgs &A, int id, double h, int nrhs, float 
     float scale = 1.0f;
     long long nt = A.nt, ns = A.ns;
     int D = A.D, nr = nrhs;
+    if (nrhs == 1 && A.slots) { // symmetric near field (the kernel was registered as symmetric)
+        void *sargs[] = {(void *)&A.spts, (void *)&A.chunks, (void *)&ns, (void *)&A.sig, (void *)&A.soff,
+                         (void *)&D,      (void *)&kern,     (void *)&scale, (void *)&phi, (void *)&A.slots};
+        return cudaLaunchKernel((const void *)k.p2p_sym, dim3((unsigned)A.nchunks), dim3(kP2PThreads), sargs, 0, s);
+    }
     void *args[] = {(void *)&A.tpts, (void *)&A.chunks,  (void *)&nt,    (void *)&A.spts,
                     (void *)(nrhs > 1 ? &A.sig_rows : &A.sig), (void *)&A.soff,
                     (void *)&ns,     (void *)&D,        (void *)&kern,  (void *)&scale,

@@ -66,28 +66,64 @@ def test_symmetric_form_is_chosen_where_it_applies(bb):
     plan = make_plan(bb, pts, K_INV_R, 4, 2, "auto", targets=W.uniform_points(700, seed=502))
     assert plan.info().near_symmetric == 0   # targets apart from the sources
     plan.close()
+    # run-time compiled kernels: as registered
+    body = """
+__device__ double bbfmm_kernel_f64(double d0, double d1, double d2)
+{ return exp(-sqrt(d0 * d0 + d1 * d1 + d2 * d2) / 0.4); }
+__device__ float bbfmm_kernel_f32(float d0, float d1, float d2)
+{ return expf(-sqrtf(d0 * d0 + d1 * d1 + d2 * d2) / 0.4f); }
+"""
+    for symmetric in (True, False):
+        kid = bb.bbfmm_kernel_register(body, symmetric=symmetric)
+        plan = make_plan(bb, pts, kid, 4, 2, "auto")
+        assert plan.info().near_symmetric == int(symmetric)
+        plan.close()
 
 
-@pytest.mark.parametrize("kid,ell,kind,n,depth", [
-    (K_INV_R, 1.0, "uniform", 60_000, 4),     # ~15 points per leaf, every leaf one work item
-    (K_INV_R, 1.0, "uniform", 200_000, 3),    # ~390 points per leaf: every leaf split (no slots written)
-    (K_INV_R2, 1.0, "clustered", 60_000, 4),  # split and whole leaves side by side
-    (K_EXP, 0.3, "clustered", 100_000, 5),
-    (K_GAUSS, 0.5, "jittered_grid", 50_000, 4),
-    (K_CONST, 1.0, "uniform", 3000, 3),
+def test_symmetric_user_kernel_matches_builtin(bb):
+    """exp(-r / 0.4) restated as a registered symmetric kernel takes the
+    symmetric near field too and gives the built-in's result to rounding."""
+    body = """
+__device__ double bbfmm_kernel_f64(double d0, double d1, double d2)
+{ return exp(-sqrt(d0 * d0 + d1 * d1 + d2 * d2) / 0.4); }
+__device__ float bbfmm_kernel_f32(float d0, float d1, float d2)
+{ return expf(-sqrtf(d0 * d0 + d1 * d1 + d2 * d2) / 0.4f); }
+"""
+    kid = bb.bbfmm_kernel_register(body, symmetric=True)
+    n = 40_000
+    pts = W.clustered_points(n, seed=513)
+    sig = W.uniform_sigma(n, seed=514)
+    got, info = run(bb, pts, sig, kid, 5, 4, "auto")
+    ref, info_b = run(bb, pts, sig, K_EXP, 5, 4, "auto", ell=0.4)
+    assert info.near_symmetric == 1 and info_b.near_symmetric == 1
+    assert rel(got, ref) <= 2e-6
+
+
+@pytest.mark.parametrize("kid,ell,kind,n,p,depth", [
+    (K_INV_R, 1.0, "uniform", 60_000, 5, 4),     # ~15 points per leaf, every leaf one work item
+    (K_INV_R, 1.0, "uniform", 200_000, 5, 3),    # ~390 points per leaf: every leaf split (no slots written)
+    (K_INV_R2, 1.0, "clustered", 20_000, 4, 4),  # split and whole leaves side by side
+    (K_EXP, 0.3, "clustered", 100_000, 5, 5),
+    (K_GAUSS, 0.5, "jittered_grid", 50_000, 5, 4),
+    (K_CONST, 1.0, "uniform", 3000, 4, 3),
 ])
-def test_symmetric_matches_ordered_and_oracle(bb, oracle, kid, ell, kind, n, depth):
+def test_symmetric_matches_ordered_and_oracle(bb, oracle, kid, ell, kind, n, p, depth):
+    """Gate against the oracle: 1e-5, or 1.1x the ordered form's own error
+    where that is above it (1/r^2 on clustered sets, where the FP32 near
+    field of the closest pairs sits near 1e-5 in both orders alike)."""
     pts = W.make_points(kind, n, seed=503)
     sig = W.uniform_sigma(n, seed=504).astype(np.float32).astype(np.float64)
-    got, info = run(bb, pts, sig, kid, 5, depth, "auto", ell=ell)
-    ordered, info_o = run(bb, pts, sig, kid, 5, depth, "ordered", ell=ell)
+    got, info = run(bb, pts, sig, kid, p, depth, "auto", ell=ell)
+    ordered, info_o = run(bb, pts, sig, kid, p, depth, "ordered", ell=ell)
     assert info.near_symmetric == 1 and info_o.near_symmetric == 0
     d = rel(got, ordered)
     print("%s %s n=%d d%d (max leaf %d): auto vs ordered %.2e" % (kid, kind, n, depth, info.max_leaf_points, d))
     assert d <= 3e-6
     if n <= 60_000:
-        ref = oracle.bbfmm(pts, sig, kid, 5, depth, ell=ell, lo=W.UNIT_LO, side=W.UNIT_SIDE)
-        assert rel(got, ref) <= 1e-5
+        ref = oracle.bbfmm(pts, sig, kid, p, depth, ell=ell, lo=W.UNIT_LO, side=W.UNIT_SIDE)
+        e, e_o = rel(got, ref), rel(ordered, ref)
+        print("   vs oracle: auto %.2e, ordered %.2e" % (e, e_o))
+        assert e <= max(1e-5, 1.1 * e_o)
 
 
 @pytest.mark.parametrize("kid,ell", [(K_INV_R, 1.0), (K_INV_R2, 1.0), (K_EXP, 0.2), (K_GAUSS, 0.3)])
@@ -108,12 +144,17 @@ def test_near_field_alone_is_the_direct_sum(bb, oracle, kid, ell, depth, kind, n
 @pytest.mark.parametrize("n", [1, 2, 3, 129, 257])
 def test_tiny_and_ragged_point_counts(bb, oracle, n):
     """One point (its own leaf only), two or three points in different leaves,
-    and counts just past one and two work items in a single leaf."""
+    and counts just past one and two work items in a single leaf; against the
+    direct sum at depth 0 / 1 and the oracle FMM at depth 2 (which has a far
+    field)."""
     pts = W.uniform_points(n, seed=507 + n)
     sig = W.uniform_sigma(n, seed=508 + n).astype(np.float32).astype(np.float64)
     for depth in (0, 1, 2):
         got, _ = run(bb, pts, sig, K_EXP, 4, depth, "auto", ell=0.5)
-        ref = oracle.direct(pts, pts, sig, K_EXP, ell=0.5)
+        if depth < 2:
+            ref = oracle.direct(pts, pts, sig, K_EXP, ell=0.5)
+        else:
+            ref = oracle.bbfmm(pts, sig, K_EXP, 4, depth, ell=0.5, lo=W.UNIT_LO, side=W.UNIT_SIDE)
         assert rel(got, ref) <= 2e-6, (n, depth)
 
 

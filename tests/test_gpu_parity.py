@@ -191,7 +191,9 @@ def test_multiple_rhs_columns_match_single(bb, oracle):
     both = gpu_matvec(bb, pts, sig, K_INV_R, 4, 3)
     for c in range(3):
         one = gpu_matvec(bb, pts, np.ascontiguousarray(sig[:, c]), K_INV_R, 4, 3)
-        np.testing.assert_allclose(both[:, c], one, rtol=0, atol=1e-6 * np.abs(one).max())
+        # one RHS takes the symmetric near field, several the ordered one: the
+        # same FP32 terms added in another order
+        np.testing.assert_allclose(both[:, c], one, rtol=0, atol=3e-6 * np.abs(one).max())
     ref = oracle_fmm(oracle, pts, sig, K_INV_R, 4, 3)
     assert oracle.rel_err(both, ref) <= 1e-5
 
