@@ -13,7 +13,7 @@ steps by writing a 512 MB buffer (the working set is smaller than L2).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                     [--workload NAME] [--precision fp16x3|tf32x3|bf16x3|tf32|fp32]
-                    [--interp chebyshev|uniform]
+                    [--interp chebyshev|uniform] [--near auto|ordered]
 
 Prints one JSON line (rank 0).  Under torchrun every rank runs an
 independent replica of the workload (the matvec is single-GPU: replicas
@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--interp", default="chebyshev", choices=["chebyshev", "uniform"],
                     help="uniform: equally spaced nodes with the Fourier-domain M2L (FP32)")
     ap.add_argument("--svd-eps", type=float, default=1e-6)
+    ap.add_argument("--near", default="auto", choices=["auto", "ordered"],
+                    help="near-field order: auto = each neighbour leaf pair once (symmetric kernels)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-depth6", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -215,10 +217,11 @@ def describe(c):
             % (c["name"], c["n"], c["kind"], KERNEL_NAMES[c["kernel"]], c["ell"], c["p"], c["depth"], c["nrhs"]))
 
 
-def time_plan(bb, torch, dev, pts, sig_dev, c, depth, precision, eps, flush, stream, nsteps=5, interp="chebyshev"):
+def time_plan(bb, torch, dev, pts, sig_dev, c, depth, precision, eps, flush, stream, nsteps=5, interp="chebyshev",
+              near="auto"):
     """Mean device time of nsteps matvecs (L2 flushed before each)."""
     plan = bb.Plan(torch.from_numpy(pts).to(dev), c["kernel"], c["p"], depth, ell=c["ell"], precision=precision,
-                   svd_eps=eps, domain=(W.UNIT_LO, W.UNIT_SIDE), max_nrhs=c["nrhs"], interp=interp)
+                   svd_eps=eps, domain=(W.UNIT_LO, W.UNIT_SIDE), max_nrhs=c["nrhs"], interp=interp, near_mode=near)
     phi = torch.empty_like(sig_dev)
     for _ in range(3):
         bb.bbfmm_matvec(plan.handle, sig_dev, phi, c["nrhs"], stream)
@@ -233,13 +236,13 @@ def time_plan(bb, torch, dev, pts, sig_dev, c, depth, precision, eps, flush, str
         ts.append(a.elapsed_time(b))
     plan.close()
     ms = float(np.mean(ts))
-    return {"depth": depth, "m2l_precision": precision, "ms_per_step": ms,
+    return {"depth": depth, "m2l_precision": precision, "near_field": near, "ms_per_step": ms,
             "value": float(c["n"]) ** 2 * c["nrhs"] / (ms / 1e3)}
 
 
 # DRAM bytes (read + write) of one k_m2l_tc launch, from the ncu capture in
 # profiles/m2l_tc_fp16x3_uniform1M_d5.md; valid for the kernel as captured
-M2L_TRAFFIC = {("uniform-1M-p5-d5", "fp16x3"): 28387072 + 660224}
+M2L_TRAFFIC = {("uniform-1M-p5-d5", "fp16x3"): 28392192 + 716288}
 
 
 def roofline(precision, info, nrhs, m2l_ms, clocks, torch, dev, workload=None, interp="chebyshev", p=5):
@@ -298,7 +301,8 @@ def run_ours(args, rank, world, local):
     c, pts, sig_host = workload(args.workload)
     n, nrhs, depth = c["n"], c["nrhs"], c["depth"]
     plan = bb.Plan(torch.from_numpy(pts).to(dev), c["kernel"], c["p"], depth, ell=c["ell"], precision=precision,
-                   svd_eps=args.svd_eps, domain=(W.UNIT_LO, W.UNIT_SIDE), max_nrhs=nrhs, interp=interp)
+                   svd_eps=args.svd_eps, domain=(W.UNIT_LO, W.UNIT_SIDE), max_nrhs=nrhs, interp=interp,
+                   near_mode=args.near)
     info = plan.info()
     sigma = torch.from_numpy(np.ascontiguousarray(sig_host.T)).to(dev)   # (nrhs, n): column-major n x nrhs
     phi = torch.empty_like(sigma)
@@ -370,9 +374,10 @@ def run_ours(args, rank, world, local):
     extra = {}
     if rank == 0 and not args.no_depth6 and args.workload == "uniform-1M-p5-d5":
         extra["depth6"] = time_plan(bb, torch, dev, pts, sigma, c, 6, precision, args.svd_eps, flush, stream,
-                                    interp=interp)
+                                    interp=interp, near=args.near)
     if rank == 0 and precision != "fp32" and not args.no_plain:
-        plain = time_plan(bb, torch, dev, pts, sigma, c, depth, "fp32", args.svd_eps, flush, stream)
+        # the plain form: FP32 M2L and the ordered near field
+        plain = time_plan(bb, torch, dev, pts, sigma, c, depth, "fp32", args.svd_eps, flush, stream, near="ordered")
         plain["speedup_of_this_form"] = plain["ms_per_step"] / ms
         extra["plain_fp32_form"] = plain
 
@@ -389,6 +394,7 @@ def run_ours(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": describe(c), "n": n, "kernel": KERNEL_NAMES[c["kernel"]], "ell": c["ell"],
                    "p": c["p"], "depth": depth, "nrhs": nrhs, "interp": interp, "m2l_precision": precision,
+                   "near_field": "symmetric pairs" if info.near_symmetric else "ordered",
                    "svd_rank": info.rank,
                    "svd_eps": args.svd_eps, "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": "replicas"},
