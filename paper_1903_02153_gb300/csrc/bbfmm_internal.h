@@ -193,7 +193,8 @@ struct bbfmm_plan_impl {
     float *sigma_s = nullptr, *phi_far = nullptr, *phi_near = nullptr;
     float *sigma_rows = nullptr;                  // max_nrhs > 1: sigma_s row-major, for the near field
     bool near_sym = false;                        // near field evaluated pairwise both ways (one RHS)
-    float *near_slots = nullptr;                  // symmetric near field: 13 x n column sums (zeroed at plan time)
+    float *near_slots = nullptr;
+    float *Ftop = nullptr;                        // depth >= 4: F of the level-(D-2) boxes (downward pass)                  // symmetric near field: 13 x n column sums (zeroed at plan time)
     float *io_sigma = nullptr, *io_phi = nullptr; // staging for host sigma / phi
     int *status = nullptr;                        // device status word
     // 16-bit split M2L: per level max |M~| (float bits) and the power-of-two
@@ -261,6 +262,7 @@ struct PassArgs {
     unsigned *maxbits;          // per level max |M~| (float bits), or null
     int *count[kMaxDepth + 1];  // upward arrival counters, levels 2..D-2
     int keep;
+    float *Ftop;                // D >= 4: local coefficients of the level-(D-2) boxes, [box][nrhs][p^3]
 };
 cudaError_t launch_upward(const PassArgs &A, int p, cudaStream_t s);
 cudaError_t launch_downward(const PassArgs &A, int p, cudaStream_t s);

@@ -512,6 +512,8 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
         PTRY(plan_alloc(P, (void **)&P->sigma_rows, 4 * n * R, false, s));
     PTRY(plan_alloc(P, (void **)&P->phi_far, 4 * nt * R, false, s));
     PTRY(plan_alloc(P, (void **)&P->phi_near, 4 * nt * R, false, s));
+    if (D >= 4)
+        PTRY(plan_alloc(P, (void **)&P->Ftop, 4 * (1LL << (3 * (D - 2))) * R * P->p3, false, s));
     if (P->near_sym) // slots nobody writes stay zero for the plan's lifetime
         PTRY(plan_alloc(P, (void **)&P->near_slots, 4 * (int64_t)kSymSlotsHost * n, true, s));
     PTRY(plan_alloc(P, (void **)&P->status, 16, true, s));
@@ -561,6 +563,7 @@ static PassArgs pass_args(const bbfmm_plan_impl *P, int nrhs, bool split16)
     A.nslices = P->m2l_groups;
     A.maxbits = split16 ? P->a16_max : nullptr;
     A.keep = P->keep_coeffs ? 1 : 0;
+    A.Ftop = P->Ftop;
     for (int l = 2; l <= P->D; ++l) {
         const Level &L = P->lev[l];
         A.M[l] = L.M;

@@ -12,12 +12,14 @@
 // sibling coefficient sets, makes and compresses the parent's, and counts
 // itself in one level up, down to level 2.  No block waits for another.
 //
-// Downward (Sec. 2.2 item 3): a block recomputes the local coefficients of
-// its ancestors from level 2 down (decompress F = U F~ of each, plus the L2L
-// of its parent's), spreads its own box's to its 8 leaves (L2L), adds the
-// leaves' decompressed far fields and evaluates them at the leaves' points
-// (L2P).  The ancestor work repeats in every block of an ancestor's subtree;
-// it is small next to the leaf work and removes the level-by-level launches.
+// Downward (Sec. 2.2 item 3): a block makes the local coefficients of its
+// box (decompress F = U F~, plus the L2L of its parent's), spreads them to
+// its 8 leaves (L2L), adds the leaves' decompressed far fields and evaluates
+// them at the leaves' points (L2P).  The levels above come from a first,
+// small launch with a block per box of level D-2: it recomputes that box's
+// ancestors from level 2 down (repeated once per level-(D-2) box, small) and
+// stores the box's F, which the main launch reads as its parent.  Below depth
+// 4 the main launch recomputes its ancestors itself.
 //
 // Coefficient layouts: M and F are Morton-ordered [box][nrhs][p^3]; M~ / F~
 // rows sit at parity_row() of their box with the plan's max_nrhs as stride.
@@ -510,8 +512,17 @@ __global__ void __launch_bounds__(kThreads) k_downward(const __grid_constant__ P
     if (!A.keep && A.toff[8 * b] == A.toff[8 * b + 8])
         return; // no targets below this box
 
-    // ---- ancestors at levels 2 .. D-1 (the last one is the block's own box)
-    for (int l = 2; l <= D - 1; ++l) {
+    // ---- ancestors at levels 2 .. D-1 (the last one is the block's own box);
+    // with Ftop the parent's F comes from the first launch
+    int l0 = 2;
+    if (A.Ftop) {
+        const float *Fp = A.Ftop + ((b >> 3) * A.nrhs + c) * (int64_t)P3;
+        for (int i = t; i < P3; i += kThreads)
+            sPar[i] = __ldcg(Fp + i);
+        __syncthreads();
+        l0 = D - 1;
+    }
+    for (int l = l0; l <= D - 1; ++l) {
         const int64_t anc = b >> (3 * (D - 1 - l));
         if (l > 2)
             l2l1<P>(A.T, sPar, (int)(anc & 7), sOne, sPar);
@@ -626,6 +637,52 @@ __global__ void __launch_bounds__(kThreads) k_downward(const __grid_constant__ P
         }
         if (has)
             A.phi[(int64_t)c * A.nt + j] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// First downward launch (depth >= 4): block = (box of level D-2, RHS); the
+// box's F from level 2 down, as the main launch would recompute it, into Ftop
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_down_top(const __grid_constant__ PassArgs A)
+{
+    constexpr int P3 = P * P * P;
+    extern __shared__ __align__(16) float sm[];
+    float *sPar = sm;         // [P3] local coefficients of the current ancestor
+    float *sOne = sm + P3;    // [P3] scratch
+    float *sFt = sm + 2 * P3; // [r] far-field coefficients (compressed)
+    const int t = threadIdx.x;
+    const int D = A.D, lt = D - 2;
+    const int64_t b = blockIdx.x; // box at level D-2
+    const int c = blockIdx.y;
+    if (!A.keep && A.toff[64 * b] == A.toff[64 * b + 64])
+        return; // no targets below this box: the main launch skips its children too
+    for (int l = 2; l <= lt; ++l) {
+        const int64_t anc = b >> (3 * (lt - l));
+        if (l > 2)
+            l2l1<P>(A.T, sPar, (int)(anc & 7), sOne, sPar);
+        const int rl = A.rl[l];
+        for (int k = t; k < rl; k += kThreads)
+            load_ft(A, l, anc, c, sFt, 1, k);
+        __syncthreads();
+        const float *Ut = A.Ut[l];
+        for (int i = t; i < P3; i += kThreads) {
+            float a0 = 0.0f, a1 = 0.0f;
+            int k = 0;
+            for (; k + 1 < rl; k += 2) {
+                a0 += sFt[k] * __ldg(Ut + (int64_t)k * A.p3p + i);
+                a1 += sFt[k + 1] * __ldg(Ut + (int64_t)(k + 1) * A.p3p + i);
+            }
+            if (k < rl)
+                a0 += sFt[k] * __ldg(Ut + (int64_t)k * A.p3p + i);
+            const float f = (l > 2 ? sPar[i] : 0.0f) + (a0 + a1);
+            sPar[i] = f;
+            if (A.keep && (b & ((1LL << (3 * (lt - l))) - 1)) == 0)
+                A.F[l][(anc * A.nrhs + c) * P3 + i] = f;
+            if (l == lt)
+                A.Ftop[(b * A.nrhs + c) * P3 + i] = f;
+        }
+        __syncthreads();
     }
 }
 
@@ -857,6 +914,15 @@ cudaError_t upward_p(const PassArgs &A, cudaStream_t s)
 template <int P>
 cudaError_t downward_p(const PassArgs &A, cudaStream_t s)
 {
+    if (A.Ftop) {
+        if (A.D < 4)
+            return cudaErrorInvalidValue;
+        dim3 grid((unsigned)(1LL << (3 * (A.D - 2))), (unsigned)A.nrhs);
+        k_down_top<P><<<grid, kThreads, sizeof(float) * 3 * P * P * P, s>>>(A);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return e;
+    }
     const size_t smem = sizeof(float) * Smem<P>::kDownFloats;
     cudaError_t e = cudaFuncSetAttribute(k_downward<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
