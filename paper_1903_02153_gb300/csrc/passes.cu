@@ -345,8 +345,13 @@ __device__ void compress1(const PassArgs &A, int l, const float *X, int64_t box,
 }
 
 // ---------------------------------------------------------------------------
+// five blocks per SM (<= 51 registers) up to p = 5: more blocks hide the
+// pass's barriers and loads (148 -> 134 us at p = 5, depth 5; six blocks were
+// slower, and p = 6 spills at five)
+template <int P> constexpr int kUpMinBlocks = P <= 5 ? 5 : 1;
+
 template <int P>
-__global__ void __launch_bounds__(kThreads) k_upward(const __grid_constant__ PassArgs A)
+__global__ void __launch_bounds__(kThreads, kUpMinBlocks<P>) k_upward(const __grid_constant__ PassArgs A)
 {
     constexpr int P3 = P * P * P;
     constexpr int NQ = (P * P + 31) / 32; // (i2, i3) pairs per lane in P2M
