@@ -316,8 +316,7 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
     // staged sources: [j] = (x, x, y, y), [kSymStage + j] = (z, z, sigma, sigma)
     __shared__ float4 stage[2 * kSymStage];
     __shared__ __align__(16) float colpart[kColBuf];
-    __shared__ int sSrc[kSymStage];            // point index of a staged source
-    __shared__ unsigned char sSlot[kSymStage]; // its slot (symmetric segment only)
+    __shared__ float *sDst[kSymStage];         // slot entry of a staged two-way source
     __shared__ int nb_start[28], nb_pre[28], nb_cnt[28], nb_slot[28];
     __shared__ float4 nb_delta[27];
     __shared__ float2 red[NPK][kP2PThreads];
@@ -397,6 +396,10 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
     const float2 floor2 = make_float2(kR2Floor, kR2Floor);
     const int NQP = (nq + 3) & ~3;                // colpart row stride
     const int PL = min(kSymStage, kColBuf / NQP); // pass length
+    // the row padding (target groups nq .. NQP-1) is never written: zero it
+    // once, so the column sums read whole rows
+    for (int e = tid; e < PL * (NQP - nq); e += kP2PThreads)
+        colpart[(e / (NQP - nq)) * NQP + nq + e % (NQP - nq)] = 0.0f;
 
     float2 acc[NPK], acc2[NPK];
 #pragma unroll
@@ -417,8 +420,7 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
             stage[g] = make_float4(x, x, y, y);
             stage[kSymStage + g] = make_float4(z, z, s, s);
             if (gg >= nsym0) {
-                sSrc[g] = src;
-                sSlot[g] = (unsigned char)nb_slot[k];
+                sDst[g] = slots + (long long)nb_slot[k] * n + src;
             }
         }
         __syncthreads();
@@ -472,19 +474,16 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
         __syncthreads();
         // column sums of this pass's two-way sources, in target-group order
         for (int g = max(0, nsym0 - base) + tid; g < cnt; g += kP2PThreads) {
-            const float *row = colpart + g * NQP;
+            const float4 *row = reinterpret_cast<const float4 *>(colpart + g * NQP);
             float v = 0.0f;
-            int q = 0;
-            for (; q + 4 <= nq; q += 4) {
-                const float4 c4 = *reinterpret_cast<const float4 *>(row + q);
+            for (int q = 0; q < NQP / 4; ++q) {
+                const float4 c4 = row[q];
                 v += c4.x;
                 v += c4.y;
                 v += c4.z;
                 v += c4.w;
             }
-            for (; q < nq; ++q)
-                v += row[q];
-            slots[(long long)sSlot[g] * n + sSrc[g]] = scale * v;
+            *sDst[g] = scale * v;
         }
         __syncthreads();
     }
