@@ -294,8 +294,9 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
 //
 // Column sums: the thread of target group q visiting source j stores its
 // partial sum over its kTPT targets in colpart[j][q] (row stride nq rounded
-// up to 4); after the pass one thread per source adds the nq partials of its
-// row in order.
+// up to 4, the padding zero); after the pass one thread per source adds its
+// row in order and stores the sum through the slot pointer staged with the
+// source.
 constexpr int kSymSlots = 13;
 struct OneWay {
     static constexpr bool value = false;
