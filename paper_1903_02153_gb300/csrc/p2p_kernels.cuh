@@ -279,17 +279,18 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
 // the work item of leaf alpha takes
 //   - its own leaf, one way (rows of alpha only, r = 0 test);
 //   - the 13 "forward" neighbours beta = alpha + d (nid > 13 in the 3x3x3
-//     numbering): both ways when alpha is one work item -- rows of alpha in
+//     numbering): both ways when alpha holds at most kSymMaxPoints points
+//     -- rows of alpha in
 //     registers, and for every source of beta the column sum
 //     sum_t K(x_t, y_j) sigma_t over alpha's targets, which goes to slot
 //     26 - nid of that point (the nid under which beta sees alpha);
-//   - a backward neighbour (nid < 13) only when that leaf is split into
-//     several work items: such a leaf writes no slots (its items would
-//     collide), so both sides then take their own rows of the pair.
+//   - a backward neighbour (nid < 13) only when that leaf holds more than
+//     kSymMaxPoints points: such a leaf writes no slots, so both sides then
+//     take their own rows of the pair.
 // Each (slot, point) is written by one work item and never by two, and the
 // combine adds the 13 slots in a fixed order after the point's own rows:
 // the result does not depend on scheduling.  Slots no work item writes (the
-// backward neighbour is absent, empty or split) stay at the zero they were
+// backward neighbour is absent, empty or above kSymMaxPoints) stay at the zero they were
 // given when the plan was made.
 //
 // Column sums: the thread of target group q visiting source j stores its
@@ -306,6 +307,13 @@ struct TwoWay {
 };
 constexpr int kSymStage = 256; // staged sources per pass
 constexpr int kColBuf = 2048;  // column partials per pass (nq x pass length)
+// leaves of more points take their pairs one way: their column rows would
+// cut the passes short (the rule is the same on both sides of a pair)
+#ifndef BBFMM_SYM_MAX_POINTS
+#define BBFMM_SYM_MAX_POINTS 64
+#endif
+constexpr int kSymMaxPoints = BBFMM_SYM_MAX_POINTS;
+static_assert(kSymMaxPoints <= kP2PChunk, "a two-way leaf is one work item");
 
 template <class Kern>
 __global__ void __launch_bounds__(kP2PThreads, 8)
@@ -329,7 +337,7 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
     const int S = kP2PThreads / nq;
     const int t = tid % nq, slice = tid / nq;
     const bool active = slice < S;
-    const bool whole = off[ch.x + 1] - off[ch.x] <= kP2PChunk; // alpha is one work item
+    const bool whole = off[ch.x + 1] - off[ch.x] <= kSymMaxPoints; // alpha takes its pairs both ways
     int ax, ay, az;
     demorton3((unsigned)ch.x, ax, ay, az);
     const int nside = 1 << D;
@@ -348,7 +356,7 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
                 cnt = off[nm + 1] - start;
             }
             if (cnt > 0)
-                key = tid == 13 ? 0 : tid > 13 ? (whole ? 2 : 1) : (cnt > kP2PChunk ? 1 : 3);
+                key = tid == 13 ? 0 : tid > 13 ? (whole ? 2 : 1) : (cnt > kSymMaxPoints ? 1 : 3);
             dl = make_float4((float)dx, (float)dy, (float)dz, 0.0f);
         }
         const unsigned lt = (1u << tid) - 1u;
@@ -395,12 +403,14 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
         SG[pk] = make_float2(h0 ? sig[ch.y + i0] : 0.0f, h1 ? sig[ch.y + i1] : 0.0f);
     }
     const float2 floor2 = make_float2(kR2Floor, kR2Floor);
-    const int NQP = (nq + 3) & ~3;                // colpart row stride
-    const int PL = min(kSymStage, kColBuf / NQP); // pass length
-    // the row padding (target groups nq .. NQP-1) is never written: zero it
-    // once, so the column sums read whole rows
-    for (int e = tid; e < PL * (NQP - nq); e += kP2PThreads)
-        colpart[(e / (NQP - nq)) * NQP + nq + e % (NQP - nq)] = 0.0f;
+    const int NQP = (nq + 3) & ~3; // colpart row stride
+    // pass length: with two-way sources PL rows of NQP partials must fit
+    // colpart (PL * NQP <= kColBuf); without, colpart is not used
+    const bool two_way = nsym0 < ns;
+    const int PL = two_way ? min(kSymStage, kColBuf / NQP) : kSymStage;
+    if (two_way) // the row padding (groups nq .. NQP-1) is never written: zero it once
+        for (int e = tid; e < PL * (NQP - nq); e += kP2PThreads)
+            colpart[(e / (NQP - nq)) * NQP + nq + e % (NQP - nq)] = 0.0f;
 
     float2 acc[NPK], acc2[NPK];
 #pragma unroll
