@@ -25,7 +25,7 @@ BBFMM_K_TEST_POLY, BBFMM_K_TEST_CONST = 100, 101
 BBFMM_PREC_FP32, BBFMM_PREC_TF32, BBFMM_PREC_TF32X3, BBFMM_PREC_BF16X3, BBFMM_PREC_FP16X3 = 0, 1, 2, 3, 4
 
 INTERPS = {"chebyshev": 0, "uniform": 1}   # BBFMM_INTERP_*
-NEAR_MODES = {"auto": 0, "ordered": 1}      # BBFMM_NEAR_*
+NEAR_MODES = {"auto": 0, "ordered": 1, "symmetric": 2}   # BBFMM_NEAR_*
 BBFMM_K_USER_FIRST = 1000                   # ids of kernels from bbfmm_kernel_register
 
 PRECISIONS = {"fp32": BBFMM_PREC_FP32, "tf32": BBFMM_PREC_TF32, "tf32x3": BBFMM_PREC_TF32X3,

@@ -193,6 +193,7 @@ struct bbfmm_plan_impl {
     float *sigma_s = nullptr, *phi_far = nullptr, *phi_near = nullptr;
     float *sigma_rows = nullptr;                  // max_nrhs > 1: sigma_s row-major, for the near field
     bool near_sym = false;                        // near field evaluated pairwise both ways (one RHS)
+    bool near_auto = false;                       // near_sym chosen from the leaf occupancy
     float *near_slots = nullptr;
     float *Ftop = nullptr;                        // depth >= 4: F of the level-(D-2) boxes (downward pass)                  // symmetric near field: 13 x n column sums (zeroed at plan time)
     float *io_sigma = nullptr, *io_phi = nullptr; // staging for host sigma / phi

@@ -514,6 +514,12 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
     PTRY(plan_alloc(P, (void **)&P->phi_near, 4 * nt * R, false, s));
     if (D >= 4)
         PTRY(plan_alloc(P, (void **)&P->Ftop, 4 * (1LL << (3 * (D - 2))) * R * P->p3, false, s));
+    if (P->near_sym && P->near_auto) {
+        // measured at 1M / 2M points: faster at ~32 points per leaf, slower at
+        // ~4 (per-item work dominates) and on clustered sets averaging ~64
+        const double mean = (double)n / (double)std::max<int64_t>(1, P->nonempty_leaves);
+        P->near_sym = mean >= 16.0 && mean <= 48.0;
+    }
     if (P->near_sym) // slots nobody writes stay zero for the plan's lifetime
         PTRY(plan_alloc(P, (void **)&P->near_slots, 4 * (int64_t)kSymSlotsHost * n, true, s));
     PTRY(plan_alloc(P, (void **)&P->status, 16, true, s));
@@ -816,7 +822,8 @@ static int plan_create(const double *points, int64_t n, const double *targets, i
         return fail(BBFMM_EINVAL, "unknown precision %d", opts.precision);
     if (opts.interp != BBFMM_INTERP_CHEBYSHEV && opts.interp != BBFMM_INTERP_UNIFORM)
         return fail(BBFMM_EINVAL, "unknown interp %d", opts.interp);
-    if (opts.near_mode != BBFMM_NEAR_AUTO && opts.near_mode != BBFMM_NEAR_ORDERED)
+    if (opts.near_mode != BBFMM_NEAR_AUTO && opts.near_mode != BBFMM_NEAR_ORDERED &&
+        opts.near_mode != BBFMM_NEAR_SYMMETRIC)
         return fail(BBFMM_EINVAL, "unknown near_mode %d", opts.near_mode);
     if (opts.interp == BBFMM_INTERP_UNIFORM && opts.precision != BBFMM_PREC_FP32)
         return fail(BBFMM_EINVAL, "equally spaced nodes run the Fourier-domain M2L in FP32 (precision must be "
@@ -867,7 +874,8 @@ static int plan_create(const double *points, int64_t n, const double *targets, i
     P->nodeset = opts.interp;
     // the symmetric near field needs K(x, y) = K(y, x) (for a user kernel, as
     // registered) and one point set
-    P->near_sym = opts.near_mode == BBFMM_NEAR_AUTO && !targets && kernel_symmetric(kernel_id);
+    P->near_sym = opts.near_mode != BBFMM_NEAR_ORDERED && !targets && kernel_symmetric(kernel_id);
+    P->near_auto = opts.near_mode == BBFMM_NEAR_AUTO;
     if (opts.domain_given) {
         for (int d = 0; d < 3; ++d)
             P->lo[d] = opts.lo[d];

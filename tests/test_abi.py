@@ -128,10 +128,10 @@ def test_unknown_user_kernel_id_is_rejected(lib):
 
 
 def test_plan_rejects_bad_near_mode(lib):
-    """near_mode must be AUTO or ORDERED: EINVAL before any device call."""
+    """near_mode must be AUTO, ORDERED or SYMMETRIC: EINVAL before any device call."""
     pts = np.random.default_rng(4).random((10, 3))
     h = ctypes.c_void_p()
-    for mode in (2, -1, 7):
+    for mode in (3, -1, 7):
         o = lib.bbfmm_default_opts()
         o.near_mode = mode
         assert lib.lib().bbfmm_plan(pts.ctypes.data, 10, 1, 4, 3, ctypes.byref(o), None,

@@ -1,5 +1,5 @@
-"""The symmetric near field (BBFMM_NEAR_AUTO: K(x, y) = K(y, x), so each pair
-of neighbour leaves is evaluated once and used both ways, Sec. 2.5) against
+"""The symmetric near field (BBFMM_NEAR_SYMMETRIC: K(x, y) = K(y, x), so each
+pair of neighbour leaves is evaluated once and used both ways, Sec. 2.5) against
 the ordered one (BBFMM_NEAR_ORDERED: every target leaf evaluates all its
 pairs), against the FP64 direct sum where the near field is the whole result
 (depth 0 and 1: every leaf is a neighbour of every other), and against the
@@ -54,16 +54,27 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def test_auto_chooses_by_leaf_occupancy(bb):
+    """AUTO takes the symmetric form at 16..48 points per occupied leaf only."""
+    for n, depth, want in [(16384, 3, 1), (2048, 3, 0), (60_000, 3, 0), (30_000, 4, 0), (100_000, 4, 1)]:
+        plan = make_plan(bb, W.uniform_points(n, seed=515), K_INV_R, 4, depth, "auto")
+        info = plan.info()
+        plan.close()
+        mean = n / info.nonempty_leaves
+        assert info.near_symmetric == want, (n, depth, mean)
+        assert info.near_symmetric == (16 <= mean <= 48)
+
+
 def test_symmetric_form_is_chosen_where_it_applies(bb):
     pts = W.uniform_points(5000, seed=501)
     for kid, want in [(K_INV_R, 1), (K_INV_R2, 1), (K_EXP, 1), (K_GAUSS, 1), (K_CONST, 1), (K_POLY, 0)]:
-        plan = make_plan(bb, pts, kid, 4, 2, "auto")
+        plan = make_plan(bb, pts, kid, 4, 2, "symmetric")
         assert plan.info().near_symmetric == want, kid
         plan.close()
     plan = make_plan(bb, pts, K_INV_R, 4, 2, "ordered")
     assert plan.info().near_symmetric == 0
     plan.close()
-    plan = make_plan(bb, pts, K_INV_R, 4, 2, "auto", targets=W.uniform_points(700, seed=502))
+    plan = make_plan(bb, pts, K_INV_R, 4, 2, "symmetric", targets=W.uniform_points(700, seed=502))
     assert plan.info().near_symmetric == 0   # targets apart from the sources
     plan.close()
     # run-time compiled kernels: as registered
@@ -75,7 +86,7 @@ __device__ float bbfmm_kernel_f32(float d0, float d1, float d2)
 """
     for symmetric in (True, False):
         kid = bb.bbfmm_kernel_register(body, symmetric=symmetric)
-        plan = make_plan(bb, pts, kid, 4, 2, "auto")
+        plan = make_plan(bb, pts, kid, 4, 2, "symmetric")
         assert plan.info().near_symmetric == int(symmetric)
         plan.close()
 
@@ -93,8 +104,8 @@ __device__ float bbfmm_kernel_f32(float d0, float d1, float d2)
     n = 40_000
     pts = W.clustered_points(n, seed=513)
     sig = W.uniform_sigma(n, seed=514)
-    got, info = run(bb, pts, sig, kid, 5, 4, "auto")
-    ref, info_b = run(bb, pts, sig, K_EXP, 5, 4, "auto", ell=0.4)
+    got, info = run(bb, pts, sig, kid, 5, 4, "symmetric")
+    ref, info_b = run(bb, pts, sig, K_EXP, 5, 4, "symmetric", ell=0.4)
     assert info.near_symmetric == 1 and info_b.near_symmetric == 1
     assert rel(got, ref) <= 2e-6
 
@@ -113,7 +124,7 @@ def test_symmetric_matches_ordered_and_oracle(bb, oracle, kid, ell, kind, n, p, 
     field of the closest pairs sits near 1e-5 in both orders alike)."""
     pts = W.make_points(kind, n, seed=503)
     sig = W.uniform_sigma(n, seed=504).astype(np.float32).astype(np.float64)
-    got, info = run(bb, pts, sig, kid, p, depth, "auto", ell=ell)
+    got, info = run(bb, pts, sig, kid, p, depth, "symmetric", ell=ell)
     ordered, info_o = run(bb, pts, sig, kid, p, depth, "ordered", ell=ell)
     assert info.near_symmetric == 1 and info_o.near_symmetric == 0
     d = rel(got, ordered)
@@ -136,7 +147,7 @@ def test_near_field_alone_is_the_direct_sum(bb, oracle, kid, ell, depth, kind, n
     costs a few 1e-6 in FP32 (the ordered form's gate too)."""
     pts = W.make_points(kind, n, seed=505)
     sig = W.uniform_sigma(n, seed=506).astype(np.float32).astype(np.float64)
-    got, info = run(bb, pts, sig, kid, 4, depth, "auto", ell=ell)
+    got, info = run(bb, pts, sig, kid, 4, depth, "symmetric", ell=ell)
     ref = oracle.direct(pts, pts, sig, kid, ell=ell)
     assert rel(got, ref) <= (5e-6 if kid == K_INV_R2 else 1e-6)
 
@@ -150,7 +161,7 @@ def test_tiny_and_ragged_point_counts(bb, oracle, n):
     pts = W.uniform_points(n, seed=507 + n)
     sig = W.uniform_sigma(n, seed=508 + n).astype(np.float32).astype(np.float64)
     for depth in (0, 1, 2):
-        got, _ = run(bb, pts, sig, K_EXP, 4, depth, "auto", ell=0.5)
+        got, _ = run(bb, pts, sig, K_EXP, 4, depth, "symmetric", ell=0.5)
         if depth < 2:
             ref = oracle.direct(pts, pts, sig, K_EXP, ell=0.5)
         else:
@@ -161,7 +172,7 @@ def test_tiny_and_ragged_point_counts(bb, oracle, n):
 def test_symmetric_form_is_repeatable_bitwise(bb):
     pts = W.clustered_points(80_000, seed=509)
     sig = W.uniform_sigma(80_000, seed=510)
-    plan = make_plan(bb, pts, K_INV_R, 5, 4, "auto", precision="fp16x3")
+    plan = make_plan(bb, pts, K_INV_R, 5, 4, "symmetric", precision="fp16x3")
     a = matvec(bb, plan, sig)
     for _ in range(3):
         assert np.array_equal(matvec(bb, plan, sig), a)
@@ -175,7 +186,7 @@ def test_several_rhs_between_single_rhs_calls(bb, oracle):
     n = 30_000
     pts = W.uniform_points(n, seed=511)
     sig3 = W.uniform_sigma(n, nrhs=3, seed=512)
-    plan = make_plan(bb, pts, K_EXP, 5, 4, "auto", ell=0.4, max_nrhs=3)
+    plan = make_plan(bb, pts, K_EXP, 5, 4, "symmetric", ell=0.4, max_nrhs=3)
     first = matvec(bb, plan, sig3[:, 0])
     many = matvec(bb, plan, np.ascontiguousarray(sig3.T)).T
     again = matvec(bb, plan, sig3[:, 0])
