@@ -61,9 +61,10 @@ extern "C" {
                                     an inverse DFT per box; FP32; no compression */
 
 /* near-field evaluation order (Sec. 2.5, symmetry of the kernel) */
-#define BBFMM_NEAR_AUTO 0      /* SYMMETRIC where it applies and the leaves hold 16 to
-                                  48 points on average (where it was measured to be
-                                  faster), otherwise ORDERED (default) */
+#define BBFMM_NEAR_AUTO 0      /* SYMMETRIC where it applies and the near-field pairs
+                                  per point / 27 (the occupancy of the leaves the work
+                                  meets) is 16 to 48, where it was measured to be
+                                  faster; otherwise ORDERED (default) */
 #define BBFMM_NEAR_ORDERED 1   /* every target leaf evaluates all its neighbour pairs */
 #define BBFMM_NEAR_SYMMETRIC 2 /* symmetric kernel, targets = sources, one right-hand
                                   side: each pair of neighbour leaves is evaluated once

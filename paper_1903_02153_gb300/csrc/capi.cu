@@ -515,10 +515,12 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
     if (D >= 4)
         PTRY(plan_alloc(P, (void **)&P->Ftop, 4 * (1LL << (3 * (D - 2))) * R * P->p3, false, s));
     if (P->near_sym && P->near_auto) {
-        // measured at 1M / 2M points: faster at ~32 points per leaf, slower at
-        // ~4 (per-item work dominates) and on clustered sets averaging ~64
-        const double mean = (double)n / (double)std::max<int64_t>(1, P->nonempty_leaves);
-        P->near_sym = mean >= 16.0 && mean <= 48.0;
+        // occupancy of the leaves the near-field work meets: pairs per point
+        // over the 27 neighbours.  Measured at 1M / 2M points: faster at ~30,
+        // slower at ~4 (per-item work dominates) and on the clustered set
+        // (~170, where the pairs sit in dense leaves)
+        const double occ = (double)P->p2p_pairs / (27.0 * (double)n);
+        P->near_sym = occ >= 16.0 && occ <= 48.0;
     }
     if (P->near_sym) // slots nobody writes stay zero for the plan's lifetime
         PTRY(plan_alloc(P, (void **)&P->near_slots, 4 * (int64_t)kSymSlotsHost * n, true, s));

@@ -55,14 +55,19 @@ def rel(a, b):
 
 
 def test_auto_chooses_by_leaf_occupancy(bb):
-    """AUTO takes the symmetric form at 16..48 points per occupied leaf only."""
-    for n, depth, want in [(16384, 3, 1), (2048, 3, 0), (60_000, 3, 0), (30_000, 4, 0), (100_000, 4, 1)]:
-        plan = make_plan(bb, W.uniform_points(n, seed=515), K_INV_R, 4, depth, "auto")
+    """AUTO takes the symmetric form when the near-field pairs per point / 27
+    (the occupancy of the leaves the work meets) is 16..48, and not on the
+    clustered set, whose pairs sit in dense leaves."""
+    cases = [(W.uniform_points(16384, seed=515), 3, 1), (W.uniform_points(2048, seed=515), 3, 0),
+             (W.uniform_points(60_000, seed=515), 3, 0), (W.uniform_points(30_000, seed=515), 4, 0),
+             (W.uniform_points(100_000, seed=515), 4, 1), (W.clustered_points(200_000, seed=515), 5, 0)]
+    for pts, depth, want in cases:
+        plan = make_plan(bb, pts, K_INV_R, 4, depth, "auto")
         info = plan.info()
         plan.close()
-        mean = n / info.nonempty_leaves
-        assert info.near_symmetric == want, (n, depth, mean)
-        assert info.near_symmetric == (16 <= mean <= 48)
+        occ = info.p2p_pairs / (27.0 * len(pts))
+        assert info.near_symmetric == want, (len(pts), depth, occ)
+        assert info.near_symmetric == (16 <= occ <= 48)
 
 
 def test_symmetric_form_is_chosen_where_it_applies(bb):
