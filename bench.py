@@ -13,7 +13,7 @@ steps by writing a 512 MB buffer (the working set is smaller than L2).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                     [--workload NAME] [--precision fp16x3|tf32x3|bf16x3|tf32|fp32]
-                    [--interp chebyshev|uniform] [--near auto|ordered]
+                    [--interp chebyshev|uniform] [--near auto|ordered|symmetric]
 
 Prints one JSON line (rank 0).  Under torchrun every rank runs an
 independent replica of the workload (the matvec is single-GPU: replicas
@@ -52,8 +52,9 @@ def parse():
     ap.add_argument("--interp", default="chebyshev", choices=["chebyshev", "uniform"],
                     help="uniform: equally spaced nodes with the Fourier-domain M2L (FP32)")
     ap.add_argument("--svd-eps", type=float, default=1e-6)
-    ap.add_argument("--near", default="auto", choices=["auto", "ordered"],
-                    help="near-field order: auto = each neighbour leaf pair once (symmetric kernels)")
+    ap.add_argument("--near", default="auto", choices=["auto", "ordered", "symmetric"],
+                    help="near-field order: symmetric = each neighbour leaf pair once (symmetric kernels), "
+                         "ordered = every target leaf its own pairs, auto = chosen from the leaf occupancy")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-depth6", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
