@@ -140,7 +140,10 @@ typedef struct {
  * field.  The source is compiled at once with NVRTC for sm_103a.
  *   homogeneity: m with k(a d) = a^m k(d) for all a > 0 (one operator set for
  *                every level, scaled), or 0 (operators per level); -8..8.
- *   symmetric:   1 if k(-d) = k(d) (one Gram matrix in the SVD), else 0.
+ *   symmetric:   1 if k(-d) = k(d): one Gram matrix in the SVD, and the
+ *                symmetric near field (BBFMM_NEAR_SYMMETRIC / AUTO) may use
+ *                each kernel value for both points of a pair; else 0.  A
+ *                kernel registered symmetric that is not gives wrong results.
  *   kernel_id:   receives an id >= BBFMM_K_USER_FIRST, usable as kernel_id
  *                in bbfmm_plan and bbfmm_plan_targets (opts.ell is unused
  *                for it).  Registrations last until the process exits.
