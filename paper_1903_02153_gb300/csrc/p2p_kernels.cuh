@@ -279,19 +279,19 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
 // the work item of leaf alpha takes
 //   - its own leaf, one way (rows of alpha only, r = 0 test);
 //   - the 13 "forward" neighbours beta = alpha + d (nid > 13 in the 3x3x3
-//     numbering): both ways when alpha holds at most kSymMaxPoints points
-//     -- rows of alpha in
-//     registers, and for every source of beta the column sum
-//     sum_t K(x_t, y_j) sigma_t over alpha's targets, which goes to slot
-//     26 - nid of that point (the nid under which beta sees alpha);
+//     numbering): both ways when alpha holds at most kSymMaxPoints points --
+//     rows of alpha in registers, and for every source of beta the column
+//     sum sum_t K(x_t, y_j) sigma_t over alpha's targets, which goes to slot
+//     26 - nid of that point (the nid under which beta sees alpha); one way
+//     otherwise;
 //   - a backward neighbour (nid < 13) only when that leaf holds more than
 //     kSymMaxPoints points: such a leaf writes no slots, so both sides then
 //     take their own rows of the pair.
 // Each (slot, point) is written by one work item and never by two, and the
 // combine adds the 13 slots in a fixed order after the point's own rows:
 // the result does not depend on scheduling.  Slots no work item writes (the
-// backward neighbour is absent, empty or above kSymMaxPoints) stay at the zero they were
-// given when the plan was made.
+// backward neighbour is absent, empty or above kSymMaxPoints) stay at the
+// zero they were given when the plan was made.
 //
 // Column sums: the thread of target group q visiting source j stores its
 // partial sum over its kTPT targets in colpart[j][q] (row stride nq rounded
