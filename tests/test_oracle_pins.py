@@ -10,6 +10,8 @@ that plausible mistakes planted in the oracle fail these pins.
 """
 import itertools
 
+import os
+
 import numpy as np
 import pytest
 
@@ -240,18 +242,31 @@ def test_fmm_error_decays_with_p(oracle, kid):
     assert errs[-1] < 1e-3 * errs[0], errs
 
 
+def _golden(name):
+    rows = []
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].split()
+            if line:
+                rows.append([float(v) for v in line])
+    return np.array(rows)
+
+
 def test_fmm_error_magnitude_anchor(oracle):
-    """Table 1 (Sec. 4.2): 1/r, Chebyshev p = 4, uniform points in the unit cube,
-    relative error 2.10e-5 / 2.08e-5 / 2.10e-5.  The paper does not print its
-    weights or points per leaf; with nonnegative weights sigma ~ U(0,1) and
-    ~40 points per leaf the oracle lands on the same figure.  (Zero-mean weights
-    make phi smaller and the relative error about 18x larger.)"""
+    """Table 1 (Sec. 4.2; tests/golden/table1_inv_r_p4_errors.txt): 1/r,
+    Chebyshev p = 4, uniform points in the unit cube, relative error 2.10e-5 /
+    2.08e-5 / 2.10e-5.  The paper does not print its weights or points per
+    leaf; with nonnegative weights sigma ~ U(0,1) and ~40 points per leaf the
+    oracle lands on the same figure, so the band is the printed values widened
+    by 0.7x .. 1.45x.  (Zero-mean weights make phi smaller and the relative
+    error about 18x larger.)"""
+    printed = _golden("table1_inv_r_p4_errors.txt")[:, 2]
     n = 20_000
     x = W.uniform_points(n, seed=19)
     s = np.random.default_rng(1).random(n)
     ref = oracle.direct(x, x, s, K_INV_R)
     err = oracle.rel_err(oracle.bbfmm(x, s, K_INV_R, p=4, depth=3), ref)
-    assert 1.5e-5 < err < 3.0e-5, err
+    assert 0.7 * printed.min() < err < 1.45 * printed.max(), (err, printed)
 
 
 def test_fmm_sampled_targets_match_full_run(oracle):
