@@ -55,14 +55,30 @@ cudaError_t launch_gather_sigma(const float *sigma, const int *perm, int64_t n, 
 // 16-bit split: x * s = hi + lo, hi = round16(x s), lo = round16(x s - hi);
 // s = 2^(13 - e) with 2^(e-1) < max|x| <= 2^e for FP16 (keeps hi below the
 // FP16 range limit and lo away from the subnormals), s = 1 for BF16.  One
-// launch for all levels: blockIdx.y picks the level.
+// launch for all levels: blockIdx.y picks the level.  A thread splits four
+// consecutive values (one 16-byte load, two 8-byte stores); the launcher
+// checks that every level's length is a multiple of 4 and its arrays aligned.
+template <int FMT>
+__device__ __forceinline__ unsigned split16(float v, unsigned &lo)
+{
+    if (FMT == 0) {
+        const __half h = __float2half_rn(v);
+        lo = __half_as_ushort(__float2half_rn(v - __half2float(h)));
+        return __half_as_ushort(h);
+    }
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    lo = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
+    return __bfloat16_as_ushort(h);
+}
+
+template <int FMT>
 __global__ void k_split16_levels(const __grid_constant__ Split16Args A)
 {
     const int l = A.lmin + blockIdx.y;
-    const float *x = A.x[l];
-    const int64_t n = A.n[l];
+    const float4 *x = reinterpret_cast<const float4 *>(A.x[l]);
+    const int64_t n4 = A.n[l] / 4;
     float s = 1.0f;
-    if (A.fmt == 0) {
+    if (FMT == 0) {
         const float mx = __uint_as_float(A.maxbits[l]);
         int e = 0;
         if (mx > 0.0f)
@@ -71,18 +87,14 @@ __global__ void k_split16_levels(const __grid_constant__ Split16Args A)
     }
     if (blockIdx.x == 0 && threadIdx.x == 0)
         A.scale[l] = s;
-    uint16_t *hi = A.hi[l], *lo = A.lo[l];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float v = x[i] * s;
-        if (A.fmt == 0) {
-            const __half h = __float2half_rn(v);
-            hi[i] = __half_as_ushort(h);
-            lo[i] = __half_as_ushort(__float2half_rn(v - __half2float(h)));
-        } else {
-            const __nv_bfloat16 h = __float2bfloat16_rn(v);
-            hi[i] = __bfloat16_as_ushort(h);
-            lo[i] = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
-        }
+    uint2 *hi = reinterpret_cast<uint2 *>(A.hi[l]), *lo = reinterpret_cast<uint2 *>(A.lo[l]);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = x[i];
+        unsigned l0, l1, l2, l3;
+        const unsigned h0 = split16<FMT>(v.x * s, l0), h1 = split16<FMT>(v.y * s, l1);
+        const unsigned h2 = split16<FMT>(v.z * s, l2), h3 = split16<FMT>(v.w * s, l3);
+        hi[i] = make_uint2(h0 | (h1 << 16), h2 | (h3 << 16));
+        lo[i] = make_uint2(l0 | (l1 << 16), l2 | (l3 << 16));
     }
 }
 
@@ -91,11 +103,19 @@ cudaError_t launch_split16_levels(const Split16Args &A, cudaStream_t s)
     if (A.lmin < 0 || A.lmax > kMaxDepth || A.lmin > A.lmax || (A.fmt != 0 && A.fmt != 1))
         return cudaErrorInvalidValue;
     int64_t most = 0;
-    for (int l = A.lmin; l <= A.lmax; ++l)
-        most = A.n[l] > most ? A.n[l] : most;
+    for (int l = A.lmin; l <= A.lmax; ++l) {
+        if (A.n[l] % 4 != 0 || reinterpret_cast<uintptr_t>(A.x[l]) % 16 != 0 ||
+            reinterpret_cast<uintptr_t>(A.hi[l]) % 8 != 0 || reinterpret_cast<uintptr_t>(A.lo[l]) % 8 != 0)
+            return cudaErrorInvalidValue;
+        most = A.n[l] / 4 > most ? A.n[l] / 4 : most;
+    }
     int64_t blocks = (most + 255) / 256;
     blocks = blocks > 2048 ? 2048 : (blocks < 1 ? 1 : blocks);
-    k_split16_levels<<<dim3((unsigned)blocks, (unsigned)(A.lmax - A.lmin + 1)), 256, 0, s>>>(A);
+    const dim3 grid((unsigned)blocks, (unsigned)(A.lmax - A.lmin + 1));
+    if (A.fmt == 0)
+        k_split16_levels<0><<<grid, 256, 0, s>>>(A);
+    else
+        k_split16_levels<1><<<grid, 256, 0, s>>>(A);
     return cudaGetLastError();
 }
 
