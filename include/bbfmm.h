@@ -5,7 +5,7 @@
  * (Sec. 1, Eq. summation / Eq. matvec of arXiv 1903.02153), targets = sources,
  * with the black-box FMM of Sec. 2: a uniform octree (Sec. 2.1, Def. 2.1),
  * Chebyshev interpolation (Sec. 2.2, Def. 2.2, Eq. low-rank-form), the four
- * stages P2M/M2M, M2L, L2L/L2P, P2P (Sec. 2.2), SVD-compressed M2L operators
+ * stages P2M/M2M, M2L, L2L/L2P, P2P (Sec. 2.3), SVD-compressed M2L operators
  * (Sec. 2.5 "Fast M2L translation"), leaf-level operators scaled per level for
  * homogeneous kernels (Sec. 2.5 "Homogeneous kernel"), and several weight
  * vectors at once (Sec. 2.5 "Multiple right-hand-sides").  Every stage of a
@@ -106,7 +106,15 @@ typedef struct {
     int near_mode;     /* BBFMM_NEAR_* (default AUTO).  The symmetric form holds 13
                           floats per point more (the two-way column sums); both
                           orders are deterministic, and they differ by FP32 rounding */
-    int reserved[2];   /* zero */
+    int close_refine;  /* 1 (default): near-field pairs closer than 1/64 of a leaf
+                          box side enter the result as if evaluated in FP64 (Sec. 2.3
+                          near field; the FP32 leaf-local coordinates round x - y by up
+                          to ~1e-7 box sides, which the singular kernels amplify on
+                          close pairs).  The plan lists such pairs once with FP64
+                          correction coefficients (a few bytes per pair); each matvec
+                          adds them in one small launch after the near field.
+                          0: the FP32 values only */
+    int reserved[1];   /* zero */
 } bbfmm_opts;
 
 typedef struct {
@@ -125,7 +133,11 @@ typedef struct {
     int64_t m2l_pairs;  /* M2L translations per right-hand side (dense grid) */
     int64_t n_targets;  /* targets (= n unless built by bbfmm_plan_targets) */
     int near_symmetric; /* 1: one-RHS matvecs evaluate each neighbour leaf pair once */
-    int reserved[5];
+    int close_pairs;    /* (target, source) near-field pairs listed for FP64
+                           correction (opts.close_refine) */
+    int64_t p2p_evals;  /* near-field kernel evaluations of a one-RHS matvec:
+                           p2p_pairs, or about half of it with the symmetric form */
+    int reserved[2];
 } bbfmm_info;
 
 /*
@@ -193,7 +205,7 @@ int bbfmm_plan_targets(const double *sources, int64_t ns, const double *targets,
                        int cheb_order, int depth, const bbfmm_opts *opts, void *stream, bbfmm_plan_t *out);
 
 /*
- * bbfmm_matvec: phi = K_hat sigma (Sec. 2.2, all four stages).
+ * bbfmm_matvec: phi = K_hat sigma (Sec. 2.3, all four stages).
  *   sigma: n x nrhs column-major FP32 (n sources), host or device; read only.
  *   phi:   nt x nrhs column-major FP32 (nt targets; nt = n unless the plan
  *          came from bbfmm_plan_targets), host or device; overwritten.
@@ -242,8 +254,8 @@ int bbfmm_rand_eig(bbfmm_plan_t plan, const float *omega, int m, int k, int powe
 /*
  * bbfmm_get_coefficients: copy the coefficients of the last matvec at one
  * level to host memory, for stage-by-stage checks.
- *   which: 0 = multipole M (Sec. 2.2 upward pass), 1 = local F after the
- *          downward pass at that level (Sec. 2.2 items 2-3).
+ *   which: 0 = multipole M (Sec. 2.3 upward pass), 1 = local F after the
+ *          downward pass at that level (Sec. 2.3 items 2-3).
  *   level: 2..D.
  *   out:   host, 8^level x nrhs x p^3 FP32, boxes in lexicographic order
  *          (a + 2^l (b + 2^l c)), node index i1 + p i2 + p^2 i3.
@@ -300,11 +312,14 @@ int bbfmm_status(bbfmm_plan_t plan, int *word);
  *             leaf with Morton index m are perm[leaf_off[m] .. leaf_off[m+1]).
  * Scratch: one file-scope device array of about 13.6 MB, resident on every GPU
  * that loads the library until the process exits.  Its address is looked up on
- * the first call made on a device (with that device current); make that first
- * call before any stream capture.  All calls share the array: calls that
- * overlap on the GPU (other streams, other threads) race and must be ordered
- * by the caller.  The call synchronizes `stream` to read the error flag.
- * Errors: EINVAL (sizes, host pointers, NaN or out-of-domain points), ECUDA.
+ * the first call made on a device (with that device current) and kept; make
+ * that first call before any stream capture.  The kept address does not
+ * survive cudaDeviceReset: do not call this entry point again after resetting
+ * a device.  All calls share the array: calls that overlap on the GPU (other
+ * streams, other threads) race and must be ordered by the caller.  The call
+ * synchronizes `stream` to read the error flag.
+ * Errors: EINVAL (sizes, host pointers, device memory of a GPU other than the
+ * current one, NaN or out-of-domain points), ECUDA.
  */
 int bbfmm_sort_points_static(const double *points, int64_t n, int depth, const double *lo, double side,
                              int32_t *perm, int32_t *leaf_off, void *stream);

@@ -10,11 +10,11 @@
  *
  * What it computes, in the paper's order and notation:
  *   - the direct sum phi_i = sum_j K(x_i, y_j) sigma_j           (Sec. 1, Eq. summation)
- *   - the black-box FMM approximation of the same sum            (Sec. 2.2, four stages)
- *       upward pass:  P2M on leaves, M2M on non-leaves            (Sec. 2.2 item 1)
- *       far field:    M2L over the interaction list I(alpha)      (Sec. 2.2 item 2, Def. 2.1)
- *       downward:     L2L, then L2P on leaves                     (Sec. 2.2 item 3)
- *       near field:   P2P over the neighbours N(alpha)            (Sec. 2.2 item 4, Def. 2.1)
+ *   - the black-box FMM approximation of the same sum            (Sec. 2.3, four stages)
+ *       upward pass:  P2M on leaves, M2M on non-leaves            (Sec. 2.3 item 1)
+ *       far field:    M2L over the interaction list I(alpha)      (Sec. 2.3 item 2, Def. 2.1)
+ *       downward:     L2L, then L2P on leaves                     (Sec. 2.3 item 3)
+ *       near field:   P2P over the neighbours N(alpha)            (Sec. 2.3 item 4, Def. 2.1)
  *     with Chebyshev nodes or equally spaced nodes (the two node sets of
  *     Sec. 2.2), the 1D/3D Lagrange basis (Def. 2.2) and the M2L operator
  *     K(x*_i, y*_j) evaluated at the nodes of the two boxes, uncompressed
@@ -33,7 +33,7 @@
  *     levels 2..D (levels 0 and 1 have empty interaction lists).
  *   - K at r == 0: 0 for the singular kernels (1/r, 1/r^2), the natural value
  *     for the smooth ones.
- *   - the traversal is the level-by-level form Sec. 2.3 names as the
+ *   - the traversal is the level-by-level form Sec. 2.4 names as the
  *     alternative to the task-based one; results do not depend on it.
  *   - equally spaced nodes: the paper prints them on [0, 1] as (k-1)/(p-1);
  *     on the reference interval [-1, 1] of a box (where the Chebyshev nodes
@@ -316,7 +316,7 @@ int oracle_interaction_list(int l, int64_t a, int64_t b, int64_t c, int64_t *out
 }
 
 /* ------------------------------------------------------------------------- */
-/* Stage 1, upward pass (Sec. 2.2 item 1). */
+/* Stage 1, upward pass (Sec. 2.3 item 1). */
 
 /* P2M: M^alpha_i = sum_{y_j in alpha} L_p(y*_i, y_j) sigma_j */
 static void or_p2m(or_tree *t)
@@ -399,7 +399,7 @@ static void or_m2m(or_tree *t, int l /* parent level */)
 }
 
 /* ------------------------------------------------------------------------- */
-/* Stage 2, far field (Sec. 2.2 item 2):
+/* Stage 2, far field (Sec. 2.3 item 2):
  *   F^alpha_i = sum_{beta in I(alpha)} sum_j K(x*_i, y*_j) M^beta_j.
  * K(x*_i, y*_j) depends only on the offset t = beta - alpha (translation
  * invariance), so the operator of each of the 7^3 - 3^3 = 316 offsets is
@@ -462,7 +462,7 @@ static void or_m2l(or_tree *t, int l)
 }
 
 /* ------------------------------------------------------------------------- */
-/* Stage 3, downward pass (Sec. 2.2 item 3). */
+/* Stage 3, downward pass (Sec. 2.3 item 3). */
 
 /* L2L: F^alpha_i += sum_j F^beta_j L_p(x*_j, x*_i), beta = P(alpha); x*_j are the
  * nodes of the parent beta, x*_i those of alpha. */
@@ -530,7 +530,7 @@ static void or_l2p(const or_tree *t, const double *x, int64_t bi, double *out /*
 }
 
 /* ------------------------------------------------------------------------- */
-/* Stage 4, near field (Sec. 2.2 item 4):
+/* Stage 4, near field (Sec. 2.3 item 4):
  *   phi_i += sum_{beta in N(alpha)} sum_{y_j in beta} K(x_i, y_j) sigma_j. */
 static void or_p2p(const or_tree *t, const double *x, int64_t bi, double *out /* nrhs */)
 {

@@ -5,7 +5,7 @@ cpu_baseline / reference legs of ``bench.py`` use it.  Nothing in the CUDA
 package imports it, and it imports nothing from that package.
 
 The C source follows the paper's definitions (Sec. 1 Eq. summation; Sec. 2.1
-Def. 2.1; Sec. 2.2 Def. 2.2, Eq. low-rank-form and the four stages).  This
+Def. 2.1; Sec. 2.2 Def. 2.2, Eq. low-rank-form; the four stages of Sec. 2.3).  This
 module only compiles it with gcc, marshals numpy arrays, and adds the default
 domain rule (bounding cube of the points).
 """
@@ -234,7 +234,7 @@ NODE_SETS = {"chebyshev": 0, "uniform": 1}
 
 def bbfmm(points, sigma, kid, p, depth, ell=1.0, lo=None, side=None, sample=None,
           dump=False, times=False, nodes="chebyshev"):
-    """FP64 black-box FMM (Sec. 2.2).  Returns phi (n,) / (n, nrhs), or for a
+    """FP64 black-box FMM (Sec. 2.3).  Returns phi (n,) / (n, nrhs), or for a
     ``sample`` of target indices phi at those targets only.  With ``dump`` also
     returns lists M[l], F[l] of arrays (8^l, nrhs, p^3) in lexicographic box
     order; with ``times`` the four stage times in seconds.  ``nodes``: the

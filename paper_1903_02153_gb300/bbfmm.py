@@ -43,7 +43,8 @@ class bbfmm_opts(ctypes.Structure):
                 ("lo", ctypes.c_double * 3), ("side", ctypes.c_double),
                 ("max_nrhs", ctypes.c_int), ("split_accumulate", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("keep_coefficients", ctypes.c_int),
-                ("interp", ctypes.c_int), ("near_mode", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("interp", ctypes.c_int), ("near_mode", ctypes.c_int), ("close_refine", ctypes.c_int),
+                ("reserved", ctypes.c_int * 1)]
 
 
 class bbfmm_info(ctypes.Structure):
@@ -53,7 +54,7 @@ class bbfmm_info(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("nonempty_leaves", ctypes.c_int64),
                 ("max_leaf_points", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64),
                 ("m2l_pairs", ctypes.c_int64), ("n_targets", ctypes.c_int64), ("near_symmetric", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("close_pairs", ctypes.c_int), ("p2p_evals", ctypes.c_int64), ("reserved", ctypes.c_int * 2)]
 
 
 class BBFMMError(RuntimeError):
@@ -272,12 +273,14 @@ class Plan:
 
     def __init__(self, points, kernel, order, depth, ell=1.0, svd_eps=1e-7, precision="fp32",
                  domain=None, max_nrhs=1, stream=None, split_accumulate=True, use_graph=True,
-                 keep_coefficients=False, targets=None, interp="chebyshev", near_mode="auto"):
+                 keep_coefficients=False, targets=None, interp="chebyshev", near_mode="auto",
+                 close_refine=True):
         import torch
         o = bbfmm_default_opts()
         o.split_accumulate = 1 if split_accumulate else 0
         o.use_graph = 1 if use_graph else 0
         o.keep_coefficients = 1 if keep_coefficients else 0
+        o.close_refine = 1 if close_refine else 0
         o.interp = INTERPS[interp] if isinstance(interp, str) else int(interp)
         o.near_mode = NEAR_MODES[near_mode] if isinstance(near_mode, str) else int(near_mode)
         o.ell = float(ell)

@@ -37,7 +37,7 @@ namespace bbfmm {
 
 constexpr int kMaxP = 10;
 constexpr int kMaxDepth = 8;
-constexpr int kNumOffsets = 316;      // 7^3 - 3^3 distinct M2L offsets (Sec. 2.2, Thm. 2.1)
+constexpr int kNumOffsets = 316;      // 7^3 - 3^3 distinct M2L offsets (Sec. 2.3)
 constexpr int kOffsetsPerClass = 189; // 6^3 - 3^3 interaction-list boxes (Def. 2.1)
 constexpr int kChunk = 128;           // near-field targets per work item (one block)
 constexpr int kSymSlotsHost = 13;     // two-way column sums per point (symmetric near field)
@@ -158,6 +158,17 @@ struct Level {
     uint16_t *Mt16_hi = nullptr, *Mt16_lo = nullptr; // split 16-bit copies of Mt
 };
 
+// near-field pairs closer than 1/64 cell with their FP64 corrections, listed
+// per target when the plan is made (k_close_pairs), added by k_near_fix
+struct CloseList {
+    int ntgt = 0;                   // targets with listed pairs
+    int64_t nentries = 0;           // listed (target, source) pairs
+    int *tgt = nullptr;             // [ntgt] target (tree order)
+    int *start = nullptr;           // [ntgt + 1] first entry of each
+    int *src = nullptr;             // [nentries] source (tree order)
+    float *c1 = nullptr, *cm = nullptr; // [nentries] coefficient for one RHS / several RHS
+};
+
 struct Stage { // indices into Plan::ev
     enum { Start = 0, Gather, Up, M2L, Down, L2P, P2P, Combine, NumEv };
 };
@@ -183,6 +194,7 @@ struct bbfmm_plan_impl {
     int4 *chunks = nullptr; // near-field work items over the target leaves
     int nchunks = 0;
     int64_t nonempty_leaves = 0, max_leaf = 0, p2p_pairs = 0, m2l_pairs = 0;
+    int64_t p2p_sym_evals = 0; // kernel evaluations of the symmetric near field (one RHS)
 
     // operators
     std::shared_ptr<DevOps> ops;
@@ -194,8 +206,10 @@ struct bbfmm_plan_impl {
     float *sigma_rows = nullptr;                  // max_nrhs > 1: sigma_s row-major, for the near field
     bool near_sym = false;                        // near field evaluated pairwise both ways (one RHS)
     bool near_auto = false;                       // near_sym chosen from the leaf occupancy
-    float *near_slots = nullptr;
-    float *Ftop = nullptr;                        // depth >= 4: F of the level-(D-2) boxes (downward pass)                  // symmetric near field: 13 x n column sums (zeroed at plan time)
+    float *near_slots = nullptr;                  // symmetric near field: 13 x n column sums (zeroed at plan time)
+    bool close_refine = true; // list the near field's close pairs with FP64 corrections
+    CloseList close;
+    float *Ftop = nullptr;                        // depth >= 4: F of the level-(D-2) boxes (downward pass)
     float *io_sigma = nullptr, *io_phi = nullptr; // staging for host sigma / phi
     int *status = nullptr;                        // device status word
     // 16-bit split M2L: per level max |M~| (float bits) and the power-of-two
@@ -355,6 +369,14 @@ struct P2PArgs {
 cudaError_t launch_p2p(const P2PArgs &A, int kernel, double ell, double h, int nrhs, float *phi_near,
                        cudaStream_t s);
 cudaError_t launch_p2p_user(const P2PArgs &A, int id, double h, int nrhs, float *phi_near, cudaStream_t s);
+// close pairs of the near field (p2p_kernels.cuh, k_close_pairs): the plan
+// lists the pairs closer than 1/64 cell with FP64 correction coefficients;
+// a matvec adds them after the near-field kernel (k_near_fix)
+struct CloseArgs;
+cudaError_t launch_close_pairs(const CloseArgs &A, int kernel, double ell, double h, bool fill, cudaStream_t s);
+cudaError_t launch_close_pairs_user(const CloseArgs &A, int id, double h, bool fill, cudaStream_t s);
+cudaError_t launch_near_fix(const CloseList &L, const float *sig, int64_t ns, int64_t nt, int nrhs, float *phi,
+                            cudaStream_t s);
 
 } // namespace bbfmm
 

@@ -1,6 +1,6 @@
 // capi.cu -- the C ABI of include/bbfmm.h: plan construction (tree build on
 // the device, FP64 operators on the host, buffer layout), the matvec driver
-// that enqueues the four stages of Sec. 2.2 (Alg. 1 as level-synchronous
+// that enqueues the four stages of Sec. 2.3 (Alg. 1 as level-synchronous
 // kernels, near field on a forked stream), and introspection helpers.
 #include <math.h>
 #include <stdarg.h>
@@ -14,6 +14,7 @@
 #include <tuple>
 
 #include "bbfmm_internal.h"
+#include "p2p_kernels.cuh" // CloseArgs
 
 namespace bbfmm {
 
@@ -415,7 +416,7 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
         for (int64_t m = 0; m < nleaf; ++m)
             leaf_occ[m] = to[m + 1] > to[m] ? 1 : 0;
         int side_cells = 1 << D;
-        int64_t pairs = 0;
+        int64_t pairs = 0, sym_evals = 0;
         for (int64_t m = 0; m < nleaf; ++m) {
             const int64_t cs = off[m + 1] - off[m], ct = to[m + 1] - to[m];
             if (cs > 0) {
@@ -426,7 +427,7 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
                 continue;
             int x, y, z;
             demorton3((uint32_t)m, x, y, z);
-            int64_t src = 0;
+            int64_t src = 0, fwd = 0;
             for (int dz = -1; dz <= 1; ++dz)
                 for (int dy = -1; dy <= 1; ++dy)
                     for (int dx = -1; dx <= 1; ++dx) {
@@ -435,10 +436,17 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
                             continue;
                         uint32_t nm = morton3(a, b, cc);
                         src += off[nm + 1] - off[nm];
+                        if ((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1) > 13)
+                            fwd += off[nm + 1] - off[nm];
                     }
             pairs += ct * src;
+            // the symmetric near field's evaluations: own leaf one way, each
+            // forward neighbour once (twice when alpha is too full to take it
+            // both ways, then both sides take their own rows)
+            sym_evals += cs * cs + cs * fwd * (cs <= kSymMaxPoints ? 1 : 2);
         }
         P->p2p_pairs = pairs;
+        P->p2p_sym_evals = sym_evals;
         for (int l = 2; l <= D; ++l)
             P->m2l_pairs += m2l_pairs_level(l);
     }
@@ -524,6 +532,64 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
     }
     if (P->near_sym) // slots nobody writes stay zero for the plan's lifetime
         PTRY(plan_alloc(P, (void **)&P->near_slots, 4 * (int64_t)kSymSlotsHost * n, true, s));
+    if (P->close_refine && P->nchunks > 0) {
+        // near-field pairs closer than 1/64 cell, with FP64 corrections of
+        // the FP32 values the near-field kernels add (k_close_pairs): count
+        // per target, lay the entries out on the host, fill
+        int *cnt = nullptr, *first = nullptr;
+        PTRY(talloc((void **)&cnt, 4 * nt));
+        CloseArgs C = {};
+        C.tpts = P->tpts;
+        C.chunks = P->chunks;
+        C.nchunks = P->nchunks;
+        C.spts = P->pts;
+        C.soff = P->leaf_off;
+        C.tx = P->separate ? dtgt : dpts;
+        C.tperm = P->tperm;
+        C.sx = dpts;
+        C.sperm = P->perm;
+        C.D = D;
+        C.same = P->separate ? 0 : 1;
+        C.sym = P->near_sym ? 1 : 0;
+        C.count = cnt;
+        const double h = P->side / (double)(1LL << D);
+        CUDA_TRY(launch_close_pairs(C, P->kernel, P->ell, h, false, s));
+        std::vector<int> hc(nt), hfirst(nt), tg, st;
+        CUDA_TRY(cudaMemcpyAsync(hc.data(), cnt, 4 * nt, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        int64_t E = 0;
+        for (int64_t t = 0; t < nt; ++t) {
+            hfirst[t] = (int)std::min<int64_t>(E, INT32_MAX);
+            if (hc[t] > 0) {
+                tg.push_back((int)t);
+                st.push_back((int)std::min<int64_t>(E, INT32_MAX));
+                E += hc[t];
+            }
+        }
+        if (E >= INT32_MAX)
+            return fail(BBFMM_ENOMEM, "%lld close near-field pairs: too many for the correction list", (long long)E);
+        st.push_back((int)E);
+        if (E > 0) {
+            CloseList &L = P->close;
+            L.ntgt = (int)tg.size();
+            L.nentries = E;
+            PTRY(talloc((void **)&first, 4 * nt));
+            PTRY(plan_alloc(P, (void **)&L.tgt, 4 * (int64_t)tg.size(), false, s));
+            PTRY(plan_alloc(P, (void **)&L.start, 4 * (int64_t)st.size(), false, s));
+            PTRY(plan_alloc(P, (void **)&L.src, 4 * E, false, s));
+            PTRY(plan_alloc(P, (void **)&L.c1, 4 * E, false, s));
+            PTRY(plan_alloc(P, (void **)&L.cm, 4 * E, false, s));
+            CUDA_TRY(cudaMemcpyAsync(first, hfirst.data(), 4 * nt, cudaMemcpyHostToDevice, s));
+            CUDA_TRY(cudaMemcpyAsync(L.tgt, tg.data(), 4 * tg.size(), cudaMemcpyHostToDevice, s));
+            CUDA_TRY(cudaMemcpyAsync(L.start, st.data(), 4 * st.size(), cudaMemcpyHostToDevice, s));
+            C.first = first;
+            C.e_src = L.src;
+            C.e_c1 = L.c1;
+            C.e_cm = L.cm;
+            CUDA_TRY(launch_close_pairs(C, P->kernel, P->ell, h, true, s));
+            CUDA_TRY(cudaStreamSynchronize(s)); // the host vectors above are read until here
+        }
+    }
     PTRY(plan_alloc(P, (void **)&P->status, 16, true, s));
 
     // constant tables the matvec kernels read, uploaded before any capture
@@ -615,6 +681,7 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
                             rows,    P->leaf_off, n,          D,  slots};
         CUDA_TRY(launch_p2p(pa, P->kernel, P->ell, P->side / (double)(1LL << D), nrhs, P->phi_near,
                             P->side_stream));
+        CUDA_TRY(launch_near_fix(P->close, P->sigma_s, n, nt, nrhs, P->phi_near, P->side_stream));
         if (tm)
             CUDA_TRY(cudaEventRecord(P->ev_p2p1, P->side_stream));
         CUDA_TRY(cudaEventRecord(P->ev_join, P->side_stream));
@@ -774,6 +841,7 @@ void bbfmm_default_opts(bbfmm_opts *o)
     o->max_nrhs = 1;
     o->split_accumulate = 1;
     o->use_graph = 1;
+    o->close_refine = 1;
 }
 
 const char *bbfmm_last_error(void) { return g_last_error.c_str(); }
@@ -874,6 +942,7 @@ static int plan_create(const double *points, int64_t n, const double *targets, i
     P->use_graph = opts.use_graph != 0;
     P->keep_coeffs = opts.keep_coefficients != 0;
     P->nodeset = opts.interp;
+    P->close_refine = opts.close_refine != 0;
     // the symmetric near field needs K(x, y) = K(y, x) (for a user kernel, as
     // registered) and one point set
     P->near_sym = opts.near_mode != BBFMM_NEAR_ORDERED && !targets && kernel_symmetric(kernel_id);
@@ -1108,6 +1177,8 @@ int bbfmm_plan_info(bbfmm_plan_t plan, bbfmm_info *info)
     info->max_leaf_points = plan->max_leaf;
     info->p2p_pairs = plan->p2p_pairs;
     info->m2l_pairs = plan->m2l_pairs;
+    info->close_pairs = (int)plan->close.nentries;
+    info->p2p_evals = plan->near_sym ? plan->p2p_sym_evals : plan->p2p_pairs;
     return BBFMM_OK;
 }
 

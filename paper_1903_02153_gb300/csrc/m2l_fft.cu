@@ -1,4 +1,4 @@
-// m2l_fft.cu -- far-field stage (Sec. 2.2 item 2) with equally spaced nodes
+// m2l_fft.cu -- far-field stage (Sec. 2.3 item 2) with equally spaced nodes
 // (Sec. 2.2 node sets): the M2L operator between two boxes is block-Toeplitz,
 // K^(t)_ij = c_t(i - j) per axis, so (Sec. 2.5 "Fast M2L translation")
 //     F^alpha = sum_{beta in I(alpha)} K^(t) M^beta

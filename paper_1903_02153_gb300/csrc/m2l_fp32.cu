@@ -1,4 +1,4 @@
-// m2l_fp32.cu -- far-field stage (Sec. 2.2 item 2) on the CUDA cores in FP32:
+// m2l_fp32.cu -- far-field stage (Sec. 2.3 item 2) on the CUDA cores in FP32:
 //   F~^alpha = scale_l * sum_{beta in I(alpha)} C^(t(alpha,beta)) M~^beta,
 // with the compressed operators C^(t) = U^T K^(t) V (Sec. 2.5 "Fast M2L
 // translation").  This is the plain-FP32 reference form of the stage; the

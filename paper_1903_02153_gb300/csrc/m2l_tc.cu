@@ -1,4 +1,4 @@
-// m2l_tc.cu -- far-field stage (Sec. 2.2 item 2) on the 5th-generation tensor
+// m2l_tc.cu -- far-field stage (Sec. 2.3 item 2) on the 5th-generation tensor
 // cores:  F~^alpha = scale_l * sum_{beta in I(alpha)} C^(t) M~^beta  with the
 // compressed operators C^(t) = U^T K^(t) V (Sec. 2.5 "Fast M2L translation").
 //

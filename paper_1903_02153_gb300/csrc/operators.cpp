@@ -8,7 +8,7 @@
 //  * Child-transfer matrices S_o[i][j] = l_i((s_j + 2o - 1)/2), o = 0 (lower
 //    half) or 1 (upper half): the node j of a child box, seen from its parent
 //    box, sits at (s_j + 2o - 1)/2.  M2M is M^parent = sum_children
-//    (S_ox (x) S_oy (x) S_oz) M^child, L2L its transpose (Sec. 2.2 items 1, 3).
+//    (S_ox (x) S_oy (x) S_oz) M^child, L2L its transpose (Sec. 2.3 items 1, 3).
 //  * M2L operators K^(t)_ij = K(x*_i, y*_j) for the 316 offsets t between a box
 //    and the members of its interaction list (Thm. 2.1 discussion), with the
 //    target box centred at 0 and the source box at t*h.

@@ -1,4 +1,4 @@
-// p2p_kernels.cuh -- the near-field kernels (Sec. 2.2 item 4), templated on
+// p2p_kernels.cuh -- the near-field kernels (Sec. 2.3 item 4), templated on
 // the kernel function.  Self-contained apart from morton.cuh: the library
 // compiles it with nvcc for the built-in kernels, and at run time with NVRTC
 // (its text is embedded at build time) for a user-supplied kernel.
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
                 const float4 d = nb_delta[k];
                 const float s = sg[src];
                 // staged negated so that x_target - y' is one packed add
-                const float x = -(u.x + d.x), y = -(u.y + d.y), z = -(u.z + d.z);
+                const float x = -__fadd_rn(u.x, d.x), y = -__fadd_rn(u.y, d.y), z = -__fadd_rn(u.z, d.z);
                 stage[g] = make_float4(x, x, y, y);
                 stage[kStageSrc + g] = make_float4(z, z, s, s);
             }
@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
             const float4 u = pts[src];
             const float4 d = nb_delta[k];
             const float s = sig[src];
-            const float x = -(u.x + d.x), y = -(u.y + d.y), z = -(u.z + d.z);
+            const float x = -__fadd_rn(u.x, d.x), y = -__fadd_rn(u.y, d.y), z = -__fadd_rn(u.z, d.z);
             stage[g] = make_float4(x, x, y, y);
             stage[kSymStage + g] = make_float4(z, z, s, s);
             if (gg >= nsym0) {
@@ -607,7 +607,8 @@ __global__ void __launch_bounds__(gemm_threads(TT))
                         src = nb_start[k] + (gg - nb_pre[k]);
                         const float4 u = spts[src];
                         const float4 d = nb_delta[k];
-                        p = make_float4(u.x + d.x, u.y + d.y, u.z + d.z, gg < nown ? 1.0f : 0.0f);
+                        p = make_float4(__fadd_rn(u.x, d.x), __fadd_rn(u.y, d.y), __fadd_rn(u.z, d.z),
+                                        gg < nown ? 1.0f : 0.0f);
                     }
                     sPos[tid] = p;
                     sSrc[tid] = src;
@@ -645,11 +646,12 @@ __global__ void __launch_bounds__(gemm_threads(TT))
 #pragma unroll 4
                     for (int sidx = tid / TT; sidx < kGemmS; sidx += SPLIT) {
                         const float4 y = sPos[sidx];
-                        const float dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z;
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        const float dx = __fsub_rn(x.x, y.x), dy = __fsub_rn(x.y, y.y), dz = __fsub_rn(x.z, y.z);
+                        const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
                         float K = 0.0f;
                         if (sidx < cnt && tv)
-                            K = y.w != 0.0f ? kern.one(r2, dx, dy, dz) : kern.far(r2 + kR2Floor, dx, dy, dz);
+                            K = y.w != 0.0f ? kern.one(r2, dx, dy, dz)
+                                            : kern.far(__fadd_rn(r2, kR2Floor), dx, dy, dz);
                         sK[sidx][t] = K;
                     }
                 }
@@ -680,6 +682,167 @@ __global__ void __launch_bounds__(gemm_threads(TT))
             }
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Close pairs (plan time).  The near-field kernels take x - y from FP32
+// leaf-local coordinates; each coordinate carries a rounding of up to
+// ~2^-25 cells, so a pair at distance r (cells) gets a relative error of
+// about 1e-7 / r in K.  For the singular kernels the few closest pairs of a
+// point set dominate the error of the whole near field (on clustered points
+// it exceeds 1e-5).  Pairs closer than 1/64 cell are therefore listed when
+// the plan is made, each with the coefficient
+//     c = K(x_i - y_j)  [FP64, from the caller's FP64 coordinates]
+//         - scale * K32(i, j)  [the FP32 value the near-field kernel adds],
+// and every matvec adds sum_j c sigma_j to the near field of target i
+// (k_near_fix), so the listed pairs enter the result as if evaluated in
+// FP64.  K32 is recomputed here with the same rounded operations as the
+// kernel that adds it (same frame, same operation order).  A point's pair
+// with itself and exact duplicates (c = 0 in both forms) are not listed.
+//
+// Frames: every near-field kernel evaluates a pair in the target leaf's
+// frame, except the symmetric one, where the value for target i in leaf A
+// and source j in leaf B != A comes from B's work item (B's frame, column
+// sums) when B precedes A in the 3x3x3 order and holds at most kSymMaxPoints
+// points.
+constexpr float kCloseR2 = 2.44140625e-4f; // (1/64 cell)^2
+
+struct CloseArgs {
+    const float4 *tpts;   // targets: leaf-local coordinates, tree order
+    const int4 *chunks;   // near-field work items over the target leaves
+    int nchunks;
+    const float4 *spts;   // sources: leaf-local coordinates, tree order
+    const int *soff;      // sources: leaf offsets
+    const double *tx;     // targets: FP64 coordinates, caller order (n x 3)
+    const int *tperm;     // target tree order -> caller order
+    const double *sx;     // sources: FP64 coordinates, caller order
+    const int *sperm;     // source tree order -> caller order
+    int D;
+    int same;             // the targets are the sources (skip i == j)
+    int sym;              // the one-RHS near field is the symmetric form
+    float scale;          // the near-field kernels write scale * sum K sigma
+    int *count;           // count pass: listed pairs per target (tree order)
+    const int *first;     // fill pass: first entry of each target
+    int *e_src;           // fill pass: source (tree order) of each entry
+    float *e_c1, *e_cm;   // fill pass: c for one RHS and for several RHS
+};
+
+// FP32 squared distances as the near-field kernels form them
+__device__ __forceinline__ float r2_rows(float dx, float dy, float dz, bool own)
+{ // k_p2p / k_p2p_sym: x first, the floor on the other 26 leaves
+    const float r2 = own ? __fmul_rn(dx, dx) : __fmaf_rn(dx, dx, kR2Floor);
+    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, r2));
+}
+__device__ __forceinline__ float r2_gemm(float dx, float dy, float dz, bool own)
+{ // k_p2p_gemm: z first, the floor added after
+    const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+    return own ? r2 : __fadd_rn(r2, kR2Floor);
+}
+
+// one block (kP2PThreads) per work item, a thread per target; the 27
+// neighbour leaves' sources are staged kStageSrc at a time.  FILL = false
+// counts the listed pairs of each target, FILL = true writes them from
+// first[target] on, in staging order (deterministic).
+template <class Kern, class Exact, bool FILL>
+__global__ void __launch_bounds__(kP2PThreads) k_close_pairs(const CloseArgs A, Kern kern, Exact exact)
+{
+    __shared__ float4 stage[kStageSrc]; // u + d of the source; w = its neighbour number (bits)
+    __shared__ int ssrc[kStageSrc];
+    __shared__ int nb_start[27], nb_cnt[27], nb_pre[28];
+    const int tid = threadIdx.x;
+    const int4 ch = A.chunks[blockIdx.x];
+    int ax, ay, az;
+    demorton3((unsigned)ch.x, ax, ay, az);
+    const int nside = 1 << A.D;
+    if (tid < 32) {
+        int cnt = 0, start = 0;
+        if (tid < 27) {
+            const int bx = ax + tid % 3 - 1, by = ay + (tid / 3) % 3 - 1, bz = az + tid / 9 - 1;
+            if (bx >= 0 && by >= 0 && bz >= 0 && bx < nside && by < nside && bz < nside) {
+                const unsigned nm = morton3((unsigned)bx, (unsigned)by, (unsigned)bz);
+                start = A.soff[nm];
+                cnt = A.soff[nm + 1] - start;
+            }
+            nb_start[tid] = start;
+            nb_cnt[tid] = cnt;
+        }
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (tid >= o)
+                incl += v;
+        }
+        if (tid < 28)
+            nb_pre[tid] = incl - cnt;
+    }
+    __syncthreads();
+    const int ns = nb_pre[27];
+    const bool act = tid < ch.z;
+    const int ti = ch.y + (act ? tid : 0);
+    const float4 X = A.tpts[ti];
+    const long long tc = A.tperm[ti];
+    const double x0 = A.tx[3 * tc], x1 = A.tx[3 * tc + 1], x2 = A.tx[3 * tc + 2];
+    int listed = 0, pos = FILL && act ? A.first[ti] : 0;
+    for (int base = 0; base < ns; base += kStageSrc) {
+        const int cnt = min(kStageSrc, ns - base);
+        int k = 0;
+        for (int g = tid; g < cnt; g += kP2PThreads) {
+            const int gg = base + g;
+            while (nb_pre[k + 1] <= gg)
+                ++k;
+            const int src = nb_start[k] + (gg - nb_pre[k]);
+            const float4 u = A.spts[src];
+            const float ox = (float)(k % 3 - 1), oy = (float)((k / 3) % 3 - 1), oz = (float)(k / 9 - 1);
+            stage[g] = make_float4(__fadd_rn(u.x, ox), __fadd_rn(u.y, oy), __fadd_rn(u.z, oz), __int_as_float(k));
+            ssrc[g] = src;
+        }
+        __syncthreads();
+        if (act) {
+            for (int j = 0; j < cnt; ++j) {
+                const float4 q = stage[j];
+                const int nid = __float_as_int(q.w);
+                const bool own = nid == 13;
+                const float dx = __fsub_rn(X.x, q.x), dy = __fsub_rn(X.y, q.y), dz = __fsub_rn(X.z, q.z);
+                const float r2 = r2_rows(dx, dy, dz, own);
+                if (!(r2 < kCloseR2))
+                    continue;
+                const int src = ssrc[j];
+                if (A.same && src == ti)
+                    continue;
+                // one RHS: the rows form, in the frame of the leaf that evaluates the pair
+                float K1;
+                if (A.sym && nid < 13 && nb_cnt[nid] <= kSymMaxPoints) {
+                    const float4 us = A.spts[src]; // the target seen from the source's leaf
+                    const float ox = (float)(1 - nid % 3), oy = (float)(1 - (nid / 3) % 3), oz = (float)(1 - nid / 9);
+                    const float ex = __fsub_rn(us.x, __fadd_rn(X.x, ox)), ey = __fsub_rn(us.y, __fadd_rn(X.y, oy)),
+                                ez = __fsub_rn(us.z, __fadd_rn(X.z, oz));
+                    K1 = kern.far(r2_rows(ex, ey, ez, false), ex, ey, ez);
+                } else {
+                    K1 = own ? kern.one(r2, dx, dy, dz) : kern.far(r2, dx, dy, dz);
+                }
+                // several RHS: k_p2p_gemm's form, the target's frame
+                const float rg = r2_gemm(dx, dy, dz, own);
+                const float Km = own ? kern.one(rg, dx, dy, dz) : kern.far(rg, dx, dy, dz);
+                const long long sc = A.sperm[src];
+                const double Kx = exact(x0 - A.sx[3 * sc], x1 - A.sx[3 * sc + 1], x2 - A.sx[3 * sc + 2]);
+                const float c1 = (float)(Kx - (double)A.scale * (double)K1);
+                const float cm = (float)(Kx - (double)A.scale * (double)Km);
+                if (c1 == 0.0f && cm == 0.0f)
+                    continue;
+                if (FILL) {
+                    A.e_src[pos] = src;
+                    A.e_c1[pos] = c1;
+                    A.e_cm[pos] = cm;
+                    ++pos;
+                } else {
+                    ++listed;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (!FILL && act)
+        A.count[ti] = listed;
 }
 
 } // namespace bbfmm

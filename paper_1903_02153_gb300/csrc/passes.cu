@@ -2,7 +2,7 @@
 // ONE launch over the boxes of level D-1 (one block per box and right-hand
 // side).
 //
-// Upward (Sec. 2.2 item 1, with the compression of Sec. 2.5 "Fast M2L
+// Upward (Sec. 2.3 item 1, with the compression of Sec. 2.5 "Fast M2L
 // translation"): a block makes the multipole coefficients of its 8 leaves
 // (P2M, Def. 2.2 applied to the sources), compresses them (M~ = V^T M),
 // combines them into its own box (M2M, the nested interpolation of Thm. 2.1
@@ -12,7 +12,7 @@
 // sibling coefficient sets, makes and compresses the parent's, and counts
 // itself in one level up, down to level 2.  No block waits for another.
 //
-// Downward (Sec. 2.2 item 3): a block makes the local coefficients of its
+// Downward (Sec. 2.3 item 3): a block makes the local coefficients of its
 // box (decompress F = U F~, plus the L2L of its parent's), spreads them to
 // its 8 leaves (L2L), adds the leaves' decompressed far fields and evaluates
 // them at the leaves' points (L2P).  The levels above come from a first,
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(kThreads, kUpMinBlocks<P>) k_upward(const __gr
     const int s0 = A.off[leaf], s1 = A.off[leaf + 1];
     const bool zero = __syncthreads_count(s1 > s0) == 0;
 
-    // ---- P2M: warp w makes M of leaf 8b + w (Sec. 2.2 item 1, Def. 2.2)
+    // ---- P2M: warp w makes M of leaf 8b + w (Sec. 2.3 item 1, Def. 2.2)
     {
         float acc[NQ][P];
 #pragma unroll
@@ -608,7 +608,7 @@ __global__ void __launch_bounds__(kThreads) k_downward(const __grid_constant__ P
             A.F[D][((8 * b + o) * A.nrhs + c) * P3 + r] = sMT[q];
         }
 
-    // ---- L2P: warp w evaluates leaf 8b + w at its targets (Sec. 2.2 item 3)
+    // ---- L2P: warp w evaluates leaf 8b + w at its targets (Sec. 2.3 item 3)
     const int64_t leaf = 8 * b + w;
     const int s0 = A.toff[leaf], s1 = A.toff[leaf + 1];
     for (int c0 = s0; c0 < s1; c0 += 32) {

@@ -14,7 +14,10 @@
 // The array, g_sort_scratch, holds kStaticSortMaxPoints points' worth of
 // scratch (about 13.6 MB) and stays resident on every GPU that loads this
 // library until the process exits.  Its device address is looked up once per
-// device, with that device current, on the first call made on that device.
+// device, with that device current, on the first call made on that device,
+// and kept (a cudaDeviceReset would invalidate it: calls after a reset of the
+// device are not supported).  Pointers must be memory of the current device
+// (or managed): the kernels read and write them from that device.
 #include <mutex>
 
 #include "bbfmm_internal.h"
@@ -63,6 +66,9 @@ extern "C" int bbfmm_sort_points_static(const double *points, int64_t n, int dep
         return BBFMM_EINVAL;
     if (n < 1 || n > kStaticSortMaxPoints || depth < 0 || depth > kMaxDepth || !(side > 0.0))
         return BBFMM_EINVAL;
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess)
+        return BBFMM_ECUDA;
     for (const void *p : {(const void *)points, (const void *)perm, (const void *)leaf_off}) {
         cudaPointerAttributes a;
         if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -71,6 +77,8 @@ extern "C" int bbfmm_sort_points_static(const double *points, int64_t n, int dep
         }
         if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
             return BBFMM_EINVAL; // no host staging: that would need an allocation
+        if (a.type == cudaMemoryTypeDevice && a.device != cur)
+            return BBFMM_EINVAL; // another GPU's memory: the kernels run on the current device
     }
     if (radix_sort_scratch_ints(n) > kStaticRadixInts)
         return BBFMM_EINTERNAL;

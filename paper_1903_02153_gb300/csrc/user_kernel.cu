@@ -69,6 +69,7 @@ struct UserKernel {
     int homogeneity = 0, symmetric = 0;
     cudaLibrary_t lib = nullptr;
     cudaKernel_t eval = nullptr, p2p = nullptr, p2p_multi = nullptr, p2p_sym = nullptr;
+    cudaKernel_t close_count = nullptr, close_fill = nullptr; // k_close_pairs, both passes
 };
 
 std::mutex g_mu;
@@ -83,6 +84,9 @@ struct KUser { // d in cell units; h = leaf box side
     float h;
     __device__ float one(float, float dx, float dy, float dz) const { return bbfmm_kernel_f32(h * dx, h * dy, h * dz); }
     __device__ float far(float, float dx, float dy, float dz) const { return bbfmm_kernel_f32(h * dx, h * dy, h * dz); }
+};
+struct KUserExact { // d in the caller's units
+    __device__ double operator()(double d0, double d1, double d2) const { return bbfmm_kernel_f64(d0, d1, d2); }
 };
 } // namespace bbfmm
 extern "C" __global__ void bbfmm_user_eval(const double *d, long long n, double *out)
@@ -127,9 +131,13 @@ int user_kernel_register(const char *source, int homogeneity, int symmetric, int
     }
     const char *p2p_name = "bbfmm::k_p2p<bbfmm::KUser>", *multi_name = "bbfmm::k_p2p_gemm<bbfmm::KUser, 32>",
                *sym_name = "bbfmm::k_p2p_sym<bbfmm::KUser>";
+    const char *count_name = "bbfmm::k_close_pairs<bbfmm::KUser, bbfmm::KUserExact, false>",
+               *fill_name = "bbfmm::k_close_pairs<bbfmm::KUser, bbfmm::KUserExact, true>";
     nv.add_name(prog, p2p_name);
     nv.add_name(prog, multi_name);
     nv.add_name(prog, sym_name);
+    nv.add_name(prog, count_name);
+    nv.add_name(prog, fill_name);
     const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-default-device"};
     const nvrtcResult rc = nv.compile(prog, 3, opts);
     size_t log_size = 0;
@@ -146,12 +154,16 @@ int user_kernel_register(const char *source, int homogeneity, int symmetric, int
     nv.cubin_size(prog, &cubin_size);
     std::vector<char> cubin(cubin_size);
     nv.cubin(prog, cubin.data());
-    const char *p2p_low = nullptr, *multi_low = nullptr, *sym_low = nullptr;
+    const char *p2p_low = nullptr, *multi_low = nullptr, *sym_low = nullptr, *count_low = nullptr,
+               *fill_low = nullptr;
     nv.lowered(prog, p2p_name, &p2p_low);
     nv.lowered(prog, multi_name, &multi_low);
     nv.lowered(prog, sym_name, &sym_low);
+    nv.lowered(prog, count_name, &count_low);
+    nv.lowered(prog, fill_name, &fill_low);
     const std::string p2p_sym = p2p_low ? p2p_low : "", multi_sym = multi_low ? multi_low : "",
-                      pair_sym = sym_low ? sym_low : "";
+                      pair_sym = sym_low ? sym_low : "", count_sym = count_low ? count_low : "",
+                      fill_sym = fill_low ? fill_low : "";
     nv.destroy(&prog);
     UserKernel k;
     k.homogeneity = homogeneity;
@@ -165,6 +177,10 @@ int user_kernel_register(const char *source, int homogeneity, int symmetric, int
         e = cudaLibraryGetKernel(&k.p2p_multi, k.lib, multi_sym.c_str());
     if (e == cudaSuccess)
         e = cudaLibraryGetKernel(&k.p2p_sym, k.lib, pair_sym.c_str());
+    if (e == cudaSuccess)
+        e = cudaLibraryGetKernel(&k.close_count, k.lib, count_sym.c_str());
+    if (e == cudaSuccess)
+        e = cudaLibraryGetKernel(&k.close_fill, k.lib, fill_sym.c_str());
 
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -259,6 +275,23 @@ cudaError_t launch_p2p_user(const P2PArgs &A, int id, double h, int nrhs, float 
         return cudaLaunchKernel((const void *)k.p2p, dim3((unsigned)A.nchunks), dim3(kP2PThreads), args, 0, s);
     return cudaLaunchKernel((const void *)k.p2p_multi, dim3((unsigned)A.nchunks), dim3(gemm_threads(kGemmT)), args, 0,
                             s);
+}
+
+cudaError_t launch_close_pairs_user(const CloseArgs &A, int id, double h, bool fill, cudaStream_t s)
+{
+    UserKernel k;
+    if (!user_kernel_get(id, k))
+        return cudaErrorInvalidValue;
+    CloseArgs B = A;
+    B.scale = 1.0f; // KUser returns K in the caller's units
+    struct {
+        float h;
+    } kern = {(float)h};
+    struct {
+    } exact;
+    void *args[] = {(void *)&B, (void *)&kern, (void *)&exact};
+    return cudaLaunchKernel((const void *)(fill ? k.close_fill : k.close_count), dim3((unsigned)A.nchunks),
+                            dim3(kP2PThreads), args, 0, s);
 }
 
 } // namespace bbfmm

@@ -1,0 +1,174 @@
+"""Close near-field pairs (Sec. 2.3 near field; error measure of Sec. 4.1).
+
+The near-field kernels form x - y from FP32 leaf-local coordinates, so a pair
+at distance r (in leaf box sides) carries a relative error of about 1e-7 / r.
+For the singular kernels the closest pairs of a point set then dominate the
+error of the whole result.  A plan lists the pairs closer than 1/64 box side
+with FP64 correction coefficients, and every matvec adds them after the near
+field (``opts.close_refine``, on by default).  These tests check:
+
+* the clustered 1/r sets where the FP32 coordinates alone miss the 1e-5 gate
+  (2.0e-5 at depth 5, 8.9e-5 at depth 6) meet it with the correction, and
+  fail it without (the mechanism, not a tolerance);
+* exact duplicates (K(0) = 0 for the singular kernels) and distinct points
+  that coincide in FP32, in one leaf and across a leaf face, element by
+  element against the FP64 direct sum, in every near-field form (symmetric,
+  ordered, several right-hand sides);
+* separate target sets and a registered user kernel take the same path.
+"""
+import numpy as np
+import pytest
+
+from paper_1903_02153_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+K_INV_R, K_INV_R2, K_EXP = 1, 2, 3
+UNIT = (W.UNIT_LO, W.UNIT_SIDE)
+
+
+@pytest.fixture(scope="module")
+def bb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1903_02153_gb300 import build
+    build.build()
+    from paper_1903_02153_gb300 import bbfmm
+    bbfmm.lib()
+    return bbfmm
+
+
+def run(bb, pts, sig, kid, p, depth, ell=1.0, eps=1e-7, near="auto", refine=True, precision="fp32",
+        targets=None):
+    dev = torch.device("cuda:0")
+    sig = np.asarray(sig, dtype=np.float32)
+    nrhs = 1 if sig.ndim == 1 else sig.shape[1]
+    plan = bb.Plan(torch.from_numpy(np.ascontiguousarray(pts)).to(dev), kid, p, depth, ell=ell, svd_eps=eps,
+                   precision=precision, domain=UNIT, max_nrhs=nrhs, near_mode=near, close_refine=refine,
+                   targets=None if targets is None else torch.from_numpy(targets).to(dev))
+    s = torch.from_numpy(np.ascontiguousarray(sig.T if nrhs > 1 else sig)).to(dev)
+    phi = plan.matvec(s)
+    torch.cuda.synchronize()
+    info = plan.info()
+    assert bb.bbfmm_status(plan.handle) == 0
+    plan.close()
+    out = phi.cpu().numpy().astype(np.float64)
+    return (out.T if nrhs > 1 else out), info
+
+
+@pytest.mark.parametrize("depth", [5, 6])
+def test_clustered_inverse_r_meets_gate_with_close_pairs(bb, oracle, depth):
+    n = 12_000
+    pts = W.clustered_points(n, seed=45)
+    sig = W.uniform_sigma(n, seed=46).astype(np.float32)
+    ref = oracle.bbfmm(pts, sig.astype(np.float64), K_INV_R, 3, depth, lo=W.UNIT_LO, side=W.UNIT_SIDE)
+    on, info = run(bb, pts, sig, K_INV_R, 3, depth, eps=0.0)
+    off, info_off = run(bb, pts, sig, K_INV_R, 3, depth, eps=0.0, refine=False)
+    e_on, e_off = oracle.rel_err(on, ref), oracle.rel_err(off, ref)
+    print("clustered 1/r depth %d: %d close pairs; vs oracle %.2e (FP32 coordinates alone %.2e)"
+          % (depth, info.close_pairs, e_on, e_off))
+    assert 0 < info.close_pairs < n and info_off.close_pairs == 0
+    assert e_on <= 2e-6
+    assert e_off > 1e-5   # the FP32-coordinate error the correction removes
+
+
+def coincident_set(n, seed):
+    """Uniform points plus: exact duplicates; pairs 1e-13 .. 1e-7 apart inside
+    one leaf and across the faces x = 1/2 and y = 1/4 (leaf faces from depth
+    1 and 2 on), both points of a pair distinct in FP64."""
+    rng = np.random.default_rng(seed)
+    base = rng.random((n, 3))
+    extra = [base[rng.choice(n, 20, replace=False)]]           # exact duplicates
+    for a in (1e-13, 1e-11, 1e-9, 1e-7):
+        q = rng.random((3, 3)) * 0.4 + 0.05
+        extra.append(q)
+        extra.append(q + np.array([a, 0.0, 0.0]))               # same leaf
+        f = rng.random((2, 3))
+        f[:, 0] = 0.5
+        extra.append(f - np.array([a, 0.0, 0.0]))               # across x = 1/2
+        extra.append(f + np.array([a, 0.0, 0.0]))
+        g = rng.random((2, 3))
+        g[:, 1] = 0.25
+        extra.append(g - np.array([0.0, a, 0.0]))               # across y = 1/4
+        extra.append(g + np.array([0.0, a * 0.5, 0.0]))
+    pts = np.concatenate([base] + extra)
+    return pts[rng.permutation(pts.shape[0])]
+
+
+@pytest.mark.parametrize("kid", [K_INV_R, K_INV_R2])
+@pytest.mark.parametrize("near,nrhs", [("symmetric", 1), ("ordered", 1), ("auto", 3)])
+@pytest.mark.parametrize("depth", [0, 1, 2])
+def test_coincident_points_element_by_element(bb, oracle, kid, near, nrhs, depth):
+    """Depth 0..2 with a small order: at depth 0 / 1 the result is the near
+    field alone, equal to the FP64 direct sum; at depth 2 the far field adds
+    its approximation (checked against the oracle FMM).  Element-wise bound:
+    |phi_gpu - phi_ref| <= 1e-5 sum_j |K_ij sigma_j| per target (the row's
+    own scale: the close pairs make some rows ~1e13 times the others)."""
+    pts = coincident_set(2500, seed=900 + depth)
+    n = pts.shape[0]
+    sig = W.uniform_sigma(n, nrhs=nrhs, seed=901).astype(np.float32).astype(np.float64)
+    got, info = run(bb, pts, sig, kid, 4, depth, eps=0.0, near=near)
+    if depth <= 1:
+        ref = oracle.direct(pts, pts, sig, kid)
+    else:
+        ref = oracle.bbfmm(pts, sig, kid, 4, depth, lo=W.UNIT_LO, side=W.UNIT_SIDE)
+    scale = oracle.direct(pts, pts, np.abs(sig), kid)        # sum_j |K_ij| |sigma_j|: K > 0
+    err = np.abs(got - ref) / scale
+    print("k%d %s nrhs %d depth %d: %d close pairs, max row error %.2e"
+          % (kid, near, nrhs, depth, info.close_pairs, err.max()))
+    assert info.close_pairs > 0
+    assert err.max() <= 1e-5
+
+
+def test_separate_targets_close_to_sources(bb, oracle):
+    """Targets placed 1e-12 .. 1e-8 from sources (and some on them exactly:
+    K = 0 there for 1/r), across leaf faces too: the pairs between the two
+    sets are listed in the targets' frame."""
+    rng = np.random.default_rng(910)
+    src = rng.random((6000, 3))
+    near = src[rng.choice(6000, 400, replace=False)]
+    off = rng.choice([0.0, 1e-12, 1e-10, 1e-8], size=(400, 1)) * rng.standard_normal((400, 3))
+    tgt = np.clip(np.concatenate([near + off, rng.random((1600, 3))]), 0.0, 1.0)
+    sig = W.uniform_sigma(6000, seed=911).astype(np.float32).astype(np.float64)
+    got, info = run(bb, src, sig, K_INV_R, 4, 3, eps=0.0, targets=tgt)
+    ref = oracle.bbfmm_targets(src, sig, tgt, K_INV_R, 4, 3, lo=W.UNIT_LO, side=W.UNIT_SIDE)
+    scale = oracle.direct(tgt, src, np.abs(sig), K_INV_R)
+    err = np.abs(got - ref) / scale
+    print("separate targets: %d close pairs, max row error %.2e, rel %.2e"
+          % (info.close_pairs, err.max(), oracle.rel_err(got, ref)))
+    assert info.close_pairs > 0
+    assert err.max() <= 1e-5
+
+
+def test_user_kernel_close_pairs(bb, oracle):
+    """A caller-registered 1/r (homogeneous of degree -1) on the clustered set
+    at depth 6: its close pairs are corrected with the caller's FP64 function."""
+    src = """
+    __device__ double bbfmm_kernel_f64(double d0, double d1, double d2)
+    { double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2); return r > 0.0 ? 1.0 / r : 0.0; }
+    __device__ float bbfmm_kernel_f32(float d0, float d1, float d2)
+    { float r2 = d0 * d0 + d1 * d1 + d2 * d2; return r2 > 0.0f ? rsqrtf(r2) : 0.0f; }
+    """
+    kid = bb.bbfmm_kernel_register(src, homogeneity=-1, symmetric=True)
+    n = 12_000
+    pts = W.clustered_points(n, seed=45)
+    sig = W.uniform_sigma(n, seed=46).astype(np.float32)
+    ref = oracle.bbfmm(pts, sig.astype(np.float64), K_INV_R, 3, 6, lo=W.UNIT_LO, side=W.UNIT_SIDE)
+    for near in ("symmetric", "ordered"):
+        got, info = run(bb, pts, sig, kid, 3, 6, eps=0.0, near=near)
+        e = oracle.rel_err(got, ref)
+        print("user 1/r %s: %d close pairs, vs oracle %.2e" % (near, info.close_pairs, e))
+        assert info.close_pairs > 0
+        assert e <= 2e-6
+
+
+def test_smooth_kernel_unchanged_by_refinement(bb):
+    """exp(-r/ell) has no singularity: the corrections are at FP32 rounding
+    level, so both settings agree to ~1e-7."""
+    n = 20_000
+    pts = W.clustered_points(n, seed=912)
+    sig = W.uniform_sigma(n, seed=913).astype(np.float32)
+    a, _ = run(bb, pts, sig, K_EXP, 4, 4, ell=0.3)
+    b, _ = run(bb, pts, sig, K_EXP, 4, 4, ell=0.3, refine=False)
+    assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-6

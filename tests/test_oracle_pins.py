@@ -2,7 +2,7 @@
 
 Each test ties the oracle to something other than itself: numpy / scipy
 routines, closed forms, identities that hold exactly (depth 0/1 FMM == direct
-sum, Sec. 2.2 with Def. 2.1; polynomial reproduction of the interpolant,
+sum, Sec. 2.3 with Def. 2.1; polynomial reproduction of the interpolant,
 Def. 2.2 / Eq. low-rank-form), the counts of Def. 2.1, symmetry of the
 approximation for a symmetric kernel, invariances, and the exponential error
 decay in p claimed in Sec. 2.2 and Sec. 4.1.  test_oracle_mutations.py shows
@@ -125,7 +125,7 @@ def test_neighbor_and_interaction_counts(oracle):
 def test_interaction_partition_bruteforce(oracle):
     """Every (target leaf, source leaf) pair is handled exactly once: by P2P if
     the leaves are adjacent, else by exactly one M2L between ancestors at one
-    level (Fig. 2 caption; Sec. 2.2 closing paragraph)."""
+    level (Fig. 2 caption; Sec. 2.3)."""
     D = 3
     n = 2 ** D
     ilists = {}
@@ -151,7 +151,7 @@ def test_leaf_binning_rule(oracle):
     np.testing.assert_array_equal(cells, [[0, 0, 0], [7, 7, 7], [4, 2, 1], [0, 7, 4]])
 
 
-# --- the FMM (Sec. 2.2) ------------------------------------------------------
+# --- the FMM (Sec. 2.3) ------------------------------------------------------
 
 @pytest.mark.parametrize("depth", [0, 1])
 @pytest.mark.parametrize("kid", [K_INV_R, K_EXP])
