@@ -61,10 +61,11 @@ extern "C" {
                                     an inverse DFT per box; FP32; no compression */
 
 /* near-field evaluation order (Sec. 2.5, symmetry of the kernel) */
-#define BBFMM_NEAR_AUTO 0      /* SYMMETRIC where it applies and the near-field pairs
-                                  per point / 27 (the occupancy of the leaves the work
-                                  meets) is 16 to 48, where it was measured to be
-                                  faster; otherwise ORDERED (default) */
+#define BBFMM_NEAR_AUTO 0      /* where SYMMETRIC applies, the faster order: measured
+                                  by the autotuner (opts.autotune), else SYMMETRIC
+                                  when the near-field pairs per point / 27 (the
+                                  occupancy of the leaves the work meets) is 16 to
+                                  48; otherwise ORDERED (default) */
 #define BBFMM_NEAR_ORDERED 1   /* every target leaf evaluates all its neighbour pairs */
 #define BBFMM_NEAR_SYMMETRIC 2 /* symmetric kernel, targets = sources, one right-hand
                                   side: each pair of neighbour leaves is evaluated once
@@ -114,7 +115,11 @@ typedef struct {
                           correction coefficients (a few bytes per pair); each matvec
                           adds them in one small launch after the near field.
                           0: the FP32 values only */
-    int reserved[1];   /* zero */
+    int autotune;      /* 1 (default): the first matvec with a given nrhs measures
+                          the launch choices of bbfmm_tuning (bbfmm_autotune) and
+                          keeps the fastest; the choice is cached per process for
+                          plans of the same shape.  0: the defaults of
+                          bbfmm_tuning, and near_mode AUTO by leaf occupancy */
 } bbfmm_opts;
 
 typedef struct {
@@ -139,6 +144,24 @@ typedef struct {
                            p2p_pairs, or about half of it with the symmetric form */
     int reserved[2];
 } bbfmm_info;
+
+/*
+ * Launch choices of a plan, per nrhs (they change how the work is cut into
+ * launches, never what is computed; results of different choices differ by
+ * FP32 rounding only).  Sec. 2.5 "Multiple right-hand-sides": the work of a
+ * launch grows with nrhs, and the fastest choice moves with it.
+ */
+typedef struct {
+    int near_mode;  /* BBFMM_NEAR_ORDERED or BBFMM_NEAR_SYMMETRIC: the near-field
+                       order of one-RHS matvecs (several-RHS ones are ordered) */
+    int m2l_tile;   /* targets per tile of the tensor-core M2L: 128, or 256 with
+                       BBFMM_PREC_FP16X3 / BF16X3 (the default there) */
+    int m2l_stages; /* pipeline stages of the tensor-core M2L: 0 = as many as fit
+                       in shared memory (default), else 2 up to that */
+    int measured;   /* bbfmm_get_tuning: 1 if chosen by a measured sweep (or its
+                       cache); ignored by bbfmm_set_tuning */
+    int reserved[4];
+} bbfmm_tuning;
 
 /*
  * bbfmm_kernel_register: a kernel function supplied by the caller (the
@@ -274,12 +297,39 @@ int bbfmm_get_leaf_cells(bbfmm_plan_t plan, int32_t *out);
 /*
  * bbfmm_stage_times: device milliseconds of each stage of the last matvec,
  * measured with CUDA events on the matvec's streams when the plan was built
- * with timing on (see bbfmm_set_timing).  out[0..7] = gather, upward (P2M +
+ * with timing on (see bbfmm_set_timing).  With timing on, the near field
+ * starts after the far field instead of beside it, so each stage's time is
+ * that stage alone (and the whole matvec is their sum).  out[0..7] = gather, upward (P2M +
  * M2M + compress), M2L, downward (decompress + L2L + L2P, one launch), L2P
  * (0: part of the downward launch), P2P, combine, whole matvec.
  * Synchronizes the device.
  */
 int bbfmm_stage_times(bbfmm_plan_t plan, float *out);
+
+/*
+ * bbfmm_get_tuning: the launch choices matvecs with nrhs right-hand sides
+ * use (or will use: the defaults, before the first such matvec of a plan with
+ * opts.autotune).  bbfmm_set_tuning: use these instead (EINVAL when the plan
+ * cannot run them: SYMMETRIC without a symmetric kernel and one point set, or
+ * with nrhs > 1, or when the plan was built with near_mode ORDERED, or without
+ * autotune and AUTO chose ORDERED; a tile size the precision does not have;
+ * more stages than fit).  Setting drops the matvec graph of that nrhs; the
+ * call synchronizes the device.  Errors: EINVAL, EBUSY.
+ */
+int bbfmm_get_tuning(bbfmm_plan_t plan, int nrhs, bbfmm_tuning *out);
+int bbfmm_set_tuning(bbfmm_plan_t plan, int nrhs, const bbfmm_tuning *tuning);
+
+/*
+ * bbfmm_autotune: measure the launch choices for nrhs now and keep the
+ * fastest (also refreshing the process-wide cache).  Candidates: both
+ * near-field orders (one RHS, near_mode AUTO, symmetric kernel, one point
+ * set), every M2L tile size of the precision, every M2L pipeline depth that
+ * fits.  Each runs 1 + 3 matvecs with zero weights in the plan's own buffers
+ * (allocating 4 (n + nt) max_nrhs bytes of staging on first use); the fastest
+ * mean device time wins.  Synchronizes the device and `stream`.
+ * Errors: EINVAL, EBUSY, ENOMEM, ECUDA.
+ */
+int bbfmm_autotune(bbfmm_plan_t plan, int nrhs, void *stream);
 
 /* Turn per-stage event timing on (1) or off (0) for later matvecs. */
 int bbfmm_set_timing(bbfmm_plan_t plan, int on);

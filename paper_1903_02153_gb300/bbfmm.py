@@ -34,7 +34,8 @@ PRECISIONS = {"fp32": BBFMM_PREC_FP32, "tf32": BBFMM_PREC_TF32, "tf32x3": BBFMM_
 EXPORTED = ["bbfmm_default_opts", "bbfmm_plan", "bbfmm_matvec", "bbfmm_destroy",
             "bbfmm_last_error", "bbfmm_plan_info", "bbfmm_get_coefficients",
             "bbfmm_get_leaf_cells", "bbfmm_stage_times", "bbfmm_set_timing", "bbfmm_status",
-            "bbfmm_sort_points_static", "bbfmm_rand_eig", "bbfmm_plan_targets", "bbfmm_kernel_register"]
+            "bbfmm_sort_points_static", "bbfmm_rand_eig", "bbfmm_plan_targets", "bbfmm_kernel_register",
+            "bbfmm_get_tuning", "bbfmm_set_tuning", "bbfmm_autotune"]
 
 
 class bbfmm_opts(ctypes.Structure):
@@ -44,7 +45,12 @@ class bbfmm_opts(ctypes.Structure):
                 ("max_nrhs", ctypes.c_int), ("split_accumulate", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("keep_coefficients", ctypes.c_int),
                 ("interp", ctypes.c_int), ("near_mode", ctypes.c_int), ("close_refine", ctypes.c_int),
-                ("reserved", ctypes.c_int * 1)]
+                ("autotune", ctypes.c_int)]
+
+
+class bbfmm_tuning(ctypes.Structure):
+    _fields_ = [("near_mode", ctypes.c_int), ("m2l_tile", ctypes.c_int), ("m2l_stages", ctypes.c_int),
+                ("measured", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class bbfmm_info(ctypes.Structure):
@@ -108,6 +114,12 @@ def lib():
             L.bbfmm_plan_targets.restype = i32
             L.bbfmm_kernel_register.argtypes = [ctypes.c_char_p, i32, i32, ctypes.POINTER(i32)]
             L.bbfmm_kernel_register.restype = i32
+            L.bbfmm_get_tuning.argtypes = [vp, i32, ctypes.POINTER(bbfmm_tuning)]
+            L.bbfmm_get_tuning.restype = i32
+            L.bbfmm_set_tuning.argtypes = [vp, i32, ctypes.POINTER(bbfmm_tuning)]
+            L.bbfmm_set_tuning.restype = i32
+            L.bbfmm_autotune.argtypes = [vp, i32, vp]
+            L.bbfmm_autotune.restype = i32
             _lib = L
     return _lib
 
@@ -255,6 +267,25 @@ def bbfmm_rand_eig(plan, omega, k, power=0, vectors=True, stream=None):
     return evals, evecs
 
 
+def bbfmm_get_tuning(plan, nrhs=1) -> bbfmm_tuning:
+    t = bbfmm_tuning()
+    _check(lib().bbfmm_get_tuning(plan, int(nrhs), ctypes.byref(t)))
+    return t
+
+
+def bbfmm_set_tuning(plan, nrhs, near_mode, m2l_tile, m2l_stages=0):
+    """near_mode: "ordered" / "symmetric" (or the BBFMM_NEAR_* value)."""
+    t = bbfmm_tuning()
+    t.near_mode = NEAR_MODES[near_mode] if isinstance(near_mode, str) else int(near_mode)
+    t.m2l_tile = int(m2l_tile)
+    t.m2l_stages = int(m2l_stages)
+    return _check(lib().bbfmm_set_tuning(plan, int(nrhs), ctypes.byref(t)))
+
+
+def bbfmm_autotune(plan, nrhs=1, stream=None):
+    return _check(lib().bbfmm_autotune(plan, int(nrhs), _stream(stream)))
+
+
 def _check_plain(st):
     # entry points that report only a status code (no message)
     if st != BBFMM_OK:
@@ -274,13 +305,14 @@ class Plan:
     def __init__(self, points, kernel, order, depth, ell=1.0, svd_eps=1e-7, precision="fp32",
                  domain=None, max_nrhs=1, stream=None, split_accumulate=True, use_graph=True,
                  keep_coefficients=False, targets=None, interp="chebyshev", near_mode="auto",
-                 close_refine=True):
+                 close_refine=True, autotune=True):
         import torch
         o = bbfmm_default_opts()
         o.split_accumulate = 1 if split_accumulate else 0
         o.use_graph = 1 if use_graph else 0
         o.keep_coefficients = 1 if keep_coefficients else 0
         o.close_refine = 1 if close_refine else 0
+        o.autotune = 1 if autotune else 0
         o.interp = INTERPS[interp] if isinstance(interp, str) else int(interp)
         o.near_mode = NEAR_MODES[near_mode] if isinstance(near_mode, str) else int(near_mode)
         o.ell = float(ell)

@@ -25,6 +25,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -166,7 +167,17 @@ struct CloseList {
     int *tgt = nullptr;             // [ntgt] target (tree order)
     int *start = nullptr;           // [ntgt + 1] first entry of each
     int *src = nullptr;             // [nentries] source (tree order)
-    float *c1 = nullptr, *cm = nullptr; // [nentries] coefficient for one RHS / several RHS
+    float *c1 = nullptr;            // [nentries] coefficient, one RHS, ordered near field
+    float *c1s = nullptr;           // [nentries] coefficient, one RHS, symmetric near field (or null)
+    float *cm = nullptr;            // [nentries] coefficient, several RHS
+};
+
+// the launch choices the autotuner measures (bbfmm_tuning in the header)
+struct Tuning {
+    bool near_sym = false; // one-RHS near field in symmetric order
+    int m2l_nt = 128;      // targets per tensor-core M2L tile
+    int m2l_stages = 0;    // tensor-core M2L pipeline stages (0 = as many as fit)
+    bool measured = false; // chosen by a measured sweep (or its cache)
 };
 
 struct Stage { // indices into Plan::ev
@@ -205,7 +216,9 @@ struct bbfmm_plan_impl {
     float *sigma_s = nullptr, *phi_far = nullptr, *phi_near = nullptr;
     float *sigma_rows = nullptr;                  // max_nrhs > 1: sigma_s row-major, for the near field
     bool near_sym = false;                        // near field evaluated pairwise both ways (one RHS)
-    bool near_auto = false;                       // near_sym chosen from the leaf occupancy
+    bool near_auto = false;                       // near_sym chosen (occupancy band, or the autotuner)
+    bool near_sym_ok = false;                     // the symmetric form applies (kernel, one point set)
+    bool near_sym_default = false;                // near_sym before any tuning (mode, occupancy band)
     float *near_slots = nullptr;                  // symmetric near field: 13 x n column sums (zeroed at plan time)
     bool close_refine = true; // list the near field's close pairs with FP64 corrections
     CloseList close;
@@ -219,9 +232,22 @@ struct bbfmm_plan_impl {
     // upward pass: arrival counters of the boxes of levels 2..D-2 (x max_nrhs),
     // zero between matvecs
     int *up_count[kMaxDepth + 1] = {};
-    // tensor-core M2L: the tiles with occupied targets (device), per level
+    // tensor-core M2L: the tiles with occupied targets (device), per level,
+    // for the tile size in use (m2l_nt) ...
     int4 *m2l_tiles = nullptr;
     int m2l_ntiles[kMaxDepth + 1] = {}, m2l_tile_off[kMaxDepth + 1] = {};
+    int m2l_nt = 128, m2l_stages = 0;
+    // ... and for every tile size the precision allows (the tuner's choices)
+    struct TileSet {
+        int nt = 0, groups = 1;
+        int4 *tiles = nullptr;
+        int ntiles[kMaxDepth + 1] = {}, off[kMaxDepth + 1] = {};
+    };
+    TileSet m2l_set[2];
+    int m2l_nsets = 0;
+    // launch choices per nrhs: set by bbfmm_set_tuning or the autotuner
+    bool autotune = false;
+    std::map<int, Tuning> tuning;
     bool keep_coeffs = false; // also store leaf M and every level's F
     // Fourier-domain M2L: the 8^3-box tiles holding targets, per level
     int4 *fft_tiles = nullptr;
@@ -345,11 +371,16 @@ void fft_active_tiles(int D, const std::vector<uint8_t> &leaf_occ, std::vector<i
 int64_t fft_grid_boxes(int l); // boxes of the zero-padded M^ grid of level l
 // m2l_tc.cu: every level of the far field in one go (FP32 or tensor cores)
 cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s);
-int m2l_groups_for(int D, int nrhs, int precision, int r, const int *ntiles, const std::vector<int> &rl);
-// the tensor-core M2L tiles that hold at least one occupied target box, level
-// by level from D down to 2, as {tx, ty, tz, octant}; count[l] per level
-void m2l_active_tiles(int D, int precision, const std::vector<uint8_t> &leaf_occ, std::vector<int4> &tiles,
-                      int *count);
+int m2l_groups_for(int D, int nrhs, int precision, int nt, int r, const int *ntiles, const std::vector<int> &rl);
+// the tensor-core M2L tiles of nt targets that hold at least one occupied
+// target box, level by level from D down to 2, as {tx, ty, tz, octant};
+// count[l] per level
+void m2l_active_tiles(int D, int nt, const std::vector<uint8_t> &leaf_occ, std::vector<int4> &tiles, int *count);
+// tile sizes (targets per tile) the tensor-core M2L runs for a precision,
+// the default first; returns how many
+int m2l_tile_choices(int precision, int *nt);
+// pipeline stages that fit in shared memory for a precision and tile size
+int m2l_max_stages(int precision, int nt);
 // p2p.cu
 // targets: tree-order coordinates and the work items over their leaves;
 // sources: tree-order coordinates, weights (ns x nrhs) and leaf offsets
@@ -375,8 +406,9 @@ cudaError_t launch_p2p_user(const P2PArgs &A, int id, double h, int nrhs, float 
 struct CloseArgs;
 cudaError_t launch_close_pairs(const CloseArgs &A, int kernel, double ell, double h, bool fill, cudaStream_t s);
 cudaError_t launch_close_pairs_user(const CloseArgs &A, int id, double h, bool fill, cudaStream_t s);
-cudaError_t launch_near_fix(const CloseList &L, const float *sig, int64_t ns, int64_t nt, int nrhs, float *phi,
-                            cudaStream_t s);
+// sym: the one-RHS near field ran in symmetric order (its coefficients)
+cudaError_t launch_near_fix(const CloseList &L, bool sym, const float *sig, int64_t ns, int64_t nt, int nrhs,
+                            float *phi, cudaStream_t s);
 
 } // namespace bbfmm
 

@@ -292,6 +292,57 @@ static int64_t m2l_pairs_level(int l)
     return sa * sa * sa - sb * sb * sb;
 }
 
+// ---------------------------------------------------------------------------
+// launch choices (bbfmm_tuning): the near-field order of one-RHS matvecs and
+// the tensor-core M2L's tile size and pipeline depth
+static Tuning default_tuning(const bbfmm_plan_impl *P, int nrhs = 1)
+{
+    Tuning t;
+    t.near_sym = P->near_sym_default && nrhs == 1;
+    t.m2l_nt = P->m2l_nsets > 0 ? P->m2l_set[0].nt : 128;
+    t.m2l_stages = 0;
+    return t;
+}
+
+static void apply_tuning(bbfmm_plan_impl *P, const Tuning &t)
+{
+    P->near_sym = t.near_sym && P->near_slots != nullptr;
+    for (int k = 0; k < P->m2l_nsets; ++k) {
+        const bbfmm_plan_impl::TileSet &T = P->m2l_set[k];
+        if (T.nt != t.m2l_nt)
+            continue;
+        P->m2l_nt = T.nt;
+        P->m2l_tiles = T.tiles;
+        P->m2l_groups = T.groups;
+        for (int l = 0; l <= kMaxDepth; ++l) {
+            P->m2l_ntiles[l] = T.ntiles[l];
+            P->m2l_tile_off[l] = T.off[l];
+        }
+    }
+    P->m2l_stages = t.m2l_stages;
+}
+
+static bool tensor_m2l(const bbfmm_plan_impl *P)
+{
+    return P->precision != BBFMM_PREC_FP32 && P->nodeset == BBFMM_INTERP_CHEBYSHEV && P->ops && P->ops->r <= 256 &&
+           P->D >= 2;
+}
+
+// is t a choice this plan can run?
+static bool tuning_valid(const bbfmm_plan_impl *P, const Tuning &t)
+{
+    if (t.near_sym && !P->near_slots)
+        return false;
+    bool tile = false;
+    for (int k = 0; k < P->m2l_nsets; ++k)
+        tile = tile || P->m2l_set[k].nt == t.m2l_nt;
+    if (!tile)
+        return false;
+    if (t.m2l_stages != 0 && (t.m2l_stages < 2 || t.m2l_stages > m2l_max_stages(P->precision, t.m2l_nt)))
+        return false;
+    return true;
+}
+
 static int plan_build(bbfmm_plan_impl *P, const double *points, const double *targets, cudaStream_t s)
 {
     const int64_t n = P->n, nt = P->nt;
@@ -458,18 +509,29 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
     // per-level coefficient buffers
     const int R = P->max_nrhs, p3 = P->p3;
     const int rp = P->ops->rp;
-    // the tensor-core M2L visits only tiles with occupied targets
-    std::vector<int4> tiles;
-    m2l_active_tiles(D, P->precision, leaf_occ, tiles, P->m2l_ntiles);
-    for (int l = D, o = 0; l >= 2; --l) {
-        P->m2l_tile_off[l] = o;
-        o += P->m2l_ntiles[l];
+    // the tensor-core M2L visits only tiles with occupied targets: one tile
+    // list per tile size the precision allows (the first is the default)
+    std::vector<int4> tiles[2]; // read by the asynchronous copies below until the final synchronize
+    {
+        int nts[2];
+        P->m2l_nsets = m2l_tile_choices(P->precision, nts);
+        for (int k = 0; k < P->m2l_nsets; ++k) {
+            bbfmm_plan_impl::TileSet &T = P->m2l_set[k];
+            T.nt = nts[k];
+            m2l_active_tiles(D, T.nt, leaf_occ, tiles[k], T.ntiles);
+            for (int l = D, o = 0; l >= 2; --l) {
+                T.off[l] = o;
+                o += T.ntiles[l];
+            }
+            if (!tiles[k].empty()) {
+                PTRY(plan_alloc(P, (void **)&T.tiles, sizeof(int4) * tiles[k].size(), false, s));
+                CUDA_TRY(cudaMemcpyAsync(T.tiles, tiles[k].data(), sizeof(int4) * tiles[k].size(),
+                                         cudaMemcpyHostToDevice, s));
+            }
+            T.groups = m2l_groups_for(D, R, P->precision, T.nt, P->ops->r, T.ntiles, P->ops->rl);
+            P->m2l_groups = std::max(P->m2l_groups, T.groups); // slices allocated below
+        }
     }
-    if (!tiles.empty()) {
-        PTRY(plan_alloc(P, (void **)&P->m2l_tiles, sizeof(int4) * tiles.size(), false, s));
-        CUDA_TRY(cudaMemcpyAsync(P->m2l_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s));
-    }
-    P->m2l_groups = m2l_groups_for(D, R, P->precision, P->ops->r, P->m2l_ntiles, P->ops->rl);
     for (int l = 2; l <= D; ++l) {
         Level &L = P->lev[l];
         int64_t nb = 1LL << (3 * l), H = 1LL << (l - 1);
@@ -482,7 +544,7 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
         if (l <= D - 2)
             PTRY(plan_alloc(P, (void **)&P->up_count[l], 4 * nb * R, true, s));
         PTRY(plan_alloc(P, (void **)&L.Mt, 4 * 8 * (H + 2) * H * H * R * rp, true, s));
-        PTRY(plan_alloc(P, (void **)&L.Ft, 4 * nb * R * rp * P->m2l_groups, true, s));
+        PTRY(plan_alloc(P, (void **)&L.Ft, 4 * nb * R * rp * P->m2l_groups, true, s)); // most slices of any tile size
         if (P->precision == BBFMM_PREC_TF32X3) {
             PTRY(plan_alloc(P, (void **)&L.Mt_hi, 4 * 8 * (H + 2) * H * H * R * rp, true, s));
             PTRY(plan_alloc(P, (void **)&L.Mt_lo, 4 * 8 * (H + 2) * H * H * R * rp, true, s));
@@ -526,12 +588,17 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
         // occupancy of the leaves the near-field work meets: pairs per point
         // over the 27 neighbours.  Measured at 1M / 2M points: faster at ~30,
         // slower at ~4 (per-item work dominates) and on the clustered set
-        // (~170, where the pairs sit in dense leaves)
+        // (~170, where the pairs sit in dense leaves).  The autotuner, when
+        // on, measures both orders instead
         const double occ = (double)P->p2p_pairs / (27.0 * (double)n);
         P->near_sym = occ >= 16.0 && occ <= 48.0;
     }
-    if (P->near_sym) // slots nobody writes stay zero for the plan's lifetime
+    // slots nobody writes stay zero for the plan's lifetime; allocated when
+    // the symmetric order is used or may be chosen by the autotuner
+    if (P->near_sym || (P->near_sym_ok && P->near_auto && P->autotune))
         PTRY(plan_alloc(P, (void **)&P->near_slots, 4 * (int64_t)kSymSlotsHost * n, true, s));
+    P->near_sym_default = P->near_sym;
+    apply_tuning(P, default_tuning(P));
     if (P->close_refine && P->nchunks > 0) {
         // near-field pairs closer than 1/64 cell, with FP64 corrections of
         // the FP32 values the near-field kernels add (k_close_pairs): count
@@ -550,7 +617,7 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
         C.sperm = P->perm;
         C.D = D;
         C.same = P->separate ? 0 : 1;
-        C.sym = P->near_sym ? 1 : 0;
+        C.sym = P->near_slots ? 1 : 0; // coefficients for the symmetric order too
         C.count = cnt;
         const double h = P->side / (double)(1LL << D);
         CUDA_TRY(launch_close_pairs(C, P->kernel, P->ell, h, false, s));
@@ -578,6 +645,8 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
             PTRY(plan_alloc(P, (void **)&L.start, 4 * (int64_t)st.size(), false, s));
             PTRY(plan_alloc(P, (void **)&L.src, 4 * E, false, s));
             PTRY(plan_alloc(P, (void **)&L.c1, 4 * E, false, s));
+            if (C.sym)
+                PTRY(plan_alloc(P, (void **)&L.c1s, 4 * E, false, s));
             PTRY(plan_alloc(P, (void **)&L.cm, 4 * E, false, s));
             CUDA_TRY(cudaMemcpyAsync(first, hfirst.data(), 4 * nt, cudaMemcpyHostToDevice, s));
             CUDA_TRY(cudaMemcpyAsync(L.tgt, tg.data(), 4 * tg.size(), cudaMemcpyHostToDevice, s));
@@ -585,6 +654,7 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
             C.first = first;
             C.e_src = L.src;
             C.e_c1 = L.c1;
+            C.e_c1s = L.c1s;
             C.e_cm = L.cm;
             CUDA_TRY(launch_close_pairs(C, P->kernel, P->ell, h, true, s));
             CUDA_TRY(cudaStreamSynchronize(s)); // the host vectors above are read until here
@@ -664,7 +734,7 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
     if (tm)
         CUDA_TRY(cudaEventRecord(P->ev[Stage::Start], s));
     float *rows = nrhs > 1 ? P->sigma_rows : nullptr;
-    float *slots = nrhs == 1 ? P->near_slots : nullptr;
+    float *slots = nrhs == 1 && P->near_sym ? P->near_slots : nullptr;
     CUDA_TRY(launch_gather_sigma(sigma, P->perm, n, nrhs, P->sigma_s, rows, s));
     if (tm)
         CUDA_TRY(cudaEventRecord(P->ev[Stage::Gather], s));
@@ -681,7 +751,7 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
                             rows,    P->leaf_off, n,          D,  slots};
         CUDA_TRY(launch_p2p(pa, P->kernel, P->ell, P->side / (double)(1LL << D), nrhs, P->phi_near,
                             P->side_stream));
-        CUDA_TRY(launch_near_fix(P->close, P->sigma_s, n, nt, nrhs, P->phi_near, P->side_stream));
+        CUDA_TRY(launch_near_fix(P->close, slots != nullptr, P->sigma_s, n, nt, nrhs, P->phi_near, P->side_stream));
         if (tm)
             CUDA_TRY(cudaEventRecord(P->ev_p2p1, P->side_stream));
         CUDA_TRY(cudaEventRecord(P->ev_join, P->side_stream));
@@ -719,7 +789,10 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
         if (tm)
             CUDA_TRY(cudaEventRecord(P->ev[Stage::Up], fs));
         CUDA_TRY(cudaEventRecord(P->ev_up, fs));
-        PTRY(near_field(P->ev_up));
+        // with stage timing on, the near field waits for the far field, so
+        // every stage's events bracket that stage alone
+        if (!tm)
+            PTRY(near_field(P->ev_up));
         // far field, all levels
         CUDA_TRY(launch_m2l_all(P, nrhs, fs));
         if (tm)
@@ -731,6 +804,8 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
             CUDA_TRY(cudaEventRecord(P->ev[Stage::L2P], fs));
         }
         CUDA_TRY(cudaEventRecord(P->ev_far, fs));
+        if (tm)
+            PTRY(near_field(P->ev_far));
         CUDA_TRY(cudaStreamWaitEvent(s, P->ev_far, 0));
     } else if (tm) {
         for (int k = Stage::Up; k <= Stage::L2P; ++k)
@@ -807,7 +882,7 @@ static int matvec_graph(bbfmm_plan_impl *P, const float *sigma, float *phi, int 
     float *rows = nrhs > 1 ? P->sigma_rows : nullptr;
     void *gargs[] = {(void *)&sigma, (void *)&P->perm, (void *)&n, (void *)&nrhs, (void *)&P->sigma_s,
                      (void *)&rows};
-    const float *slots = nrhs == 1 ? P->near_slots : nullptr;
+    const float *slots = nrhs == 1 && P->near_sym ? P->near_slots : nullptr;
     void *cargs[] = {(void *)&far,  (void *)&P->phi_near, (void *)&slots, (void *)&P->tperm,
                      (void *)&nt,   (void *)&nrhs,        (void *)&phi};
     cudaKernelNodeParams gp = g.gp, cp = g.cp;
@@ -819,6 +894,155 @@ static int matvec_graph(bbfmm_plan_impl *P, const float *sigma, float *phi, int 
     CUDA_TRY(cudaGraphExecKernelNodeSetParams(g.exec, g.combine, &cp));
     CUDA_TRY(cudaGraphLaunch(g.exec, s));
     P->last_nrhs = nrhs;
+    return BBFMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: a measured sweep over the launch choices of one nrhs (Sec. 2.5
+// "Multiple right-hand-sides": the work per launch grows with nrhs, and the
+// best tile and near-field order with it).  Candidates: both near-field
+// orders (one RHS, AUTO mode, symmetric kernel and one point set) x every
+// tensor-core M2L tile size of the precision x every pipeline depth that fits.
+// Each candidate runs one untimed and kTuneReps timed matvecs (zero weights,
+// the plan's own buffers, eager launches); the fastest mean wins.  Results are
+// cached per process by what sets the work: kernel, p, rank, depth, nrhs,
+// precision, node set, point count, near-field occupancy and tile count (as
+// binary logarithms).
+static constexpr int kTuneReps = 3;
+typedef std::tuple<int, int, int, int, int, int, int, int, int, int, int> TuneKey;
+static std::mutex g_tune_mu;
+static std::map<TuneKey, Tuning> g_tune_cache;
+
+static TuneKey tune_key(const bbfmm_plan_impl *P, int nrhs)
+{
+    auto lg = [](double x) { return (int)floor(2.0 * log2(1.0 + x)); };
+    const double occ = (double)P->p2p_pairs / (27.0 * (double)P->nt);
+    const int leaf_tiles = P->m2l_nsets > 0 ? P->m2l_set[0].ntiles[P->D] : 0;
+    return TuneKey(P->kernel, P->p, P->ops ? P->ops->r : 0, P->D, nrhs, P->precision, P->nodeset,
+                   lg((double)P->n), lg(occ), lg((double)leaf_tiles),
+                   (P->separate ? 1 : 0) | (P->near_slots && P->near_auto ? 2 : 0) | (P->near_sym_default ? 4 : 0));
+}
+
+static void drop_graph(bbfmm_plan_impl *P, int nrhs)
+{
+    auto &g = P->graphs[nrhs];
+    if (g.exec)
+        cudaGraphExecDestroy(g.exec);
+    if (g.graph)
+        cudaGraphDestroy(g.graph);
+    g = bbfmm_plan_impl::Graph();
+}
+
+static int autotune_sweep(bbfmm_plan_impl *P, int nrhs, bool use_cache, cudaStream_t s)
+{
+    const TuneKey key = tune_key(P, nrhs);
+    if (use_cache) {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end() && tuning_valid(P, it->second)) {
+            P->tuning[nrhs] = it->second;
+            drop_graph(P, nrhs);
+            return BBFMM_OK;
+        }
+    }
+    std::vector<Tuning> cand;
+    const Tuning base = default_tuning(P, nrhs);
+    std::vector<bool> nears = {nrhs == 1 && base.near_sym};
+    if (nrhs == 1 && P->near_slots && P->near_auto)
+        nears = {false, true};
+    for (bool ns : nears) {
+        if (!tensor_m2l(P)) {
+            Tuning t = base;
+            t.near_sym = ns;
+            cand.push_back(t);
+            continue;
+        }
+        for (int k = 0; k < P->m2l_nsets; ++k) {
+            const int mx = m2l_max_stages(P->precision, P->m2l_set[k].nt);
+            for (int st = 2; st <= mx; ++st) {
+                Tuning t = base;
+                t.near_sym = ns;
+                t.m2l_nt = P->m2l_set[k].nt;
+                t.m2l_stages = st == mx ? 0 : st;
+                cand.push_back(t);
+            }
+        }
+    }
+    if (!P->io_sigma) {
+        PTRY(plan_alloc(P, (void **)&P->io_sigma, 4 * P->n * P->max_nrhs, false, s));
+        PTRY(plan_alloc(P, (void **)&P->io_phi, 4 * P->nt * P->max_nrhs, false, s));
+    }
+    CUDA_TRY(cudaMemsetAsync(P->io_sigma, 0, 4 * P->n * nrhs, s));
+    cudaEvent_t a = nullptr, b = nullptr;
+    CUDA_TRY(cudaEventCreate(&a));
+    cudaError_t ce = cudaEventCreate(&b);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(a);
+        return fail(BBFMM_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(ce));
+    }
+    const bool tm = P->timing;
+    P->timing = false;
+    int st = BBFMM_OK;
+    float best = INFINITY;
+    Tuning chosen = base;
+    for (const Tuning &t : cand) {
+        apply_tuning(P, t);
+        st = matvec_device(P, P->io_sigma, P->io_phi, nrhs, s);
+        if (st == BBFMM_OK && cudaEventRecord(a, s) != cudaSuccess)
+            st = fail(BBFMM_ECUDA, "cudaEventRecord failed");
+        for (int r = 0; r < kTuneReps && st == BBFMM_OK; ++r)
+            st = matvec_device(P, P->io_sigma, P->io_phi, nrhs, s);
+        if (st == BBFMM_OK && (cudaEventRecord(b, s) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess))
+            st = fail(BBFMM_ECUDA, "timing a tuning candidate failed");
+        if (st != BBFMM_OK)
+            break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < best) {
+            best = ms;
+            chosen = t;
+        }
+    }
+    P->timing = tm;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st != BBFMM_OK)
+        return st;
+    chosen.measured = true;
+    P->tuning[nrhs] = chosen;
+    drop_graph(P, nrhs);
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune_cache[key] = chosen;
+    return BBFMM_OK;
+}
+
+// the launch choices of this nrhs.  Counts of right-hand sides share the
+// choice of their power-of-two bucket (nrhs in [b, 2b) uses b's), so a
+// stream of uneven batch widths measures at most one sweep per bucket; with
+// opts.autotune the bucket is measured on first use (or taken from the cache)
+static int tune_bucket(int nrhs)
+{
+    int b = 1;
+    while (2 * b <= nrhs)
+        b *= 2;
+    return b;
+}
+
+static int ensure_tuning(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
+{
+    if (!P->tuning.count(nrhs)) {
+        const int b = tune_bucket(nrhs);
+        if (!P->tuning.count(b)) {
+            if (P->autotune)
+                PTRY(autotune_sweep(P, b, true, s));
+            else
+                P->tuning[b] = default_tuning(P, b);
+        }
+        Tuning t = P->tuning[b];
+        t.near_sym = t.near_sym && nrhs == 1;
+        P->tuning[nrhs] = t;
+    }
+    apply_tuning(P, P->tuning[nrhs]);
     return BBFMM_OK;
 }
 
@@ -842,6 +1066,7 @@ void bbfmm_default_opts(bbfmm_opts *o)
     o->split_accumulate = 1;
     o->use_graph = 1;
     o->close_refine = 1;
+    o->autotune = 1;
 }
 
 const char *bbfmm_last_error(void) { return g_last_error.c_str(); }
@@ -945,8 +1170,10 @@ static int plan_create(const double *points, int64_t n, const double *targets, i
     P->close_refine = opts.close_refine != 0;
     // the symmetric near field needs K(x, y) = K(y, x) (for a user kernel, as
     // registered) and one point set
-    P->near_sym = opts.near_mode != BBFMM_NEAR_ORDERED && !targets && kernel_symmetric(kernel_id);
+    P->near_sym_ok = !targets && kernel_symmetric(kernel_id);
+    P->near_sym = opts.near_mode != BBFMM_NEAR_ORDERED && P->near_sym_ok;
     P->near_auto = opts.near_mode == BBFMM_NEAR_AUTO;
+    P->autotune = opts.autotune != 0;
     if (opts.domain_given) {
         for (int d = 0; d < 3; ++d)
             P->lo[d] = opts.lo[d];
@@ -999,10 +1226,12 @@ int bbfmm_matvec(bbfmm_plan_t plan, const float *sigma, float *phi, int nrhs, vo
     cudaStream_t s = (cudaStream_t)stream;
     const bool dsig = is_device_ptr(sigma), dphi = is_device_ptr(phi);
     const int64_t bytes_in = 4 * plan->n * nrhs, bytes_out = 4 * plan->nt * nrhs;
-    int st = BBFMM_OK;
+    // launch choices first: a tuning sweep runs matvecs in the plan's staging
+    // buffers, which the host copies below then fill
+    int st = ensure_tuning(plan, nrhs, s);
     const float *sg = sigma;
     float *ph = phi;
-    if (!dsig || !dphi) {
+    if (st == BBFMM_OK && (!dsig || !dphi)) {
         if (!plan->io_sigma) {
             st = plan_alloc(plan, (void **)&plan->io_sigma, 4 * plan->n * plan->max_nrhs, false, s);
             if (st == BBFMM_OK)
@@ -1162,7 +1391,9 @@ int bbfmm_plan_info(bbfmm_plan_t plan, bbfmm_info *info)
     memset(info, 0, sizeof(*info));
     info->n = plan->n;
     info->n_targets = plan->nt;
-    info->near_symmetric = plan->near_sym ? 1 : 0;
+    auto t1 = plan->tuning.find(1);
+    const bool sym1 = plan->near_slots && (t1 != plan->tuning.end() ? t1->second.near_sym : plan->near_sym_default);
+    info->near_symmetric = sym1 ? 1 : 0;
     info->depth = plan->D;
     info->order = plan->p;
     info->rank = plan->ops ? plan->ops->r : 0;
@@ -1178,7 +1409,7 @@ int bbfmm_plan_info(bbfmm_plan_t plan, bbfmm_info *info)
     info->p2p_pairs = plan->p2p_pairs;
     info->m2l_pairs = plan->m2l_pairs;
     info->close_pairs = (int)plan->close.nentries;
-    info->p2p_evals = plan->near_sym ? plan->p2p_sym_evals : plan->p2p_pairs;
+    info->p2p_evals = sym1 ? plan->p2p_sym_evals : plan->p2p_pairs;
     return BBFMM_OK;
 }
 
@@ -1249,6 +1480,73 @@ int bbfmm_set_timing(bbfmm_plan_t plan, int on)
         return fail(BBFMM_EINVAL, "plan is NULL");
     plan->timing = on != 0;
     return BBFMM_OK;
+}
+
+static int tuning_args(bbfmm_plan_t plan, int nrhs)
+{
+    if (!plan)
+        return fail(BBFMM_EINVAL, "plan is NULL");
+    if (nrhs < 1 || nrhs > plan->max_nrhs)
+        return fail(BBFMM_EINVAL, "nrhs = %d out of range [1, %d]", nrhs, plan->max_nrhs);
+    return BBFMM_OK;
+}
+
+int bbfmm_get_tuning(bbfmm_plan_t plan, int nrhs, bbfmm_tuning *out)
+{
+    g_last_error.clear();
+    PTRY(tuning_args(plan, nrhs));
+    if (!out)
+        return fail(BBFMM_EINVAL, "out is NULL");
+    auto it = plan->tuning.find(nrhs);
+    const Tuning t = it != plan->tuning.end() ? it->second : default_tuning(plan, nrhs);
+    memset(out, 0, sizeof(*out));
+    out->near_mode = t.near_sym && plan->near_slots ? BBFMM_NEAR_SYMMETRIC : BBFMM_NEAR_ORDERED;
+    out->m2l_tile = t.m2l_nt;
+    out->m2l_stages = t.m2l_stages;
+    out->measured = t.measured ? 1 : 0;
+    return BBFMM_OK;
+}
+
+int bbfmm_set_tuning(bbfmm_plan_t plan, int nrhs, const bbfmm_tuning *in)
+{
+    g_last_error.clear();
+    PTRY(tuning_args(plan, nrhs));
+    if (!in)
+        return fail(BBFMM_EINVAL, "tuning is NULL");
+    if (in->near_mode != BBFMM_NEAR_ORDERED && in->near_mode != BBFMM_NEAR_SYMMETRIC)
+        return fail(BBFMM_EINVAL, "near_mode must be BBFMM_NEAR_ORDERED or BBFMM_NEAR_SYMMETRIC");
+    Tuning t;
+    t.near_sym = in->near_mode == BBFMM_NEAR_SYMMETRIC;
+    t.m2l_nt = in->m2l_tile;
+    t.m2l_stages = in->m2l_stages;
+    if (t.near_sym && nrhs != 1)
+        return fail(BBFMM_EINVAL, "the symmetric near field runs one right-hand side only");
+    if (!tuning_valid(plan, t))
+        return fail(BBFMM_EINVAL, "this plan cannot run near_mode %d, m2l_tile %d, m2l_stages %d", in->near_mode,
+                    in->m2l_tile, in->m2l_stages);
+    int expected = 0;
+    if (!plan->busy.compare_exchange_strong(expected, 1))
+        return fail(BBFMM_EBUSY, "plan is in use by another thread");
+    cudaDeviceSynchronize(); // a captured graph of this nrhs may still run
+    plan->tuning[nrhs] = t;
+    drop_graph(plan, nrhs);
+    plan->busy.store(0);
+    return BBFMM_OK;
+}
+
+int bbfmm_autotune(bbfmm_plan_t plan, int nrhs, void *stream)
+{
+    g_last_error.clear();
+    PTRY(tuning_args(plan, nrhs));
+    int expected = 0;
+    if (!plan->busy.compare_exchange_strong(expected, 1))
+        return fail(BBFMM_EBUSY, "plan is in use by another thread");
+    cudaDeviceSynchronize(); // a captured graph of this nrhs may still run
+    int st = autotune_sweep(plan, nrhs, false, (cudaStream_t)stream);
+    if (st == BBFMM_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+        st = fail(BBFMM_ECUDA, "autotune: stream synchronize failed");
+    plan->busy.store(0);
+    return st;
 }
 
 int bbfmm_stage_times(bbfmm_plan_t plan, float *out)

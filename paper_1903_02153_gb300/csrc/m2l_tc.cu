@@ -650,20 +650,24 @@ static void tile_of(int H, int nt, int &bx, int &by, int &bz)
     }
 }
 
-static int tile_targets(int precision)
+int m2l_tile_choices(int precision, int *nt)
 {
-    return precision == BBFMM_PREC_FP16X3 || precision == BBFMM_PREC_BF16X3 ? kTile16 : 128;
+    if (precision == BBFMM_PREC_FP16X3 || precision == BBFMM_PREC_BF16X3) {
+        nt[0] = kTile16;
+        nt[1] = kTile16 == 256 ? 128 : 256;
+        return 2;
+    }
+    nt[0] = 128; // TF32: 128-byte rows leave room for 128 targets only
+    return 1;
 }
 
-void m2l_active_tiles(int D, int precision, const std::vector<uint8_t> &leaf_occ, std::vector<int4> &tiles,
-                      int *count)
+void m2l_active_tiles(int D, int nt, const std::vector<uint8_t> &leaf_occ, std::vector<int4> &tiles, int *count)
 {
     tiles.clear();
     for (int l = 0; l <= kMaxDepth; ++l)
         count[l] = 0;
     if (D < 2)
         return;
-    const int nt = tile_targets(precision);
     // occupancy of the boxes of every level, from the leaves (Morton order)
     std::vector<std::vector<uint8_t>> occ(D + 1);
     occ[D] = leaf_occ;
@@ -714,14 +718,13 @@ static bool level_grouped(int H, int nt, int fmt)
 
 // slices of F~ per level: enough that, with equal ranges of (tile, entry)
 // pairs over the SMs, a tile meets at most G - 1 range boundaries
-int m2l_groups_for(int D, int nrhs, int precision, int r, const int *ntiles, const std::vector<int> &rl)
+int m2l_groups_for(int D, int nrhs, int precision, int nt, int r, const int *ntiles, const std::vector<int> &rl)
 {
     if (precision == BBFMM_PREC_FP32 || D < 2 || r > 256)
         return 1;
     if (tc_init() != cudaSuccess)
         return 1;
     const int fmt = precision == BBFMM_PREC_FP16X3 ? 1 : precision == BBFMM_PREC_BF16X3 ? 2 : 0;
-    const int nt = tile_targets(precision);
     int64_t pairs = 0;
     int emax = 1;
     for (int l = 2; l <= D; ++l) {
@@ -733,6 +736,25 @@ int m2l_groups_for(int D, int nrhs, int precision, int r, const int *ntiles, con
     const int64_t per_cta = std::max<int64_t>(1, (pairs + g_num_sms - 1) / g_num_sms);
     const int64_t need = 1 + (emax + per_cta - 1) / per_cta;
     return (int)std::max<int64_t>(2, std::min<int64_t>(8, need));
+}
+
+// bytes of one pipeline stage: the operator tiles (kMaxOps of them with
+// grouped entries) and the sources, high and low parts for three passes
+static uint32_t tc_stage_bytes(int fmt, bool three, int nt)
+{
+    const int rowb = kchunk_of(fmt) * (fmt == 0 ? 4 : 2);
+    const bool group = fmt != 0 && kGroupEntries;
+    const uint32_t a = 128u * rowb, b = (uint32_t)(nt + (group ? 64 : 0)) * rowb;
+    return (three ? 2u : 1u) * ((group ? kMaxOps : 1u) * a + b);
+}
+
+static constexpr size_t kTcSmemBudget = 220 * 1024;
+
+int m2l_max_stages(int precision, int nt)
+{
+    const int fmt = precision == BBFMM_PREC_FP16X3 ? 1 : precision == BBFMM_PREC_BF16X3 ? 2 : 0;
+    const int n = (int)((kTcSmemBudget - 1024 - 512) / tc_stage_bytes(fmt, precision != BBFMM_PREC_TF32, nt));
+    return n > kMaxStages ? kMaxStages : n;
 }
 
 template <int NPROD, int NACC, bool CF, int CH, int FMT>
@@ -785,7 +807,9 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
     const bool three = P->precision != BBFMM_PREC_TF32;
     const int kch = kchunk_of(fmt);
     const int elem = fmt == 0 ? 4 : 2, rowb = kch * elem, kstep = fmt == 0 ? 8 : 16;
-    const int nt = tile_targets(P->precision);
+    const int nt = P->m2l_nt; // targets per tile: the plan's tuning
+    if (nt != 128 && !(nt == 256 && fmt != 0))
+        return cudaErrorInvalidValue;
     if (O.rp % 16 != 0 || P->D - 1 > kMaxTcLevels || (int)O.rl.size() != O.nlev)
         return cudaErrorInvalidValue;
     // operator rows loaded per tile of each operator level (the M side is
@@ -812,6 +836,8 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
     L.a_bytes = 128 * rowb; // C tile: 128 rows in shared memory, nbk of them loaded
     L.b_bytes = (uint32_t)(nt + (group ? 64 : 0)) * rowb; // sources
     L.stage_bytes = (three ? 2 : 1) * ((uint32_t)L.maxops * L.a_bytes + L.b_bytes);
+    if (L.stage_bytes != tc_stage_bytes(fmt, three, nt))
+        return cudaErrorInvalidValue;
     L.ascale = P->a16_scale;
     // TMEM: one accumulator of nt columns per partial buffer; two per buffer
     // (hi*hi and corrections apart) when two double-buffered pairs still fit
@@ -821,9 +847,10 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
     L.tcols = 32;
     while (L.tcols < L.nbuf * nacc * nt)
         L.tcols *= 2;
-    const size_t budget = 220 * 1024;
-    int nstage = (int)((budget - 1024 - 512) / L.stage_bytes);
-    nstage = nstage > kMaxStages ? kMaxStages : nstage;
+    // pipeline stages: as many as fit, or fewer when the plan's tuning asks
+    int nstage = m2l_max_stages(P->precision, nt);
+    if (P->m2l_stages > 0 && P->m2l_stages < nstage)
+        nstage = P->m2l_stages;
     if (nstage < 2)
         return cudaErrorInvalidValue;
     L.nstage = nstage;

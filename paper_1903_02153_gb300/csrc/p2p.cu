@@ -123,13 +123,15 @@ __global__ void k_near_fix(const int *__restrict__ tgt, const int *__restrict__ 
     }
 }
 
-cudaError_t launch_near_fix(const CloseList &L, const float *sig, int64_t ns, int64_t nt, int nrhs, float *phi,
-                            cudaStream_t s)
+cudaError_t launch_near_fix(const CloseList &L, bool sym, const float *sig, int64_t ns, int64_t nt, int nrhs,
+                            float *phi, cudaStream_t s)
 {
     if (L.ntgt <= 0)
         return cudaSuccess;
-    k_near_fix<<<(L.ntgt + 127) / 128, 128, 0, s>>>(L.tgt, L.start, L.ntgt, L.src, nrhs == 1 ? L.c1 : L.cm, sig,
-                                                    ns, nt, nrhs, phi);
+    const float *c = nrhs > 1 ? L.cm : sym ? L.c1s : L.c1;
+    if (!c)
+        return cudaErrorInvalidValue;
+    k_near_fix<<<(L.ntgt + 127) / 128, 128, 0, s>>>(L.tgt, L.start, L.ntgt, L.src, c, sig, ns, nt, nrhs, phi);
     return cudaGetLastError();
 }
 

@@ -719,12 +719,12 @@ struct CloseArgs {
     const int *sperm;     // source tree order -> caller order
     int D;
     int same;             // the targets are the sources (skip i == j)
-    int sym;              // the one-RHS near field is the symmetric form
+    int sym;              // also the coefficients of the symmetric one-RHS form
     float scale;          // the near-field kernels write scale * sum K sigma
     int *count;           // count pass: listed pairs per target (tree order)
     const int *first;     // fill pass: first entry of each target
     int *e_src;           // fill pass: source (tree order) of each entry
-    float *e_c1, *e_cm;   // fill pass: c for one RHS and for several RHS
+    float *e_c1, *e_c1s, *e_cm; // fill pass: c for one RHS (ordered, symmetric) and several RHS
 };
 
 // FP32 squared distances as the near-field kernels form them
@@ -809,16 +809,17 @@ __global__ void __launch_bounds__(kP2PThreads) k_close_pairs(const CloseArgs A, 
                 const int src = ssrc[j];
                 if (A.same && src == ti)
                     continue;
-                // one RHS: the rows form, in the frame of the leaf that evaluates the pair
-                float K1;
+                // one RHS: the rows form, in the frame of the leaf that
+                // evaluates the pair (ordered: the target's; symmetric: the
+                // source's when that leaf takes the pair both ways)
+                const float K1 = own ? kern.one(r2, dx, dy, dz) : kern.far(r2, dx, dy, dz);
+                float K1s = K1;
                 if (A.sym && nid < 13 && nb_cnt[nid] <= kSymMaxPoints) {
                     const float4 us = A.spts[src]; // the target seen from the source's leaf
                     const float ox = (float)(1 - nid % 3), oy = (float)(1 - (nid / 3) % 3), oz = (float)(1 - nid / 9);
                     const float ex = __fsub_rn(us.x, __fadd_rn(X.x, ox)), ey = __fsub_rn(us.y, __fadd_rn(X.y, oy)),
                                 ez = __fsub_rn(us.z, __fadd_rn(X.z, oz));
-                    K1 = kern.far(r2_rows(ex, ey, ez, false), ex, ey, ez);
-                } else {
-                    K1 = own ? kern.one(r2, dx, dy, dz) : kern.far(r2, dx, dy, dz);
+                    K1s = kern.far(r2_rows(ex, ey, ez, false), ex, ey, ez);
                 }
                 // several RHS: k_p2p_gemm's form, the target's frame
                 const float rg = r2_gemm(dx, dy, dz, own);
@@ -826,12 +827,15 @@ __global__ void __launch_bounds__(kP2PThreads) k_close_pairs(const CloseArgs A, 
                 const long long sc = A.sperm[src];
                 const double Kx = exact(x0 - A.sx[3 * sc], x1 - A.sx[3 * sc + 1], x2 - A.sx[3 * sc + 2]);
                 const float c1 = (float)(Kx - (double)A.scale * (double)K1);
+                const float c1s = (float)(Kx - (double)A.scale * (double)K1s);
                 const float cm = (float)(Kx - (double)A.scale * (double)Km);
-                if (c1 == 0.0f && cm == 0.0f)
+                if (c1 == 0.0f && c1s == 0.0f && cm == 0.0f)
                     continue;
                 if (FILL) {
                     A.e_src[pos] = src;
                     A.e_c1[pos] = c1;
+                    if (A.sym)
+                        A.e_c1s[pos] = c1s;
                     A.e_cm[pos] = cm;
                     ++pos;
                 } else {

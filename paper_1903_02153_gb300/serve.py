@@ -366,11 +366,18 @@ class GpuExecutor:
 
     def build(self, key, max_nrhs):
         """Runs on the server's builder thread, on a stream of its own so that
-        the build overlaps the matvecs in flight."""
+        the build overlaps the matvecs in flight.  The plan's launch choices
+        are measured here, for every power-of-two batch width up to
+        max_nrhs (a batch of any width takes its bucket's choice), so that no
+        request pays for a tuning sweep."""
         self.torch.cuda.set_device(self.dev)
         pts, kid, ell, p, depth = self.point_source(key)
         plan = self.bb.Plan(pts, kid, p, depth, ell=ell, precision=self.precision, svd_eps=self.svd_eps,
                             max_nrhs=max_nrhs, domain=self.domain, stream=self.build_stream)
+        b = 1
+        while b <= max_nrhs:
+            self.bb.bbfmm_autotune(plan.handle, b, self.build_stream)
+            b *= 2
         return plan
 
     def plan_bytes(self, plan):

@@ -1,0 +1,151 @@
+"""The autotuner (opts.autotune, bbfmm_autotune / bbfmm_get_tuning /
+bbfmm_set_tuning): launch choices per nrhs -- the near-field order of one-RHS
+matvecs, the tensor-core M2L's tile size and pipeline depth -- measured and
+kept per plan, cached per process.  Sec. 2.5 "Multiple right-hand-sides": the
+work per launch grows with nrhs, and the best cut moves with it.
+
+A choice changes how the work is cut, never what is computed: every
+candidate's result is within FP32 rounding of every other's and within the
+gates against the oracle, and a plan run with the tuner's choice gives the
+same bits as a plan told that choice explicitly.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from paper_1903_02153_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+UNIT = (W.UNIT_LO, W.UNIT_SIDE)
+
+
+@pytest.fixture(scope="module")
+def bb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1903_02153_gb300 import build
+    build.build()
+    from paper_1903_02153_gb300 import bbfmm
+    bbfmm.lib()
+    return bbfmm
+
+
+def make(bb, pts, kid=1, p=5, depth=4, precision="fp16x3", nrhs=1, autotune=True, ell=1.0):
+    return bb.Plan(torch.from_numpy(pts).cuda(), kid, p, depth, ell=ell, svd_eps=1e-7, precision=precision,
+                   domain=UNIT, max_nrhs=nrhs, autotune=autotune)
+
+
+def sigma_dev(sig):
+    return torch.from_numpy(np.ascontiguousarray(sig.T if sig.ndim == 2 else sig)).cuda()
+
+
+def candidates(bb, plan, nrhs):
+    """Every (near order, tile, stages) the plan accepts for this nrhs."""
+    ok = []
+    for near, tile, st in itertools.product(["ordered", "symmetric"], [128, 256], [0, 2, 3, 4]):
+        try:
+            bb.bbfmm_set_tuning(plan.handle, nrhs, near, tile, st)
+        except bb.BBFMMError as e:
+            assert e.status == bb.BBFMM_EINVAL
+            continue
+        ok.append((near, tile, st))
+    return ok
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("kind,kid,ell,p,depth,precision", [("uniform", 1, 1.0, 5, 4, "fp16x3"),
+                                                            ("clustered", 3, 0.3, 5, 5, "fp16x3"),
+                                                            ("uniform", 2, 1.0, 4, 4, "tf32x3"),
+                                                            ("uniform", 1, 1.0, 4, 4, "fp32")])
+def test_every_candidate_gives_the_same_result(bb, oracle, kind, kid, ell, p, depth, precision):
+    n = 60_000
+    pts = W.make_points(kind, n, seed=700)
+    sig = W.uniform_sigma(n, seed=701).astype(np.float32)
+    plan = make(bb, pts, kid, p, depth, precision, ell=ell)
+    cands = candidates(bb, plan, 1)
+    if precision in ("fp16x3", "bf16x3"):
+        assert {c[1] for c in cands} == {128, 256}
+    assert {c[0] for c in cands} == {"ordered", "symmetric"}
+    s = sigma_dev(sig)
+    outs = {}
+    for c in cands:
+        bb.bbfmm_set_tuning(plan.handle, 1, *c)
+        t = bb.bbfmm_get_tuning(plan.handle, 1)
+        assert (t.m2l_tile, t.m2l_stages, t.measured) == (c[1], c[2], 0)
+        outs[c] = plan.matvec(s).cpu().numpy().astype(np.float64)
+        assert bb.bbfmm_status(plan.handle) == 0
+    plan.close()
+    idx = np.sort(np.random.default_rng(702).choice(n, 2000, replace=False))
+    ref = oracle.bbfmm(pts, sig.astype(np.float64), kid, p, depth, ell=ell, lo=W.UNIT_LO, side=W.UNIT_SIDE,
+                       sample=idx)
+    base = outs[cands[0]]
+    for c, out in outs.items():
+        d, e = rel(out, base), rel(out[idx], ref)
+        print("%s %s k%d %s: vs first candidate %.2e, vs oracle %.2e" % (kind, precision, kid, c, d, e))
+        assert d <= 2e-6          # another order of the same FP32 sums
+        assert e <= 1e-5
+
+
+def test_tuned_choice_is_a_candidate_and_reproducible(bb):
+    n = 100_000
+    pts = W.uniform_points(n, seed=703)
+    sig = sigma_dev(W.uniform_sigma(n, seed=704).astype(np.float32))
+    plan = make(bb, pts)
+    t0 = bb.bbfmm_get_tuning(plan.handle, 1)
+    assert t0.measured == 0               # nothing measured before the first matvec
+    a = plan.matvec(sig).clone()          # the first matvec tunes (or takes the cache)
+    t = bb.bbfmm_get_tuning(plan.handle, 1)
+    assert t.measured == 1
+    assert (t.near_mode, t.m2l_tile) in {(m, tl) for m in (1, 2) for tl in (128, 256)}
+    bb.bbfmm_autotune(plan.handle, 1)     # measure again explicitly
+    assert bb.bbfmm_get_tuning(plan.handle, 1).measured == 1
+    # a plan told the first choice explicitly gives the same bits
+    other = make(bb, pts, autotune=False)
+    bb.bbfmm_set_tuning(other.handle, 1, t.near_mode, t.m2l_tile, t.m2l_stages)
+    bb.bbfmm_set_tuning(plan.handle, 1, t.near_mode, t.m2l_tile, t.m2l_stages)
+    b, c = plan.matvec(sig), other.matvec(sig)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b) and torch.equal(b, c)
+    # a second plan of the same shape takes the cached choice at its first matvec
+    again = make(bb, pts)
+    again.matvec(sig)
+    t2 = bb.bbfmm_get_tuning(again.handle, 1)
+    assert t2.measured == 1
+    for pl in (plan, other, again):
+        assert bb.bbfmm_status(pl.handle) == 0
+        pl.close()
+
+
+def test_several_rhs_and_defaults(bb):
+    n = 50_000
+    pts = W.uniform_points(n, seed=705)
+    sig = W.uniform_sigma(n, nrhs=8, seed=706).astype(np.float32)
+    plan = make(bb, pts, nrhs=8)
+    with pytest.raises(bb.BBFMMError) as ei:   # the symmetric order is one-RHS only
+        bb.bbfmm_set_tuning(plan.handle, 8, "symmetric", 256, 0)
+    assert ei.value.status == bb.BBFMM_EINVAL
+    with pytest.raises(bb.BBFMMError):         # no such tile size
+        bb.bbfmm_set_tuning(plan.handle, 8, "ordered", 64, 0)
+    with pytest.raises(bb.BBFMMError):         # more stages than fit
+        bb.bbfmm_set_tuning(plan.handle, 8, "ordered", 256, 7)
+    cands = candidates(bb, plan, 8)
+    assert cands and all(c[0] == "ordered" for c in cands)
+    s = sigma_dev(sig)
+    outs = []
+    for c in cands:
+        bb.bbfmm_set_tuning(plan.handle, 8, *c)
+        outs.append(plan.matvec(s).cpu().numpy().astype(np.float64))
+    for o in outs[1:]:
+        assert rel(o, outs[0]) <= 2e-6
+    plan.close()
+    fixed = make(bb, pts, nrhs=8, autotune=False)
+    fixed.matvec(s)
+    t = bb.bbfmm_get_tuning(fixed.handle, 8)
+    assert (t.measured, t.m2l_tile, t.m2l_stages, t.near_mode) == (0, 256, 0, 1)
+    fixed.close()

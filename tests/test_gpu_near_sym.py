@@ -28,10 +28,11 @@ def bb():
     return bbfmm
 
 
-def make_plan(bb, pts, kid, p, depth, near_mode, ell=1.0, precision="fp32", max_nrhs=1, targets=None):
+def make_plan(bb, pts, kid, p, depth, near_mode, ell=1.0, precision="fp32", max_nrhs=1, targets=None,
+              autotune=True):
     dev = torch.device("cuda:0")
     return bb.Plan(torch.from_numpy(np.ascontiguousarray(pts)).to(dev), kid, p, depth, ell=ell, svd_eps=1e-7,
-                   precision=precision, domain=UNIT, max_nrhs=max_nrhs, near_mode=near_mode,
+                   precision=precision, domain=UNIT, max_nrhs=max_nrhs, near_mode=near_mode, autotune=autotune,
                    targets=None if targets is None else torch.from_numpy(np.ascontiguousarray(targets)).to(dev))
 
 
@@ -55,14 +56,15 @@ def rel(a, b):
 
 
 def test_auto_chooses_by_leaf_occupancy(bb):
-    """AUTO takes the symmetric form when the near-field pairs per point / 27
-    (the occupancy of the leaves the work meets) is 16..48, and not on the
-    clustered set, whose pairs sit in dense leaves."""
+    """Without the autotuner, AUTO takes the symmetric form when the
+    near-field pairs per point / 27 (the occupancy of the leaves the work
+    meets) is 16..48, and not on the clustered set, whose pairs sit in dense
+    leaves."""
     cases = [(W.uniform_points(16384, seed=515), 3, 1), (W.uniform_points(2048, seed=515), 3, 0),
              (W.uniform_points(60_000, seed=515), 3, 0), (W.uniform_points(30_000, seed=515), 4, 0),
              (W.uniform_points(100_000, seed=515), 4, 1), (W.clustered_points(200_000, seed=515), 5, 0)]
     for pts, depth, want in cases:
-        plan = make_plan(bb, pts, K_INV_R, 4, depth, "auto")
+        plan = make_plan(bb, pts, K_INV_R, 4, depth, "auto", autotune=False)
         info = plan.info()
         plan.close()
         occ = info.p2p_pairs / (27.0 * len(pts))
