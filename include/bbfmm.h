@@ -160,7 +160,11 @@ typedef struct {
                        in shared memory (default), else 2 up to that */
     int measured;   /* bbfmm_get_tuning: 1 if chosen by a measured sweep (or its
                        cache); ignored by bbfmm_set_tuning */
-    int reserved[4];
+    int near_box;   /* ORDERED one-RHS near field: 1 = a work item per level-(D-1)
+                       box (its 8 leaves' targets against the 4x4x4 leaves around
+                       it, staged once), for leaves of a few points; 0 = a work
+                       item per leaf (default).  Needs depth >= 1 */
+    int reserved[3];
 } bbfmm_tuning;
 
 /*

@@ -50,7 +50,7 @@ class bbfmm_opts(ctypes.Structure):
 
 class bbfmm_tuning(ctypes.Structure):
     _fields_ = [("near_mode", ctypes.c_int), ("m2l_tile", ctypes.c_int), ("m2l_stages", ctypes.c_int),
-                ("measured", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("measured", ctypes.c_int), ("near_box", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class bbfmm_info(ctypes.Structure):
@@ -273,12 +273,13 @@ def bbfmm_get_tuning(plan, nrhs=1) -> bbfmm_tuning:
     return t
 
 
-def bbfmm_set_tuning(plan, nrhs, near_mode, m2l_tile, m2l_stages=0):
+def bbfmm_set_tuning(plan, nrhs, near_mode, m2l_tile, m2l_stages=0, near_box=False):
     """near_mode: "ordered" / "symmetric" (or the BBFMM_NEAR_* value)."""
     t = bbfmm_tuning()
     t.near_mode = NEAR_MODES[near_mode] if isinstance(near_mode, str) else int(near_mode)
     t.m2l_tile = int(m2l_tile)
     t.m2l_stages = int(m2l_stages)
+    t.near_box = 1 if near_box else 0
     return _check(lib().bbfmm_set_tuning(plan, int(nrhs), ctypes.byref(t)))
 
 

@@ -169,12 +169,14 @@ struct CloseList {
     int *src = nullptr;             // [nentries] source (tree order)
     float *c1 = nullptr;            // [nentries] coefficient, one RHS, ordered near field
     float *c1s = nullptr;           // [nentries] coefficient, one RHS, symmetric near field (or null)
+    float *c1b = nullptr;           // [nentries] coefficient, one RHS, ordered by level-(D-1) box
     float *cm = nullptr;            // [nentries] coefficient, several RHS
 };
 
 // the launch choices the autotuner measures (bbfmm_tuning in the header)
 struct Tuning {
     bool near_sym = false; // one-RHS near field in symmetric order
+    bool near_box = false; // one-RHS ordered near field in work items of one level-(D-1) box
     int m2l_nt = 128;      // targets per tensor-core M2L tile
     int m2l_stages = 0;    // tensor-core M2L pipeline stages (0 = as many as fit)
     bool measured = false; // chosen by a measured sweep (or its cache)
@@ -204,6 +206,9 @@ struct bbfmm_plan_impl {
     int *tleaf_off = nullptr;
     int4 *chunks = nullptr; // near-field work items over the target leaves
     int nchunks = 0;
+    int4 *box_items = nullptr; // near-field work items of one level-(D-1) box (D >= 1)
+    int nbox_items = 0;
+    bool near_box = false;     // one-RHS ordered near field by box items (tuning)
     int64_t nonempty_leaves = 0, max_leaf = 0, p2p_pairs = 0, m2l_pairs = 0;
     int64_t p2p_sym_evals = 0; // kernel evaluations of the symmetric near field (one RHS)
 
@@ -396,6 +401,11 @@ struct P2PArgs {
     int64_t ns;
     int D;
     float *slots; // non-null: symmetric near field (one RHS), 13 x ns two-way column sums
+    // non-null (one RHS, ordered): work items of one level-(D-1) box each
+    // (k_p2p_box) instead of the leaf chunks; toff = target leaf offsets
+    const int4 *boxes;
+    int nboxes;
+    const int *toff;
 };
 cudaError_t launch_p2p(const P2PArgs &A, int kernel, double ell, double h, int nrhs, float *phi_near,
                        cudaStream_t s);
@@ -406,8 +416,9 @@ cudaError_t launch_p2p_user(const P2PArgs &A, int id, double h, int nrhs, float 
 struct CloseArgs;
 cudaError_t launch_close_pairs(const CloseArgs &A, int kernel, double ell, double h, bool fill, cudaStream_t s);
 cudaError_t launch_close_pairs_user(const CloseArgs &A, int id, double h, bool fill, cudaStream_t s);
-// sym: the one-RHS near field ran in symmetric order (its coefficients)
-cudaError_t launch_near_fix(const CloseList &L, bool sym, const float *sig, int64_t ns, int64_t nt, int nrhs,
+// form of the one-RHS near field that ran (its coefficients): 0 ordered by
+// leaf, 1 symmetric, 2 ordered by box
+cudaError_t launch_near_fix(const CloseList &L, int form, const float *sig, int64_t ns, int64_t nt, int nrhs,
                             float *phi, cudaStream_t s);
 
 } // namespace bbfmm

@@ -307,6 +307,7 @@ static Tuning default_tuning(const bbfmm_plan_impl *P, int nrhs = 1)
 static void apply_tuning(bbfmm_plan_impl *P, const Tuning &t)
 {
     P->near_sym = t.near_sym && P->near_slots != nullptr;
+    P->near_box = t.near_box && !P->near_sym && P->box_items != nullptr;
     for (int k = 0; k < P->m2l_nsets; ++k) {
         const bbfmm_plan_impl::TileSet &T = P->m2l_set[k];
         if (T.nt != t.m2l_nt)
@@ -332,6 +333,8 @@ static bool tensor_m2l(const bbfmm_plan_impl *P)
 static bool tuning_valid(const bbfmm_plan_impl *P, const Tuning &t)
 {
     if (t.near_sym && !P->near_slots)
+        return false;
+    if (t.near_box && (t.near_sym || !P->box_items))
         return false;
     bool tile = false;
     for (int k = 0; k < P->m2l_nsets; ++k)
@@ -452,6 +455,7 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
 
     // statistics of the tree (host copies of the leaf offsets)
     std::vector<uint8_t> leaf_occ; // leaves holding targets
+    std::vector<int4> box_items;   // read by an asynchronous copy until the final synchronize
     {
         std::vector<int> off(nleaf + 1), toff;
         CUDA_TRY(cudaMemcpyAsync(off.data(), P->leaf_off, 4 * (nleaf + 1), cudaMemcpyDeviceToHost, s));
@@ -498,8 +502,23 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
         }
         P->p2p_pairs = pairs;
         P->p2p_sym_evals = sym_evals;
+        // near-field work items of one level-(D-1) box (its 8 leaves' targets,
+        // at most kChunk per item), for small leaves
+        if (D >= 1) {
+            const int64_t npar = nleaf / 8;
+            for (int64_t b = 0; b < npar; ++b)
+                for (int a = to[8 * b]; a < to[8 * b + 8]; a += kChunk)
+                    box_items.push_back(make_int4((int)b, a, std::min(kChunk, to[8 * b + 8] - a), 0));
+        }
         for (int l = 2; l <= D; ++l)
             P->m2l_pairs += m2l_pairs_level(l);
+    }
+
+    if (!box_items.empty()) {
+        P->nbox_items = (int)box_items.size();
+        PTRY(plan_alloc(P, (void **)&P->box_items, sizeof(int4) * box_items.size(), false, s));
+        CUDA_TRY(cudaMemcpyAsync(P->box_items, box_items.data(), sizeof(int4) * box_items.size(),
+                                 cudaMemcpyHostToDevice, s));
     }
 
     // operators
@@ -645,6 +664,7 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
             PTRY(plan_alloc(P, (void **)&L.start, 4 * (int64_t)st.size(), false, s));
             PTRY(plan_alloc(P, (void **)&L.src, 4 * E, false, s));
             PTRY(plan_alloc(P, (void **)&L.c1, 4 * E, false, s));
+            PTRY(plan_alloc(P, (void **)&L.c1b, 4 * E, false, s));
             if (C.sym)
                 PTRY(plan_alloc(P, (void **)&L.c1s, 4 * E, false, s));
             PTRY(plan_alloc(P, (void **)&L.cm, 4 * E, false, s));
@@ -654,6 +674,7 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
             C.first = first;
             C.e_src = L.src;
             C.e_c1 = L.c1;
+            C.e_c1b = L.c1b;
             C.e_c1s = L.c1s;
             C.e_cm = L.cm;
             CUDA_TRY(launch_close_pairs(C, P->kernel, P->ell, h, true, s));
@@ -747,11 +768,14 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
         CUDA_TRY(cudaStreamWaitEvent(P->side_stream, after, 0));
         if (tm)
             CUDA_TRY(cudaEventRecord(P->ev_p2p0, P->side_stream));
+        const bool box = nrhs == 1 && !slots && P->near_box;
         const P2PArgs pa = {P->tpts, P->chunks,   P->nchunks, nt, P->pts, P->sigma_s,
-                            rows,    P->leaf_off, n,          D,  slots};
+                            rows,    P->leaf_off, n,          D,  slots,
+                            box ? P->box_items : nullptr, box ? P->nbox_items : 0, P->tleaf_off};
         CUDA_TRY(launch_p2p(pa, P->kernel, P->ell, P->side / (double)(1LL << D), nrhs, P->phi_near,
                             P->side_stream));
-        CUDA_TRY(launch_near_fix(P->close, slots != nullptr, P->sigma_s, n, nt, nrhs, P->phi_near, P->side_stream));
+        CUDA_TRY(launch_near_fix(P->close, slots ? 1 : box ? 2 : 0, P->sigma_s, n, nt, nrhs, P->phi_near,
+                                 P->side_stream));
         if (tm)
             CUDA_TRY(cudaEventRecord(P->ev_p2p1, P->side_stream));
         CUDA_TRY(cudaEventRecord(P->ev_join, P->side_stream));
@@ -947,13 +971,17 @@ static int autotune_sweep(bbfmm_plan_impl *P, int nrhs, bool use_cache, cudaStre
     }
     std::vector<Tuning> cand;
     const Tuning base = default_tuning(P, nrhs);
-    std::vector<bool> nears = {nrhs == 1 && base.near_sym};
+    // near-field forms (symmetric, box items): 0 ordered by leaf, 1 symmetric, 2 ordered by box
+    std::vector<int> nears = {nrhs == 1 && base.near_sym ? 1 : 0};
     if (nrhs == 1 && P->near_slots && P->near_auto)
-        nears = {false, true};
-    for (bool ns : nears) {
+        nears = {0, 1};
+    if (nrhs == 1 && P->box_items && !(P->near_slots && !P->near_auto))
+        nears.push_back(2);
+    for (int nf : nears) {
         if (!tensor_m2l(P)) {
             Tuning t = base;
-            t.near_sym = ns;
+            t.near_sym = nf == 1;
+            t.near_box = nf == 2;
             cand.push_back(t);
             continue;
         }
@@ -961,7 +989,8 @@ static int autotune_sweep(bbfmm_plan_impl *P, int nrhs, bool use_cache, cudaStre
             const int mx = m2l_max_stages(P->precision, P->m2l_set[k].nt);
             for (int st = 2; st <= mx; ++st) {
                 Tuning t = base;
-                t.near_sym = ns;
+                t.near_sym = nf == 1;
+                t.near_box = nf == 2;
                 t.m2l_nt = P->m2l_set[k].nt;
                 t.m2l_stages = st == mx ? 0 : st;
                 cand.push_back(t);
@@ -1504,6 +1533,7 @@ int bbfmm_get_tuning(bbfmm_plan_t plan, int nrhs, bbfmm_tuning *out)
     out->m2l_tile = t.m2l_nt;
     out->m2l_stages = t.m2l_stages;
     out->measured = t.measured ? 1 : 0;
+    out->near_box = t.near_box && !t.near_sym && plan->box_items && nrhs == 1 ? 1 : 0;
     return BBFMM_OK;
 }
 
@@ -1519,11 +1549,14 @@ int bbfmm_set_tuning(bbfmm_plan_t plan, int nrhs, const bbfmm_tuning *in)
     t.near_sym = in->near_mode == BBFMM_NEAR_SYMMETRIC;
     t.m2l_nt = in->m2l_tile;
     t.m2l_stages = in->m2l_stages;
+    t.near_box = in->near_box != 0;
+    if ((t.near_sym || t.near_box) && nrhs != 1)
+        return fail(BBFMM_EINVAL, "the symmetric and box near-field forms run one right-hand side only");
     if (t.near_sym && nrhs != 1)
         return fail(BBFMM_EINVAL, "the symmetric near field runs one right-hand side only");
     if (!tuning_valid(plan, t))
-        return fail(BBFMM_EINVAL, "this plan cannot run near_mode %d, m2l_tile %d, m2l_stages %d", in->near_mode,
-                    in->m2l_tile, in->m2l_stages);
+        return fail(BBFMM_EINVAL, "this plan cannot run near_mode %d, near_box %d, m2l_tile %d, m2l_stages %d",
+                    in->near_mode, in->near_box, in->m2l_tile, in->m2l_stages);
     int expected = 0;
     if (!plan->busy.compare_exchange_strong(expected, 1))
         return fail(BBFMM_EBUSY, "plan is in use by another thread");

@@ -17,6 +17,10 @@ static cudaError_t p2p_launch(const P2PArgs &A, Kern k, float scale, int nrhs, f
     if (nrhs == 1 && A.slots) {
         k_p2p_sym<Kern><<<A.nchunks, kP2PThreads, 0, s>>>(A.spts, A.chunks, A.ns, A.sig, A.soff, A.D, k, scale, phi,
                                                            A.slots);
+    } else if (nrhs == 1 && A.boxes) {
+        if (A.nboxes > 0)
+            k_p2p_box<Kern><<<A.nboxes, kP2PThreads, 0, s>>>(A.tpts, A.toff, A.boxes, A.nt, A.spts, A.sig, A.soff,
+                                                               A.D, k, scale, phi);
     } else if (nrhs > 1) {
         k_p2p_gemm<Kern, kGemmT><<<A.nchunks, gemm_threads(kGemmT), 0, s>>>(
             A.tpts, A.chunks, A.nt, A.spts, A.sig_rows, A.soff, A.ns, A.D, k, scale, nrhs, phi);
@@ -123,12 +127,12 @@ __global__ void k_near_fix(const int *__restrict__ tgt, const int *__restrict__ 
     }
 }
 
-cudaError_t launch_near_fix(const CloseList &L, bool sym, const float *sig, int64_t ns, int64_t nt, int nrhs,
+cudaError_t launch_near_fix(const CloseList &L, int form, const float *sig, int64_t ns, int64_t nt, int nrhs,
                             float *phi, cudaStream_t s)
 {
     if (L.ntgt <= 0)
         return cudaSuccess;
-    const float *c = nrhs > 1 ? L.cm : sym ? L.c1s : L.c1;
+    const float *c = nrhs > 1 ? L.cm : form == 1 ? L.c1s : form == 2 ? L.c1b : L.c1;
     if (!c)
         return cudaErrorInvalidValue;
     k_near_fix<<<(L.ntgt + 127) / 128, 128, 0, s>>>(L.tgt, L.start, L.ntgt, L.src, c, sig, ns, nt, nrhs, phi);

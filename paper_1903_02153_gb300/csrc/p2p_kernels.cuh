@@ -273,6 +273,186 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
     }
 }
 
+// Small leaves (a few points each): a work item is up to kP2PChunk targets
+// of one level-(D-1) box, i.e. of its 8 child leaves, and the sources of the
+// 4x4x4 block of leaves around that box are staged once for all of them (a
+// per-leaf item would stage its 27 leaves for a handful of targets).  The
+// union's leaves are staged in (z, y, x) order, so the 27 neighbours of a
+// child are 9 rows of 3 consecutive leaves, i.e. 9 runs of the stage (the
+// row through the child itself split at its own leaf, which takes the r = 0
+// test).  Coordinates are in the frame of child (0, 0, 0): a point of leaf L
+// sits at u + (L - 2P) with |L - 2P| <= 2 per axis (targets: 0 or 1).
+// Threads are (group of <= kTPT targets of one child, slice), as in k_p2p.
+constexpr int kBoxStage = 512; // staged sources per pass (16 KB)
+
+template <class Kern>
+__global__ void __launch_bounds__(kP2PThreads, 8)
+    k_p2p_box(const float4 *__restrict__ tpts, const int *__restrict__ toff, const int4 *__restrict__ items,
+              long long n_tgt, const float4 *__restrict__ spts, const float *__restrict__ sig,
+              const int *__restrict__ soff, int D, Kern kern, float scale, float *__restrict__ phi)
+{
+    constexpr int NPK = kTPT / 2;
+    __shared__ float4 stage[2 * kBoxStage];
+    __shared__ int lpre[65];      // prefix of the source counts of the 64 union leaves
+    __shared__ int lfirst[64];    // first source (tree order) of each union leaf
+    __shared__ int cfirst[9];     // the item's targets by child: [cfirst[c], cfirst[c + 1])
+    __shared__ int gpre[9];       // target groups by child (prefix)
+    __shared__ float2 red[NPK][kP2PThreads];
+    const int tid = threadIdx.x;
+    const int4 it = items[blockIdx.x];
+    int px, py, pz;
+    demorton3((unsigned)it.x, px, py, pz);
+    const int nside = 1 << D;
+    if (tid < 64) { // union leaves: counts, then a scan over the two warps
+        const int lx = 2 * px - 1 + (tid & 3), ly = 2 * py - 1 + ((tid >> 2) & 3), lz = 2 * pz - 1 + (tid >> 4);
+        int cnt = 0, start = 0;
+        if (lx >= 0 && ly >= 0 && lz >= 0 && lx < nside && ly < nside && lz < nside) {
+            const unsigned m = morton3((unsigned)lx, (unsigned)ly, (unsigned)lz);
+            start = soff[m];
+            cnt = soff[m + 1] - start;
+        }
+        lfirst[tid] = start;
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((tid & 31) >= o)
+                incl += v;
+        }
+        lpre[tid + 1] = incl; // warp-local inclusive prefix; warp 1 adds warp 0's total below
+    }
+    if (tid >= 64 && tid < 64 + 9) { // the item's targets by child leaf, clipped to the item
+        const int c = tid - 64;
+        const int a = c < 8 ? toff[8 * it.x + c] : toff[8 * it.x + 8];
+        cfirst[c] = min(max(a, it.y), it.y + it.z);
+    }
+    __syncthreads();
+    if (tid >= 32 && tid < 64)
+        lpre[tid + 1] += lpre[32];
+    if (tid == 0) {
+        lpre[0] = 0;
+        int q = 0;
+        for (int c = 0; c < 8; ++c) {
+            gpre[c] = q;
+            q += (cfirst[c + 1] - cfirst[c] + kTPT - 1) / kTPT;
+        }
+        gpre[8] = q;
+    }
+    __syncthreads();
+    const int Q = gpre[8];
+    const int S = kP2PThreads / Q;
+    const int q = tid % Q, slice = tid / Q;
+    const bool active = slice < S;
+    int c = 0;
+    while (c < 7 && gpre[c + 1] <= q)
+        ++c;
+    const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+    const int t0 = cfirst[c] + kTPT * (q - gpre[c]), tend = cfirst[c + 1];
+    float2 X[NPK], Y[NPK], Z[NPK];
+#pragma unroll
+    for (int pk = 0; pk < NPK; ++pk) {
+        const int i0 = t0 + 2 * pk, i1 = i0 + 1;
+        const float4 xa = tpts[active && i0 < tend ? i0 : t0];
+        const float4 xb = tpts[active && i1 < tend ? i1 : t0];
+        X[pk] = make_float2(__fadd_rn(xa.x, (float)cx), __fadd_rn(xb.x, (float)cx));
+        Y[pk] = make_float2(__fadd_rn(xa.y, (float)cy), __fadd_rn(xb.y, (float)cy));
+        Z[pk] = make_float2(__fadd_rn(xa.z, (float)cz), __fadd_rn(xb.z, (float)cz));
+    }
+    const float2 floor2 = make_float2(kR2Floor, kR2Floor);
+    float2 acc[NPK], acc2[NPK];
+#pragma unroll
+    for (int pk = 0; pk < NPK; ++pk)
+        acc[pk] = acc2[pk] = make_float2(0.0f, 0.0f);
+    const int ns = lpre[64];
+    for (int base = 0; base < ns; base += kBoxStage) {
+        const int cnt = min(kBoxStage, ns - base);
+        for (int g = tid; g < cnt; g += kP2PThreads) {
+            const int gg = base + g;
+            int lo = 0, hi = 63; // the union leaf holding source gg: lpre[lo] <= gg < lpre[lo + 1]
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (lpre[mid] <= gg)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            const int src = lfirst[lo] + (gg - lpre[lo]);
+            const float4 u = spts[src];
+            const float s = sig[src];
+            // staged negated, in the frame of child (0, 0, 0): union leaf x index - 1
+            const float x = -__fadd_rn(u.x, (float)((lo & 3) - 1)), y = -__fadd_rn(u.y, (float)(((lo >> 2) & 3) - 1)),
+                        z = -__fadd_rn(u.z, (float)((lo >> 4) - 1));
+            stage[g] = make_float4(x, x, y, y);
+            stage[kBoxStage + g] = make_float4(z, z, s, s);
+        }
+        __syncthreads();
+        if (active) {
+            auto visit = [&](auto own, const float4 *p, float2 *a) {
+                const float4 qa = p[0];
+                const float4 qb = p[kBoxStage];
+#pragma unroll
+                for (int pk = 0; pk < NPK; ++pk) {
+                    const float2 dx = __fadd2_rn(X[pk], make_float2(qa.x, qa.y));
+                    const float2 dy = __fadd2_rn(Y[pk], make_float2(qa.z, qa.w));
+                    const float2 dz = __fadd2_rn(Z[pk], make_float2(qb.x, qb.y));
+                    float2 r2 = decltype(own)::value ? __fmul2_rn(dx, dx) : __ffma2_rn(dx, dx, floor2);
+                    r2 = __ffma2_rn(dy, dy, r2);
+                    r2 = __ffma2_rn(dz, dz, r2);
+                    const float2 K = kern2<decltype(own)::value>(kern, r2, dx, dy, dz);
+                    a[pk] = __ffma2_rn(K, make_float2(qb.z, qb.w), a[pk]);
+                }
+            };
+            // the child's neighbours: 9 rows of 3 union leaves (x = cx .. cx + 2)
+            for (int row = 0; row < 9; ++row) {
+                const int u0 = cx + 4 * (cy + row % 3) + 16 * (cz + row / 3);
+                const int A = lpre[u0], B = lpre[u0 + 1], C = lpre[u0 + 2], E = lpre[u0 + 3];
+                // runs of this row: [A, E) far, or, on the child's own row,
+                // [A, B) far, [B, C) own, [C, E) far
+                const bool ownrow = row == 4;
+                for (int part = 0; part < (ownrow ? 3 : 1); ++part) {
+                    const int r0 = ownrow ? (part == 0 ? A : part == 1 ? B : C) : A;
+                    const int r1 = ownrow ? (part == 0 ? B : part == 1 ? C : E) : E;
+                    const int lo = max(r0, base) - base, hi = min(r1, base + cnt) - base;
+                    const float4 *p = stage + lo + slice;
+                    const float4 *const pend = stage + max(hi, lo);
+                    if (ownrow && part == 1) {
+                        for (; p < pend; p += S)
+                            visit(OwnLeaf{}, p, acc);
+                    } else {
+#pragma unroll 2
+                        for (; p + S < pend; p += 2 * S) {
+                            visit(FarLeaf{}, p, acc);
+                            visit(FarLeaf{}, p + S, acc2);
+                        }
+                        if (p < pend)
+                            visit(FarLeaf{}, p, acc);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int pk = 0; pk < NPK; ++pk)
+        red[pk][tid] = active ? make_float2(acc[pk].x + acc2[pk].x, acc[pk].y + acc2[pk].y) : make_float2(0.0f, 0.0f);
+    __syncthreads();
+    if (tid < Q) {
+#pragma unroll
+        for (int pk = 0; pk < NPK; ++pk) {
+            float sa = 0.0f, sb = 0.0f;
+            for (int k = 0; k < S; ++k) {
+                const float2 v = red[pk][tid + k * Q];
+                sa += v.x;
+                sb += v.y;
+            }
+            const int i0 = t0 + 2 * pk, i1 = i0 + 1;
+            if (i0 < tend)
+                phi[i0] = scale * sa;
+            if (i1 < tend)
+                phi[i1] = scale * sb;
+        }
+    }
+}
+
 // Symmetric near field (K(d) = K(-d), the targets are the sources, one
 // right-hand side).  K(x_i, y_j) = K(x_j, y_i), so a pair of neighbour leaves
 // needs its kernel values once (the paper's remark on symmetry, Sec. 2.5):
@@ -724,7 +904,8 @@ struct CloseArgs {
     int *count;           // count pass: listed pairs per target (tree order)
     const int *first;     // fill pass: first entry of each target
     int *e_src;           // fill pass: source (tree order) of each entry
-    float *e_c1, *e_c1s, *e_cm; // fill pass: c for one RHS (ordered, symmetric) and several RHS
+    float *e_c1, *e_c1s, *e_c1b, *e_cm; // fill pass: c for one RHS (ordered by leaf, symmetric,
+                                        // ordered by box) and several RHS
 };
 
 // FP32 squared distances as the near-field kernels form them
@@ -821,6 +1002,19 @@ __global__ void __launch_bounds__(kP2PThreads) k_close_pairs(const CloseArgs A, 
                                 ez = __fsub_rn(us.z, __fadd_rn(X.z, oz));
                     K1s = kern.far(r2_rows(ex, ey, ez, false), ex, ey, ez);
                 }
+                // one RHS by level-(D-1) box (k_p2p_box): the frame of the
+                // box's first child, target at u + (cell & 1), source at
+                // u + (cell & 1) + neighbour offset
+                float K1b;
+                {
+                    const float4 us = A.spts[src];
+                    const int tx = ax & 1, ty = ay & 1, tz = az & 1;
+                    const float bx = __fsub_rn(__fadd_rn(X.x, (float)tx), __fadd_rn(us.x, (float)(tx + nid % 3 - 1)));
+                    const float by = __fsub_rn(__fadd_rn(X.y, (float)ty), __fadd_rn(us.y, (float)(ty + (nid / 3) % 3 - 1)));
+                    const float bz = __fsub_rn(__fadd_rn(X.z, (float)tz), __fadd_rn(us.z, (float)(tz + nid / 9 - 1)));
+                    const float rb = r2_rows(bx, by, bz, own);
+                    K1b = own ? kern.one(rb, bx, by, bz) : kern.far(rb, bx, by, bz);
+                }
                 // several RHS: k_p2p_gemm's form, the target's frame
                 const float rg = r2_gemm(dx, dy, dz, own);
                 const float Km = own ? kern.one(rg, dx, dy, dz) : kern.far(rg, dx, dy, dz);
@@ -828,12 +1022,14 @@ __global__ void __launch_bounds__(kP2PThreads) k_close_pairs(const CloseArgs A, 
                 const double Kx = exact(x0 - A.sx[3 * sc], x1 - A.sx[3 * sc + 1], x2 - A.sx[3 * sc + 2]);
                 const float c1 = (float)(Kx - (double)A.scale * (double)K1);
                 const float c1s = (float)(Kx - (double)A.scale * (double)K1s);
+                const float c1b = (float)(Kx - (double)A.scale * (double)K1b);
                 const float cm = (float)(Kx - (double)A.scale * (double)Km);
-                if (c1 == 0.0f && c1s == 0.0f && cm == 0.0f)
+                if (c1 == 0.0f && c1s == 0.0f && c1b == 0.0f && cm == 0.0f)
                     continue;
                 if (FILL) {
                     A.e_src[pos] = src;
                     A.e_c1[pos] = c1;
+                    A.e_c1b[pos] = c1b;
                     if (A.sym)
                         A.e_c1s[pos] = c1s;
                     A.e_cm[pos] = cm;

@@ -43,15 +43,15 @@ def sigma_dev(sig):
 
 
 def candidates(bb, plan, nrhs):
-    """Every (near order, tile, stages) the plan accepts for this nrhs."""
+    """Every (near order, tile, stages, box items) the plan accepts for this nrhs."""
     ok = []
-    for near, tile, st in itertools.product(["ordered", "symmetric"], [128, 256], [0, 2, 3, 4]):
+    for near, tile, st, box in itertools.product(["ordered", "symmetric"], [128, 256], [0, 2, 3, 4], [False, True]):
         try:
-            bb.bbfmm_set_tuning(plan.handle, nrhs, near, tile, st)
+            bb.bbfmm_set_tuning(plan.handle, nrhs, near, tile, st, near_box=box)
         except bb.BBFMMError as e:
             assert e.status == bb.BBFMM_EINVAL
             continue
-        ok.append((near, tile, st))
+        ok.append((near, tile, st, box))
     return ok
 
 
@@ -72,12 +72,13 @@ def test_every_candidate_gives_the_same_result(bb, oracle, kind, kid, ell, p, de
     if precision in ("fp16x3", "bf16x3"):
         assert {c[1] for c in cands} == {128, 256}
     assert {c[0] for c in cands} == {"ordered", "symmetric"}
+    assert {(c[0], c[3]) for c in cands} == {("ordered", False), ("ordered", True), ("symmetric", False)}
     s = sigma_dev(sig)
     outs = {}
     for c in cands:
         bb.bbfmm_set_tuning(plan.handle, 1, *c)
         t = bb.bbfmm_get_tuning(plan.handle, 1)
-        assert (t.m2l_tile, t.m2l_stages, t.measured) == (c[1], c[2], 0)
+        assert (t.m2l_tile, t.m2l_stages, t.measured, t.near_box) == (c[1], c[2], 0, int(c[3]))
         outs[c] = plan.matvec(s).cpu().numpy().astype(np.float64)
         assert bb.bbfmm_status(plan.handle) == 0
     plan.close()
@@ -107,8 +108,8 @@ def test_tuned_choice_is_a_candidate_and_reproducible(bb):
     assert bb.bbfmm_get_tuning(plan.handle, 1).measured == 1
     # a plan told the first choice explicitly gives the same bits
     other = make(bb, pts, autotune=False)
-    bb.bbfmm_set_tuning(other.handle, 1, t.near_mode, t.m2l_tile, t.m2l_stages)
-    bb.bbfmm_set_tuning(plan.handle, 1, t.near_mode, t.m2l_tile, t.m2l_stages)
+    bb.bbfmm_set_tuning(other.handle, 1, t.near_mode, t.m2l_tile, t.m2l_stages, t.near_box)
+    bb.bbfmm_set_tuning(plan.handle, 1, t.near_mode, t.m2l_tile, t.m2l_stages, t.near_box)
     b, c = plan.matvec(sig), other.matvec(sig)
     torch.cuda.synchronize()
     assert torch.equal(a, b) and torch.equal(b, c)
@@ -134,6 +135,8 @@ def test_several_rhs_and_defaults(bb):
         bb.bbfmm_set_tuning(plan.handle, 8, "ordered", 64, 0)
     with pytest.raises(bb.BBFMMError):         # more stages than fit
         bb.bbfmm_set_tuning(plan.handle, 8, "ordered", 256, 7)
+    with pytest.raises(bb.BBFMMError):         # box items are a one-RHS form
+        bb.bbfmm_set_tuning(plan.handle, 8, "ordered", 256, 0, near_box=True)
     cands = candidates(bb, plan, 8)
     assert cands and all(c[0] == "ordered" for c in cands)
     s = sigma_dev(sig)
@@ -147,5 +150,30 @@ def test_several_rhs_and_defaults(bb):
     fixed = make(bb, pts, nrhs=8, autotune=False)
     fixed.matvec(s)
     t = bb.bbfmm_get_tuning(fixed.handle, 8)
-    assert (t.measured, t.m2l_tile, t.m2l_stages, t.near_mode) == (0, 256, 0, 1)
+    assert (t.measured, t.m2l_tile, t.m2l_stages, t.near_mode, t.near_box) == (0, 256, 0, 1, 0)
     fixed.close()
+
+
+@pytest.mark.parametrize("kind,n,depth", [("uniform", 300_000, 6), ("clustered", 200_000, 5), ("uniform", 5000, 1)])
+def test_box_items_match_leaf_items(bb, oracle, kind, n, depth):
+    """Leaves of a few points: the ordered near field by level-(D-1) box
+    items gives the leaf items' result to FP32 rounding, and both match the
+    oracle (the close pairs corrected in each form's frame)."""
+    pts = W.make_points(kind, n, seed=707)
+    sig = W.uniform_sigma(n, seed=708).astype(np.float32)
+    plan = make(bb, pts, 1, 4, depth, "fp16x3")
+    s = sigma_dev(sig)
+    tile = bb.bbfmm_get_tuning(plan.handle, 1).m2l_tile
+    bb.bbfmm_set_tuning(plan.handle, 1, "ordered", tile, 0, near_box=False)
+    a = plan.matvec(s).cpu().numpy().astype(np.float64)
+    bb.bbfmm_set_tuning(plan.handle, 1, "ordered", tile, 0, near_box=True)
+    b = plan.matvec(s).cpu().numpy().astype(np.float64)
+    assert bb.bbfmm_get_tuning(plan.handle, 1).near_box == 1
+    assert bb.bbfmm_status(plan.handle) == 0
+    plan.close()
+    idx = np.sort(np.random.default_rng(709).choice(n, min(n, 1500), replace=False))
+    ref = oracle.bbfmm(pts, sig.astype(np.float64), 1, 4, depth, lo=W.UNIT_LO, side=W.UNIT_SIDE, sample=idx)
+    print("%s n=%d d%d: box vs leaf items %.2e; vs oracle %.2e / %.2e"
+          % (kind, n, depth, rel(b, a), rel(b[idx], ref), rel(a[idx], ref)))
+    assert rel(b, a) <= 2e-6
+    assert rel(b[idx], ref) <= 1e-5 and rel(a[idx], ref) <= 1e-5

@@ -13,7 +13,7 @@ field (``opts.close_refine``, on by default).  These tests check:
 * exact duplicates (K(0) = 0 for the singular kernels) and distinct points
   that coincide in FP32, in one leaf and across a leaf face, element by
   element against the FP64 direct sum, in every near-field form (symmetric,
-  ordered, several right-hand sides);
+  ordered by leaf and by level-(D-1) box, several right-hand sides);
 * separate target sets and a registered user kernel take the same path.
 """
 import numpy as np
@@ -41,12 +41,17 @@ def bb():
 
 def run(bb, pts, sig, kid, p, depth, ell=1.0, eps=1e-7, near="auto", refine=True, precision="fp32",
         targets=None):
+    """near: "auto", "ordered", "symmetric", or "box" (ordered, a work item
+    per level-(D-1) box)."""
     dev = torch.device("cuda:0")
     sig = np.asarray(sig, dtype=np.float32)
     nrhs = 1 if sig.ndim == 1 else sig.shape[1]
     plan = bb.Plan(torch.from_numpy(np.ascontiguousarray(pts)).to(dev), kid, p, depth, ell=ell, svd_eps=eps,
-                   precision=precision, domain=UNIT, max_nrhs=nrhs, near_mode=near, close_refine=refine,
-                   targets=None if targets is None else torch.from_numpy(targets).to(dev))
+                   precision=precision, domain=UNIT, max_nrhs=nrhs, near_mode="ordered" if near == "box" else near,
+                   close_refine=refine, targets=None if targets is None else torch.from_numpy(targets).to(dev))
+    if near == "box":
+        t = bb.bbfmm_get_tuning(plan.handle, nrhs)
+        bb.bbfmm_set_tuning(plan.handle, nrhs, "ordered", t.m2l_tile, t.m2l_stages, near_box=True)
     s = torch.from_numpy(np.ascontiguousarray(sig.T if nrhs > 1 else sig)).to(dev)
     phi = plan.matvec(s)
     torch.cuda.synchronize()
@@ -97,7 +102,7 @@ def coincident_set(n, seed):
 
 
 @pytest.mark.parametrize("kid", [K_INV_R, K_INV_R2])
-@pytest.mark.parametrize("near,nrhs", [("symmetric", 1), ("ordered", 1), ("auto", 3)])
+@pytest.mark.parametrize("near,nrhs", [("symmetric", 1), ("ordered", 1), ("box", 1), ("auto", 3)])
 @pytest.mark.parametrize("depth", [0, 1, 2])
 def test_coincident_points_element_by_element(bb, oracle, kid, near, nrhs, depth):
     """Depth 0..2 with a small order: at depth 0 / 1 the result is the near
@@ -105,6 +110,8 @@ def test_coincident_points_element_by_element(bb, oracle, kid, near, nrhs, depth
     its approximation (checked against the oracle FMM).  Element-wise bound:
     |phi_gpu - phi_ref| <= 1e-5 sum_j |K_ij sigma_j| per target (the row's
     own scale: the close pairs make some rows ~1e13 times the others)."""
+    if near == "box" and depth == 0:
+        pytest.skip("box work items need a level D - 1")
     pts = coincident_set(2500, seed=900 + depth)
     n = pts.shape[0]
     sig = W.uniform_sigma(n, nrhs=nrhs, seed=901).astype(np.float32).astype(np.float64)

@@ -88,14 +88,15 @@ def test_same_points_as_targets_equal_the_square_plan(bb):
     """Targets = sources through the separate-target entry point gives the
     square plan's result bit for bit (same tree, same kernels, same order:
     the square plan with the ordered near field, which a target set always
-    takes)."""
+    takes, and both with the default launch choices rather than each its own
+    measured ones)."""
     n = 30_000
     dev = torch.device("cuda:0")
     pts = torch.from_numpy(W.clustered_points(n, seed=208)).to(dev)
     sig = torch.from_numpy(W.uniform_sigma(n, seed=209).astype(np.float32)).to(dev)
     for prec in ("fp32", "fp16x3"):
-        a = bb.Plan(pts, K_INV_R, 5, 5, precision=prec, domain=UNIT, near_mode="ordered")
-        b = bb.Plan(pts, K_INV_R, 5, 5, precision=prec, domain=UNIT, targets=pts.clone())
+        a = bb.Plan(pts, K_INV_R, 5, 5, precision=prec, domain=UNIT, near_mode="ordered", autotune=False)
+        b = bb.Plan(pts, K_INV_R, 5, 5, precision=prec, domain=UNIT, targets=pts.clone(), autotune=False)
         pa, pb = a.matvec(sig).cpu().numpy(), b.matvec(sig).cpu().numpy()
         ia, ib = a.info(), b.info()
         a.close()
