@@ -164,7 +164,12 @@ typedef struct {
                        box (its 8 leaves' targets against the 4x4x4 leaves around
                        it, staged once), for leaves of a few points; 0 = a work
                        item per leaf (default).  Needs depth >= 1 */
-    int reserved[3];
+    int leaf_gemm;  /* 1: the leaf level's compression M~ = V^T M runs as a
+                       tensor-core GEMM (3 x TF32) after the upward pass (the
+                       default where the plan has it: Chebyshev nodes, depth >= 2,
+                       V fits in shared memory, e.g. p <= 5); 0: inside the
+                       upward pass on the CUDA cores */
+    int reserved[2];
 } bbfmm_tuning;
 
 /*

@@ -21,6 +21,7 @@
 // of one octant, a block of consecutive parent cells of one source octant.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -138,6 +139,7 @@ struct DevOps {
     std::vector<float *> Ut; // [r][p3p]    decompress weights (U transposed)
     std::vector<float *> C;  // [316][rows64][rp]
     std::vector<float *> Chi, Clo; // split copies for the tensor-core M2L (hi/lo)
+    std::vector<float *> Vt_hi, Vt_lo; // [rp][p3p] V transposed, TF32 hi / lo (leaf compression GEMM)
     // 16-bit split copies, made on first use: [0] = FP16 (scaled by c16_scale),
     // [1] = BF16; same [316][rows64][rp] layout
     std::vector<uint16_t *> C16hi[2], C16lo[2];
@@ -177,6 +179,7 @@ struct CloseList {
 struct Tuning {
     bool near_sym = false; // one-RHS near field in symmetric order
     bool near_box = false; // one-RHS ordered near field in work items of one level-(D-1) box
+    bool leaf_gemm = false; // leaf compression as a tensor-core GEMM after the upward pass
     int m2l_nt = 128;      // targets per tensor-core M2L tile
     int m2l_stages = 0;    // tensor-core M2L pipeline stages (0 = as many as fit)
     bool measured = false; // chosen by a measured sweep (or its cache)
@@ -206,6 +209,8 @@ struct bbfmm_plan_impl {
     int *tleaf_off = nullptr;
     int4 *chunks = nullptr; // near-field work items over the target leaves
     int nchunks = 0;
+    float *Mleaf = nullptr;    // [R][8^D][p3p] leaf multipoles for the compression GEMM (or null)
+    bool leaf_gemm = false;    // leaf compression by the GEMM (tuning)
     int4 *box_items = nullptr; // near-field work items of one level-(D-1) box (D >= 1)
     int nbox_items = 0;
     bool near_box = false;     // one-RHS ordered near field by box items (tuning)
@@ -309,8 +314,21 @@ struct PassArgs {
     int *count[kMaxDepth + 1];  // upward arrival counters, levels 2..D-2
     int keep;
     float *Ftop;                // D >= 4: local coefficients of the level-(D-2) boxes, [box][nrhs][p^3]
+    float *Mleaf;               // non-null: store leaf M here ([R][8^D][p3p]) instead of compressing it
 };
 cudaError_t launch_upward(const PassArgs &A, int p, cudaStream_t s);
+// box_gemm.cu: the leaf compression M~ = V^T M as a tensor-core GEMM (3 x TF32)
+struct LeafCompressArgs {
+    const float *M;              // [R][nb][p3p] leaf multipoles, zero past p^3
+    const float *Vt_hi, *Vt_lo;  // [rp][p3p] V transposed, TF32 split
+    int64_t nb;                  // leaf boxes (8^D)
+    int nrhs, R, r, rp, p3p, H;  // r = rank of the leaf level; H = 2^(D-1)
+    float *out, *out_hi, *out_lo; // M~ of the leaf level (and its TF32 split, or null)
+    unsigned *maxbits;           // the level's max |M~| slot, or null
+    int *status;
+};
+bool leaf_compress_fits(int r, int p3p);
+cudaError_t launch_leaf_compress(const LeafCompressArgs &L, cudaStream_t s);
 cudaError_t launch_downward(const PassArgs &A, int p, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
@@ -386,6 +404,11 @@ void m2l_active_tiles(int D, int nt, const std::vector<uint8_t> &leaf_occ, std::
 int m2l_tile_choices(int precision, int *nt);
 // pipeline stages that fit in shared memory for a precision and tile size
 int m2l_max_stages(int precision, int nt);
+// m2l_tc.cu: a 2D FP32 TMA map (box_inner x box_outer, 128-byte swizzle) and
+// the SM count, for the leaf-box GEMMs
+cudaError_t tc_encode_2d_f32(CUtensorMap *tm, const void *ptr, uint64_t inner, uint64_t outer, uint64_t row_bytes,
+                             uint32_t box_inner, uint32_t box_outer);
+int tc_sm_count();
 // p2p.cu
 // targets: tree-order coordinates and the work items over their leaves;
 // sources: tree-order coordinates, weights (ns x nrhs) and leaf offsets

@@ -55,7 +55,7 @@ static int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 // operator cache: one device copy per (kernel, ell, p, eps, depth, side)
 DevOps::~DevOps()
 {
-    for (auto *v : {&V, &Ut, &C, &Chi, &Clo})
+    for (auto *v : {&V, &Ut, &C, &Chi, &Clo, &Vt_hi, &Vt_lo})
         for (float *ptr : *v)
             if (ptr)
                 cudaFree(ptr);
@@ -173,6 +173,24 @@ static int get_ops(int kernel, double ell, int p, double eps, int depth, double 
         CUDA_TRY(cudaMemcpy(dV, V.data(), V.size() * 4, cudaMemcpyHostToDevice));
         CUDA_TRY(cudaMemcpy(dUt, Ut.data(), Ut.size() * 4, cudaMemcpyHostToDevice));
         d->bytes += (int64_t)(V.size() + Ut.size()) * 4;
+        if (host->interp == BBFMM_INTERP_CHEBYSHEV) {
+            // V transposed ([rp][p3p], K = p3 contiguous), split into TF32 hi / lo
+            // for the leaf compression GEMM; columns past the level's rank zero
+            std::vector<float> Vt((size_t)rp * p3p, 0.f), Vh(Vt.size()), Vl(Vt.size());
+            const int rk = host->rl[k];
+            for (int a = 0; a < rk; ++a)
+                for (int i = 0; i < p3; ++i)
+                    Vt[(size_t)a * p3p + i] = (float)host->V[k][(size_t)i * r + a];
+            split_tf32(Vt.data(), Vh.data(), Vl.data(), (int64_t)Vt.size());
+            float *dh = nullptr, *dl = nullptr;
+            CUDA_TRY(cudaMalloc(&dh, Vt.size() * 4));
+            d->Vt_hi.push_back(dh);
+            CUDA_TRY(cudaMalloc(&dl, Vt.size() * 4));
+            d->Vt_lo.push_back(dl);
+            CUDA_TRY(cudaMemcpy(dh, Vh.data(), Vt.size() * 4, cudaMemcpyHostToDevice));
+            CUDA_TRY(cudaMemcpy(dl, Vl.data(), Vt.size() * 4, cudaMemcpyHostToDevice));
+            d->bytes += (int64_t)(2 * Vt.size()) * 4;
+        }
         if (host->interp == BBFMM_INTERP_UNIFORM) {
             // kernel spectra for the Fourier-domain M2L
             const std::vector<double> &kh = host->khat[k];
@@ -301,6 +319,7 @@ static Tuning default_tuning(const bbfmm_plan_impl *P, int nrhs = 1)
     t.near_sym = P->near_sym_default && nrhs == 1;
     t.m2l_nt = P->m2l_nsets > 0 ? P->m2l_set[0].nt : 128;
     t.m2l_stages = 0;
+    t.leaf_gemm = P->Mleaf != nullptr;
     return t;
 }
 
@@ -308,6 +327,7 @@ static void apply_tuning(bbfmm_plan_impl *P, const Tuning &t)
 {
     P->near_sym = t.near_sym && P->near_slots != nullptr;
     P->near_box = t.near_box && !P->near_sym && P->box_items != nullptr;
+    P->leaf_gemm = t.leaf_gemm && P->Mleaf != nullptr;
     for (int k = 0; k < P->m2l_nsets; ++k) {
         const bbfmm_plan_impl::TileSet &T = P->m2l_set[k];
         if (T.nt != t.m2l_nt)
@@ -335,6 +355,8 @@ static bool tuning_valid(const bbfmm_plan_impl *P, const Tuning &t)
     if (t.near_sym && !P->near_slots)
         return false;
     if (t.near_box && (t.near_sym || !P->box_items))
+        return false;
+    if (t.leaf_gemm && !P->Mleaf)
         return false;
     bool tile = false;
     for (int k = 0; k < P->m2l_nsets; ++k)
@@ -603,6 +625,11 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
     PTRY(plan_alloc(P, (void **)&P->phi_near, 4 * nt * R, false, s));
     if (D >= 4)
         PTRY(plan_alloc(P, (void **)&P->Ftop, 4 * (1LL << (3 * (D - 2))) * R * P->p3, false, s));
+    // leaf multipoles for the compression GEMM, zero past p^3 and for empty
+    // leaves; the TMA setup is made here, outside any stream capture
+    if (P->nodeset == BBFMM_INTERP_CHEBYSHEV && D >= 2 && !P->ops->Vt_hi.empty() &&
+        leaf_compress_fits(P->ops->rl[P->ops->nlev == 1 ? 0 : D - 2], P->ops->p3p) && tc_sm_count() > 0)
+        PTRY(plan_alloc(P, (void **)&P->Mleaf, 4 * (int64_t)R * (1LL << (3 * D)) * P->ops->p3p, true, s));
     if (P->near_sym && P->near_auto) {
         // occupancy of the leaves the near-field work meets: pairs per point
         // over the 27 neighbours.  Measured at 1M / 2M points: faster at ~30,
@@ -729,6 +756,7 @@ static PassArgs pass_args(const bbfmm_plan_impl *P, int nrhs, bool split16)
     A.maxbits = split16 ? P->a16_max : nullptr;
     A.keep = P->keep_coeffs ? 1 : 0;
     A.Ftop = P->Ftop;
+    A.Mleaf = P->leaf_gemm ? P->Mleaf : nullptr;
     for (int l = 2; l <= P->D; ++l) {
         const Level &L = P->lev[l];
         A.M[l] = L.M;
@@ -794,6 +822,26 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
         if (split16)
             CUDA_TRY(cudaMemsetAsync(P->a16_max, 0, 4 * (kMaxDepth + 1), fs));
         CUDA_TRY(launch_upward(A, p, fs));
+        if (A.Mleaf) { // the leaf level's compression as a tensor-core GEMM
+            const int opl = O.nlev == 1 ? 0 : D - 2;
+            LeafCompressArgs L = {};
+            L.M = P->Mleaf;
+            L.Vt_hi = O.Vt_hi[opl];
+            L.Vt_lo = O.Vt_lo[opl];
+            L.nb = 1LL << (3 * D);
+            L.nrhs = nrhs;
+            L.R = P->max_nrhs;
+            L.r = O.rl[opl];
+            L.rp = O.rp;
+            L.p3p = O.p3p;
+            L.H = 1 << (D - 1);
+            L.out = P->lev[D].Mt;
+            L.out_hi = P->lev[D].Mt_hi;
+            L.out_lo = P->lev[D].Mt_lo;
+            L.maxbits = split16 ? P->a16_max + D : nullptr;
+            L.status = P->status;
+            CUDA_TRY(launch_leaf_compress(L, fs));
+        }
         if (split16) {
             Split16Args S = {};
             S.fmt = P->precision == BBFMM_PREC_FP16X3 ? 0 : 1;
@@ -969,34 +1017,7 @@ static int autotune_sweep(bbfmm_plan_impl *P, int nrhs, bool use_cache, cudaStre
             return BBFMM_OK;
         }
     }
-    std::vector<Tuning> cand;
     const Tuning base = default_tuning(P, nrhs);
-    // near-field forms (symmetric, box items): 0 ordered by leaf, 1 symmetric, 2 ordered by box
-    std::vector<int> nears = {nrhs == 1 && base.near_sym ? 1 : 0};
-    if (nrhs == 1 && P->near_slots && P->near_auto)
-        nears = {0, 1};
-    if (nrhs == 1 && P->box_items && !(P->near_slots && !P->near_auto))
-        nears.push_back(2);
-    for (int nf : nears) {
-        if (!tensor_m2l(P)) {
-            Tuning t = base;
-            t.near_sym = nf == 1;
-            t.near_box = nf == 2;
-            cand.push_back(t);
-            continue;
-        }
-        for (int k = 0; k < P->m2l_nsets; ++k) {
-            const int mx = m2l_max_stages(P->precision, P->m2l_set[k].nt);
-            for (int st = 2; st <= mx; ++st) {
-                Tuning t = base;
-                t.near_sym = nf == 1;
-                t.near_box = nf == 2;
-                t.m2l_nt = P->m2l_set[k].nt;
-                t.m2l_stages = st == mx ? 0 : st;
-                cand.push_back(t);
-            }
-        }
-    }
     if (!P->io_sigma) {
         PTRY(plan_alloc(P, (void **)&P->io_sigma, 4 * P->n * P->max_nrhs, false, s));
         PTRY(plan_alloc(P, (void **)&P->io_phi, 4 * P->nt * P->max_nrhs, false, s));
@@ -1014,7 +1035,16 @@ static int autotune_sweep(bbfmm_plan_impl *P, int nrhs, bool use_cache, cudaStre
     int st = BBFMM_OK;
     float best = INFINITY;
     Tuning chosen = base;
-    for (const Tuning &t : cand) {
+    std::vector<Tuning> seen;
+    // one candidate: an untimed matvec, then kTuneReps timed ones
+    auto measure = [&](const Tuning &t) {
+        for (const Tuning &u : seen)
+            if (u.near_sym == t.near_sym && u.near_box == t.near_box && u.m2l_nt == t.m2l_nt &&
+                u.m2l_stages == t.m2l_stages && u.leaf_gemm == t.leaf_gemm)
+                return;
+        seen.push_back(t);
+        if (st != BBFMM_OK || !tuning_valid(P, t))
+            return;
         apply_tuning(P, t);
         st = matvec_device(P, P->io_sigma, P->io_phi, nrhs, s);
         if (st == BBFMM_OK && cudaEventRecord(a, s) != cudaSuccess)
@@ -1024,13 +1054,49 @@ static int autotune_sweep(bbfmm_plan_impl *P, int nrhs, bool use_cache, cudaStre
         if (st == BBFMM_OK && (cudaEventRecord(b, s) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess))
             st = fail(BBFMM_ECUDA, "timing a tuning candidate failed");
         if (st != BBFMM_OK)
-            break;
+            return;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, a, b);
         if (ms < best) {
             best = ms;
             chosen = t;
         }
+    };
+    // the choices are nearly independent (different stages of the matvec), so
+    // they are measured one group at a time, each against the best so far:
+    // 1. the tensor-core M2L's tile size and pipeline depth
+    if (tensor_m2l(P))
+        for (int k = 0; k < P->m2l_nsets; ++k) {
+            const int mx = m2l_max_stages(P->precision, P->m2l_set[k].nt);
+            for (int sg = 2; sg <= mx; ++sg) {
+                Tuning t = base;
+                t.m2l_nt = P->m2l_set[k].nt;
+                t.m2l_stages = sg == mx ? 0 : sg;
+                measure(t);
+            }
+        }
+    else
+        measure(base);
+    // 2. the near-field form of one-RHS matvecs: ordered by leaf, symmetric
+    // (AUTO mode, symmetric kernel, one point set), ordered by box
+    if (nrhs == 1) {
+        const Tuning m = chosen;
+        for (int nf = 0; nf < 3; ++nf) {
+            if (nf == 1 && !(P->near_slots && P->near_auto))
+                continue;
+            if (nf != 1 && P->near_slots && !P->near_auto)
+                continue; // near_mode SYMMETRIC: the caller's choice stands
+            Tuning t = m;
+            t.near_sym = nf == 1;
+            t.near_box = nf == 2;
+            measure(t);
+        }
+    }
+    // 3. the leaf compression: tensor-core GEMM or inside the upward pass
+    if (P->Mleaf) {
+        Tuning t = chosen;
+        t.leaf_gemm = !t.leaf_gemm;
+        measure(t);
     }
     P->timing = tm;
     cudaEventDestroy(a);
@@ -1534,6 +1600,7 @@ int bbfmm_get_tuning(bbfmm_plan_t plan, int nrhs, bbfmm_tuning *out)
     out->m2l_stages = t.m2l_stages;
     out->measured = t.measured ? 1 : 0;
     out->near_box = t.near_box && !t.near_sym && plan->box_items && nrhs == 1 ? 1 : 0;
+    out->leaf_gemm = t.leaf_gemm && plan->Mleaf ? 1 : 0;
     return BBFMM_OK;
 }
 
@@ -1550,13 +1617,15 @@ int bbfmm_set_tuning(bbfmm_plan_t plan, int nrhs, const bbfmm_tuning *in)
     t.m2l_nt = in->m2l_tile;
     t.m2l_stages = in->m2l_stages;
     t.near_box = in->near_box != 0;
+    t.leaf_gemm = in->leaf_gemm != 0;
     if ((t.near_sym || t.near_box) && nrhs != 1)
         return fail(BBFMM_EINVAL, "the symmetric and box near-field forms run one right-hand side only");
     if (t.near_sym && nrhs != 1)
         return fail(BBFMM_EINVAL, "the symmetric near field runs one right-hand side only");
     if (!tuning_valid(plan, t))
-        return fail(BBFMM_EINVAL, "this plan cannot run near_mode %d, near_box %d, m2l_tile %d, m2l_stages %d",
-                    in->near_mode, in->near_box, in->m2l_tile, in->m2l_stages);
+        return fail(BBFMM_EINVAL,
+                    "this plan cannot run near_mode %d, near_box %d, m2l_tile %d, m2l_stages %d, leaf_gemm %d",
+                    in->near_mode, in->near_box, in->m2l_tile, in->m2l_stages, in->leaf_gemm);
     int expected = 0;
     if (!plan->busy.compare_exchange_strong(expected, 1))
         return fail(BBFMM_EBUSY, "plan is in use by another thread");

@@ -615,6 +615,30 @@ static cudaError_t encode_src(CUtensorMap *tm, const void *ptr, int H, int R, in
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// a 2D FP32 matrix (outer rows of inner elements, row pitch row_bytes), box
+// of box_inner x box_outer with the 128-byte swizzle (box_inner = 32); shared
+// with the leaf-box GEMMs (box_gemm.cu)
+cudaError_t tc_encode_2d_f32(CUtensorMap *tm, const void *ptr, uint64_t inner, uint64_t outer, uint64_t row_bytes,
+                             uint32_t box_inner, uint32_t box_outer)
+{
+    cudaError_t e = tc_init();
+    if (e != cudaSuccess)
+        return e;
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+    cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)ptr, dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+int tc_sm_count()
+{
+    return tc_init() == cudaSuccess ? g_num_sms : 0;
+}
+
 // C (operators): dims (rp, rows64, 316); box (32 elements of K, nb rows, 1)
 static cudaError_t encode_op(CUtensorMap *tm, const void *ptr, int rp, int rows64, int nb, int fmt)
 {

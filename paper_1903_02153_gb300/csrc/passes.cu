@@ -315,6 +315,19 @@ __device__ void compress8(const PassArgs &A, int l, const float *X, int64_t box0
     flush_max(A, l, mx);
 }
 
+// leaf multipoles for the compression GEMM: columns box0 .. box0 + ncol - 1
+// of X ([P3][XS]) into rows (c, box) of A.Mleaf ([R][8^D][p3p])
+template <int P, int XS>
+__device__ void store_leaves(const PassArgs &A, const float *X, int64_t box0, int ncol, int c)
+{
+    constexpr int P3 = P * P * P;
+    const int64_t nb = 1LL << (3 * A.D);
+    for (int q = threadIdx.x; q < ncol * P3; q += kThreads) {
+        const int o = q / P3, i = q - o * P3;
+        A.Mleaf[((int64_t)c * nb + box0 + o) * A.p3p + i] = X[i * XS + o];
+    }
+}
+
 // compress one box at level l from F32 coefficients X[P3]
 template <int P>
 __device__ void compress1(const PassArgs &A, int l, const float *X, int64_t box, int c)
@@ -433,8 +446,12 @@ __global__ void __launch_bounds__(kThreads, kUpMinBlocks<P>) k_upward(const __gr
     }
     __syncthreads();
 
-    // ---- compress the leaves
-    compress8<P>(A, D, sMT, 8 * b, c, zero);
+    // ---- compress the leaves (or leave them to the compression GEMM; a box
+    // without points keeps the zeros its rows were given at plan time)
+    if (!A.Mleaf)
+        compress8<P>(A, D, sMT, 8 * b, c, zero);
+    else if (!zero)
+        store_leaves<P, 8>(A, sMT, 8 * b, 8, c);
     if (D - 1 < 2)
         return;
 
@@ -846,7 +863,10 @@ __global__ void __launch_bounds__(kThreads) k_upward_wide(const __grid_constant_
     for (int j = 0; j < 8; ++j)
         p2m_leaf<P, 64>(A, 64 * B + 8 * j + w, c, sScr + w * 96 * P, sLeaf, 8 * j + w);
     __syncthreads();
-    compress64<P>(A, sLeaf, B, c, zero);
+    if (!A.Mleaf)
+        compress64<P>(A, sLeaf, B, c, zero);
+    else if (!zero)
+        store_leaves<P, 64>(A, sLeaf, 64 * B, 64, c);
     // the 8 boxes of level D-1: M2M of their leaves, compression
     for (int m = 0; m < 8; ++m)
         m2m8<P, 64, 8>(A.T, sLeaf + 8 * m, sScr, sScr + 8 * P3, sMid + m);

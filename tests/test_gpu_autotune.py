@@ -43,15 +43,17 @@ def sigma_dev(sig):
 
 
 def candidates(bb, plan, nrhs):
-    """Every (near order, tile, stages, box items) the plan accepts for this nrhs."""
+    """Every (near order, tile, stages, box items, leaf GEMM) the plan accepts
+    for this nrhs."""
     ok = []
-    for near, tile, st, box in itertools.product(["ordered", "symmetric"], [128, 256], [0, 2, 3, 4], [False, True]):
+    for near, tile, st, box, lg in itertools.product(["ordered", "symmetric"], [128, 256], [0, 2, 3, 4],
+                                                     [False, True], [False, True]):
         try:
-            bb.bbfmm_set_tuning(plan.handle, nrhs, near, tile, st, near_box=box)
+            bb.bbfmm_set_tuning(plan.handle, nrhs, near, tile, st, near_box=box, leaf_gemm=lg)
         except bb.BBFMMError as e:
             assert e.status == bb.BBFMM_EINVAL
             continue
-        ok.append((near, tile, st, box))
+        ok.append((near, tile, st, box, lg))
     return ok
 
 
@@ -73,12 +75,14 @@ def test_every_candidate_gives_the_same_result(bb, oracle, kind, kid, ell, p, de
         assert {c[1] for c in cands} == {128, 256}
     assert {c[0] for c in cands} == {"ordered", "symmetric"}
     assert {(c[0], c[3]) for c in cands} == {("ordered", False), ("ordered", True), ("symmetric", False)}
+    assert {c[4] for c in cands} == {False, True}     # the leaf compression GEMM or the pass
     s = sigma_dev(sig)
     outs = {}
     for c in cands:
         bb.bbfmm_set_tuning(plan.handle, 1, *c)
         t = bb.bbfmm_get_tuning(plan.handle, 1)
-        assert (t.m2l_tile, t.m2l_stages, t.measured, t.near_box) == (c[1], c[2], 0, int(c[3]))
+        assert (t.m2l_tile, t.m2l_stages, t.measured, t.near_box, t.leaf_gemm) == (c[1], c[2], 0, int(c[3]),
+                                                                                  int(c[4]))
         outs[c] = plan.matvec(s).cpu().numpy().astype(np.float64)
         assert bb.bbfmm_status(plan.handle) == 0
     plan.close()
@@ -108,8 +112,8 @@ def test_tuned_choice_is_a_candidate_and_reproducible(bb):
     assert bb.bbfmm_get_tuning(plan.handle, 1).measured == 1
     # a plan told the first choice explicitly gives the same bits
     other = make(bb, pts, autotune=False)
-    bb.bbfmm_set_tuning(other.handle, 1, t.near_mode, t.m2l_tile, t.m2l_stages, t.near_box)
-    bb.bbfmm_set_tuning(plan.handle, 1, t.near_mode, t.m2l_tile, t.m2l_stages, t.near_box)
+    bb.bbfmm_set_tuning(other.handle, 1, t.near_mode, t.m2l_tile, t.m2l_stages, t.near_box, t.leaf_gemm)
+    bb.bbfmm_set_tuning(plan.handle, 1, t.near_mode, t.m2l_tile, t.m2l_stages, t.near_box, t.leaf_gemm)
     b, c = plan.matvec(sig), other.matvec(sig)
     torch.cuda.synchronize()
     assert torch.equal(a, b) and torch.equal(b, c)
@@ -150,7 +154,7 @@ def test_several_rhs_and_defaults(bb):
     fixed = make(bb, pts, nrhs=8, autotune=False)
     fixed.matvec(s)
     t = bb.bbfmm_get_tuning(fixed.handle, 8)
-    assert (t.measured, t.m2l_tile, t.m2l_stages, t.near_mode, t.near_box) == (0, 256, 0, 1, 0)
+    assert (t.measured, t.m2l_tile, t.m2l_stages, t.near_mode, t.near_box, t.leaf_gemm) == (0, 256, 0, 1, 0, 1)
     fixed.close()
 
 
@@ -177,3 +181,34 @@ def test_box_items_match_leaf_items(bb, oracle, kind, n, depth):
           % (kind, n, depth, rel(b, a), rel(b[idx], ref), rel(a[idx], ref)))
     assert rel(b, a) <= 2e-6
     assert rel(b[idx], ref) <= 1e-5 and rel(a[idx], ref) <= 1e-5
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32x3", "fp16x3", "bf16x3"])
+@pytest.mark.parametrize("depth,nrhs,kind", [(2, 1, "uniform"), (5, 1, "uniform"), (6, 1, "clustered"),
+                                             (4, 3, "uniform")])
+def test_leaf_compression_gemm_matches_the_pass(bb, oracle, precision, depth, nrhs, kind):
+    """The leaf level's compression as a 3 x TF32 tensor-core GEMM gives the
+    pass's FP32 compression to FP32 rounding, for every M2L form (FP32 M~,
+    its TF32 split, the 16-bit split with the level scale from the GEMM's max),
+    one and several right-hand sides (a plan holding more columns than the
+    call uses)."""
+    n = {2: 3000, 4: 40_000, 5: 200_000, 6: 300_000}[depth]
+    pts = W.make_points(kind, n, seed=710 + depth)
+    sig = W.uniform_sigma(n, nrhs=nrhs, seed=711).astype(np.float32)
+    plan = bb.Plan(torch.from_numpy(pts).cuda(), 1, 5, depth, svd_eps=1e-7, precision=precision, domain=UNIT,
+                   max_nrhs=nrhs + 1, autotune=False)
+    s = sigma_dev(sig)
+    t = bb.bbfmm_get_tuning(plan.handle, nrhs)
+    assert t.leaf_gemm == 1
+    a = plan.matvec(s).cpu().numpy().astype(np.float64)
+    bb.bbfmm_set_tuning(plan.handle, nrhs, t.near_mode, t.m2l_tile, t.m2l_stages, t.near_box, leaf_gemm=False)
+    b = plan.matvec(s).cpu().numpy().astype(np.float64)
+    assert bb.bbfmm_status(plan.handle) == 0
+    plan.close()
+    a, b = (a.T, b.T) if nrhs > 1 else (a, b)
+    idx = np.sort(np.random.default_rng(712).choice(n, min(n, 1000), replace=False))
+    ref = oracle.bbfmm(pts, sig.astype(np.float64), 1, 5, depth, lo=W.UNIT_LO, side=W.UNIT_SIDE, sample=idx)
+    d, e = rel(a, b), rel(a[idx], ref)
+    print("%s depth %d nrhs %d: GEMM vs pass %.2e, GEMM vs oracle %.2e" % (precision, depth, nrhs, d, e))
+    assert d <= (2e-5 if precision == "bf16x3" else 2e-6)
+    assert e <= (1e-4 if precision == "bf16x3" else 1e-5)
