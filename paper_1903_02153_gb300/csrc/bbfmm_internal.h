@@ -140,6 +140,7 @@ struct DevOps {
     std::vector<float *> C;  // [316][rows64][rp]
     std::vector<float *> Chi, Clo; // split copies for the tensor-core M2L (hi/lo)
     std::vector<float *> Vt_hi, Vt_lo; // [rp][p3p] V transposed, TF32 hi / lo (leaf compression GEMM)
+    std::vector<float *> U_hi, U_lo;   // [p3p][rp] U, TF32 hi / lo (leaf decompression GEMM)
     // 16-bit split copies, made on first use: [0] = FP16 (scaled by c16_scale),
     // [1] = BF16; same [316][rows64][rp] layout
     std::vector<uint16_t *> C16hi[2], C16lo[2];
@@ -210,6 +211,7 @@ struct bbfmm_plan_impl {
     int4 *chunks = nullptr; // near-field work items over the target leaves
     int nchunks = 0;
     float *Mleaf = nullptr;    // [R][8^D][p3p] leaf multipoles for the compression GEMM (or null)
+    float *Fdec = nullptr;     // [8^D R][p3p] decompressed leaf far fields (parity-split rows), or null
     bool leaf_gemm = false;    // leaf compression by the GEMM (tuning)
     int4 *box_items = nullptr; // near-field work items of one level-(D-1) box (D >= 1)
     int nbox_items = 0;
@@ -315,6 +317,7 @@ struct PassArgs {
     int keep;
     float *Ftop;                // D >= 4: local coefficients of the level-(D-2) boxes, [box][nrhs][p^3]
     float *Mleaf;               // non-null: store leaf M here ([R][8^D][p3p]) instead of compressing it
+    const float *Fdec;          // non-null: the leaves' decompressed far fields, [parity row][p3p]
 };
 cudaError_t launch_upward(const PassArgs &A, int p, cudaStream_t s);
 // box_gemm.cu: the leaf compression M~ = V^T M as a tensor-core GEMM (3 x TF32)
@@ -329,6 +332,18 @@ struct LeafCompressArgs {
 };
 bool leaf_compress_fits(int r, int p3p);
 cudaError_t launch_leaf_compress(const LeafCompressArgs &L, cudaStream_t s);
+// the leaf decompression F = U F~ (summed over F~'s offset-group slices) as
+// the same kind of GEMM, into [rows][p3p] for the downward pass
+struct LeafDecompressArgs {
+    const float *Ft;             // F~ of the leaf level: slices x slice_rows rows of rp floats
+    const float *U_hi, *U_lo;    // [p3p][rp] U, TF32 split
+    int64_t rows, slice_rows;    // rows of one slice (8 H^3 R), rows between slices
+    int slices, rp, p3p;
+    float *out;                  // [rows][p3p]
+    int *status;
+};
+bool leaf_decompress_fits(int rp, int p3p);
+cudaError_t launch_leaf_decompress(const LeafDecompressArgs &L, cudaStream_t s);
 cudaError_t launch_downward(const PassArgs &A, int p, cudaStream_t s);
 
 // ---------------------------------------------------------------------------

@@ -1,15 +1,22 @@
-// box_gemm.cu -- the compression of the leaf multipole coefficients,
-// M~ = V^T M (Sec. 2.5 "Fast M2L translation", applied to every leaf box of
-// the upward pass, Sec. 2.3 item 1), as a GEMM on the tensor cores.
+// box_gemm.cu -- the compression of the leaf multipole coefficients and the
+// decompression of the leaf local coefficients (Sec. 2.5 "Fast M2L
+// translation", applied to every leaf box by the upward and downward passes,
+// Sec. 2.3 items 1 and 3) as GEMMs on the tensor cores.
 //
-// Rows are (right-hand side c, leaf box): one row of M is the p^3
-// coefficients of one box for one column, so the leaf level is the product
+// Compression (MODE 0): rows are (right-hand side c, leaf box), one row of M
+// the p^3 coefficients of one box for one column, and the leaf level is
 //     M~[row][k] = sum_i M[row][i] V[i][k],   rows = nrhs x 8^D, i < p^3, k < r,
 // a tall GEMM with K = p^3 and N = r (p = 5: K = 125, N = 89).  The upward
 // pass writes M of the leaves ([R][8^D][p3p], zero past p^3) instead of
-// compressing them; this kernel compresses and stores M~ at the leaf's row of
-// the parity-split layout (with the TF32 split and the level's max |M~| when
-// the M2L needs them).
+// compressing them; this kernel stores M~ at the leaf's row of the
+// parity-split layout (with the TF32 split and the level's max |M~| when the
+// M2L needs them).
+//
+// Decompression (MODE 1): rows are the rows of the parity-split F~ (leaf
+// cell x R + c), summed over the M2L's offset-group slices as part of K:
+//     F[row][i] = sum_g sum_k F~_g[row][k] U[i][k],   K = r, N = p^3,
+// written to [rows][p3p] for the downward pass, which adds it to the L2L
+// part of each leaf's local coefficients.
 //
 // Arithmetic: kind::tf32 with FP32 accumulation, 3 products per K step
 // (hi*hi + hi*lo + lo*hi, the split-TF32 scheme of Ootomo & Yokota, 2022).
@@ -44,10 +51,13 @@ constexpr uint32_t kAChunkBytes = kGemmRows * kGemmK * 4; // 16 KB
 constexpr int kStatusTimeoutBit = 2;
 
 struct GemmLaunch {
-    CUtensorMap a;        // M: [rows][p3p] FP32, box (32, 128)
-    CUtensorMap bhi, blo; // V^T hi / lo: [rp][p3p] FP32, box (32, N)
+    CUtensorMap a;        // A: [slices x slice_rows][K] FP32, box (32, 128)
+    CUtensorMap bhi, blo; // B hi / lo: [N'][K] FP32, box (32, N)
     int ntiles;           // tiles of 128 rows
-    int kchunks;          // K chunks of 32
+    int kchunks;          // K chunks of 32 per slice
+    int slices;           // A slices summed into one product (decompression: F~'s offset groups)
+    int64_t slice_rows;   // rows between slices
+    int ldo;              // decompression: output row pitch (floats)
     int N;                // MMA N: r rounded up to 16 (<= 256)
     uint32_t idesc;
     uint32_t tcols;       // TMEM columns allocated (two accumulators)
@@ -66,7 +76,8 @@ __device__ __forceinline__ float tf32_rna(float x)
     return __uint_as_float(r);
 }
 
-__global__ void __launch_bounds__(kGemmThreads, 1) k_leaf_compress(const __grid_constant__ GemmLaunch G)
+template <int MODE>
+__global__ void __launch_bounds__(kGemmThreads, 1) k_leaf_gemm(const __grid_constant__ GemmLaunch G)
 {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -108,12 +119,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_leaf_compress(const __grid_
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    const int nk = G.kchunks;
+    const int nkc = G.kchunks, nk = G.kchunks * G.slices; // chunks per tile (over all slices)
 
     if (warp == 0 && lane == 0) {
         // ------------------------------------------------------------ producer
-        mbar_arrive_expect_tx(bfull, 2u * (uint32_t)nk * bchunk);
-        for (int kc = 0; kc < nk; ++kc) {
+        mbar_arrive_expect_tx(bfull, 2u * (uint32_t)nkc * bchunk);
+        for (int kc = 0; kc < nkc; ++kc) {
             tma_load_2d(bhi0 + (uint32_t)kc * bchunk, &G.bhi, bfull, kGemmK * kc, 0);
             tma_load_2d(blo0 + (uint32_t)kc * bchunk, &G.blo, bfull, kGemmK * kc, 0);
         }
@@ -125,8 +136,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_leaf_compress(const __grid_
                     break;
                 mbar_arrive_expect_tx(full0 + 8 * s, kAChunkBytes);
                 last_round[s] = round;
-                tma_load_2d(a0 + (uint32_t)s * 2u * kAChunkBytes, &G.a, full0 + 8 * s, kGemmK * kc,
-                            kGemmRows * tile);
+                const int g = kc / nkc, kk = kc - g * nkc;
+                tma_load_2d(a0 + (uint32_t)s * 2u * kAChunkBytes, &G.a, full0 + 8 * s, kGemmK * kk,
+                            (int)(g * G.slice_rows + (int64_t)kGemmRows * tile));
                 if (++s == kGemmStages) {
                     s = 0;
                     round ^= 1;
@@ -164,7 +176,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_leaf_compress(const __grid_
                 }
                 tc_fence_after();
                 const uint64_t ah = da + (uint64_t)(s * d_st), al = ah + d_lo;
-                const uint64_t bh = dbh + (uint64_t)(kc * d_bch), bl = dbl + (uint64_t)(kc * d_bch);
+                const int kk = kc % nkc; // the B chunk: K position within the slice
+                const uint64_t bh = dbh + (uint64_t)(kk * d_bch), bl = dbl + (uint64_t)(kk * d_bch);
 #pragma unroll
                 for (int k = 0; k < kGemmK / 8; ++k) { // K = 8 per MMA: 32 bytes
                     const uint64_t dk = (uint64_t)(2 * k);
@@ -236,15 +249,24 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_leaf_compress(const __grid_
             const int64_t row = (int64_t)kGemmRows * tile + e;
             int64_t off = -1;
             if (row < G.rows) {
-                const int c = (int)(row / G.nb);
-                int x, y, z;
-                demorton3((uint32_t)(row % G.nb), x, y, z);
-                off = parity_row(x, y, z, c, G.H, 1, G.R) * G.rp;
+                if (MODE == 0) {
+                    const int c = (int)(row / G.nb);
+                    int x, y, z;
+                    demorton3((uint32_t)(row % G.nb), x, y, z);
+                    off = parity_row(x, y, z, c, G.H, 1, G.R) * G.rp;
+                } else {
+                    off = row * G.ldo;
+                }
             }
             for (int n0 = 0; n0 < G.N; n0 += 16) {
                 float v[16];
                 tmem_ld16(tmem_base + lane_base + (uint32_t)(buf * G.N + n0), v);
-                if (off >= 0) {
+                if (MODE == 1 && off >= 0) { // all N columns (zero past p^3): 16-byte stores
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        *reinterpret_cast<float4 *>(G.out + off + n0 + j) =
+                            make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                } else if (off >= 0) {
                     // columns past the level's rank stay as they are (zero)
 #pragma unroll
                     for (int j = 0; j < 16; ++j)
@@ -289,7 +311,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_leaf_compress(const __grid_
                 bph ^= 1;
             }
         }
-        if (G.maxbits) {
+        if (MODE == 0 && G.maxbits) {
             for (int o = 16; o > 0; o >>= 1)
                 mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
             if (lane == 0 && mx > 0.0f)
@@ -318,6 +340,28 @@ bool leaf_compress_fits(int r, int p3p)
     return r >= 1 && N <= 256 && gemm_smem_bytes(N, nk) <= 227 * 1024;
 }
 
+bool leaf_decompress_fits(int rp, int p3p)
+{
+    const int nk = (rp + kGemmK - 1) / kGemmK;
+    return p3p % 16 == 0 && p3p <= 256 && gemm_smem_bytes(p3p, nk) <= 227 * 1024;
+}
+
+static cudaError_t run_gemm(GemmLaunch &G, int mode, cudaStream_t s)
+{
+    const size_t smem = gemm_smem_bytes(G.N, G.kchunks);
+    const void *fn = mode == 0 ? (const void *)k_leaf_gemm<0> : (const void *)k_leaf_gemm<1>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    const int sms = tc_sm_count();
+    const int grid = std::max(1, std::min(G.ntiles, sms > 0 ? sms : 1));
+    if (mode == 0)
+        k_leaf_gemm<0><<<grid, kGemmThreads, smem, s>>>(G);
+    else
+        k_leaf_gemm<1><<<grid, kGemmThreads, smem, s>>>(G);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_leaf_compress(const LeafCompressArgs &L, cudaStream_t s)
 {
     if (!leaf_compress_fits(L.r, L.p3p) || L.nrhs < 1 || L.nb < 1 || L.p3p % 4 != 0 || L.rp % 4 != 0)
@@ -326,7 +370,9 @@ cudaError_t launch_leaf_compress(const LeafCompressArgs &L, cudaStream_t s)
     memset(&G, 0, sizeof(G));
     G.N = (L.r + 15) / 16 * 16;
     G.kchunks = (L.p3p + kGemmK - 1) / kGemmK;
+    G.slices = 1;
     G.rows = (int64_t)L.nrhs * L.nb;
+    G.slice_rows = G.rows;
     G.ntiles = (int)((G.rows + kGemmRows - 1) / kGemmRows);
     G.idesc = idesc_tf32(kGemmRows, G.N);
     G.tcols = 32;
@@ -352,14 +398,41 @@ cudaError_t launch_leaf_compress(const LeafCompressArgs &L, cudaStream_t s)
                              (uint32_t)G.N);
     if (e != cudaSuccess)
         return e;
-    const size_t smem = gemm_smem_bytes(G.N, G.kchunks);
-    e = cudaFuncSetAttribute(k_leaf_compress, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return run_gemm(G, 0, s);
+}
+
+cudaError_t launch_leaf_decompress(const LeafDecompressArgs &L, cudaStream_t s)
+{
+    if (!leaf_decompress_fits(L.rp, L.p3p) || L.rows < 1 || L.slices < 1 || L.rp % 4 != 0)
+        return cudaErrorInvalidValue;
+    GemmLaunch G;
+    memset(&G, 0, sizeof(G));
+    G.N = L.p3p;
+    G.kchunks = (L.rp + kGemmK - 1) / kGemmK;
+    G.slices = L.slices;
+    G.rows = L.rows;
+    G.slice_rows = L.slice_rows;
+    G.ntiles = (int)((G.rows + kGemmRows - 1) / kGemmRows);
+    G.idesc = idesc_tf32(kGemmRows, G.N);
+    G.tcols = 32;
+    while (G.tcols < (uint32_t)(2 * G.N))
+        G.tcols *= 2;
+    G.ldo = L.p3p;
+    G.ncols = L.p3p;
+    G.out = L.out;
+    G.status = L.status;
+    // A: the slices of F~ as one 2D matrix of slices x slice_rows rows
+    cudaError_t e = tc_encode_2d_f32(&G.a, L.Ft, (uint64_t)L.rp, (uint64_t)L.slices * L.slice_rows,
+                                     (uint64_t)L.rp * 4, kGemmK, kGemmRows);
+    if (e == cudaSuccess)
+        e = tc_encode_2d_f32(&G.bhi, L.U_hi, (uint64_t)L.rp, (uint64_t)L.p3p, (uint64_t)L.rp * 4, kGemmK,
+                             (uint32_t)G.N);
+    if (e == cudaSuccess)
+        e = tc_encode_2d_f32(&G.blo, L.U_lo, (uint64_t)L.rp, (uint64_t)L.p3p, (uint64_t)L.rp * 4, kGemmK,
+                             (uint32_t)G.N);
     if (e != cudaSuccess)
         return e;
-    const int sms = tc_sm_count();
-    const int grid = std::max(1, std::min(G.ntiles, sms > 0 ? sms : 1));
-    k_leaf_compress<<<grid, kGemmThreads, smem, s>>>(G);
-    return cudaGetLastError();
+    return run_gemm(G, 1, s);
 }
 
 } // namespace bbfmm

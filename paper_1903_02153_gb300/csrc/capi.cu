@@ -55,7 +55,7 @@ static int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 // operator cache: one device copy per (kernel, ell, p, eps, depth, side)
 DevOps::~DevOps()
 {
-    for (auto *v : {&V, &Ut, &C, &Chi, &Clo, &Vt_hi, &Vt_lo})
+    for (auto *v : {&V, &Ut, &C, &Chi, &Clo, &Vt_hi, &Vt_lo, &U_hi, &U_lo})
         for (float *ptr : *v)
             if (ptr)
                 cudaFree(ptr);
@@ -190,6 +190,20 @@ static int get_ops(int kernel, double ell, int p, double eps, int depth, double 
             CUDA_TRY(cudaMemcpy(dh, Vh.data(), Vt.size() * 4, cudaMemcpyHostToDevice));
             CUDA_TRY(cudaMemcpy(dl, Vl.data(), Vt.size() * 4, cudaMemcpyHostToDevice));
             d->bytes += (int64_t)(2 * Vt.size()) * 4;
+            // U ([p3p][rp], K = r contiguous) for the leaf decompression GEMM
+            std::vector<float> Um((size_t)p3p * rp, 0.f), Uh(Um.size()), Ul(Um.size());
+            for (int i = 0; i < p3; ++i)
+                for (int a = 0; a < rk; ++a)
+                    Um[(size_t)i * rp + a] = (float)host->U[k][(size_t)i * r + a];
+            split_tf32(Um.data(), Uh.data(), Ul.data(), (int64_t)Um.size());
+            float *uh = nullptr, *ul = nullptr;
+            CUDA_TRY(cudaMalloc(&uh, Um.size() * 4));
+            d->U_hi.push_back(uh);
+            CUDA_TRY(cudaMalloc(&ul, Um.size() * 4));
+            d->U_lo.push_back(ul);
+            CUDA_TRY(cudaMemcpy(uh, Uh.data(), Um.size() * 4, cudaMemcpyHostToDevice));
+            CUDA_TRY(cudaMemcpy(ul, Ul.data(), Um.size() * 4, cudaMemcpyHostToDevice));
+            d->bytes += (int64_t)(2 * Um.size()) * 4;
         }
         if (host->interp == BBFMM_INTERP_UNIFORM) {
             // kernel spectra for the Fourier-domain M2L
@@ -630,6 +644,9 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
     if (P->nodeset == BBFMM_INTERP_CHEBYSHEV && D >= 2 && !P->ops->Vt_hi.empty() &&
         leaf_compress_fits(P->ops->rl[P->ops->nlev == 1 ? 0 : D - 2], P->ops->p3p) && tc_sm_count() > 0)
         PTRY(plan_alloc(P, (void **)&P->Mleaf, 4 * (int64_t)R * (1LL << (3 * D)) * P->ops->p3p, true, s));
+    // the leaves' decompressed far fields (the downward GEMM's output)
+    if (P->Mleaf && leaf_decompress_fits(P->ops->rp, P->ops->p3p))
+        PTRY(plan_alloc(P, (void **)&P->Fdec, 4 * (int64_t)R * (1LL << (3 * D)) * P->ops->p3p, false, s));
     if (P->near_sym && P->near_auto) {
         // occupancy of the leaves the near-field work meets: pairs per point
         // over the 27 neighbours.  Measured at 1M / 2M points: faster at ~30,
@@ -757,6 +774,7 @@ static PassArgs pass_args(const bbfmm_plan_impl *P, int nrhs, bool split16)
     A.keep = P->keep_coeffs ? 1 : 0;
     A.Ftop = P->Ftop;
     A.Mleaf = P->leaf_gemm ? P->Mleaf : nullptr;
+    A.Fdec = P->leaf_gemm ? P->Fdec : nullptr;
     for (int l = 2; l <= P->D; ++l) {
         const Level &L = P->lev[l];
         A.M[l] = L.M;
@@ -869,7 +887,23 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
         CUDA_TRY(launch_m2l_all(P, nrhs, fs));
         if (tm)
             CUDA_TRY(cudaEventRecord(P->ev[Stage::M2L], fs));
-        // downward pass: decompression, L2L and L2P in one launch
+        // downward pass: decompression, L2L and L2P in one launch (the
+        // leaves' decompression before it, as a GEMM, when the plan has it)
+        if (A.Fdec) {
+            const int opl = O.nlev == 1 ? 0 : D - 2;
+            LeafDecompressArgs L = {};
+            L.Ft = P->lev[D].Ft;
+            L.U_hi = O.U_hi[opl];
+            L.U_lo = O.U_lo[opl];
+            L.rows = (1LL << (3 * D)) * P->max_nrhs;
+            L.slice_rows = L.rows;
+            L.slices = P->m2l_groups;
+            L.rp = O.rp;
+            L.p3p = O.p3p;
+            L.out = P->Fdec;
+            L.status = P->status;
+            CUDA_TRY(launch_leaf_decompress(L, fs));
+        }
         CUDA_TRY(launch_downward(A, p, fs));
         if (tm) {
             CUDA_TRY(cudaEventRecord(P->ev[Stage::Down], fs));

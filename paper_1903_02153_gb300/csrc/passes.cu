@@ -578,7 +578,20 @@ __global__ void __launch_bounds__(kThreads) k_downward(const __grid_constant__ P
         for (int q = t; q < 8 * P3; q += kThreads)
             sMT[q] = 0.0f;
     }
-    {
+    if (A.Fdec) {
+        // the leaves' far fields, decompressed by the GEMM before this launch
+        __shared__ int64_t sDec[8];
+        if (t < 8) {
+            int x, y, z;
+            demorton3((uint32_t)(8 * b + t), x, y, z);
+            sDec[t] = parity_row(x, y, z, c, 1 << (D - 1), 0, A.R) * A.p3p;
+        }
+        __syncthreads();
+        for (int q = t; q < 8 * P3; q += kThreads) {
+            const int o = q / P3, i = q - o * P3;
+            sMT[i * 8 + o] += __ldg(A.Fdec + sDec[o] + i);
+        }
+    } else {
         __shared__ int64_t sRow[8]; // F~ row offsets of the 8 leaves
         if (t < 8) {
             int x, y, z;
@@ -594,9 +607,7 @@ __global__ void __launch_bounds__(kThreads) k_downward(const __grid_constant__ P
                 v += __ldg(src + g * A.slice[D]);
             sFt[k * 8 + o] = v;
         }
-    }
-    __syncthreads();
-    {
+        __syncthreads();
         const float *Ut = A.Ut[D];
         const int h = t >> 7;
         for (int i0 = 0; i0 < P3; i0 += 128) {
