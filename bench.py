@@ -52,11 +52,11 @@ def parse():
     ap.add_argument("--interp", default="chebyshev", choices=["chebyshev", "uniform"],
                     help="uniform: equally spaced nodes with the Fourier-domain M2L (FP32)")
     ap.add_argument("--svd-eps", type=float, default=1e-6)
-    ap.add_argument("--near", default="auto", choices=["auto", "ordered", "symmetric", "box", "symw"],
+    ap.add_argument("--near", default="auto", choices=["auto", "ordered", "symmetric", "box"],
                     help="near-field form: symmetric = each neighbour leaf pair once (symmetric kernels), "
                          "ordered = every target leaf its own pairs, box = ordered with a work item per "
-                         "level-(D-1) box, symw = symmetric with a warp per neighbour leaf, auto = measured "
-                         "by the autotuner; a fixed form keeps the tuner's other choices (a profiler run "
+                         "level-(D-1) box, auto = measured by the autotuner; a fixed form keeps the "
+                         "tuner's other choices (a profiler run "
                          "pins the form the plain run chose, since the tuner's timings under it mislead)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-depth6", action="store_true")
@@ -227,7 +227,7 @@ def tuning_summary(bb, plan, nrhs):
     """The plan's launch choices for nrhs (after the autotuner ran)."""
     t = bb.bbfmm_get_tuning(plan.handle, nrhs)
     if t.near_mode == bb.NEAR_MODES["symmetric"]:
-        near = "symmetric pairs, a warp per neighbour leaf" if t.near_symw else "symmetric pairs"
+        near = "symmetric pairs"
     else:
         near = "ordered, a work item per level-(D-1) box" if t.near_box else "ordered"
     return {"near_field": near, "m2l_tile": int(t.m2l_tile), "m2l_stages": int(t.m2l_stages),
@@ -235,16 +235,16 @@ def tuning_summary(bb, plan, nrhs):
 
 
 def make_plan(bb, torch, dev, pts, c, depth, precision, eps, interp="chebyshev", near="auto"):
-    """A plan of workload c; near "box" / "symw" (the variants of the ordered /
-    symmetric form) runs the tuning sweep and then fixes the near-field form."""
-    mode = {"box": "ordered", "symw": "symmetric"}.get(near, near)
+    """A plan of workload c; near "box" (the ordered form by level-(D-1) box)
+    runs the tuning sweep and then fixes the near-field form."""
+    mode = {"box": "ordered"}.get(near, near)
     plan = bb.Plan(torch.from_numpy(pts).to(dev), c["kernel"], c["p"], depth, ell=c["ell"], precision=precision,
                    svd_eps=eps, domain=(W.UNIT_LO, W.UNIT_SIDE), max_nrhs=c["nrhs"], interp=interp, near_mode=mode)
-    if near in ("box", "symw"):
+    if near == "box":
         bb.bbfmm_autotune(plan.handle, c["nrhs"])
         t = bb.bbfmm_get_tuning(plan.handle, c["nrhs"])
-        bb.bbfmm_set_tuning(plan.handle, c["nrhs"], mode, t.m2l_tile, t.m2l_stages, near_box=near == "box",
-                            leaf_gemm=bool(t.leaf_gemm), near_symw=near == "symw")
+        bb.bbfmm_set_tuning(plan.handle, c["nrhs"], mode, t.m2l_tile, t.m2l_stages, near_box=True,
+                            leaf_gemm=bool(t.leaf_gemm))
     return plan
 
 
@@ -533,7 +533,10 @@ def run_ours(args, rank, world, local):
         d6, phi6 = time_plan(bb, torch, dev, pts, sigma, c, 6, precision, args.svd_eps, flush, stream,
                              interp=interp, near=args.near)
         d6["accuracy"] = accuracy_check(pts, sig_host, phi6, dict(c, depth=6), nodes=interp)
-        d6.pop("_info")
+        d6info = d6.pop("_info")
+        # the depth-6 M2L against the same peak (its DRAM traffic when captured for this build)
+        d6["m2l_roofline"] = roofline(precision, d6info, nrhs, d6["stages_ms"]["m2l"], {"sm_mhz": None}, torch, dev,
+                                      "uniform-1M-p5-d6", interp, c["p"])
         extra["depth6"] = d6
     if rank == 0 and precision != "fp32" and not args.no_plain:
         # the plain form: FP32 M2L and the ordered near field, its own

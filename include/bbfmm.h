@@ -169,11 +169,7 @@ typedef struct {
                        default where the plan has it: Chebyshev nodes, depth >= 2,
                        V fits in shared memory, e.g. p <= 5); 0: inside the
                        upward pass on the CUDA cores */
-    int near_symw;  /* SYMMETRIC one-RHS near field: 1 = a warp per neighbour leaf
-                       (column sums kept in registers, transposed once per 32
-                       sources); 0 = a block per leaf with per-visit column
-                       partials (default).  Same visiting rule and values */
-    int reserved[1];
+    int reserved[2];
 } bbfmm_tuning;
 
 /*

@@ -51,7 +51,7 @@ class bbfmm_opts(ctypes.Structure):
 class bbfmm_tuning(ctypes.Structure):
     _fields_ = [("near_mode", ctypes.c_int), ("m2l_tile", ctypes.c_int), ("m2l_stages", ctypes.c_int),
                 ("measured", ctypes.c_int), ("near_box", ctypes.c_int), ("leaf_gemm", ctypes.c_int),
-                ("near_symw", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("reserved", ctypes.c_int * 2)]
 
 
 class bbfmm_info(ctypes.Structure):
@@ -274,14 +274,12 @@ def bbfmm_get_tuning(plan, nrhs=1) -> bbfmm_tuning:
     return t
 
 
-def bbfmm_set_tuning(plan, nrhs, near_mode, m2l_tile, m2l_stages=0, near_box=False, leaf_gemm=None,
-                     near_symw=False):
+def bbfmm_set_tuning(plan, nrhs, near_mode, m2l_tile, m2l_stages=0, near_box=False, leaf_gemm=None):
     """near_mode: "ordered" / "symmetric" (or the BBFMM_NEAR_* value);
     leaf_gemm None keeps the plan's current choice for this nrhs."""
     if leaf_gemm is None:
         leaf_gemm = bool(bbfmm_get_tuning(plan, nrhs).leaf_gemm)
     t = bbfmm_tuning()
-    t.near_symw = 1 if near_symw else 0
     t.leaf_gemm = 1 if leaf_gemm else 0
     t.near_mode = NEAR_MODES[near_mode] if isinstance(near_mode, str) else int(near_mode)
     t.m2l_tile = int(m2l_tile)

@@ -181,7 +181,6 @@ struct Tuning {
     bool near_sym = false; // one-RHS near field in symmetric order
     bool near_box = false; // one-RHS ordered near field in work items of one level-(D-1) box
     bool leaf_gemm = false; // leaf compression as a tensor-core GEMM after the upward pass
-    bool near_symw = false; // symmetric near field by k_p2p_symw (a warp per neighbour leaf)
     int m2l_nt = 128;      // targets per tensor-core M2L tile
     int m2l_stages = 0;    // tensor-core M2L pipeline stages (0 = as many as fit)
     bool measured = false; // chosen by a measured sweep (or its cache)
@@ -214,7 +213,6 @@ struct bbfmm_plan_impl {
     float *Mleaf = nullptr;    // [R][8^D][p3p] leaf multipoles for the compression GEMM (or null)
     float *Fdec = nullptr;     // [8^D R][p3p] decompressed leaf far fields (parity-split rows), or null
     bool leaf_gemm = false;    // leaf compression by the GEMM (tuning)
-    bool near_symw = false;    // symmetric near field by k_p2p_symw (tuning)
     int4 *box_items = nullptr; // near-field work items of one level-(D-1) box (D >= 1)
     int nbox_items = 0;
     bool near_box = false;     // one-RHS ordered near field by box items (tuning)
@@ -446,7 +444,6 @@ struct P2PArgs {
     const int4 *boxes;
     int nboxes;
     const int *toff;
-    int symw;     // symmetric near field: a warp per neighbour leaf (k_p2p_symw) instead of k_p2p_sym
 };
 cudaError_t launch_p2p(const P2PArgs &A, int kernel, double ell, double h, int nrhs, float *phi_near,
                        cudaStream_t s);

@@ -342,7 +342,6 @@ static void apply_tuning(bbfmm_plan_impl *P, const Tuning &t)
     P->near_sym = t.near_sym && P->near_slots != nullptr;
     P->near_box = t.near_box && !P->near_sym && P->box_items != nullptr;
     P->leaf_gemm = t.leaf_gemm && P->Mleaf != nullptr;
-    P->near_symw = t.near_symw && P->near_sym;
     for (int k = 0; k < P->m2l_nsets; ++k) {
         const bbfmm_plan_impl::TileSet &T = P->m2l_set[k];
         if (T.nt != t.m2l_nt)
@@ -372,8 +371,6 @@ static bool tuning_valid(const bbfmm_plan_impl *P, const Tuning &t)
     if (t.near_box && (t.near_sym || !P->box_items))
         return false;
     if (t.leaf_gemm && !P->Mleaf)
-        return false;
-    if (t.near_symw && !t.near_sym)
         return false;
     bool tile = false;
     for (int k = 0; k < P->m2l_nsets; ++k)
@@ -820,8 +817,7 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
         const bool box = nrhs == 1 && !slots && P->near_box;
         const P2PArgs pa = {P->tpts, P->chunks,   P->nchunks, nt, P->pts, P->sigma_s,
                             rows,    P->leaf_off, n,          D,  slots,
-                            box ? P->box_items : nullptr, box ? P->nbox_items : 0, P->tleaf_off,
-                            P->near_symw ? 1 : 0};
+                            box ? P->box_items : nullptr, box ? P->nbox_items : 0, P->tleaf_off};
         CUDA_TRY(launch_p2p(pa, P->kernel, P->ell, P->side / (double)(1LL << D), nrhs, P->phi_near,
                             P->side_stream));
         CUDA_TRY(launch_near_fix(P->close, slots ? 1 : box ? 2 : 0, P->sigma_s, n, nt, nrhs, P->phi_near,
@@ -1078,7 +1074,7 @@ static int autotune_sweep(bbfmm_plan_impl *P, int nrhs, bool use_cache, cudaStre
     auto measure = [&](const Tuning &t) {
         for (const Tuning &u : seen)
             if (u.near_sym == t.near_sym && u.near_box == t.near_box && u.m2l_nt == t.m2l_nt &&
-                u.m2l_stages == t.m2l_stages && u.leaf_gemm == t.leaf_gemm && u.near_symw == t.near_symw)
+                u.m2l_stages == t.m2l_stages && u.leaf_gemm == t.leaf_gemm)
                 return;
         seen.push_back(t);
         if (st != BBFMM_OK || !tuning_valid(P, t))
@@ -1118,12 +1114,11 @@ static int autotune_sweep(bbfmm_plan_impl *P, int nrhs, bool use_cache, cudaStre
     // 2. the near-field form of one-RHS matvecs: ordered by leaf, symmetric
     // (AUTO mode, symmetric kernel, one point set), ordered by box
     if (nrhs == 1) {
-        // forms: 0 ordered by leaf, 1 symmetric, 2 ordered by box, 3 symmetric
-        // with a warp per neighbour leaf
+        // forms: 0 ordered by leaf, 1 symmetric, 2 ordered by box
         const Tuning m = chosen;
         const bool sym_ok = P->near_slots != nullptr, forced_sym = sym_ok && !P->near_auto;
-        for (int nf = 0; nf < 4; ++nf) {
-            const bool sym = nf == 1 || nf == 3;
+        for (int nf = 0; nf < 3; ++nf) {
+            const bool sym = nf == 1;
             if (sym && !sym_ok)
                 continue;
             if (!sym && forced_sym)
@@ -1131,7 +1126,6 @@ static int autotune_sweep(bbfmm_plan_impl *P, int nrhs, bool use_cache, cudaStre
             Tuning t = m;
             t.near_sym = sym;
             t.near_box = nf == 2;
-            t.near_symw = nf == 3;
             measure(t);
         }
     }
@@ -1644,7 +1638,6 @@ int bbfmm_get_tuning(bbfmm_plan_t plan, int nrhs, bbfmm_tuning *out)
     out->measured = t.measured ? 1 : 0;
     out->near_box = t.near_box && !t.near_sym && plan->box_items && nrhs == 1 ? 1 : 0;
     out->leaf_gemm = t.leaf_gemm && plan->Mleaf ? 1 : 0;
-    out->near_symw = out->near_mode == BBFMM_NEAR_SYMMETRIC && t.near_symw ? 1 : 0;
     return BBFMM_OK;
 }
 
@@ -1662,7 +1655,6 @@ int bbfmm_set_tuning(bbfmm_plan_t plan, int nrhs, const bbfmm_tuning *in)
     t.m2l_stages = in->m2l_stages;
     t.near_box = in->near_box != 0;
     t.leaf_gemm = in->leaf_gemm != 0;
-    t.near_symw = in->near_symw != 0 && t.near_sym;
     if ((t.near_sym || t.near_box) && nrhs != 1)
         return fail(BBFMM_EINVAL, "the symmetric and box near-field forms run one right-hand side only");
     if (t.near_sym && nrhs != 1)

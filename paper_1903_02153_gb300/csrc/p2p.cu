@@ -15,12 +15,8 @@ static cudaError_t p2p_launch(const P2PArgs &A, Kern k, float scale, int nrhs, f
     if (A.nchunks <= 0)
         return cudaSuccess;
     if (nrhs == 1 && A.slots) {
-        if (A.symw)
-            k_p2p_symw<Kern><<<A.nchunks, kP2PThreads, 0, s>>>(A.spts, A.chunks, A.ns, A.sig, A.soff, A.D, k, scale,
-                                                                phi, A.slots);
-        else
-            k_p2p_sym<Kern><<<A.nchunks, kP2PThreads, 0, s>>>(A.spts, A.chunks, A.ns, A.sig, A.soff, A.D, k, scale,
-                                                               phi, A.slots);
+        k_p2p_sym<Kern><<<A.nchunks, kP2PThreads, 0, s>>>(A.spts, A.chunks, A.ns, A.sig, A.soff, A.D, k, scale, phi,
+                                                           A.slots);
     } else if (nrhs == 1 && A.boxes) {
         if (A.nboxes > 0)
             k_p2p_box<Kern><<<A.nboxes, kP2PThreads, 0, s>>>(A.tpts, A.toff, A.boxes, A.nt, A.spts, A.sig, A.soff,

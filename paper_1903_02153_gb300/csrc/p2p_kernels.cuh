@@ -700,190 +700,6 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
     }
 }
 
-// Symmetric near field, a warp per neighbour leaf.  The same visiting rule,
-// frames and kernel values as k_p2p_sym (so the same close-pair coefficients
-// apply), organised so that the column sums need no per-visit bookkeeping:
-// every warp holds all of the item's targets (lane t: targets t, t + 32, ...)
-// and takes whole neighbour leaves (own, one-way, two-way; warp w the list
-// entries w, w + 4, ...).  A neighbour's sources go through in blocks of 32,
-// staged by the warp in pairs, so that one packed operation serves two
-// sources of one target.  For a two-way block each lane keeps the 32 column
-// partials K(t, j) sigma_t in registers while it walks the block; then the
-// warp transposes them through shared memory and lane j adds the 32 partials
-// of source j in lane order and writes its slot.  Rows: each warp's partial
-// rows are added over the warps in warp order.  Everything is in a fixed
-// order, so the result does not depend on scheduling.
-constexpr int kSwWarps = kP2PThreads / 32;
-constexpr int kSwPitch = 36; // floats per row of the column transpose (16-byte rows, no bank conflicts)
-
-// one block of up to 32 sources of one neighbour against the warp's targets;
-// TWO: also the column sums of the block (written to slot_base[j])
-template <bool OWN, bool TWO, class Kern>
-__device__ __forceinline__ void symw_block(const Kern &kern, const float4 *sa, const float4 *sb, int cntb,
-                                           const float (&X)[4], const float (&Y)[4], const float (&Z)[4],
-                                           const float (&SG)[4], float2 (&row)[4], int nh, float *ctr,
-                                           float *slot_base, float scale)
-{
-    const float2 floor2 = make_float2(kR2Floor, kR2Floor);
-    float2 col[16];
-    if (TWO) {
-#pragma unroll
-        for (int m = 0; m < 16; ++m)
-            col[m] = make_float2(0.0f, 0.0f);
-    }
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-        if (h >= nh)
-            break;
-        const float2 xx = make_float2(X[h], X[h]), yy = make_float2(Y[h], Y[h]), zz = make_float2(Z[h], Z[h]);
-        const float2 st = make_float2(SG[h], SG[h]);
-        float2 r0 = row[h];
-#pragma unroll
-        for (int m = 0; m < 16; ++m) {
-            if (2 * m >= cntb)
-                break;
-            const float4 qa = sa[m], qb = sb[m]; // (x0, x1, y0, y1), (z0, z1, s0, s1): sources 2m, 2m + 1
-            const float2 dx = __fadd2_rn(xx, make_float2(qa.x, qa.y));
-            const float2 dy = __fadd2_rn(yy, make_float2(qa.z, qa.w));
-            const float2 dz = __fadd2_rn(zz, make_float2(qb.x, qb.y));
-            float2 r2 = OWN ? __fmul2_rn(dx, dx) : __ffma2_rn(dx, dx, floor2);
-            r2 = __ffma2_rn(dy, dy, r2);
-            r2 = __ffma2_rn(dz, dz, r2);
-            const float2 K = kern2<OWN>(kern, r2, dx, dy, dz);
-            r0 = __ffma2_rn(K, make_float2(qb.z, qb.w), r0);
-            if (TWO)
-                col[m] = __ffma2_rn(K, st, col[m]);
-        }
-        row[h] = r0;
-    }
-    if (TWO) {
-        const int lane = threadIdx.x & 31;
-        float4 *dst = reinterpret_cast<float4 *>(ctr + lane * kSwPitch);
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-            dst[q] = make_float4(col[2 * q].x, col[2 * q].y, col[2 * q + 1].x, col[2 * q + 1].y);
-        __syncwarp();
-        float v = 0.0f;
-#pragma unroll 8
-        for (int L = 0; L < 32; ++L)
-            v += ctr[L * kSwPitch + lane];
-        if (lane < cntb)
-            slot_base[lane] = scale * v;
-        __syncwarp();
-    }
-}
-
-template <class Kern>
-__global__ void __launch_bounds__(kP2PThreads, 4)
-    k_p2p_symw(const float4 *__restrict__ pts, const int4 *__restrict__ chunks, long long n,
-               const float *__restrict__ sig, const int *__restrict__ off, int D, Kern kern, float scale,
-               float *__restrict__ phi, float *__restrict__ slots)
-{
-    __shared__ __align__(16) float4 sst[kSwWarps][2][16];
-    __shared__ __align__(16) float ctr[kSwWarps][32 * kSwPitch];
-    __shared__ float rowpart[kSwWarps][kP2PChunk];
-    __shared__ int nb_start[27], nb_cnt[27], nb_key[27], nb_list[27];
-    __shared__ float4 nb_delta[27];
-    __shared__ int s_nlist;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int4 ch = chunks[blockIdx.x];
-    const int nt = ch.z, nh = (nt + 31) >> 5;
-    const bool whole = off[ch.x + 1] - off[ch.x] <= kSymMaxPoints;
-    int ax, ay, az;
-    demorton3((unsigned)ch.x, ax, ay, az);
-    const int nside = 1 << D;
-    if (warp == 0) {
-        // neighbours and their keys, as k_p2p_sym: own (0), one way (1), both
-        // ways (2), not visited (3); the visited ones listed in neighbour order
-        int cnt = 0, start = 0, key = 3;
-        if (lane < 27) {
-            const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
-            const int bx = ax + dx, by = ay + dy, bz = az + dz;
-            if (bx >= 0 && by >= 0 && bz >= 0 && bx < nside && by < nside && bz < nside) {
-                const unsigned nm = morton3((unsigned)bx, (unsigned)by, (unsigned)bz);
-                start = off[nm];
-                cnt = off[nm + 1] - start;
-            }
-            if (cnt > 0)
-                key = lane == 13 ? 0 : lane > 13 ? (whole ? 2 : 1) : (cnt > kSymMaxPoints ? 1 : 3);
-            nb_start[lane] = start;
-            nb_cnt[lane] = cnt;
-            nb_key[lane] = key;
-            nb_delta[lane] = make_float4((float)dx, (float)dy, (float)dz, 0.0f);
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, key != 3);
-        if (key != 3)
-            nb_list[__popc(m & ((1u << lane) - 1u))] = lane;
-        if (lane == 0)
-            s_nlist = __popc(m);
-    }
-    // the item's targets: lane t holds targets t + 32 h (a missing one copies
-    // the first target and adds nothing to the columns)
-    float X[4], Y[4], Z[4], SG[4];
-    float2 row[4];
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-        const int i = lane + 32 * h;
-        const bool v = i < nt;
-        const float4 u = pts[ch.y + (v ? i : 0)];
-        X[h] = u.x;
-        Y[h] = u.y;
-        Z[h] = u.z;
-        SG[h] = v ? sig[ch.y + i] : 0.0f;
-        row[h] = make_float2(0.0f, 0.0f);
-    }
-    __syncthreads();
-    const int nlist = s_nlist;
-    float *sa_f = reinterpret_cast<float *>(&sst[warp][0][0]), *sb_f = reinterpret_cast<float *>(&sst[warp][1][0]);
-    for (int e = warp; e < nlist; e += kSwWarps) {
-        const int k = nb_list[e], key = nb_key[k], start = nb_start[k], cnt = nb_cnt[k];
-        const float4 d = nb_delta[k];
-        for (int b0 = 0; b0 < cnt; b0 += 32) {
-            const int cntb = min(32, cnt - b0);
-            // stage: source b0 + lane, negated and shifted into the target
-            // leaf's frame, at pair lane / 2, half lane & 1; missing sources
-            // far away with zero weight
-            float x = -1.0e4f, y = -1.0e4f, z = -1.0e4f, s = 0.0f;
-            if (lane < cntb) {
-                const float4 u = pts[start + b0 + lane];
-                s = sig[start + b0 + lane];
-                x = -__fadd_rn(u.x, d.x);
-                y = -__fadd_rn(u.y, d.y);
-                z = -__fadd_rn(u.z, d.z);
-            }
-            const int at = 4 * (lane >> 1) + (lane & 1);
-            sa_f[at] = x;
-            sa_f[at + 2] = y;
-            sb_f[at] = z;
-            sb_f[at + 2] = s;
-            __syncwarp();
-            float *slot_base = slots + (long long)(26 - k) * n + start + b0;
-            if (key == 0)
-                symw_block<true, false>(kern, sst[warp][0], sst[warp][1], cntb, X, Y, Z, SG, row, nh, ctr[warp],
-                                        slot_base, scale);
-            else if (key == 1)
-                symw_block<false, false>(kern, sst[warp][0], sst[warp][1], cntb, X, Y, Z, SG, row, nh,
-                                         ctr[warp], slot_base, scale);
-            else
-                symw_block<false, true>(kern, sst[warp][0], sst[warp][1], cntb, X, Y, Z, SG, row, nh, ctr[warp],
-                                        slot_base, scale);
-            __syncwarp();
-        }
-    }
-#pragma unroll
-    for (int h = 0; h < 4; ++h)
-        if (lane + 32 * h < nt)
-            rowpart[warp][lane + 32 * h] = row[h].x + row[h].y;
-    __syncthreads();
-    if (tid < nt) {
-        float v = 0.0f;
-#pragma unroll
-        for (int w = 0; w < kSwWarps; ++w)
-            v += rowpart[w][tid];
-        phi[ch.y + tid] = scale * v;
-    }
-}
-
 // Several right-hand sides (Sec. 2.5 "Multiple right-hand-sides"): the near
 // field of a work item is a product of its kernel matrix (targets x
 // neighbourhood sources) with the weights (sources x nrhs, read row-major).  The block walks

@@ -70,7 +70,7 @@ struct UserKernel {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t eval = nullptr, p2p = nullptr, p2p_multi = nullptr, p2p_sym = nullptr;
     cudaKernel_t close_count = nullptr, close_fill = nullptr; // k_close_pairs, both passes
-    cudaKernel_t p2p_box = nullptr, p2p_symw = nullptr;
+    cudaKernel_t p2p_box = nullptr;
 };
 
 std::mutex g_mu;
@@ -139,9 +139,8 @@ int user_kernel_register(const char *source, int homogeneity, int symmetric, int
     nv.add_name(prog, sym_name);
     nv.add_name(prog, count_name);
     nv.add_name(prog, fill_name);
-    const char *box_name = "bbfmm::k_p2p_box<bbfmm::KUser>", *symw_name = "bbfmm::k_p2p_symw<bbfmm::KUser>";
+    const char *box_name = "bbfmm::k_p2p_box<bbfmm::KUser>";
     nv.add_name(prog, box_name);
-    nv.add_name(prog, symw_name);
     const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-default-device"};
     const nvrtcResult rc = nv.compile(prog, 3, opts);
     size_t log_size = 0;
@@ -165,10 +164,9 @@ int user_kernel_register(const char *source, int homogeneity, int symmetric, int
     nv.lowered(prog, sym_name, &sym_low);
     nv.lowered(prog, count_name, &count_low);
     nv.lowered(prog, fill_name, &fill_low);
-    const char *box_low = nullptr, *symw_low = nullptr;
+    const char *box_low = nullptr;
     nv.lowered(prog, box_name, &box_low);
-    nv.lowered(prog, symw_name, &symw_low);
-    const std::string box_sym = box_low ? box_low : "", symw_sym = symw_low ? symw_low : "";
+    const std::string box_sym = box_low ? box_low : "";
     const std::string p2p_sym = p2p_low ? p2p_low : "", multi_sym = multi_low ? multi_low : "",
                       pair_sym = sym_low ? sym_low : "", count_sym = count_low ? count_low : "",
                       fill_sym = fill_low ? fill_low : "";
@@ -191,8 +189,6 @@ int user_kernel_register(const char *source, int homogeneity, int symmetric, int
         e = cudaLibraryGetKernel(&k.close_fill, k.lib, fill_sym.c_str());
     if (e == cudaSuccess)
         e = cudaLibraryGetKernel(&k.p2p_box, k.lib, box_sym.c_str());
-    if (e == cudaSuccess)
-        e = cudaLibraryGetKernel(&k.p2p_symw, k.lib, symw_sym.c_str());
 
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -277,8 +273,8 @@ cudaError_t launch_p2p_user(const P2PArgs &A, int id, double h, int nrhs, float 
     if (nrhs == 1 && A.slots) { // symmetric near field (the kernel was registered as symmetric)
         void *sargs[] = {(void *)&A.spts, (void *)&A.chunks, (void *)&ns, (void *)&A.sig, (void *)&A.soff,
                          (void *)&D,      (void *)&kern,     (void *)&scale, (void *)&phi, (void *)&A.slots};
-        return cudaLaunchKernel((const void *)(A.symw ? k.p2p_symw : k.p2p_sym), dim3((unsigned)A.nchunks),
-                                dim3(kP2PThreads), sargs, 0, s);
+        return cudaLaunchKernel((const void *)k.p2p_sym, dim3((unsigned)A.nchunks), dim3(kP2PThreads), sargs, 0,
+                                s);
     }
     if (nrhs == 1 && A.boxes) { // ordered, work items of one level-(D-1) box
         if (A.nboxes <= 0)

@@ -43,19 +43,17 @@ def sigma_dev(sig):
 
 
 def candidates(bb, plan, nrhs):
-    """Every (near order, tile, stages, box items, leaf GEMM, warp-per-leaf
-    symmetric kernel) the plan accepts for this nrhs."""
+    """Every (near order, tile, stages, box items, leaf GEMM) the plan accepts
+    for this nrhs."""
     ok = []
-    for near, tile, st, box, lg, sw in itertools.product(["ordered", "symmetric"], [128, 256], [0, 2, 3, 4],
-                                                         [False, True], [False, True], [False, True]):
-        if sw and near != "symmetric":
-            continue
+    for near, tile, st, box, lg in itertools.product(["ordered", "symmetric"], [128, 256], [0, 2, 3, 4],
+                                                     [False, True], [False, True]):
         try:
-            bb.bbfmm_set_tuning(plan.handle, nrhs, near, tile, st, near_box=box, leaf_gemm=lg, near_symw=sw)
+            bb.bbfmm_set_tuning(plan.handle, nrhs, near, tile, st, near_box=box, leaf_gemm=lg)
         except bb.BBFMMError as e:
             assert e.status == bb.BBFMM_EINVAL
             continue
-        ok.append((near, tile, st, box, lg, sw))
+        ok.append((near, tile, st, box, lg))
     return ok
 
 
@@ -78,14 +76,13 @@ def test_every_candidate_gives_the_same_result(bb, oracle, kind, kid, ell, p, de
     assert {c[0] for c in cands} == {"ordered", "symmetric"}
     assert {(c[0], c[3]) for c in cands} == {("ordered", False), ("ordered", True), ("symmetric", False)}
     assert {c[4] for c in cands} == {False, True}     # the leaf compression GEMM or the pass
-    assert {c[5] for c in cands if c[0] == "symmetric"} == {False, True}   # both symmetric kernels
     s = sigma_dev(sig)
     outs = {}
     for c in cands:
         bb.bbfmm_set_tuning(plan.handle, 1, *c)
         t = bb.bbfmm_get_tuning(plan.handle, 1)
-        assert (t.m2l_tile, t.m2l_stages, t.measured, t.near_box, t.leaf_gemm, t.near_symw) == (
-            c[1], c[2], 0, int(c[3]), int(c[4]), int(c[5]))
+        assert (t.m2l_tile, t.m2l_stages, t.measured, t.near_box, t.leaf_gemm) == (
+            c[1], c[2], 0, int(c[3]), int(c[4]))
         outs[c] = plan.matvec(s).cpu().numpy().astype(np.float64)
         assert bb.bbfmm_status(plan.handle) == 0
     plan.close()
@@ -115,10 +112,8 @@ def test_tuned_choice_is_a_candidate_and_reproducible(bb):
     assert bb.bbfmm_get_tuning(plan.handle, 1).measured == 1
     # a plan told the first choice explicitly gives the same bits
     other = make(bb, pts, autotune=False)
-    bb.bbfmm_set_tuning(other.handle, 1, t.near_mode, t.m2l_tile, t.m2l_stages, t.near_box, t.leaf_gemm,
-                        t.near_symw)
-    bb.bbfmm_set_tuning(plan.handle, 1, t.near_mode, t.m2l_tile, t.m2l_stages, t.near_box, t.leaf_gemm,
-                        t.near_symw)
+    bb.bbfmm_set_tuning(other.handle, 1, t.near_mode, t.m2l_tile, t.m2l_stages, t.near_box, t.leaf_gemm)
+    bb.bbfmm_set_tuning(plan.handle, 1, t.near_mode, t.m2l_tile, t.m2l_stages, t.near_box, t.leaf_gemm)
     b, c = plan.matvec(sig), other.matvec(sig)
     torch.cuda.synchronize()
     assert torch.equal(a, b) and torch.equal(b, c)

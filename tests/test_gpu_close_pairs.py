@@ -12,9 +12,8 @@ field (``opts.close_refine``, on by default).  These tests check:
   fail it without (the mechanism, not a tolerance);
 * exact duplicates (K(0) = 0 for the singular kernels) and distinct points
   that coincide in FP32, in one leaf and across a leaf face, element by
-  element against the FP64 direct sum, in every near-field form (symmetric
-  by leaf and by warp per neighbour leaf, ordered by leaf and by level-(D-1)
-  box, several right-hand sides);
+  element against the FP64 direct sum, in every near-field form (symmetric,
+  ordered by leaf and by level-(D-1) box, several right-hand sides);
 * separate target sets and a registered user kernel take the same path.
 """
 import numpy as np
@@ -42,21 +41,18 @@ def bb():
 
 def run(bb, pts, sig, kid, p, depth, ell=1.0, eps=1e-7, near="auto", refine=True, precision="fp32",
         targets=None):
-    """near: "auto", "ordered", "symmetric", "box" (ordered, a work item per
-    level-(D-1) box) or "symw" (symmetric, a warp per neighbour leaf)."""
+    """near: "auto", "ordered", "symmetric" or "box" (ordered, a work item per
+    level-(D-1) box)."""
     dev = torch.device("cuda:0")
     sig = np.asarray(sig, dtype=np.float32)
     nrhs = 1 if sig.ndim == 1 else sig.shape[1]
     plan = bb.Plan(torch.from_numpy(np.ascontiguousarray(pts)).to(dev), kid, p, depth, ell=ell, svd_eps=eps,
                    precision=precision, domain=UNIT, max_nrhs=nrhs,
-                   near_mode={"box": "ordered", "symw": "symmetric"}.get(near, near),
+                   near_mode={"box": "ordered"}.get(near, near),
                    close_refine=refine, targets=None if targets is None else torch.from_numpy(targets).to(dev))
     if near == "box":
         t = bb.bbfmm_get_tuning(plan.handle, nrhs)
         bb.bbfmm_set_tuning(plan.handle, nrhs, "ordered", t.m2l_tile, t.m2l_stages, near_box=True)
-    if near == "symw":
-        t = bb.bbfmm_get_tuning(plan.handle, nrhs)
-        bb.bbfmm_set_tuning(plan.handle, nrhs, "symmetric", t.m2l_tile, t.m2l_stages, near_symw=True)
     s = torch.from_numpy(np.ascontiguousarray(sig.T if nrhs > 1 else sig)).to(dev)
     phi = plan.matvec(s)
     torch.cuda.synchronize()
@@ -107,7 +103,7 @@ def coincident_set(n, seed):
 
 
 @pytest.mark.parametrize("kid", [K_INV_R, K_INV_R2])
-@pytest.mark.parametrize("near,nrhs", [("symmetric", 1), ("symw", 1), ("ordered", 1), ("box", 1), ("auto", 3)])
+@pytest.mark.parametrize("near,nrhs", [("symmetric", 1), ("ordered", 1), ("box", 1), ("auto", 3)])
 @pytest.mark.parametrize("depth", [0, 1, 2])
 def test_coincident_points_element_by_element(bb, oracle, kid, near, nrhs, depth):
     """Depth 0..2 with a small order: at depth 0 / 1 the result is the near

@@ -202,34 +202,3 @@ def test_several_rhs_between_single_rhs_calls(bb, oracle):
         one = matvec(bb, plan, sig3[:, c])
         assert rel(many[:, c], one) <= 2e-6, c
     plan.close()
-
-
-@pytest.mark.parametrize("kid,ell,kind,n,p,depth", [
-    (K_INV_R, 1.0, "uniform", 200_000, 4, 4),    # ~50 points per leaf: two-way blocks of two target halves
-    (K_INV_R, 1.0, "uniform", 60_000, 5, 4),     # ~15 points per leaf
-    (K_EXP, 0.3, "clustered", 60_000, 5, 4),     # dense leaves: one-way blocks of many sources
-    (K_INV_R2, 1.0, "uniform", 3000, 4, 1),      # depth 1: every pair a near pair
-])
-def test_warp_per_leaf_kernel_matches_block_kernel(bb, oracle, kid, ell, kind, n, p, depth):
-    """The symmetric near field with a warp per neighbour leaf (columns kept in
-    registers and transposed per 32 sources) gives the block kernel's result
-    to FP32 rounding: the same pairs, visiting rule and kernel values."""
-    pts = W.make_points(kind, n, seed=520)
-    sig = W.uniform_sigma(n, seed=521).astype(np.float32)
-    plan = make_plan(bb, pts, kid, p, depth, "symmetric", ell=ell, autotune=False)
-    s = torch.from_numpy(sig).to("cuda:0")
-    a = plan.matvec(s).cpu().numpy().astype(np.float64)
-    t = bb.bbfmm_get_tuning(plan.handle, 1)
-    bb.bbfmm_set_tuning(plan.handle, 1, "symmetric", t.m2l_tile, t.m2l_stages, near_symw=True)
-    b = plan.matvec(s).cpu().numpy().astype(np.float64)
-    again = plan.matvec(s).cpu().numpy().astype(np.float64)
-    assert bb.bbfmm_get_tuning(plan.handle, 1).near_symw == 1
-    assert bb.bbfmm_status(plan.handle) == 0
-    plan.close()
-    np.testing.assert_array_equal(b, again)          # deterministic
-    d = rel(b, a)
-    print("%d %s n=%d d%d: warp-per-leaf vs block kernel %.2e" % (kid, kind, n, depth, d))
-    assert d <= 2e-6
-    if n <= 60_000:
-        ref = oracle.bbfmm(pts, sig.astype(np.float64), kid, p, depth, ell=ell, lo=W.UNIT_LO, side=W.UNIT_SIDE)
-        assert rel(b, ref) <= 1e-5
