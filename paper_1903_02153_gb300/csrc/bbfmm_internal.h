@@ -212,6 +212,10 @@ struct bbfmm_plan_impl {
     int nchunks = 0;
     float *Mleaf = nullptr;    // [R][8^D][p3p] leaf multipoles for the compression GEMM (or null)
     float *Fdec = nullptr;     // [8^D R][p3p] decompressed leaf far fields (parity-split rows), or null
+    // the same two GEMMs for the boxes of level D-1 (D >= 3): their multipoles
+    // [R][8^(D-1)][p3p] and decompressed far fields [8^(D-1) R][p3p], or null
+    float *Mlev1 = nullptr;
+    float *Fdec1 = nullptr;
     bool leaf_gemm = false;    // leaf compression by the GEMM (tuning)
     int4 *box_items = nullptr; // near-field work items of one level-(D-1) box (D >= 1)
     int nbox_items = 0;
@@ -318,6 +322,8 @@ struct PassArgs {
     float *Ftop;                // D >= 4: local coefficients of the level-(D-2) boxes, [box][nrhs][p^3]
     float *Mleaf;               // non-null: store leaf M here ([R][8^D][p3p]) instead of compressing it
     const float *Fdec;          // non-null: the leaves' decompressed far fields, [parity row][p3p]
+    float *Mlev1;               // non-null: store level-(D-1) M here ([R][8^(D-1)][p3p]) instead of compressing it
+    const float *Fdec1;         // non-null: level D-1's decompressed far fields, [parity row][p3p]
 };
 cudaError_t launch_upward(const PassArgs &A, int p, cudaStream_t s);
 // box_gemm.cu: the leaf compression M~ = V^T M as a tensor-core GEMM (3 x TF32)

@@ -647,6 +647,12 @@ static int plan_build(bbfmm_plan_impl *P, const double *points, const double *ta
     // the leaves' decompressed far fields (the downward GEMM's output)
     if (P->Mleaf && leaf_decompress_fits(P->ops->rp, P->ops->p3p))
         PTRY(plan_alloc(P, (void **)&P->Fdec, 4 * (int64_t)R * (1LL << (3 * D)) * P->ops->p3p, false, s));
+    // and for the boxes of level D-1 (the passes then neither compress nor
+    // decompress on the CUDA cores below level D-2)
+    if (P->Fdec && D >= 3 && leaf_compress_fits(P->ops->rl[P->ops->nlev == 1 ? 0 : D - 3], P->ops->p3p)) {
+        PTRY(plan_alloc(P, (void **)&P->Mlev1, 4 * (int64_t)R * (1LL << (3 * (D - 1))) * P->ops->p3p, true, s));
+        PTRY(plan_alloc(P, (void **)&P->Fdec1, 4 * (int64_t)R * (1LL << (3 * (D - 1))) * P->ops->p3p, false, s));
+    }
     if (P->near_sym && P->near_auto) {
         // occupancy of the leaves the near-field work meets: pairs per point
         // over the 27 neighbours.  Measured at 1M / 2M points: faster at ~30,
@@ -775,6 +781,8 @@ static PassArgs pass_args(const bbfmm_plan_impl *P, int nrhs, bool split16)
     A.Ftop = P->Ftop;
     A.Mleaf = P->leaf_gemm ? P->Mleaf : nullptr;
     A.Fdec = P->leaf_gemm ? P->Fdec : nullptr;
+    A.Mlev1 = P->leaf_gemm ? P->Mlev1 : nullptr;
+    A.Fdec1 = P->leaf_gemm ? P->Fdec1 : nullptr;
     for (int l = 2; l <= P->D; ++l) {
         const Level &L = P->lev[l];
         A.M[l] = L.M;
@@ -840,26 +848,33 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
         if (split16)
             CUDA_TRY(cudaMemsetAsync(P->a16_max, 0, 4 * (kMaxDepth + 1), fs));
         CUDA_TRY(launch_upward(A, p, fs));
-        if (A.Mleaf) { // the leaf level's compression as a tensor-core GEMM
-            const int opl = O.nlev == 1 ? 0 : D - 2;
+        // the compression of level l (the leaves, and level D-1) as a
+        // tensor-core GEMM over the multipoles the pass stored in M
+        auto box_compress = [&](int l, const float *M) -> int {
+            const int opl = O.nlev == 1 ? 0 : l - 2;
             LeafCompressArgs L = {};
-            L.M = P->Mleaf;
+            L.M = M;
             L.Vt_hi = O.Vt_hi[opl];
             L.Vt_lo = O.Vt_lo[opl];
-            L.nb = 1LL << (3 * D);
+            L.nb = 1LL << (3 * l);
             L.nrhs = nrhs;
             L.R = P->max_nrhs;
             L.r = O.rl[opl];
             L.rp = O.rp;
             L.p3p = O.p3p;
-            L.H = 1 << (D - 1);
-            L.out = P->lev[D].Mt;
-            L.out_hi = P->lev[D].Mt_hi;
-            L.out_lo = P->lev[D].Mt_lo;
-            L.maxbits = split16 ? P->a16_max + D : nullptr;
+            L.H = 1 << (l - 1);
+            L.out = P->lev[l].Mt;
+            L.out_hi = P->lev[l].Mt_hi;
+            L.out_lo = P->lev[l].Mt_lo;
+            L.maxbits = split16 ? P->a16_max + l : nullptr;
             L.status = P->status;
             CUDA_TRY(launch_leaf_compress(L, fs));
-        }
+            return BBFMM_OK;
+        };
+        if (A.Mleaf)
+            PTRY(box_compress(D, A.Mleaf));
+        if (A.Mlev1)
+            PTRY(box_compress(D - 1, A.Mlev1));
         if (split16) {
             Split16Args S = {};
             S.fmt = P->precision == BBFMM_PREC_FP16X3 ? 0 : 1;
@@ -889,21 +904,26 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
             CUDA_TRY(cudaEventRecord(P->ev[Stage::M2L], fs));
         // downward pass: decompression, L2L and L2P in one launch (the
         // leaves' decompression before it, as a GEMM, when the plan has it)
-        if (A.Fdec) {
-            const int opl = O.nlev == 1 ? 0 : D - 2;
+        auto box_decompress = [&](int l, float *out) -> int {
+            const int opl = O.nlev == 1 ? 0 : l - 2;
             LeafDecompressArgs L = {};
-            L.Ft = P->lev[D].Ft;
+            L.Ft = P->lev[l].Ft;
             L.U_hi = O.U_hi[opl];
             L.U_lo = O.U_lo[opl];
-            L.rows = (1LL << (3 * D)) * P->max_nrhs;
+            L.rows = (1LL << (3 * l)) * P->max_nrhs;
             L.slice_rows = L.rows;
             L.slices = P->m2l_groups;
             L.rp = O.rp;
             L.p3p = O.p3p;
-            L.out = P->Fdec;
+            L.out = out;
             L.status = P->status;
             CUDA_TRY(launch_leaf_decompress(L, fs));
-        }
+            return BBFMM_OK;
+        };
+        if (A.Fdec1)
+            PTRY(box_decompress(D - 1, P->Fdec1));
+        if (A.Fdec)
+            PTRY(box_decompress(D, P->Fdec));
         CUDA_TRY(launch_downward(A, p, fs));
         if (tm) {
             CUDA_TRY(cudaEventRecord(P->ev[Stage::Down], fs));

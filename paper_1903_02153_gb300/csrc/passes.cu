@@ -465,7 +465,11 @@ __global__ void __launch_bounds__(kThreads, kUpMinBlocks<P>) k_upward(const __gr
     }
     for (int r = t; r < P3; r += kThreads)
         A.M[D - 1][(b * A.nrhs + c) * P3 + r] = sPar[r];
-    compress1<P>(A, D - 1, sPar, b, c);
+    if (A.Mlev1) // compressed by the GEMM after this launch
+        for (int r = t; r < P3; r += kThreads)
+            A.Mlev1[((int64_t)c * (1LL << (3 * (D - 1))) + b) * A.p3p + r] = sPar[r];
+    else
+        compress1<P>(A, D - 1, sPar, b, c);
 
     // ---- upper levels: the last of 8 siblings to arrive makes the parent
     int64_t box = b;
@@ -548,6 +552,20 @@ __global__ void __launch_bounds__(kThreads) k_downward(const __grid_constant__ P
         const int64_t anc = b >> (3 * (D - 1 - l));
         if (l > 2)
             l2l1<P>(A.T, sPar, (int)(anc & 7), sOne, sPar);
+        if (l == D - 1 && A.Fdec1) {
+            // the block's own box, decompressed by the GEMM before this launch
+            int x, y, z;
+            demorton3((uint32_t)anc, x, y, z);
+            const float *src = A.Fdec1 + parity_row(x, y, z, c, 1 << (l - 1), 0, A.R) * A.p3p;
+            for (int i = t; i < P3; i += kThreads) {
+                const float f = (l > 2 ? sPar[i] : 0.0f) + __ldg(src + i);
+                sPar[i] = f;
+                if (A.keep)
+                    A.F[l][(anc * A.nrhs + c) * P3 + i] = f;
+            }
+            __syncthreads();
+            continue;
+        }
         const int rl = A.rl[l];
         for (int k = t; k < rl; k += kThreads)
             load_ft(A, l, anc, c, sFt, 1, k);
@@ -884,7 +902,13 @@ __global__ void __launch_bounds__(kThreads) k_upward_wide(const __grid_constant_
     if (A.keep)
         for (int q = t; q < 8 * P3; q += kThreads)
             A.M[D - 1][((8 * B + (q & 7)) * A.nrhs + c) * P3 + (q >> 3)] = sMid[q];
-    compress8<P>(A, D - 1, sMid, 8 * B, c, zero);
+    if (!A.Mlev1)
+        compress8<P>(A, D - 1, sMid, 8 * B, c, zero);
+    else if (!zero) // compressed by the GEMM after this launch
+        for (int q = t; q < 8 * P3; q += kThreads) {
+            const int o = q / P3, i = q - o * P3;
+            A.Mlev1[((int64_t)c * (1LL << (3 * (D - 1))) + 8 * B + o) * A.p3p + i] = sMid[i * 8 + o];
+        }
     if (D - 2 < 2)
         return;
     // the block's own box (level D-2)
@@ -925,9 +949,712 @@ __global__ void __launch_bounds__(kThreads) k_upward_wide(const __grid_constant_
     }
 }
 
+// ---------------------------------------------------------------------------
+// Several right-hand sides (Sec. 2.5 "Multiple right-hand-sides"): the same
+// passes with a block per (box, chunk of RC columns).  The basis values of a
+// leaf's points, every operator element a compression or decompression loads
+// and every transfer matrix are shared by RC columns, and each phase between
+// two barriers has RC times the lines of the one-column kernels.  With a block
+// per (box, column) the passes were bound by the latency of their short
+// phases (3.4 ms each way for 500k points x 64 columns at depth 5).
+//
+// Shared-memory layouts (floats): X [RC][P3][8] (8 sibling boxes of one
+// column, as the one-column kernels keep them); P [P3][RC] (one box, the
+// columns side by side, so one vector load gives a thread its columns);
+// the leaves' local coefficients in the downward pass [P3][8][RC] (L2P reads
+// a leaf's RC columns of one coefficient with one vector load).
+template <int P> constexpr int kRC = P <= 5 ? 8 : (P <= 7 ? 4 : 2);
+
+template <int P> struct SmemRC {
+    static constexpr int P3 = P * P * P, RC = kRC<P>;
+    // upward: X | Y (the P2M basis scratch 256 x (3P + RC) aliases it) | P
+    static constexpr int kUpY = 8 * P3 * RC;
+    static constexpr int kUpYN = 8 * P3 * RC > 256 * (3 * P + RC) ? 8 * P3 * RC : 256 * (3 * P + RC);
+    static constexpr int kUpPar = kUpY + kUpYN;
+    static constexpr int kUpFloats = kUpPar + P3 * RC;
+    // downward: leaves [P3][8][RC] | Y [RC][2][P3] | Z [RC][4][P3] | P | scratch P | F~ [r][RC]
+    static constexpr int kDnY = 8 * P3 * RC, kDnZ = 10 * P3 * RC, kDnPar = 14 * P3 * RC, kDnOne = 15 * P3 * RC,
+                         kDnFt = 16 * P3 * RC, kDnFloats = 17 * P3 * RC;
+    static_assert(kDnPar % 2 == 0 && kUpPar % 2 == 0, "vector loads of the column sets");
+};
+
+// N consecutive floats of shared memory (N = 1, 2, 4, 8; aligned to N)
+template <int N>
+__device__ __forceinline__ void ldv(const float *p, float (&v)[N])
+{
+    if constexpr (N % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < N / 4; ++q) {
+            const float4 f = reinterpret_cast<const float4 *>(p)[q];
+            v[4 * q] = f.x;
+            v[4 * q + 1] = f.y;
+            v[4 * q + 2] = f.z;
+            v[4 * q + 3] = f.w;
+        }
+    } else if constexpr (N == 2) {
+        const float2 f = *reinterpret_cast<const float2 *>(p);
+        v[0] = f.x;
+        v[1] = f.y;
+    } else {
+        v[0] = p[0];
+    }
+}
+
+// P2M of leaf `leaf` for columns c0 .. c0 + RC - 1 (nc of them real) by one
+// warp, into column leaf & 7 of X [RC][P3][8]; L: the warp's 32 x (3P + RC)
+// scratch (basis values of 32 points, then their RC weights)
+template <int P, int RC>
+__device__ __forceinline__ void p2m_leaf_rc(const PassArgs &A, int64_t leaf, int c0, int nc, float *L, float *X)
+{
+    constexpr int P3 = P * P * P, NQ = (P * P + 31) / 32, LS = 3 * P + RC;
+    const int lane = threadIdx.x & 31, o = (int)(leaf & 7);
+    const int s0 = A.off[leaf], s1 = A.off[leaf + 1];
+    float acc[NQ][RC][P];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int c = 0; c < RC; ++c)
+#pragma unroll
+            for (int i = 0; i < P; ++i)
+                acc[q][c][i] = 0.0f;
+    for (int j0 = s0; j0 < s1; j0 += 32) {
+        const int cnt = min(32, s1 - j0);
+        __syncwarp();
+        if (lane < cnt) {
+            const float4 u = A.pts[j0 + lane];
+            float *Lr = L + lane * LS;
+            basis_1d<P>(A.T, 2.0f * u.x, Lr);
+            basis_1d<P>(A.T, 2.0f * u.y, Lr + P);
+            basis_1d<P>(A.T, 2.0f * u.z, Lr + 2 * P);
+#pragma unroll
+            for (int c = 0; c < RC; ++c)
+                Lr[3 * P + c] = c < nc ? A.sig[(int64_t)(c0 + c) * A.n + j0 + lane] : 0.0f;
+        }
+        __syncwarp();
+        for (int j = 0; j < cnt; ++j) {
+            const float *Lr = L + j * LS;
+            float lx[P], sg[RC];
+#pragma unroll
+            for (int i = 0; i < P; ++i)
+                lx[i] = Lr[i];
+#pragma unroll
+            for (int c = 0; c < RC; ++c)
+                sg[c] = Lr[3 * P + c];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int pq = lane + 32 * q;
+                if (pq < P * P) {
+                    const float yz = Lr[P + pq % P] * Lr[2 * P + pq / P];
+#pragma unroll
+                    for (int c = 0; c < RC; ++c) {
+                        const float s = sg[c] * yz;
+#pragma unroll
+                        for (int i = 0; i < P; ++i)
+                            acc[q][c][i] += lx[i] * s;
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int pq = lane + 32 * q;
+        if (pq < P * P) {
+#pragma unroll
+            for (int c = 0; c < RC; ++c)
+#pragma unroll
+                for (int i = 0; i < P; ++i) {
+                    const int idx = i + P * pq;
+                    X[(c * P3 + idx) * 8 + o] = acc[q][c][i];
+                    if (A.keep && c < nc)
+                        A.M[A.D][(leaf * A.nrhs + c0 + c) * P3 + idx] = acc[q][c][i];
+                }
+        }
+    }
+}
+
+// M2M of 8 children, RC columns: X [RC][P3][8] -> out [P3][RC]; scratch Y
+// [RC][P3][8] and Z [RC][P3][4] (Z may alias X: X is read by the first pass only)
+template <int P, int RC>
+__device__ void m2m8_rc(const InterpTables &T, const float *X, float *Y, float *Z, float *out)
+{
+    constexpr int P2 = P * P, P3 = P2 * P;
+    const int t = threadIdx.x;
+    for (int q = t; q < RC * 8 * P2; q += kThreads) { // x pass: line (child o, j2 + P j3, column)
+        const int o = q & 7, u = q >> 3, rest = u % P2, c = u / P2;
+        const float *Xc = X + c * 8 * P3;
+        float x[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j)
+            x[j] = Xc[(j + P * rest) * 8 + o];
+        float *Yc = Y + c * 8 * P3;
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            float a = 0.0f;
+#pragma unroll
+            for (int j = 0; j < P; ++j)
+                a += T.S[o & 1][i][j] * x[j];
+            Yc[(i + P * rest) * 8 + o] = a;
+        }
+    }
+    __syncthreads();
+    for (int q = t; q < RC * 4 * P2; q += kThreads) { // y pass: x pairs summed
+        const int yz = q & 3, u = q >> 2, v = u % P2, c = u / P2, i1 = v % P, j3 = v / P;
+        const float *Yc = Y + c * 8 * P3;
+        float y[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            const float *src = Yc + (i1 + P * j + P2 * j3) * 8 + 2 * yz;
+            y[j] = src[0] + src[1];
+        }
+        float *Zc = Z + c * 4 * P3;
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            float a = 0.0f;
+#pragma unroll
+            for (int j = 0; j < P; ++j)
+                a += T.S[yz & 1][i][j] * y[j];
+            Zc[(i1 + P * i + P2 * j3) * 4 + yz] = a;
+        }
+    }
+    __syncthreads();
+    for (int q = t; q < RC * P2; q += kThreads) { // z pass: y pairs summed
+        const int v = q % P2, c = q / P2;
+        const float *Zc = Z + c * 4 * P3;
+        float z0[P], z1[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            const float *src = Zc + (v + P2 * j) * 4;
+            z0[j] = src[0] + src[1];
+            z1[j] = src[2] + src[3];
+        }
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            float a = 0.0f;
+#pragma unroll
+            for (int j = 0; j < P; ++j)
+                a += T.S[0][i][j] * z0[j] + T.S[1][i][j] * z1[j];
+            out[(v + P2 * i) * RC + c] = a;
+        }
+    }
+    __syncthreads();
+}
+
+// L2L of a parent F [P3][RC] into its child o only, in place allowed (out may
+// be F); scratch Y [P3][RC]
+template <int P, int RC>
+__device__ void l2l1_rc(const InterpTables &T, const float *F, int o, float *Y, float *out)
+{
+    constexpr int P2 = P * P;
+    const int t = threadIdx.x;
+    for (int q = t; q < RC * P2; q += kThreads) { // z pass: line (j1 + P j2, column)
+        const int c = q % RC, v = q / RC;
+        float f[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j)
+            f[j] = F[(v + P2 * j) * RC + c];
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            float a = 0.0f;
+#pragma unroll
+            for (int j = 0; j < P; ++j)
+                a += T.S[o >> 2][j][i] * f[j];
+            Y[(v + P2 * i) * RC + c] = a;
+        }
+    }
+    __syncthreads();
+    for (int q = t; q < RC * P2; q += kThreads) { // y pass: line (j1, i3, column), into out
+        const int c = q % RC, v = q / RC, j1 = v % P, i3 = v / P;
+        float f[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j)
+            f[j] = Y[(j1 + P * j + P2 * i3) * RC + c];
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            float a = 0.0f;
+#pragma unroll
+            for (int j = 0; j < P; ++j)
+                a += T.S[(o >> 1) & 1][j][i] * f[j];
+            out[(j1 + P * i + P2 * i3) * RC + c] = a;
+        }
+    }
+    __syncthreads();
+    for (int q = t; q < RC * P2; q += kThreads) { // x pass: line (i2 + P i3, column), in place
+        const int c = q % RC, v = q / RC;
+        float f[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j)
+            f[j] = out[(P * v + j) * RC + c];
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            float a = 0.0f;
+#pragma unroll
+            for (int j = 0; j < P; ++j)
+                a += T.S[o & 1][j][i] * f[j];
+            out[(P * v + i) * RC + c] = a;
+        }
+    }
+    __syncthreads();
+}
+
+// L2L of one parent F [P3][RC] into its 8 children out [P3][8][RC]; scratch
+// Y [RC][2][P3], Z [RC][4][P3]
+template <int P, int RC>
+__device__ void l2l8_rc(const InterpTables &T, const float *F, float *Y, float *Z, float *out)
+{
+    constexpr int P2 = P * P, P3 = P2 * P;
+    const int t = threadIdx.x;
+    for (int q = t; q < RC * 2 * P2; q += kThreads) { // z pass: line (oz, j1 + P j2, column)
+        const int c = q % RC, u = q / RC, oz = u & 1, j12 = u >> 1;
+        float f[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j)
+            f[j] = F[(j12 + P2 * j) * RC + c];
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            float a = 0.0f;
+#pragma unroll
+            for (int j = 0; j < P; ++j)
+                a += T.S[oz][j][i] * f[j];
+            Y[(c * 2 + oz) * P3 + j12 + P2 * i] = a;
+        }
+    }
+    __syncthreads();
+    for (int q = t; q < RC * 4 * P2; q += kThreads) { // y pass: line (oy + 2 oz, j1, i3, column)
+        const int c = q % RC, u = q / RC, yz = u & 3, v = u >> 2, j1 = v % P, i3 = v / P;
+        const float *src = Y + (c * 2 + (yz >> 1)) * P3 + j1 + P2 * i3;
+        float f[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j)
+            f[j] = src[P * j];
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            float a = 0.0f;
+#pragma unroll
+            for (int j = 0; j < P; ++j)
+                a += T.S[yz & 1][j][i] * f[j];
+            Z[(c * 4 + yz) * P3 + j1 + P * i + P2 * i3] = a;
+        }
+    }
+    __syncthreads();
+    for (int q = t; q < RC * 8 * P2; q += kThreads) { // x pass: line (child o, i2 + P i3, column)
+        const int c = q % RC, u = q / RC, o = u & 7, rest = u >> 3;
+        const float *src = Z + (c * 4 + (o >> 1)) * P3 + P * rest;
+        float f[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j)
+            f[j] = src[j];
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            float a = 0.0f;
+#pragma unroll
+            for (int j = 0; j < P; ++j)
+                a += T.S[o & 1][j][i] * f[j];
+            out[((i + P * rest) * 8 + o) * RC + c] = a;
+        }
+    }
+    __syncthreads();
+}
+
+// compress one box at level l, RC columns of X [P3][RC]: thread (k, half h)
+// makes columns RC/2 h .. RC/2 h + RC/2 - 1 of coefficient k
+template <int P, int RC>
+__device__ void compress1_rc(const PassArgs &A, int l, const float *X, int64_t box, int c0, int nc)
+{
+    constexpr int P3 = P * P * P, CPT = RC / 2;
+    const int t = threadIdx.x, kk = t & 127, h = t >> 7;
+    const int H = 1 << (l - 1);
+    const float *V = A.V[l];
+    int x, y, z;
+    demorton3((uint32_t)box, x, y, z);
+    float mx = 0.0f;
+    for (int k0 = 0; k0 < A.rl[l]; k0 += 128) { // uniform trip count (warp shuffles in flush_max)
+        const int k = k0 + kk;
+        if (k < A.rl[l]) {
+            float acc[CPT];
+#pragma unroll
+            for (int j = 0; j < CPT; ++j)
+                acc[j] = 0.0f;
+#pragma unroll 5
+            for (int i = 0; i < P3; ++i) {
+                const float v = __ldg(V + (int64_t)i * A.rp + k);
+                float m[CPT];
+                ldv<CPT>(X + i * RC + h * CPT, m);
+#pragma unroll
+                for (int j = 0; j < CPT; ++j)
+                    acc[j] += m[j] * v;
+            }
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) {
+                const int c = h * CPT + j;
+                if (c < nc)
+                    put_mt(A, l, parity_row(x, y, z, c0 + c, H, 1, A.R) * A.rp + k, acc[j], mx);
+            }
+        }
+    }
+    flush_max(A, l, mx);
+}
+
+// local coefficients of one box at level l, RC columns: sPar [P3][RC] (the
+// L2L part when add, else 0) + U F~ with F~ [r][RC] in sFt; with keep also
+// stored to F[l] (when `store`)
+template <int P, int RC>
+__device__ void decompress1_rc(const PassArgs &A, int l, const float *sFt, float *sPar, bool add, int64_t box,
+                               int c0, int nc, bool store)
+{
+    constexpr int P3 = P * P * P, CPT = RC / 2;
+    const int t = threadIdx.x, h = t >> 7;
+    const int rl = A.rl[l];
+    const float *Ut = A.Ut[l];
+    for (int i0 = 0; i0 < P3; i0 += 128) {
+        const int i = i0 + (t & 127);
+        if (i < P3) {
+            float acc[CPT];
+#pragma unroll
+            for (int j = 0; j < CPT; ++j)
+                acc[j] = 0.0f;
+#pragma unroll 4
+            for (int k = 0; k < rl; ++k) {
+                const float u = __ldg(Ut + (int64_t)k * A.p3p + i);
+                float f[CPT];
+                ldv<CPT>(sFt + k * RC + h * CPT, f);
+#pragma unroll
+                for (int j = 0; j < CPT; ++j)
+                    acc[j] += f[j] * u;
+            }
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) {
+                const int c = h * CPT + j;
+                const float f = (add ? sPar[i * RC + c] : 0.0f) + acc[j];
+                sPar[i * RC + c] = f;
+                if (store && c < nc)
+                    A.F[l][(box * A.nrhs + c0 + c) * P3 + i] = f;
+            }
+        }
+    }
+}
+
+// F~ of one box at level l, RC columns (slices summed), into sFt [r][RC]
+template <int RC>
+__device__ __forceinline__ void load_ft_rc(const PassArgs &A, int l, int64_t box, int c0, int nc, float *sFt)
+{
+    const int rl = A.rl[l];
+    for (int q = threadIdx.x; q < rl * RC; q += kThreads) {
+        const int c = q % RC, k = q / RC;
+        if (c < nc)
+            load_ft(A, l, box, c0 + c, sFt + c, RC, k);
+        else
+            sFt[q] = 0.0f;
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_upward_rc(const __grid_constant__ PassArgs A)
+{
+    constexpr int P3 = P * P * P, RC = kRC<P>;
+    extern __shared__ __align__(16) float sm[];
+    float *sX = sm, *sY = sm + SmemRC<P>::kUpY, *sPar = sm + SmemRC<P>::kUpPar;
+    __shared__ int sLast;
+    const int t = threadIdx.x, w = t >> 5;
+    const int D = A.D;
+    const int64_t b = blockIdx.x; // box at level D-1
+    const int c0 = blockIdx.y * RC, nc = min(RC, A.nrhs - c0);
+    const int64_t leaf = 8 * b + w, nb = 1LL << (3 * D);
+    const bool zero = __syncthreads_count(A.off[leaf + 1] > A.off[leaf]) == 0;
+
+    // ---- P2M: warp w makes M of leaf 8b + w for the chunk's columns
+    p2m_leaf_rc<P, RC>(A, leaf, c0, nc, sY + w * 32 * (3 * P + RC), sX);
+    __syncthreads();
+    // ---- the leaves' compression, or their rows for the compression GEMM
+    if (!A.Mleaf) {
+        for (int c = 0; c < nc; ++c)
+            compress8<P>(A, D, sX + c * 8 * P3, 8 * b, c0 + c, zero);
+    } else if (!zero) {
+        for (int q = t; q < nc * 8 * P3; q += kThreads) {
+            const int i = q % P3, u = q / P3, o = u & 7, c = u >> 3;
+            A.Mleaf[((int64_t)(c0 + c) * nb + 8 * b + o) * A.p3p + i] = sX[(c * P3 + i) * 8 + o];
+        }
+    }
+    if (D - 1 < 2)
+        return;
+
+    // ---- own box at level D-1 (the M2M's third pass overwrites X: the
+    // compression above read it before the M2M's first barrier)
+    if (zero) {
+        for (int r = t; r < P3 * RC; r += kThreads)
+            sPar[r] = 0.0f;
+        __syncthreads();
+    } else {
+        m2m8_rc<P, RC>(A.T, sX, sY, sX, sPar);
+    }
+    for (int q = t; q < nc * P3; q += kThreads) {
+        const int r = q % P3, c = q / P3;
+        A.M[D - 1][(b * A.nrhs + c0 + c) * P3 + r] = sPar[r * RC + c];
+    }
+    if (A.Mlev1) // compressed by the GEMM after this launch
+        for (int q = t; q < nc * P3; q += kThreads) {
+            const int r = q % P3, c = q / P3;
+            A.Mlev1[((int64_t)(c0 + c) * (1LL << (3 * (D - 1))) + b) * A.p3p + r] = sPar[r * RC + c];
+        }
+    else
+        compress1_rc<P, RC>(A, D - 1, sPar, b, c0, nc);
+
+    // ---- upper levels: the last of 8 siblings to arrive makes the parent
+    int64_t box = b;
+    for (int l = D - 2; l >= 2; --l) {
+        const int64_t par = box >> 3;
+        __threadfence(); // this thread's stores of the level-(l+1) box are visible device-wide
+        __syncthreads();
+        if (t == 0) {
+            int *cnt = A.count[l] + par * A.R + c0; // one counter per (box, chunk)
+            const int before = atomicAdd(cnt, 1);
+            sLast = before == 7;
+            if (before == 7) {
+                atomicExch(cnt, 0); // ready for the next matvec
+                __threadfence();
+            }
+        }
+        __syncthreads();
+        if (!sLast)
+            return;
+        for (int q = t; q < RC * 8 * P3; q += kThreads) {
+            const int o = q & 7, r = (q >> 3) % P3, c = (q >> 3) / P3;
+            sX[q] = c < nc ? __ldcg(A.M[l + 1] + ((8 * par + o) * A.nrhs + c0 + c) * (int64_t)P3 + r) : 0.0f;
+        }
+        __syncthreads();
+        m2m8_rc<P, RC>(A.T, sX, sY, sX, sPar);
+        for (int q = t; q < nc * P3; q += kThreads) {
+            const int r = q % P3, c = q / P3;
+            A.M[l][(par * A.nrhs + c0 + c) * P3 + r] = sPar[r * RC + c];
+        }
+        compress1_rc<P, RC>(A, l, sPar, par, c0, nc);
+        box = par;
+    }
+}
+
+// first downward launch (depth >= 4), several columns: block = (box of level
+// D-2, chunk of RC columns)
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_down_top_rc(const __grid_constant__ PassArgs A)
+{
+    constexpr int P3 = P * P * P, RC = kRC<P>;
+    extern __shared__ __align__(16) float sm[];
+    float *sPar = sm, *sOne = sm + P3 * RC, *sFt = sm + 2 * P3 * RC;
+    const int t = threadIdx.x;
+    const int D = A.D, lt = D - 2;
+    const int64_t b = blockIdx.x; // box at level D-2
+    const int c0 = blockIdx.y * RC, nc = min(RC, A.nrhs - c0);
+    if (!A.keep && A.toff[64 * b] == A.toff[64 * b + 64])
+        return; // no targets below this box: the main launch skips its children too
+    for (int l = 2; l <= lt; ++l) {
+        const int64_t anc = b >> (3 * (lt - l));
+        if (l > 2)
+            l2l1_rc<P, RC>(A.T, sPar, (int)(anc & 7), sOne, sPar);
+        load_ft_rc<RC>(A, l, anc, c0, nc, sFt);
+        __syncthreads();
+        const bool store = A.keep && (b & ((1LL << (3 * (lt - l))) - 1)) == 0;
+        decompress1_rc<P, RC>(A, l, sFt, sPar, l > 2, anc, c0, nc, store);
+        __syncthreads();
+    }
+    for (int q = t; q < nc * P3; q += kThreads) {
+        const int i = q % P3, c = q / P3;
+        A.Ftop[(b * A.nrhs + c0 + c) * P3 + i] = sPar[i * RC + c];
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_downward_rc(const __grid_constant__ PassArgs A)
+{
+    constexpr int P2 = P * P, P3 = P2 * P, RC = kRC<P>;
+    extern __shared__ __align__(16) float sm[];
+    float *sMT = sm;                        // [P3][8][RC] the leaves' local coefficients
+    float *sY = sm + SmemRC<P>::kDnY;       // [RC][2][P3] scratch
+    float *sZ = sm + SmemRC<P>::kDnZ;       // [RC][4][P3] scratch
+    float *sPar = sm + SmemRC<P>::kDnPar;   // [P3][RC] the current ancestor
+    float *sOne = sm + SmemRC<P>::kDnOne;   // [P3][RC] scratch
+    float *sFt = sm + SmemRC<P>::kDnFt;     // [r][RC] compressed far field of the current ancestor
+    __shared__ int64_t sRow[8 * RC];
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    const int D = A.D;
+    const int64_t b = blockIdx.x; // box at level D-1
+    const int c0 = blockIdx.y * RC, nc = min(RC, A.nrhs - c0);
+    if (!A.keep && A.toff[8 * b] == A.toff[8 * b + 8])
+        return; // no targets below this box
+
+    // ---- ancestors at levels 2 .. D-1 (with Ftop: the parent from the first launch)
+    int l0 = 2;
+    if (A.Ftop) {
+        for (int q = t; q < P3 * RC; q += kThreads) {
+            const int i = q / RC, c = q % RC;
+            sPar[q] = c < nc ? __ldcg(A.Ftop + ((b >> 3) * A.nrhs + c0 + c) * (int64_t)P3 + i) : 0.0f;
+        }
+        __syncthreads();
+        l0 = D - 1;
+    }
+    for (int l = l0; l <= D - 1; ++l) {
+        const int64_t anc = b >> (3 * (D - 1 - l));
+        if (l > 2)
+            l2l1_rc<P, RC>(A.T, sPar, (int)(anc & 7), sOne, sPar);
+        if (l == D - 1 && A.Fdec1) {
+            // the block's own box, decompressed by the GEMM before this launch
+            if (t < RC) {
+                int x, y, z;
+                demorton3((uint32_t)anc, x, y, z);
+                sRow[t] = t < nc ? parity_row(x, y, z, c0 + t, 1 << (l - 1), 0, A.R) : -1;
+            }
+            __syncthreads();
+            for (int q = t; q < nc * P3; q += kThreads) {
+                const int i = q % P3, c = q / P3;
+                const float f = (l > 2 ? sPar[i * RC + c] : 0.0f) + __ldg(A.Fdec1 + sRow[c] * A.p3p + i);
+                sPar[i * RC + c] = f;
+                if (A.keep)
+                    A.F[l][(anc * A.nrhs + c0 + c) * P3 + i] = f;
+            }
+            __syncthreads();
+            continue;
+        }
+        load_ft_rc<RC>(A, l, anc, c0, nc, sFt);
+        __syncthreads();
+        const bool store = A.keep && (b & ((1LL << (3 * (D - 1 - l))) - 1)) == 0;
+        decompress1_rc<P, RC>(A, l, sFt, sPar, l > 2, anc, c0, nc, store);
+        __syncthreads();
+    }
+
+    // ---- the 8 leaves: L2L from the block's box plus their own far field
+    if (D - 1 >= 2) {
+        l2l8_rc<P, RC>(A.T, sPar, sY, sZ, sMT);
+    } else {
+        for (int q = t; q < 8 * P3 * RC; q += kThreads)
+            sMT[q] = 0.0f;
+        __syncthreads();
+    }
+    if (t < 8 * RC) {
+        const int o = t & 7, c = t >> 3;
+        int x, y, z;
+        demorton3((uint32_t)(8 * b + o), x, y, z);
+        sRow[t] = c < nc ? parity_row(x, y, z, c0 + c, 1 << (D - 1), 0, A.R) : -1;
+    }
+    __syncthreads();
+    if (A.Fdec) {
+        // decompressed by the GEMM before this launch
+        for (int q = t; q < 8 * P3 * nc; q += kThreads) {
+            const int i = q % P3, u = q / P3, o = u & 7, c = u >> 3;
+            sMT[(i * 8 + o) * RC + c] += __ldg(A.Fdec + sRow[u] * A.p3p + i);
+        }
+    } else {
+        // per column: the 8 leaves' F~ [r][8] (in the scratch, free after the
+        // L2L) decompressed on the CUDA cores, 4 leaves per thread
+        float *sF8 = sY;
+        const float *Ut = A.Ut[D];
+        const int h = t >> 7, rl = A.rl[D];
+        for (int c = 0; c < nc; ++c) {
+            for (int q = t; q < 8 * rl; q += kThreads) {
+                const int o = q & 7, k = q >> 3;
+                const float *src = A.Ft[D] + sRow[8 * c + o] * A.rp + k;
+                float v = __ldg(src);
+                for (int g = 1; g < A.nslices; ++g)
+                    v += __ldg(src + g * A.slice[D]);
+                sF8[k * 8 + o] = v;
+            }
+            __syncthreads();
+            for (int i0 = 0; i0 < P3; i0 += 128) {
+                const int i = i0 + (t & 127);
+                if (i < P3) {
+                    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 4
+                    for (int k = 0; k < rl; ++k) {
+                        const float u = __ldg(Ut + (int64_t)k * A.p3p + i);
+                        const float4 f = *reinterpret_cast<const float4 *>(sF8 + k * 8 + 4 * h);
+                        acc[0] += f.x * u;
+                        acc[1] += f.y * u;
+                        acc[2] += f.z * u;
+                        acc[3] += f.w * u;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        sMT[(i * 8 + 4 * h + q) * RC + c] += acc[q];
+                }
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    if (A.keep)
+        for (int q = t; q < 8 * P3 * nc; q += kThreads) {
+            const int r = q % P3, u = q / P3, o = u & 7, c = u >> 3;
+            A.F[D][((8 * b + o) * A.nrhs + c0 + c) * P3 + r] = sMT[(r * 8 + o) * RC + c];
+        }
+
+    // ---- L2P: warp w evaluates leaf 8b + w at its targets, RC columns
+    const int64_t leaf = 8 * b + w;
+    const int s0 = A.toff[leaf], s1 = A.toff[leaf + 1];
+    for (int j0 = s0; j0 < s1; j0 += 32) {
+        const int j = j0 + lane;
+        const bool has = j < s1;
+        const float4 u = A.tpts[has ? j : s0];
+        float Lx[P], Ly[P];
+        basis_1d<P>(A.T, 2.0f * u.x, Lx);
+        basis_1d<P>(A.T, 2.0f * u.y, Ly);
+        const float sz = 2.0f * u.z;
+        float acc[RC];
+#pragma unroll
+        for (int c = 0; c < RC; ++c)
+            acc[c] = 0.0f;
+#pragma unroll 1
+        for (int i3 = 0; i3 < P; ++i3) {
+            float lz = A.T.wbary[i3];
+#pragma unroll
+            for (int k = 0; k < P; ++k)
+                lz *= k != i3 ? sz - A.T.nodes[k] : 1.0f;
+            const float *Fz = sMT + ((P2 * i3) * 8 + w) * RC;
+            float slice[RC];
+#pragma unroll
+            for (int c = 0; c < RC; ++c)
+                slice[c] = 0.0f;
+#pragma unroll
+            for (int i2 = 0; i2 < P; ++i2) {
+                float part[RC];
+#pragma unroll
+                for (int c = 0; c < RC; ++c)
+                    part[c] = 0.0f;
+#pragma unroll
+                for (int i1 = 0; i1 < P; ++i1) {
+                    float f[RC];
+                    ldv<RC>(Fz + ((i1 + P * i2) * 8) * RC, f);
+#pragma unroll
+                    for (int c = 0; c < RC; ++c)
+                        part[c] += f[c] * Lx[i1];
+                }
+#pragma unroll
+                for (int c = 0; c < RC; ++c)
+                    slice[c] += part[c] * Ly[i2];
+            }
+#pragma unroll
+            for (int c = 0; c < RC; ++c)
+                acc[c] += slice[c] * lz;
+        }
+        if (has)
+#pragma unroll
+            for (int c = 0; c < RC; ++c)
+                if (c < nc)
+                    A.phi[(int64_t)(c0 + c) * A.nt + j] = acc[c];
+    }
+}
+
 template <int P>
 cudaError_t upward_p(const PassArgs &A, cudaStream_t s)
 {
+    if (A.nrhs > 1) {
+        const size_t smem = sizeof(float) * SmemRC<P>::kUpFloats;
+        cudaError_t e =
+            cudaFuncSetAttribute(k_upward_rc<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        dim3 grid((unsigned)(1LL << (3 * (A.D - 1))), (unsigned)((A.nrhs + kRC<P> - 1) / kRC<P>));
+        k_upward_rc<P><<<grid, kThreads, smem, s>>>(A);
+        return cudaGetLastError();
+    }
     if (P <= kWideMaxP && A.D >= kWideMinDepth) {
         const size_t smem = sizeof(float) * SmemW<P>::kUpFloats;
         cudaError_t e =
@@ -950,6 +1677,31 @@ cudaError_t upward_p(const PassArgs &A, cudaStream_t s)
 template <int P>
 cudaError_t downward_p(const PassArgs &A, cudaStream_t s)
 {
+    if (A.nrhs > 1) {
+        const unsigned chunks = (unsigned)((A.nrhs + kRC<P> - 1) / kRC<P>);
+        if (A.Ftop) {
+            if (A.D < 4)
+                return cudaErrorInvalidValue;
+            const size_t smem = sizeof(float) * 3 * P * P * P * kRC<P>;
+            cudaError_t e =
+                cudaFuncSetAttribute(k_down_top_rc<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess)
+                return e;
+            dim3 grid((unsigned)(1LL << (3 * (A.D - 2))), chunks);
+            k_down_top_rc<P><<<grid, kThreads, smem, s>>>(A);
+            e = cudaGetLastError();
+            if (e != cudaSuccess)
+                return e;
+        }
+        const size_t smem = sizeof(float) * SmemRC<P>::kDnFloats;
+        cudaError_t e =
+            cudaFuncSetAttribute(k_downward_rc<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        dim3 grid((unsigned)(1LL << (3 * (A.D - 1))), chunks);
+        k_downward_rc<P><<<grid, kThreads, smem, s>>>(A);
+        return cudaGetLastError();
+    }
     if (A.Ftop) {
         if (A.D < 4)
             return cudaErrorInvalidValue;

@@ -197,6 +197,46 @@ def test_multiple_rhs_columns_match_single(bb, oracle):
     assert oracle.rel_err(both, ref) <= 1e-5
 
 
+@pytest.mark.parametrize("p,depth,kind,nrhs,leaf_gemm", [(4, 4, "uniform", 11, True), (5, 5, "clustered", 9, True),
+                                                        (5, 4, "uniform", 3, False), (6, 4, "uniform", 5, False),
+                                                        (8, 3, "uniform", 3, False), (3, 2, "uniform", 2, True)])
+def test_several_rhs_passes_match_one_column(bb, oracle, p, depth, kind, nrhs, leaf_gemm):
+    """Several right-hand sides run the upward and downward passes with a
+    block per (box, chunk of columns): chunks of 8 columns for p <= 5, 4 for
+    p = 6, 7 and 2 above, so these counts leave a partial last chunk.  Every
+    level's M and F and the result equal one-column matvecs of the same plan
+    column by column (to FP32 rounding), with the leaves' compression on the
+    tensor cores or in the pass; depth 5 runs the arrival chain over three
+    levels, depth 4 and 5 the level-(D-2) first launch of the downward pass."""
+    n = 12_000
+    dev = torch.device("cuda:0")
+    pts = W.make_points(kind, n, seed=61)
+    sig = W.uniform_sigma(n, nrhs=nrhs, seed=62).astype(np.float32)
+    plan = bb.Plan(torch.from_numpy(pts).to(dev), K_INV_R, p, depth, svd_eps=0.0, domain=UNIT, max_nrhs=nrhs,
+                   keep_coefficients=True, autotune=False)
+    for m in (1, nrhs):
+        t = bb.bbfmm_get_tuning(plan.handle, m)
+        bb.bbfmm_set_tuning(plan.handle, m, "ordered", t.m2l_tile, t.m2l_stages, leaf_gemm=leaf_gemm)
+        assert bb.bbfmm_get_tuning(plan.handle, m).leaf_gemm == int(leaf_gemm)
+    many = plan.matvec(torch.from_numpy(np.ascontiguousarray(sig.T)).to(dev)).cpu().numpy().astype(np.float64).T
+    Ms = {l: bb.bbfmm_get_coefficients(plan.handle, 0, l, nrhs, p) for l in range(2, depth + 1)}
+    Fs = {l: bb.bbfmm_get_coefficients(plan.handle, 1, l, nrhs, p) for l in range(2, depth + 1)}
+    for c in range(nrhs):
+        one = plan.matvec(torch.from_numpy(np.ascontiguousarray(sig[:, c])).to(dev)).cpu().numpy().astype(np.float64)
+        for l in range(2, depth + 1):
+            m1 = bb.bbfmm_get_coefficients(plan.handle, 0, l, 1, p)[:, 0]
+            f1 = bb.bbfmm_get_coefficients(plan.handle, 1, l, 1, p)[:, 0]
+            assert oracle.rel_err(Ms[l][:, c], m1) < 2e-6, ("M", l, c)
+            assert oracle.rel_err(Fs[l][:, c], f1) < 2e-6, ("F", l, c)
+        # the near fields differ in summation order (k_p2p_gemm against the
+        # one-column kernel: up to ~5000 FP32 terms per target at depth 2)
+        np.testing.assert_allclose(many[:, c], one, rtol=0, atol=3e-6 * np.abs(one).max())
+    assert bb.bbfmm_status(plan.handle) == 0
+    plan.close()
+    ref = oracle_fmm(oracle, pts, sig, K_INV_R, p, depth)
+    assert oracle.rel_err(many, ref) <= 1e-5
+
+
 def test_repeatable_bitwise(bb):
     n = 30_000
     pts = W.clustered_points(n, seed=53)
