@@ -279,8 +279,9 @@ __device__ __forceinline__ void flush_max(const PassArgs &A, int l, float mx)
         atomicMax(A.maxbits + l, __float_as_uint(mx));
 }
 
-// compress 8 sibling boxes box0..box0+7 at level l: M~[k] = sum_i V[i][k] M[i]
-template <int P>
+// compress 8 sibling boxes box0..box0+7 at level l: M~[k] = sum_i V[i][k] M[i];
+// X is [P3][8], or [8][P3] with XT
+template <int P, bool XT = false>
 __device__ void compress8(const PassArgs &A, int l, const float *X, int64_t box0, int c, bool zero)
 {
     constexpr int P3 = P * P * P;
@@ -296,7 +297,9 @@ __device__ void compress8(const PassArgs &A, int l, const float *X, int64_t box0
 #pragma unroll 5
             for (int i = 0; i < P3; ++i) {
                 const float v = __ldg(V + (int64_t)i * A.rp + k);
-                const float4 m = *reinterpret_cast<const float4 *>(X + i * 8 + 4 * h);
+                const float4 m = XT ? make_float4(X[4 * h * P3 + i], X[(4 * h + 1) * P3 + i],
+                                                  X[(4 * h + 2) * P3 + i], X[(4 * h + 3) * P3 + i])
+                                    : *reinterpret_cast<const float4 *>(X + i * 8 + 4 * h);
                 acc[0] += m.x * v;
                 acc[1] += m.y * v;
                 acc[2] += m.z * v;
@@ -958,11 +961,14 @@ __global__ void __launch_bounds__(kThreads) k_upward_wide(const __grid_constant_
 // per (box, column) the passes were bound by the latency of their short
 // phases (3.4 ms each way for 500k points x 64 columns at depth 5).
 //
-// Shared-memory layouts (floats): X [RC][P3][8] (8 sibling boxes of one
-// column, as the one-column kernels keep them); P [P3][RC] (one box, the
+// Shared-memory layouts (floats): X [RC][8][P3] (8 sibling boxes of each
+// column, a box's coefficients contiguous: P2M's lanes, 5 coefficients
+// apart, and the rows stored for the compression GEMM meet distinct banks);
+// P [P3][RC] (one box, the
 // columns side by side, so one vector load gives a thread its columns);
-// the leaves' local coefficients in the downward pass [P3][8][RC] (L2P reads
-// a leaf's RC columns of one coefficient with one vector load).
+// the leaves' local coefficients in the downward pass [8][P3][RC] (L2P reads
+// a leaf's RC columns of one coefficient with one vector load; the far-field
+// rows are added by lanes that run over (column, coefficient), 32 banks apart).
 template <int P> constexpr int kRC = P <= 5 ? 8 : (P <= 7 ? 4 : 2);
 
 template <int P> struct SmemRC {
@@ -972,9 +978,11 @@ template <int P> struct SmemRC {
     static constexpr int kUpYN = 8 * P3 * RC > 256 * (3 * P + RC) ? 8 * P3 * RC : 256 * (3 * P + RC);
     static constexpr int kUpPar = kUpY + kUpYN;
     static constexpr int kUpFloats = kUpPar + P3 * RC;
-    // downward: leaves [P3][8][RC] | Y [RC][2][P3] | Z [RC][4][P3] | P | scratch P | F~ [r][RC]
-    static constexpr int kDnY = 8 * P3 * RC, kDnZ = 10 * P3 * RC, kDnPar = 14 * P3 * RC, kDnOne = 15 * P3 * RC,
-                         kDnFt = 16 * P3 * RC, kDnFloats = 17 * P3 * RC;
+    // downward: leaves [8][P3][RC] (the L2L's Y [RC][2][P3] aliases them: Y
+    // is dead before the L2L's last pass writes the leaves) | Z [RC][4][P3]
+    // (the ancestors' scratch P and F~ [r][RC] alias it) | P
+    static constexpr int kDnY = 0, kDnZ = 8 * P3 * RC, kDnOne = 8 * P3 * RC, kDnFt = 9 * P3 * RC,
+                         kDnPar = 12 * P3 * RC, kDnFloats = 13 * P3 * RC;
     static_assert(kDnPar % 2 == 0 && kUpPar % 2 == 0, "vector loads of the column sets");
 };
 
@@ -1001,7 +1009,7 @@ __device__ __forceinline__ void ldv(const float *p, float (&v)[N])
 }
 
 // P2M of leaf `leaf` for columns c0 .. c0 + RC - 1 (nc of them real) by one
-// warp, into column leaf & 7 of X [RC][P3][8]; L: the warp's 32 x (3P + RC)
+// warp, into box leaf & 7 of X [RC][8][P3]; L: the warp's 32 x (3P + RC)
 // scratch (basis values of 32 points, then their RC weights)
 template <int P, int RC>
 __device__ __forceinline__ void p2m_leaf_rc(const PassArgs &A, int64_t leaf, int c0, int nc, float *L, float *X)
@@ -1066,7 +1074,7 @@ __device__ __forceinline__ void p2m_leaf_rc(const PassArgs &A, int64_t leaf, int
 #pragma unroll
                 for (int i = 0; i < P; ++i) {
                     const int idx = i + P * pq;
-                    X[(c * P3 + idx) * 8 + o] = acc[q][c][i];
+                    X[(c * 8 + o) * P3 + idx] = acc[q][c][i];
                     if (A.keep && c < nc)
                         A.M[A.D][(leaf * A.nrhs + c0 + c) * P3 + idx] = acc[q][c][i];
                 }
@@ -1074,7 +1082,7 @@ __device__ __forceinline__ void p2m_leaf_rc(const PassArgs &A, int64_t leaf, int
     }
 }
 
-// M2M of 8 children, RC columns: X [RC][P3][8] -> out [P3][RC]; scratch Y
+// M2M of 8 children, RC columns: X [RC][8][P3] -> out [P3][RC]; scratch Y
 // [RC][P3][8] and Z [RC][P3][4] (Z may alias X: X is read by the first pass only)
 template <int P, int RC>
 __device__ void m2m8_rc(const InterpTables &T, const float *X, float *Y, float *Z, float *out)
@@ -1083,11 +1091,11 @@ __device__ void m2m8_rc(const InterpTables &T, const float *X, float *Y, float *
     const int t = threadIdx.x;
     for (int q = t; q < RC * 8 * P2; q += kThreads) { // x pass: line (child o, j2 + P j3, column)
         const int o = q & 7, u = q >> 3, rest = u % P2, c = u / P2;
-        const float *Xc = X + c * 8 * P3;
+        const float *Xc = X + (c * 8 + o) * P3 + P * rest;
         float x[P];
 #pragma unroll
         for (int j = 0; j < P; ++j)
-            x[j] = Xc[(j + P * rest) * 8 + o];
+            x[j] = Xc[j];
         float *Yc = Y + c * 8 * P3;
 #pragma unroll
         for (int i = 0; i < P; ++i) {
@@ -1198,7 +1206,7 @@ __device__ void l2l1_rc(const InterpTables &T, const float *F, int o, float *Y, 
     __syncthreads();
 }
 
-// L2L of one parent F [P3][RC] into its 8 children out [P3][8][RC]; scratch
+// L2L of one parent F [P3][RC] into its 8 children out [8][P3][RC]; scratch
 // Y [RC][2][P3], Z [RC][4][P3]
 template <int P, int RC>
 __device__ void l2l8_rc(const InterpTables &T, const float *F, float *Y, float *Z, float *out)
@@ -1251,7 +1259,7 @@ __device__ void l2l8_rc(const InterpTables &T, const float *F, float *Y, float *
 #pragma unroll
             for (int j = 0; j < P; ++j)
                 a += T.S[o & 1][j][i] * f[j];
-            out[((i + P * rest) * 8 + o) * RC + c] = a;
+            out[(o * P3 + i + P * rest) * RC + c] = a;
         }
     }
     __syncthreads();
@@ -1369,11 +1377,11 @@ __global__ void __launch_bounds__(kThreads) k_upward_rc(const __grid_constant__ 
     // ---- the leaves' compression, or their rows for the compression GEMM
     if (!A.Mleaf) {
         for (int c = 0; c < nc; ++c)
-            compress8<P>(A, D, sX + c * 8 * P3, 8 * b, c0 + c, zero);
+            compress8<P, true>(A, D, sX + c * 8 * P3, 8 * b, c0 + c, zero);
     } else if (!zero) {
         for (int q = t; q < nc * 8 * P3; q += kThreads) {
-            const int i = q % P3, u = q / P3, o = u & 7, c = u >> 3;
-            A.Mleaf[((int64_t)(c0 + c) * nb + 8 * b + o) * A.p3p + i] = sX[(c * P3 + i) * 8 + o];
+            const int i = q % P3, u = q / P3; // u = 8 c + o
+            A.Mleaf[((int64_t)(c0 + (u >> 3)) * nb + 8 * b + (u & 7)) * A.p3p + i] = sX[q];
         }
     }
     if (D - 1 < 2)
@@ -1419,7 +1427,7 @@ __global__ void __launch_bounds__(kThreads) k_upward_rc(const __grid_constant__ 
         if (!sLast)
             return;
         for (int q = t; q < RC * 8 * P3; q += kThreads) {
-            const int o = q & 7, r = (q >> 3) % P3, c = (q >> 3) / P3;
+            const int r = q % P3, o = (q / P3) & 7, c = q / (8 * P3);
             sX[q] = c < nc ? __ldcg(A.M[l + 1] + ((8 * par + o) * A.nrhs + c0 + c) * (int64_t)P3 + r) : 0.0f;
         }
         __syncthreads();
@@ -1468,12 +1476,12 @@ __global__ void __launch_bounds__(kThreads) k_downward_rc(const __grid_constant_
 {
     constexpr int P2 = P * P, P3 = P2 * P, RC = kRC<P>;
     extern __shared__ __align__(16) float sm[];
-    float *sMT = sm;                        // [P3][8][RC] the leaves' local coefficients
-    float *sY = sm + SmemRC<P>::kDnY;       // [RC][2][P3] scratch
-    float *sZ = sm + SmemRC<P>::kDnZ;       // [RC][4][P3] scratch
+    float *sMT = sm;                        // [8][P3][RC] the leaves' local coefficients
+    float *sY = sm + SmemRC<P>::kDnY;       // [RC][2][P3] L2L scratch (aliases the leaves)
+    float *sZ = sm + SmemRC<P>::kDnZ;       // [RC][4][P3] L2L scratch
     float *sPar = sm + SmemRC<P>::kDnPar;   // [P3][RC] the current ancestor
-    float *sOne = sm + SmemRC<P>::kDnOne;   // [P3][RC] scratch
-    float *sFt = sm + SmemRC<P>::kDnFt;     // [r][RC] compressed far field of the current ancestor
+    float *sOne = sm + SmemRC<P>::kDnOne;   // [P3][RC] ancestors' scratch (aliases Z)
+    float *sFt = sm + SmemRC<P>::kDnFt;     // [r][RC] compressed far field of the current ancestor (aliases Z)
     __shared__ int64_t sRow[8 * RC];
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const int D = A.D;
@@ -1538,14 +1546,16 @@ __global__ void __launch_bounds__(kThreads) k_downward_rc(const __grid_constant_
     __syncthreads();
     if (A.Fdec) {
         // decompressed by the GEMM before this launch
-        for (int q = t; q < 8 * P3 * nc; q += kThreads) {
-            const int i = q % P3, u = q / P3, o = u & 7, c = u >> 3;
-            sMT[(i * 8 + o) * RC + c] += __ldg(A.Fdec + sRow[u] * A.p3p + i);
+#pragma unroll 4
+        for (int q = t; q < 8 * P3 * RC; q += kThreads) {
+            const int c = q % RC, u = q / RC, i = u % P3, o = u / P3;
+            if (c < nc)
+                sMT[q] += __ldg(A.Fdec + sRow[8 * c + o] * A.p3p + i);
         }
     } else {
-        // per column: the 8 leaves' F~ [r][8] (in the scratch, free after the
-        // L2L) decompressed on the CUDA cores, 4 leaves per thread
-        float *sF8 = sY;
+        // per column: the 8 leaves' F~ [r][8] (in Z, free after the L2L)
+        // decompressed on the CUDA cores, 4 leaves per thread
+        float *sF8 = sZ;
         const float *Ut = A.Ut[D];
         const int h = t >> 7, rl = A.rl[D];
         for (int c = 0; c < nc; ++c) {
@@ -1573,7 +1583,7 @@ __global__ void __launch_bounds__(kThreads) k_downward_rc(const __grid_constant_
                     }
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
-                        sMT[(i * 8 + 4 * h + q) * RC + c] += acc[q];
+                        sMT[((4 * h + q) * P3 + i) * RC + c] += acc[q];
                 }
             }
             __syncthreads();
@@ -1583,7 +1593,7 @@ __global__ void __launch_bounds__(kThreads) k_downward_rc(const __grid_constant_
     if (A.keep)
         for (int q = t; q < 8 * P3 * nc; q += kThreads) {
             const int r = q % P3, u = q / P3, o = u & 7, c = u >> 3;
-            A.F[D][((8 * b + o) * A.nrhs + c0 + c) * P3 + r] = sMT[(r * 8 + o) * RC + c];
+            A.F[D][((8 * b + o) * A.nrhs + c0 + c) * P3 + r] = sMT[(o * P3 + r) * RC + c];
         }
 
     // ---- L2P: warp w evaluates leaf 8b + w at its targets, RC columns
@@ -1607,7 +1617,7 @@ __global__ void __launch_bounds__(kThreads) k_downward_rc(const __grid_constant_
 #pragma unroll
             for (int k = 0; k < P; ++k)
                 lz *= k != i3 ? sz - A.T.nodes[k] : 1.0f;
-            const float *Fz = sMT + ((P2 * i3) * 8 + w) * RC;
+            const float *Fz = sMT + (w * P3 + P2 * i3) * RC;
             float slice[RC];
 #pragma unroll
             for (int c = 0; c < RC; ++c)
@@ -1621,7 +1631,7 @@ __global__ void __launch_bounds__(kThreads) k_downward_rc(const __grid_constant_
 #pragma unroll
                 for (int i1 = 0; i1 < P; ++i1) {
                     float f[RC];
-                    ldv<RC>(Fz + ((i1 + P * i2) * 8) * RC, f);
+                    ldv<RC>(Fz + (i1 + P * i2) * RC, f);
 #pragma unroll
                     for (int c = 0; c < RC; ++c)
                         part[c] += f[c] * Lx[i1];
