@@ -522,6 +522,58 @@ __device__ __forceinline__ void load_ft(const PassArgs &A, int l, int64_t box, i
     dst[k * stride] = v;
 }
 
+// L2P of a leaf with few points (Sec. 2.3 item 3): a warp takes 32 / P
+// points at a time, lane = (point, i3); the lane sums the z slice i3 of the
+// leaf's coefficients at its point, times the z basis value, and the P lanes
+// of a point are added in order of i3 by shuffles.  Per point this costs P^2
+// products on each of P lanes instead of P^3 on one lane (most of a warp is
+// idle when a leaf holds a handful of points).  F: the leaf's coefficients,
+// element i at F[8 i].  Used up to p = 6: above it the extra path would cost
+// the kernel registers, i.e. blocks per SM.
+template <int P> __host__ __device__ constexpr int l2p_round() { return 32 / P; }
+template <int P> constexpr bool kL2PSmall = P <= 6;
+
+template <int P>
+__device__ void l2p_small(const PassArgs &A, const float *F, int s0, int s1, int c)
+{
+    constexpr int R = l2p_round<P>();
+    const int lane = threadIdx.x & 31;
+    const int pl = lane / P, i3 = lane - pl * P;
+    const float *Fz = F + (P * P * i3) * 8;
+    for (int c0 = s0; c0 < s1; c0 += R) {
+        const int j = c0 + pl;
+        const bool has = pl < R && j < s1;
+        const float4 u = A.tpts[has ? j : s0];
+        float Lx[P], Ly[P];
+        basis_1d<P>(A.T, 2.0f * u.x, Lx);
+        basis_1d<P>(A.T, 2.0f * u.y, Ly);
+        const float sz = 2.0f * u.z;
+        float lz = A.T.wbary[i3];
+#pragma unroll
+        for (int k = 0; k < P; ++k)
+            lz *= k != i3 ? sz - A.T.nodes[k] : 1.0f;
+        // one row of P coefficients live at a time (the kernel's other
+        // phases fit in 32 registers; so must this one)
+        float slice = 0.0f;
+#pragma unroll 1
+        for (int i2 = 0; i2 < P; ++i2) {
+            float part = 0.0f;
+#pragma unroll
+            for (int i1 = 0; i1 < P; ++i1)
+                part += Fz[(i1 + P * i2) * 8] * Lx[i1];
+            slice += part * Ly[i2];
+        }
+        const float v = slice * lz;
+        // the point's P slices in order of i3 (lanes pl P .. pl P + P - 1)
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < P; ++k)
+            acc += __shfl_sync(0xffffffffu, v, pl * P + k);
+        if (has && i3 == 0)
+            A.phi[(int64_t)c * A.nt + j] = acc;
+    }
+}
+
 template <int P>
 __global__ void __launch_bounds__(kThreads) k_downward(const __grid_constant__ PassArgs A)
 {
@@ -660,6 +712,10 @@ __global__ void __launch_bounds__(kThreads) k_downward(const __grid_constant__ P
     // ---- L2P: warp w evaluates leaf 8b + w at its targets (Sec. 2.3 item 3)
     const int64_t leaf = 8 * b + w;
     const int s0 = A.toff[leaf], s1 = A.toff[leaf + 1];
+    if (kL2PSmall<P> && s1 - s0 <= 2 * l2p_round<P>()) {
+        l2p_small<P>(A, sMT + w, s0, s1, c);
+        return;
+    }
     for (int c0 = s0; c0 < s1; c0 += 32) {
         const int j = c0 + lane;
         const bool has = j < s1;
