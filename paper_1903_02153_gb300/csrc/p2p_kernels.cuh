@@ -588,9 +588,10 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
     // colpart (PL * NQP <= kColBuf); without, colpart is not used
     const bool two_way = nsym0 < ns;
     const int PL = two_way ? min(kSymStage, kColBuf / NQP) : kSymStage;
-    if (two_way) // the row padding (groups nq .. NQP-1) is never written: zero it once
-        for (int e = tid; e < PL * (NQP - nq); e += kP2PThreads)
-            colpart[(e / (NQP - nq)) * NQP + nq + e % (NQP - nq)] = 0.0f;
+    if (two_way && NQP > nq) // the row padding (groups nq .. NQP-1) is never written: zero it once
+        for (int r = tid; r < PL; r += kP2PThreads)
+            for (int q = nq; q < NQP; ++q)
+                colpart[r * NQP + q] = 0.0f;
 
     float2 acc[NPK], acc2[NPK];
 #pragma unroll
