@@ -275,7 +275,7 @@ struct bbfmm_plan_impl {
     // the far field runs on a high-priority stream, the near field on a
     // low-priority one, so near-field blocks fill what the far field leaves
     cudaStream_t far_stream = nullptr, side_stream = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_far = nullptr, ev_up = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_far = nullptr;
     bool timing = false;
     cudaEvent_t ev[Stage::NumEv] = {};
     cudaEvent_t ev_p2p0 = nullptr, ev_p2p1 = nullptr;
