@@ -395,9 +395,11 @@ cudaError_t launch_gram(const float *A, const float *B, int64_t n, int m, double
 cudaError_t launch_rmul(const float *Y, int64_t n, int m, const float *T, int mo, float *out, cudaStream_t s);
 cudaError_t launch_combine(const float *phi_far, const float *phi_near, const float *slots, const int *perm, int64_t n,
                            int nrhs, float *phi, cudaStream_t s);
-// entry points of the two kernels whose pointer arguments (the caller's sigma
-// and phi) change from call to call of a captured matvec graph
+// entry points of the kernels whose pointer arguments (the caller's sigma and
+// phi) change from call to call of a captured matvec graph: the gather (either
+// form; both take the same parameters) and the combine
 const void *gather_kernel();
+const void *gather4_kernel();
 const void *combine_kernel();
 cudaError_t m2l_fp32_init(); // uploads the offset table (outside any stream capture)
 // m2l_fp32.cu

@@ -978,7 +978,7 @@ static int matvec_graph(bbfmm_plan_impl *P, const float *sigma, float *phi, int 
                 cudaGetLastError();
                 continue;
             }
-            if (kp.func == gather_kernel()) {
+            if (kp.func == gather_kernel() || kp.func == gather4_kernel()) {
                 g.gather = node;
                 g.gp = kp;
             } else if (kp.func == combine_kernel()) {

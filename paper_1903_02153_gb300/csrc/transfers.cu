@@ -43,11 +43,35 @@ __global__ void k_gather(const float *__restrict__ sigma, const int *__restrict_
     }
 }
 
+// one right-hand side: four points per thread (one 16-byte load of perm,
+// four independent loads of sigma in flight, one 16-byte store), the last
+// n % 4 points one per thread.  Same parameters as k_gather (nrhs and rows
+// unused), so a captured matvec graph patches either the same way.
+__global__ void k_gather4(const float *__restrict__ sigma, const int *__restrict__ perm, int64_t n, int,
+                          float *__restrict__ out, float *)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, n4 = n / 4;
+    if (q < n4) {
+        const int4 j = reinterpret_cast<const int4 *>(perm)[q];
+        reinterpret_cast<float4 *>(out)[q] = make_float4(sigma[j.x], sigma[j.y], sigma[j.z], sigma[j.w]);
+    } else if (q < n4 + (n & 3)) {
+        const int64_t i = 4 * n4 + (q - n4);
+        out[i] = sigma[perm[i]];
+    }
+}
+
 const void *gather_kernel() { return (const void *)k_gather; }
+const void *gather4_kernel() { return (const void *)k_gather4; }
 
 cudaError_t launch_gather_sigma(const float *sigma, const int *perm, int64_t n, int nrhs, float *out, float *rows,
                                 cudaStream_t s)
 {
+    if (nrhs == 1 && !rows && reinterpret_cast<uintptr_t>(perm) % 16 == 0 &&
+        reinterpret_cast<uintptr_t>(out) % 16 == 0) {
+        const int64_t threads = n / 4 + (n & 3);
+        k_gather4<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(sigma, perm, n, 1, out, nullptr);
+        return cudaGetLastError();
+    }
     k_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sigma, perm, n, nrhs, out, rows);
     return cudaGetLastError();
 }
