@@ -35,6 +35,9 @@
 //                  offset's partial accumulator into FP32 registers; at the
 //                  end of an item it scales and stores (a warp's 32 lanes
 //                  store 32 consecutive coefficients of one target)
+//   (When no level's rank exceeds 96, TMEM lane quadrant 3 holds no
+//   coefficients: the 256-target launch then has 8 warps, epilogue warps
+//   0-2 and 4-6, the producer 3 and the MMA issuer 7.)
 //
 // Precision: kind::tf32 reads 10 explicit mantissa bits.  The 3-pass mode
 // splits each operand into hi and lo and forms hi*hi + hi*lo + lo*hi (the
@@ -155,6 +158,7 @@ struct TcLaunch {
     int nlev, ntiles;               // levels; tiles of all levels
     int64_t total, per_cta;         // (tile, entry) pairs; pairs per CTA
     int maxops;                     // operator tiles per stage
+    int q3;                         // three epilogue quadrants (ranks <= 96): 256 threads, see the kernel
     int *status;
     int rp, nrhs, R, nstage;            // R: right-hand-side stride of M~ / F~ rows
     int nbuf, bcols, tcols;             // TMEM partial buffers, columns per accumulator, allocated
@@ -226,13 +230,20 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
         }
         for (int b = 0; b < NB; ++b) {
             mbar_init(pfull0 + 8 * b, 1);
-            mbar_init(pempty0 + 8 * b, 4 * CH);
+            mbar_init(pempty0 + 8 * b, (P.q3 ? 3 : 4) * CH);
         }
         mbar_init(done_bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) {
+    // warp roles: producer, MMA issuer and 4 CH epilogue warps (TMEM lane
+    // quadrant q = warp & 3); with q3 (every level's rank <= 96, so lane
+    // quadrant 3 holds no coefficients) the block is 8 warps: epilogue warps
+    // 0-2 and 4-6 (quadrants 0-2 of the two column halves), producer 3, MMA 7.
+    // The two dropped warps' registers let the near field keep more blocks on
+    // the SM beside this one.
+    const int wprod = P.q3 ? 3 : 0, wmma = P.q3 ? 7 : 1;
+    if (warp == wmma) {
         tmem_alloc(smem_u32(tmem_slot), tcols);
         tmem_relinquish();
     }
@@ -241,7 +252,7 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    if (warp == 0 && lane == 0) {
+    if (warp == wprod && lane == 0) {
         // ------------------------------------------------------------ producer
         int last_round[kMaxStages];
         for (int s = 0; s < kMaxStages; ++s)
@@ -298,7 +309,7 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
                 while (!mbar_test(full0 + 8 * q, (uint32_t)last_round[q]) && clock64() - t0 < kWaitCycles) {
                 }
             }
-    } else if (warp == 1 && lane == 0) {
+    } else if (warp == wmma && lane == 0) {
         // ------------------------------------------------------------ MMA issuer
         // One thread issues every MMA of the CTA, so this loop is kept short:
         // ring positions are counters (no division), the descriptors of a
@@ -419,9 +430,9 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
         long long t0 = clock64();
         while (!mbar_test(done_bar, 0) && clock64() - t0 < kWaitCycles) {
         }
-    } else if (warp >= 2) {
+    } else if (P.q3 ? (warp != wprod && warp != wmma) : warp >= 2) {
         // ------------------------------------------------------------ epilogue
-        const int ew = warp - 2;
+        const int ew = P.q3 ? warp : warp - 2;
         const int q = warp & 3;   // TMEM lane quadrant this warp may access
         const int half = ew >> 2; // target columns [128 half, 128 half + 128)
         const uint32_t tlane = tmem_base + ((uint32_t)(32 * q) << 16);
@@ -506,7 +517,7 @@ __global__ void __launch_bounds__(64 + 128 * CH, 1) k_m2l_tc(const __grid_consta
     tc_fence_after();
     if (*abort_flag && threadIdx.x == 0)
         atomicOr(P.status, kStatusTimeout);
-    if (warp == 1) {
+    if (warp == wmma) {
         __syncwarp();
         tmem_dealloc(tmem_base, tcols);
     }
@@ -788,7 +799,7 @@ static cudaError_t launch_tc(const TcLaunch &P, int grid, size_t smem, cudaStrea
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    k_m2l_tc<NPROD, NACC, CF, CH, FMT><<<grid, 64 + 128 * CH, smem, s>>>(P);
+    k_m2l_tc<NPROD, NACC, CF, CH, FMT><<<grid, P.q3 ? 256 : 64 + 128 * CH, smem, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -970,6 +981,13 @@ cudaError_t launch_m2l_all(bbfmm_plan_impl *P, int nrhs, cudaStream_t s)
         if (e != cudaSuccess)
             return e;
     }
+    // three epilogue quadrants when no level's rank needs the fourth (256-target
+    // tiles of the 16-bit forms): measured 0.817 -> 0.813 ms per matvec at
+    // depth 5 and 3.367 -> 3.337 ms at depth 6 (1M points, 1/r, p = 5, r = 89)
+    L.q3 = fmt != 0 && nt == 256 ? 1 : 0;
+    for (int k = 0; k < O.nlev; ++k)
+        if (O.rl[k] > 96)
+            L.q3 = 0;
     const bool cf = P->split_acc;
     if (!three)
         return launch_tc<1, 1, false, 1, 0>(L, grid, smem, s);
