@@ -813,10 +813,11 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
 
     CUDA_TRY(cudaEventRecord(P->ev_fork, s));
     // near field on the low-priority side stream, started once `after` has
-    // fired (the gather, in a timed-free matvec): its blocks fill whatever the
-    // high-priority far field leaves of the SMs, from the upward pass on
-    // (measured 0.850 -> 0.817 ms on 1M points at depth 5, against starting
-    // after the upward pass; in a graph only with node priorities in force)
+    // fired: the gather, unless stage timing is on (then the far field, so
+    // each stage is timed alone).  Its blocks fill whatever the high-priority
+    // far field leaves of the SMs, from the upward pass on (measured 0.850 ->
+    // 0.817 ms on 1M points at depth 5, against starting after the upward
+    // pass; in a graph only with node priorities in force)
     auto near_field = [&](cudaEvent_t after) -> int {
         CUDA_TRY(cudaStreamWaitEvent(P->side_stream, after, 0));
         if (tm)
