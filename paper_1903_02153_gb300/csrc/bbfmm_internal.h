@@ -338,6 +338,8 @@ struct LeafCompressArgs {
 };
 bool leaf_compress_fits(int r, int p3p);
 cudaError_t launch_leaf_compress(const LeafCompressArgs &L, cudaStream_t s);
+// two levels in one launch when they share the operator (else two launches)
+cudaError_t launch_leaf_compress2(const LeafCompressArgs &L, const LeafCompressArgs &L2, cudaStream_t s);
 // the leaf decompression F = U F~ (summed over F~'s offset-group slices) as
 // the same kind of GEMM, into [rows][p3p] for the downward pass
 struct LeafDecompressArgs {
@@ -350,6 +352,7 @@ struct LeafDecompressArgs {
 };
 bool leaf_decompress_fits(int rp, int p3p);
 cudaError_t launch_leaf_decompress(const LeafDecompressArgs &L, cudaStream_t s);
+cudaError_t launch_leaf_decompress2(const LeafDecompressArgs &L, const LeafDecompressArgs &L2, cudaStream_t s);
 cudaError_t launch_downward(const PassArgs &A, int p, cudaStream_t s);
 
 // ---------------------------------------------------------------------------

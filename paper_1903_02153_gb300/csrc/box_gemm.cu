@@ -22,7 +22,10 @@
 // (hi*hi + hi*lo + lo*hi, the split-TF32 scheme of Ootomo & Yokota, 2022).
 // V^T's hi / lo parts are split once on the host; M's are split in shared
 // memory after each TMA load (two warps), so the upward pass writes plain
-// FP32.
+// FP32.  The tensor core's FP32 accumulation truncates; with N <= 128 each
+// K chunk of 32 goes to a fresh TMEM partial (two alternate) and the
+// epilogue sums the partials with round-to-nearest FP32 adds, so a long K
+// (decompression sums several slices of r) loses no more than one chunk.
 //
 //   warp 0      TMA producer: V^T (hi, lo; all of K) once, then per tile of
 //               128 rows and K chunk of 32 the rows' chunk of M
@@ -67,6 +70,15 @@ struct GemmLaunch {
     float *out, *out_hi, *out_lo;
     unsigned *maxbits;    // the level's max |M~| (float bits), or null
     int *status;
+    // a second segment (the boxes of level D-1 when they share the leaves'
+    // operator): tiles tile2 .. ntiles-1, its own A, rows, output and max
+    CUtensorMap a2;
+    int tile2;            // ntiles when there is no second segment
+    int drain;            // a fresh TMEM partial per K chunk, summed in FP32 by the epilogue (N <= 128)
+    int64_t rows2, slice_rows2, nb2;
+    int H2;
+    float *out2, *out2_hi, *out2_lo;
+    unsigned *maxbits2;
 };
 
 __device__ __forceinline__ float tf32_rna(float x)
@@ -137,8 +149,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_leaf_gemm(const __grid_cons
                 mbar_arrive_expect_tx(full0 + 8 * s, kAChunkBytes);
                 last_round[s] = round;
                 const int g = kc / nkc, kk = kc - g * nkc;
-                tma_load_2d(a0 + (uint32_t)s * 2u * kAChunkBytes, &G.a, full0 + 8 * s, kGemmK * kk,
-                            (int)(g * G.slice_rows + (int64_t)kGemmRows * tile));
+                const bool sec = tile >= G.tile2;
+                const int lt = sec ? tile - G.tile2 : tile;
+                tma_load_2d(a0 + (uint32_t)s * 2u * kAChunkBytes, sec ? &G.a2 : &G.a, full0 + 8 * s, kGemmK * kk,
+                            (int)(g * (sec ? G.slice_rows2 : G.slice_rows) + (int64_t)kGemmRows * lt));
                 if (++s == kGemmStages) {
                     s = 0;
                     round ^= 1;
@@ -162,14 +176,18 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_leaf_gemm(const __grid_cons
         const uint32_t d_bch = bchunk >> 4, d_st = (2u * kAChunkBytes) >> 4, d_lo = kAChunkBytes >> 4;
         int s = 0, sph = 0, buf = 0, bph = 0;
         for (int tile = blockIdx.x; ok && tile < G.ntiles; tile += gridDim.x) {
-            if (!mbar_wait(aempty0 + 8 * buf, bph ^ 1, abort_flag)) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            const uint32_t d = tmem_base + (uint32_t)(buf * G.N);
-            uint32_t acc = 0;
+            uint32_t d = 0, acc = 0;
             for (int kc = 0; kc < nk; ++kc) {
+                // a fresh accumulator per tile, or per chunk with drain
+                if (G.drain || kc == 0) {
+                    if (!mbar_wait(aempty0 + 8 * buf, bph ^ 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    d = tmem_base + (uint32_t)(buf * G.N);
+                    acc = 0;
+                }
                 if (!mbar_wait(split0 + 8 * s, sph, abort_flag)) {
                     ok = false;
                     break;
@@ -191,14 +209,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_leaf_gemm(const __grid_cons
                     s = 0;
                     sph ^= 1;
                 }
+                if (G.drain || kc == nk - 1) {
+                    mma_commit(afull0 + 8 * buf); // the chunk's (or the tile's) partial is complete
+                    if (++buf == 2) {
+                        buf = 0;
+                        bph ^= 1;
+                    }
+                }
             }
             if (!ok)
                 break;
-            mma_commit(afull0 + 8 * buf); // the tile's accumulator is complete
-            if (++buf == 2) {
-                buf = 0;
-                bph ^= 1;
-            }
         }
         mma_commit(done_bar); // every MMA of this thread has completed before TMEM is freed
         long long t0 = clock64();
@@ -241,30 +261,32 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_leaf_gemm(const __grid_cons
         const int e = threadIdx.x - 128; // TMEM lane = row of the tile
         const uint32_t lane_base = (uint32_t)(32 * (warp - 4)) << 16;
         int buf = 0, bph = 0;
-        float mx = 0.0f;
+        float mx = 0.0f, mx2 = 0.0f; // the two segments' max |M~|
         for (int tile = blockIdx.x; tile < G.ntiles; tile += gridDim.x) {
-            if (!mbar_wait(afull0 + 8 * buf, bph, abort_flag))
-                break;
-            tc_fence_after();
-            const int64_t row = (int64_t)kGemmRows * tile + e;
+            const bool sec = tile >= G.tile2;
+            const int64_t row = (int64_t)kGemmRows * (sec ? tile - G.tile2 : tile) + e;
+            const int64_t nb = sec ? G.nb2 : G.nb;
+            float *const out = sec ? G.out2 : G.out;
+            float *const out_hi = sec ? G.out2_hi : G.out_hi;
+            float *const out_lo = sec ? G.out2_lo : G.out_lo;
+            float mt = 0.0f; // this tile's max |M~|
             int64_t off = -1;
-            if (row < G.rows) {
+            if (row < (sec ? G.rows2 : G.rows)) {
                 if (MODE == 0) {
-                    const int c = (int)(row / G.nb);
+                    const int c = (int)(row / nb);
                     int x, y, z;
-                    demorton3((uint32_t)(row % G.nb), x, y, z);
-                    off = parity_row(x, y, z, c, G.H, 1, G.R) * G.rp;
+                    demorton3((uint32_t)(row % nb), x, y, z);
+                    off = parity_row(x, y, z, c, sec ? G.H2 : G.H, 1, G.R) * G.rp;
                 } else {
                     off = row * G.ldo;
                 }
             }
-            for (int n0 = 0; n0 < G.N; n0 += 16) {
-                float v[16];
-                tmem_ld16(tmem_base + lane_base + (uint32_t)(buf * G.N + n0), v);
+            // columns n0 .. n0 + 15 of this thread's row
+            auto emit = [&](int n0, float *v) {
                 if (MODE == 1 && off >= 0) { // all N columns (zero past p^3): 16-byte stores
 #pragma unroll
                     for (int j = 0; j < 16; j += 4)
-                        *reinterpret_cast<float4 *>(G.out + off + n0 + j) =
+                        *reinterpret_cast<float4 *>(out + off + n0 + j) =
                             make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
                 } else if (off >= 0) {
                     // columns past the level's rank stay as they are (zero)
@@ -276,46 +298,103 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_leaf_gemm(const __grid_cons
                     if (nv == 16) { // 16-byte stores (off and n0 are multiples of 16)
 #pragma unroll
                         for (int j = 0; j < 16; j += 4) {
-                            *reinterpret_cast<float4 *>(G.out + off + n0 + j) =
+                            *reinterpret_cast<float4 *>(out + off + n0 + j) =
                                 make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-                            if (G.out_hi) {
+                            if (out_hi) {
                                 float h[4], l[4];
 #pragma unroll
                                 for (int q = 0; q < 4; ++q) {
                                     h[q] = tf32_rna(v[j + q]);
                                     l[q] = tf32_rna(v[j + q] - h[q]);
                                 }
-                                *reinterpret_cast<float4 *>(G.out_hi + off + n0 + j) = make_float4(h[0], h[1], h[2], h[3]);
-                                *reinterpret_cast<float4 *>(G.out_lo + off + n0 + j) = make_float4(l[0], l[1], l[2], l[3]);
+                                *reinterpret_cast<float4 *>(out_hi + off + n0 + j) = make_float4(h[0], h[1], h[2], h[3]);
+                                *reinterpret_cast<float4 *>(out_lo + off + n0 + j) = make_float4(l[0], l[1], l[2], l[3]);
                             }
                         }
                     } else {
                         for (int j = 0; j < nv; ++j) {
-                            G.out[off + n0 + j] = v[j];
-                            if (G.out_hi) {
+                            out[off + n0 + j] = v[j];
+                            if (out_hi) {
                                 const float h = tf32_rna(v[j]);
-                                G.out_hi[off + n0 + j] = h;
-                                G.out_lo[off + n0 + j] = tf32_rna(v[j] - h);
+                                out_hi[off + n0 + j] = h;
+                                out_lo[off + n0 + j] = tf32_rna(v[j] - h);
                             }
                         }
                     }
 #pragma unroll
                     for (int j = 0; j < 16; ++j)
-                        mx = fmaxf(mx, fabsf(v[j]));
+                        mt = fmaxf(mt, fabsf(v[j]));
+                }
+            };
+            bool ok = true;
+            if (G.drain) {
+                // the tile's K chunks arrive as separate partials: their FP32
+                // sum (round to nearest, in chunk order) keeps the tensor
+                // core's truncating accumulation to one chunk
+                float sum[8][16];
+#pragma unroll
+                for (int b = 0; b < 8; ++b)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        sum[b][j] = 0.0f;
+                for (int kc = 0; kc < nk && ok; ++kc) {
+                    if (!mbar_wait(afull0 + 8 * buf, bph, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+#pragma unroll
+                    for (int b = 0; b < 8; ++b)
+                        if (16 * b < G.N) {
+                            float v[16];
+                            tmem_ld16(tmem_base + lane_base + (uint32_t)(buf * G.N + 16 * b), v);
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                sum[b][j] += v[j];
+                        }
+                    tc_fence_before();
+                    mbar_arrive(aempty0 + 8 * buf);
+                    if (++buf == 2) {
+                        buf = 0;
+                        bph ^= 1;
+                    }
+                }
+                if (!ok)
+                    break;
+#pragma unroll
+                for (int b = 0; b < 8; ++b)
+                    if (16 * b < G.N)
+                        emit(16 * b, sum[b]);
+            } else {
+                if (!mbar_wait(afull0 + 8 * buf, bph, abort_flag))
+                    break;
+                tc_fence_after();
+                for (int n0 = 0; n0 < G.N; n0 += 16) {
+                    float v[16];
+                    tmem_ld16(tmem_base + lane_base + (uint32_t)(buf * G.N + n0), v);
+                    emit(n0, v);
+                }
+                tc_fence_before();
+                mbar_arrive(aempty0 + 8 * buf);
+                if (++buf == 2) {
+                    buf = 0;
+                    bph ^= 1;
                 }
             }
-            tc_fence_before();
-            mbar_arrive(aempty0 + 8 * buf);
-            if (++buf == 2) {
-                buf = 0;
-                bph ^= 1;
-            }
+            if (sec)
+                mx2 = fmaxf(mx2, mt);
+            else
+                mx = fmaxf(mx, mt);
         }
-        if (MODE == 0 && G.maxbits) {
-            for (int o = 16; o > 0; o >>= 1)
+        if (MODE == 0) {
+            for (int o = 16; o > 0; o >>= 1) {
                 mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            if (lane == 0 && mx > 0.0f)
+                mx2 = fmaxf(mx2, __shfl_xor_sync(0xffffffffu, mx2, o));
+            }
+            if (lane == 0 && mx > 0.0f && G.maxbits)
                 atomicMax(G.maxbits, __float_as_uint(mx));
+            if (lane == 0 && mx2 > 0.0f && G.maxbits2)
+                atomicMax(G.maxbits2, __float_as_uint(mx2));
         }
     }
     __syncthreads();
@@ -362,11 +441,11 @@ static cudaError_t run_gemm(GemmLaunch &G, int mode, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_leaf_compress(const LeafCompressArgs &L, cudaStream_t s)
+// the GEMM of one compression (rows = nrhs x nb boxes of one level)
+static cudaError_t compress_setup(GemmLaunch &G, const LeafCompressArgs &L)
 {
     if (!leaf_compress_fits(L.r, L.p3p) || L.nrhs < 1 || L.nb < 1 || L.p3p % 4 != 0 || L.rp % 4 != 0)
         return cudaErrorInvalidValue;
-    GemmLaunch G;
     memset(&G, 0, sizeof(G));
     G.N = (L.r + 15) / 16 * 16;
     G.kchunks = (L.p3p + kGemmK - 1) / kGemmK;
@@ -374,6 +453,8 @@ cudaError_t launch_leaf_compress(const LeafCompressArgs &L, cudaStream_t s)
     G.rows = (int64_t)L.nrhs * L.nb;
     G.slice_rows = G.rows;
     G.ntiles = (int)((G.rows + kGemmRows - 1) / kGemmRows);
+    G.tile2 = G.ntiles;
+    G.drain = G.N <= 128 ? 1 : 0;
     G.idesc = idesc_tf32(kGemmRows, G.N);
     G.tcols = 32;
     while (G.tcols < (uint32_t)(2 * G.N))
@@ -396,16 +477,53 @@ cudaError_t launch_leaf_compress(const LeafCompressArgs &L, cudaStream_t s)
     if (e == cudaSuccess)
         e = tc_encode_2d_f32(&G.blo, L.Vt_lo, (uint64_t)L.p3p, (uint64_t)L.rp, (uint64_t)L.p3p * 4, kGemmK,
                              (uint32_t)G.N);
+    return e;
+}
+
+cudaError_t launch_leaf_compress(const LeafCompressArgs &L, cudaStream_t s)
+{
+    GemmLaunch G;
+    cudaError_t e = compress_setup(G, L);
     if (e != cudaSuccess)
         return e;
     return run_gemm(G, 0, s);
 }
 
-cudaError_t launch_leaf_decompress(const LeafDecompressArgs &L, cudaStream_t s)
+// two levels in one launch when they share the operator (and the shapes):
+// the second level's tiles follow the first's
+cudaError_t launch_leaf_compress2(const LeafCompressArgs &L, const LeafCompressArgs &L2, cudaStream_t s)
+{
+    if (L.Vt_hi != L2.Vt_hi || L.Vt_lo != L2.Vt_lo || L.r != L2.r || L.rp != L2.rp || L.p3p != L2.p3p ||
+        L.nrhs != L2.nrhs || L.R != L2.R || L.status != L2.status) {
+        cudaError_t e = launch_leaf_compress(L, s);
+        return e == cudaSuccess ? launch_leaf_compress(L2, s) : e;
+    }
+    GemmLaunch G;
+    cudaError_t e = compress_setup(G, L);
+    if (e != cudaSuccess || L2.nb < 1)
+        return e == cudaSuccess ? cudaErrorInvalidValue : e;
+    G.rows2 = (int64_t)L2.nrhs * L2.nb;
+    G.slice_rows2 = G.rows2;
+    G.tile2 = G.ntiles;
+    G.ntiles += (int)((G.rows2 + kGemmRows - 1) / kGemmRows);
+    G.nb2 = L2.nb;
+    G.H2 = L2.H;
+    G.out2 = L2.out;
+    G.out2_hi = L2.out_hi;
+    G.out2_lo = L2.out_lo;
+    G.maxbits2 = L2.maxbits;
+    e = tc_encode_2d_f32(&G.a2, L2.M, (uint64_t)L2.p3p, (uint64_t)G.rows2, (uint64_t)L2.p3p * 4, kGemmK,
+                         kGemmRows);
+    if (e != cudaSuccess)
+        return e;
+    return run_gemm(G, 0, s);
+}
+
+// the GEMM of one decompression (rows = the rows of one F~ slice)
+static cudaError_t decompress_setup(GemmLaunch &G, const LeafDecompressArgs &L)
 {
     if (!leaf_decompress_fits(L.rp, L.p3p) || L.rows < 1 || L.slices < 1 || L.rp % 4 != 0)
         return cudaErrorInvalidValue;
-    GemmLaunch G;
     memset(&G, 0, sizeof(G));
     G.N = L.p3p;
     G.kchunks = (L.rp + kGemmK - 1) / kGemmK;
@@ -413,6 +531,8 @@ cudaError_t launch_leaf_decompress(const LeafDecompressArgs &L, cudaStream_t s)
     G.rows = L.rows;
     G.slice_rows = L.slice_rows;
     G.ntiles = (int)((G.rows + kGemmRows - 1) / kGemmRows);
+    G.tile2 = G.ntiles;
+    G.drain = G.N <= 128 ? 1 : 0;
     G.idesc = idesc_tf32(kGemmRows, G.N);
     G.tcols = 32;
     while (G.tcols < (uint32_t)(2 * G.N))
@@ -430,6 +550,36 @@ cudaError_t launch_leaf_decompress(const LeafDecompressArgs &L, cudaStream_t s)
     if (e == cudaSuccess)
         e = tc_encode_2d_f32(&G.blo, L.U_lo, (uint64_t)L.rp, (uint64_t)L.p3p, (uint64_t)L.rp * 4, kGemmK,
                              (uint32_t)G.N);
+    return e;
+}
+
+cudaError_t launch_leaf_decompress(const LeafDecompressArgs &L, cudaStream_t s)
+{
+    GemmLaunch G;
+    cudaError_t e = decompress_setup(G, L);
+    if (e != cudaSuccess)
+        return e;
+    return run_gemm(G, 1, s);
+}
+
+cudaError_t launch_leaf_decompress2(const LeafDecompressArgs &L, const LeafDecompressArgs &L2, cudaStream_t s)
+{
+    if (L.U_hi != L2.U_hi || L.U_lo != L2.U_lo || L.rp != L2.rp || L.p3p != L2.p3p || L.slices != L2.slices ||
+        L.status != L2.status) {
+        cudaError_t e = launch_leaf_decompress(L, s);
+        return e == cudaSuccess ? launch_leaf_decompress(L2, s) : e;
+    }
+    GemmLaunch G;
+    cudaError_t e = decompress_setup(G, L);
+    if (e != cudaSuccess || L2.rows < 1)
+        return e == cudaSuccess ? cudaErrorInvalidValue : e;
+    G.rows2 = L2.rows;
+    G.slice_rows2 = L2.slice_rows;
+    G.tile2 = G.ntiles;
+    G.ntiles += (int)((G.rows2 + kGemmRows - 1) / kGemmRows);
+    G.out2 = L2.out;
+    e = tc_encode_2d_f32(&G.a2, L2.Ft, (uint64_t)L2.rp, (uint64_t)L2.slices * L2.slice_rows, (uint64_t)L2.rp * 4,
+                         kGemmK, kGemmRows);
     if (e != cudaSuccess)
         return e;
     return run_gemm(G, 1, s);

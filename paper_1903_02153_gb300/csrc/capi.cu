@@ -850,7 +850,7 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
         CUDA_TRY(launch_upward(A, p, fs));
         // the compression of level l (the leaves, and level D-1) as a
         // tensor-core GEMM over the multipoles the pass stored in M
-        auto box_compress = [&](int l, const float *M) -> int {
+        auto compress_args = [&](int l, const float *M) {
             const int opl = O.nlev == 1 ? 0 : l - 2;
             LeafCompressArgs L = {};
             L.M = M;
@@ -868,13 +868,15 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
             L.out_lo = P->lev[l].Mt_lo;
             L.maxbits = split16 ? P->a16_max + l : nullptr;
             L.status = P->status;
-            CUDA_TRY(launch_leaf_compress(L, fs));
-            return BBFMM_OK;
+            return L;
         };
-        if (A.Mleaf)
-            PTRY(box_compress(D, A.Mleaf));
-        if (A.Mlev1)
-            PTRY(box_compress(D - 1, A.Mlev1));
+        // both levels in one launch when they share the operator
+        if (A.Mleaf && A.Mlev1)
+            CUDA_TRY(launch_leaf_compress2(compress_args(D, A.Mleaf), compress_args(D - 1, A.Mlev1), fs));
+        else if (A.Mleaf)
+            CUDA_TRY(launch_leaf_compress(compress_args(D, A.Mleaf), fs));
+        else if (A.Mlev1)
+            CUDA_TRY(launch_leaf_compress(compress_args(D - 1, A.Mlev1), fs));
         if (split16) {
             Split16Args S = {};
             S.fmt = P->precision == BBFMM_PREC_FP16X3 ? 0 : 1;
@@ -899,7 +901,7 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
             CUDA_TRY(cudaEventRecord(P->ev[Stage::M2L], fs));
         // downward pass: decompression, L2L and L2P in one launch (the
         // leaves' decompression before it, as a GEMM, when the plan has it)
-        auto box_decompress = [&](int l, float *out) -> int {
+        auto decompress_args = [&](int l, float *out) {
             const int opl = O.nlev == 1 ? 0 : l - 2;
             LeafDecompressArgs L = {};
             L.Ft = P->lev[l].Ft;
@@ -912,13 +914,14 @@ static int matvec_device(bbfmm_plan_impl *P, const float *sigma, float *phi, int
             L.p3p = O.p3p;
             L.out = out;
             L.status = P->status;
-            CUDA_TRY(launch_leaf_decompress(L, fs));
-            return BBFMM_OK;
+            return L;
         };
-        if (A.Fdec1)
-            PTRY(box_decompress(D - 1, P->Fdec1));
-        if (A.Fdec)
-            PTRY(box_decompress(D, P->Fdec));
+        if (A.Fdec && A.Fdec1)
+            CUDA_TRY(launch_leaf_decompress2(decompress_args(D, P->Fdec), decompress_args(D - 1, P->Fdec1), fs));
+        else if (A.Fdec)
+            CUDA_TRY(launch_leaf_decompress(decompress_args(D, P->Fdec), fs));
+        else if (A.Fdec1)
+            CUDA_TRY(launch_leaf_decompress(decompress_args(D - 1, P->Fdec1), fs));
         CUDA_TRY(launch_downward(A, p, fs));
         if (tm) {
             CUDA_TRY(cudaEventRecord(P->ev[Stage::Down], fs));
