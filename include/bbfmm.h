@@ -340,6 +340,18 @@ int bbfmm_set_tuning(bbfmm_plan_t plan, int nrhs, const bbfmm_tuning *tuning);
  */
 int bbfmm_autotune(bbfmm_plan_t plan, int nrhs, void *stream);
 
+/*
+ * bbfmm_matvec_launches: the kernels one matvec with nrhs right-hand sides
+ * launches, counted as the kernel nodes of the CUDA graph that the plan
+ * captured for that nrhs (its first matvec with opts.use_graph and timing
+ * off).  The count follows the tuning in force when the graph was captured;
+ * bbfmm_set_tuning drops the graph.
+ *   launches: receives the count.
+ * Errors: EINVAL (NULL plan or launches, nrhs out of range, no graph captured
+ * for nrhs yet).
+ */
+int bbfmm_matvec_launches(bbfmm_plan_t plan, int nrhs, int *launches);
+
 /* Turn per-stage event timing on (1) or off (0) for later matvecs. */
 int bbfmm_set_timing(bbfmm_plan_t plan, int on);
 

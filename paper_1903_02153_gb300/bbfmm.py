@@ -35,7 +35,7 @@ EXPORTED = ["bbfmm_default_opts", "bbfmm_plan", "bbfmm_matvec", "bbfmm_destroy",
             "bbfmm_last_error", "bbfmm_plan_info", "bbfmm_get_coefficients",
             "bbfmm_get_leaf_cells", "bbfmm_stage_times", "bbfmm_set_timing", "bbfmm_status",
             "bbfmm_sort_points_static", "bbfmm_rand_eig", "bbfmm_plan_targets", "bbfmm_kernel_register",
-            "bbfmm_get_tuning", "bbfmm_set_tuning", "bbfmm_autotune"]
+            "bbfmm_get_tuning", "bbfmm_set_tuning", "bbfmm_autotune", "bbfmm_matvec_launches"]
 
 
 class bbfmm_opts(ctypes.Structure):
@@ -121,6 +121,8 @@ def lib():
             L.bbfmm_set_tuning.restype = i32
             L.bbfmm_autotune.argtypes = [vp, i32, vp]
             L.bbfmm_autotune.restype = i32
+            L.bbfmm_matvec_launches.argtypes = [vp, i32, ctypes.POINTER(i32)]
+            L.bbfmm_matvec_launches.restype = i32
             _lib = L
     return _lib
 
@@ -290,6 +292,14 @@ def bbfmm_set_tuning(plan, nrhs, near_mode, m2l_tile, m2l_stages=0, near_box=Fal
 
 def bbfmm_autotune(plan, nrhs=1, stream=None):
     return _check(lib().bbfmm_autotune(plan, int(nrhs), _stream(stream)))
+
+
+def bbfmm_matvec_launches(plan, nrhs=1):
+    """Kernels one matvec with nrhs right-hand sides launches (the kernel
+    nodes of its captured graph; a graphed matvec of that nrhs must have run)."""
+    c = ctypes.c_int(0)
+    _check(lib().bbfmm_matvec_launches(plan, int(nrhs), ctypes.byref(c)))
+    return c.value
 
 
 def _check_plain(st):

@@ -290,6 +290,7 @@ struct bbfmm_plan_impl {
         cudaGraphExec_t exec = nullptr;
         cudaGraphNode_t gather = nullptr, combine = nullptr;
         cudaKernelNodeParams gp{}, cp{};
+        int nkernels = 0; // kernel nodes: the launches of one matvec
     };
     Graph graphs[1025];
 };

@@ -975,6 +975,7 @@ static int matvec_graph(bbfmm_plan_impl *P, const float *sigma, float *phi, int 
             CUDA_TRY(cudaGraphNodeGetType(node, &type));
             if (type != cudaGraphNodeTypeKernel)
                 continue;
+            ++g.nkernels;
             cudaKernelNodeParams kp;
             if (cudaGraphKernelNodeGetParams(node, &kp) != cudaSuccess) {
                 // kernels of a run-time compiled library (user kernels) do not
@@ -1660,6 +1661,19 @@ int bbfmm_get_tuning(bbfmm_plan_t plan, int nrhs, bbfmm_tuning *out)
     out->measured = t.measured ? 1 : 0;
     out->near_box = t.near_box && !t.near_sym && plan->box_items && nrhs == 1 ? 1 : 0;
     out->leaf_gemm = t.leaf_gemm && plan->Mleaf ? 1 : 0;
+    return BBFMM_OK;
+}
+
+int bbfmm_matvec_launches(bbfmm_plan_t plan, int nrhs, int *launches)
+{
+    g_last_error.clear();
+    PTRY(tuning_args(plan, nrhs));
+    if (!launches)
+        return fail(BBFMM_EINVAL, "launches is NULL");
+    const auto &g = plan->graphs[nrhs];
+    if (!g.exec)
+        return fail(BBFMM_EINVAL, "no matvec graph for nrhs = %d yet", nrhs);
+    *launches = g.nkernels;
     return BBFMM_OK;
 }
 

@@ -212,3 +212,32 @@ def test_leaf_compression_gemm_matches_the_pass(bb, oracle, precision, depth, nr
     print("%s depth %d nrhs %d: GEMM vs pass %.2e, GEMM vs oracle %.2e" % (precision, depth, nrhs, d, e))
     assert d <= (2e-5 if precision == "bf16x3" else 2e-6)
     assert e <= (1e-4 if precision == "bf16x3" else 1e-5)
+
+
+@pytest.mark.parametrize("kid,leaf_launches", [(1, 2), (3, 4)])
+def test_launch_count_of_the_captured_graph(bb, kid, leaf_launches):
+    """bbfmm_matvec_launches counts the kernel nodes of the matvec graph.  The
+    leaf GEMMs add one compression and one decompression launch when the
+    leaves and level D-1 share the operator (1/r: one scaled operator for
+    every level), two each when they do not (exp(-r/ell): an operator per
+    level).  The count is unavailable until a graph is captured, and again
+    after a tuning change drops it."""
+    n = 40_000
+    pts = W.make_points("uniform", n, seed=720)
+    s = sigma_dev(W.uniform_sigma(n, seed=721).astype(np.float32))
+    plan = make(bb, pts, kid, 5, 4, "fp16x3", autotune=False, ell=0.3 if kid == 3 else 1.0)
+    with pytest.raises(bb.BBFMMError):
+        bb.bbfmm_matvec_launches(plan.handle, 1)
+    tile = bb.bbfmm_get_tuning(plan.handle, 1).m2l_tile
+    counts = {}
+    for lg in (True, False):
+        bb.bbfmm_set_tuning(plan.handle, 1, "ordered", tile, 0, leaf_gemm=lg)
+        with pytest.raises(bb.BBFMMError):
+            bb.bbfmm_matvec_launches(plan.handle, 1)
+        plan.matvec(s)
+        counts[lg] = bb.bbfmm_matvec_launches(plan.handle, 1)
+    assert bb.bbfmm_status(plan.handle) == 0
+    plan.close()
+    # gather, upward pass, 16-bit split, near field, M2L, two downward launches, combine
+    assert counts[False] >= 8
+    assert counts[True] - counts[False] == leaf_launches
