@@ -149,6 +149,18 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
     int ax, ay, az;
     demorton3((unsigned)ch.x, ax, ay, az);
     const int nside = 1 << D;
+    // the group's targets t + q nq (a missing one duplicates target t),
+    // loaded while warp 0 looks up the neighbours
+    float2 X[NPK], Y[NPK], Z[NPK];
+#pragma unroll
+    for (int pk = 0; pk < NPK; ++pk) {
+        const int i0 = t + 2 * pk * nq, i1 = i0 + nq;
+        const float4 xa = tpts[ch.y + (active && i0 < nt ? i0 : 0)];
+        const float4 xb = tpts[ch.y + (active && i1 < nt ? i1 : 0)];
+        X[pk] = make_float2(xa.x, xb.x);
+        Y[pk] = make_float2(xa.y, xb.y);
+        Z[pk] = make_float2(xa.z, xb.z);
+    }
 
     // neighbour leaves: start, count (prefix) and cell offset; the target's
     // own leaf comes first, so its sources are staged ahead of the others
@@ -177,17 +189,6 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
     }
     __syncthreads();
     const int ns = nb_pre[27], nown = nb_pre[1]; // all sources; those of the own leaf
-    // the group's targets t + q nq; a missing one duplicates target t
-    float2 X[NPK], Y[NPK], Z[NPK];
-#pragma unroll
-    for (int pk = 0; pk < NPK; ++pk) {
-        const int i0 = t + 2 * pk * nq, i1 = i0 + nq;
-        const float4 xa = tpts[ch.y + (active && i0 < nt ? i0 : 0)];
-        const float4 xb = tpts[ch.y + (active && i1 < nt ? i1 : 0)];
-        X[pk] = make_float2(xa.x, xb.x);
-        Y[pk] = make_float2(xa.y, xb.y);
-        Z[pk] = make_float2(xa.z, xb.z);
-    }
     const float2 floor2 = make_float2(kR2Floor, kR2Floor);
 
     for (int c = 0; c < nrhs; ++c) {
@@ -521,6 +522,20 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
     int ax, ay, az;
     demorton3((unsigned)ch.x, ax, ay, az);
     const int nside = 1 << D;
+    // the thread's targets, loaded while warp 0 looks up the neighbours
+    float2 X[NPK], Y[NPK], Z[NPK], SG[NPK];
+#pragma unroll
+    for (int pk = 0; pk < NPK; ++pk) {
+        const int i0 = t + 2 * pk * nq, i1 = i0 + nq;
+        const bool h0 = active && i0 < nt, h1 = active && i1 < nt;
+        const float4 xa = pts[ch.y + (h0 ? i0 : 0)];
+        const float4 xb = pts[ch.y + (h1 ? i1 : 0)];
+        X[pk] = make_float2(xa.x, xb.x);
+        Y[pk] = make_float2(xa.y, xb.y);
+        Z[pk] = make_float2(xa.z, xb.z);
+        // a missing target (a duplicate of target t) adds nothing to the columns
+        SG[pk] = make_float2(h0 ? sig[ch.y + i0] : 0.0f, h1 ? sig[ch.y + i1] : 0.0f);
+    }
 
     // neighbour leaves in staging order: own (key 0), one way (key 1), both
     // ways (key 2); key 3 is not visited
@@ -569,19 +584,6 @@ __global__ void __launch_bounds__(kP2PThreads, 8)
     }
     __syncthreads();
     const int ns = nb_pre[27], nown = nb_pre[1], nsym0 = s_nsym0;
-    float2 X[NPK], Y[NPK], Z[NPK], SG[NPK];
-#pragma unroll
-    for (int pk = 0; pk < NPK; ++pk) {
-        const int i0 = t + 2 * pk * nq, i1 = i0 + nq;
-        const bool h0 = active && i0 < nt, h1 = active && i1 < nt;
-        const float4 xa = pts[ch.y + (h0 ? i0 : 0)];
-        const float4 xb = pts[ch.y + (h1 ? i1 : 0)];
-        X[pk] = make_float2(xa.x, xb.x);
-        Y[pk] = make_float2(xa.y, xb.y);
-        Z[pk] = make_float2(xa.z, xb.z);
-        // a missing target (a duplicate of target t) adds nothing to the columns
-        SG[pk] = make_float2(h0 ? sig[ch.y + i0] : 0.0f, h1 ? sig[ch.y + i1] : 0.0f);
-    }
     const float2 floor2 = make_float2(kR2Floor, kR2Floor);
     const int NQP = (nq + 3) & ~3; // colpart row stride
     // pass length: with two-way sources PL rows of NQP partials must fit

@@ -387,7 +387,6 @@ __global__ void __launch_bounds__(kThreads, kUpMinBlocks<P>) k_upward(const __gr
     const int c = blockIdx.y;     // right-hand side
     const int64_t leaf = 8 * b + w;
     const int s0 = A.off[leaf], s1 = A.off[leaf + 1];
-    const bool zero = __syncthreads_count(s1 > s0) == 0;
 
     // ---- P2M: warp w makes M of leaf 8b + w (Sec. 2.3 item 1, Def. 2.2)
     {
@@ -450,7 +449,8 @@ __global__ void __launch_bounds__(kThreads, kUpMinBlocks<P>) k_upward(const __gr
             }
         }
     }
-    __syncthreads();
+    // the barrier after P2M also tells whether the box holds points
+    const bool zero = __syncthreads_count(s1 > s0) == 0;
 
     // ---- compress the leaves (or leave them to the compression GEMM; a box
     // without points keeps the zeros its rows were given at plan time)
@@ -481,9 +481,12 @@ __global__ void __launch_bounds__(kThreads, kUpMinBlocks<P>) k_upward(const __gr
     int64_t box = b;
     for (int l = D - 2; l >= 2; --l) {
         const int64_t par = box >> 3;
-        __threadfence(); // this thread's stores of the level-(l+1) box are visible device-wide
+        // the barrier orders every thread's stores of the level-(l+1) box
+        // before thread 0's fence, which makes them visible device-wide
+        // before its arrival is counted
         __syncthreads();
         if (t == 0) {
+            __threadfence();
             int *cnt = A.count[l] + par * A.R + c;
             const int before = atomicAdd(cnt, 1);
             sLast = before == 7;
@@ -983,9 +986,12 @@ __global__ void __launch_bounds__(kThreads) k_upward_wide(const __grid_constant_
     int64_t box = B;
     for (int l = D - 3; l >= 2; --l) {
         const int64_t par = box >> 3;
-        __threadfence(); // this thread's stores of the level-(l+1) box are visible device-wide
+        // the barrier orders every thread's stores of the level-(l+1) box
+        // before thread 0's fence, which makes them visible device-wide
+        // before its arrival is counted
         __syncthreads();
         if (t == 0) {
+            __threadfence();
             int *cnt = A.count[l] + par * A.R + c;
             const int before = atomicAdd(cnt, 1);
             sLast = before == 7;
@@ -1471,9 +1477,12 @@ __global__ void __launch_bounds__(kThreads) k_upward_rc(const __grid_constant__ 
     int64_t box = b;
     for (int l = D - 2; l >= 2; --l) {
         const int64_t par = box >> 3;
-        __threadfence(); // this thread's stores of the level-(l+1) box are visible device-wide
+        // the barrier orders every thread's stores of the level-(l+1) box
+        // before thread 0's fence, which makes them visible device-wide
+        // before its arrival is counted
         __syncthreads();
         if (t == 0) {
+            __threadfence();
             int *cnt = A.count[l] + par * A.R + c0; // one counter per (box, chunk)
             const int before = atomicAdd(cnt, 1);
             sLast = before == 7;
