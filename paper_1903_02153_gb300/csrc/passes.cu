@@ -580,6 +580,17 @@ __device__ void l2p_small(const PassArgs &A, const float *F, int s0, int s1, int
     }
 }
 
+// 4-byte asynchronous copies global -> shared (the block waits for its own
+// groups, then a barrier makes every thread's copies visible)
+__device__ __forceinline__ void cp_async4(float *dst, const float *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 template <int P>
 __global__ void __launch_bounds__(kThreads) k_downward(const __grid_constant__ PassArgs A)
 {
@@ -599,6 +610,50 @@ __global__ void __launch_bounds__(kThreads) k_downward(const __grid_constant__ P
     if (!A.keep && A.toff[8 * b] == A.toff[8 * b + 8])
         return; // no targets below this box
 
+    if (A.Ftop && A.Fdec1 && A.Fdec) {
+        // everything this block reads from the earlier launches, copied in at
+        // once: the parent's F (first launch), then the own box's and the 8
+        // leaves' decompressed far fields (GEMM), which land while the
+        // parent's F is carried down to the own box
+        float *sOwnF = sY;  // [P3]: sY is free until the 8-child L2L
+        float *sDec = sFt;  // [8][P3]: sFt is not used on this path
+        __shared__ int64_t sRows[9];
+        const float *Fp = A.Ftop + ((b >> 3) * A.nrhs + c) * (int64_t)P3;
+        for (int i = t; i < P3; i += kThreads)
+            cp_async4(sPar + i, Fp + i);
+        cp_async_commit();
+        if (t < 9) {
+            const int64_t box = t < 8 ? 8 * b + t : b;
+            int x, y, z;
+            demorton3((uint32_t)box, x, y, z);
+            sRows[t] = parity_row(x, y, z, c, 1 << (t < 8 ? D - 1 : D - 2), 0, A.R) * A.p3p;
+        }
+        __syncthreads();
+        for (int i = t; i < P3; i += kThreads)
+            cp_async4(sOwnF + i, A.Fdec1 + sRows[8] + i);
+        for (int q = t; q < 8 * P3; q += kThreads) {
+            const int o = q / P3;
+            cp_async4(sDec + q, A.Fdec + sRows[o] + (q - o * P3));
+        }
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        l2l1<P>(A.T, sPar, (int)(b & 7), sOne, sPar); // parent -> own box (level D-1 >= 3)
+        cp_async_wait<0>();
+        __syncthreads();
+        for (int i = t; i < P3; i += kThreads) {
+            const float f = sPar[i] + sOwnF[i];
+            sPar[i] = f;
+            if (A.keep)
+                A.F[D - 1][(b * A.nrhs + c) * P3 + i] = f;
+        }
+        __syncthreads();
+        l2l8<P>(A.T, sPar, sY, sZ, sMT);
+        for (int q = t; q < 8 * P3; q += kThreads) {
+            const int o = q / P3, i = q - o * P3;
+            sMT[i * 8 + o] += sDec[q];
+        }
+    } else {
     // ---- ancestors at levels 2 .. D-1 (the last one is the block's own box);
     // with Ftop the parent's F comes from the first launch
     int l0 = 2;
@@ -707,6 +762,7 @@ __global__ void __launch_bounds__(kThreads) k_downward(const __grid_constant__ P
                     sMT[i * 8 + 4 * h + q] += acc[q];
             }
         }
+    }
     }
     __syncthreads();
     if (A.keep)
