@@ -88,6 +88,10 @@ def test_null_handles(lib):
     assert L.bbfmm_destroy(None) == 0
     assert L.bbfmm_matvec(None, None, None, 1, None) == lib.BBFMM_EINVAL
     assert L.bbfmm_plan_info(None, None) == lib.BBFMM_EINVAL
+    c = ctypes.c_int(-1)
+    assert L.bbfmm_matvec_launches(None, 1, ctypes.byref(c)) == lib.BBFMM_EINVAL and c.value == -1
+    t = lib.bbfmm_tuning()
+    assert L.bbfmm_get_tuning(None, 1, ctypes.byref(t)) == lib.BBFMM_EINVAL
 
 
 def test_plan_targets_rejects_bad_arguments(lib):
