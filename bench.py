@@ -536,7 +536,7 @@ def run_ours(args, rank, world, local):
                              interp=interp, near=args.near)
         d6["accuracy"] = accuracy_check(pts, sig_host, phi6, dict(c, depth=6), nodes=interp)
         d6info = d6.pop("_info")
-        # the depth-6 M2L against the same peak (its DRAM traffic when captured for this build)
+        # the depth-6 M2L against the same peak (its DRAM traffic while the kernel sources match the capture)
         d6["m2l_roofline"] = roofline(precision, d6info, nrhs, d6["stages_ms"]["m2l"], {"sm_mhz": None}, torch, dev,
                                       "uniform-1M-p5-d6", interp, c["p"])
         extra["depth6"] = d6
